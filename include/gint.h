@@ -1,0 +1,145 @@
+/*
+ * gint.h -- C ABI of libgint: uniform-grid integration of numerical atomic
+ * orbitals (NAOs) at the Gamma point on one GB300 GPU (sm_103a).
+ *
+ * The operations are those of the paper's Sec. 3.3.1 ("Uniform Grid Integration
+ * for Usual Quantities"): with periodised orbitals
+ *     Phi_mu(r) = sum_R phi_mu(r - tau_I - R),   phi_mu = f_{I l zeta}(|r|) Y_lm(r^)   (Eqs. 1-2, k = 0)
+ * on the grid r_g = (i/n1) a1 + (j/n2) a2 + (k/n3) a3 with weight w = |det A| / (n1 n2 n3):
+ *     density         rho_g    = sum_{mu nu} D_{mu nu} Phi_mu(r_g) Phi_nu(r_g)
+ *     local H         H_{mu nu} = sum_g w V_g Phi_mu(r_g) Phi_nu(r_g)
+ *     local Pulay     F_I      = - dE/dtau_I,  E = sum_g w V_g rho_g  (V fixed)
+ *
+ * Conventions
+ *   - Units: Bohr, Hartree.  Cell rows are the lattice vectors a1, a2, a3.
+ *   - Grid arrays (rho, V) are float64, C order [n1][n2][n3] (k fastest), device memory.
+ *   - Orbitals of an atom follow its species' radial list in the given order; each radial
+ *     with angular momentum l contributes 2l+1 orbitals, m ordered 0, +1, -1, +2, -2
+ *     (real, orthonormal Y_lm without the Condon-Shortley sign; l <= 2).
+ *   - Radial tables hold R(r_k) (including the r^l factor) and R'(r_k) at r_k = k dr; the
+ *     library interpolates with cubic Hermite polynomials; R = 0 for r >= rc.
+ *   - Matrices (D in, H out) are stored as atom-pair blocks.  Pair p = (I, J) exists when
+ *     some lattice image of J lies closer to I than rcut(I) + rcut(J) + skin; both (I, J) and
+ *     (J, I) are stored.  Block p is row-major norb(I) x norb(J) at element offset
+ *     pair_off[p] of a float64 device array of nblock_elems elements.  Pairs are sorted by
+ *     I, then J.  D must be symmetric (block (J, I) = block (I, J)^T).
+ *
+ * Ownership and streams
+ *   - gint_create copies everything it needs; the caller's host arrays may be freed after.
+ *   - The handle owns its device state (tables, neighbour lists, workspace).  Compute calls
+ *     take caller-owned device pointers (non-owning) and allocate nothing.
+ *   - Compute calls are asynchronous on the given CUDA stream (NULL: legacy default stream).
+ *     Calls on one handle must not overlap (they share the handle's workspace).
+ *
+ * Errors: every function returns GINT_OK (0) or a negative GINT_E* code; no exceptions
+ * cross the ABI.  gint_strerror() names a code.
+ */
+#ifndef GINT_H
+#define GINT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GINT_OK 0
+#define GINT_EINVAL (-1)     /* bad argument or descriptor */
+#define GINT_ENOMEM (-2)     /* device allocation failed */
+#define GINT_ECUDA (-3)      /* a CUDA runtime call failed */
+#define GINT_ETIMEDOUT (-4)  /* a bounded device wait gave up */
+#define GINT_EDEVICE (-5)    /* a kernel reported an inconsistency through the device error word */
+#define GINT_ECAPACITY (-6)  /* a brick holds more orbitals/atoms than the kernels support */
+#define GINT_ESKIN (-7)      /* atoms moved so that a pair outside the block set now overlaps */
+#define GINT_EUNSUPPORTED (-8) /* precision mode or feature not available on this device */
+
+/* Precision of the brick contractions.  Cross-brick reductions, the charge and energy
+ * reductions and the per-atom force reduction are float64 in every mode. */
+#define GINT_FP64 0   /* float64 everywhere */
+#define GINT_FP32 1   /* float32 orbitals and SIMT contractions */
+#define GINT_TF32X3 2 /* float32 orbitals, tensor-core contractions with 3-term TF32 splitting */
+#define GINT_TF32X1 3 /* float32 orbitals, single-pass TF32 tensor-core contractions (fastest, ~1e-3) */
+
+typedef struct gint_radial {
+  int l;            /* angular momentum, 0..2 */
+  int npts;         /* number of knots (>= 2) */
+  double dr;        /* knot spacing (> 0) */
+  double rc;        /* support radius: R = 0 for r >= rc; rc <= (npts-1) dr */
+  const double *f;  /* host [npts]: R(k dr) including r^l */
+  const double *df; /* host [npts]: R'(k dr) */
+} gint_radial;
+
+typedef struct gint_species {
+  int nradial;               /* number of radial functions (1..16) */
+  const gint_radial *radial; /* host [nradial] */
+} gint_species;
+
+typedef struct gint_desc {
+  double cell[9];          /* row-major a1, a2, a3 (Bohr) */
+  int natoms;              /* >= 1 */
+  const double *pos;       /* host [natoms][3] Cartesian (Bohr) */
+  const int *species;      /* host [natoms], 0..nspecies-1 */
+  int nspecies;            /* 1..8 */
+  const gint_species *sp;  /* host [nspecies] */
+  int n1, n2, n3;          /* grid (each >= 1) */
+  double skin;             /* extra pair-set margin (Bohr, >= 0) for later gint_set_positions */
+} gint_desc;
+
+typedef struct gint_handle gint_handle;
+
+/* Builds the handle on the current CUDA device: radial tables, the grid-brick -> atom
+ * neighbour lists (device kernels), the atom-pair block set and the workspace (the
+ * paper's GintInfo / MeshGrid / BigGrid set-up, Sec. 3.3.1 and Fig. 2).  Synchronous.
+ * Returns GINT_EINVAL for a malformed descriptor, GINT_ENOMEM / GINT_ECUDA on CUDA failure,
+ * GINT_ECAPACITY if a brick exceeds the kernels' limits.  *out is NULL on failure. */
+int gint_create(const gint_desc *desc, gint_handle **out);
+
+/* Frees the handle and all its device memory.  NULL is accepted. */
+int gint_destroy(gint_handle *h);
+
+/* Sizes of the block layout: total orbitals, number of pairs, float64 elements of a
+ * block array.  Any output pointer may be NULL. */
+int gint_layout(const gint_handle *h, int *norb, int *npairs, long long *nblock_elems);
+
+/* Copies the pair list to host arrays: pair_IJ [npairs][2], pair_off [npairs + 1]. */
+int gint_pairs(const gint_handle *h, int *pair_IJ, long long *pair_off);
+
+/* Work statistics of the current geometry (host outputs, any may be NULL):
+ *   W         = sum_g n_g^2, n_g = orbitals whose support covers grid point g (exact,
+ *               ordered pairs; the algorithmic work of one rho or H pass);
+ *   W_exec    = sum over bricks of 128 * norb(brick)^2 (the padded work a brick kernel sees);
+ *   nbricks, max orbitals of a brick, max atoms of a brick. */
+int gint_stats(const gint_handle *h, double *W, double *W_exec, long long *nbricks, int *max_brick_orb,
+               int *max_brick_atoms);
+
+/* Replaces the atom positions from a DEVICE array [natoms][3] and rebuilds the neighbour
+ * lists on the device.  The pair set stays fixed: GINT_ESKIN if a pair outside it now
+ * overlaps.  Synchronises the stream. */
+int gint_set_positions(gint_handle *h, const double *pos_dev, void *stream);
+
+/* Density pass: rho [n1 n2 n3] (device, overwritten) from D blocks (device). */
+int gint_rho(gint_handle *h, int precision, const double *D_blocks, double *rho, void *stream);
+
+/* Local-Hamiltonian pass: H blocks (device, overwritten) from V [n1 n2 n3] (device). */
+int gint_vlocal(gint_handle *h, int precision, const double *V, double *H_blocks, void *stream);
+
+/* Local Pulay forces F [natoms][3] (device, overwritten) = -dE/dtau for E = sum_g w V rho.
+ * If rho is not NULL the density is written as well (same pass). */
+int gint_force(gint_handle *h, int precision, const double *D_blocks, const double *V, double *F, double *rho,
+               void *stream);
+
+/* Float64 reductions on the device, written to out_dev[0] (device):
+ *   V != NULL: w * sum_g V_g rho_g  (the energy E);   V == NULL: w * sum_g rho_g (N_e = Tr(DS)). */
+int gint_grid_dot(gint_handle *h, const double *V, const double *rho, double *out_dev, void *stream);
+
+/* Float64 block-array dot product sum_p sum_e A[e] B[e] written to out_dev[0] (e.g. Tr(DH)). */
+int gint_block_dot(gint_handle *h, const double *A_blocks, const double *B_blocks, double *out_dev, void *stream);
+
+/* Grid weight w = |det A| / (n1 n2 n3). */
+double gint_weight(const gint_handle *h);
+
+/* Static message for a status code. */
+const char *gint_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GINT_H */

@@ -1,0 +1,413 @@
+// gint_capi.cu -- the extern "C" boundary of libgint (declared in include/gint.h).
+//
+// Set-up mirrors the paper's GintInfo (Sec. 3.3.1, Fig. 2): geometry, the fine grid and its
+// coarse blocks ("bricks"), the brick -> atom neighbour relation (built on the device), and
+// the atom-pair block layout of the matrices.  Compute calls dispatch to the SIMT (FP64,
+// FP32) or tensor-core (TF32x3, TF32x1) kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gint_handle.cuh"
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+int dalloc(T **p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  if (cudaMalloc((void **)p, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return GINT_ENOMEM;
+  }
+  return GINT_OK;
+}
+
+template <typename T>
+void dfree(T *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_all(gint_handle *h) {
+  dfree(h->tab64); dfree(h->tab32);
+  dfree(h->pos_dev); dfree(h->species_dev);
+  dfree(h->pair_row_dev); dfree(h->pair_col_dev); dfree(h->pair_off_dev); dfree(h->pair_T_dev);
+  dfree(h->n_at); dfree(h->n_ent); dfree(h->n_orb);
+  dfree(h->b_at_off); dfree(h->b_ent_off); dfree(h->b_pair_off); dfree(h->scan_out);
+  dfree(h->s_atom); dfree(h->s_col); dfree(h->s_ent); dfree(h->e_shift); dfree(h->b_pair);
+  dfree(h->D32); dfree(h->Dsplit); dfree(h->red); dfree(h->scal); dfree(h->err_word);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  h->own_stream = nullptr;
+}
+
+void inverse3(const double a[9], double inv[9], double *det) {
+  double d = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+             a[2] * (a[3] * a[7] - a[4] * a[6]);
+  inv[0] = (a[4] * a[8] - a[5] * a[7]) / d;
+  inv[1] = (a[2] * a[7] - a[1] * a[8]) / d;
+  inv[2] = (a[1] * a[5] - a[2] * a[4]) / d;
+  inv[3] = (a[5] * a[6] - a[3] * a[8]) / d;
+  inv[4] = (a[0] * a[8] - a[2] * a[6]) / d;
+  inv[5] = (a[2] * a[3] - a[0] * a[5]) / d;
+  inv[6] = (a[3] * a[7] - a[4] * a[6]) / d;
+  inv[7] = (a[1] * a[6] - a[0] * a[7]) / d;
+  inv[8] = (a[0] * a[4] - a[1] * a[3]) / d;
+  *det = d;
+}
+
+double host_min_image(const GGeom &g, const double *pos, int I, int J, double limit) {
+  double d0[3], u[3];
+  for (int d = 0; d < 3; ++d) d0[d] = pos[3 * J + d] - pos[3 * I + d];
+  for (int d = 0; d < 3; ++d) u[d] = d0[0] * g.inv[d] + d0[1] * g.inv[3 + d] + d0[2] * g.inv[6 + d];
+  double best = 1e300;
+  int lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = (int)std::ceil(-u[d] - limit * g.reach[d]);
+    hi[d] = (int)std::floor(-u[d] + limit * g.reach[d]);
+  }
+  for (int n0 = lo[0]; n0 <= hi[0]; ++n0)
+    for (int n1 = lo[1]; n1 <= hi[1]; ++n1)
+      for (int n2 = lo[2]; n2 <= hi[2]; ++n2) {
+        double x[3];
+        for (int d = 0; d < 3; ++d) x[d] = d0[d] + n0 * g.cell[d] + n1 * g.cell[3 + d] + n2 * g.cell[6 + d];
+        best = std::min(best, std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
+      }
+  return best;
+}
+
+int validate(const gint_desc *d) {
+  if (!d || d->natoms < 1 || !d->pos || !d->species || d->nspecies < 1 || d->nspecies > GINT_MAX_SPECIES || !d->sp)
+    return GINT_EINVAL;
+  if (d->n1 < 1 || d->n2 < 1 || d->n3 < 1 || !(d->skin >= 0)) return GINT_EINVAL;
+  int nrad = 0;
+  for (int s = 0; s < d->nspecies; ++s) {
+    const gint_species &S = d->sp[s];
+    if (S.nradial < 1 || S.nradial > 16 || !S.radial) return GINT_EINVAL;
+    int norb = 0;
+    for (int k = 0; k < S.nradial; ++k) {
+      const gint_radial &R = S.radial[k];
+      if (R.l < 0 || R.l > 2 || R.npts < 2 || !(R.dr > 0) || !(R.rc > 0) || !R.f || !R.df) return GINT_EINVAL;
+      if (R.rc > (R.npts - 1) * R.dr * (1 + 1e-12)) return GINT_EINVAL;
+      norb += 2 * R.l + 1;
+    }
+    if (norb > GINT_MAX_ORB_ATOM) return GINT_EINVAL;
+    nrad += S.nradial;
+  }
+  if (nrad > GINT_MAX_RADIAL) return GINT_EINVAL;
+  for (int a = 0; a < d->natoms; ++a) {
+    if (d->species[a] < 0 || d->species[a] >= d->nspecies) return GINT_EINVAL;
+    for (int c = 0; c < 3; ++c)
+      if (!std::isfinite(d->pos[3 * a + c])) return GINT_EINVAL;
+  }
+  double inv[9], det;
+  inverse3(d->cell, inv, &det);
+  if (!(std::fabs(det) > 1e-12) || !std::isfinite(det)) return GINT_EINVAL;
+  return GINT_OK;
+}
+
+#define TRY(x)              \
+  do {                      \
+    int rc_ = (x);          \
+    if (rc_) {              \
+      free_all(h);          \
+      delete h;             \
+      return rc_;           \
+    }                       \
+  } while (0)
+#define TRYCU(x) TRY((x) == cudaSuccess ? GINT_OK : GINT_ECUDA)
+
+}  // namespace
+
+int gint_reserve_nbr(gint_handle *h) {
+  if (h->nslots + 1 > h->cap_slots) {
+    dfree(h->s_atom); dfree(h->s_col); dfree(h->s_ent);
+    long long cap = h->nslots + h->nslots / 4 + 64;
+    if (dalloc(&h->s_atom, cap) || dalloc(&h->s_col, cap) || dalloc(&h->s_ent, cap + 1)) return GINT_ENOMEM;
+    h->cap_slots = cap;
+  }
+  if (h->nent > h->cap_ent) {
+    dfree(h->e_shift);
+    long long cap = h->nent + h->nent / 4 + 64;
+    if (dalloc(&h->e_shift, 3 * cap)) return GINT_ENOMEM;
+    h->cap_ent = cap;
+  }
+  if (h->npairtab > h->cap_pairtab) {
+    dfree(h->b_pair);
+    long long cap = h->npairtab + h->npairtab / 4 + 64;
+    if (dalloc(&h->b_pair, cap)) return GINT_ENOMEM;
+    h->cap_pairtab = cap;
+  }
+  return GINT_OK;
+}
+
+extern "C" {
+
+int gint_create(const gint_desc *d, gint_handle **out) {
+  if (!out) return GINT_EINVAL;
+  *out = nullptr;
+  int v = validate(d);
+  if (v) return v;
+  gint_handle *h = new (std::nothrow) gint_handle();
+  if (!h) return GINT_ENOMEM;
+  TRYCU(cudaGetDevice(&h->device));
+  TRYCU(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+  cudaStream_t st = h->own_stream;
+  GGeom &g = h->geom;
+  std::memcpy(g.cell, d->cell, sizeof(g.cell));
+  double det;
+  inverse3(g.cell, g.inv, &det);
+  for (int c = 0; c < 3; ++c)
+    g.reach[c] = std::sqrt(g.inv[c] * g.inv[c] + g.inv[3 + c] * g.inv[3 + c] + g.inv[6 + c] * g.inv[6 + c]);
+  g.n1 = d->n1; g.n2 = d->n2; g.n3 = d->n3;
+  g.ngrid = (long long)d->n1 * d->n2 * d->n3;
+  g.w = std::fabs(det) / (double)g.ngrid;
+  g.nbi = (d->n1 + GINT_BI - 1) / GINT_BI;
+  g.nbj = (d->n2 + GINT_BJ - 1) / GINT_BJ;
+  g.nbk = (d->n3 + GINT_BK - 1) / GINT_BK;
+  g.nbricks = (long long)g.nbi * g.nbj * g.nbk;
+  g.natoms = d->natoms;
+  g.nspecies = d->nspecies;
+  // radial tables
+  std::vector<double2> t64;
+  int r = 0;
+  for (int s = 0; s < d->nspecies; ++s) {
+    const gint_species &S = d->sp[s];
+    GSpecies &GS = g.sp[s];
+    GS.nrad = S.nradial;
+    GS.rad0 = r;
+    GS.norb = 0;
+    GS.rcut = 0;
+    for (int k = 0; k < S.nradial; ++k, ++r) {
+      const gint_radial &R = S.radial[k];
+      GRadial &GR = g.rad[r];
+      GR.l = R.l;
+      GR.npts = R.npts;
+      GR.off = (int)t64.size();
+      GR.dr = R.dr;
+      GR.inv_dr = 1.0 / R.dr;
+      GR.rc = R.rc;
+      GR.rc2 = R.rc * R.rc;
+      for (int i = 0; i < R.npts; ++i) t64.push_back(make_double2(R.f[i], R.df[i]));
+      GS.norb += 2 * R.l + 1;
+      GS.rcut = std::max(GS.rcut, R.rc);
+    }
+    GS.rcut2 = GS.rcut * GS.rcut;
+    h->max_species_norb = std::max(h->max_species_norb, GS.norb);
+  }
+  g.nrad = r;
+  h->nknots = (long long)t64.size();
+  std::vector<float2> t32(t64.size());
+  for (size_t i = 0; i < t64.size(); ++i) t32[i] = make_float2((float)t64[i].x, (float)t64[i].y);
+  TRY(dalloc(&h->tab64, t64.size()));
+  TRY(dalloc(&h->tab32, t32.size()));
+  TRYCU(cudaMemcpy(h->tab64, t64.data(), t64.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  TRYCU(cudaMemcpy(h->tab32, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  // atoms
+  h->pos_host.assign(d->pos, d->pos + 3 * (size_t)d->natoms);
+  h->species_host.assign(d->species, d->species + d->natoms);
+  h->atom_norb.resize(d->natoms);
+  h->atom_off.resize(d->natoms + 1);
+  h->atom_off[0] = 0;
+  for (int a = 0; a < d->natoms; ++a) {
+    h->atom_norb[a] = g.sp[d->species[a]].norb;
+    h->atom_off[a + 1] = h->atom_off[a] + h->atom_norb[a];
+  }
+  h->norb = h->atom_off[d->natoms];
+  TRY(dalloc(&h->pos_dev, 3 * (size_t)d->natoms));
+  TRY(dalloc(&h->species_dev, (size_t)d->natoms));
+  TRYCU(cudaMemcpy(h->pos_dev, h->pos_host.data(), h->pos_host.size() * sizeof(double), cudaMemcpyHostToDevice));
+  TRYCU(cudaMemcpy(h->species_dev, h->species_host.data(), d->natoms * sizeof(int), cudaMemcpyHostToDevice));
+  // pair set: some image of J closer to I than rcut(I) + rcut(J) + skin
+  h->pair_row.assign(d->natoms + 1, 0);
+  h->pair_col.clear();
+  h->pair_off.assign(1, 0);
+  for (int I = 0; I < d->natoms; ++I) {
+    for (int J = 0; J < d->natoms; ++J) {
+      double lim = g.sp[d->species[I]].rcut + g.sp[d->species[J]].rcut;
+      if (host_min_image(g, d->pos, I, J, lim + d->skin) < lim + d->skin) {
+        h->pair_col.push_back(J);
+        h->pair_off.push_back(h->pair_off.back() + (long long)h->atom_norb[I] * h->atom_norb[J]);
+      }
+    }
+    h->pair_row[I + 1] = (int)h->pair_col.size();
+  }
+  h->npairs = (int)h->pair_col.size();
+  h->nblock = h->pair_off.back();
+  std::vector<int> pairT(h->npairs);
+  for (int I = 0; I < d->natoms; ++I)
+    for (int p = h->pair_row[I]; p < h->pair_row[I + 1]; ++p) {
+      int J = h->pair_col[p];
+      auto b = h->pair_col.begin() + h->pair_row[J], e = h->pair_col.begin() + h->pair_row[J + 1];
+      auto it = std::lower_bound(b, e, I);
+      pairT[p] = (it != e && *it == I) ? (int)(it - h->pair_col.begin()) : -1;
+      if (pairT[p] < 0) TRY(GINT_EINVAL);  // the relation is symmetric by construction
+    }
+  TRY(dalloc(&h->pair_row_dev, h->pair_row.size()));
+  TRY(dalloc(&h->pair_col_dev, h->pair_col.size()));
+  TRY(dalloc(&h->pair_off_dev, h->pair_off.size()));
+  TRY(dalloc(&h->pair_T_dev, pairT.size()));
+  TRYCU(cudaMemcpy(h->pair_row_dev, h->pair_row.data(), h->pair_row.size() * sizeof(int), cudaMemcpyHostToDevice));
+  TRYCU(cudaMemcpy(h->pair_col_dev, h->pair_col.data(), h->pair_col.size() * sizeof(int), cudaMemcpyHostToDevice));
+  TRYCU(cudaMemcpy(h->pair_off_dev, h->pair_off.data(), h->pair_off.size() * sizeof(long long),
+                   cudaMemcpyHostToDevice));
+  TRYCU(cudaMemcpy(h->pair_T_dev, pairT.data(), pairT.size() * sizeof(int), cudaMemcpyHostToDevice));
+  // neighbour structure
+  const size_t nb = (size_t)g.nbricks;
+  TRY(dalloc(&h->n_at, nb)); TRY(dalloc(&h->n_ent, nb)); TRY(dalloc(&h->n_orb, nb));
+  TRY(dalloc(&h->b_at_off, nb + 1)); TRY(dalloc(&h->b_ent_off, nb + 1)); TRY(dalloc(&h->b_pair_off, nb + 1));
+  TRY(dalloc(&h->scan_out, 8));
+  TRY(dalloc(&h->red, 1024));
+  TRY(dalloc(&h->scal, 16));
+  TRY(dalloc(&h->err_word, 4));
+  TRY(gint_build_neighbours(h, st));
+  // workspace
+  TRY(dalloc(&h->D32, (size_t)h->nblock));
+  TRYCU(cudaStreamSynchronize(st));
+  *out = h;
+  return GINT_OK;
+}
+
+int gint_destroy(gint_handle *h) {
+  if (!h) return GINT_OK;
+  DeviceGuard guard(h->device);
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+  return GINT_OK;
+}
+
+int gint_layout(const gint_handle *h, int *norb, int *npairs, long long *nblock_elems) {
+  if (!h) return GINT_EINVAL;
+  if (norb) *norb = h->norb;
+  if (npairs) *npairs = h->npairs;
+  if (nblock_elems) *nblock_elems = h->nblock;
+  return GINT_OK;
+}
+
+int gint_pairs(const gint_handle *h, int *pair_IJ, long long *pair_off) {
+  if (!h) return GINT_EINVAL;
+  if (pair_IJ) {
+    for (int I = 0; I < h->geom.natoms; ++I)
+      for (int p = h->pair_row[I]; p < h->pair_row[I + 1]; ++p) {
+        pair_IJ[2 * p] = I;
+        pair_IJ[2 * p + 1] = h->pair_col[p];
+      }
+  }
+  if (pair_off) std::memcpy(pair_off, h->pair_off.data(), h->pair_off.size() * sizeof(long long));
+  return GINT_OK;
+}
+
+int gint_stats(const gint_handle *h, double *W, double *W_exec, long long *nbricks, int *max_brick_orb,
+               int *max_brick_atoms) {
+  if (!h) return GINT_EINVAL;
+  if (W) *W = h->W;
+  if (W_exec) *W_exec = h->W_exec;
+  if (nbricks) *nbricks = h->geom.nbricks;
+  if (max_brick_orb) *max_brick_orb = h->max_brick_orb;
+  if (max_brick_atoms) *max_brick_atoms = h->max_brick_atoms;
+  return GINT_OK;
+}
+
+int gint_set_positions(gint_handle *h, const double *pos_dev, void *stream) {
+  if (!h || !pos_dev) return GINT_EINVAL;
+  DeviceGuard guard(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(h->pos_dev, pos_dev, 3 * sizeof(double) * h->geom.natoms, cudaMemcpyDeviceToDevice, st) !=
+      cudaSuccess)
+    return GINT_ECUDA;
+  int rc = gint_build_neighbours(h, st);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(h->pos_host.data(), h->pos_dev, 3 * sizeof(double) * h->geom.natoms, cudaMemcpyDeviceToHost,
+                      st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GINT_ECUDA;
+  return GINT_OK;
+}
+
+static int check_precision(int precision) {
+  return (precision == GINT_FP64 || precision == GINT_FP32 || precision == GINT_TF32X3 || precision == GINT_TF32X1)
+             ? GINT_OK
+             : GINT_EINVAL;
+}
+
+int gint_rho(gint_handle *h, int precision, const double *D_blocks, double *rho, void *stream) {
+  if (!h || !D_blocks || !rho) return GINT_EINVAL;
+  if (check_precision(precision)) return GINT_EINVAL;
+  DeviceGuard guard(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == GINT_FP64 || precision == GINT_FP32)
+    return gint_simt_rho(h, precision == GINT_FP64, D_blocks, rho, nullptr, nullptr, st);
+  return gint_tc_rho(h, precision, D_blocks, rho, nullptr, nullptr, st);
+}
+
+int gint_vlocal(gint_handle *h, int precision, const double *V, double *H_blocks, void *stream) {
+  if (!h || !V || !H_blocks) return GINT_EINVAL;
+  if (check_precision(precision)) return GINT_EINVAL;
+  DeviceGuard guard(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(H_blocks, 0, sizeof(double) * (size_t)h->nblock, st) != cudaSuccess) return GINT_ECUDA;
+  if (precision == GINT_FP64 || precision == GINT_FP32)
+    return gint_simt_vlocal(h, precision == GINT_FP64, V, H_blocks, st);
+  return gint_tc_vlocal(h, precision, V, H_blocks, st);
+}
+
+int gint_force(gint_handle *h, int precision, const double *D_blocks, const double *V, double *F, double *rho,
+               void *stream) {
+  if (!h || !D_blocks || !V || !F) return GINT_EINVAL;
+  if (check_precision(precision)) return GINT_EINVAL;
+  DeviceGuard guard(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(F, 0, sizeof(double) * 3 * (size_t)h->geom.natoms, st) != cudaSuccess) return GINT_ECUDA;
+  if (precision == GINT_FP64 || precision == GINT_FP32)
+    return gint_simt_rho(h, precision == GINT_FP64, D_blocks, rho, V, F, st);
+  return gint_tc_rho(h, precision, D_blocks, rho, V, F, st);
+}
+
+int gint_grid_dot(gint_handle *h, const double *V, const double *rho, double *out_dev, void *stream) {
+  if (!h || !rho || !out_dev) return GINT_EINVAL;
+  DeviceGuard guard(h->device);
+  return gint_reduce_dot(h, rho, V, h->geom.ngrid, h->geom.w, out_dev, (cudaStream_t)stream);
+}
+
+int gint_block_dot(gint_handle *h, const double *A, const double *B, double *out_dev, void *stream) {
+  if (!h || !A || !B || !out_dev) return GINT_EINVAL;
+  DeviceGuard guard(h->device);
+  return gint_reduce_dot(h, A, B, h->nblock, 1.0, out_dev, (cudaStream_t)stream);
+}
+
+double gint_weight(const gint_handle *h) { return h ? h->geom.w : 0.0; }
+
+const char *gint_strerror(int code) {
+  switch (code) {
+    case GINT_OK: return "success";
+    case GINT_EINVAL: return "invalid argument";
+    case GINT_ENOMEM: return "device allocation failed";
+    case GINT_ECUDA: return "CUDA runtime error";
+    case GINT_ETIMEDOUT: return "bounded device wait timed out";
+    case GINT_EDEVICE: return "device-side consistency check failed";
+    case GINT_ECAPACITY: return "brick exceeds kernel capacity";
+    case GINT_ESKIN: return "atoms moved beyond the pair-set skin";
+    case GINT_EUNSUPPORTED: return "unsupported precision or feature";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,235 @@
+"""ctypes binding of libgint (the C ABI declared in include/gint.h).
+
+Argument marshalling only: every step of the density, local-Hamiltonian and force
+passes runs in the CUDA library.  PyTorch provides device memory and streams.
+Importing this module fails loudly if libgint.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgint.so")
+
+FP64, FP32, TF32X3, TF32X1 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3, "tf32x1": TF32X1}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libgint.so is not built ({LIB_PATH}); run `python -m paper_2603_21835_gb300.build`")
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class GintError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.gint_strerror(code).decode()
+        super().__init__(f"{where}: {msg} (code {code})")
+        self.code = code
+
+
+class _Radial(ctypes.Structure):
+    _fields_ = [("l", ctypes.c_int), ("npts", ctypes.c_int), ("dr", ctypes.c_double), ("rc", ctypes.c_double),
+                ("f", ctypes.c_void_p), ("df", ctypes.c_void_p)]
+
+
+class _Species(ctypes.Structure):
+    _fields_ = [("nradial", ctypes.c_int), ("radial", ctypes.POINTER(_Radial))]
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("cell", ctypes.c_double * 9), ("natoms", ctypes.c_int), ("pos", ctypes.c_void_p),
+                ("species", ctypes.c_void_p), ("nspecies", ctypes.c_int), ("sp", ctypes.POINTER(_Species)),
+                ("n1", ctypes.c_int), ("n2", ctypes.c_int), ("n3", ctypes.c_int), ("skin", ctypes.c_double)]
+
+
+_vp, _ll, _i, _d = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int, ctypes.c_double
+_lib.gint_strerror.restype = ctypes.c_char_p
+_lib.gint_strerror.argtypes = [_i]
+_lib.gint_create.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(_vp)]
+_lib.gint_destroy.argtypes = [_vp]
+_lib.gint_layout.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_ll)]
+_lib.gint_pairs.argtypes = [_vp, _vp, _vp]
+_lib.gint_stats.argtypes = [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_ll), ctypes.POINTER(_i),
+                            ctypes.POINTER(_i)]
+_lib.gint_set_positions.argtypes = [_vp, _vp, _vp]
+_lib.gint_rho.argtypes = [_vp, _i, _vp, _vp, _vp]
+_lib.gint_vlocal.argtypes = [_vp, _i, _vp, _vp, _vp]
+_lib.gint_force.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp]
+_lib.gint_grid_dot.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.gint_block_dot.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.gint_weight.restype = _d
+_lib.gint_weight.argtypes = [_vp]
+
+C_ABI_SYMBOLS = ("gint_create", "gint_destroy", "gint_layout", "gint_pairs", "gint_stats", "gint_set_positions",
+                 "gint_rho", "gint_vlocal", "gint_force", "gint_grid_dot", "gint_block_dot", "gint_weight",
+                 "gint_strerror")
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise GintError(code, where)
+
+
+def _dptr(t: Optional[torch.Tensor], dtype=torch.float64, numel: Optional[int] = None):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor, got {t.dtype} on {t.device}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Gint:
+    """One geometry (cell, atoms, species radial tables, grid) resident on the current GPU."""
+
+    def __init__(self, system, skin: float = 0.0):
+        rad_keep, sp_arr = [], (_Species * len(system.sp))()
+        for s, sp in enumerate(system.sp):
+            arr = (_Radial * len(sp.radials))()
+            for k, r in enumerate(sp.radials):
+                f = np.ascontiguousarray(r.f, dtype=np.float64)
+                df = np.ascontiguousarray(r.df, dtype=np.float64)
+                rad_keep += [f, df]
+                arr[k] = _Radial(int(r.l), int(f.shape[0]), float(r.dr), float(r.rc), f.ctypes.data, df.ctypes.data)
+            rad_keep.append(arr)
+            sp_arr[s] = _Species(len(sp.radials), arr)
+        pos = np.ascontiguousarray(system.pos, dtype=np.float64)
+        spc = np.ascontiguousarray(system.species, dtype=np.int32)
+        d = _Desc()
+        d.cell[:] = [float(x) for x in np.asarray(system.cell, dtype=np.float64).reshape(-1)]
+        d.natoms, d.pos, d.species = int(pos.shape[0]), pos.ctypes.data, spc.ctypes.data
+        d.nspecies, d.sp = len(system.sp), sp_arr
+        d.n1, d.n2, d.n3 = (int(x) for x in system.grid)
+        d.skin = float(skin)
+        h = ctypes.c_void_p()
+        _check(_lib.gint_create(ctypes.byref(d), ctypes.byref(h)), "gint_create")
+        self._h = h
+        self.grid = tuple(int(x) for x in system.grid)
+        self.ngrid = int(np.prod(self.grid))
+        self.natoms = int(pos.shape[0])
+        norb, npairs, nblock = _i(), _i(), _ll()
+        _check(_lib.gint_layout(h, ctypes.byref(norb), ctypes.byref(npairs), ctypes.byref(nblock)), "gint_layout")
+        self.norb, self.npairs, self.nblock = norb.value, npairs.value, nblock.value
+        self.pair_IJ = np.zeros((self.npairs, 2), dtype=np.int32)
+        self.pair_off = np.zeros(self.npairs + 1, dtype=np.int64)
+        _check(_lib.gint_pairs(h, self.pair_IJ.ctypes.data, self.pair_off.ctypes.data), "gint_pairs")
+        norbs = np.array([sum(2 * r.l + 1 for r in system.sp[s].radials) for s in system.species], dtype=np.int64)
+        self.atom_norb = norbs
+        self.atom_off = np.concatenate([[0], np.cumsum(norbs)]).astype(np.int64)
+        self.weight = float(_lib.gint_weight(h))
+
+    # -- bookkeeping
+    def stats(self) -> dict:
+        W, Wx, nb, mo, ma = _d(), _d(), _ll(), _i(), _i()
+        _check(_lib.gint_stats(self._h, ctypes.byref(W), ctypes.byref(Wx), ctypes.byref(nb), ctypes.byref(mo),
+                               ctypes.byref(ma)), "gint_stats")
+        return dict(W=W.value, W_exec=Wx.value, nbricks=nb.value, max_brick_orb=mo.value, max_brick_atoms=ma.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.gint_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- compute (device tensors in, device tensors out)
+    def rho(self, D_blocks: torch.Tensor, precision: int = FP64, out: Optional[torch.Tensor] = None,
+            stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.grid, dtype=torch.float64, device=D_blocks.device)
+        _check(_lib.gint_rho(self._h, int(precision), _dptr(D_blocks, numel=self.nblock),
+                             _dptr(out, numel=self.ngrid), _stream(stream)), "gint_rho")
+        return out
+
+    def vlocal(self, V: torch.Tensor, precision: int = FP64, out: Optional[torch.Tensor] = None,
+               stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.nblock, dtype=torch.float64, device=V.device)
+        _check(_lib.gint_vlocal(self._h, int(precision), _dptr(V, numel=self.ngrid), _dptr(out, numel=self.nblock),
+                                _stream(stream)), "gint_vlocal")
+        return out
+
+    def force(self, D_blocks: torch.Tensor, V: torch.Tensor, precision: int = FP64,
+              out: Optional[torch.Tensor] = None, rho_out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.natoms, 3), dtype=torch.float64, device=V.device)
+        _check(_lib.gint_force(self._h, int(precision), _dptr(D_blocks, numel=self.nblock),
+                               _dptr(V, numel=self.ngrid), _dptr(out, numel=3 * self.natoms),
+                               _dptr(rho_out, numel=self.ngrid) if rho_out is not None else None, _stream(stream)),
+               "gint_force")
+        return out
+
+    def grid_dot(self, V: Optional[torch.Tensor], rho: torch.Tensor, out: Optional[torch.Tensor] = None,
+                 stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(1, dtype=torch.float64, device=rho.device)
+        _check(_lib.gint_grid_dot(self._h, _dptr(V, numel=self.ngrid) if V is not None else None,
+                                  _dptr(rho, numel=self.ngrid), _dptr(out), _stream(stream)), "gint_grid_dot")
+        return out
+
+    def block_dot(self, A: torch.Tensor, B: torch.Tensor, out: Optional[torch.Tensor] = None,
+                  stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(1, dtype=torch.float64, device=A.device)
+        _check(_lib.gint_block_dot(self._h, _dptr(A, numel=self.nblock), _dptr(B, numel=self.nblock), _dptr(out),
+                                   _stream(stream)), "gint_block_dot")
+        return out
+
+    def set_positions(self, pos: torch.Tensor, stream=None):
+        _check(_lib.gint_set_positions(self._h, _dptr(pos, numel=3 * self.natoms), _stream(stream)),
+               "gint_set_positions")
+
+    # -- layout helpers (host, numpy): dense <-> atom-pair blocks
+    def dense_to_blocks(self, M: np.ndarray) -> np.ndarray:
+        out = np.empty(self.nblock, dtype=np.float64)
+        ao = self.atom_off
+        for p, (I, J) in enumerate(self.pair_IJ):
+            out[self.pair_off[p]:self.pair_off[p + 1]] = M[ao[I]:ao[I + 1], ao[J]:ao[J + 1]].reshape(-1)
+        return out
+
+    def blocks_to_dense(self, blocks: np.ndarray) -> np.ndarray:
+        M = np.zeros((self.norb, self.norb))
+        ao = self.atom_off
+        for p, (I, J) in enumerate(self.pair_IJ):
+            nI, nJ = ao[I + 1] - ao[I], ao[J + 1] - ao[J]
+            M[ao[I]:ao[I + 1], ao[J]:ao[J + 1]] = blocks[self.pair_off[p]:self.pair_off[p + 1]].reshape(nI, nJ)
+        return M
+
+    def blocks_from_coefficients(self, C: np.ndarray) -> np.ndarray:
+        """D blocks of D = C C^T computed pair row by pair row (no dense D)."""
+        out = np.empty(self.nblock, dtype=np.float64)
+        ao = self.atom_off
+        starts = np.searchsorted(self.pair_IJ[:, 0], np.arange(self.natoms + 1))
+        for I in range(self.natoms):
+            p0, p1 = starts[I], starts[I + 1]
+            Js = self.pair_IJ[p0:p1, 1]
+            rows = np.concatenate([np.arange(ao[J], ao[J + 1]) for J in Js])
+            blk = C[ao[I]:ao[I + 1]] @ C[rows].T  # (nI, sum nJ)
+            col = 0
+            for q, J in enumerate(Js):
+                nJ = ao[J + 1] - ao[J]
+                out[self.pair_off[p0 + q]:self.pair_off[p0 + q + 1]] = blk[:, col:col + nJ].reshape(-1)
+                col += nJ
+        return out
+
+    def block_index(self, I: int, J: int) -> int:
+        lo = np.searchsorted(self.pair_IJ[:, 0], I)
+        hi = np.searchsorted(self.pair_IJ[:, 0], I + 1)
+        k = np.searchsorted(self.pair_IJ[lo:hi, 1], J)
+        if k >= hi - lo or self.pair_IJ[lo + k, 1] != J:
+            return -1
+        return int(lo + k)

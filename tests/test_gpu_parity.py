@@ -1,0 +1,173 @@
+"""GPU parity: the CUDA passes against the FP64 oracle on the same seeded inputs.
+
+Error metric (max-norm relative): err(X) = max|X - X_ref| / max|X_ref| for rho and H; forces
+in absolute Ha/Bohr.  Tolerances: FP64 path 1e-12 (relative; forces 1e-11 of max|F|),
+tensor-core TF32x3 path 1e-6 (rho, H) and 1e-5 Ha/Bohr (forces), float32 SIMT 1e-5.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2603_21835_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "tf32x3": 1e-6}
+FTOL_ABS = {"fp64": None, "fp32": 1e-5, "tf32x3": 1e-5}
+
+
+def _rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max())
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    from paper_2603_21835_gb300 import gint  # noqa: F401  (fails loudly without the library)
+
+    return torch
+
+
+def _run(G, g, D_blocks, V, prec, torch):
+    Dd = torch.from_numpy(D_blocks).cuda()
+    Vd = torch.from_numpy(np.ascontiguousarray(V.reshape(-1))).cuda()
+    rho = g.rho(Dd, prec).cpu().numpy()
+    H = g.vlocal(Vd, prec).cpu().numpy()
+    rho2 = torch.empty(g.grid, dtype=torch.float64, device="cuda")
+    F = g.force(Dd, Vd, prec, rho_out=rho2).cpu().numpy()
+    torch.cuda.synchronize()
+    return rho, H, F, rho2.cpu().numpy()
+
+
+class Case:
+    def __init__(self, w, torch):
+        from paper_2603_21835_gb300 import gint as G
+
+        self.w = w
+        self.o = Oracle(w.system)
+        self.g = G.Gint(w.system)
+        self.G = G
+        self.rho = self.o.rho(w.D)
+        self.H = self.o.vlocal(w.V)
+        self.F = self.o.force(w.D, w.V)
+        self.Db = self.g.dense_to_blocks(w.D)
+
+
+@pytest.fixture(scope="module")
+def si8(torch_cuda):
+    return Case(inputs.config_workload("si8_g48"), torch_cuda)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_si8_parity(si8, torch_cuda, prec):
+    c = si8
+    p = c.G.PRECISIONS[prec]
+    rho, H, F, rho2 = _run(c.G, c.g, c.Db, c.w.V, p, torch_cuda)
+    Hd = c.g.blocks_to_dense(H)
+    assert _rel(rho, c.rho) <= TOL[prec]
+    assert _rel(rho2, c.rho) <= TOL[prec]
+    assert _rel(Hd, c.H) <= TOL[prec]
+    if prec == "fp64":
+        assert np.abs(F - c.F).max() <= 1e-11 * np.abs(c.F).max()
+    else:
+        assert np.abs(F - c.F).max() <= FTOL_ABS[prec]
+
+
+def test_si8_work_count(si8):
+    st = si8.g.stats()
+    W, _ = si8.o.count_pairs()
+    assert st["W"] == W
+    assert st["W_exec"] >= W
+
+
+def test_si8_identities_on_device(si8, torch_cuda):
+    """sum_g w rho = Tr(DS) and sum_g w V rho = Tr(DH), all reductions on the device in FP64."""
+    torch = torch_cuda
+    c = si8
+    Dd = torch.from_numpy(c.Db).cuda()
+    V = torch.from_numpy(c.w.V.reshape(-1)).cuda()
+    one = torch.ones_like(V)
+    rho = c.g.rho(Dd)
+    S = c.g.vlocal(one)
+    H = c.g.vlocal(V)
+    ne = c.g.grid_dot(None, rho).item()
+    trDS = c.g.block_dot(Dd, S).item()
+    E = c.g.grid_dot(V, rho).item()
+    trDH = c.g.block_dot(Dd, H).item()
+    assert ne == pytest.approx(trDS, rel=1e-12)
+    assert E == pytest.approx(trDH, rel=1e-12)
+    Hn = c.g.blocks_to_dense(H.cpu().numpy())
+    assert np.abs(Hn - Hn.T).max() <= 1e-14 * np.abs(Hn).max()
+
+
+def _small_case(torch, system, seed=3, nb=6):
+    from paper_2603_21835_gb300 import gint as G
+
+    rng = np.random.default_rng(seed)
+    o = Oracle(system)
+    C = rng.normal(size=(o.norb, nb)) / 4
+    D = C @ C.T
+    V = inputs.draw_V(rng, system.cell, system.grid).reshape(-1)
+    g = G.Gint(system)
+    rho, H, F, _ = _run(G, g, g.dense_to_blocks(D), V, G.FP64, torch)
+    assert _rel(rho.reshape(-1), o.rho(D).reshape(-1)) <= 1e-12
+    assert _rel(g.blocks_to_dense(H), o.vlocal(V)) <= 1e-12
+    Fo = o.force(D, V)
+    assert np.abs(F - Fo).max() <= 1e-11 * np.abs(Fo).max()
+    return g
+
+
+def test_ragged_grid(torch_cuda):
+    """Grid not divisible by the 4x4x8 brick: partial bricks on every axis."""
+    w = inputs.si_workload((1, 1, 1), (21, 18, 27), seed=2, disp_sigma=0.07)
+    _small_case(torch_cuda, w.system)
+
+
+def test_triclinic_cell_with_folded_images(torch_cuda):
+    """fcc primitive cell smaller than the orbital diameter: many images of one atom fold."""
+    sp = inputs.si_species()
+    a = inputs.SI_A
+    cell = np.array([[0, a / 2, a / 2], [a / 2, 0, a / 2], [a / 2, a / 2, 0]])
+    pos = np.array([[0.0, 0.0, 0.0], [a / 4, a / 4, a / 4]]) + 0.031
+    sysm = inputs.System(cell=cell, pos=pos, species=np.zeros(2, np.int32), sp=[sp], grid=(20, 20, 24))
+    _small_case(torch_cuda, sysm)
+
+
+def test_vacuum_and_two_species(torch_cuda):
+    """Water molecules in a box: empty bricks, two species with different orbital counts."""
+    w = inputs.h2o_workload(2, seed=5, box=16.0, grid=(40, 40, 40))
+    _small_case(torch_cuda, w.system)
+
+
+@pytest.fixture(scope="module")
+def si64(torch_cuda):
+    w = inputs.config_workload("si64_g96")
+    o = Oracle(w.system)
+    from paper_2603_21835_gb300 import gint as G
+
+    g = G.Gint(w.system)
+    rng = np.random.default_rng(123)
+    idx = rng.choice(o.ngrid, 3000, replace=False)
+    return dict(w=w, o=o, g=g, G=G, idx=idx, rho=o.rho(w.D, idx), Db=g.dense_to_blocks(w.D))
+
+
+@pytest.mark.parametrize("prec", ["fp64"])
+def test_si64_sampled_parity(si64, torch_cuda, prec):
+    torch = torch_cuda
+    s = si64
+    g, o, w = s["g"], s["o"], s["w"]
+    p = s["G"].PRECISIONS[prec]
+    Dd = torch.from_numpy(s["Db"]).cuda()
+    Vd = torch.from_numpy(w.V.reshape(-1)).cuda()
+    rho = g.rho(Dd, p).cpu().numpy().reshape(-1)
+    assert _rel(rho[s["idx"]], s["rho"]) <= TOL[prec]
+    H = g.vlocal(Vd, p).cpu().numpy()
+    scale = None
+    for (I, J) in [(0, 0), (0, 5), (3, 17), (63, 2), (40, 41)]:
+        k = g.block_index(I, J)
+        assert k >= 0
+        ref = o.vlocal_block(w.V, I, J)
+        blk = H[g.pair_off[k]:g.pair_off[k + 1]].reshape(ref.shape)
+        scale = max(scale or 0, np.abs(ref).max())
+        assert np.abs(blk - ref).max() <= TOL[prec] * np.abs(ref).max() * 10
