@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark: grid-integration throughput (density + local Hamiltonian) on one GB300.
+
+One step = one density pass and one local-Hamiltonian pass over the whole grid of the
+workload (inputs resident in HBM).  Work unit: ordered orbital pairs per grid point,
+W = sum_g n_g^2 per pass, so one step is 2W pair updates; the metric is Gpt-pair/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32x3|fp64|fp32|tf32x1]
+                  [--workload si64_g96|si8_g48|si512_g192] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per rank, launched by torch.distributed.run): the
+path needs no exchange between GPUs; value is the total work of all ranks over the slowest
+rank's time.  --impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gint Gpt-pair/s (rho+H_loc) mixed vs FP64 on GB300 at <=1e-6 rel err; p50/p99 ms"
+UNIT = "Gpt-pair/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# nominal dense ratios to bf16 (2.25 PF): tf32 1.1 PF; float64 1.25 TF (GB300)
+TF32_PER_BF16 = 1.1 / 2.25
+FP64_NOMINAL_TFLOPS = 1.25
+FP32_SIMT_TFLOPS_PER_GHZ = 152 * 128 * 2 / 1e3  # 152 SMs x 128 FP32 lanes x 2 flops per clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp64", "fp32", "tf32x1"])
+    ap.add_argument("--workload", default="si64_g96")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ oracle (CPU) baseline
+def oracle_sample(workload_name: str, target_s: float, seed: int = 7):
+    """Times the FP64 oracle (rho + H over a random subset of grid points) on the host cores.
+    Returns (Gpt-pair/s, threads, description)."""
+    from oracle.oracle import Oracle
+    from paper_2603_21835_gb300 import inputs
+
+    w = inputs.config_workload(workload_name, dense_D=True)
+    o = Oracle(w.system)
+    rng = np.random.default_rng(seed)
+    n = 4000
+    while True:
+        idx = np.sort(rng.choice(o.ngrid, n, replace=False))
+        t0 = time.perf_counter()
+        o.rho(w.D, idx)
+        o.vlocal(w.V, idx)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * target_s or n >= o.ngrid:
+            break
+        n = int(min(o.ngrid, n * max(2.0, 0.9 * target_s / max(dt, 1e-3))))
+    Wsample, _ = o.count_pairs(idx)
+    value = 2.0 * Wsample / dt / 1e9
+    desc = (f"FP64 oracle rho + H_loc over {n} random grid points of {workload_name} "
+            f"({n / o.ngrid:.3%} of the grid, 2W = {2 * Wsample:.3e} pair updates) in {dt:.1f} s")
+    return value, Oracle.num_threads(), desc, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle.oracle import build
+
+    build()
+    vals, cores, desc = [], None, ""
+    per_step = max(5.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
+    for k in range(args.warmup + args.steps):
+        v, cores, desc, dt = oracle_sample(args.workload, per_step, seed=100 + k)
+        if k >= args.warmup:
+            vals.append((v, dt))
+    value = float(np.mean([v for v, _ in vals]))
+    ms = float(np.mean([dt for _, dt in vals]) * 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "precision": "fp64-cpu-oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ our arm
+KERNEL_LAUNCHES = {  # kernels of ours per step (rho pass + H pass); memsets are not kernels
+    "fp64": 2, "fp32": 3, "tf32x3": None, "tf32x1": None,
+}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2603_21835_gb300 import gint as G
+    from paper_2603_21835_gb300 import inputs
+
+    prec = G.PRECISIONS[args.precision]
+    w = inputs.config_workload(args.workload, dense_D=False)
+    g = G.Gint(w.system)
+    st = g.stats()
+    W = st["W"]
+    Db_host = g.blocks_from_coefficients(w.C)
+    V_host = np.ascontiguousarray(w.V.reshape(-1))
+    Db = torch.from_numpy(Db_host).to(dev)
+    V = torch.from_numpy(V_host).to(dev)
+    rho = torch.empty(g.grid, dtype=torch.float64, device=dev)
+    H = torch.empty(g.nblock, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    def step():
+        g.rho(Db, prec, out=rho)
+        g.vlocal(V, prec, out=H)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evh = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        evr[k][0].record(stream)
+        g.rho(Db, prec, out=rho)
+        evr[k][1].record(stream)
+        evh[k][0].record(stream)
+        g.vlocal(V, prec, out=H)
+        evh[k][1].record(stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+    t_steps = [a.elapsed_time(b) for a, b in ev]
+    t_rho = [a.elapsed_time(b) for a, b in evr]
+    t_h = [a.elapsed_time(b) for a, b in evh]
+    tot = torch.tensor([sum(t_steps)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    ms_per_step = tot.item() / args.steps
+    value = world * 2.0 * W / (ms_per_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (per-launch mean over the timed region)
+    peaks, peak_kind = load_peaks()
+    mr, mh = statistics.mean(t_rho), statistics.mean(t_h)
+    dom, tdom = ("rho", mr) if mr >= mh else ("vlocal", mh)
+    flops = W  # one FMA per unordered orbital pair per grid point (D, H symmetric)
+    if args.precision in ("tf32x3", "tf32x1"):
+        bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        peak = bf16 * TF32_PER_BF16
+        bound, punit, pdesc = "tensor", "TFLOP/s", f"tf32 dense = {peak_kind} bf16 sustained x 1.1/2.25"
+    elif args.precision == "fp64":
+        peak = FP64_NOMINAL_TFLOPS
+        bound, punit, pdesc = "alu", "TFLOP/s", "fp64 nominal 1.25 TFLOP/s (GB300)"
+    else:
+        mhz = clocks.get("sm_mhz") or 2070.0
+        peak = FP32_SIMT_TFLOPS_PER_GHZ * mhz / 1e3
+        bound, punit, pdesc = "alu", "TFLOP/s", "fp32 SIMT 152 SMs x 128 lanes x 2 flops x sampled SM clock"
+    achieved = flops / (tdom * 1e-3) / 1e12
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": punit,
+                "frac": achieved / peak, "traffic": None, "peak_source": pdesc,
+                "algorithmic_flops_per_launch": flops}
+
+    # end to end through the public API: pinned host in, pinned host out, copies in the timed region
+    e2e = None
+    if not args.no_e2e:
+        Dh = torch.from_numpy(Db_host).pin_memory()
+        Vh = torch.from_numpy(V_host).pin_memory()
+        rho_h = torch.empty(g.grid, dtype=torch.float64).pin_memory()
+        H_h = torch.empty(g.nblock, dtype=torch.float64).pin_memory()
+        Dd = torch.empty_like(Db)
+        Vd = torch.empty_like(V)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        te = []
+        for k in range(args.steps + 1):
+            flush.fill_(float(k))
+            e0.record(stream)
+            Dd.copy_(Dh, non_blocking=True)
+            Vd.copy_(Vh, non_blocking=True)
+            g.rho(Dd, prec, out=rho)
+            g.vlocal(Vd, prec, out=H)
+            rho_h.copy_(rho, non_blocking=True)
+            H_h.copy_(H, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if k > 0:
+                te.append(e0.elapsed_time(e1))
+        tt = torch.tensor([sum(te)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_e2e = tt.item() / len(te)
+        e2e = {"value": world * 2.0 * W / (ms_e2e * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_e2e,
+               "h2d_bytes_per_step": int(Db.numel() * 8 + V.numel() * 8),
+               "d2h_bytes_per_step": int(rho.numel() * 8 + H.numel() * 8)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, desc, _ = oracle_sample(args.workload, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    launches = KERNEL_LAUNCHES.get(args.precision)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "tf32x3": "tf32x3+f64",
+                                      "tf32x1": "tf32+f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "natoms": g.natoms, "norb": g.norb, "grid": list(g.grid),
+                   "precision": args.precision, "W_pairs_per_pass": W, "W_exec_padded": st["W_exec"],
+                   "nbricks": st["nbricks"], "max_brick_orb": st["max_brick_orb"], "l2": "flushed (256 MB write)",
+                   "parallelism": f"replicas{world}"},
+        "ms_rho": statistics.mean(t_rho), "ms_vlocal": statistics.mean(t_h),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": (launches * args.steps) if launches is not None else None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
