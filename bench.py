@@ -5,7 +5,7 @@ One step = one density pass and one local-Hamiltonian pass over the whole grid o
 workload (inputs resident in HBM).  Work unit: ordered orbital pairs per grid point,
 W = sum_g n_g^2 per pass, so one step is 2W pair updates; the metric is Gpt-pair/s.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32x3|fp64|fp32|tf32x1]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f16x3|fp64|fp32|f16x1]
                   [--workload si64_g96|si8_g48|si512_g192] [--impl ours|reference]
 
 N > 1 runs N independent replicas (one per rank, launched by torch.distributed.run): the
@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp64", "fp32", "tf32x1"])
+    ap.add_argument("--precision", default="f16x3", choices=["f16x3", "fp64", "fp32", "f16x1"])
     ap.add_argument("--workload", default="si64_g96")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -171,7 +171,7 @@ def run_reference(args):
 
 # ------------------------------------------------------------------------------ our arm
 KERNEL_LAUNCHES = {  # kernels of ours per step (rho pass + H pass); memsets are not kernels
-    "fp64": 2, "fp32": 3, "tf32x3": None, "tf32x1": None,
+    "fp64": 2, "fp32": 3, "f16x3": None, "f16x1": None,
 }
 
 
@@ -252,7 +252,7 @@ def main():
     mr, mh = statistics.mean(t_rho), statistics.mean(t_h)
     dom, tdom = ("rho", mr) if mr >= mh else ("vlocal", mh)
     flops = W  # one FMA per unordered orbital pair per grid point (D, H symmetric)
-    if args.precision in ("tf32x3", "tf32x1"):
+    if args.precision in ("f16x3", "f16x1"):
         bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         peak = bf16 * TF32_PER_BF16
         bound, punit, pdesc = "tensor", "TFLOP/s", f"tf32 dense = {peak_kind} bf16 sustained x 1.1/2.25"
@@ -309,8 +309,8 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "tf32x3": "tf32x3+f64",
-                                      "tf32x1": "tf32+f64"}[args.precision],
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "f16x3": "f16x3+f64",
+                                      "f16x1": "f16+f64"}[args.precision],
         "data": "synthetic",
         "config": {"workload": args.workload, "natoms": g.natoms, "norb": g.norb, "grid": list(g.grid),
                    "precision": args.precision, "W_pairs_per_pass": W, "W_exec_padded": st["W_exec"],

@@ -53,10 +53,12 @@ extern "C" {
 
 /* Precision of the brick contractions.  Cross-brick reductions, the charge and energy
  * reductions and the per-atom force reduction are float64 in every mode. */
-#define GINT_FP64 0   /* float64 everywhere */
-#define GINT_FP32 1   /* float32 orbitals and SIMT contractions */
-#define GINT_TF32X3 2 /* float32 orbitals, tensor-core contractions with 3-term TF32 splitting */
-#define GINT_TF32X1 3 /* float32 orbitals, single-pass TF32 tensor-core contractions (fastest, ~1e-3) */
+#define GINT_FP64 0  /* float64 everywhere (CUDA cores) */
+#define GINT_FP32 1  /* float32 orbitals and CUDA-core contractions */
+#define GINT_F16X3 2 /* float32 orbitals; tensor-core contractions on operands split into two float16
+                        parts (hi + lo, 22 significant bits, power-of-two scaled), products
+                        hi*hi + hi*lo + lo*hi, float32 accumulation */
+#define GINT_F16X1 3 /* as GINT_F16X3 with the hi*hi product only (about 3 significant digits) */
 
 typedef struct gint_radial {
   int l;            /* angular momentum, 0..2 */
@@ -132,6 +134,16 @@ int gint_grid_dot(gint_handle *h, const double *V, const double *rho, double *ou
 
 /* Float64 block-array dot product sum_p sum_e A[e] B[e] written to out_dev[0] (e.g. Tr(DH)). */
 int gint_block_dot(gint_handle *h, const double *A_blocks, const double *B_blocks, double *out_dev, void *stream);
+
+/* Waits for the stream and reports errors that kernels recorded in the handle's device error
+ * word since the last check (GINT_ETIMEDOUT for a bounded wait that gave up, GINT_ECAPACITY,
+ * GINT_EDEVICE); clears the word.  Compute calls are asynchronous, so such errors surface here. */
+int gint_sync(gint_handle *h, void *stream);
+
+/* Diagnostic: runs one tcgen05 TF32 MMA (M=128, N=n, K=8) per operand layout used by the brick
+ * kernels on exactly representable integer data and returns the largest absolute deviation from
+ * the exact product in *max_err (host).  n in {16, ..., 256}, multiple of 16.  Synchronous. */
+int gint_tc_selftest(int n, double *max_err);
 
 /* Grid weight w = |det A| / (n1 n2 n3). */
 double gint_weight(const gint_handle *h);

@@ -3,7 +3,7 @@
 // Set-up mirrors the paper's GintInfo (Sec. 3.3.1, Fig. 2): geometry, the fine grid and its
 // coarse blocks ("bricks"), the brick -> atom neighbour relation (built on the device), and
 // the atom-pair block layout of the matrices.  Compute calls dispatch to the SIMT (FP64,
-// FP32) or tensor-core (TF32x3, TF32x1) kernels.
+// FP32) or tensor-core (F16x3, F16x1) kernels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,11 +49,12 @@ void dfree(T *&p) {
 void free_all(gint_handle *h) {
   dfree(h->tab64); dfree(h->tab32);
   dfree(h->pos_dev); dfree(h->species_dev);
-  dfree(h->pair_row_dev); dfree(h->pair_col_dev); dfree(h->pair_off_dev); dfree(h->pair_T_dev);
+  dfree(h->pair_row_dev); dfree(h->pair_col_dev); dfree(h->pair_off_dev); dfree(h->pair_T_dev); dfree(h->pair_I_dev);
   dfree(h->n_at); dfree(h->n_ent); dfree(h->n_orb);
   dfree(h->b_at_off); dfree(h->b_ent_off); dfree(h->b_pair_off); dfree(h->scan_out);
   dfree(h->s_atom); dfree(h->s_col); dfree(h->s_ent); dfree(h->e_shift); dfree(h->b_pair);
-  dfree(h->D32); dfree(h->Dsplit); dfree(h->red); dfree(h->scal); dfree(h->err_word);
+  dfree(h->D32); dfree(h->work_ctr); dfree(h->red); dfree(h->scal); dfree(h->err_word);
+  gint_tc_free(h);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   h->own_stream = nullptr;
 }
@@ -205,12 +206,21 @@ int gint_create(const gint_desc *d, gint_handle **out) {
       GR.inv_dr = 1.0 / R.dr;
       GR.rc = R.rc;
       GR.rc2 = R.rc * R.rc;
+      GR.idr_hi = (float)GR.inv_dr;
+      GR.idr_lo = (float)(GR.inv_dr - (double)GR.idr_hi);
+      GR.rc_f = (float)R.rc;
+      GR.dr_f = (float)R.dr;
       for (int i = 0; i < R.npts; ++i) t64.push_back(make_double2(R.f[i], R.df[i]));
       GS.norb += 2 * R.l + 1;
       GS.rcut = std::max(GS.rcut, R.rc);
     }
     GS.rcut2 = GS.rcut * GS.rcut;
+    GS.porb = (GS.norb + 7) / 8 * 8;
     h->max_species_norb = std::max(h->max_species_norb, GS.norb);
+    double fmax = 0;
+    for (int k = 0; k < S.nradial; ++k)
+      for (int i = 0; i < S.radial[k].npts; ++i) fmax = std::max(fmax, std::fabs(S.radial[k].f[i]));
+    h->phi_bound = std::max(h->phi_bound, fmax * 1.1);
   }
   g.nrad = r;
   h->nknots = (long long)t64.size();
@@ -264,6 +274,11 @@ int gint_create(const gint_desc *d, gint_handle **out) {
   TRY(dalloc(&h->pair_col_dev, h->pair_col.size()));
   TRY(dalloc(&h->pair_off_dev, h->pair_off.size()));
   TRY(dalloc(&h->pair_T_dev, pairT.size()));
+  std::vector<int> pairI(h->npairs);
+  for (int I = 0; I < d->natoms; ++I)
+    for (int p = h->pair_row[I]; p < h->pair_row[I + 1]; ++p) pairI[p] = I;
+  TRY(dalloc(&h->pair_I_dev, pairI.size()));
+  TRYCU(cudaMemcpy(h->pair_I_dev, pairI.data(), pairI.size() * sizeof(int), cudaMemcpyHostToDevice));
   TRYCU(cudaMemcpy(h->pair_row_dev, h->pair_row.data(), h->pair_row.size() * sizeof(int), cudaMemcpyHostToDevice));
   TRYCU(cudaMemcpy(h->pair_col_dev, h->pair_col.data(), h->pair_col.size() * sizeof(int), cudaMemcpyHostToDevice));
   TRYCU(cudaMemcpy(h->pair_off_dev, h->pair_off.data(), h->pair_off.size() * sizeof(long long),
@@ -280,6 +295,10 @@ int gint_create(const gint_desc *d, gint_handle **out) {
   TRY(gint_build_neighbours(h, st));
   // workspace
   TRY(dalloc(&h->D32, (size_t)h->nblock));
+  TRY(dalloc(&h->work_ctr, 4));
+  TRYCU(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  TRYCU(cudaMemset(h->err_word, 0, sizeof(unsigned)));
+  TRY(gint_tc_prepare(h));
   TRYCU(cudaStreamSynchronize(st));
   *out = h;
   return GINT_OK;
@@ -335,6 +354,8 @@ int gint_set_positions(gint_handle *h, const double *pos_dev, void *stream) {
     return GINT_ECUDA;
   int rc = gint_build_neighbours(h, st);
   if (rc) return rc;
+  rc = gint_tc_prepare(h);
+  if (rc) return rc;
   if (cudaMemcpyAsync(h->pos_host.data(), h->pos_dev, 3 * sizeof(double) * h->geom.natoms, cudaMemcpyDeviceToHost,
                       st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
@@ -343,7 +364,7 @@ int gint_set_positions(gint_handle *h, const double *pos_dev, void *stream) {
 }
 
 static int check_precision(int precision) {
-  return (precision == GINT_FP64 || precision == GINT_FP32 || precision == GINT_TF32X3 || precision == GINT_TF32X1)
+  return (precision == GINT_FP64 || precision == GINT_FP32 || precision == GINT_F16X3 || precision == GINT_F16X1)
              ? GINT_OK
              : GINT_EINVAL;
 }
@@ -394,6 +415,24 @@ int gint_block_dot(gint_handle *h, const double *A, const double *B, double *out
 }
 
 double gint_weight(const gint_handle *h) { return h ? h->geom.w : 0.0; }
+
+int gint_sync(gint_handle *h, void *stream) {
+  if (!h) return GINT_EINVAL;
+  DeviceGuard guard(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned err = 0;
+  if (cudaMemcpyAsync(&err, h->err_word, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GINT_ECUDA;
+  if (err) {
+    if (cudaMemsetAsync(h->err_word, 0, sizeof(unsigned), st) != cudaSuccess) return GINT_ECUDA;
+    cudaStreamSynchronize(st);
+    if (err & GINT_ERRBIT_TIMEOUT) return GINT_ETIMEDOUT;
+    if (err & GINT_ERRBIT_CAPACITY) return GINT_ECAPACITY;
+    return GINT_EDEVICE;
+  }
+  return GINT_OK;
+}
 
 const char *gint_strerror(int code) {
   switch (code) {

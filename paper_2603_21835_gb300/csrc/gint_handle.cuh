@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cuda_fp16.h>
+
 #include <vector>
 
 #include "gint_internal.cuh"
@@ -30,6 +32,7 @@ struct gint_handle {
   int *pair_row_dev = nullptr, *pair_col_dev = nullptr;
   long long *pair_off_dev = nullptr;
   int *pair_T_dev = nullptr;  // index of the transposed pair (J, I)
+  int *pair_I_dev = nullptr;  // row atom I of each pair
   // neighbour structure
   int *n_at = nullptr, *n_ent = nullptr, *n_orb = nullptr;
   long long *b_at_off = nullptr, *b_ent_off = nullptr, *b_pair_off = nullptr;
@@ -40,12 +43,28 @@ struct gint_handle {
   int *b_pair = nullptr;
   long long cap_slots = 0, cap_ent = 0, cap_pairtab = 0;
   long long nslots = 0, nent = 0, npairtab = 0;
-  int max_brick_orb = 0, max_brick_atoms = 0;
+  int max_brick_orb = 0, max_brick_atoms = 0, max_brick_ent = 0;
   double W = 0, W_exec = 0;
   // workspace
   float *D32 = nullptr;       // float32 copy of D blocks (FP32 SIMT mode)
-  float *Dsplit = nullptr;    // tensor-core operand image of D (hi, lo)
-  long long dsplit_elems = 0;
+  int *work_ctr = nullptr;    // dynamic brick counter of the persistent kernels
+  int num_sms = 0;
+  // tensor-core path (float16 3-term split)
+  double phi_bound = 0;       // bound on |phi| used for the orbital scale
+  std::vector<long long> tile_off;        // per pair: element offset of its padded D tile
+  long long ntile_elems = 0;
+  __half *Dt_hi = nullptr, *Dt_lo = nullptr;  // D tiles: rows norb(I), K = porb(J) (zero padded)
+  long long *tile_off_dev = nullptr;
+  float *scales = nullptr;    // device: [0] S_phi, [1] S_D (density), [2] S_Q (local H)
+  int max_brick_porb = 0;     // largest padded (aligned) orbital count of a brick
+  // local-H scratch: per brick, upper-triangle slot-pair tiles (float32), reduced per pair
+  long long *hs_brick_off = nullptr;      // [nbricks + 1] element offset of each brick's tiles
+  long long hs_elems = 0;
+  float *hs = nullptr;
+  int nupper = 0;                         // pairs with I <= J
+  int *hu_pair = nullptr;                 // [nupper] pair index
+  long long *hu_off = nullptr;            // [nupper + 1] CSR into hu_src
+  long long *hu_src = nullptr;            // scratch element offset of each contribution
   double *red = nullptr;      // reduction partials
   double *scal = nullptr;     // device scalars
   unsigned *err_word = nullptr;
@@ -82,3 +101,6 @@ int gint_reduce_dot(gint_handle *h, const double *a, const double *b, long long 
 int gint_tc_rho(gint_handle *h, int precision, const double *D, double *rho, const double *V, double *F,
                 cudaStream_t st);
 int gint_tc_vlocal(gint_handle *h, int precision, const double *V, double *H, cudaStream_t st);
+int gint_tc_check_capacity(const gint_handle *h);
+int gint_tc_prepare(gint_handle *h);  // layouts and scratch of the tensor-core path (after neighbours)
+void gint_tc_free(gint_handle *h);

@@ -24,11 +24,12 @@
 struct GRadial {
   int l, npts, off, pad;  // off: first knot of this radial in the packed tables
   double dr, inv_dr, rc, rc2;
+  float idr_hi, idr_lo, rc_f, dr_f;  // float32 images: 1/dr as hi + lo, rc, dr
 };
 
 struct GSpecies {
-  int nrad, rad0, norb, pad;
-  double rcut, rcut2;  // largest rc of the species and its square
+  int nrad, rad0, norb, porb;  // porb: orbitals padded to a multiple of 8 (tensor-core layouts)
+  double rcut, rcut2;          // largest rc of the species and its square
 };
 
 struct GGeom {

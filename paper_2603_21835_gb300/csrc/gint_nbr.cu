@@ -138,18 +138,19 @@ __global__ void k_brick_count(GGeom g, const double *pos, const int *species, in
 
 // Single-CTA exclusive scans of the per-brick counts; also the totals and maxima.
 //   out[0] = slots, out[1] = entries, out[2] = pair-table size, out[3] = max orbitals,
-//   out[4] = max atoms, out[5] = executed pair work sum_b 128 norb_b^2 (as long long)
+//   out[4] = max atoms, out[5] = executed pair work sum_b 128 norb_b^2, out[6] = max entries
 __global__ void k_brick_scan(long long nb, const int *n_at, const int *n_ent, const int *n_orb, long long *at_off,
                              long long *ent_off, long long *pair_off, long long *out) {
   __shared__ long long s_at[1024], s_ent[1024], s_pr[1024];
-  __shared__ int s_mo[1024], s_ma[1024];
+  __shared__ int s_mo[1024], s_ma[1024], s_me[1024];
   __shared__ long long s_wx[1024];
   const int t = threadIdx.x, nt = blockDim.x;
   long long chunk = (nb + nt - 1) / nt;
   long long b0 = t * chunk, b1 = min(nb, b0 + chunk);
   long long a = 0, e = 0, p = 0, wx = 0;
-  int mo = 0, ma = 0;
+  int mo = 0, ma = 0, me = 0;
   for (long long b = b0; b < b1; ++b) {
+    me = max(me, n_ent[b]);
     a += n_at[b];
     e += n_ent[b];
     p += (long long)n_at[b] * n_at[b];
@@ -157,19 +158,20 @@ __global__ void k_brick_scan(long long nb, const int *n_at, const int *n_ent, co
     mo = max(mo, n_orb[b]);
     ma = max(ma, n_at[b]);
   }
-  s_at[t] = a; s_ent[t] = e; s_pr[t] = p; s_mo[t] = mo; s_ma[t] = ma; s_wx[t] = wx;
+  s_at[t] = a; s_ent[t] = e; s_pr[t] = p; s_mo[t] = mo; s_ma[t] = ma; s_wx[t] = wx; s_me[t] = me;
   __syncthreads();
   if (t == 0) {
     long long ra = 0, re = 0, rp = 0, rw = 0;
-    int rmo = 0, rma = 0;
+    int rmo = 0, rma = 0, rme = 0;
     for (int i = 0; i < nt; ++i) {
+      rme = max(rme, s_me[i]);
       long long ta = s_at[i], te = s_ent[i], tp = s_pr[i];
       s_at[i] = ra; s_ent[i] = re; s_pr[i] = rp;
       ra += ta; re += te; rp += tp; rw += s_wx[i];
       rmo = max(rmo, s_mo[i]);
       rma = max(rma, s_ma[i]);
     }
-    out[0] = ra; out[1] = re; out[2] = rp; out[3] = rmo; out[4] = rma; out[5] = rw * GINT_BPTS;
+    out[0] = ra; out[1] = re; out[2] = rp; out[3] = rmo; out[4] = rma; out[5] = rw * GINT_BPTS; out[6] = rme;
     at_off[nb] = ra; ent_off[nb] = re; pair_off[nb] = rp;
   }
   __syncthreads();
@@ -329,7 +331,7 @@ int gint_build_neighbours(gint_handle *h, cudaStream_t st) {
   k_brick_scan<<<1, 1024, 0, st>>>(nb, h->n_at, h->n_ent, h->n_orb, h->b_at_off, h->b_ent_off, h->b_pair_off,
                                    h->scan_out);
   NBR_CHECK(cudaGetLastError());
-  long long tot[6];
+  long long tot[7];
   NBR_CHECK(cudaMemcpyAsync(tot, h->scan_out, sizeof(tot), cudaMemcpyDeviceToHost, st));
   NBR_CHECK(cudaStreamSynchronize(st));
   h->nslots = tot[0];
@@ -338,6 +340,7 @@ int gint_build_neighbours(gint_handle *h, cudaStream_t st) {
   h->max_brick_orb = (int)tot[3];
   h->max_brick_atoms = (int)tot[4];
   h->W_exec = (double)tot[5];
+  h->max_brick_ent = (int)tot[6];
   if (h->max_brick_atoms > GINT_MAX_ATOMS_BRICK) return GINT_ECAPACITY;
   int rc = gint_reserve_nbr(h);
   if (rc) return rc;

@@ -1,7 +1,1166 @@
-// gint_tc.cu -- tensor-core (tcgen05) brick kernels.  Placeholder until the kernels land.
+// gint_tc.cu -- tensor-core (tcgen05, sm_103a) brick kernels for the density, force and
+// local-Hamiltonian passes of uniform-grid integration (paper Sec. 3.3.1: orbitals packed into
+// dense tiles per grid block, then batched tile contractions).
+//
+// Arithmetic: float32 orbital evaluation with compensated (double-float) distance and knot
+// parameter; operands split x = hi + lo into two float16 values (22 significant bits, with
+// power-of-two scales that keep every value inside the float16 range); products
+// hi*hi + hi*lo + lo*hi on kind::f16 tensor cores with float32 accumulation in tensor memory;
+// float64 for every cross-brick reduction.
+//
+// Layout: the orbitals of each atom occupy porb = roundup(norb, 8) columns of the brick's
+// orbital space (zero padded), no atom crosses a multiple of 128 columns, NP = padded total.
+// D is pre-tiled per atom pair into float16 (hi, lo) rows of porb(J) values, so that every
+// 16-byte segment of a B operand row is one cp.async from global memory.
+//
+// Density (D symmetric): columns are streamed in chunks of 16.  With the chunk's own
+// diagonal block halved, rho = 2 sum_k P_k Y_k where Y_k accumulates P_j D_jk over the chunks
+// j <= chunk(k) only, so chunk c's columns are final right after chunk c's MMA: the epilogue of
+// chunk c overlaps the MMA of chunk c+1 and the MMA work is halved.
+// Force: full Y = P D (all chunks, all columns), then per atom 2 w V grad(phi) . Y.
+// Local H: K = grid points (chunks of 32), M = N = orbitals (128-row tiles, upper block
+// triangle); each brick writes its float32 slot-pair tiles to a scratch area and a per-pair
+// float64 reduction (fixed order, no atomics) produces both H(I,J) and H(J,I).
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "gint_handle.cuh"
 
-int gint_tc_rho(gint_handle *, int, const double *, double *, const double *, double *, cudaStream_t) {
-  return GINT_EUNSUPPORTED;
+namespace {
+
+constexpr int kT = 512;          // threads of the brick kernels (16 warps)
+constexpr int kNPMAX = 320;      // padded orbitals of a brick (density / force)
+constexpr int kNPMAXH = 288;     // padded orbitals of a brick (local H: tensor-memory limit)
+constexpr int kMAXA = 40;        // atoms of a brick
+constexpr int kMAXE = 160;       // (atom, image) entries of a brick
+constexpr int kRC = 16;          // density chunk width (one f16 K step)
+constexpr int kHP = 32;          // local-H chunk: grid points (two K steps)
+constexpr uint32_t kHLBO = 144;  // local-H operands: padded K-direction core-matrix stride
+constexpr uint32_t kHSBO = 576;  // 4 core matrices of K per 8-row group
+constexpr long long kWaitNs = 2000000000LL;  // bounded mbarrier waits: 2 s
+constexpr unsigned char kNoSlot = 255;
+
+// ------------------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-int gint_tc_vlocal(gint_handle *, int, const double *, double *, cudaStream_t) { return GINT_EUNSUPPORTED; }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ long long globaltimer() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: false (and the timeout bit in *err) if the phase did not complete within kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer() - t0 > kWaitNs) {
+      atomicOr(err, GINT_ERRBIT_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// Shared-memory matrix descriptor, no swizzle, K-major core matrices of 8 rows x 16 bytes:
+// lbo = byte stride between core matrices along K, sbo = byte stride between 8-row groups.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  return d;                // base offset 0, no swizzle
+}
+// Instruction descriptor of kind::f16: f32 accumulator, f16 A and B, both K-major.
+__device__ __forceinline__ uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// 32 lanes x 32 bit x 16 columns: thread i of the warp receives its lane's 16 values.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// x = hi + lo with both parts float16 (hi = round(x), lo = round(x - hi)).
+__device__ __forceinline__ void split_h(float x, __half &hi, __half &lo) {
+  hi = __float2half_rn(x);
+  lo = __float2half_rn(x - __half2float(hi));
+}
+__device__ __forceinline__ uint32_t pack2(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+// ------------------------------------------------------------------------------ compensated float32
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Cubic Hermite of the tabulated (f, f') at r = rh + rl (double-float), float32 arithmetic with
+// an exact knot index and a knot parameter t accurate to float32 rounding.
+__device__ __forceinline__ void radial_df(const float2 *__restrict__ tab, const GRadial &R, float rh, float rl, float &f,
+                                          float &df) {
+  const float xh = rh * R.idr_hi;
+  const float xl = fmaf(rh, R.idr_hi, -xh) + (rl * R.idr_hi + rh * R.idr_lo);
+  int i = (int)floorf(xh);
+  float t = (xh - (float)i) + xl;
+  if (t < 0.f) {
+    i -= 1;
+    t += 1.f;
+  } else if (t >= 1.f) {
+    i += 1;
+    t -= 1.f;
+  }
+  if (i < 0) {
+    i = 0;
+    t = 0.f;
+  }
+  if (i >= R.npts - 1) {
+    f = 0.f;
+    df = 0.f;
+    return;
+  }
+  const float2 a = tab[R.off + i], b = tab[R.off + i + 1];
+  const float g0 = a.y * R.dr_f, g1 = b.y * R.dr_f;
+  const float t2 = t * t, u = 1.f - t;
+  const float s = t2 * (3.f - 2.f * t);
+  f = a.x + (b.x - a.x) * s + g0 * t * u * u + g1 * t2 * (t - 1.f);
+  df = ((b.x - a.x) * 6.f * t * u + g0 * u * (1.f - 3.f * t) + g1 * t * (3.f * t - 2.f)) * R.idr_hi;
+}
+
+// Adds phi (and grad phi if GRAD) of one image of species sp at displacement dh + dl to
+// v[0..norb) and gv[3*i + c].  |d| < rcut is tested by the caller.
+template <bool GRAD>
+__device__ __forceinline__ void add_atom_df(const GGeom &g, const float2 *__restrict__ tab, int sp, const float dh[3],
+                                            const float dl[3], float *v, float *gv) {
+  const GSpecies &S = g.sp[sp];
+  const float px = dh[0] * dh[0], py = dh[1] * dh[1], pz = dh[2] * dh[2];
+  const float ex = fmaf(dh[0], dh[0], -px), ey = fmaf(dh[1], dh[1], -py), ez = fmaf(dh[2], dh[2], -pz);
+  float s1, e1, s2, e2;
+  two_sum(px, py, s1, e1);
+  two_sum(s1, pz, s2, e2);
+  float r2l = (ex + ey + ez) + (e1 + e2) + 2.f * (dh[0] * dl[0] + dh[1] * dl[1] + dh[2] * dl[2]);
+  const float r2h = s2 + r2l;
+  r2l = r2l - (r2h - s2);
+  const bool at0 = r2h < 1e-24f;
+  const float r = at0 ? 0.f : sqrtf(r2h);
+  const float ir = at0 ? 0.f : 1.f / r;
+  const float rl = at0 ? 0.f : (fmaf(-r, r, r2h) + r2l) * (0.5f * ir);
+  const float ux = dh[0] * ir, uy = dh[1] * ir, uz = dh[2] * ir;
+  int col = 0;
+  for (int k = 0; k < S.nrad; ++k) {
+    const GRadial &R = g.rad[S.rad0 + k];
+    const int l = R.l, nm = 2 * l + 1;
+    if (r < R.rc_f) {
+      float f, df;
+      radial_df(tab, R, r, rl, f, df);
+      if (at0) {
+        if (l == 0) v[col] += f * 0.28209479177387814347f;
+        if (GRAD && l == 1) {
+          const float c = 0.48860251190291992159f * df;
+          gv[3 * (col + 0) + 2] += c;
+          gv[3 * (col + 1) + 0] += c;
+          gv[3 * (col + 2) + 1] += c;
+        }
+      } else {
+        float y[5], gy[5][3];
+        ylm_unit<float>(l, ux, uy, uz, y, gy);
+        const float fr = f * ir;
+        for (int m = 0; m < nm; ++m) {
+          v[col + m] += f * y[m];
+          if (GRAD) {
+            const float a = df * y[m] - (float)l * fr * y[m];
+            gv[3 * (col + m) + 0] += a * ux + fr * gy[m][0];
+            gv[3 * (col + m) + 1] += a * uy + fr * gy[m][1];
+            gv[3 * (col + m) + 2] += a * uz + fr * gy[m][2];
+          }
+        }
+      }
+    }
+    col += nm;
+  }
+}
+
+// ------------------------------------------------------------------------------ brick metadata
+struct BrickSh {
+  uint64_t bar[2];
+  uint32_t tmem;
+  int brick, na, np, nent, abort;
+  int s_atom[kMAXA], s_no[kMAXA], s_po[kMAXA], s_sp[kMAXA], s_pcol[kMAXA], s_e0[kMAXA + 1];
+  int s_cumno[kMAXA + 1];       // prefix of norb over slots
+  int s_rowst[kMAXA];           // local-H scratch: first element of slot a's tile row
+  int s_tile[kMAXA * kMAXA];    // D tile element offset of (row slot b, K slot a), -1 if none
+  float e_hi[kMAXE][3], e_lo[kMAXE][3];  // entry positions relative to the brick origin
+  float pt_hi[128][3], pt_lo[128][3];    // grid point positions relative to the brick origin
+  unsigned char col2slot[kNPMAX];
+  float fpart[kMAXA][3];
+  float rpart[4][128];
+  float sc[4];  // scales
+};
+
+__device__ __forceinline__ void split2(double v, float &hi, float &lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
+__device__ void init_points(const GGeom &g, BrickSh &sh) {
+  for (int p = threadIdx.x; p < 128; p += blockDim.x) {
+    const int pi = p >> 5, pj = (p >> 3) & 3, pk = p & 7;
+    for (int c = 0; c < 3; ++c) {
+      const double v =
+          (double)pi / g.n1 * g.cell[c] + (double)pj / g.n2 * g.cell[3 + c] + (double)pk / g.n3 * g.cell[6 + c];
+      split2(v, sh.pt_hi[p][c], sh.pt_lo[p][c]);
+    }
+  }
+}
+
+// Padded column layout of the brick's slots: 8-aligned, never crossing a multiple of 128.
+// Shared by the device kernels and the host preparation (identical integer arithmetic).
+__host__ __device__ __forceinline__ int place_slot(int cur, int po) {
+  int pc = (cur + 7) & ~7;
+  if ((pc & 127) + po > 128) pc = (pc + 127) & ~127;
+  return pc;
+}
+
+// Loads slots, entries, padded layout, tile table, local-H tile offsets.
+__device__ void load_brick(const GGeom &g, const GNbr &nb, const long long *__restrict__ tile_off, long long b,
+                           BrickSh &sh) {
+  const int t = threadIdx.x;
+  const int bk = (int)(b % g.nbk), bj = (int)((b / g.nbk) % g.nbj), bi = (int)(b / ((long long)g.nbk * g.nbj));
+  double ob[3];
+  grid_point(g, bi * GINT_BI, bj * GINT_BJ, bk * GINT_BK, ob);
+  const long long s0 = nb.b_at_off[b];
+  const int na = (int)(nb.b_at_off[b + 1] - s0);
+  const long long e_begin = nb.s_ent[s0], e_end = nb.s_ent[s0 + na];
+  const int nent = (int)(e_end - e_begin);
+  for (int a = t; a < na; a += blockDim.x) {
+    const int I = nb.s_atom[s0 + a], sp = nb.atom_species[I];
+    sh.s_atom[a] = I;
+    sh.s_sp[a] = sp;
+    sh.s_no[a] = g.sp[sp].norb;
+    sh.s_po[a] = g.sp[sp].porb;
+    sh.s_e0[a] = (int)(nb.s_ent[s0 + a] - e_begin);
+    sh.fpart[a][0] = sh.fpart[a][1] = sh.fpart[a][2] = 0.f;
+  }
+  for (int e = t; e < nent; e += blockDim.x)
+    for (int c = 0; c < 3; ++c) split2(nb.e_shift[3 * (e_begin + e) + c] - ob[c], sh.e_hi[e][c], sh.e_lo[e][c]);
+  for (int k = t; k < kNPMAX; k += blockDim.x) sh.col2slot[k] = kNoSlot;
+  __syncthreads();
+  if (t == 0) {
+    sh.na = na;
+    sh.nent = nent;
+    sh.s_e0[na] = nent;
+    int cur = 0, cum = 0;
+    for (int a = 0; a < na; ++a) {
+      const int pc = place_slot(cur, sh.s_po[a]);
+      sh.s_pcol[a] = pc;
+      cur = pc + sh.s_po[a];
+      sh.s_cumno[a] = cum;
+      cum += sh.s_no[a];
+    }
+    sh.s_cumno[na] = cum;
+    sh.np = (cur + 15) & ~15;
+    int rs = 0;
+    for (int a = 0; a < na; ++a) {
+      sh.s_rowst[a] = rs;
+      rs += sh.s_no[a] * (cum - sh.s_cumno[a]);
+    }
+  }
+  __syncthreads();
+  const long long pbase = nb.b_pair_off[b];
+  for (int e = t; e < na * na; e += blockDim.x) {
+    const int p = nb.b_pair[pbase + e];  // row slot e / na, column slot e % na
+    sh.s_tile[e] = p < 0 ? -1 : (int)tile_off[p];
+  }
+  for (int a = t; a < na; a += blockDim.x)
+    for (int i = 0; i < sh.s_po[a]; ++i) sh.col2slot[sh.s_pcol[a] + i] = (unsigned char)a;
+  __syncthreads();
+}
+
+__device__ __forceinline__ void rel_disp_df(const BrickSh &sh, int p, int e, float dh[3], float dl[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float s, err;
+    two_sum(sh.pt_hi[p][c], -sh.e_hi[e][c], s, err);
+    const float lo = err + (sh.pt_lo[p][c] - sh.e_lo[e][c]);
+    dh[c] = s + lo;
+    dl[c] = lo - (dh[c] - s);
+  }
+}
+
+// Periodised orbitals (all images) of slot a at local point p into v[0..norb) (+ gradients).
+template <bool GRAD>
+__device__ __forceinline__ void eval_slot(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
+                                          int p, float *v, float *gv) {
+  const int sp = sh.s_sp[a];
+  const float rc2 = (float)g.sp[sp].rcut2;
+  for (int e = sh.s_e0[a]; e < sh.s_e0[a + 1]; ++e) {
+    float dh[3], dl[3];
+    rel_disp_df(sh, p, e, dh, dl);
+    if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < rc2) add_atom_df<GRAD>(g, tab, sp, dh, dl, v, gv);
+  }
+}
+
+// rho epilogue of one 16-column chunk: sum_k (P_hi + P_lo)_k y_k for point p.
+__device__ __forceinline__ float chunk_dot(const unsigned char *Ph, const unsigned char *Pl, uint32_t sboP, int p,
+                                           int k0, const float *y) {
+  float part = 0.f;
+#pragma unroll
+  for (int hseg = 0; hseg < 2; ++hseg) {
+    const uint32_t off = (p >> 3) * sboP + ((k0 >> 3) + hseg) * 128 + (p & 7) * 16;
+    const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + off), wl = *reinterpret_cast<const uint4 *>(Pl + off);
+    const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
+      const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
+      part += (hf.x + lf.x) * y[hseg * 8 + 2 * e] + (hf.y + lf.y) * y[hseg * 8 + 2 * e + 1];
+    }
+  }
+  return part;
+}
+
+// ------------------------------------------------------------------------------ density / force
+// Dynamic shared memory: P (hi, lo) [128 x np_max] | 2 x B stage (hi, lo) [np_max x 16].
+// P element (p, k): (p/8)*16*np_max + (k/8)*128 + (p%8)*16 + (k%8)*2.
+// B element (r, j): (r/8)*256 + (j/8)*128 + (r%8)*16 + (j%8)*2.
+template <bool FORCE>
+__global__ void __launch_bounds__(kT, 1)
+    k_tc_rho(GGeom g, GNbr nb, const float2 *__restrict__ tab, const __half *__restrict__ Dhi,
+             const __half *__restrict__ Dlo, const long long *__restrict__ tile_off, const float *__restrict__ scales,
+             const double *__restrict__ V, double *__restrict__ rho, double *__restrict__ F, int *work,
+             unsigned *err, int np_max, int split3) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ BrickSh sh;
+  const int t = threadIdx.x, warp = t >> 5;
+  const uint32_t sboP = 16u * np_max;
+  unsigned char *Ph = smem, *Pl = smem + 128u * np_max * 2;
+  unsigned char *B0 = smem + 128u * np_max * 4;
+  const uint32_t bop = (uint32_t)np_max * kRC * 2;  // one B operand (hi or lo) of one stage
+  if (t == 0) {
+    mbar_init(&sh.bar[0], 1);
+    mbar_init(&sh.bar[1], 1);
+    fence_mbar_init();
+    sh.abort = 0;
+    sh.sc[0] = scales[0];
+    sh.sc[1] = scales[1];
+  }
+  if (warp == 0) {
+    tmem_alloc(&sh.tmem, 512);
+    tmem_relinquish();
+  }
+  init_points(g, sh);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sh.tmem;
+  const float Sphi = sh.sc[0], SD = sh.sc[1];
+  const int p = t & 127, q = t >> 7;  // grid point, slot slice (0..3)
+  const uint32_t lane_base = (uint32_t)((p >> 5) * 32) << 16;
+  uint32_t G = 0;  // chunks issued by this CTA
+  for (;;) {
+    __syncthreads();
+    if (t == 0) sh.brick = atomicAdd(work, 1);
+    __syncthreads();
+    const long long b = sh.brick;
+    if (b >= g.nbricks || sh.abort) break;
+    load_brick(g, nb, tile_off, b, sh);
+    const int na = sh.na, NP = sh.np;
+    int gi, gj, gk;
+    const bool valid = brick_point(g, b, p, gi, gj, gk);
+    const long long gidx = valid ? grid_index(g, gi, gj, gk) : 0;
+    if (na == 0) {
+      if (q == 0 && valid && rho) rho[gidx] = 0.0;
+      continue;
+    }
+    // ---- phase A: scaled orbitals of all atoms at every point -> P (hi, lo), zero padding
+    for (int a = q; a < na; a += 4) {
+      float v[GINT_MAX_ORB_ATOM];
+      const int po = sh.s_po[a], pc = sh.s_pcol[a];
+      for (int i = 0; i < po; ++i) v[i] = 0.f;
+      if (valid) eval_slot<false>(g, tab, sh, a, p, v, nullptr);
+      const int gap0 = a == 0 ? 0 : sh.s_pcol[a - 1] + sh.s_po[a - 1];
+      const int end = (a == na - 1) ? NP : pc + po;
+      for (int k = gap0; k < end; k += 8) {
+        uint32_t wh[4], wl[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          __half h0, l0, h1, l1;
+          const int k0 = k + 2 * e - pc, k1 = k0 + 1;
+          split_h((k0 >= 0 && k0 < po) ? v[k0] * Sphi : 0.f, h0, l0);
+          split_h((k1 >= 0 && k1 < po) ? v[k1] * Sphi : 0.f, h1, l1);
+          wh[e] = pack2(h0, h1);
+          wl[e] = pack2(l0, l1);
+        }
+        const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
+        *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+        *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+      }
+    }
+    // ---- phase B: chunks of 16 columns
+    const int nch = NP / kRC;
+    const uint32_t corr_base = (NP <= 256) ? 256u : 0u;  // separate correction accumulator if it fits
+    bool ok = true;
+    double racc = 0.0;
+    auto issue_copies = [&](int c, int stage) {
+      unsigned char *Bh = B0 + stage * 2 * bop, *Bl = Bh + bop;
+      const int rowbase = FORCE ? 0 : c * kRC;
+      const int N = NP - rowbase;
+      for (int u = t; u < N * 4; u += kT) {
+        const int r = u >> 2, s = (u >> 1) & 1, hl = u & 1;
+        const int k = rowbase + r, j0 = c * kRC + 8 * s;
+        unsigned char *dst = (hl ? Bl : Bh) + (r >> 3) * 256 + s * 128 + (r & 7) * 16;
+        const int bs = sh.col2slot[k], as = sh.col2slot[j0];
+        int tile = -1, kl = 0, jseg = 0, poa = 0;
+        if (bs != kNoSlot && as != kNoSlot) {
+          kl = k - sh.s_pcol[bs];
+          if (kl < sh.s_no[bs]) {
+            tile = sh.s_tile[bs * na + as];
+            jseg = j0 - sh.s_pcol[as];
+            poa = sh.s_po[as];
+          }
+        }
+        if (tile >= 0)
+          cp_async16(dst, (hl ? Dlo : Dhi) + (long long)tile + (long long)kl * poa + jseg);
+        else
+          *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+      }
+    };
+    // B stage G&1 was last read by MMA G-2, complete since the previous brick's final wait
+    issue_copies(0, G & 1);
+    cp_async_commit();
+    for (int c = 0; c < nch; ++c, ++G) {
+      const int s = G & 1;
+      if (c + 1 < nch) {
+        // stage (G+1)&1 was read by MMA G-1
+        if (G >= 1 && !mbar_wait(&sh.bar[(G + 1) & 1], ((G - 1) >> 1) & 1, err)) ok = false;
+        issue_copies(c + 1, (G + 1) & 1);
+      }
+      cp_async_commit();
+      cp_async_wait1();
+      fence_async_smem();
+      __syncthreads();
+      unsigned char *Bh = B0 + s * 2 * bop, *Bl = Bh + bop;
+      if (!FORCE) {
+        // halve the chunk's own diagonal block (rows 0..15 of the B tile)
+        const int r = t >> 5, hl = (t >> 4) & 1, j = t & 15;
+        __half *e = reinterpret_cast<__half *>((hl ? Bl : Bh) + (r >> 3) * 256 + (j >> 3) * 128 + (r & 7) * 16 + (j & 7) * 2);
+        *e = __hmul(*e, __float2half(0.5f));
+        fence_async_smem();
+        __syncthreads();
+      }
+      if (t == 0) {
+        tc_fence_after();
+        const int rowbase = FORCE ? 0 : c * kRC;
+        const int N = NP - rowbase;
+        const uint64_t dah = sdesc(smem_u32(Ph) + (c * kRC / 8) * 128, 128, sboP);
+        const uint64_t dal = sdesc(smem_u32(Pl) + (c * kRC / 8) * 128, 128, sboP);
+        for (int n0 = 0; n0 < N; n0 += 256) {
+          const int nn = min(256, N - n0);
+          const uint32_t id = idesc_f16(128, nn);
+          const uint64_t dbh = sdesc(smem_u32(Bh) + (n0 >> 3) * 256, 128, 256);
+          const uint64_t dbl = sdesc(smem_u32(Bl) + (n0 >> 3) * 256, 128, 256);
+          const uint32_t dm = tmem + rowbase + n0, dc = tmem + corr_base + rowbase + n0;
+          mma_f16(dm, dah, dbh, id, c > 0 ? 1u : 0u);
+          if (split3) {
+            mma_f16(dc, dah, dbl, id, (c > 0 || corr_base == 0) ? 1u : 0u);
+            mma_f16(dc, dal, dbh, id, 1u);
+          }
+        }
+        mma_commit(&sh.bar[s]);
+      }
+      if (!FORCE && c > 0 && q == 0) {
+        // epilogue of chunk c-1 (its columns are final): rho += P_k Y_k
+        const uint32_t Gp = G - 1;
+        if (!mbar_wait(&sh.bar[Gp & 1], (Gp >> 1) & 1, err)) ok = false;
+        tc_fence_after();
+        const int k0 = (c - 1) * kRC;
+        float y[16], yc[16];
+        tmem_ld16(tmem + lane_base + k0, y);
+        if (split3 && corr_base) {
+          tmem_ld16(tmem + lane_base + corr_base + k0, yc);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) y[i] += yc[i];
+        }
+        racc += (double)chunk_dot(Ph, Pl, sboP, p, k0, y);
+      }
+    }
+    cp_async_wait0();
+    {
+      const uint32_t Gp = G - 1;
+      if (!mbar_wait(&sh.bar[Gp & 1], (Gp >> 1) & 1, err)) ok = false;
+      tc_fence_after();
+    }
+    if (!FORCE) {
+      if (q == 0) {
+        const int k0 = NP - kRC;
+        float y[16], yc[16];
+        tmem_ld16(tmem + lane_base + k0, y);
+        if (split3 && corr_base) {
+          tmem_ld16(tmem + lane_base + corr_base + k0, yc);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) y[i] += yc[i];
+        }
+        racc += (double)chunk_dot(Ph, Pl, sboP, p, k0, y);
+        if (valid && rho) rho[gidx] = racc * (2.0 / ((double)Sphi * (double)Sphi * (double)SD));
+      }
+    } else {
+      // full Y: per atom, rho and force from recomputed phi and grad phi (unscaled float32)
+      const float inv = 1.f / (Sphi * SD);
+      const float wv = valid ? (float)(g.w * V[gidx]) : 0.f;
+      float rp = 0.f;
+      for (int a = q; a < na; a += 4) {
+        const int pc = sh.s_pcol[a], no = sh.s_no[a];
+        float y[32], yc[16];
+        tmem_ld16(tmem + lane_base + pc, y);
+        if (split3 && corr_base) {
+          tmem_ld16(tmem + lane_base + corr_base + pc, yc);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) y[i] += yc[i];
+        }
+        if (sh.s_po[a] > 16) {
+          tmem_ld16(tmem + lane_base + pc + 16, y + 16);
+          if (split3 && corr_base) {
+            tmem_ld16(tmem + lane_base + corr_base + pc + 16, yc);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) y[16 + i] += yc[i];
+          }
+        }
+        float v[GINT_MAX_ORB_ATOM], gv[3 * GINT_MAX_ORB_ATOM];
+        for (int i = 0; i < no; ++i) {
+          v[i] = 0.f;
+          gv[3 * i] = gv[3 * i + 1] = gv[3 * i + 2] = 0.f;
+        }
+        if (valid) eval_slot<true>(g, tab, sh, a, p, v, gv);
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        for (int i = 0; i < no; ++i) {
+          const float yi = y[i] * inv;
+          rp += v[i] * yi;
+          fx += gv[3 * i] * yi;
+          fy += gv[3 * i + 1] * yi;
+          fz += gv[3 * i + 2] * yi;
+        }
+        fx *= 2.f * wv;
+        fy *= 2.f * wv;
+        fz *= 2.f * wv;
+        for (int o = 16; o > 0; o >>= 1) {
+          fx += __shfl_xor_sync(0xffffffffu, fx, o);
+          fy += __shfl_xor_sync(0xffffffffu, fy, o);
+          fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        }
+        if ((t & 31) == 0) {
+          atomicAdd(&sh.fpart[a][0], fx);
+          atomicAdd(&sh.fpart[a][1], fy);
+          atomicAdd(&sh.fpart[a][2], fz);
+        }
+      }
+      sh.rpart[q][p] = rp;
+      __syncthreads();
+      if (q == 0 && valid && rho)
+        rho[gidx] = (double)sh.rpart[0][p] + (double)sh.rpart[1][p] + (double)sh.rpart[2][p] + (double)sh.rpart[3][p];
+      for (int a = t; a < na; a += kT) {
+        const int I = sh.s_atom[a];
+        atomicAdd(F + 3 * I + 0, (double)sh.fpart[a][0]);
+        atomicAdd(F + 3 * I + 1, (double)sh.fpart[a][1]);
+        atomicAdd(F + 3 * I + 2, (double)sh.fpart[a][2]);
+      }
+    }
+    tc_fence_before();
+    if (!ok) sh.abort = 1;
+  }
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// ------------------------------------------------------------------------------ local Hamiltonian
+// Dynamic shared memory per stage: A hi, A lo, B hi, B lo, each [np_max rows x 32 points]
+// (element (r, p): (r/8)*576 + (p/8)*144 + (r%8)*16 + (p%8)*2), plus a tail pad for the rows
+// above NP that the last 128-row A tile reads (they only feed output rows that are ignored).
+__global__ void __launch_bounds__(kT, 1)
+    k_tc_vlocal(GGeom g, GNbr nb, const float2 *__restrict__ tab, const long long *__restrict__ tile_off,
+                const float *__restrict__ scales, const double *__restrict__ V,
+                const long long *__restrict__ hs_brick_off, float *__restrict__ hs, int *work, unsigned *err,
+                int np_max, int split3) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ BrickSh sh;
+  const int t = threadIdx.x, warp = t >> 5;
+  const uint32_t op = (uint32_t)(np_max / 8) * kHSBO;
+  const uint32_t stage_bytes = 4 * op;
+  if (t == 0) {
+    mbar_init(&sh.bar[0], 1);
+    mbar_init(&sh.bar[1], 1);
+    fence_mbar_init();
+    sh.abort = 0;
+    sh.sc[0] = scales[0];
+    sh.sc[2] = scales[2];
+  }
+  if (warp == 0) {
+    tmem_alloc(&sh.tmem, 512);
+    tmem_relinquish();
+  }
+  init_points(g, sh);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sh.tmem;
+  const float Sphi = sh.sc[0], SA = sh.sc[2];
+  const float out_scale = 1.f / (Sphi * SA);
+  const int pp = t & (kHP - 1), q = t >> 5;  // point within the chunk, slot slice (0..15)
+  uint32_t G = 0;
+  for (;;) {
+    __syncthreads();
+    if (t == 0) sh.brick = atomicAdd(work, 1);
+    __syncthreads();
+    const long long b = sh.brick;
+    if (b >= g.nbricks || sh.abort) break;
+    load_brick(g, nb, tile_off, b, sh);
+    const int na = sh.na, NP = sh.np;
+    if (na == 0) continue;
+    const int ntile = (NP + 127) / 128;
+    int tb[3] = {0, 0, 0}, T = 0;
+    for (int m = 0; m < ntile; ++m) {
+      tb[m] = T;
+      T += NP - 128 * m;
+    }
+    const uint32_t corr_base = (2 * T <= 512) ? (uint32_t)T : 0u;
+    bool ok = true;
+    for (int c = 0; c < 128 / kHP; ++c, ++G) {
+      const int s = G & 1;
+      unsigned char *Ah = smem + s * stage_bytes, *Al = Ah + op, *Bh = Al + op, *Bl = Bh + op;
+      if (G >= 2 && !mbar_wait(&sh.bar[s], ((G - 2) >> 1) & 1, err)) ok = false;
+      const int pt = c * kHP + pp;
+      int gi, gj, gk;
+      const bool valid = brick_point(g, b, pt, gi, gj, gk);
+      const float wv = valid ? (float)(g.w * V[grid_index(g, gi, gj, gk)]) : 0.f;
+      for (int a = q; a < na; a += 16) {
+        float v[GINT_MAX_ORB_ATOM];
+        const int po = sh.s_po[a], pc = sh.s_pcol[a];
+        for (int i = 0; i < po; ++i) v[i] = 0.f;
+        if (valid) eval_slot<false>(g, tab, sh, a, pt, v, nullptr);
+        const int gap0 = a == 0 ? 0 : sh.s_pcol[a - 1] + sh.s_po[a - 1];
+        const int end = (a == na - 1) ? NP : pc + po;
+        for (int r = gap0; r < end; ++r) {
+          const int i = r - pc;
+          const float x = (i >= 0 && i < po) ? v[i] : 0.f;
+          __half bh, bl, ah, al;
+          split_h(x * Sphi, bh, bl);
+          split_h(x * wv * SA, ah, al);
+          const uint32_t off = (r >> 3) * kHSBO + (pp >> 3) * kHLBO + (r & 7) * 16 + (pp & 7) * 2;
+          *reinterpret_cast<__half *>(Bh + off) = bh;
+          *reinterpret_cast<__half *>(Bl + off) = bl;
+          *reinterpret_cast<__half *>(Ah + off) = ah;
+          *reinterpret_cast<__half *>(Al + off) = al;
+        }
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (t == 0) {
+        tc_fence_after();
+        for (int ks = 0; ks < kHP / 16; ++ks) {
+          for (int m = 0; m < ntile; ++m) {
+            const uint64_t dah = sdesc(smem_u32(Ah) + m * 16 * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
+            const uint64_t dal = sdesc(smem_u32(Al) + m * 16 * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
+            const int N = NP - 128 * m;
+            for (int n0 = 0; n0 < N; n0 += 256) {
+              const int nn = min(256, N - n0);
+              const uint32_t id = idesc_f16(128, nn);
+              const uint32_t brow = (uint32_t)(128 * m + n0);
+              const uint64_t dbh = sdesc(smem_u32(Bh) + (brow >> 3) * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
+              const uint64_t dbl = sdesc(smem_u32(Bl) + (brow >> 3) * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
+              const uint32_t dm = tmem + tb[m] + n0, dc = tmem + corr_base + tb[m] + n0;
+              const bool first = (c == 0 && ks == 0);
+              mma_f16(dm, dah, dbh, id, first ? 0u : 1u);
+              if (split3) {
+                mma_f16(dc, dah, dbl, id, (first && corr_base) ? 0u : 1u);
+                mma_f16(dc, dal, dbh, id, 1u);
+              }
+            }
+          }
+        }
+        mma_commit(&sh.bar[s]);
+      }
+    }
+    {
+      const uint32_t Gp = G - 1;
+      if (!mbar_wait(&sh.bar[Gp & 1], (Gp >> 1) & 1, err)) ok = false;
+      tc_fence_after();
+    }
+    // epilogue: upper slot-pair tiles -> scratch (float32, unscaled)
+    {
+      const int lane = t & 127, qq = t >> 7;
+      const uint32_t lane_base = (uint32_t)((lane >> 5) * 32) << 16;
+      const long long base = hs_brick_off[b];
+      for (int m = 0; m < ntile; ++m) {
+        const int mu = 128 * m + lane;
+        const int as = mu < NP ? sh.col2slot[mu] : kNoSlot;
+        const int il = as != kNoSlot ? mu - sh.s_pcol[as] : 0;
+        const bool rowok = as != kNoSlot && il < sh.s_no[as];
+        const int N = NP - 128 * m;
+        for (int gcol = qq; gcol < N / 16; gcol += 4) {
+          float y[16], yc[16];
+          tmem_ld16(tmem + lane_base + tb[m] + gcol * 16, y);
+          if (split3 && corr_base) {
+            tmem_ld16(tmem + lane_base + corr_base + tb[m] + gcol * 16, yc);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) y[i] += yc[i];
+          }
+          if (!rowok) continue;
+#pragma unroll 4
+          for (int i = 0; i < 16; ++i) {
+            const int nu = 128 * m + gcol * 16 + i;
+            const int cs = sh.col2slot[nu];
+            if (cs == kNoSlot || cs < as) continue;
+            const int jl = nu - sh.s_pcol[cs];
+            if (jl >= sh.s_no[cs]) continue;
+            const int no_c = sh.s_no[cs];
+            const long long o = base + sh.s_rowst[as] +
+                                (long long)sh.s_no[as] * (sh.s_cumno[cs] - sh.s_cumno[as]) + il * no_c + jl;
+            hs[o] = y[i] * out_scale;
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    if (!ok) sh.abort = 1;
+  }
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// Per pair (I <= J): H_IJ = sum over the bricks containing both (fixed order, float64);
+// H_JI = H_IJ^T.
+__global__ void k_h_reduce(const int *__restrict__ hu_pair, const long long *__restrict__ hu_off,
+                           const long long *__restrict__ hu_src, const float *__restrict__ hs,
+                           const int *__restrict__ pair_I, const int *__restrict__ pair_J,
+                           const int *__restrict__ pair_T, const long long *__restrict__ pair_off,
+                           const int *__restrict__ species, GGeom g, double *__restrict__ H) {
+  const int u = blockIdx.x;
+  const int p = hu_pair[u];
+  const int I = pair_I[p], J = pair_J[p];
+  const int nI = g.sp[species[I]].norb, nJ = g.sp[species[J]].norb;
+  const long long k0 = hu_off[u], k1 = hu_off[u + 1];
+  for (int e = threadIdx.x; e < nI * nJ; e += blockDim.x) {
+    double acc = 0.0;
+    for (long long k = k0; k < k1; ++k) acc += (double)hs[hu_src[k] + e];
+    H[pair_off[p] + e] = acc;
+    if (I != J) {
+      const int i = e / nJ, j = e - (e / nJ) * nJ;
+      H[pair_off[pair_T[p]] + (long long)j * nI + i] = acc;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ per-call preparation
+__global__ void k_absmax(const double *__restrict__ x, long long n, unsigned *out) {
+  float m = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, (float)fabs(x[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+__device__ double pow2_scale(double lim, double m) {
+  if (!(m > 0)) return 1048576.0;
+  return exp2(floor(log2(lim / m)));
+}
+
+// Power-of-two scales: [0] orbitals, [1] D, [2] w V orbitals.  Largest scaled magnitudes stay
+// below 2^15 (float16 max 65504); a zero input gets the scale 2^20.
+__global__ void k_scales(const unsigned *maxbits, double phi_bound, double w, float *scales) {
+  const double pb = 4.0 * phi_bound;
+  scales[0] = (float)pow2_scale(30000.0, pb);
+  scales[1] = (float)pow2_scale(30000.0, (double)__uint_as_float(maxbits[0]));
+  scales[2] = (float)pow2_scale(30000.0, pb * w * (double)__uint_as_float(maxbits[1]));
+}
+
+// D blocks (float64, row-major norb(I) x norb(J)) -> tiles norb(I) x porb(J), scaled, (hi, lo).
+__global__ void k_build_tiles(const double *__restrict__ D, const int *__restrict__ pair_I,
+                              const int *__restrict__ pair_J, const long long *__restrict__ pair_off,
+                              const long long *__restrict__ tile_off, const int *__restrict__ species, GGeom g,
+                              const float *__restrict__ scales, __half *__restrict__ Dhi, __half *__restrict__ Dlo) {
+  const int p = blockIdx.x;
+  const int I = pair_I[p], J = pair_J[p];
+  const int nI = g.sp[species[I]].norb, nJ = g.sp[species[J]].norb, pJ = g.sp[species[J]].porb;
+  const float S = scales[1];
+  const long long o = pair_off[p], to = tile_off[p];
+  for (int e = threadIdx.x; e < nI * pJ; e += blockDim.x) {
+    const int i = e / pJ, j = e - (e / pJ) * pJ;
+    __half h = __float2half(0.f), l = __float2half(0.f);
+    if (j < nJ) {
+      const double v = D[o + (long long)i * nJ + j] * (double)S;
+      h = __float2half_rn((float)v);
+      l = __float2half_rn((float)(v - (double)__half2float(h)));
+    }
+    Dhi[to + e] = h;
+    Dlo[to + e] = l;
+  }
+}
+
+// ------------------------------------------------------------------------------ self-test
+// One f16 MMA per operand layout on integer data; err_out[0] = max |D - exact|.
+__global__ void __launch_bounds__(128, 1) k_tc_selftest(int N, float *err_out, unsigned *status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_s;
+  const int t = threadIdx.x, warp = t >> 5;
+  if (t == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_s, 256);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_s;
+  float maxerr = 0.f;
+  const uint32_t lbos[3] = {128, 128, kHLBO}, sbos[3] = {256, 512, kHSBO};
+  for (int layout = 0; layout < 3; ++layout) {
+    const uint32_t lbo = lbos[layout], sbo = sbos[layout];
+    unsigned char *A = smem, *B = smem + 16 * sbo;
+    for (int e = t; e < 128 * 16; e += 128) {
+      const int i = e >> 4, k = e & 15;
+      *reinterpret_cast<__half *>(A + (i >> 3) * sbo + (k >> 3) * lbo + (i & 7) * 16 + (k & 7) * 2) =
+          __float2half((float)(((i * 7 + k * 3) % 9) - 4));
+    }
+    for (int e = t; e < N * 16; e += 128) {
+      const int n = e >> 4, k = e & 15;
+      *reinterpret_cast<__half *>(B + (n >> 3) * sbo + (k >> 3) * lbo + (n & 7) * 16 + (k & 7) * 2) =
+          __float2half((float)(((n * 5 + k * 11) % 9) - 4));
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      mma_f16(tmem, sdesc(smem_u32(A), lbo, sbo), sdesc(smem_u32(B), lbo, sbo), idesc_f16(128, N), 0u);
+      mma_commit(&bar);
+    }
+    if (!mbar_wait(&bar, (uint32_t)layout & 1, status)) break;
+    tc_fence_after();
+    for (int cg = 0; cg < N / 16; ++cg) {
+      float y[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cg * 16, y);
+      for (int i = 0; i < 16; ++i) {
+        const int n = cg * 16 + i;
+        float ex = 0.f;
+        for (int k = 0; k < 16; ++k) ex += (float)(((t * 7 + k * 3) % 9) - 4) * (float)(((n * 5 + k * 11) % 9) - 4);
+        maxerr = fmaxf(maxerr, fabsf(y[i] - ex));
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  atomicMax(reinterpret_cast<int *>(err_out), __float_as_int(maxerr));
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+inline uint32_t rho_smem_bytes(int np) { return 128u * np * 4 + 2u * np * kRC * 4; }
+inline uint32_t h_smem_bytes(int np) { return 2u * 4 * (uint32_t)(np / 8) * kHSBO + 16 * kHSBO; }
+
+template <typename K>
+int set_smem(K kern, uint32_t bytes) {
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+    return GINT_ECUDA;
+  return GINT_OK;
+}
+
+template <typename T>
+void dfree(T *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+}  // namespace
+
+#define TC_CHECK(x)                            \
+  do {                                         \
+    if ((x) != cudaSuccess) return GINT_ECUDA; \
+  } while (0)
+
+void gint_tc_free(gint_handle *h) {
+  dfree(h->Dt_hi);
+  dfree(h->Dt_lo);
+  dfree(h->tile_off_dev);
+  dfree(h->scales);
+  dfree(h->hs_brick_off);
+  dfree(h->hs);
+  dfree(h->hu_pair);
+  dfree(h->hu_off);
+  dfree(h->hu_src);
+}
+
+// Layouts of the tensor-core path for the current neighbour lists: D tile offsets, the padded
+// brick width, the local-H scratch offsets and the per-pair contribution lists (host, fixed
+// brick order so that the float64 reduction order is deterministic).
+int gint_tc_prepare(gint_handle *h) {
+  gint_tc_free(h);
+  const GGeom &g = h->geom;
+  const int na_tot = g.natoms;
+  // D tiles
+  h->tile_off.assign(h->npairs + 1, 0);
+  for (int I = 0; I < na_tot; ++I)
+    for (int p = h->pair_row[I]; p < h->pair_row[I + 1]; ++p) {
+      const int J = h->pair_col[p];
+      h->tile_off[p + 1] = h->tile_off[p] + (long long)h->atom_norb[I] * g.sp[h->species_host[J]].porb;
+    }
+  h->ntile_elems = h->tile_off[h->npairs];
+  if (cudaMalloc(&h->Dt_hi, std::max<long long>(h->ntile_elems, 8) * sizeof(__half)) != cudaSuccess ||
+      cudaMalloc(&h->Dt_lo, std::max<long long>(h->ntile_elems, 8) * sizeof(__half)) != cudaSuccess ||
+      cudaMalloc(&h->tile_off_dev, (h->npairs + 1) * sizeof(long long)) != cudaSuccess ||
+      cudaMalloc(&h->scales, 8 * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return GINT_ENOMEM;
+  }
+  TC_CHECK(cudaMemcpy(h->tile_off_dev, h->tile_off.data(), (h->npairs + 1) * sizeof(long long),
+                      cudaMemcpyHostToDevice));
+  // brick slot lists on the host
+  const long long nb = g.nbricks;
+  std::vector<long long> at_off(nb + 1);
+  std::vector<int> satom(std::max<long long>(h->nslots, 1));
+  TC_CHECK(cudaMemcpy(at_off.data(), h->b_at_off, (nb + 1) * sizeof(long long), cudaMemcpyDeviceToHost));
+  if (h->nslots) TC_CHECK(cudaMemcpy(satom.data(), h->s_atom, h->nslots * sizeof(int), cudaMemcpyDeviceToHost));
+  std::vector<long long> hs_off(nb + 1, 0);
+  std::vector<long long> cnt(h->npairs + 1, 0);
+  int npmax = 0;
+  auto find_pair = [&](int I, int J) -> int {
+    auto b = h->pair_col.begin() + h->pair_row[I], e = h->pair_col.begin() + h->pair_row[I + 1];
+    auto it = std::lower_bound(b, e, J);
+    return (it != e && *it == J) ? (int)(it - h->pair_col.begin()) : -1;
+  };
+  std::vector<int> no;
+  // pass 1: sizes and counts
+  for (long long b = 0; b < nb; ++b) {
+    const long long s0 = at_off[b], s1 = at_off[b + 1];
+    int cur = 0;
+    long long cum = 0;
+    no.assign(s1 - s0, 0);
+    for (long long s = s0; s < s1; ++s) {
+      const GSpecies &S = g.sp[h->species_host[satom[s]]];
+      cur = place_slot(cur, S.porb) + S.porb;
+      no[s - s0] = S.norb;
+      cum += S.norb;
+    }
+    npmax = std::max(npmax, (cur + 15) & ~15);
+    long long tot = 0, rest = cum;
+    for (long long a = 0; a < s1 - s0; ++a) {
+      tot += (long long)no[a] * rest;
+      rest -= no[a];
+    }
+    hs_off[b + 1] = hs_off[b] + tot;
+    for (long long a = s0; a < s1; ++a)
+      for (long long c = a; c < s1; ++c) {
+        const int p = find_pair(satom[a], satom[c]);
+        if (p >= 0) cnt[p + 1]++;
+      }
+  }
+  h->max_brick_porb = npmax;
+  h->hs_elems = hs_off[nb];
+  // upper pairs (I <= J) and their contribution lists (CSR, brick order)
+  std::vector<int> upair;
+  std::vector<long long> uoff(1, 0);
+  std::vector<long long> pstart(h->npairs, -1);
+  for (int I = 0; I < na_tot; ++I)
+    for (int p = h->pair_row[I]; p < h->pair_row[I + 1]; ++p)
+      if (h->pair_col[p] >= I) {
+        pstart[p] = uoff.back();
+        upair.push_back(p);
+        uoff.push_back(uoff.back() + cnt[p + 1]);
+      }
+  std::vector<long long> src(std::max<long long>(uoff.back(), 1));
+  std::vector<long long> fill(h->npairs, 0);
+  for (long long b = 0; b < nb; ++b) {
+    const long long s0 = at_off[b], s1 = at_off[b + 1];
+    no.assign(s1 - s0, 0);
+    long long cum = 0;
+    for (long long s = s0; s < s1; ++s) {
+      no[s - s0] = g.sp[h->species_host[satom[s]]].norb;
+      cum += no[s - s0];
+    }
+    long long rowst = 0, cumno_a = 0;
+    for (long long a = 0; a < s1 - s0; ++a) {
+      long long cumno_c = cumno_a;
+      for (long long c = a; c < s1 - s0; ++c) {
+        const int p = find_pair(satom[s0 + a], satom[s0 + c]);
+        if (p >= 0) src[pstart[p] + fill[p]++] = hs_off[b] + rowst + (long long)no[a] * (cumno_c - cumno_a);
+        cumno_c += no[c];
+      }
+      rowst += (long long)no[a] * (cum - cumno_a);
+      cumno_a += no[a];
+    }
+  }
+  h->nupper = (int)upair.size();
+  if (cudaMalloc(&h->hs_brick_off, (nb + 1) * sizeof(long long)) != cudaSuccess ||
+      cudaMalloc(&h->hs, std::max<long long>(h->hs_elems, 1) * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&h->hu_pair, std::max<size_t>(upair.size(), 1) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->hu_off, uoff.size() * sizeof(long long)) != cudaSuccess ||
+      cudaMalloc(&h->hu_src, src.size() * sizeof(long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return GINT_ENOMEM;
+  }
+  TC_CHECK(cudaMemcpy(h->hs_brick_off, hs_off.data(), (nb + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+  if (!upair.empty())
+    TC_CHECK(cudaMemcpy(h->hu_pair, upair.data(), upair.size() * sizeof(int), cudaMemcpyHostToDevice));
+  TC_CHECK(cudaMemcpy(h->hu_off, uoff.data(), uoff.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  TC_CHECK(cudaMemcpy(h->hu_src, src.data(), src.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  return GINT_OK;
+}
+
+int gint_tc_check_capacity(const gint_handle *h) {
+  if (h->max_brick_porb > kNPMAX || h->max_brick_atoms > kMAXA || h->max_brick_ent > kMAXE ||
+      h->max_species_norb > GINT_MAX_ORB_ATOM || h->ntile_elems > 0x7fffffffLL || !h->Dt_hi)
+    return GINT_ECAPACITY;
+  return GINT_OK;
+}
+
+static int compute_scales(gint_handle *h, const double *D, const double *V, cudaStream_t st) {
+  unsigned *mx = reinterpret_cast<unsigned *>(h->scales + 4);
+  TC_CHECK(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned), st));
+  if (D && h->nblock > 0) k_absmax<<<2 * h->num_sms, 256, 0, st>>>(D, h->nblock, mx);
+  if (V) k_absmax<<<2 * h->num_sms, 256, 0, st>>>(V, h->geom.ngrid, mx + 1);
+  k_scales<<<1, 1, 0, st>>>(mx, h->phi_bound, h->geom.w, h->scales);
+  TC_CHECK(cudaGetLastError());
+  return GINT_OK;
+}
+
+int gint_tc_rho(gint_handle *h, int precision, const double *D, double *rho, const double *V, double *F,
+                cudaStream_t st) {
+  int rc = gint_tc_check_capacity(h);
+  if (rc) return rc;
+  if (h->geom.nbricks == 0) return GINT_OK;
+  const int split3 = precision == GINT_F16X3 ? 1 : 0;
+  if ((rc = compute_scales(h, D, nullptr, st))) return rc;
+  if (h->npairs > 0)
+    k_build_tiles<<<h->npairs, 128, 0, st>>>(D, h->pair_I_dev, h->pair_col_dev, h->pair_off_dev, h->tile_off_dev,
+                                             h->species_dev, h->geom, h->scales, h->Dt_hi, h->Dt_lo);
+  TC_CHECK(cudaGetLastError());
+  const int np = std::max(h->max_brick_porb, kRC);
+  const uint32_t smem = rho_smem_bytes(np);
+  TC_CHECK(cudaMemsetAsync(h->work_ctr, 0, sizeof(int), st));
+  const unsigned grid = (unsigned)std::min<long long>(h->num_sms, h->geom.nbricks);
+  if (F) {
+    auto kern = k_tc_rho<true>;
+    if ((rc = set_smem(kern, smem))) return rc;
+    kern<<<grid, kT, smem, st>>>(h->geom, h->nbr(), h->tab32, h->Dt_hi, h->Dt_lo, h->tile_off_dev, h->scales, V, rho,
+                                 F, h->work_ctr, h->err_word, np, split3);
+  } else {
+    auto kern = k_tc_rho<false>;
+    if ((rc = set_smem(kern, smem))) return rc;
+    kern<<<grid, kT, smem, st>>>(h->geom, h->nbr(), h->tab32, h->Dt_hi, h->Dt_lo, h->tile_off_dev, h->scales, V, rho,
+                                 F, h->work_ctr, h->err_word, np, split3);
+  }
+  TC_CHECK(cudaGetLastError());
+  return GINT_OK;
+}
+
+int gint_tc_vlocal(gint_handle *h, int precision, const double *V, double *H, cudaStream_t st) {
+  int rc = gint_tc_check_capacity(h);
+  if (rc) return rc;
+  if (h->max_brick_porb > kNPMAXH) return GINT_ECAPACITY;
+  if (h->geom.nbricks == 0) return GINT_OK;
+  const int split3 = precision == GINT_F16X3 ? 1 : 0;
+  if ((rc = compute_scales(h, nullptr, V, st))) return rc;
+  const int np = std::max(h->max_brick_porb, 16);
+  const uint32_t smem = h_smem_bytes(np);
+  TC_CHECK(cudaMemsetAsync(h->work_ctr, 0, sizeof(int), st));
+  const unsigned grid = (unsigned)std::min<long long>(h->num_sms, h->geom.nbricks);
+  if ((rc = set_smem(k_tc_vlocal, smem))) return rc;
+  k_tc_vlocal<<<grid, kT, smem, st>>>(h->geom, h->nbr(), h->tab32, h->tile_off_dev, h->scales, V, h->hs_brick_off,
+                                      h->hs, h->work_ctr, h->err_word, np, split3);
+  TC_CHECK(cudaGetLastError());
+  if (h->nupper > 0) {
+    k_h_reduce<<<h->nupper, 192, 0, st>>>(h->hu_pair, h->hu_off, h->hu_src, h->hs, h->pair_I_dev, h->pair_col_dev,
+                                          h->pair_T_dev, h->pair_off_dev, h->species_dev, h->geom, H);
+    TC_CHECK(cudaGetLastError());
+  }
+  return GINT_OK;
+}
+
+extern "C" int gint_tc_selftest(int n, double *max_err) {
+  if (n < 16 || n > 256 || (n % 16) || !max_err) return GINT_EINVAL;
+  float *d_err = nullptr;
+  unsigned *d_status = nullptr;
+  if (cudaMalloc(&d_err, sizeof(float)) != cudaSuccess) return GINT_ENOMEM;
+  if (cudaMalloc(&d_status, sizeof(unsigned)) != cudaSuccess) {
+    cudaFree(d_err);
+    return GINT_ENOMEM;
+  }
+  int rc = GINT_OK;
+  cudaMemset(d_err, 0, sizeof(float));
+  cudaMemset(d_status, 0, sizeof(unsigned));
+  const uint32_t smem = 48 * kHSBO;
+  if (set_smem(k_tc_selftest, smem) != GINT_OK) rc = GINT_ECUDA;
+  if (!rc) {
+    k_tc_selftest<<<1, 128, smem>>>(n, d_err, d_status);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) rc = GINT_ECUDA;
+  }
+  float e = -1.f;
+  unsigned status = 0;
+  if (!rc) {
+    cudaMemcpy(&e, d_err, sizeof(float), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&status, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (status) rc = GINT_ETIMEDOUT;
+  }
+  *max_err = (double)e;
+  cudaFree(d_err);
+  cudaFree(d_status);
+  return rc;
+}

@@ -16,8 +16,8 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgint.so")
 
-FP64, FP32, TF32X3, TF32X1 = 0, 1, 2, 3
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3, "tf32x1": TF32X1}
+FP64, FP32, F16X3, F16X1 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "f16x3": F16X3, "f16x1": F16X1}
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libgint.so is not built ({LIB_PATH}); run `python -m paper_2603_21835_gb300.build`")
@@ -63,10 +63,20 @@ _lib.gint_grid_dot.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.gint_block_dot.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.gint_weight.restype = _d
 _lib.gint_weight.argtypes = [_vp]
+_lib.gint_sync.argtypes = [_vp, _vp]
+_lib.gint_tc_selftest.argtypes = [_i, ctypes.POINTER(_d)]
 
 C_ABI_SYMBOLS = ("gint_create", "gint_destroy", "gint_layout", "gint_pairs", "gint_stats", "gint_set_positions",
                  "gint_rho", "gint_vlocal", "gint_force", "gint_grid_dot", "gint_block_dot", "gint_weight",
-                 "gint_strerror")
+                 "gint_strerror", "gint_sync", "gint_tc_selftest")
+
+
+def tc_selftest(n: int = 256) -> float:
+    """Largest deviation of one tcgen05 f16 MMA (M=128, N=n, K=16, integer data) from exact,
+    over the three shared-memory operand layouts the brick kernels use."""
+    e = _d()
+    _check(_lib.gint_tc_selftest(int(n), ctypes.byref(e)), "gint_tc_selftest")
+    return e.value
 
 
 def _check(code: int, where: str):
@@ -188,6 +198,10 @@ class Gint:
         _check(_lib.gint_block_dot(self._h, _dptr(A, numel=self.nblock), _dptr(B, numel=self.nblock), _dptr(out),
                                    _stream(stream)), "gint_block_dot")
         return out
+
+    def sync(self, stream=None):
+        """Waits for the stream; raises if a kernel recorded an error (e.g. a bounded wait timed out)."""
+        _check(_lib.gint_sync(self._h, _stream(stream)), "gint_sync")
 
     def set_positions(self, pos: torch.Tensor, stream=None):
         _check(_lib.gint_set_positions(self._h, _dptr(pos, numel=3 * self.natoms), _stream(stream)),
