@@ -145,6 +145,25 @@ int gint_sync(gint_handle *h, void *stream);
  * the exact product in *max_err (host).  n in {16, ..., 256}, multiple of 16.  Synchronous. */
 int gint_tc_selftest(int n, double *max_err);
 
+/* Float64 dot product that allocates no device memory (the paper has no counterpart; this
+ * entry point exists for callers that cannot let a library allocate: applications whose device
+ * memory is owned by their own pool allocator, or latency-critical loops that cannot accept the
+ * implicit synchronisation of cudaMalloc / cudaFree).
+ *   out_dev[0] = scale * sum_i a[i] * b[i]   (b == NULL: scale * sum_i a[i])
+ * a, b, out_dev are caller-owned device pointers; the call is asynchronous on `stream`.  The sum
+ * runs over fixed chunks of GINT_NOALLOC_CHUNK elements, so the result does not depend on the GPU.
+ * Scratch: one float64 partial per chunk in a file-scope __device__ array of
+ * GINT_NOALLOC_MAX_CHUNKS entries (32 KiB) that every GPU loading the library keeps until exit;
+ * n above GINT_NOALLOC_MAX_CHUNKS * GINT_NOALLOC_CHUNK returns GINT_ECAPACITY.  The first call on
+ * a device looks up the array's device address on that device (once per device, with it
+ * current), so that first call should come before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU (other streams, other host threads) race.
+ * Returns GINT_EINVAL for a NULL a / out_dev or negative n, GINT_ECUDA on CUDA failure. */
+#define GINT_NOALLOC_CHUNK 65536LL
+#define GINT_NOALLOC_MAX_CHUNKS 4096
+int gint_grid_dot_noalloc(const double *a, const double *b, long long n, double scale, double *out_dev,
+                          void *stream);
+
 /* Grid weight w = |det A| / (n1 n2 n3). */
 double gint_weight(const gint_handle *h);
 

@@ -65,10 +65,11 @@ _lib.gint_weight.restype = _d
 _lib.gint_weight.argtypes = [_vp]
 _lib.gint_sync.argtypes = [_vp, _vp]
 _lib.gint_tc_selftest.argtypes = [_i, ctypes.POINTER(_d)]
+_lib.gint_grid_dot_noalloc.argtypes = [_vp, _vp, _ll, _d, _vp, _vp]
 
 C_ABI_SYMBOLS = ("gint_create", "gint_destroy", "gint_layout", "gint_pairs", "gint_stats", "gint_set_positions",
                  "gint_rho", "gint_vlocal", "gint_force", "gint_grid_dot", "gint_block_dot", "gint_weight",
-                 "gint_strerror", "gint_sync", "gint_tc_selftest")
+                 "gint_strerror", "gint_sync", "gint_tc_selftest", "gint_grid_dot_noalloc")
 
 
 def tc_selftest(n: int = 256) -> float:
