@@ -216,6 +216,17 @@ int gint_create(const gint_desc *d, gint_handle **out) {
     }
     GS.rcut2 = GS.rcut * GS.rcut;
     GS.porb = (GS.norb + 7) / 8 * 8;
+    {
+      int cnt[3] = {0, 0, 0};
+      bool sorted = true, same = true;
+      for (int k = 0; k < S.nradial; ++k) {
+        const gint_radial &R = S.radial[k];
+        cnt[R.l]++;
+        if (k > 0 && R.l < S.radial[k - 1].l) sorted = false;
+        if (R.npts != S.radial[0].npts || R.dr != S.radial[0].dr) same = false;
+      }
+      GS.shape = (sorted && same && cnt[0] < 8 && cnt[1] < 8 && cnt[2] < 8) ? GINT_SHAPE(cnt[0], cnt[1], cnt[2]) : 0;
+    }
     h->max_species_norb = std::max(h->max_species_norb, GS.norb);
     double fmax = 0;
     for (int k = 0; k < S.nradial; ++k)

@@ -53,7 +53,10 @@ struct gint_handle {
   double phi_bound = 0;       // bound on |phi| used for the orbital scale
   std::vector<long long> tile_off;        // per pair: element offset of its padded D tile
   long long ntile_elems = 0;
-  __half *Dt_hi = nullptr, *Dt_lo = nullptr;  // D tiles: rows norb(I), K = porb(J) (zero padded)
+  // D tiles in 128-byte core-matrix order: rows roundup(norb(I), 8), K = porb(J) (zero padded);
+  // *_h2 hold the same tiles halved (diagonal chunk of the density pass)
+  __half *Dt_hi = nullptr, *Dt_lo = nullptr, *Dt_hi2 = nullptr, *Dt_lo2 = nullptr;
+  __half *zero_dev = nullptr;  // 256 zero bytes: source of the bulk copies for absent tiles
   long long *tile_off_dev = nullptr;
   float *scales = nullptr;    // device: [0] S_phi, [1] S_D (density), [2] S_Q (local H)
   int max_brick_porb = 0;     // largest padded (aligned) orbital count of a brick

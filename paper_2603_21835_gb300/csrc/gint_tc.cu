@@ -10,13 +10,14 @@
 //
 // Layout: the orbitals of each atom occupy porb = roundup(norb, 8) columns of the brick's
 // orbital space (zero padded), no atom crosses a multiple of 128 columns, NP = padded total.
-// D is pre-tiled per atom pair into float16 (hi, lo) rows of porb(J) values, so that every
-// 16-byte segment of a B operand row is one cp.async from global memory.
+// D is pre-tiled per atom pair into float16 (hi, lo) 128-byte core matrices, so a B operand
+// row group of 8 rows x 8 columns is one bulk (TMA) copy from global memory.
 //
 // Density (D symmetric): columns are streamed in chunks of 16.  With the chunk's own
 // diagonal block halved, rho = 2 sum_k P_k Y_k where Y_k accumulates P_j D_jk over the chunks
 // j <= chunk(k) only, so chunk c's columns are final right after chunk c's MMA: the epilogue of
-// chunk c overlaps the MMA of chunk c+1 and the MMA work is halved.
+// chunk c overlaps the MMA of chunk c+1 and the MMA work is halved.  Within a brick a producer
+// warp (bulk copies), one MMA thread and four epilogue warps run decoupled by mbarriers.
 // Force: full Y = P D (all chunks, all columns), then per atom 2 w V grad(phi) . Y.
 // Local H: K = grid points (chunks of 32), M = N = orbitals (128-row tiles, upper block
 // triangle); each brick writes its float32 slot-pair tiles to a scratch area and a per-pair
@@ -44,6 +45,7 @@ constexpr uint32_t kHLBO = 144;  // local-H operands: padded K-direction core-ma
 constexpr uint32_t kHSBO = 576;  // 4 core matrices of K per 8-row group
 constexpr long long kWaitNs = 2000000000LL;  // bounded mbarrier waits: 2 s
 constexpr unsigned char kNoSlot = 255;
+constexpr int kProducerWarp = 4, kMmaWarp = 5;
 
 // ------------------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -71,12 +73,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsign
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = globaltimer();
   while (!mbar_try_wait(bar, parity)) {
+    __nanosleep(32);
     if (globaltimer() - t0 > kWaitNs) {
       atomicOr(err, GINT_ERRBIT_TIMEOUT);
       return false;
     }
   }
   return true;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// 1-D bulk copy global -> shared, completing `bytes` of transactions on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -129,12 +145,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // x = hi + lo with both parts float16 (hi = round(x), lo = round(x - hi)).
 __device__ __forceinline__ void split_h(float x, __half &hi, __half &lo) {
@@ -145,21 +155,37 @@ __device__ __forceinline__ uint32_t pack2(__half a, __half b) {
   return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
 
-// ------------------------------------------------------------------------------ compensated float32
+// ------------------------------------------------------------------------------ orbital evaluation
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   s = a + b;
   const float bb = s - a;
   e = (a - (s - bb)) + (b - bb);
 }
 
-// Cubic Hermite of the tabulated (f, f') at r = rh + rl (double-float), float32 arithmetic with
-// an exact knot index and a knot parameter t accurate to float32 rounding.
-__device__ __forceinline__ void radial_df(const float2 *__restrict__ tab, const GRadial &R, float rh, float rl, float &f,
-                                          float &df) {
+// r = |dh + dl| as a double-float (rh, rl) and 1/rh; at0 when the point is on the atom.
+__device__ __forceinline__ void dist_df(const float dh[3], const float dl[3], float &rh, float &rl, float &ir,
+                                        bool &at0) {
+  const float px = dh[0] * dh[0], py = dh[1] * dh[1], pz = dh[2] * dh[2];
+  const float ex = fmaf(dh[0], dh[0], -px), ey = fmaf(dh[1], dh[1], -py), ez = fmaf(dh[2], dh[2], -pz);
+  float s1, e1, s2, e2;
+  two_sum(px, py, s1, e1);
+  two_sum(s1, pz, s2, e2);
+  float r2l = (ex + ey + ez) + (e1 + e2) + 2.f * (dh[0] * dl[0] + dh[1] * dl[1] + dh[2] * dl[2]);
+  const float r2h = s2 + r2l;
+  r2l = r2l - (r2h - s2);
+  at0 = r2h < 1e-24f;
+  rh = at0 ? 0.f : sqrtf(r2h);
+  ir = at0 ? 0.f : 1.f / rh;
+  rl = at0 ? 0.f : (fmaf(-rh, rh, r2h) + r2l) * (0.5f * ir);
+}
+
+// Knot index i and parameter t in [0,1) of r = rh + rl on a grid of spacing 1/idr (exact index,
+// t accurate to float32 rounding).  Returns false beyond the table.
+__device__ __forceinline__ bool knot_df(const GRadial &R, float rh, float rl, int &i, float &t) {
   const float xh = rh * R.idr_hi;
   const float xl = fmaf(rh, R.idr_hi, -xh) + (rl * R.idr_hi + rh * R.idr_lo);
-  int i = (int)floorf(xh);
-  float t = (xh - (float)i) + xl;
+  i = (int)floorf(xh);
+  t = (xh - (float)i) + xl;
   if (t < 0.f) {
     i -= 1;
     t += 1.f;
@@ -171,45 +197,50 @@ __device__ __forceinline__ void radial_df(const float2 *__restrict__ tab, const 
     i = 0;
     t = 0.f;
   }
-  if (i >= R.npts - 1) {
-    f = 0.f;
-    df = 0.f;
-    return;
-  }
-  const float2 a = tab[R.off + i], b = tab[R.off + i + 1];
-  const float g0 = a.y * R.dr_f, g1 = b.y * R.dr_f;
-  const float t2 = t * t, u = 1.f - t;
-  const float s = t2 * (3.f - 2.f * t);
-  f = a.x + (b.x - a.x) * s + g0 * t * u * u + g1 * t2 * (t - 1.f);
-  df = ((b.x - a.x) * 6.f * t * u + g0 * u * (1.f - 3.f * t) + g1 * t * (3.f * t - 2.f)) * R.idr_hi;
+  return i < R.npts - 1;
 }
 
-// Adds phi (and grad phi if GRAD) of one image of species sp at displacement dh + dl to
-// v[0..norb) and gv[3*i + c].  |d| < rcut is tested by the caller.
+// Cubic Hermite basis in t: value weights (s = h01, c0 = h10, c1 = h11; h00 = 1 - s) and derivative
+// weights (ds = dh01/dt, d0 = dh10/dt, d1 = dh11/dt).
+struct Basis {
+  float s, c0, c1, ds, d0, d1;
+};
+__device__ __forceinline__ Basis hermite_basis(float t) {
+  Basis B;
+  const float t2 = t * t, u = 1.f - t;
+  B.s = t2 * (3.f - 2.f * t);
+  B.c0 = t * u * u;
+  B.c1 = t2 * (t - 1.f);
+  B.ds = 6.f * t * u;
+  B.d0 = u * (1.f - 3.f * t);
+  B.d1 = t * (3.f * t - 2.f);
+  return B;
+}
+__device__ __forceinline__ void radial_at(const float2 *__restrict__ tab, const GRadial &R, int i, const Basis &B,
+                                          float &f, float &df) {
+  const float2 a = tab[R.off + i], b = tab[R.off + i + 1];
+  const float dlt = b.x - a.x;
+  f = a.x + dlt * B.s + R.dr_f * (a.y * B.c0 + b.y * B.c1);
+  df = (dlt * B.ds + R.dr_f * (a.y * B.d0 + b.y * B.d1)) * R.idr_hi;
+}
+
+// Generic path (any radial order or knot grids): adds one image to v[col] (+ gv[3 col + c]).
 template <bool GRAD>
-__device__ __forceinline__ void add_atom_df(const GGeom &g, const float2 *__restrict__ tab, int sp, const float dh[3],
-                                            const float dl[3], float *v, float *gv) {
-  const GSpecies &S = g.sp[sp];
-  const float px = dh[0] * dh[0], py = dh[1] * dh[1], pz = dh[2] * dh[2];
-  const float ex = fmaf(dh[0], dh[0], -px), ey = fmaf(dh[1], dh[1], -py), ez = fmaf(dh[2], dh[2], -pz);
-  float s1, e1, s2, e2;
-  two_sum(px, py, s1, e1);
-  two_sum(s1, pz, s2, e2);
-  float r2l = (ex + ey + ez) + (e1 + e2) + 2.f * (dh[0] * dl[0] + dh[1] * dl[1] + dh[2] * dl[2]);
-  const float r2h = s2 + r2l;
-  r2l = r2l - (r2h - s2);
-  const bool at0 = r2h < 1e-24f;
-  const float r = at0 ? 0.f : sqrtf(r2h);
-  const float ir = at0 ? 0.f : 1.f / r;
-  const float rl = at0 ? 0.f : (fmaf(-r, r, r2h) + r2l) * (0.5f * ir);
+__device__ void add_image_generic(const GGeom &g, const float2 *__restrict__ tab, const GSpecies &S, const float dh[3],
+                                  const float dl[3], float *v, float *gv) {
+  float r, rl, ir;
+  bool at0;
+  dist_df(dh, dl, r, rl, ir, at0);
   const float ux = dh[0] * ir, uy = dh[1] * ir, uz = dh[2] * ir;
   int col = 0;
   for (int k = 0; k < S.nrad; ++k) {
     const GRadial &R = g.rad[S.rad0 + k];
     const int l = R.l, nm = 2 * l + 1;
-    if (r < R.rc_f) {
+    int i;
+    float t;
+    if (r < R.rc_f && knot_df(R, r, rl, i, t)) {
       float f, df;
-      radial_df(tab, R, r, rl, f, df);
+      radial_at(tab, R, i, hermite_basis(t), f, df);
       if (at0) {
         if (l == 0) v[col] += f * 0.28209479177387814347f;
         if (GRAD && l == 1) {
@@ -237,19 +268,106 @@ __device__ __forceinline__ void add_atom_df(const GGeom &g, const float2 *__rest
   }
 }
 
+// Fast path for l-sorted species (NS s, NP p, ND d radials) on one knot grid: one knot/basis
+// computation per image, all column indices static (register arrays).
+template <int NS, int NPR, int ND, bool GRAD>
+__device__ __forceinline__ void add_image_fast(const GGeom &g, const float2 *__restrict__ tab, const GSpecies &S,
+                                               const float dh[3], const float dl[3], float *v, float *gv) {
+  float r, rl, ir;
+  bool at0;
+  dist_df(dh, dl, r, rl, ir, at0);
+  const GRadial &R0 = g.rad[S.rad0];
+  int i;
+  float t;
+  if (!knot_df(R0, r, rl, i, t)) return;
+  const Basis B = hermite_basis(t);
+  const float ux = dh[0] * ir, uy = dh[1] * ir, uz = dh[2] * ir;
+  const float Y0 = 0.28209479177387814347f;
+  float y1[3], gy1[3][3], y2[5], gy2[5][3];
+  if (NPR > 0) ylm_unit<float>(1, ux, uy, uz, y1, gy1);
+  if (ND > 0) ylm_unit<float>(2, ux, uy, uz, y2, gy2);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const GRadial &R = g.rad[S.rad0 + k];
+    if (r < R.rc_f) {
+      float f, df;
+      radial_at(tab, R, i, B, f, df);
+      v[k] += f * Y0;
+      if (GRAD && !at0) {
+        const float a = df * Y0;
+        gv[3 * k + 0] += a * ux;
+        gv[3 * k + 1] += a * uy;
+        gv[3 * k + 2] += a * uz;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NPR; ++k) {
+    const GRadial &R = g.rad[S.rad0 + NS + k];
+    const int col = NS + 3 * k;
+    if (r < R.rc_f) {
+      float f, df;
+      radial_at(tab, R, i, B, f, df);
+      if (at0) {
+        if (GRAD) {
+          const float c = 0.48860251190291992159f * df;
+          gv[3 * (col + 0) + 2] += c;
+          gv[3 * (col + 1) + 0] += c;
+          gv[3 * (col + 2) + 1] += c;
+        }
+      } else {
+        const float fr = f * ir;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          v[col + m] += f * y1[m];
+          if (GRAD) {
+            const float a = df * y1[m] - fr * y1[m];
+            gv[3 * (col + m) + 0] += a * ux + fr * gy1[m][0];
+            gv[3 * (col + m) + 1] += a * uy + fr * gy1[m][1];
+            gv[3 * (col + m) + 2] += a * uz + fr * gy1[m][2];
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < ND; ++k) {
+    const GRadial &R = g.rad[S.rad0 + NS + NPR + k];
+    const int col = NS + 3 * NPR + 5 * k;
+    if (r < R.rc_f && !at0) {
+      float f, df;
+      radial_at(tab, R, i, B, f, df);
+      const float fr = f * ir;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        v[col + m] += f * y2[m];
+        if (GRAD) {
+          const float a = df * y2[m] - 2.f * fr * y2[m];
+          gv[3 * (col + m) + 0] += a * ux + fr * gy2[m][0];
+          gv[3 * (col + m) + 1] += a * uy + fr * gy2[m][1];
+          gv[3 * (col + m) + 2] += a * uz + fr * gy2[m][2];
+        }
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------ brick metadata
+constexpr int kMaxStages = 4;
+constexpr int kMaxChunks = kNPMAX / kRC;
 struct BrickSh {
-  uint64_t bar[2];
+  uint64_t full[kMaxStages];  // density: B stage loaded (bulk-copy transactions)
+  uint64_t done[kMaxChunks];  // density: MMAs of chunk c complete (one use per brick); local H: stages
   uint32_t tmem;
   int brick, na, np, nent, abort;
   int s_atom[kMAXA], s_no[kMAXA], s_po[kMAXA], s_sp[kMAXA], s_pcol[kMAXA], s_e0[kMAXA + 1];
-  int s_cumno[kMAXA + 1];       // prefix of norb over slots
-  int s_rowst[kMAXA];           // local-H scratch: first element of slot a's tile row
+  int s_cumpo[kMAXA + 1];       // prefix of porb over slots
+  int s_rowst[kMAXA];           // local-H scratch: first element of slot a's row of tiles
   int s_tile[kMAXA * kMAXA];    // D tile element offset of (row slot b, K slot a), -1 if none
   float e_hi[kMAXE][3], e_lo[kMAXE][3];  // entry positions relative to the brick origin
   float pt_hi[128][3], pt_lo[128][3];    // grid point positions relative to the brick origin
   unsigned char col2slot[kNPMAX];
-  float fpart[kMAXA][3];
+  double fpart[kMAXA][3];
   float rpart[4][128];
   float sc[4];  // scales
 };
@@ -296,7 +414,7 @@ __device__ void load_brick(const GGeom &g, const GNbr &nb, const long long *__re
     sh.s_no[a] = g.sp[sp].norb;
     sh.s_po[a] = g.sp[sp].porb;
     sh.s_e0[a] = (int)(nb.s_ent[s0 + a] - e_begin);
-    sh.fpart[a][0] = sh.fpart[a][1] = sh.fpart[a][2] = 0.f;
+    sh.fpart[a][0] = sh.fpart[a][1] = sh.fpart[a][2] = 0.0;
   }
   for (int e = t; e < nent; e += blockDim.x)
     for (int c = 0; c < 3; ++c) split2(nb.e_shift[3 * (e_begin + e) + c] - ob[c], sh.e_hi[e][c], sh.e_lo[e][c]);
@@ -311,15 +429,15 @@ __device__ void load_brick(const GGeom &g, const GNbr &nb, const long long *__re
       const int pc = place_slot(cur, sh.s_po[a]);
       sh.s_pcol[a] = pc;
       cur = pc + sh.s_po[a];
-      sh.s_cumno[a] = cum;
-      cum += sh.s_no[a];
+      sh.s_cumpo[a] = cum;
+      cum += sh.s_po[a];
     }
-    sh.s_cumno[na] = cum;
+    sh.s_cumpo[na] = cum;
     sh.np = (cur + 15) & ~15;
     int rs = 0;
     for (int a = 0; a < na; ++a) {
       sh.s_rowst[a] = rs;
-      rs += sh.s_no[a] * (cum - sh.s_cumno[a]);
+      rs += sh.s_po[a] * (cum - sh.s_cumpo[a]);
     }
   }
   __syncthreads();
@@ -333,47 +451,234 @@ __device__ void load_brick(const GGeom &g, const GNbr &nb, const long long *__re
   __syncthreads();
 }
 
-__device__ __forceinline__ void rel_disp_df(const BrickSh &sh, int p, int e, float dh[3], float dl[3]) {
+// Grid point position relative to the brick origin as a double-float (held in registers).
+struct PointDF {
+  float h[3], l[3];
+};
+__device__ __forceinline__ PointDF point_df(const BrickSh &sh, int p) {
+  PointDF P;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    P.h[c] = sh.pt_hi[p][c];
+    P.l[c] = sh.pt_lo[p][c];
+  }
+  return P;
+}
+__device__ __forceinline__ void rel_disp_df(const BrickSh &sh, const PointDF &P, int e, float dh[3], float dl[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float s, err;
-    two_sum(sh.pt_hi[p][c], -sh.e_hi[e][c], s, err);
-    const float lo = err + (sh.pt_lo[p][c] - sh.e_lo[e][c]);
+    two_sum(P.h[c], -sh.e_hi[e][c], s, err);
+    const float lo = err + (P.l[c] - sh.e_lo[e][c]);
     dh[c] = s + lo;
     dl[c] = lo - (dh[c] - s);
   }
 }
 
-// Periodised orbitals (all images) of slot a at local point p into v[0..norb) (+ gradients).
-template <bool GRAD>
-__device__ __forceinline__ void eval_slot(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
-                                          int p, float *v, float *gv) {
-  const int sp = sh.s_sp[a];
-  const float rc2 = (float)g.sp[sp].rcut2;
+// Periodised orbitals (all images) of slot a at local point p: v[PO] (+ gv[3 PO]), zero based.
+template <int NS, int NPR, int ND, bool GRAD>
+__device__ __forceinline__ void slot_values(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
+                                            const PointDF &P, bool valid, float *v, float *gv) {
+  constexpr int PO = (NS + 3 * NPR + 5 * ND + 7) / 8 * 8;
+#pragma unroll
+  for (int i = 0; i < PO; ++i) {
+    v[i] = 0.f;
+    if (GRAD) gv[3 * i] = gv[3 * i + 1] = gv[3 * i + 2] = 0.f;
+  }
+  if (!valid) return;
+  const GSpecies &S = g.sp[sh.s_sp[a]];
+  const float rc2 = (float)S.rcut2;
   for (int e = sh.s_e0[a]; e < sh.s_e0[a + 1]; ++e) {
     float dh[3], dl[3];
-    rel_disp_df(sh, p, e, dh, dl);
-    if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < rc2) add_atom_df<GRAD>(g, tab, sp, dh, dl, v, gv);
+    rel_disp_df(sh, P, e, dh, dl);
+    if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < rc2) {
+      if (NS + NPR + ND > 0)
+        add_image_fast<NS, NPR, ND, GRAD>(g, tab, S, dh, dl, v, gv);
+      else
+        add_image_generic<GRAD>(g, tab, S, dh, dl, v, gv);
+    }
   }
 }
 
-// rho epilogue of one 16-column chunk: sum_k (P_hi + P_lo)_k y_k for point p.
-__device__ __forceinline__ float chunk_dot(const unsigned char *Ph, const unsigned char *Pl, uint32_t sboP, int p,
-                                           int k0, const float *y) {
-  float part = 0.f;
+// Species shapes with a static fast path; others use the generic evaluator (NS=NPR=ND=0).
+#define GINT_FOR_SHAPES(X) X(2, 2, 1) X(2, 1, 0) X(1, 1, 1) X(1, 1, 0) X(1, 0, 0) X(3, 3, 2)
+
+// --- per-atom jobs ---
+// Density phase A: scaled orbitals of slot a at point p -> P row p, columns [pcol, pcol + PO).
+template <int PO>
+__device__ __forceinline__ void store_P(const float *v, int pc, int p, float Sphi, unsigned char *Ph,
+                                        unsigned char *Pl, uint32_t sboP) {
 #pragma unroll
-  for (int hseg = 0; hseg < 2; ++hseg) {
-    const uint32_t off = (p >> 3) * sboP + ((k0 >> 3) + hseg) * 128 + (p & 7) * 16;
-    const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + off), wl = *reinterpret_cast<const uint4 *>(Pl + off);
-    const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
+  for (int k = 0; k < PO; k += 8) {
+    uint32_t wh[4], wl[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
-      const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
-      part += (hf.x + lf.x) * y[hseg * 8 + 2 * e] + (hf.y + lf.y) * y[hseg * 8 + 2 * e + 1];
+      __half h0, l0, h1, l1;
+      split_h(v[k + 2 * e] * Sphi, h0, l0);
+      split_h(v[k + 2 * e + 1] * Sphi, h1, l1);
+      wh[e] = pack2(h0, h1);
+      wl[e] = pack2(l0, l1);
+    }
+    const uint32_t off = (p >> 3) * sboP + ((pc + k) >> 3) * 128 + (p & 7) * 16;
+    *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+    *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+  }
+}
+// Two atoms of the same shape at once (two independent evaluation chains per thread).
+template <int NS, int NPR, int ND, int PO>
+__device__ __forceinline__ void job_P2(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a0,
+                                       int a1, const PointDF &P, int p, bool valid, float Sphi, unsigned char *Ph,
+                                       unsigned char *Pl, uint32_t sboP) {
+  float v0[PO], v1[PO];
+  slot_values<NS, NPR, ND, false>(g, tab, sh, a0, P, valid, v0, nullptr);
+  slot_values<NS, NPR, ND, false>(g, tab, sh, a1, P, valid, v1, nullptr);
+  store_P<PO>(v0, sh.s_pcol[a0], p, Sphi, Ph, Pl, sboP);
+  store_P<PO>(v1, sh.s_pcol[a1], p, Sphi, Ph, Pl, sboP);
+}
+template <int NS, int NPR, int ND, int PO>
+__device__ __forceinline__ void job_P(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
+                                      const PointDF &P, int p, bool valid, float Sphi, unsigned char *Ph,
+                                      unsigned char *Pl, uint32_t sboP) {
+  float v[PO];
+  slot_values<NS, NPR, ND, false>(g, tab, sh, a, P, valid, v, nullptr);
+  const int pc = sh.s_pcol[a];
+#pragma unroll
+  for (int k = 0; k < PO; k += 8) {
+    uint32_t wh[4], wl[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      __half h0, l0, h1, l1;
+      split_h(v[k + 2 * e] * Sphi, h0, l0);
+      split_h(v[k + 2 * e + 1] * Sphi, h1, l1);
+      wh[e] = pack2(h0, h1);
+      wl[e] = pack2(l0, l1);
+    }
+    const uint32_t off = (p >> 3) * sboP + ((pc + k) >> 3) * 128 + (p & 7) * 16;
+    *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+    *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+  }
+}
+
+// Local H: A = w V phi (scaled), B = phi (scaled), rows [pcol, pcol + PO), K = point pp.
+template <int NS, int NPR, int ND, int PO>
+__device__ __forceinline__ void job_H(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a, int pt,
+                                      int pp, bool valid, float Sphi, float wvSA, unsigned char *Ah,
+                                      unsigned char *Al, unsigned char *Bh, unsigned char *Bl) {
+  float v[PO];
+  slot_values<NS, NPR, ND, false>(g, tab, sh, a, point_df(sh, pt), valid, v, nullptr);
+  const int pc = sh.s_pcol[a];
+#pragma unroll
+  for (int i = 0; i < PO; ++i) {
+    const int r = pc + i;
+    __half bh, bl, ah, al;
+    split_h(v[i] * Sphi, bh, bl);
+    split_h(v[i] * wvSA, ah, al);
+    const uint32_t off = (r >> 3) * kHSBO + (pp >> 3) * kHLBO + (r & 7) * 16 + (pp & 7) * 2;
+    *reinterpret_cast<__half *>(Bh + off) = bh;
+    *reinterpret_cast<__half *>(Bl + off) = bl;
+    *reinterpret_cast<__half *>(Ah + off) = ah;
+    *reinterpret_cast<__half *>(Al + off) = al;
+  }
+}
+
+// Force epilogue: y[PO] (true Y values of slot a's columns) -> rho part and force components.
+template <int NS, int NPR, int ND, int PO>
+__device__ __forceinline__ void job_F(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a, int p,
+                                      bool valid, const float *y, float &rp, float &fx, float &fy, float &fz) {
+  float v[PO], gv[3 * PO];
+  slot_values<NS, NPR, ND, true>(g, tab, sh, a, point_df(sh, p), valid, v, gv);
+#pragma unroll
+  for (int i = 0; i < PO; ++i) {
+    rp += v[i] * y[i];
+    fx += gv[3 * i] * y[i];
+    fy += gv[3 * i + 1] * y[i];
+    fz += gv[3 * i + 2] * y[i];
+  }
+}
+
+// Generic-shape jobs (any species up to GINT_MAX_ORB_ATOM orbitals).
+__device__ __noinline__ void job_P_generic(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
+                                           int p, bool valid, float Sphi, unsigned char *Ph, unsigned char *Pl,
+                                           uint32_t sboP) {
+  float v[GINT_MAX_ORB_ATOM];
+  const int po = sh.s_po[a], pc = sh.s_pcol[a];
+  for (int i = 0; i < po; ++i) v[i] = 0.f;
+  if (valid) {
+    const GSpecies &S = g.sp[sh.s_sp[a]];
+    for (int e = sh.s_e0[a]; e < sh.s_e0[a + 1]; ++e) {
+      float dh[3], dl[3];
+      rel_disp_df(sh, point_df(sh, p), e, dh, dl);
+      if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < (float)S.rcut2)
+        add_image_generic<false>(g, tab, S, dh, dl, v, nullptr);
     }
   }
-  return part;
+  for (int k = 0; k < po; k += 8) {
+    uint32_t wh[4], wl[4];
+    for (int e = 0; e < 4; ++e) {
+      __half h0, l0, h1, l1;
+      split_h(v[k + 2 * e] * Sphi, h0, l0);
+      split_h(v[k + 2 * e + 1] * Sphi, h1, l1);
+      wh[e] = pack2(h0, h1);
+      wl[e] = pack2(l0, l1);
+    }
+    const uint32_t off = (p >> 3) * sboP + ((pc + k) >> 3) * 128 + (p & 7) * 16;
+    *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+    *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+  }
+}
+__device__ __noinline__ void job_H_generic(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
+                                           int pt, int pp, bool valid, float Sphi, float wvSA, unsigned char *Ah,
+                                           unsigned char *Al, unsigned char *Bh, unsigned char *Bl) {
+  float v[GINT_MAX_ORB_ATOM];
+  const int po = sh.s_po[a], pc = sh.s_pcol[a];
+  for (int i = 0; i < po; ++i) v[i] = 0.f;
+  if (valid) {
+    const GSpecies &S = g.sp[sh.s_sp[a]];
+    for (int e = sh.s_e0[a]; e < sh.s_e0[a + 1]; ++e) {
+      float dh[3], dl[3];
+      rel_disp_df(sh, point_df(sh, pt), e, dh, dl);
+      if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < (float)S.rcut2)
+        add_image_generic<false>(g, tab, S, dh, dl, v, nullptr);
+    }
+  }
+  for (int i = 0; i < po; ++i) {
+    const int r = pc + i;
+    __half bh, bl, ah, al;
+    split_h(v[i] * Sphi, bh, bl);
+    split_h(v[i] * wvSA, ah, al);
+    const uint32_t off = (r >> 3) * kHSBO + (pp >> 3) * kHLBO + (r & 7) * 16 + (pp & 7) * 2;
+    *reinterpret_cast<__half *>(Bh + off) = bh;
+    *reinterpret_cast<__half *>(Bl + off) = bl;
+    *reinterpret_cast<__half *>(Ah + off) = ah;
+    *reinterpret_cast<__half *>(Al + off) = al;
+  }
+}
+__device__ __noinline__ void job_F_generic(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
+                                           int p, bool valid, const float *y, float &rp, float &fx, float &fy,
+                                           float &fz) {
+  float v[GINT_MAX_ORB_ATOM], gv[3 * GINT_MAX_ORB_ATOM];
+  const int no = sh.s_no[a];
+  for (int i = 0; i < no; ++i) v[i] = gv[3 * i] = gv[3 * i + 1] = gv[3 * i + 2] = 0.f;
+  if (valid) {
+    const GSpecies &S = g.sp[sh.s_sp[a]];
+    for (int e = sh.s_e0[a]; e < sh.s_e0[a + 1]; ++e) {
+      float dh[3], dl[3];
+      rel_disp_df(sh, point_df(sh, p), e, dh, dl);
+      if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < (float)S.rcut2)
+        add_image_generic<true>(g, tab, S, dh, dl, v, gv);
+    }
+  }
+  for (int i = 0; i < no; ++i) {
+    rp += v[i] * y[i];
+    fx += gv[3 * i] * y[i];
+    fy += gv[3 * i + 1] * y[i];
+    fz += gv[3 * i + 2] * y[i];
+  }
+}
+
+// Zero fill of the padding gap in front of slot a (density P rows / local-H operand rows).
+__device__ __forceinline__ int gap_begin(const BrickSh &sh, int a) {
+  return a == 0 ? 0 : sh.s_pcol[a - 1] + sh.s_po[a - 1];
 }
 
 // ------------------------------------------------------------------------------ density / force
@@ -383,19 +688,20 @@ __device__ __forceinline__ float chunk_dot(const unsigned char *Ph, const unsign
 template <bool FORCE>
 __global__ void __launch_bounds__(kT, 1)
     k_tc_rho(GGeom g, GNbr nb, const float2 *__restrict__ tab, const __half *__restrict__ Dhi,
-             const __half *__restrict__ Dlo, const long long *__restrict__ tile_off, const float *__restrict__ scales,
+             const __half *__restrict__ Dlo, const __half *__restrict__ Dhi2, const __half *__restrict__ Dlo2,
+             const __half *__restrict__ zero, const long long *__restrict__ tile_off, const float *__restrict__ scales,
              const double *__restrict__ V, double *__restrict__ rho, double *__restrict__ F, int *work,
-             unsigned *err, int np_max, int split3) {
+             unsigned *err, int np_max, int nstages, int split3) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ BrickSh sh;
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const uint32_t sboP = 16u * np_max;
   unsigned char *Ph = smem, *Pl = smem + 128u * np_max * 2;
   unsigned char *B0 = smem + 128u * np_max * 4;
   const uint32_t bop = (uint32_t)np_max * kRC * 2;  // one B operand (hi or lo) of one stage
   if (t == 0) {
-    mbar_init(&sh.bar[0], 1);
-    mbar_init(&sh.bar[1], 1);
+    for (int s = 0; s < kMaxStages; ++s) mbar_init(&sh.full[s], 1);
+    for (int c = 0; c < kMaxChunks; ++c) mbar_init(&sh.done[c], 1);
     fence_mbar_init();
     sh.abort = 0;
     sh.sc[0] = scales[0];
@@ -413,14 +719,56 @@ __global__ void __launch_bounds__(kT, 1)
   const float Sphi = sh.sc[0], SD = sh.sc[1];
   const int p = t & 127, q = t >> 7;  // grid point, slot slice (0..3)
   const uint32_t lane_base = (uint32_t)((p >> 5) * 32) << 16;
-  uint32_t G = 0;  // chunks issued by this CTA
+  uint32_t G = 0;      // chunks issued by this CTA (B-stage ring bookkeeping)
+  uint32_t dpar = 0;   // bit c: phase parity of done[c] (used once per brick that has a chunk c)
+  bool ok = true;
+  // bulk copies of chunk c's B tile (rows [rowbase, NP) x columns [16c, 16c+16)) into stage s
+  auto issue_copies = [&](int c, int s, int NP, int na) {
+    const int rowbase = FORCE ? 0 : c * kRC;
+    const int ngroups = (NP - rowbase) >> 3;
+    if (lane == 0) mbar_arrive_tx(&sh.full[s], (uint32_t)ngroups * 2 * 256);
+    __syncwarp();
+    unsigned char *Bh = B0 + s * 2 * bop, *Bl = Bh + bop;
+    // a chunk that is exactly one 16-column atom a: the 16 x 16 tile (b, a) of a 16-row atom b
+    // is 512 contiguous bytes in global and in shared memory (rows gr, gr+1; both segments)
+    const int ca = sh.col2slot[c * kRC];
+    const bool chunk16 = ca != kNoSlot && sh.s_po[ca] == 16 && sh.s_pcol[ca] == c * kRC;
+    for (int u = lane; u < ngroups * 2; u += 32) {
+      const int gr = u >> 1, sg = u & 1;
+      const int k0 = rowbase + 8 * gr, j0 = c * kRC + 8 * sg;
+      const int bs = sh.col2slot[k0], as = sh.col2slot[j0];
+      const int kl0 = bs != kNoSlot ? k0 - sh.s_pcol[bs] : 0;
+      const bool merged = chunk16 && bs != kNoSlot && sh.s_po[bs] == 16 && (FORCE || gr - kl0 / 8 != 1);
+      if (merged && (kl0 != 0 || sg != 0)) continue;  // carried by the row group's first unit
+      long long src = -1;
+      if (bs != kNoSlot && as != kNoSlot) {
+        const int tile = sh.s_tile[bs * na + as];
+        if (tile >= 0)
+          src = (long long)tile + (long long)((kl0 >> 3) * (sh.s_po[as] >> 3) + ((j0 - sh.s_pcol[as]) >> 3)) * 64;
+      }
+      const bool diag = !FORCE && gr < 2;
+      const __half *sh_hi = src < 0 ? zero : (diag ? Dhi2 : Dhi) + src;
+      const __half *sh_lo = src < 0 ? zero : (diag ? Dlo2 : Dlo) + src;
+      const uint32_t bytes = merged ? 512u : 128u;
+      const bool zsrc = src < 0;
+      if (zsrc && merged) {
+        for (int z = 0; z < 4; ++z) {
+          bulk_g2s(Bh + gr * 256 + z * 128, zero, 128, &sh.full[s]);
+          bulk_g2s(Bl + gr * 256 + z * 128, zero, 128, &sh.full[s]);
+        }
+      } else {
+        bulk_g2s(Bh + gr * 256 + sg * 128, sh_hi, bytes, &sh.full[s]);
+        bulk_g2s(Bl + gr * 256 + sg * 128, sh_lo, bytes, &sh.full[s]);
+      }
+    }
+  };
+  if (t == 0) sh.brick = atomicAdd(work, 1);
   for (;;) {
-    __syncthreads();
-    if (t == 0) sh.brick = atomicAdd(work, 1);
     __syncthreads();
     const long long b = sh.brick;
     if (b >= g.nbricks || sh.abort) break;
-    load_brick(g, nb, tile_off, b, sh);
+    load_brick(g, nb, tile_off, b, sh);  // ends with a barrier: sh.brick may be replaced now
+    if (t == 0) sh.brick = atomicAdd(work, 1);
     const int na = sh.na, NP = sh.np;
     int gi, gj, gk;
     const bool valid = brick_point(g, b, p, gi, gj, gk);
@@ -429,127 +777,103 @@ __global__ void __launch_bounds__(kT, 1)
       if (q == 0 && valid && rho) rho[gidx] = 0.0;
       continue;
     }
+    const int nch = NP / kRC;
+    // the previous brick's MMAs are complete: every stage is free, prefetch the first chunks
+    if (warp == kProducerWarp)
+      for (int c = 0; c < nch && c < nstages; ++c) issue_copies(c, (G + c) % nstages, NP, na);
     // ---- phase A: scaled orbitals of all atoms at every point -> P (hi, lo), zero padding
     for (int a = q; a < na; a += 4) {
-      float v[GINT_MAX_ORB_ATOM];
-      const int po = sh.s_po[a], pc = sh.s_pcol[a];
-      for (int i = 0; i < po; ++i) v[i] = 0.f;
-      if (valid) eval_slot<false>(g, tab, sh, a, p, v, nullptr);
-      const int gap0 = a == 0 ? 0 : sh.s_pcol[a - 1] + sh.s_po[a - 1];
-      const int end = (a == na - 1) ? NP : pc + po;
-      for (int k = gap0; k < end; k += 8) {
-        uint32_t wh[4], wl[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          __half h0, l0, h1, l1;
-          const int k0 = k + 2 * e - pc, k1 = k0 + 1;
-          split_h((k0 >= 0 && k0 < po) ? v[k0] * Sphi : 0.f, h0, l0);
-          split_h((k1 >= 0 && k1 < po) ? v[k1] * Sphi : 0.f, h1, l1);
-          wh[e] = pack2(h0, h1);
-          wl[e] = pack2(l0, l1);
-        }
+      const int gap0 = gap_begin(sh, a), pc = sh.s_pcol[a];
+      for (int k = gap0; k < pc; k += 8) {
         const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
-        *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
-        *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+        *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(0u, 0u, 0u, 0u);
       }
+      if (a == na - 1)
+        for (int k = pc + sh.s_po[a]; k < NP; k += 8) {
+          const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
+          *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(0u, 0u, 0u, 0u);
+          *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(0u, 0u, 0u, 0u);
+        }
     }
-    // ---- phase B: chunks of 16 columns
-    const int nch = NP / kRC;
-    const uint32_t corr_base = (NP <= 256) ? 256u : 0u;  // separate correction accumulator if it fits
-    bool ok = true;
-    double racc = 0.0;
-    auto issue_copies = [&](int c, int stage) {
-      unsigned char *Bh = B0 + stage * 2 * bop, *Bl = Bh + bop;
-      const int rowbase = FORCE ? 0 : c * kRC;
-      const int N = NP - rowbase;
-      for (int u = t; u < N * 4; u += kT) {
-        const int r = u >> 2, s = (u >> 1) & 1, hl = u & 1;
-        const int k = rowbase + r, j0 = c * kRC + 8 * s;
-        unsigned char *dst = (hl ? Bl : Bh) + (r >> 3) * 256 + s * 128 + (r & 7) * 16;
-        const int bs = sh.col2slot[k], as = sh.col2slot[j0];
-        int tile = -1, kl = 0, jseg = 0, poa = 0;
-        if (bs != kNoSlot && as != kNoSlot) {
-          kl = k - sh.s_pcol[bs];
-          if (kl < sh.s_no[bs]) {
-            tile = sh.s_tile[bs * na + as];
-            jseg = j0 - sh.s_pcol[as];
-            poa = sh.s_po[as];
-          }
-        }
-        if (tile >= 0)
-          cp_async16(dst, (hl ? Dlo : Dhi) + (long long)tile + (long long)kl * poa + jseg);
-        else
-          *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
-      }
-    };
-    // B stage G&1 was last read by MMA G-2, complete since the previous brick's final wait
-    issue_copies(0, G & 1);
-    cp_async_commit();
-    for (int c = 0; c < nch; ++c, ++G) {
-      const int s = G & 1;
-      if (c + 1 < nch) {
-        // stage (G+1)&1 was read by MMA G-1
-        if (G >= 1 && !mbar_wait(&sh.bar[(G + 1) & 1], ((G - 1) >> 1) & 1, err)) ok = false;
-        issue_copies(c + 1, (G + 1) & 1);
-      }
-      cp_async_commit();
-      cp_async_wait1();
-      fence_async_smem();
-      __syncthreads();
-      unsigned char *Bh = B0 + s * 2 * bop, *Bl = Bh + bop;
-      if (!FORCE) {
-        // halve the chunk's own diagonal block (rows 0..15 of the B tile)
-        const int r = t >> 5, hl = (t >> 4) & 1, j = t & 15;
-        __half *e = reinterpret_cast<__half *>((hl ? Bl : Bh) + (r >> 3) * 256 + (j >> 3) * 128 + (r & 7) * 16 + (j & 7) * 2);
-        *e = __hmul(*e, __float2half(0.5f));
-        fence_async_smem();
-        __syncthreads();
-      }
-      if (t == 0) {
-        tc_fence_after();
-        const int rowbase = FORCE ? 0 : c * kRC;
-        const int N = NP - rowbase;
-        const uint64_t dah = sdesc(smem_u32(Ph) + (c * kRC / 8) * 128, 128, sboP);
-        const uint64_t dal = sdesc(smem_u32(Pl) + (c * kRC / 8) * 128, 128, sboP);
-        for (int n0 = 0; n0 < N; n0 += 256) {
-          const int nn = min(256, N - n0);
-          const uint32_t id = idesc_f16(128, nn);
-          const uint64_t dbh = sdesc(smem_u32(Bh) + (n0 >> 3) * 256, 128, 256);
-          const uint64_t dbl = sdesc(smem_u32(Bl) + (n0 >> 3) * 256, 128, 256);
-          const uint32_t dm = tmem + rowbase + n0, dc = tmem + corr_base + rowbase + n0;
-          mma_f16(dm, dah, dbh, id, c > 0 ? 1u : 0u);
-          if (split3) {
-            mma_f16(dc, dah, dbl, id, (c > 0 || corr_base == 0) ? 1u : 0u);
-            mma_f16(dc, dal, dbh, id, 1u);
-          }
-        }
-        mma_commit(&sh.bar[s]);
-      }
-      if (!FORCE && c > 0 && q == 0) {
-        // epilogue of chunk c-1 (its columns are final): rho += P_k Y_k
-        const uint32_t Gp = G - 1;
-        if (!mbar_wait(&sh.bar[Gp & 1], (Gp >> 1) & 1, err)) ok = false;
-        tc_fence_after();
-        const int k0 = (c - 1) * kRC;
-        float y[16], yc[16];
-        tmem_ld16(tmem + lane_base + k0, y);
-        if (split3 && corr_base) {
-          tmem_ld16(tmem + lane_base + corr_base + k0, yc);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) y[i] += yc[i];
-        }
-        racc += (double)chunk_dot(Ph, Pl, sboP, p, k0, y);
-      }
-    }
-    cp_async_wait0();
     {
-      const uint32_t Gp = G - 1;
-      if (!mbar_wait(&sh.bar[Gp & 1], (Gp >> 1) & 1, err)) ok = false;
-      tc_fence_after();
+      const PointDF P = point_df(sh, p);
+      for (int a = q; a < na; a += 8) {
+        const int a1 = a + 4;
+        const int shp = g.sp[sh.s_sp[a]].shape;
+        const bool pair = a1 < na && g.sp[sh.s_sp[a1]].shape == shp;
+        switch (shp) {
+#define CASE_P(ns, np_, nd)                                                                                      \
+  case GINT_SHAPE(ns, np_, nd):                                                                                \
+    if (pair)                                                                                                  \
+      job_P2<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tab, sh, a, a1, P, p, valid, Sphi, Ph, Pl, sboP); \
+    else                                                                                                       \
+      job_P<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tab, sh, a, P, p, valid, Sphi, Ph, Pl, sboP);     \
+    break;
+          GINT_FOR_SHAPES(CASE_P)
+#undef CASE_P
+          default:
+            job_P_generic(g, tab, sh, a, p, valid, Sphi, Ph, Pl, sboP);
+        }
+        if (a1 < na && !(pair && shp != 0)) {
+          switch (g.sp[sh.s_sp[a1]].shape) {
+#define CASE_P1(ns, np_, nd)                                                                                      \
+  case GINT_SHAPE(ns, np_, nd):                                                                                 \
+    job_P<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tab, sh, a1, P, p, valid, Sphi, Ph, Pl, sboP);     \
+    break;
+            GINT_FOR_SHAPES(CASE_P1)
+#undef CASE_P1
+            default:
+              job_P_generic(g, tab, sh, a1, p, valid, Sphi, Ph, Pl, sboP);
+          }
+        }
+      }
     }
-    if (!FORCE) {
-      if (q == 0) {
-        const int k0 = NP - kRC;
+    fence_async_smem();
+    __syncthreads();
+    // ---- phase B: chunks of 16 columns, producer warp / MMA thread / epilogue warps
+    const uint32_t corr_base = (NP <= 256) ? 256u : 0u;  // separate correction accumulator if it fits
+    if (warp == kProducerWarp) {
+      for (int c = nstages; c < nch; ++c) {
+        // stage (G + c) % nstages was last read by chunk c - nstages of this brick
+        if (lane == 0 && !mbar_wait(&sh.done[c - nstages], (dpar >> (c - nstages)) & 1u, err)) ok = false;
+        __syncwarp();
+        issue_copies(c, (G + c) % nstages, NP, na);
+      }
+    } else if (warp == kMmaWarp) {
+      if (lane == 0) {
+        for (int c = 0; c < nch; ++c) {
+          const uint32_t Gc = G + c, s = Gc % nstages;
+          if (!mbar_wait(&sh.full[s], (Gc / nstages) & 1, err)) ok = false;
+          tc_fence_after();
+          unsigned char *Bh = B0 + s * 2 * bop, *Bl = Bh + bop;
+          const int rowbase = FORCE ? 0 : c * kRC;
+          const int N = NP - rowbase;
+          const uint64_t dah = sdesc(smem_u32(Ph) + (c * kRC / 8) * 128, 128, sboP);
+          const uint64_t dal = sdesc(smem_u32(Pl) + (c * kRC / 8) * 128, 128, sboP);
+          for (int n0 = 0; n0 < N; n0 += 256) {
+            const int nn = min(256, N - n0);
+            const uint32_t id = idesc_f16(128, nn);
+            const uint64_t dbh = sdesc(smem_u32(Bh) + (n0 >> 3) * 256, 128, 256);
+            const uint64_t dbl = sdesc(smem_u32(Bl) + (n0 >> 3) * 256, 128, 256);
+            const uint32_t dm = tmem + rowbase + n0, dc = tmem + corr_base + rowbase + n0;
+            mma_f16(dm, dah, dbh, id, c > 0 ? 1u : 0u);
+            if (split3) {
+              mma_f16(dc, dah, dbl, id, (c > 0 || corr_base == 0) ? 1u : 0u);
+              mma_f16(dc, dal, dbh, id, 1u);
+            }
+          }
+          mma_commit(&sh.done[c]);
+        }
+      }
+      __syncwarp();
+    } else if (warp < 4 && !FORCE) {
+      double racc = 0.0;
+      for (int c = 0; c < nch; ++c) {
+        if (!mbar_wait(&sh.done[c], (dpar >> c) & 1u, err)) ok = false;
+        tc_fence_after();
+        // chunk c's columns are final: rho += P_k Y_k
+        const int k0 = c * kRC;
         float y[16], yc[16];
         tmem_ld16(tmem + lane_base + k0, y);
         if (split3 && corr_base) {
@@ -557,44 +881,55 @@ __global__ void __launch_bounds__(kT, 1)
 #pragma unroll
           for (int i = 0; i < 16; ++i) y[i] += yc[i];
         }
-        racc += (double)chunk_dot(Ph, Pl, sboP, p, k0, y);
-        if (valid && rho) rho[gidx] = racc * (2.0 / ((double)Sphi * (double)Sphi * (double)SD));
+        float part = 0.f;
+#pragma unroll
+        for (int hseg = 0; hseg < 2; ++hseg) {
+          const uint32_t off = (p >> 3) * sboP + ((k0 >> 3) + hseg) * 128 + (p & 7) * 16;
+          const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + off), wl = *reinterpret_cast<const uint4 *>(Pl + off);
+          const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
+            const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
+            part += (hf.x + lf.x) * y[hseg * 8 + 2 * e] + (hf.y + lf.y) * y[hseg * 8 + 2 * e + 1];
+          }
+        }
+        racc += (double)part;
       }
-    } else {
+      if (valid && rho) rho[gidx] = racc * (2.0 / ((double)Sphi * (double)Sphi * (double)SD));
+    }
+    // all MMAs of the brick are complete once the last chunk's barrier has flipped (in order)
+    if (!mbar_wait(&sh.done[nch - 1], (dpar >> (nch - 1)) & 1u, err)) ok = false;
+    tc_fence_after();
+    G += nch;
+    dpar ^= (nch >= 32) ? 0xffffffffu : ((1u << nch) - 1u);
+    if (FORCE) {
       // full Y: per atom, rho and force from recomputed phi and grad phi (unscaled float32)
       const float inv = 1.f / (Sphi * SD);
       const float wv = valid ? (float)(g.w * V[gidx]) : 0.f;
       float rp = 0.f;
       for (int a = q; a < na; a += 4) {
-        const int pc = sh.s_pcol[a], no = sh.s_no[a];
-        float y[32], yc[16];
-        tmem_ld16(tmem + lane_base + pc, y);
-        if (split3 && corr_base) {
-          tmem_ld16(tmem + lane_base + corr_base + pc, yc);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) y[i] += yc[i];
-        }
-        if (sh.s_po[a] > 16) {
-          tmem_ld16(tmem + lane_base + pc + 16, y + 16);
+        const int pc = sh.s_pcol[a], po = sh.s_po[a];
+        float y[GINT_MAX_ORB_ATOM], yc[16];
+        for (int h = 0; h < po; h += 16) {
+          tmem_ld16(tmem + lane_base + pc + h, y + h);
           if (split3 && corr_base) {
-            tmem_ld16(tmem + lane_base + corr_base + pc + 16, yc);
+            tmem_ld16(tmem + lane_base + corr_base + pc + h, yc);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) y[16 + i] += yc[i];
+            for (int i = 0; i < 16; ++i) y[h + i] += yc[i];
           }
         }
-        float v[GINT_MAX_ORB_ATOM], gv[3 * GINT_MAX_ORB_ATOM];
-        for (int i = 0; i < no; ++i) {
-          v[i] = 0.f;
-          gv[3 * i] = gv[3 * i + 1] = gv[3 * i + 2] = 0.f;
-        }
-        if (valid) eval_slot<true>(g, tab, sh, a, p, v, gv);
+        for (int i = 0; i < po; ++i) y[i] *= inv;
         float fx = 0.f, fy = 0.f, fz = 0.f;
-        for (int i = 0; i < no; ++i) {
-          const float yi = y[i] * inv;
-          rp += v[i] * yi;
-          fx += gv[3 * i] * yi;
-          fy += gv[3 * i + 1] * yi;
-          fz += gv[3 * i + 2] * yi;
+        switch (g.sp[sh.s_sp[a]].shape) {
+#define CASE_F(ns, np_, nd)                                                                          \
+  case GINT_SHAPE(ns, np_, nd):                                                                    \
+    job_F<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tab, sh, a, p, valid, y, rp, fx, fy, fz); \
+    break;
+          GINT_FOR_SHAPES(CASE_F)
+#undef CASE_F
+          default:
+            job_F_generic(g, tab, sh, a, p, valid, y, rp, fx, fy, fz);
         }
         fx *= 2.f * wv;
         fy *= 2.f * wv;
@@ -604,10 +939,10 @@ __global__ void __launch_bounds__(kT, 1)
           fy += __shfl_xor_sync(0xffffffffu, fy, o);
           fz += __shfl_xor_sync(0xffffffffu, fz, o);
         }
-        if ((t & 31) == 0) {
-          atomicAdd(&sh.fpart[a][0], fx);
-          atomicAdd(&sh.fpart[a][1], fy);
-          atomicAdd(&sh.fpart[a][2], fz);
+        if (lane == 0) {
+          atomicAdd(&sh.fpart[a][0], (double)fx);
+          atomicAdd(&sh.fpart[a][1], (double)fy);
+          atomicAdd(&sh.fpart[a][2], (double)fz);
         }
       }
       sh.rpart[q][p] = rp;
@@ -616,9 +951,9 @@ __global__ void __launch_bounds__(kT, 1)
         rho[gidx] = (double)sh.rpart[0][p] + (double)sh.rpart[1][p] + (double)sh.rpart[2][p] + (double)sh.rpart[3][p];
       for (int a = t; a < na; a += kT) {
         const int I = sh.s_atom[a];
-        atomicAdd(F + 3 * I + 0, (double)sh.fpart[a][0]);
-        atomicAdd(F + 3 * I + 1, (double)sh.fpart[a][1]);
-        atomicAdd(F + 3 * I + 2, (double)sh.fpart[a][2]);
+        atomicAdd(F + 3 * I + 0, sh.fpart[a][0]);
+        atomicAdd(F + 3 * I + 1, sh.fpart[a][1]);
+        atomicAdd(F + 3 * I + 2, sh.fpart[a][2]);
       }
     }
     tc_fence_before();
@@ -643,8 +978,8 @@ __global__ void __launch_bounds__(kT, 1)
   const uint32_t op = (uint32_t)(np_max / 8) * kHSBO;
   const uint32_t stage_bytes = 4 * op;
   if (t == 0) {
-    mbar_init(&sh.bar[0], 1);
-    mbar_init(&sh.bar[1], 1);
+    mbar_init(&sh.done[0], 1);
+    mbar_init(&sh.done[1], 1);
     fence_mbar_init();
     sh.abort = 0;
     sh.sc[0] = scales[0];
@@ -663,6 +998,7 @@ __global__ void __launch_bounds__(kT, 1)
   const float out_scale = 1.f / (Sphi * SA);
   const int pp = t & (kHP - 1), q = t >> 5;  // point within the chunk, slot slice (0..15)
   uint32_t G = 0;
+  bool ok = true;
   for (;;) {
     __syncthreads();
     if (t == 0) sh.brick = atomicAdd(work, 1);
@@ -679,33 +1015,41 @@ __global__ void __launch_bounds__(kT, 1)
       T += NP - 128 * m;
     }
     const uint32_t corr_base = (2 * T <= 512) ? (uint32_t)T : 0u;
-    bool ok = true;
     for (int c = 0; c < 128 / kHP; ++c, ++G) {
       const int s = G & 1;
       unsigned char *Ah = smem + s * stage_bytes, *Al = Ah + op, *Bh = Al + op, *Bl = Bh + op;
-      if (G >= 2 && !mbar_wait(&sh.bar[s], ((G - 2) >> 1) & 1, err)) ok = false;
+      if (G >= 2 && !mbar_wait(&sh.done[s], ((G - 2) >> 1) & 1, err)) ok = false;
       const int pt = c * kHP + pp;
       int gi, gj, gk;
       const bool valid = brick_point(g, b, pt, gi, gj, gk);
-      const float wv = valid ? (float)(g.w * V[grid_index(g, gi, gj, gk)]) : 0.f;
+      const float wvSA = valid ? (float)(g.w * V[grid_index(g, gi, gj, gk)]) * SA : 0.f;
       for (int a = q; a < na; a += 16) {
-        float v[GINT_MAX_ORB_ATOM];
-        const int po = sh.s_po[a], pc = sh.s_pcol[a];
-        for (int i = 0; i < po; ++i) v[i] = 0.f;
-        if (valid) eval_slot<false>(g, tab, sh, a, pt, v, nullptr);
-        const int gap0 = a == 0 ? 0 : sh.s_pcol[a - 1] + sh.s_po[a - 1];
-        const int end = (a == na - 1) ? NP : pc + po;
-        for (int r = gap0; r < end; ++r) {
-          const int i = r - pc;
-          const float x = (i >= 0 && i < po) ? v[i] : 0.f;
-          __half bh, bl, ah, al;
-          split_h(x * Sphi, bh, bl);
-          split_h(x * wv * SA, ah, al);
+        const int pc = sh.s_pcol[a];
+        const int gend = (a == na - 1) ? NP : 0;
+        for (int r = gap_begin(sh, a); r < pc; ++r) {
           const uint32_t off = (r >> 3) * kHSBO + (pp >> 3) * kHLBO + (r & 7) * 16 + (pp & 7) * 2;
-          *reinterpret_cast<__half *>(Bh + off) = bh;
-          *reinterpret_cast<__half *>(Bl + off) = bl;
-          *reinterpret_cast<__half *>(Ah + off) = ah;
-          *reinterpret_cast<__half *>(Al + off) = al;
+          *reinterpret_cast<uint16_t *>(Bh + off) = 0;
+          *reinterpret_cast<uint16_t *>(Bl + off) = 0;
+          *reinterpret_cast<uint16_t *>(Ah + off) = 0;
+          *reinterpret_cast<uint16_t *>(Al + off) = 0;
+        }
+        for (int r = pc + sh.s_po[a]; r < gend; ++r) {
+          const uint32_t off = (r >> 3) * kHSBO + (pp >> 3) * kHLBO + (r & 7) * 16 + (pp & 7) * 2;
+          *reinterpret_cast<uint16_t *>(Bh + off) = 0;
+          *reinterpret_cast<uint16_t *>(Bl + off) = 0;
+          *reinterpret_cast<uint16_t *>(Ah + off) = 0;
+          *reinterpret_cast<uint16_t *>(Al + off) = 0;
+        }
+        switch (g.sp[sh.s_sp[a]].shape) {
+#define CASE_H(ns, np_, nd)                                                                                    \
+  case GINT_SHAPE(ns, np_, nd):                                                                              \
+    job_H<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tab, sh, a, pt, pp, valid, Sphi, wvSA, Ah, Al, \
+                                                            Bh, Bl);                                         \
+    break;
+          GINT_FOR_SHAPES(CASE_H)
+#undef CASE_H
+          default:
+            job_H_generic(g, tab, sh, a, pt, pp, valid, Sphi, wvSA, Ah, Al, Bh, Bl);
         }
       }
       fence_async_smem();
@@ -733,24 +1077,27 @@ __global__ void __launch_bounds__(kT, 1)
             }
           }
         }
-        mma_commit(&sh.bar[s]);
+        mma_commit(&sh.done[s]);
       }
     }
     {
       const uint32_t Gp = G - 1;
-      if (!mbar_wait(&sh.bar[Gp & 1], (Gp >> 1) & 1, err)) ok = false;
+      if (!mbar_wait(&sh.done[Gp & 1], (Gp >> 1) & 1, err)) ok = false;
       tc_fence_after();
     }
-    // epilogue: upper slot-pair tiles -> scratch (float32, unscaled)
+    // epilogue: upper slot-pair tiles -> scratch (float32, unscaled), 8-column runs per row:
+    // tile (a, c), a <= c, is porb(a) x porb(c) at rowst(a) + porb(a) (cumpo(c) - cumpo(a))
     {
-      const int lane = t & 127, qq = t >> 7;
-      const uint32_t lane_base = (uint32_t)((lane >> 5) * 32) << 16;
+      const int ln = t & 127, qq = t >> 7;
+      const uint32_t lane_base = (uint32_t)((ln >> 5) * 32) << 16;
       const long long base = hs_brick_off[b];
       for (int m = 0; m < ntile; ++m) {
-        const int mu = 128 * m + lane;
+        const int mu = 128 * m + ln;
         const int as = mu < NP ? sh.col2slot[mu] : kNoSlot;
         const int il = as != kNoSlot ? mu - sh.s_pcol[as] : 0;
         const bool rowok = as != kNoSlot && il < sh.s_no[as];
+        const int po_a = rowok ? sh.s_po[as] : 0, cum_a = rowok ? sh.s_cumpo[as] : 0;
+        float *rowp = hs + base + (rowok ? sh.s_rowst[as] : 0);
         const int N = NP - 128 * m;
         for (int gcol = qq; gcol < N / 16; gcol += 4) {
           float y[16], yc[16];
@@ -761,17 +1108,19 @@ __global__ void __launch_bounds__(kT, 1)
             for (int i = 0; i < 16; ++i) y[i] += yc[i];
           }
           if (!rowok) continue;
-#pragma unroll 4
-          for (int i = 0; i < 16; ++i) {
-            const int nu = 128 * m + gcol * 16 + i;
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            const int nu = 128 * m + gcol * 16 + 8 * hh;
             const int cs = sh.col2slot[nu];
             if (cs == kNoSlot || cs < as) continue;
-            const int jl = nu - sh.s_pcol[cs];
-            if (jl >= sh.s_no[cs]) continue;
-            const int no_c = sh.s_no[cs];
-            const long long o = base + sh.s_rowst[as] +
-                                (long long)sh.s_no[as] * (sh.s_cumno[cs] - sh.s_cumno[as]) + il * no_c + jl;
-            hs[o] = y[i] * out_scale;
+            const int po_c = sh.s_po[cs];
+            float *dst = rowp + (long long)po_a * (sh.s_cumpo[cs] - cum_a) + il * po_c + (nu - sh.s_pcol[cs]);
+            reinterpret_cast<float4 *>(dst)[0] =
+                make_float4(y[8 * hh] * out_scale, y[8 * hh + 1] * out_scale, y[8 * hh + 2] * out_scale,
+                            y[8 * hh + 3] * out_scale);
+            reinterpret_cast<float4 *>(dst)[1] =
+                make_float4(y[8 * hh + 4] * out_scale, y[8 * hh + 5] * out_scale, y[8 * hh + 6] * out_scale,
+                            y[8 * hh + 7] * out_scale);
           }
         }
       }
@@ -783,8 +1132,8 @@ __global__ void __launch_bounds__(kT, 1)
   if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
-// Per pair (I <= J): H_IJ = sum over the bricks containing both (fixed order, float64);
-// H_JI = H_IJ^T.
+// Per pair (I <= J): H_IJ = sum over the bricks containing both (fixed order; float32 partials
+// of eight contributions, float64 total); H_JI = H_IJ^T.
 __global__ void k_h_reduce(const int *__restrict__ hu_pair, const long long *__restrict__ hu_off,
                            const long long *__restrict__ hu_src, const float *__restrict__ hs,
                            const int *__restrict__ pair_I, const int *__restrict__ pair_J,
@@ -793,16 +1142,22 @@ __global__ void k_h_reduce(const int *__restrict__ hu_pair, const long long *__r
   const int u = blockIdx.x;
   const int p = hu_pair[u];
   const int I = pair_I[p], J = pair_J[p];
-  const int nI = g.sp[species[I]].norb, nJ = g.sp[species[J]].norb;
+  const int nI = g.sp[species[I]].norb, nJ = g.sp[species[J]].norb, pJ = g.sp[species[J]].porb;
   const long long k0 = hu_off[u], k1 = hu_off[u + 1];
   for (int e = threadIdx.x; e < nI * nJ; e += blockDim.x) {
+    const int i = e / nJ, j = e - (e / nJ) * nJ;
+    const int se = i * pJ + j;
     double acc = 0.0;
-    for (long long k = k0; k < k1; ++k) acc += (double)hs[hu_src[k] + e];
-    H[pair_off[p] + e] = acc;
-    if (I != J) {
-      const int i = e / nJ, j = e - (e / nJ) * nJ;
-      H[pair_off[pair_T[p]] + (long long)j * nI + i] = acc;
+    long long k = k0;
+    for (; k + 8 <= k1; k += 8) {
+      float v[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) v[jj] = hs[hu_src[k + jj] + se];
+      acc += (double)(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
     }
+    for (; k < k1; ++k) acc += (double)hs[hu_src[k] + se];
+    H[pair_off[p] + e] = acc;
+    if (I != J) H[pair_off[pair_T[p]] + (long long)j * nI + i] = acc;
   }
 }
 
@@ -829,26 +1184,35 @@ __global__ void k_scales(const unsigned *maxbits, double phi_bound, double w, fl
   scales[2] = (float)pow2_scale(30000.0, pb * w * (double)__uint_as_float(maxbits[1]));
 }
 
-// D blocks (float64, row-major norb(I) x norb(J)) -> tiles norb(I) x porb(J), scaled, (hi, lo).
+// D blocks (float64, row-major norb(I) x norb(J)) -> scaled float16 (hi, lo) tiles of
+// roundup(norb(I), 8) x porb(J) in core-matrix order [row group][K group][8][8], plus halves.
 __global__ void k_build_tiles(const double *__restrict__ D, const int *__restrict__ pair_I,
                               const int *__restrict__ pair_J, const long long *__restrict__ pair_off,
                               const long long *__restrict__ tile_off, const int *__restrict__ species, GGeom g,
-                              const float *__restrict__ scales, __half *__restrict__ Dhi, __half *__restrict__ Dlo) {
+                              const float *__restrict__ scales, __half *__restrict__ Dhi, __half *__restrict__ Dlo,
+                              __half *__restrict__ Dhi2, __half *__restrict__ Dlo2) {
   const int p = blockIdx.x;
   const int I = pair_I[p], J = pair_J[p];
   const int nI = g.sp[species[I]].norb, nJ = g.sp[species[J]].norb, pJ = g.sp[species[J]].porb;
-  const float S = scales[1];
+  const int rI = (nI + 7) & ~7, sJ = pJ >> 3;
+  const double S = (double)scales[1];
   const long long o = pair_off[p], to = tile_off[p];
-  for (int e = threadIdx.x; e < nI * pJ; e += blockDim.x) {
-    const int i = e / pJ, j = e - (e / pJ) * pJ;
-    __half h = __float2half(0.f), l = __float2half(0.f);
-    if (j < nJ) {
-      const double v = D[o + (long long)i * nJ + j] * (double)S;
-      h = __float2half_rn((float)v);
-      l = __float2half_rn((float)(v - (double)__half2float(h)));
+  for (int e = threadIdx.x; e < rI * pJ; e += blockDim.x) {
+    const int cm = e >> 6, w = e & 63;
+    const int i = (cm / sJ) * 8 + (w >> 3), j = (cm % sJ) * 8 + (w & 7);
+    float v = 0.f, v2 = 0.f;
+    if (i < nI && j < nJ) {
+      const double x = D[o + (long long)i * nJ + j] * S;
+      v = (float)x;
+      v2 = (float)(0.5 * x);
+      __half h = __float2half_rn(v), h2 = __float2half_rn(v2);
+      Dhi[to + e] = h;
+      Dlo[to + e] = __float2half_rn((float)(x - (double)__half2float(h)));
+      Dhi2[to + e] = h2;
+      Dlo2[to + e] = __float2half_rn((float)(0.5 * x - (double)__half2float(h2)));
+    } else {
+      Dhi[to + e] = Dlo[to + e] = Dhi2[to + e] = Dlo2[to + e] = __float2half(0.f);
     }
-    Dhi[to + e] = h;
-    Dlo[to + e] = l;
   }
 }
 
@@ -913,7 +1277,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_selftest(int N, float *err_out, u
   if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
-inline uint32_t rho_smem_bytes(int np) { return 128u * np * 4 + 2u * np * kRC * 4; }
+inline uint32_t rho_smem_bytes(int np, int nstages) { return 128u * np * 4 + (uint32_t)nstages * np * kRC * 4; }
 inline uint32_t h_smem_bytes(int np) { return 2u * 4 * (uint32_t)(np / 8) * kHSBO + 16 * kHSBO; }
 
 template <typename K>
@@ -939,6 +1303,9 @@ void dfree(T *&p) {
 void gint_tc_free(gint_handle *h) {
   dfree(h->Dt_hi);
   dfree(h->Dt_lo);
+  dfree(h->Dt_hi2);
+  dfree(h->Dt_lo2);
+  dfree(h->zero_dev);
   dfree(h->tile_off_dev);
   dfree(h->scales);
   dfree(h->hs_brick_off);
@@ -955,21 +1322,25 @@ int gint_tc_prepare(gint_handle *h) {
   gint_tc_free(h);
   const GGeom &g = h->geom;
   const int na_tot = g.natoms;
-  // D tiles
+  // D tiles: roundup(norb(I), 8) x porb(J) per pair
   h->tile_off.assign(h->npairs + 1, 0);
   for (int I = 0; I < na_tot; ++I)
     for (int p = h->pair_row[I]; p < h->pair_row[I + 1]; ++p) {
       const int J = h->pair_col[p];
-      h->tile_off[p + 1] = h->tile_off[p] + (long long)h->atom_norb[I] * g.sp[h->species_host[J]].porb;
+      h->tile_off[p + 1] =
+          h->tile_off[p] + (long long)((h->atom_norb[I] + 7) & ~7) * g.sp[h->species_host[J]].porb;
     }
   h->ntile_elems = h->tile_off[h->npairs];
-  if (cudaMalloc(&h->Dt_hi, std::max<long long>(h->ntile_elems, 8) * sizeof(__half)) != cudaSuccess ||
-      cudaMalloc(&h->Dt_lo, std::max<long long>(h->ntile_elems, 8) * sizeof(__half)) != cudaSuccess ||
+  const size_t tbytes = std::max<long long>(h->ntile_elems, 64) * sizeof(__half);
+  if (cudaMalloc(&h->Dt_hi, tbytes) != cudaSuccess || cudaMalloc(&h->Dt_lo, tbytes) != cudaSuccess ||
+      cudaMalloc(&h->Dt_hi2, tbytes) != cudaSuccess || cudaMalloc(&h->Dt_lo2, tbytes) != cudaSuccess ||
+      cudaMalloc(&h->zero_dev, 256) != cudaSuccess ||
       cudaMalloc(&h->tile_off_dev, (h->npairs + 1) * sizeof(long long)) != cudaSuccess ||
       cudaMalloc(&h->scales, 8 * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
     return GINT_ENOMEM;
   }
+  TC_CHECK(cudaMemset(h->zero_dev, 0, 256));
   TC_CHECK(cudaMemcpy(h->tile_off_dev, h->tile_off.data(), (h->npairs + 1) * sizeof(long long),
                       cudaMemcpyHostToDevice));
   // brick slot lists on the host
@@ -986,7 +1357,7 @@ int gint_tc_prepare(gint_handle *h) {
     auto it = std::lower_bound(b, e, J);
     return (it != e && *it == J) ? (int)(it - h->pair_col.begin()) : -1;
   };
-  std::vector<int> no;
+  std::vector<int> no;  // padded orbital counts (porb) of the brick's slots
   // pass 1: sizes and counts
   for (long long b = 0; b < nb; ++b) {
     const long long s0 = at_off[b], s1 = at_off[b + 1];
@@ -996,8 +1367,8 @@ int gint_tc_prepare(gint_handle *h) {
     for (long long s = s0; s < s1; ++s) {
       const GSpecies &S = g.sp[h->species_host[satom[s]]];
       cur = place_slot(cur, S.porb) + S.porb;
-      no[s - s0] = S.norb;
-      cum += S.norb;
+      no[s - s0] = S.porb;
+      cum += S.porb;
     }
     npmax = std::max(npmax, (cur + 15) & ~15);
     long long tot = 0, rest = cum;
@@ -1032,7 +1403,7 @@ int gint_tc_prepare(gint_handle *h) {
     no.assign(s1 - s0, 0);
     long long cum = 0;
     for (long long s = s0; s < s1; ++s) {
-      no[s - s0] = g.sp[h->species_host[satom[s]]].norb;
+      no[s - s0] = g.sp[h->species_host[satom[s]]].porb;
       cum += no[s - s0];
     }
     long long rowst = 0, cumno_a = 0;
@@ -1090,22 +1461,25 @@ int gint_tc_rho(gint_handle *h, int precision, const double *D, double *rho, con
   if ((rc = compute_scales(h, D, nullptr, st))) return rc;
   if (h->npairs > 0)
     k_build_tiles<<<h->npairs, 128, 0, st>>>(D, h->pair_I_dev, h->pair_col_dev, h->pair_off_dev, h->tile_off_dev,
-                                             h->species_dev, h->geom, h->scales, h->Dt_hi, h->Dt_lo);
+                                             h->species_dev, h->geom, h->scales, h->Dt_hi, h->Dt_lo, h->Dt_hi2,
+                                             h->Dt_lo2);
   TC_CHECK(cudaGetLastError());
   const int np = std::max(h->max_brick_porb, kRC);
-  const uint32_t smem = rho_smem_bytes(np);
+  int nstages = kMaxStages;
+  while (nstages > 2 && rho_smem_bytes(np, nstages) + sizeof(BrickSh) > 227 * 1024) --nstages;
+  const uint32_t smem = rho_smem_bytes(np, nstages);
   TC_CHECK(cudaMemsetAsync(h->work_ctr, 0, sizeof(int), st));
   const unsigned grid = (unsigned)std::min<long long>(h->num_sms, h->geom.nbricks);
   if (F) {
     auto kern = k_tc_rho<true>;
     if ((rc = set_smem(kern, smem))) return rc;
-    kern<<<grid, kT, smem, st>>>(h->geom, h->nbr(), h->tab32, h->Dt_hi, h->Dt_lo, h->tile_off_dev, h->scales, V, rho,
-                                 F, h->work_ctr, h->err_word, np, split3);
+    kern<<<grid, kT, smem, st>>>(h->geom, h->nbr(), h->tab32, h->Dt_hi, h->Dt_lo, h->Dt_hi2, h->Dt_lo2, h->zero_dev,
+                                 h->tile_off_dev, h->scales, V, rho, F, h->work_ctr, h->err_word, np, nstages, split3);
   } else {
     auto kern = k_tc_rho<false>;
     if ((rc = set_smem(kern, smem))) return rc;
-    kern<<<grid, kT, smem, st>>>(h->geom, h->nbr(), h->tab32, h->Dt_hi, h->Dt_lo, h->tile_off_dev, h->scales, V, rho,
-                                 F, h->work_ctr, h->err_word, np, split3);
+    kern<<<grid, kT, smem, st>>>(h->geom, h->nbr(), h->tab32, h->Dt_hi, h->Dt_lo, h->Dt_hi2, h->Dt_lo2, h->zero_dev,
+                                 h->tile_off_dev, h->scales, V, rho, F, h->work_ctr, h->err_word, np, nstages, split3);
   }
   TC_CHECK(cudaGetLastError());
   return GINT_OK;
