@@ -138,6 +138,8 @@ class Gint:
         self.atom_norb = norbs
         self.atom_off = np.concatenate([[0], np.cumsum(norbs)]).astype(np.int64)
         self.weight = float(_lib.gint_weight(h))
+        self._pos_host = pos.copy()
+        self._pos_dev = None
 
     # -- bookkeeping
     def stats(self) -> dict:
@@ -205,8 +207,18 @@ class Gint:
         _check(_lib.gint_sync(self._h, _stream(stream)), "gint_sync")
 
     def set_positions(self, pos: torch.Tensor, stream=None):
+        """New positions (device float64 [natoms, 3]); neighbour lists are rebuilt on the device."""
+        pos = pos.detach().contiguous()
         _check(_lib.gint_set_positions(self._h, _dptr(pos, numel=3 * self.natoms), _stream(stream)),
                "gint_set_positions")
+        self._pos_dev = pos.clone()
+
+    def ensure_positions(self, pos: torch.Tensor, stream=None):
+        """Rebuilds the neighbour lists only if pos differs from the current geometry."""
+        if self._pos_dev is None:
+            self._pos_dev = torch.from_numpy(self._pos_host).to(pos.device)
+        if not torch.equal(self._pos_dev, pos.detach()):
+            self.set_positions(pos, stream)
 
     # -- layout helpers (host, numpy): dense <-> atom-pair blocks
     def dense_to_blocks(self, M: np.ndarray) -> np.ndarray:

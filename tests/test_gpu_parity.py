@@ -188,3 +188,38 @@ def test_si64_sampled_parity(si64, torch_cuda, prec):
         ref = o.vlocal_block(w.V, I, J)
         blk = H[g.pair_off[k]:g.pair_off[k + 1]].reshape(ref.shape)
         assert np.abs(blk - ref).max() <= TOL[prec] * hmax
+
+
+@pytest.fixture(scope="module")
+def si512(torch_cuda):
+    """512-atom Si (4x4x4 supercell, N(0,0.05) displacements), 192^3 grid, D from C 6656x1024 / 32."""
+    from paper_2603_21835_gb300 import gint as G
+
+    w = inputs.config_workload("si512_g192", dense_D=True)
+    o = Oracle(w.system)
+    g = G.Gint(w.system)
+    rng = np.random.default_rng(512)
+    idx = rng.choice(o.ngrid, 400, replace=False)
+    blocks = [(0, 0), (5, 77), (130, 131), (511, 300)]
+    blocks = [(I, J) for I, J in blocks if g.block_index(I, J) >= 0][:3] + [(200, 200)]
+    ref_H = {bl: o.vlocal_block(w.V, *bl) for bl in blocks}
+    return dict(w=w, g=g, G=G, idx=idx, rho=o.rho(w.D, idx), H=ref_H, Db=g.blocks_from_coefficients(w.C))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f16x3"])
+def test_si512_sampled_parity(si512, torch_cuda, prec):
+    torch = torch_cuda
+    s = si512
+    g = s["g"]
+    p = s["G"].PRECISIONS[prec]
+    Dd = torch.from_numpy(s["Db"]).cuda()
+    Vd = torch.from_numpy(s["w"].V.reshape(-1)).cuda()
+    rho = g.rho(Dd, p).cpu().numpy().reshape(-1)
+    H = g.vlocal(Vd, p).cpu().numpy()
+    g.sync()
+    assert _rel(rho[s["idx"]], s["rho"]) <= TOL[prec]
+    hmax = np.abs(H).max()
+    for bl, ref in s["H"].items():
+        k = g.block_index(*bl)
+        blk = H[g.pair_off[k]:g.pair_off[k + 1]].reshape(ref.shape)
+        assert np.abs(blk - ref).max() <= TOL[prec] * hmax, bl
