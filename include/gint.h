@@ -112,6 +112,10 @@ int gint_pairs(const gint_handle *h, int *pair_IJ, long long *pair_off);
 int gint_stats(const gint_handle *h, double *W, double *W_exec, long long *nbricks, int *max_brick_orb,
                int *max_brick_atoms);
 
+/* Device memory held by the handle (tables, neighbour lists, workspace), in bytes (host
+ * output).  The footprint that a serving loop counts against its HBM budget. */
+int gint_memory(const gint_handle *h, long long *device_bytes);
+
 /* Replaces the atom positions from a DEVICE array [natoms][3] and rebuilds the neighbour
  * lists on the device.  The pair set stays fixed: GINT_ESKIN if a pair outside it now
  * overlaps.  Synchronises the stream. */
@@ -128,6 +132,34 @@ int gint_vlocal(gint_handle *h, int precision, const double *V, double *H_blocks
 int gint_force(gint_handle *h, int precision, const double *D_blocks, const double *V, double *F, double *rho,
                void *stream);
 
+/* One unit of work for gint_run_batch: the passes of one system (its own handle).  Outputs
+ * that are NULL are not computed:
+ *   rho      [n1 n2 n3]  density (needs D_blocks)
+ *   H_blocks [nblock]    local H (needs V)
+ *   F        [natoms][3] local Pulay forces (needs D_blocks and V); rho is written in the same
+ *                        pass if it is not NULL
+ * All pointers are caller-owned device memory; the handle's workspace is used, so one handle may
+ * appear only once per batch and must not be used concurrently elsewhere. */
+typedef struct gint_task {
+  gint_handle *h;
+  const double *D_blocks;
+  const double *V;
+  double *rho;
+  double *H_blocks;
+  double *F;
+} gint_task;
+
+/* Runs the tasks of several systems together (continuous batching of a serving loop).  With the
+ * tensor-core precisions the bricks of all tasks (density / force bricks and local-H bricks) are
+ * items of ONE persistent launch, up to 32 tasks per launch (more are split into groups of 32);
+ * the per-pair H reduction and the per-call preparation are one launch each for the group.
+ * Results equal those of the single-system calls on each handle, because every brick is computed
+ * the same way whatever else shares the launch.  The FP64 / FP32 precisions run the tasks one
+ * after another (separate launches).  Asynchronous on `stream`.  Every handle must live on the
+ * same device and have been created with the same species list (identical radial metadata);
+ * otherwise GINT_EINVAL, as for a repeated handle or a missing input. */
+int gint_run_batch(const gint_task *tasks, int ntasks, int precision, void *stream);
+
 /* Float64 reductions on the device, written to out_dev[0] (device):
  *   V != NULL: w * sum_g V_g rho_g  (the energy E);   V == NULL: w * sum_g rho_g (N_e = Tr(DS)). */
 int gint_grid_dot(gint_handle *h, const double *V, const double *rho, double *out_dev, void *stream);
@@ -140,9 +172,9 @@ int gint_block_dot(gint_handle *h, const double *A_blocks, const double *B_block
  * GINT_EDEVICE); clears the word.  Compute calls are asynchronous, so such errors surface here. */
 int gint_sync(gint_handle *h, void *stream);
 
-/* Diagnostic: runs one tcgen05 TF32 MMA (M=128, N=n, K=8) per operand layout used by the brick
- * kernels on exactly representable integer data and returns the largest absolute deviation from
- * the exact product in *max_err (host).  n in {16, ..., 256}, multiple of 16.  Synchronous. */
+/* Diagnostic: runs one tcgen05 kind::f16 MMA (M=128, N=n, K=16) per operand layout used by the
+ * brick kernels on exactly representable integer data and returns the largest absolute deviation
+ * from the exact product in *max_err (host).  n in {16, ..., 256}, multiple of 16.  Synchronous. */
 int gint_tc_selftest(int n, double *max_err);
 
 /* Float64 dot product that allocates no device memory (the paper has no counterpart; this

@@ -168,6 +168,7 @@ int gint_create(const gint_desc *d, gint_handle **out) {
   if (v) return v;
   gint_handle *h = new (std::nothrow) gint_handle();
   if (!h) return GINT_ENOMEM;
+  std::memset(static_cast<void *>(&h->geom), 0, sizeof(GGeom));  // batched launches compare GTabs bytes
   TRYCU(cudaGetDevice(&h->device));
   TRYCU(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
   cudaStream_t st = h->own_stream;
@@ -356,6 +357,20 @@ int gint_stats(const gint_handle *h, double *W, double *W_exec, long long *nbric
   return GINT_OK;
 }
 
+int gint_memory(const gint_handle *h, long long *device_bytes) {
+  if (!h || !device_bytes) return GINT_EINVAL;
+  const long long nb = h->geom.nbricks, na = h->geom.natoms, np = h->npairs, L = sizeof(long long);
+  long long b = h->nknots * (long long)(sizeof(double2) + sizeof(float2));                 // tables
+  b += na * (3 * (long long)sizeof(double) + 4);                                            // atoms
+  b += (na + 1) * 4 + np * 4 + (np + 1) * L + 2 * np * 4;                                  // pair set
+  b += nb * 3 * 4 + (nb + 1) * 3 * L + 8 * L;                                               // brick counts
+  b += h->cap_slots * 8 + (h->cap_slots + 1) * L + h->cap_ent * 3 * (long long)sizeof(double) +
+       h->cap_pairtab * 4;                                                                  // neighbours
+  b += 1024 * (long long)sizeof(double) + 16 * (long long)sizeof(double) + 16 + h->nblock * 4 + 16;  // workspace
+  *device_bytes = b + h->tc_bytes;
+  return GINT_OK;
+}
+
 int gint_set_positions(gint_handle *h, const double *pos_dev, void *stream) {
   if (!h || !pos_dev) return GINT_EINVAL;
   DeviceGuard guard(h->device);
@@ -395,10 +410,11 @@ int gint_vlocal(gint_handle *h, int precision, const double *V, double *H_blocks
   if (check_precision(precision)) return GINT_EINVAL;
   DeviceGuard guard(h->device);
   cudaStream_t st = (cudaStream_t)stream;
-  if (cudaMemsetAsync(H_blocks, 0, sizeof(double) * (size_t)h->nblock, st) != cudaSuccess) return GINT_ECUDA;
-  if (precision == GINT_FP64 || precision == GINT_FP32)
+  if (precision == GINT_FP64 || precision == GINT_FP32) {
+    if (cudaMemsetAsync(H_blocks, 0, sizeof(double) * (size_t)h->nblock, st) != cudaSuccess) return GINT_ECUDA;
     return gint_simt_vlocal(h, precision == GINT_FP64, V, H_blocks, st);
-  return gint_tc_vlocal(h, precision, V, H_blocks, st);
+  }
+  return gint_tc_vlocal(h, precision, V, H_blocks, st);  // every block element is written
 }
 
 int gint_force(gint_handle *h, int precision, const double *D_blocks, const double *V, double *F, double *rho,
@@ -407,10 +423,48 @@ int gint_force(gint_handle *h, int precision, const double *D_blocks, const doub
   if (check_precision(precision)) return GINT_EINVAL;
   DeviceGuard guard(h->device);
   cudaStream_t st = (cudaStream_t)stream;
-  if (cudaMemsetAsync(F, 0, sizeof(double) * 3 * (size_t)h->geom.natoms, st) != cudaSuccess) return GINT_ECUDA;
-  if (precision == GINT_FP64 || precision == GINT_FP32)
+  if (precision == GINT_FP64 || precision == GINT_FP32) {
+    if (cudaMemsetAsync(F, 0, sizeof(double) * 3 * (size_t)h->geom.natoms, st) != cudaSuccess) return GINT_ECUDA;
     return gint_simt_rho(h, precision == GINT_FP64, D_blocks, rho, V, F, st);
-  return gint_tc_rho(h, precision, D_blocks, rho, V, F, st);
+  }
+  return gint_tc_rho(h, precision, D_blocks, rho, V, F, st);  // F is zeroed by the preparation kernel
+}
+
+int gint_run_batch(const gint_task *tasks, int ntasks, int precision, void *stream) {
+  if (ntasks < 0 || (ntasks > 0 && !tasks)) return GINT_EINVAL;
+  if (check_precision(precision)) return GINT_EINVAL;
+  for (int i = 0; i < ntasks; ++i) {
+    const gint_task &T = tasks[i];
+    if (!T.h) return GINT_EINVAL;
+    if ((T.rho || T.F) && !T.D_blocks) return GINT_EINVAL;
+    if ((T.H_blocks || T.F) && !T.V) return GINT_EINVAL;
+  }
+  if (ntasks == 0) return GINT_OK;
+  DeviceGuard guard(tasks[0].h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == GINT_F16X3 || precision == GINT_F16X1) return gint_tc_batch(tasks, ntasks, precision, st);
+  for (int i = 0; i < ntasks; ++i) {
+    const gint_task &T = tasks[i];
+    gint_handle *h = T.h;
+    if (h->device != tasks[0].h->device) return GINT_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (tasks[j].h == h) return GINT_EINVAL;
+    const bool fp64 = precision == GINT_FP64;
+    int rc = GINT_OK;
+    if (T.F) {
+      if (cudaMemsetAsync(T.F, 0, sizeof(double) * 3 * (size_t)h->geom.natoms, st) != cudaSuccess) return GINT_ECUDA;
+      rc = gint_simt_rho(h, fp64, T.D_blocks, T.rho, T.V, T.F, st);
+    } else if (T.rho) {
+      rc = gint_simt_rho(h, fp64, T.D_blocks, T.rho, nullptr, nullptr, st);
+    }
+    if (rc) return rc;
+    if (T.H_blocks) {
+      if (cudaMemsetAsync(T.H_blocks, 0, sizeof(double) * (size_t)h->nblock, st) != cudaSuccess) return GINT_ECUDA;
+      rc = gint_simt_vlocal(h, fp64, T.V, T.H_blocks, st);
+      if (rc) return rc;
+    }
+  }
+  return GINT_OK;
 }
 
 int gint_grid_dot(gint_handle *h, const double *V, const double *rho, double *out_dev, void *stream) {

@@ -68,6 +68,7 @@ struct gint_handle {
   int *hu_pair = nullptr;                 // [nupper] pair index
   long long *hu_off = nullptr;            // [nupper + 1] CSR into hu_src
   long long *hu_src = nullptr;            // scratch element offset of each contribution
+  long long tc_bytes = 0;                 // device bytes of the tensor-core workspace above
   double *red = nullptr;      // reduction partials
   double *scal = nullptr;     // device scalars
   unsigned *err_word = nullptr;
@@ -104,6 +105,7 @@ int gint_reduce_dot(gint_handle *h, const double *a, const double *b, long long 
 int gint_tc_rho(gint_handle *h, int precision, const double *D, double *rho, const double *V, double *F,
                 cudaStream_t st);
 int gint_tc_vlocal(gint_handle *h, int precision, const double *V, double *H, cudaStream_t st);
+int gint_tc_batch(const gint_task *tasks, int n, int precision, cudaStream_t st);
 int gint_tc_check_capacity(const gint_handle *h);
 int gint_tc_prepare(gint_handle *h);  // layouts and scratch of the tensor-core path (after neighbours)
 void gint_tc_free(gint_handle *h);

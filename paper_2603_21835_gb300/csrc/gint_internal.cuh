@@ -35,7 +35,8 @@ struct GSpecies {
 };
 #define GINT_SHAPE(ns, np, nd) (1 + (ns) + 8 * (np) + 64 * (nd))
 
-struct GGeom {
+// Geometry of one system: cell, grid and bricks.
+struct GCell {
   double cell[9];   // rows a1, a2, a3
   double inv[9];    // inverse: fractional u = d . inv
   double reach[3];  // |column c of inv| (fractional extent of a unit Cartesian length)
@@ -43,10 +44,18 @@ struct GGeom {
   long long ngrid, nbricks;
   int n1, n2, n3;
   int nbi, nbj, nbk;  // bricks per axis
-  int natoms, nspecies, nrad, pad;
+  int natoms, pad;
+};
+
+// Species and radial-table metadata (the knot values live in a separate packed array).
+// Systems whose GTabs compare equal byte for byte can share one batched launch.
+struct GTabs {
+  int nspecies, nrad;
   GSpecies sp[GINT_MAX_SPECIES];
   GRadial rad[GINT_MAX_RADIAL];
 };
+
+struct GGeom : GCell, GTabs {};
 
 // Neighbour structure of the bricks (device arrays, CSR).
 //   bricks  : b_at_off[b] .. b_at_off[b+1]  distinct atoms of brick b ("slots")
@@ -69,14 +78,14 @@ struct GNbr {
 
 #define GINT_PI 3.14159265358979323846
 
-__host__ __device__ __forceinline__ void grid_point(const GGeom &g, int i, int j, int k, double r[3]) {
+__host__ __device__ __forceinline__ void grid_point(const GCell &g, int i, int j, int k, double r[3]) {
   double fi = (double)i / g.n1, fj = (double)j / g.n2, fk = (double)k / g.n3;
 #pragma unroll
   for (int c = 0; c < 3; ++c) r[c] = fi * g.cell[c] + fj * g.cell[3 + c] + fk * g.cell[6 + c];
 }
 
 // Decode a local point index 0..127 of a brick into grid indices; returns false outside the grid.
-__host__ __device__ __forceinline__ bool brick_point(const GGeom &g, long long b, int p, int &i, int &j, int &k) {
+__host__ __device__ __forceinline__ bool brick_point(const GCell &g, long long b, int p, int &i, int &j, int &k) {
   int bk = (int)(b % g.nbk);
   int bj = (int)((b / g.nbk) % g.nbj);
   int bi = (int)(b / ((long long)g.nbk * g.nbj));
@@ -87,7 +96,7 @@ __host__ __device__ __forceinline__ bool brick_point(const GGeom &g, long long b
   return i < g.n1 && j < g.n2 && k < g.n3;
 }
 
-__host__ __device__ __forceinline__ long long grid_index(const GGeom &g, int i, int j, int k) {
+__host__ __device__ __forceinline__ long long grid_index(const GCell &g, int i, int j, int k) {
   return ((long long)i * g.n2 + j) * g.n3 + k;
 }
 
@@ -160,7 +169,7 @@ __device__ __forceinline__ float gsqrt<float>(float x) { return sqrtf(x); }
 // by the caller) to phi[0..norb) if PHI and to grad[0..norb)[3] if GRAD.
 // grad phi = u (f' Y - l f Y / r) + (f / r) grad_u y(u), with Y = y(u), u = d / r.
 template <typename T, bool PHI, bool GRAD>
-__device__ __forceinline__ void add_orbitals(const GGeom &g, const typename Tab2<T>::type *__restrict__ tab, int sp,
+__device__ __forceinline__ void add_orbitals(const GTabs &g, const typename Tab2<T>::type *__restrict__ tab, int sp,
                                              T dx, T dy, T dz, T *phi, T (*grad)[3]) {
   const GSpecies &S = g.sp[sp];
   T r2 = dx * dx + dy * dy + dz * dz;

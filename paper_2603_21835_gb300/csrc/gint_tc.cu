@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "gint_handle.cuh"
@@ -80,9 +81,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsign
     }
   }
   return true;
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
@@ -226,7 +224,7 @@ __device__ __forceinline__ void radial_at(const float2 *__restrict__ tab, const 
 
 // Generic path (any radial order or knot grids): adds one image to v[col] (+ gv[3 col + c]).
 template <bool GRAD>
-__device__ void add_image_generic(const GGeom &g, const float2 *__restrict__ tab, const GSpecies &S, const float dh[3],
+__device__ void add_image_generic(const GTabs &g, const float2 *__restrict__ tab, const GSpecies &S, const float dh[3],
                                   const float dl[3], float *v, float *gv) {
   float r, rl, ir;
   bool at0;
@@ -271,7 +269,7 @@ __device__ void add_image_generic(const GGeom &g, const float2 *__restrict__ tab
 // Fast path for l-sorted species (NS s, NP p, ND d radials) on one knot grid: one knot/basis
 // computation per image, all column indices static (register arrays).
 template <int NS, int NPR, int ND, bool GRAD>
-__device__ __forceinline__ void add_image_fast(const GGeom &g, const float2 *__restrict__ tab, const GSpecies &S,
+__device__ __forceinline__ void add_image_fast(const GTabs &g, const float2 *__restrict__ tab, const GSpecies &S,
                                                const float dh[3], const float dl[3], float *v, float *gv) {
   float r, rl, ir;
   bool at0;
@@ -357,9 +355,10 @@ constexpr int kMaxStages = 4;
 constexpr int kMaxChunks = kNPMAX / kRC;
 struct BrickSh {
   uint64_t full[kMaxStages];  // density: B stage loaded (bulk-copy transactions)
-  uint64_t done[kMaxChunks];  // density: MMAs of chunk c complete (one use per brick); local H: stages
+  uint64_t done[kMaxChunks];  // density: MMAs of chunk c complete (one use per brick)
+  uint64_t hdone[2];          // local H: MMAs of a stage complete
   uint32_t tmem;
-  int brick, na, np, nent, abort;
+  int item, na, np, nent, abort;
   int s_atom[kMAXA], s_no[kMAXA], s_po[kMAXA], s_sp[kMAXA], s_pcol[kMAXA], s_e0[kMAXA + 1];
   int s_cumpo[kMAXA + 1];       // prefix of porb over slots
   int s_rowst[kMAXA];           // local-H scratch: first element of slot a's row of tiles
@@ -377,7 +376,7 @@ __device__ __forceinline__ void split2(double v, float &hi, float &lo) {
   lo = (float)(v - (double)hi);
 }
 
-__device__ void init_points(const GGeom &g, BrickSh &sh) {
+__device__ void init_points(const GCell &g, BrickSh &sh) {
   for (int p = threadIdx.x; p < 128; p += blockDim.x) {
     const int pi = p >> 5, pj = (p >> 3) & 3, pk = p & 7;
     for (int c = 0; c < 3; ++c) {
@@ -397,8 +396,8 @@ __host__ __device__ __forceinline__ int place_slot(int cur, int po) {
 }
 
 // Loads slots, entries, padded layout, tile table, local-H tile offsets.
-__device__ void load_brick(const GGeom &g, const GNbr &nb, const long long *__restrict__ tile_off, long long b,
-                           BrickSh &sh) {
+__device__ void load_brick(const GCell &g, const GTabs &tb, const GNbr &nb, const long long *__restrict__ tile_off,
+                           long long b, BrickSh &sh) {
   const int t = threadIdx.x;
   const int bk = (int)(b % g.nbk), bj = (int)((b / g.nbk) % g.nbj), bi = (int)(b / ((long long)g.nbk * g.nbj));
   double ob[3];
@@ -411,8 +410,8 @@ __device__ void load_brick(const GGeom &g, const GNbr &nb, const long long *__re
     const int I = nb.s_atom[s0 + a], sp = nb.atom_species[I];
     sh.s_atom[a] = I;
     sh.s_sp[a] = sp;
-    sh.s_no[a] = g.sp[sp].norb;
-    sh.s_po[a] = g.sp[sp].porb;
+    sh.s_no[a] = tb.sp[sp].norb;
+    sh.s_po[a] = tb.sp[sp].porb;
     sh.s_e0[a] = (int)(nb.s_ent[s0 + a] - e_begin);
     sh.fpart[a][0] = sh.fpart[a][1] = sh.fpart[a][2] = 0.0;
   }
@@ -477,7 +476,7 @@ __device__ __forceinline__ void rel_disp_df(const BrickSh &sh, const PointDF &P,
 
 // Periodised orbitals (all images) of slot a at local point p: v[PO] (+ gv[3 PO]), zero based.
 template <int NS, int NPR, int ND, bool GRAD>
-__device__ __forceinline__ void slot_values(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
+__device__ __forceinline__ void slot_values(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
                                             const PointDF &P, bool valid, float *v, float *gv) {
   constexpr int PO = (NS + 3 * NPR + 5 * ND + 7) / 8 * 8;
 #pragma unroll
@@ -526,7 +525,7 @@ __device__ __forceinline__ void store_P(const float *v, int pc, int p, float Sph
 }
 // Two atoms of the same shape at once (two independent evaluation chains per thread).
 template <int NS, int NPR, int ND, int PO>
-__device__ __forceinline__ void job_P2(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a0,
+__device__ __forceinline__ void job_P2(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a0,
                                        int a1, const PointDF &P, int p, bool valid, float Sphi, unsigned char *Ph,
                                        unsigned char *Pl, uint32_t sboP) {
   float v0[PO], v1[PO];
@@ -536,7 +535,7 @@ __device__ __forceinline__ void job_P2(const GGeom &g, const float2 *__restrict_
   store_P<PO>(v1, sh.s_pcol[a1], p, Sphi, Ph, Pl, sboP);
 }
 template <int NS, int NPR, int ND, int PO>
-__device__ __forceinline__ void job_P(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
+__device__ __forceinline__ void job_P(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
                                       const PointDF &P, int p, bool valid, float Sphi, unsigned char *Ph,
                                       unsigned char *Pl, uint32_t sboP) {
   float v[PO];
@@ -561,7 +560,7 @@ __device__ __forceinline__ void job_P(const GGeom &g, const float2 *__restrict__
 
 // Local H: A = w V phi (scaled), B = phi (scaled), rows [pcol, pcol + PO), K = point pp.
 template <int NS, int NPR, int ND, int PO>
-__device__ __forceinline__ void job_H(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a, int pt,
+__device__ __forceinline__ void job_H(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a, int pt,
                                       int pp, bool valid, float Sphi, float wvSA, unsigned char *Ah,
                                       unsigned char *Al, unsigned char *Bh, unsigned char *Bl) {
   float v[PO];
@@ -583,7 +582,7 @@ __device__ __forceinline__ void job_H(const GGeom &g, const float2 *__restrict__
 
 // Force epilogue: y[PO] (true Y values of slot a's columns) -> rho part and force components.
 template <int NS, int NPR, int ND, int PO>
-__device__ __forceinline__ void job_F(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a, int p,
+__device__ __forceinline__ void job_F(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a, int p,
                                       bool valid, const float *y, float &rp, float &fx, float &fy, float &fz) {
   float v[PO], gv[3 * PO];
   slot_values<NS, NPR, ND, true>(g, tab, sh, a, point_df(sh, p), valid, v, gv);
@@ -597,7 +596,7 @@ __device__ __forceinline__ void job_F(const GGeom &g, const float2 *__restrict__
 }
 
 // Generic-shape jobs (any species up to GINT_MAX_ORB_ATOM orbitals).
-__device__ __noinline__ void job_P_generic(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
+__device__ __noinline__ void job_P_generic(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
                                            int p, bool valid, float Sphi, unsigned char *Ph, unsigned char *Pl,
                                            uint32_t sboP) {
   float v[GINT_MAX_ORB_ATOM];
@@ -626,7 +625,7 @@ __device__ __noinline__ void job_P_generic(const GGeom &g, const float2 *__restr
     *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
   }
 }
-__device__ __noinline__ void job_H_generic(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
+__device__ __noinline__ void job_H_generic(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
                                            int pt, int pp, bool valid, float Sphi, float wvSA, unsigned char *Ah,
                                            unsigned char *Al, unsigned char *Bh, unsigned char *Bl) {
   float v[GINT_MAX_ORB_ATOM];
@@ -653,7 +652,7 @@ __device__ __noinline__ void job_H_generic(const GGeom &g, const float2 *__restr
     *reinterpret_cast<__half *>(Al + off) = al;
   }
 }
-__device__ __noinline__ void job_F_generic(const GGeom &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
+__device__ __noinline__ void job_F_generic(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
                                            int p, bool valid, const float *y, float &rp, float &fx, float &fy,
                                            float &fz) {
   float v[GINT_MAX_ORB_ATOM], gv[3 * GINT_MAX_ORB_ATOM];
@@ -681,49 +680,95 @@ __device__ __forceinline__ int gap_begin(const BrickSh &sh, int a) {
   return a == 0 ? 0 : sh.s_pcol[a - 1] + sh.s_po[a - 1];
 }
 
-// ------------------------------------------------------------------------------ density / force
-// Dynamic shared memory: P (hi, lo) [128 x np_max] | 2 x B stage (hi, lo) [np_max x 16].
-// P element (p, k): (p/8)*16*np_max + (k/8)*128 + (p%8)*16 + (k%8)*2.
-// B element (r, j): (r/8)*256 + (j/8)*128 + (r%8)*16 + (j%8)*2.
+// ------------------------------------------------------------------------------ batch descriptors
+// Several systems share one persistent launch.  They must have identical species/radial
+// metadata (GTabs, a kernel parameter); everything else is per system.  Work items are the
+// density (or force) bricks of system 0, then its local-H bricks, then those of system 1, ...
+constexpr int kMaxBatch = 32;
+
+struct GSys {
+  GCell c;
+  GNbr nb;
+  const float2 *tab;                         // float32 knot table of this system's handle
+  const __half *Dhi, *Dlo, *Dhi2, *Dlo2;     // D tiles (density / force items)
+  const long long *tile_off;
+  const float *scales;                       // [0] S_phi, [1] S_D, [2] S_Q
+  const double *V;                           // NULL: no local-H items, zero force weight
+  double *rho, *F;                           // NULL: not written
+  const long long *hs_brick_off;
+  float *hs;                                 // local-H scratch tiles
+  unsigned *err;                             // device error word of the handle
+  long long nrho, nh;                        // items of each kind: 0 or nbricks
+};
+
+struct GBatch {
+  int nsys, np_max, nstages, split3;
+  long long start[kMaxBatch + 1];  // first item of each system; start[nsys] = total
+  GSys sys[kMaxBatch];
+};
+
+// System owning item `it` (largest s with start[s] <= it; systems without items are skipped).
+__device__ __forceinline__ int batch_sys(const GBatch &B, long long it) {
+  int lo = 0, hi = B.nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.start[mid] <= it)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------------------------ brick kernel
+// One persistent CTA per SM walks the batch's items.  Dynamic shared memory is used by either
+// kind of item:
+//   density: P (hi, lo) [128 x np_max] | nstages x B stage (hi, lo) [np_max x 16]
+//     P element (p, k): (p/8)*16*np_max + (k/8)*128 + (p%8)*16 + (k%8)*2
+//     B element (r, j): (r/8)*256 + (j/8)*128 + (r%8)*16 + (j%8)*2
+//   local H: 2 stages of A hi, A lo, B hi, B lo, each [np_max rows x 32 points]
+//     element (r, p): (r/8)*576 + (p/8)*144 + (r%8)*16 + (p%8)*2, plus a tail pad for the rows
+//     above NP that the last 128-row A tile reads (they only feed output rows that are ignored).
+// FORCE: density items produce rho and forces (full Y); a system without F only gets rho.
 template <bool FORCE>
 __global__ void __launch_bounds__(kT, 1)
-    k_tc_rho(GGeom g, GNbr nb, const float2 *__restrict__ tab, const __half *__restrict__ Dhi,
-             const __half *__restrict__ Dlo, const __half *__restrict__ Dhi2, const __half *__restrict__ Dlo2,
-             const __half *__restrict__ zero, const long long *__restrict__ tile_off, const float *__restrict__ scales,
-             const double *__restrict__ V, double *__restrict__ rho, double *__restrict__ F, int *work,
-             unsigned *err, int np_max, int nstages, int split3) {
+    k_tc_fused(const __grid_constant__ GTabs g, const __grid_constant__ GBatch B, const __half *__restrict__ zero,
+               int *work) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ BrickSh sh;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int np_max = B.np_max, nstages = B.nstages, split3 = B.split3;
   const uint32_t sboP = 16u * np_max;
   unsigned char *Ph = smem, *Pl = smem + 128u * np_max * 2;
   unsigned char *B0 = smem + 128u * np_max * 4;
   const uint32_t bop = (uint32_t)np_max * kRC * 2;  // one B operand (hi or lo) of one stage
+  const uint32_t hop = (uint32_t)(np_max / 8) * kHSBO;
+  const uint32_t hstage = 4 * hop;
   if (t == 0) {
     for (int s = 0; s < kMaxStages; ++s) mbar_init(&sh.full[s], 1);
     for (int c = 0; c < kMaxChunks; ++c) mbar_init(&sh.done[c], 1);
+    mbar_init(&sh.hdone[0], 1);
+    mbar_init(&sh.hdone[1], 1);
     fence_mbar_init();
     sh.abort = 0;
-    sh.sc[0] = scales[0];
-    sh.sc[1] = scales[1];
+    sh.item = atomicAdd(work, 1);
   }
   if (warp == 0) {
     tmem_alloc(&sh.tmem, 512);
     tmem_relinquish();
   }
-  init_points(g, sh);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sh.tmem;
-  const float Sphi = sh.sc[0], SD = sh.sc[1];
-  const int p = t & 127, q = t >> 7;  // grid point, slot slice (0..3)
-  const uint32_t lane_base = (uint32_t)((p >> 5) * 32) << 16;
-  uint32_t G = 0;      // chunks issued by this CTA (B-stage ring bookkeeping)
-  uint32_t dpar = 0;   // bit c: phase parity of done[c] (used once per brick that has a chunk c)
+  const long long total = B.start[B.nsys];
+  uint32_t G = 0;     // density chunks issued by this CTA (B-stage ring bookkeeping)
+  uint32_t dpar = 0;  // bit c: phase parity of done[c] (used once per density brick that has a chunk c)
+  uint32_t GH = 0;    // local-H stages issued by this CTA
+  int cur = -1;       // system whose points and scales are in shared memory
   bool ok = true;
   // bulk copies of chunk c's B tile (rows [rowbase, NP) x columns [16c, 16c+16)) into stage s
-  auto issue_copies = [&](int c, int s, int NP, int na) {
+  auto issue_copies = [&](const GSys &S, int c, int s, int NP, int na) {
     const int rowbase = FORCE ? 0 : c * kRC;
     const int ngroups = (NP - rowbase) >> 3;
     if (lane == 0) mbar_arrive_tx(&sh.full[s], (uint32_t)ngroups * 2 * 256);
@@ -747,8 +792,8 @@ __global__ void __launch_bounds__(kT, 1)
           src = (long long)tile + (long long)((kl0 >> 3) * (sh.s_po[as] >> 3) + ((j0 - sh.s_pcol[as]) >> 3)) * 64;
       }
       const bool diag = !FORCE && gr < 2;
-      const __half *sh_hi = src < 0 ? zero : (diag ? Dhi2 : Dhi) + src;
-      const __half *sh_lo = src < 0 ? zero : (diag ? Dlo2 : Dlo) + src;
+      const __half *sh_hi = src < 0 ? zero : (diag ? S.Dhi2 : S.Dhi) + src;
+      const __half *sh_lo = src < 0 ? zero : (diag ? S.Dlo2 : S.Dlo) + src;
       const uint32_t bytes = merged ? 512u : 128u;
       const bool zsrc = src < 0;
       if (zsrc && merged) {
@@ -762,47 +807,67 @@ __global__ void __launch_bounds__(kT, 1)
       }
     }
   };
-  if (t == 0) sh.brick = atomicAdd(work, 1);
   for (;;) {
     __syncthreads();
-    const long long b = sh.brick;
-    if (b >= g.nbricks || sh.abort) break;
-    load_brick(g, nb, tile_off, b, sh);  // ends with a barrier: sh.brick may be replaced now
-    if (t == 0) sh.brick = atomicAdd(work, 1);
-    const int na = sh.na, NP = sh.np;
-    int gi, gj, gk;
-    const bool valid = brick_point(g, b, p, gi, gj, gk);
-    const long long gidx = valid ? grid_index(g, gi, gj, gk) : 0;
-    if (na == 0) {
-      if (q == 0 && valid && rho) rho[gidx] = 0.0;
-      continue;
-    }
-    const int nch = NP / kRC;
-    // the previous brick's MMAs are complete: every stage is free, prefetch the first chunks
-    if (warp == kProducerWarp)
-      for (int c = 0; c < nch && c < nstages; ++c) issue_copies(c, (G + c) % nstages, NP, na);
-    // ---- phase A: scaled orbitals of all atoms at every point -> P (hi, lo), zero padding
-    for (int a = q; a < na; a += 4) {
-      const int gap0 = gap_begin(sh, a), pc = sh.s_pcol[a];
-      for (int k = gap0; k < pc; k += 8) {
-        const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
-        *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(0u, 0u, 0u, 0u);
-        *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(0u, 0u, 0u, 0u);
+    const long long it = sh.item;
+    if (it >= total || sh.abort) break;
+    const int sidx = batch_sys(B, it);
+    const GSys &S = B.sys[sidx];
+    const long long local = it - B.start[sidx];
+    const bool hitem = local >= S.nrho;
+    const long long b = hitem ? local - S.nrho : local;
+    if (sidx != cur) {  // the previous item is finished (barrier above): replace points and scales
+      init_points(S.c, sh);
+      if (t == 0) {
+        sh.sc[0] = S.scales[0];
+        sh.sc[1] = S.scales[1];
+        sh.sc[2] = S.scales[2];
       }
-      if (a == na - 1)
-        for (int k = pc + sh.s_po[a]; k < NP; k += 8) {
+      cur = sidx;
+    }
+    load_brick(S.c, g, S.nb, S.tile_off, b, sh);  // ends with a barrier: sh.item may be replaced now
+    if (t == 0) sh.item = atomicAdd(work, 1);
+    const int na = sh.na, NP = sh.np;
+    const float Sphi = sh.sc[0];
+    if (!hitem) {
+      // ================================================================ density / force brick
+      const float SD = sh.sc[1];
+      const int p = t & 127, q = t >> 7;  // grid point, slot slice (0..3)
+      const uint32_t lane_base = (uint32_t)((p >> 5) * 32) << 16;
+      int gi, gj, gk;
+      const bool valid = brick_point(S.c, b, p, gi, gj, gk);
+      const long long gidx = valid ? grid_index(S.c, gi, gj, gk) : 0;
+      if (na == 0) {
+        if (q == 0 && valid && S.rho) S.rho[gidx] = 0.0;
+        continue;
+      }
+      const int nch = NP / kRC;
+      // the previous density item's MMAs are complete: every stage is free, prefetch the first chunks
+      if (warp == kProducerWarp)
+        for (int c = 0; c < nch && c < nstages; ++c) issue_copies(S, c, (G + c) % nstages, NP, na);
+      // ---- phase A: scaled orbitals of all atoms at every point -> P (hi, lo), zero padding
+      for (int a = q; a < na; a += 4) {
+        const int gap0 = gap_begin(sh, a), pc = sh.s_pcol[a];
+        for (int k = gap0; k < pc; k += 8) {
           const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
           *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(0u, 0u, 0u, 0u);
           *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(0u, 0u, 0u, 0u);
         }
-    }
-    {
-      const PointDF P = point_df(sh, p);
-      for (int a = q; a < na; a += 8) {
-        const int a1 = a + 4;
-        const int shp = g.sp[sh.s_sp[a]].shape;
-        const bool pair = a1 < na && g.sp[sh.s_sp[a1]].shape == shp;
-        switch (shp) {
+        if (a == na - 1)
+          for (int k = pc + sh.s_po[a]; k < NP; k += 8) {
+            const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
+            *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(0u, 0u, 0u, 0u);
+          }
+      }
+      {
+        const float2 *tab = S.tab;
+        const PointDF P = point_df(sh, p);
+        for (int a = q; a < na; a += 8) {
+          const int a1 = a + 4;
+          const int shp = g.sp[sh.s_sp[a]].shape;
+          const bool pair = a1 < na && g.sp[sh.s_sp[a1]].shape == shp;
+          switch (shp) {
 #define CASE_P(ns, np_, nd)                                                                                      \
   case GINT_SHAPE(ns, np_, nd):                                                                                \
     if (pair)                                                                                                  \
@@ -810,317 +875,276 @@ __global__ void __launch_bounds__(kT, 1)
     else                                                                                                       \
       job_P<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tab, sh, a, P, p, valid, Sphi, Ph, Pl, sboP);     \
     break;
-          GINT_FOR_SHAPES(CASE_P)
+            GINT_FOR_SHAPES(CASE_P)
 #undef CASE_P
-          default:
-            job_P_generic(g, tab, sh, a, p, valid, Sphi, Ph, Pl, sboP);
-        }
-        if (a1 < na && !(pair && shp != 0)) {
-          switch (g.sp[sh.s_sp[a1]].shape) {
+            default:
+              job_P_generic(g, tab, sh, a, p, valid, Sphi, Ph, Pl, sboP);
+          }
+          if (a1 < na && !(pair && shp != 0)) {
+            switch (g.sp[sh.s_sp[a1]].shape) {
 #define CASE_P1(ns, np_, nd)                                                                                      \
   case GINT_SHAPE(ns, np_, nd):                                                                                 \
     job_P<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tab, sh, a1, P, p, valid, Sphi, Ph, Pl, sboP);     \
     break;
-            GINT_FOR_SHAPES(CASE_P1)
+              GINT_FOR_SHAPES(CASE_P1)
 #undef CASE_P1
-            default:
-              job_P_generic(g, tab, sh, a1, p, valid, Sphi, Ph, Pl, sboP);
-          }
-        }
-      }
-    }
-    fence_async_smem();
-    __syncthreads();
-    // ---- phase B: chunks of 16 columns, producer warp / MMA thread / epilogue warps
-    const uint32_t corr_base = (NP <= 256) ? 256u : 0u;  // separate correction accumulator if it fits
-    if (warp == kProducerWarp) {
-      for (int c = nstages; c < nch; ++c) {
-        // stage (G + c) % nstages was last read by chunk c - nstages of this brick
-        if (lane == 0 && !mbar_wait(&sh.done[c - nstages], (dpar >> (c - nstages)) & 1u, err)) ok = false;
-        __syncwarp();
-        issue_copies(c, (G + c) % nstages, NP, na);
-      }
-    } else if (warp == kMmaWarp) {
-      if (lane == 0) {
-        for (int c = 0; c < nch; ++c) {
-          const uint32_t Gc = G + c, s = Gc % nstages;
-          if (!mbar_wait(&sh.full[s], (Gc / nstages) & 1, err)) ok = false;
-          tc_fence_after();
-          unsigned char *Bh = B0 + s * 2 * bop, *Bl = Bh + bop;
-          const int rowbase = FORCE ? 0 : c * kRC;
-          const int N = NP - rowbase;
-          const uint64_t dah = sdesc(smem_u32(Ph) + (c * kRC / 8) * 128, 128, sboP);
-          const uint64_t dal = sdesc(smem_u32(Pl) + (c * kRC / 8) * 128, 128, sboP);
-          for (int n0 = 0; n0 < N; n0 += 256) {
-            const int nn = min(256, N - n0);
-            const uint32_t id = idesc_f16(128, nn);
-            const uint64_t dbh = sdesc(smem_u32(Bh) + (n0 >> 3) * 256, 128, 256);
-            const uint64_t dbl = sdesc(smem_u32(Bl) + (n0 >> 3) * 256, 128, 256);
-            const uint32_t dm = tmem + rowbase + n0, dc = tmem + corr_base + rowbase + n0;
-            mma_f16(dm, dah, dbh, id, c > 0 ? 1u : 0u);
-            if (split3) {
-              mma_f16(dc, dah, dbl, id, (c > 0 || corr_base == 0) ? 1u : 0u);
-              mma_f16(dc, dal, dbh, id, 1u);
+              default:
+                job_P_generic(g, tab, sh, a1, p, valid, Sphi, Ph, Pl, sboP);
             }
           }
-          mma_commit(&sh.done[c]);
         }
       }
-      __syncwarp();
-    } else if (warp < 4 && !FORCE) {
-      double racc = 0.0;
-      for (int c = 0; c < nch; ++c) {
-        if (!mbar_wait(&sh.done[c], (dpar >> c) & 1u, err)) ok = false;
-        tc_fence_after();
-        // chunk c's columns are final: rho += P_k Y_k
-        const int k0 = c * kRC;
-        float y[16], yc[16];
-        tmem_ld16(tmem + lane_base + k0, y);
-        if (split3 && corr_base) {
-          tmem_ld16(tmem + lane_base + corr_base + k0, yc);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) y[i] += yc[i];
+      fence_async_smem();
+      __syncthreads();
+      // ---- phase B: chunks of 16 columns, producer warp / MMA thread / epilogue warps
+      const uint32_t corr_base = (NP <= 256) ? 256u : 0u;  // separate correction accumulator if it fits
+      if (warp == kProducerWarp) {
+        for (int c = nstages; c < nch; ++c) {
+          // stage (G + c) % nstages was last read by chunk c - nstages of this brick
+          if (lane == 0 && !mbar_wait(&sh.done[c - nstages], (dpar >> (c - nstages)) & 1u, S.err)) ok = false;
+          __syncwarp();
+          issue_copies(S, c, (G + c) % nstages, NP, na);
         }
-        float part = 0.f;
-#pragma unroll
-        for (int hseg = 0; hseg < 2; ++hseg) {
-          const uint32_t off = (p >> 3) * sboP + ((k0 >> 3) + hseg) * 128 + (p & 7) * 16;
-          const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + off), wl = *reinterpret_cast<const uint4 *>(Pl + off);
-          const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
-            const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
-            part += (hf.x + lf.x) * y[hseg * 8 + 2 * e] + (hf.y + lf.y) * y[hseg * 8 + 2 * e + 1];
+      } else if (warp == kMmaWarp) {
+        if (lane == 0) {
+          for (int c = 0; c < nch; ++c) {
+            const uint32_t Gc = G + c, s = Gc % nstages;
+            if (!mbar_wait(&sh.full[s], (Gc / nstages) & 1, S.err)) ok = false;
+            tc_fence_after();
+            unsigned char *Bh = B0 + s * 2 * bop, *Bl = Bh + bop;
+            const int rowbase = FORCE ? 0 : c * kRC;
+            const int N = NP - rowbase;
+            const uint64_t dah = sdesc(smem_u32(Ph) + (c * kRC / 8) * 128, 128, sboP);
+            const uint64_t dal = sdesc(smem_u32(Pl) + (c * kRC / 8) * 128, 128, sboP);
+            for (int n0 = 0; n0 < N; n0 += 256) {
+              const int nn = min(256, N - n0);
+              const uint32_t id = idesc_f16(128, nn);
+              const uint64_t dbh = sdesc(smem_u32(Bh) + (n0 >> 3) * 256, 128, 256);
+              const uint64_t dbl = sdesc(smem_u32(Bl) + (n0 >> 3) * 256, 128, 256);
+              const uint32_t dm = tmem + rowbase + n0, dc = tmem + corr_base + rowbase + n0;
+              mma_f16(dm, dah, dbh, id, c > 0 ? 1u : 0u);
+              if (split3) {
+                mma_f16(dc, dah, dbl, id, (c > 0 || corr_base == 0) ? 1u : 0u);
+                mma_f16(dc, dal, dbh, id, 1u);
+              }
+            }
+            mma_commit(&sh.done[c]);
           }
         }
-        racc += (double)part;
-      }
-      if (valid && rho) rho[gidx] = racc * (2.0 / ((double)Sphi * (double)Sphi * (double)SD));
-    }
-    // all MMAs of the brick are complete once the last chunk's barrier has flipped (in order)
-    if (!mbar_wait(&sh.done[nch - 1], (dpar >> (nch - 1)) & 1u, err)) ok = false;
-    tc_fence_after();
-    G += nch;
-    dpar ^= (nch >= 32) ? 0xffffffffu : ((1u << nch) - 1u);
-    if (FORCE) {
-      // full Y: per atom, rho and force from recomputed phi and grad phi (unscaled float32)
-      const float inv = 1.f / (Sphi * SD);
-      const float wv = valid ? (float)(g.w * V[gidx]) : 0.f;
-      float rp = 0.f;
-      for (int a = q; a < na; a += 4) {
-        const int pc = sh.s_pcol[a], po = sh.s_po[a];
-        float y[GINT_MAX_ORB_ATOM], yc[16];
-        for (int h = 0; h < po; h += 16) {
-          tmem_ld16(tmem + lane_base + pc + h, y + h);
+        __syncwarp();
+      } else if (warp < 4 && !FORCE) {
+        double racc = 0.0;
+        for (int c = 0; c < nch; ++c) {
+          if (!mbar_wait(&sh.done[c], (dpar >> c) & 1u, S.err)) ok = false;
+          tc_fence_after();
+          // chunk c's columns are final: rho += P_k Y_k
+          const int k0 = c * kRC;
+          float y[16], yc[16];
+          tmem_ld16(tmem + lane_base + k0, y);
           if (split3 && corr_base) {
-            tmem_ld16(tmem + lane_base + corr_base + pc + h, yc);
+            tmem_ld16(tmem + lane_base + corr_base + k0, yc);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) y[h + i] += yc[i];
+            for (int i = 0; i < 16; ++i) y[i] += yc[i];
           }
+          float part = 0.f;
+#pragma unroll
+          for (int hseg = 0; hseg < 2; ++hseg) {
+            const uint32_t off = (p >> 3) * sboP + ((k0 >> 3) + hseg) * 128 + (p & 7) * 16;
+            const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + off), wl = *reinterpret_cast<const uint4 *>(Pl + off);
+            const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
+              const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
+              part += (hf.x + lf.x) * y[hseg * 8 + 2 * e] + (hf.y + lf.y) * y[hseg * 8 + 2 * e + 1];
+            }
+          }
+          racc += (double)part;
         }
-        for (int i = 0; i < po; ++i) y[i] *= inv;
-        float fx = 0.f, fy = 0.f, fz = 0.f;
-        switch (g.sp[sh.s_sp[a]].shape) {
+        if (valid && S.rho) S.rho[gidx] = racc * (2.0 / ((double)Sphi * (double)Sphi * (double)SD));
+      }
+      // all MMAs of the brick are complete once the last chunk's barrier has flipped (in order)
+      if (!mbar_wait(&sh.done[nch - 1], (dpar >> (nch - 1)) & 1u, S.err)) ok = false;
+      tc_fence_after();
+      G += nch;
+      dpar ^= (nch >= 32) ? 0xffffffffu : ((1u << nch) - 1u);
+      if (FORCE) {
+        // full Y: per atom, rho and force from recomputed phi and grad phi (unscaled float32)
+        const float2 *tab = S.tab;
+        const float inv = 1.f / (Sphi * SD);
+        const float wv = (valid && S.V) ? (float)(S.c.w * S.V[gidx]) : 0.f;
+        float rp = 0.f;
+        for (int a = q; a < na; a += 4) {
+          const int pc = sh.s_pcol[a], po = sh.s_po[a];
+          float y[GINT_MAX_ORB_ATOM], yc[16];
+          for (int h = 0; h < po; h += 16) {
+            tmem_ld16(tmem + lane_base + pc + h, y + h);
+            if (split3 && corr_base) {
+              tmem_ld16(tmem + lane_base + corr_base + pc + h, yc);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) y[h + i] += yc[i];
+            }
+          }
+          for (int i = 0; i < po; ++i) y[i] *= inv;
+          float fx = 0.f, fy = 0.f, fz = 0.f;
+          switch (g.sp[sh.s_sp[a]].shape) {
 #define CASE_F(ns, np_, nd)                                                                          \
   case GINT_SHAPE(ns, np_, nd):                                                                    \
     job_F<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tab, sh, a, p, valid, y, rp, fx, fy, fz); \
     break;
-          GINT_FOR_SHAPES(CASE_F)
+            GINT_FOR_SHAPES(CASE_F)
 #undef CASE_F
-          default:
-            job_F_generic(g, tab, sh, a, p, valid, y, rp, fx, fy, fz);
+            default:
+              job_F_generic(g, tab, sh, a, p, valid, y, rp, fx, fy, fz);
+          }
+          fx *= 2.f * wv;
+          fy *= 2.f * wv;
+          fz *= 2.f * wv;
+          for (int o = 16; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+          }
+          if (lane == 0) {
+            atomicAdd(&sh.fpart[a][0], (double)fx);
+            atomicAdd(&sh.fpart[a][1], (double)fy);
+            atomicAdd(&sh.fpart[a][2], (double)fz);
+          }
         }
-        fx *= 2.f * wv;
-        fy *= 2.f * wv;
-        fz *= 2.f * wv;
-        for (int o = 16; o > 0; o >>= 1) {
-          fx += __shfl_xor_sync(0xffffffffu, fx, o);
-          fy += __shfl_xor_sync(0xffffffffu, fy, o);
-          fz += __shfl_xor_sync(0xffffffffu, fz, o);
-        }
-        if (lane == 0) {
-          atomicAdd(&sh.fpart[a][0], (double)fx);
-          atomicAdd(&sh.fpart[a][1], (double)fy);
-          atomicAdd(&sh.fpart[a][2], (double)fz);
-        }
+        sh.rpart[q][p] = rp;
+        __syncthreads();
+        if (q == 0 && valid && S.rho)
+          S.rho[gidx] =
+              (double)sh.rpart[0][p] + (double)sh.rpart[1][p] + (double)sh.rpart[2][p] + (double)sh.rpart[3][p];
+        if (S.F)
+          for (int a = t; a < na; a += kT) {
+            const int I = sh.s_atom[a];
+            atomicAdd(S.F + 3 * I + 0, sh.fpart[a][0]);
+            atomicAdd(S.F + 3 * I + 1, sh.fpart[a][1]);
+            atomicAdd(S.F + 3 * I + 2, sh.fpart[a][2]);
+          }
       }
-      sh.rpart[q][p] = rp;
-      __syncthreads();
-      if (q == 0 && valid && rho)
-        rho[gidx] = (double)sh.rpart[0][p] + (double)sh.rpart[1][p] + (double)sh.rpart[2][p] + (double)sh.rpart[3][p];
-      for (int a = t; a < na; a += kT) {
-        const int I = sh.s_atom[a];
-        atomicAdd(F + 3 * I + 0, sh.fpart[a][0]);
-        atomicAdd(F + 3 * I + 1, sh.fpart[a][1]);
-        atomicAdd(F + 3 * I + 2, sh.fpart[a][2]);
+    } else {
+      // ================================================================ local-H brick
+      if (na == 0) continue;
+      const float SA = sh.sc[2];
+      const float out_scale = 1.f / (Sphi * SA);
+      const int pp = t & (kHP - 1), q = t >> 5;  // point within the chunk, slot slice (0..15)
+      const int ntile = (NP + 127) / 128;
+      int tb[3] = {0, 0, 0}, T = 0;
+      for (int m = 0; m < ntile; ++m) {
+        tb[m] = T;
+        T += NP - 128 * m;
       }
-    }
-    tc_fence_before();
-    if (!ok) sh.abort = 1;
-  }
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, 512);
-}
-
-// ------------------------------------------------------------------------------ local Hamiltonian
-// Dynamic shared memory per stage: A hi, A lo, B hi, B lo, each [np_max rows x 32 points]
-// (element (r, p): (r/8)*576 + (p/8)*144 + (r%8)*16 + (p%8)*2), plus a tail pad for the rows
-// above NP that the last 128-row A tile reads (they only feed output rows that are ignored).
-__global__ void __launch_bounds__(kT, 1)
-    k_tc_vlocal(GGeom g, GNbr nb, const float2 *__restrict__ tab, const long long *__restrict__ tile_off,
-                const float *__restrict__ scales, const double *__restrict__ V,
-                const long long *__restrict__ hs_brick_off, float *__restrict__ hs, int *work, unsigned *err,
-                int np_max, int split3) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ BrickSh sh;
-  const int t = threadIdx.x, warp = t >> 5;
-  const uint32_t op = (uint32_t)(np_max / 8) * kHSBO;
-  const uint32_t stage_bytes = 4 * op;
-  if (t == 0) {
-    mbar_init(&sh.done[0], 1);
-    mbar_init(&sh.done[1], 1);
-    fence_mbar_init();
-    sh.abort = 0;
-    sh.sc[0] = scales[0];
-    sh.sc[2] = scales[2];
-  }
-  if (warp == 0) {
-    tmem_alloc(&sh.tmem, 512);
-    tmem_relinquish();
-  }
-  init_points(g, sh);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = sh.tmem;
-  const float Sphi = sh.sc[0], SA = sh.sc[2];
-  const float out_scale = 1.f / (Sphi * SA);
-  const int pp = t & (kHP - 1), q = t >> 5;  // point within the chunk, slot slice (0..15)
-  uint32_t G = 0;
-  bool ok = true;
-  for (;;) {
-    __syncthreads();
-    if (t == 0) sh.brick = atomicAdd(work, 1);
-    __syncthreads();
-    const long long b = sh.brick;
-    if (b >= g.nbricks || sh.abort) break;
-    load_brick(g, nb, tile_off, b, sh);
-    const int na = sh.na, NP = sh.np;
-    if (na == 0) continue;
-    const int ntile = (NP + 127) / 128;
-    int tb[3] = {0, 0, 0}, T = 0;
-    for (int m = 0; m < ntile; ++m) {
-      tb[m] = T;
-      T += NP - 128 * m;
-    }
-    const uint32_t corr_base = (2 * T <= 512) ? (uint32_t)T : 0u;
-    for (int c = 0; c < 128 / kHP; ++c, ++G) {
-      const int s = G & 1;
-      unsigned char *Ah = smem + s * stage_bytes, *Al = Ah + op, *Bh = Al + op, *Bl = Bh + op;
-      if (G >= 2 && !mbar_wait(&sh.done[s], ((G - 2) >> 1) & 1, err)) ok = false;
-      const int pt = c * kHP + pp;
-      int gi, gj, gk;
-      const bool valid = brick_point(g, b, pt, gi, gj, gk);
-      const float wvSA = valid ? (float)(g.w * V[grid_index(g, gi, gj, gk)]) * SA : 0.f;
-      for (int a = q; a < na; a += 16) {
-        const int pc = sh.s_pcol[a];
-        const int gend = (a == na - 1) ? NP : 0;
-        for (int r = gap_begin(sh, a); r < pc; ++r) {
-          const uint32_t off = (r >> 3) * kHSBO + (pp >> 3) * kHLBO + (r & 7) * 16 + (pp & 7) * 2;
-          *reinterpret_cast<uint16_t *>(Bh + off) = 0;
-          *reinterpret_cast<uint16_t *>(Bl + off) = 0;
-          *reinterpret_cast<uint16_t *>(Ah + off) = 0;
-          *reinterpret_cast<uint16_t *>(Al + off) = 0;
-        }
-        for (int r = pc + sh.s_po[a]; r < gend; ++r) {
-          const uint32_t off = (r >> 3) * kHSBO + (pp >> 3) * kHLBO + (r & 7) * 16 + (pp & 7) * 2;
-          *reinterpret_cast<uint16_t *>(Bh + off) = 0;
-          *reinterpret_cast<uint16_t *>(Bl + off) = 0;
-          *reinterpret_cast<uint16_t *>(Ah + off) = 0;
-          *reinterpret_cast<uint16_t *>(Al + off) = 0;
-        }
-        switch (g.sp[sh.s_sp[a]].shape) {
+      const uint32_t corr_base = (2 * T <= 512) ? (uint32_t)T : 0u;
+      for (int c = 0; c < 128 / kHP; ++c, ++GH) {
+        const int s = GH & 1;
+        unsigned char *Ah = smem + s * hstage, *Al = Ah + hop, *Bh = Al + hop, *Bl = Bh + hop;
+        if (GH >= 2 && !mbar_wait(&sh.hdone[s], ((GH - 2) >> 1) & 1, S.err)) ok = false;
+        const int pt = c * kHP + pp;
+        int gi, gj, gk;
+        const bool valid = brick_point(S.c, b, pt, gi, gj, gk);
+        const float wvSA = valid ? (float)(S.c.w * S.V[grid_index(S.c, gi, gj, gk)]) * SA : 0.f;
+        for (int a = q; a < na; a += 16) {
+          const int pc = sh.s_pcol[a];
+          const int gend = (a == na - 1) ? NP : 0;
+          for (int r = gap_begin(sh, a); r < pc; ++r) {
+            const uint32_t off = (r >> 3) * kHSBO + (pp >> 3) * kHLBO + (r & 7) * 16 + (pp & 7) * 2;
+            *reinterpret_cast<uint16_t *>(Bh + off) = 0;
+            *reinterpret_cast<uint16_t *>(Bl + off) = 0;
+            *reinterpret_cast<uint16_t *>(Ah + off) = 0;
+            *reinterpret_cast<uint16_t *>(Al + off) = 0;
+          }
+          for (int r = pc + sh.s_po[a]; r < gend; ++r) {
+            const uint32_t off = (r >> 3) * kHSBO + (pp >> 3) * kHLBO + (r & 7) * 16 + (pp & 7) * 2;
+            *reinterpret_cast<uint16_t *>(Bh + off) = 0;
+            *reinterpret_cast<uint16_t *>(Bl + off) = 0;
+            *reinterpret_cast<uint16_t *>(Ah + off) = 0;
+            *reinterpret_cast<uint16_t *>(Al + off) = 0;
+          }
+          const float2 *tab = S.tab;
+          switch (g.sp[sh.s_sp[a]].shape) {
 #define CASE_H(ns, np_, nd)                                                                                    \
   case GINT_SHAPE(ns, np_, nd):                                                                              \
     job_H<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tab, sh, a, pt, pp, valid, Sphi, wvSA, Ah, Al, \
                                                             Bh, Bl);                                         \
     break;
-          GINT_FOR_SHAPES(CASE_H)
+            GINT_FOR_SHAPES(CASE_H)
 #undef CASE_H
-          default:
-            job_H_generic(g, tab, sh, a, pt, pp, valid, Sphi, wvSA, Ah, Al, Bh, Bl);
+            default:
+              job_H_generic(g, tab, sh, a, pt, pp, valid, Sphi, wvSA, Ah, Al, Bh, Bl);
+          }
         }
-      }
-      fence_async_smem();
-      __syncthreads();
-      if (t == 0) {
-        tc_fence_after();
-        for (int ks = 0; ks < kHP / 16; ++ks) {
-          for (int m = 0; m < ntile; ++m) {
-            const uint64_t dah = sdesc(smem_u32(Ah) + m * 16 * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
-            const uint64_t dal = sdesc(smem_u32(Al) + m * 16 * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
-            const int N = NP - 128 * m;
-            for (int n0 = 0; n0 < N; n0 += 256) {
-              const int nn = min(256, N - n0);
-              const uint32_t id = idesc_f16(128, nn);
-              const uint32_t brow = (uint32_t)(128 * m + n0);
-              const uint64_t dbh = sdesc(smem_u32(Bh) + (brow >> 3) * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
-              const uint64_t dbl = sdesc(smem_u32(Bl) + (brow >> 3) * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
-              const uint32_t dm = tmem + tb[m] + n0, dc = tmem + corr_base + tb[m] + n0;
-              const bool first = (c == 0 && ks == 0);
-              mma_f16(dm, dah, dbh, id, first ? 0u : 1u);
-              if (split3) {
-                mma_f16(dc, dah, dbl, id, (first && corr_base) ? 0u : 1u);
-                mma_f16(dc, dal, dbh, id, 1u);
+        fence_async_smem();
+        __syncthreads();
+        if (t == 0) {
+          tc_fence_after();
+          for (int ks = 0; ks < kHP / 16; ++ks) {
+            for (int m = 0; m < ntile; ++m) {
+              const uint64_t dah = sdesc(smem_u32(Ah) + m * 16 * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
+              const uint64_t dal = sdesc(smem_u32(Al) + m * 16 * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
+              const int N = NP - 128 * m;
+              for (int n0 = 0; n0 < N; n0 += 256) {
+                const int nn = min(256, N - n0);
+                const uint32_t id = idesc_f16(128, nn);
+                const uint32_t brow = (uint32_t)(128 * m + n0);
+                const uint64_t dbh = sdesc(smem_u32(Bh) + (brow >> 3) * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
+                const uint64_t dbl = sdesc(smem_u32(Bl) + (brow >> 3) * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
+                const uint32_t dm = tmem + tb[m] + n0, dc = tmem + corr_base + tb[m] + n0;
+                const bool first = (c == 0 && ks == 0);
+                mma_f16(dm, dah, dbh, id, first ? 0u : 1u);
+                if (split3) {
+                  mma_f16(dc, dah, dbl, id, (first && corr_base) ? 0u : 1u);
+                  mma_f16(dc, dal, dbh, id, 1u);
+                }
               }
             }
           }
+          mma_commit(&sh.hdone[s]);
         }
-        mma_commit(&sh.done[s]);
       }
-    }
-    {
-      const uint32_t Gp = G - 1;
-      if (!mbar_wait(&sh.done[Gp & 1], (Gp >> 1) & 1, err)) ok = false;
-      tc_fence_after();
-    }
-    // epilogue: upper slot-pair tiles -> scratch (float32, unscaled), 8-column runs per row:
-    // tile (a, c), a <= c, is porb(a) x porb(c) at rowst(a) + porb(a) (cumpo(c) - cumpo(a))
-    {
-      const int ln = t & 127, qq = t >> 7;
-      const uint32_t lane_base = (uint32_t)((ln >> 5) * 32) << 16;
-      const long long base = hs_brick_off[b];
-      for (int m = 0; m < ntile; ++m) {
-        const int mu = 128 * m + ln;
-        const int as = mu < NP ? sh.col2slot[mu] : kNoSlot;
-        const int il = as != kNoSlot ? mu - sh.s_pcol[as] : 0;
-        const bool rowok = as != kNoSlot && il < sh.s_no[as];
-        const int po_a = rowok ? sh.s_po[as] : 0, cum_a = rowok ? sh.s_cumpo[as] : 0;
-        float *rowp = hs + base + (rowok ? sh.s_rowst[as] : 0);
-        const int N = NP - 128 * m;
-        for (int gcol = qq; gcol < N / 16; gcol += 4) {
-          float y[16], yc[16];
-          tmem_ld16(tmem + lane_base + tb[m] + gcol * 16, y);
-          if (split3 && corr_base) {
-            tmem_ld16(tmem + lane_base + corr_base + tb[m] + gcol * 16, yc);
+      {
+        const uint32_t Gp = GH - 1;
+        if (!mbar_wait(&sh.hdone[Gp & 1], (Gp >> 1) & 1, S.err)) ok = false;
+        tc_fence_after();
+      }
+      // epilogue: upper slot-pair tiles -> scratch (float32, unscaled), 8-column runs per row:
+      // tile (a, c), a <= c, is porb(a) x porb(c) at rowst(a) + porb(a) (cumpo(c) - cumpo(a))
+      {
+        const int ln = t & 127, qq = t >> 7;
+        const uint32_t lane_base = (uint32_t)((ln >> 5) * 32) << 16;
+        const long long base = S.hs_brick_off[b];
+        for (int m = 0; m < ntile; ++m) {
+          const int mu = 128 * m + ln;
+          const int as = mu < NP ? sh.col2slot[mu] : kNoSlot;
+          const int il = as != kNoSlot ? mu - sh.s_pcol[as] : 0;
+          const bool rowok = as != kNoSlot && il < sh.s_no[as];
+          const int po_a = rowok ? sh.s_po[as] : 0, cum_a = rowok ? sh.s_cumpo[as] : 0;
+          float *rowp = S.hs + base + (rowok ? sh.s_rowst[as] : 0);
+          const int N = NP - 128 * m;
+          for (int gcol = qq; gcol < N / 16; gcol += 4) {
+            float y[16], yc[16];
+            tmem_ld16(tmem + lane_base + tb[m] + gcol * 16, y);
+            if (split3 && corr_base) {
+              tmem_ld16(tmem + lane_base + corr_base + tb[m] + gcol * 16, yc);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) y[i] += yc[i];
-          }
-          if (!rowok) continue;
+              for (int i = 0; i < 16; ++i) y[i] += yc[i];
+            }
+            if (!rowok) continue;
 #pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
-            const int nu = 128 * m + gcol * 16 + 8 * hh;
-            const int cs = sh.col2slot[nu];
-            if (cs == kNoSlot || cs < as) continue;
-            const int po_c = sh.s_po[cs];
-            float *dst = rowp + (long long)po_a * (sh.s_cumpo[cs] - cum_a) + il * po_c + (nu - sh.s_pcol[cs]);
-            reinterpret_cast<float4 *>(dst)[0] =
-                make_float4(y[8 * hh] * out_scale, y[8 * hh + 1] * out_scale, y[8 * hh + 2] * out_scale,
-                            y[8 * hh + 3] * out_scale);
-            reinterpret_cast<float4 *>(dst)[1] =
-                make_float4(y[8 * hh + 4] * out_scale, y[8 * hh + 5] * out_scale, y[8 * hh + 6] * out_scale,
-                            y[8 * hh + 7] * out_scale);
+            for (int hh = 0; hh < 2; ++hh) {
+              const int nu = 128 * m + gcol * 16 + 8 * hh;
+              const int cs = sh.col2slot[nu];
+              if (cs == kNoSlot || cs < as) continue;
+              const int po_c = sh.s_po[cs];
+              float *dst = rowp + (long long)po_a * (sh.s_cumpo[cs] - cum_a) + il * po_c + (nu - sh.s_pcol[cs]);
+              reinterpret_cast<float4 *>(dst)[0] =
+                  make_float4(y[8 * hh] * out_scale, y[8 * hh + 1] * out_scale, y[8 * hh + 2] * out_scale,
+                              y[8 * hh + 3] * out_scale);
+              reinterpret_cast<float4 *>(dst)[1] =
+                  make_float4(y[8 * hh + 4] * out_scale, y[8 * hh + 5] * out_scale, y[8 * hh + 6] * out_scale,
+                              y[8 * hh + 7] * out_scale);
+            }
           }
         }
       }
@@ -1132,18 +1156,42 @@ __global__ void __launch_bounds__(kT, 1)
   if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
-// Per pair (I <= J): H_IJ = sum over the bricks containing both (fixed order; float32 partials
-// of eight contributions, float64 total); H_JI = H_IJ^T.
-__global__ void k_h_reduce(const int *__restrict__ hu_pair, const long long *__restrict__ hu_off,
-                           const long long *__restrict__ hu_src, const float *__restrict__ hs,
-                           const int *__restrict__ pair_I, const int *__restrict__ pair_J,
-                           const int *__restrict__ pair_T, const long long *__restrict__ pair_off,
-                           const int *__restrict__ species, GGeom g, double *__restrict__ H) {
-  const int u = blockIdx.x;
-  const int p = hu_pair[u];
-  const int I = pair_I[p], J = pair_J[p];
-  const int nI = g.sp[species[I]].norb, nJ = g.sp[species[J]].norb, pJ = g.sp[species[J]].porb;
-  const long long k0 = hu_off[u], k1 = hu_off[u + 1];
+// ------------------------------------------------------------------------------ batched reduction
+struct GRedSys {
+  const int *hu_pair;
+  const long long *hu_off, *hu_src;
+  const float *hs;
+  const int *pair_I, *pair_J, *pair_T;
+  const long long *pair_off;
+  const int *species;
+  double *H;
+};
+struct GRed {
+  int nsys;
+  long long start[kMaxBatch + 1];  // first upper pair of each system
+  GRedSys sys[kMaxBatch];
+};
+
+// One CTA per upper pair (I <= J) of any system: H_IJ = sum over the bricks containing both
+// (fixed order; float32 partials of eight contributions, float64 total); H_JI = H_IJ^T.
+__global__ void k_h_reduce(const __grid_constant__ GTabs g, const __grid_constant__ GRed R) {
+  const long long gu = blockIdx.x;
+  int lo = 0, hi = R.nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (R.start[mid] <= gu)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const GRedSys &S = R.sys[lo];
+  const int u = (int)(gu - R.start[lo]);
+  const int p = S.hu_pair[u];
+  const int I = S.pair_I[p], J = S.pair_J[p];
+  const int nI = g.sp[S.species[I]].norb, nJ = g.sp[S.species[J]].norb, pJ = g.sp[S.species[J]].porb;
+  const long long k0 = S.hu_off[u], k1 = S.hu_off[u + 1];
+  const float *__restrict__ hs = S.hs;
+  const long long *__restrict__ src = S.hu_src;
   for (int e = threadIdx.x; e < nI * nJ; e += blockDim.x) {
     const int i = e / nJ, j = e - (e / nJ) * nJ;
     const int se = i * pJ + j;
@@ -1152,22 +1200,53 @@ __global__ void k_h_reduce(const int *__restrict__ hu_pair, const long long *__r
     for (; k + 8 <= k1; k += 8) {
       float v[8];
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) v[jj] = hs[hu_src[k + jj] + se];
+      for (int jj = 0; jj < 8; ++jj) v[jj] = hs[src[k + jj] + se];
       acc += (double)(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
     }
-    for (; k < k1; ++k) acc += (double)hs[hu_src[k] + se];
-    H[pair_off[p] + e] = acc;
-    if (I != J) H[pair_off[pair_T[p]] + (long long)j * nI + i] = acc;
+    for (; k < k1; ++k) acc += (double)hs[src[k] + se];
+    S.H[S.pair_off[p] + e] = acc;
+    if (I != J) S.H[S.pair_off[S.pair_T[p]] + (long long)j * nI + i] = acc;
   }
 }
 
-// ------------------------------------------------------------------------------ per-call preparation
-__global__ void k_absmax(const double *__restrict__ x, long long n, unsigned *out) {
-  float m = 0.f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    m = fmaxf(m, (float)fabs(x[i]));
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+// ------------------------------------------------------------------------------ batched preparation
+struct GPrepSys {
+  const double *D;  // NULL: no density / force items
+  long long nblock;
+  const double *V;  // NULL: no local-H / force items
+  long long ngrid;
+  double *F;        // zeroed here (the brick kernel accumulates into it)
+  long long natoms;
+  unsigned *mx;     // [0] bits of max |D|, [1] bits of max |V| (atomicMax on non-negative floats)
+  float *scales;
+  double phi_bound, w;
+};
+struct GPrep {
+  int nsys;
+  int *work;
+  GPrepSys sys[kMaxBatch];
+};
+
+// blockIdx.y = system: max |D|, max |V| (float32, rounded), zero F; also resets the work counter.
+__global__ void k_prep(const __grid_constant__ GPrep P) {
+  const GPrepSys &S = P.sys[blockIdx.y];
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  float mD = 0.f, mV = 0.f;
+  if (S.D)
+    for (long long i = i0; i < S.nblock; i += stride) mD = fmaxf(mD, (float)fabs(S.D[i]));
+  if (S.V)
+    for (long long i = i0; i < S.ngrid; i += stride) mV = fmaxf(mV, (float)fabs(S.V[i]));
+  if (S.F)
+    for (long long i = i0; i < 3 * S.natoms; i += stride) S.F[i] = 0.0;
+  for (int o = 16; o > 0; o >>= 1) {
+    mD = fmaxf(mD, __shfl_xor_sync(0xffffffffu, mD, o));
+    mV = fmaxf(mV, __shfl_xor_sync(0xffffffffu, mV, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (mD > 0.f) atomicMax(S.mx, __float_as_uint(mD));
+    if (mV > 0.f) atomicMax(S.mx + 1, __float_as_uint(mV));
+  }
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *P.work = 0;
 }
 
 __device__ double pow2_scale(double lim, double m) {
@@ -1175,43 +1254,67 @@ __device__ double pow2_scale(double lim, double m) {
   return exp2(floor(log2(lim / m)));
 }
 
-// Power-of-two scales: [0] orbitals, [1] D, [2] w V orbitals.  Largest scaled magnitudes stay
-// below 2^15 (float16 max 65504); a zero input gets the scale 2^20.
-__global__ void k_scales(const unsigned *maxbits, double phi_bound, double w, float *scales) {
-  const double pb = 4.0 * phi_bound;
-  scales[0] = (float)pow2_scale(30000.0, pb);
-  scales[1] = (float)pow2_scale(30000.0, (double)__uint_as_float(maxbits[0]));
-  scales[2] = (float)pow2_scale(30000.0, pb * w * (double)__uint_as_float(maxbits[1]));
+// Thread s: power-of-two scales of system s ([0] orbitals, [1] D, [2] w V orbitals), with the
+// largest scaled magnitudes below 2^15 (float16 max 65504; a zero input gets 2^20); then clears
+// the maxima for the next call.
+__global__ void k_prep_scales(const __grid_constant__ GPrep P) {
+  const int s = threadIdx.x;
+  if (s >= P.nsys) return;
+  const GPrepSys &S = P.sys[s];
+  const double pb = 4.0 * S.phi_bound;
+  S.scales[0] = (float)pow2_scale(30000.0, pb);
+  S.scales[1] = (float)pow2_scale(30000.0, (double)__uint_as_float(S.mx[0]));
+  S.scales[2] = (float)pow2_scale(30000.0, pb * S.w * (double)__uint_as_float(S.mx[1]));
+  S.mx[0] = 0u;
+  S.mx[1] = 0u;
 }
 
-// D blocks (float64, row-major norb(I) x norb(J)) -> scaled float16 (hi, lo) tiles of
-// roundup(norb(I), 8) x porb(J) in core-matrix order [row group][K group][8][8], plus halves.
-__global__ void k_build_tiles(const double *__restrict__ D, const int *__restrict__ pair_I,
-                              const int *__restrict__ pair_J, const long long *__restrict__ pair_off,
-                              const long long *__restrict__ tile_off, const int *__restrict__ species, GGeom g,
-                              const float *__restrict__ scales, __half *__restrict__ Dhi, __half *__restrict__ Dlo,
-                              __half *__restrict__ Dhi2, __half *__restrict__ Dlo2) {
-  const int p = blockIdx.x;
-  const int I = pair_I[p], J = pair_J[p];
-  const int nI = g.sp[species[I]].norb, nJ = g.sp[species[J]].norb, pJ = g.sp[species[J]].porb;
+struct GTileSys {
+  const double *D;
+  const int *pair_I, *pair_J;
+  const long long *pair_off, *tile_off;
+  const int *species;
+  const float *scales;
+  __half *Dhi, *Dlo, *Dhi2, *Dlo2;
+};
+struct GTile {
+  int nsys;
+  long long start[kMaxBatch + 1];  // first pair of each system
+  GTileSys sys[kMaxBatch];
+};
+
+// One CTA per pair of any system: D blocks (float64, row-major norb(I) x norb(J)) -> scaled
+// float16 (hi, lo) tiles of roundup(norb(I), 8) x porb(J) in core-matrix order
+// [row group][K group][8][8], plus the same tiles halved.
+__global__ void k_build_tiles(const __grid_constant__ GTabs g, const __grid_constant__ GTile TB) {
+  const long long gp = blockIdx.x;
+  int lo = 0, hi = TB.nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (TB.start[mid] <= gp)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const GTileSys &S = TB.sys[lo];
+  const int p = (int)(gp - TB.start[lo]);
+  const int I = S.pair_I[p], J = S.pair_J[p];
+  const int nI = g.sp[S.species[I]].norb, nJ = g.sp[S.species[J]].norb, pJ = g.sp[S.species[J]].porb;
   const int rI = (nI + 7) & ~7, sJ = pJ >> 3;
-  const double S = (double)scales[1];
-  const long long o = pair_off[p], to = tile_off[p];
+  const double sc = (double)S.scales[1];
+  const long long o = S.pair_off[p], to = S.tile_off[p];
   for (int e = threadIdx.x; e < rI * pJ; e += blockDim.x) {
     const int cm = e >> 6, w = e & 63;
     const int i = (cm / sJ) * 8 + (w >> 3), j = (cm % sJ) * 8 + (w & 7);
-    float v = 0.f, v2 = 0.f;
     if (i < nI && j < nJ) {
-      const double x = D[o + (long long)i * nJ + j] * S;
-      v = (float)x;
-      v2 = (float)(0.5 * x);
-      __half h = __float2half_rn(v), h2 = __float2half_rn(v2);
-      Dhi[to + e] = h;
-      Dlo[to + e] = __float2half_rn((float)(x - (double)__half2float(h)));
-      Dhi2[to + e] = h2;
-      Dlo2[to + e] = __float2half_rn((float)(0.5 * x - (double)__half2float(h2)));
+      const double x = S.D[o + (long long)i * nJ + j] * sc;
+      const __half h = __float2half_rn((float)x), h2 = __float2half_rn((float)(0.5 * x));
+      S.Dhi[to + e] = h;
+      S.Dlo[to + e] = __float2half_rn((float)(x - (double)__half2float(h)));
+      S.Dhi2[to + e] = h2;
+      S.Dlo2[to + e] = __float2half_rn((float)(0.5 * x - (double)__half2float(h2)));
     } else {
-      Dhi[to + e] = Dlo[to + e] = Dhi2[to + e] = Dlo2[to + e] = __float2half(0.f);
+      S.Dhi[to + e] = S.Dlo[to + e] = S.Dhi2[to + e] = S.Dlo2[to + e] = __float2half(0.f);
     }
   }
 }
@@ -1301,6 +1404,7 @@ void dfree(T *&p) {
   } while (0)
 
 void gint_tc_free(gint_handle *h) {
+  h->tc_bytes = 0;
   dfree(h->Dt_hi);
   dfree(h->Dt_lo);
   dfree(h->Dt_hi2);
@@ -1341,6 +1445,7 @@ int gint_tc_prepare(gint_handle *h) {
     return GINT_ENOMEM;
   }
   TC_CHECK(cudaMemset(h->zero_dev, 0, 256));
+  TC_CHECK(cudaMemset(h->scales, 0, 8 * sizeof(float)));
   TC_CHECK(cudaMemcpy(h->tile_off_dev, h->tile_off.data(), (h->npairs + 1) * sizeof(long long),
                       cudaMemcpyHostToDevice));
   // brick slot lists on the host
@@ -1427,6 +1532,10 @@ int gint_tc_prepare(gint_handle *h) {
     cudaGetLastError();
     return GINT_ENOMEM;
   }
+  h->tc_bytes = 4 * (long long)tbytes + 256 + (h->npairs + 1) * (long long)sizeof(long long) + 8 * sizeof(float) +
+                (nb + 1) * (long long)sizeof(long long) + std::max<long long>(h->hs_elems, 1) * (long long)sizeof(float) +
+                (long long)std::max<size_t>(upair.size(), 1) * (long long)sizeof(int) +
+                (long long)(uoff.size() + src.size()) * (long long)sizeof(long long);
   TC_CHECK(cudaMemcpy(h->hs_brick_off, hs_off.data(), (nb + 1) * sizeof(long long), cudaMemcpyHostToDevice));
   if (!upair.empty())
     TC_CHECK(cudaMemcpy(h->hu_pair, upair.data(), upair.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -1442,70 +1551,166 @@ int gint_tc_check_capacity(const gint_handle *h) {
   return GINT_OK;
 }
 
-static int compute_scales(gint_handle *h, const double *D, const double *V, cudaStream_t st) {
-  unsigned *mx = reinterpret_cast<unsigned *>(h->scales + 4);
-  TC_CHECK(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned), st));
-  if (D && h->nblock > 0) k_absmax<<<2 * h->num_sms, 256, 0, st>>>(D, h->nblock, mx);
-  if (V) k_absmax<<<2 * h->num_sms, 256, 0, st>>>(V, h->geom.ngrid, mx + 1);
-  k_scales<<<1, 1, 0, st>>>(mx, h->phi_bound, h->geom.w, h->scales);
+static_assert(sizeof(GTabs) + sizeof(GBatch) + 64 <= 32764, "brick kernel parameters exceed the launch limit");
+static_assert(sizeof(GTabs) + sizeof(GTile) <= 32764 && sizeof(GTabs) + sizeof(GRed) <= 32764 &&
+                  sizeof(GPrep) <= 32764,
+              "batch kernel parameters exceed the launch limit");
+
+// One launch group (at most kMaxBatch tasks, validated by the caller).
+static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st) {
+  gint_handle *h0 = tk[0].h;
+  const GTabs &tabs = h0->geom;
+  GPrep P{};
+  GTile TB{};
+  GBatch B{};
+  GRed R{};
+  P.nsys = n;
+  P.work = h0->work_ctr;
+  bool force = false, any_rho = false, any_h = false;
+  int np = kRC;
+  long long items = 0, pairs = 0, uppers = 0;
+  int nt = 0, nr = 0;
+  for (int i = 0; i < n; ++i) {
+    const gint_task &T = tk[i];
+    gint_handle *h = T.h;
+    const bool dens = T.rho || T.F, loc = T.H_blocks != nullptr;
+    force |= T.F != nullptr;
+    any_rho |= dens;
+    any_h |= loc;
+    GPrepSys &ps = P.sys[i];
+    ps.D = dens ? T.D_blocks : nullptr;
+    ps.nblock = h->nblock;
+    ps.V = (loc || T.F) ? T.V : nullptr;
+    ps.ngrid = h->geom.ngrid;
+    ps.F = T.F;
+    ps.natoms = h->geom.natoms;
+    ps.mx = reinterpret_cast<unsigned *>(h->scales + 4);
+    ps.scales = h->scales;
+    ps.phi_bound = h->phi_bound;
+    ps.w = h->geom.w;
+    if (dens && h->npairs > 0) {
+      TB.start[nt] = pairs;
+      GTileSys &ts = TB.sys[nt++];
+      ts.D = T.D_blocks;
+      ts.pair_I = h->pair_I_dev;
+      ts.pair_J = h->pair_col_dev;
+      ts.pair_off = h->pair_off_dev;
+      ts.tile_off = h->tile_off_dev;
+      ts.species = h->species_dev;
+      ts.scales = h->scales;
+      ts.Dhi = h->Dt_hi;
+      ts.Dlo = h->Dt_lo;
+      ts.Dhi2 = h->Dt_hi2;
+      ts.Dlo2 = h->Dt_lo2;
+      pairs += h->npairs;
+    }
+    GSys &S = B.sys[i];
+    S.c = static_cast<const GCell &>(h->geom);
+    S.nb = h->nbr();
+    S.tab = h->tab32;
+    S.Dhi = h->Dt_hi;
+    S.Dlo = h->Dt_lo;
+    S.Dhi2 = h->Dt_hi2;
+    S.Dlo2 = h->Dt_lo2;
+    S.tile_off = h->tile_off_dev;
+    S.scales = h->scales;
+    S.V = T.V;
+    S.rho = T.rho;
+    S.F = T.F;
+    S.hs_brick_off = h->hs_brick_off;
+    S.hs = h->hs;
+    S.err = h->err_word;
+    S.nrho = dens ? h->geom.nbricks : 0;
+    S.nh = loc ? h->geom.nbricks : 0;
+    B.start[i] = items;
+    items += S.nrho + S.nh;
+    if (dens || loc) np = std::max(np, h->max_brick_porb);
+    if (loc && h->nupper > 0) {
+      R.start[nr] = uppers;
+      GRedSys &rs = R.sys[nr++];
+      rs.hu_pair = h->hu_pair;
+      rs.hu_off = h->hu_off;
+      rs.hu_src = h->hu_src;
+      rs.hs = h->hs;
+      rs.pair_I = h->pair_I_dev;
+      rs.pair_J = h->pair_col_dev;
+      rs.pair_T = h->pair_T_dev;
+      rs.pair_off = h->pair_off_dev;
+      rs.species = h->species_dev;
+      rs.H = T.H_blocks;
+      uppers += h->nupper;
+    }
+  }
+  B.nsys = n;
+  B.start[n] = items;
+  TB.nsys = nt;
+  TB.start[nt] = pairs;
+  R.nsys = nr;
+  R.start[nr] = uppers;
+  np = (np + 15) & ~15;
+  int nstages = kMaxStages;
+  if (any_rho)
+    while (nstages > 2 && rho_smem_bytes(np, nstages) + sizeof(BrickSh) > 227 * 1024) --nstages;
+  const uint32_t smem = std::max(any_rho ? rho_smem_bytes(np, nstages) : 0u, any_h ? h_smem_bytes(np) : 0u);
+  if (smem + sizeof(BrickSh) > 227 * 1024) return GINT_ECAPACITY;
+  B.np_max = np;
+  B.nstages = nstages;
+  B.split3 = split3;
+  const int bx = std::max(8, 2 * h0->num_sms / n);
+  k_prep<<<dim3(bx, n), 256, 0, st>>>(P);
+  k_prep_scales<<<1, kMaxBatch, 0, st>>>(P);
   TC_CHECK(cudaGetLastError());
+  if (pairs > 0) {
+    k_build_tiles<<<(unsigned)pairs, 128, 0, st>>>(tabs, TB);
+    TC_CHECK(cudaGetLastError());
+  }
+  if (items > 0) {
+    const unsigned grid = (unsigned)std::min<long long>(h0->num_sms, items);
+    auto kern = force ? k_tc_fused<true> : k_tc_fused<false>;
+    int rc = set_smem(kern, smem);
+    if (rc) return rc;
+    kern<<<grid, kT, smem, st>>>(tabs, B, h0->zero_dev, h0->work_ctr);
+    TC_CHECK(cudaGetLastError());
+  }
+  if (uppers > 0) {
+    k_h_reduce<<<(unsigned)uppers, 192, 0, st>>>(tabs, R);
+    TC_CHECK(cudaGetLastError());
+  }
+  return GINT_OK;
+}
+
+int gint_tc_batch(const gint_task *tasks, int n, int precision, cudaStream_t st) {
+  if (n <= 0) return GINT_OK;
+  const gint_handle *h0 = tasks[0].h;
+  for (int i = 0; i < n; ++i) {
+    const gint_task &T = tasks[i];
+    const gint_handle *h = T.h;
+    int rc = gint_tc_check_capacity(h);
+    if (rc) return rc;
+    if (T.H_blocks && h->max_brick_porb > kNPMAXH) return GINT_ECAPACITY;
+    if (h->device != h0->device) return GINT_EINVAL;
+    if (std::memcmp(static_cast<const GTabs *>(&h->geom), static_cast<const GTabs *>(&h0->geom), sizeof(GTabs)))
+      return GINT_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (tasks[j].h == h) return GINT_EINVAL;
+  }
+  const int split3 = precision == GINT_F16X3 ? 1 : 0;
+  for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
+    int rc = run_group(tasks + i0, std::min(kMaxBatch, n - i0), split3, st);
+    if (rc) return rc;
+  }
   return GINT_OK;
 }
 
 int gint_tc_rho(gint_handle *h, int precision, const double *D, double *rho, const double *V, double *F,
                 cudaStream_t st) {
-  int rc = gint_tc_check_capacity(h);
-  if (rc) return rc;
-  if (h->geom.nbricks == 0) return GINT_OK;
-  const int split3 = precision == GINT_F16X3 ? 1 : 0;
-  if ((rc = compute_scales(h, D, nullptr, st))) return rc;
-  if (h->npairs > 0)
-    k_build_tiles<<<h->npairs, 128, 0, st>>>(D, h->pair_I_dev, h->pair_col_dev, h->pair_off_dev, h->tile_off_dev,
-                                             h->species_dev, h->geom, h->scales, h->Dt_hi, h->Dt_lo, h->Dt_hi2,
-                                             h->Dt_lo2);
-  TC_CHECK(cudaGetLastError());
-  const int np = std::max(h->max_brick_porb, kRC);
-  int nstages = kMaxStages;
-  while (nstages > 2 && rho_smem_bytes(np, nstages) + sizeof(BrickSh) > 227 * 1024) --nstages;
-  const uint32_t smem = rho_smem_bytes(np, nstages);
-  TC_CHECK(cudaMemsetAsync(h->work_ctr, 0, sizeof(int), st));
-  const unsigned grid = (unsigned)std::min<long long>(h->num_sms, h->geom.nbricks);
-  if (F) {
-    auto kern = k_tc_rho<true>;
-    if ((rc = set_smem(kern, smem))) return rc;
-    kern<<<grid, kT, smem, st>>>(h->geom, h->nbr(), h->tab32, h->Dt_hi, h->Dt_lo, h->Dt_hi2, h->Dt_lo2, h->zero_dev,
-                                 h->tile_off_dev, h->scales, V, rho, F, h->work_ctr, h->err_word, np, nstages, split3);
-  } else {
-    auto kern = k_tc_rho<false>;
-    if ((rc = set_smem(kern, smem))) return rc;
-    kern<<<grid, kT, smem, st>>>(h->geom, h->nbr(), h->tab32, h->Dt_hi, h->Dt_lo, h->Dt_hi2, h->Dt_lo2, h->zero_dev,
-                                 h->tile_off_dev, h->scales, V, rho, F, h->work_ctr, h->err_word, np, nstages, split3);
-  }
-  TC_CHECK(cudaGetLastError());
-  return GINT_OK;
+  const gint_task t{h, D, V, rho, nullptr, F};
+  return gint_tc_batch(&t, 1, precision, st);
 }
 
 int gint_tc_vlocal(gint_handle *h, int precision, const double *V, double *H, cudaStream_t st) {
-  int rc = gint_tc_check_capacity(h);
-  if (rc) return rc;
-  if (h->max_brick_porb > kNPMAXH) return GINT_ECAPACITY;
-  if (h->geom.nbricks == 0) return GINT_OK;
-  const int split3 = precision == GINT_F16X3 ? 1 : 0;
-  if ((rc = compute_scales(h, nullptr, V, st))) return rc;
-  const int np = std::max(h->max_brick_porb, 16);
-  const uint32_t smem = h_smem_bytes(np);
-  TC_CHECK(cudaMemsetAsync(h->work_ctr, 0, sizeof(int), st));
-  const unsigned grid = (unsigned)std::min<long long>(h->num_sms, h->geom.nbricks);
-  if ((rc = set_smem(k_tc_vlocal, smem))) return rc;
-  k_tc_vlocal<<<grid, kT, smem, st>>>(h->geom, h->nbr(), h->tab32, h->tile_off_dev, h->scales, V, h->hs_brick_off,
-                                      h->hs, h->work_ctr, h->err_word, np, split3);
-  TC_CHECK(cudaGetLastError());
-  if (h->nupper > 0) {
-    k_h_reduce<<<h->nupper, 192, 0, st>>>(h->hu_pair, h->hu_off, h->hu_src, h->hs, h->pair_I_dev, h->pair_col_dev,
-                                          h->pair_T_dev, h->pair_off_dev, h->species_dev, h->geom, H);
-    TC_CHECK(cudaGetLastError());
-  }
-  return GINT_OK;
+  const gint_task t{h, nullptr, V, nullptr, H, nullptr};
+  return gint_tc_batch(&t, 1, precision, st);
 }
 
 extern "C" int gint_tc_selftest(int n, double *max_err) {

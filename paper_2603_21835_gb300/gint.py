@@ -8,7 +8,8 @@ from __future__ import annotations
 
 import ctypes
 import os
-from typing import Optional
+from dataclasses import dataclass
+from typing import Optional, Sequence
 
 import numpy as np
 import torch
@@ -46,6 +47,11 @@ class _Desc(ctypes.Structure):
                 ("n1", ctypes.c_int), ("n2", ctypes.c_int), ("n3", ctypes.c_int), ("skin", ctypes.c_double)]
 
 
+class _Task(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_void_p), ("D_blocks", ctypes.c_void_p), ("V", ctypes.c_void_p),
+                ("rho", ctypes.c_void_p), ("H_blocks", ctypes.c_void_p), ("F", ctypes.c_void_p)]
+
+
 _vp, _ll, _i, _d = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int, ctypes.c_double
 _lib.gint_strerror.restype = ctypes.c_char_p
 _lib.gint_strerror.argtypes = [_i]
@@ -66,10 +72,13 @@ _lib.gint_weight.argtypes = [_vp]
 _lib.gint_sync.argtypes = [_vp, _vp]
 _lib.gint_tc_selftest.argtypes = [_i, ctypes.POINTER(_d)]
 _lib.gint_grid_dot_noalloc.argtypes = [_vp, _vp, _ll, _d, _vp, _vp]
+_lib.gint_run_batch.argtypes = [ctypes.POINTER(_Task), _i, _i, _vp]
+_lib.gint_memory.argtypes = [_vp, ctypes.POINTER(_ll)]
 
 C_ABI_SYMBOLS = ("gint_create", "gint_destroy", "gint_layout", "gint_pairs", "gint_stats", "gint_set_positions",
                  "gint_rho", "gint_vlocal", "gint_force", "gint_grid_dot", "gint_block_dot", "gint_weight",
-                 "gint_strerror", "gint_sync", "gint_tc_selftest", "gint_grid_dot_noalloc")
+                 "gint_strerror", "gint_sync", "gint_tc_selftest", "gint_grid_dot_noalloc", "gint_run_batch",
+                 "gint_memory")
 
 
 def tc_selftest(n: int = 256) -> float:
@@ -98,6 +107,28 @@ def _dptr(t: Optional[torch.Tensor], dtype=torch.float64, numel: Optional[int] =
 def _stream(stream) -> ctypes.c_void_p:
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class Task:
+    """The passes of one system in a batch: outputs left as None are not computed (see gint_task)."""
+    g: "Gint"
+    D: Optional[torch.Tensor] = None     # D blocks [nblock]
+    V: Optional[torch.Tensor] = None     # potential [ngrid]
+    rho: Optional[torch.Tensor] = None   # out: density [ngrid]
+    H: Optional[torch.Tensor] = None     # out: local-H blocks [nblock]
+    F: Optional[torch.Tensor] = None     # out: forces [natoms, 3]
+
+
+def run_batch(tasks: Sequence[Task], precision: int = F16X3, stream=None) -> None:
+    """All tasks' bricks in one persistent launch (tensor-core precisions; up to 32 systems per
+    launch), asynchronous on `stream`."""
+    arr = (_Task * max(len(tasks), 1))()
+    for i, t in enumerate(tasks):
+        g = t.g
+        arr[i] = _Task(g._h, _dptr(t.D, numel=g.nblock), _dptr(t.V, numel=g.ngrid), _dptr(t.rho, numel=g.ngrid),
+                       _dptr(t.H, numel=g.nblock), _dptr(t.F, numel=3 * g.natoms))
+    _check(_lib.gint_run_batch(arr, len(tasks), int(precision), _stream(stream)), "gint_run_batch")
 
 
 class Gint:
@@ -148,6 +179,12 @@ class Gint:
                                ctypes.byref(ma)), "gint_stats")
         return dict(W=W.value, W_exec=Wx.value, nbricks=nb.value, max_brick_orb=mo.value, max_brick_atoms=ma.value)
 
+    def memory(self) -> int:
+        """Device bytes held by the handle (tables, neighbour lists, workspace)."""
+        b = _ll()
+        _check(_lib.gint_memory(self._h, ctypes.byref(b)), "gint_memory")
+        return b.value
+
     def close(self):
         if getattr(self, "_h", None):
             _lib.gint_destroy(self._h)
@@ -185,6 +222,13 @@ class Gint:
                                _dptr(rho_out, numel=self.ngrid) if rho_out is not None else None, _stream(stream)),
                "gint_force")
         return out
+
+    def run(self, D_blocks: Optional[torch.Tensor], V: Optional[torch.Tensor], precision: int = F16X3,
+            rho: Optional[torch.Tensor] = None, H: Optional[torch.Tensor] = None, F: Optional[torch.Tensor] = None,
+            stream=None) -> None:
+        """Several passes of this system in one call (with the tensor-core precisions the density
+        or force bricks and the local-H bricks share one persistent launch)."""
+        run_batch([Task(self, D_blocks, V, rho, H, F)], precision, stream)
 
     def grid_dot(self, V: Optional[torch.Tensor], rho: torch.Tensor, out: Optional[torch.Tensor] = None,
                  stream=None) -> torch.Tensor:

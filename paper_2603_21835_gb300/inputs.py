@@ -226,6 +226,16 @@ def wrap_positions(cell: np.ndarray, pos: np.ndarray) -> np.ndarray:
     return frac @ cell
 
 
+def on_species(system: System, library: Sequence[Species]) -> System:
+    """The same system with its atoms' species re-indexed into ``library`` (matched by name).
+
+    Systems that share one species list share the radial-table metadata, which is what lets a
+    serving loop run them in one batched launch."""
+    idx = {sp.name: k for k, sp in enumerate(library)}
+    remap = np.array([idx[sp.name] for sp in system.sp], dtype=np.int32)
+    return dataclasses.replace(system, species=remap[system.species].astype(np.int32), sp=list(library))
+
+
 @dataclasses.dataclass
 class Workload:
     system: System

@@ -60,7 +60,7 @@ def si8(torch_cuda):
 
 
 def test_tc_mma_selftest(torch_cuda):
-    """One tcgen05 TF32 MMA per operand layout on exact integer data."""
+    """One tcgen05 kind::f16 MMA per operand layout on exact integer data."""
     from paper_2603_21835_gb300 import gint as G
 
     for n in (16, 32, 112, 208, 256):
