@@ -8,6 +8,11 @@ W = sum_g n_g^2 per pass, so one step is 2W pair updates; the metric is Gpt-pair
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f16x3|fp64|fp32|f16x1]
                   [--workload si64_g96|si8_g48|si512_g192] [--impl ours|reference]
 
+With the tensor-core precisions both passes' bricks run in one persistent launch per step.
+After the timed steps (rank 0, N = 1) a serving run submits a Poisson stream of density +
+local-H + force requests over a mix of Si supercells (8-216 atoms) and water clusters (8-64
+molecules) to the continuous-batching server and reports p50/p99 latency and throughput.
+
 N > 1 runs N independent replicas (one per rank, launched by torch.distributed.run): the
 path needs no exchange between GPUs; value is the total work of all ranks over the slowest
 rank's time.  --impl reference times the FP64 CPU oracle on the host cores on a bounded
@@ -32,8 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "gint Gpt-pair/s (rho+H_loc) mixed vs FP64 on GB300 at <=1e-6 rel err; p50/p99 ms"
 UNIT = "Gpt-pair/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-# nominal dense ratios to bf16 (2.25 PF): tf32 1.1 PF; float64 1.25 TF (GB300)
-TF32_PER_BF16 = 1.1 / 2.25
+# nominal float64 rate of GB300 (no fast float64 tensor path)
 FP64_NOMINAL_TFLOPS = 1.25
 FP32_SIMT_TFLOPS_PER_GHZ = 152 * 128 * 2 / 1e3  # 152 SMs x 128 FP32 lanes x 2 flops per clock
 
@@ -49,6 +53,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=256, help="Poisson serving run (0: skip)")
+    ap.add_argument("--serve-load", type=float, default=0.6, help="arrival rate / measured burst capacity")
+    ap.add_argument("--serve-budget-gb", type=float, default=32.0)
     return ap.parse_args()
 
 
@@ -170,9 +177,80 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------ our arm
-KERNEL_LAUNCHES = {  # kernels of ours per step (rho pass + H pass); memsets are not kernels
-    "fp64": 2, "fp32": 3, "f16x3": None, "f16x1": None,
-}
+# kernels of ours per step (density + local-H passes; memsets are not kernels):
+#   fp64: k_simt_rho, k_simt_vlocal;  fp32: k_to_f32, k_simt_rho, k_simt_vlocal;
+#   f16x3 / f16x1: k_prep, k_prep_scales, k_build_tiles, k_tc_fused (both passes), k_h_reduce
+KERNEL_LAUNCHES = {"fp64": 2, "fp32": 3, "f16x3": 5, "f16x1": 5}
+TENSOR_PRECISIONS = ("f16x3", "f16x1")
+
+
+def run_serving(args, prec, dev):
+    """Continuous batching: a Poisson stream of rho + H + F requests over the serving mix."""
+    import torch
+
+    from paper_2603_21835_gb300 import inputs, serve
+
+    pool = inputs.serving_pool()
+    srv = serve.Server(inputs.serving_library(), budget_bytes=int(args.serve_budget_gb * (1 << 30)), precision=prec,
+                       device=dev)
+    try:
+        sessions = [srv.open(s) for s in pool]
+        nvar = 4
+        rng = np.random.default_rng(5)
+        choice = rng.integers(0, len(pool), args.serve_requests)
+        cache = {}
+
+        def req(i, k):
+            if (i, k) not in cache:
+                V, C = inputs.serving_inputs(pool[i], seed=100 * i + k)
+                cache[(i, k)] = (torch.from_numpy(sessions[i].blocks_from_coefficients(C)).pin_memory(),
+                                 torch.from_numpy(np.ascontiguousarray(V.reshape(-1))).pin_memory())
+            return cache[(i, k)]
+
+        plan = [(int(i), n % nvar) for n, i in enumerate(choice)]
+        for i, k in plan:
+            req(i, k)
+        # warm-up and burst capacity: every geometry twice, submitted at once
+        burst = [(i, k) for k in range(2) for i in range(len(pool))]
+        for _ in range(2):
+            t0 = time.perf_counter()
+            futs = [srv.submit(sessions[i], *req(i, k)) for i, k in burst]
+            res = [f.result(timeout=300) for f in futs]
+            t_burst = max(r.done_t for r in res) - t0
+        capacity = len(burst) / t_burst
+        rate = args.serve_load * capacity
+        gaps = rng.exponential(1.0 / rate, len(plan))
+        nb0 = len(srv.batch_sizes)
+        futs = []
+        t0 = time.perf_counter()
+        due = t0
+        for (i, k), gap in zip(plan, gaps):
+            due += gap
+            while True:
+                dt = due - time.perf_counter()
+                if dt <= 0:
+                    break
+                time.sleep(min(dt, 0.002))
+            futs.append(srv.submit(sessions[i], *req(i, k)))
+        res = [f.result(timeout=300) for f in futs]
+        t_end = max(r.done_t for r in res)
+        lat = serve.percentiles([r.latency_ms for r in res])
+        pairs = sum(2.0 * sessions[i].W for i, _ in plan)
+        sizes = srv.batch_sizes[nb0:]
+        out = {
+            "requests": len(plan), "outputs": "rho+H+F", "pool": [s.name for s in pool],
+            "arrivals": f"Poisson, rate = {args.serve_load:g} x burst capacity",
+            "rate_hz": rate, "burst_capacity_req_s": capacity,
+            "p50_ms": lat["p50"], "p99_ms": lat["p99"], "mean_ms": lat["mean"], "max_ms": lat["max"],
+            "throughput_req_s": len(plan) / (t_end - t0),
+            "throughput_gpt_pair_s": pairs / (t_end - t0) / 1e9,
+            "throughput_note": "2W per request (rho + H pair updates); the force pass is extra work not counted",
+            "batches": len(sizes), "mean_batch": float(np.mean(sizes)), "max_batch": int(max(sizes)),
+            "budget_bytes": srv.budget.budget, "peak_bytes": srv.budget.peak, "errors": len(srv.errors),
+        }
+    finally:
+        srv.close()
+    return out
 
 
 def main():
@@ -207,10 +285,30 @@ def main():
     H = torch.empty(g.nblock, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+    tensor = args.precision in TENSOR_PRECISIONS
 
-    def step():
-        g.rho(Db, prec, out=rho)
-        g.vlocal(V, prec, out=H)
+    def new_events(n):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for a, b in evs:  # CUDA events are created on first record
+            a.record(stream)
+            b.record(stream)
+        return evs
+
+    def step(kev=None, rev=None, hev=None):
+        """One step: density + local-H passes.  Tensor-core precisions: one call, both passes'
+        bricks in one persistent launch (kev brackets that kernel); SIMT: two calls."""
+        if tensor:
+            g.run(Db, V, prec, rho=rho, H=H, kernel_events=kev)
+        else:
+            if rev:
+                rev[0].record(stream)
+            g.rho(Db, prec, out=rho)
+            if rev:
+                rev[1].record(stream)
+                hev[0].record(stream)
+            g.vlocal(V, prec, out=H)
+            if hev:
+                hev[1].record(stream)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -218,44 +316,52 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    ev, evk, evr, evh = (new_events(args.steps) for _ in range(4))
+    torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    evh = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for k in range(args.steps):
         flush.fill_(float(k))
         ev[k][0].record(stream)
-        evr[k][0].record(stream)
-        g.rho(Db, prec, out=rho)
-        evr[k][1].record(stream)
-        evh[k][0].record(stream)
-        g.vlocal(V, prec, out=H)
-        evh[k][1].record(stream)
+        step(evk[k], evr[k], evh[k])
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
     if world > 1:
         dist.barrier()
     t_steps = [a.elapsed_time(b) for a, b in ev]
-    t_rho = [a.elapsed_time(b) for a, b in evr]
-    t_h = [a.elapsed_time(b) for a, b in evh]
+    # the passes one at a time (informational, outside the timed steps)
+    t_rho, t_h = [], []
+    for k in range(3):
+        for fn, lst in ((lambda: g.rho(Db, prec, out=rho), t_rho), (lambda: g.vlocal(V, prec, out=H), t_h)):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            lst.append(a.elapsed_time(b))
     tot = torch.tensor([sum(t_steps)], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(tot, op=dist.ReduceOp.MAX)
     ms_per_step = tot.item() / args.steps
     value = world * 2.0 * W / (ms_per_step * 1e-3) / 1e9
 
-    # roofline of the dominant kernel (per-launch mean over the timed region)
+    # roofline of the dominant kernel (per-launch mean over the timed region, CUDA events on its stream)
     peaks, peak_kind = load_peaks()
-    mr, mh = statistics.mean(t_rho), statistics.mean(t_h)
-    dom, tdom = ("rho", mr) if mr >= mh else ("vlocal", mh)
-    flops = W  # one FMA per unordered orbital pair per grid point (D, H symmetric)
-    if args.precision in ("f16x3", "f16x1"):
-        bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-        peak = bf16 * TF32_PER_BF16
-        bound, punit, pdesc = "tensor", "TFLOP/s", f"tf32 dense = {peak_kind} bf16 sustained x 1.1/2.25"
+    if tensor:
+        dom, tdom = "k_tc_fused (density + local-H bricks)", statistics.mean(a.elapsed_time(b) for a, b in evk)
+        flops = 2.0 * W  # per pass one FMA per unordered orbital pair per grid point (D, H symmetric)
+    else:
+        mr = statistics.mean(a.elapsed_time(b) for a, b in evr)
+        mh = statistics.mean(a.elapsed_time(b) for a, b in evh)
+        dom, tdom = ("k_simt_rho", mr) if mr >= mh else ("k_simt_vlocal", mh)
+        flops = W
+    if tensor:
+        peak = peaks.get("bf16_tflops")
+        bound, punit = "tensor", "TFLOP/s"
+        pdesc = f"f16 dense = {peak_kind} bf16 burst (nominal f16 and bf16 dense rates are equal)"
     elif args.precision == "fp64":
         peak = FP64_NOMINAL_TFLOPS
         bound, punit, pdesc = "alu", "TFLOP/s", "fp64 nominal 1.25 TFLOP/s (GB300)"
@@ -284,8 +390,11 @@ def main():
             e0.record(stream)
             Dd.copy_(Dh, non_blocking=True)
             Vd.copy_(Vh, non_blocking=True)
-            g.rho(Dd, prec, out=rho)
-            g.vlocal(Vd, prec, out=H)
+            if tensor:
+                g.run(Dd, Vd, prec, rho=rho, H=H)
+            else:
+                g.rho(Dd, prec, out=rho)
+                g.vlocal(Vd, prec, out=H)
             rho_h.copy_(rho, non_blocking=True)
             H_h.copy_(H, non_blocking=True)
             e1.record(stream)
@@ -305,6 +414,10 @@ def main():
         v, cores, desc, _ = oracle_sample(args.workload, args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
+    serving = None
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        serving = run_serving(args, prec, dev)
+
     launches = KERNEL_LAUNCHES.get(args.precision)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -316,9 +429,9 @@ def main():
                    "precision": args.precision, "W_pairs_per_pass": W, "W_exec_padded": st["W_exec"],
                    "nbricks": st["nbricks"], "max_brick_orb": st["max_brick_orb"], "l2": "flushed (256 MB write)",
                    "parallelism": f"replicas{world}"},
-        "ms_rho": statistics.mean(t_rho), "ms_vlocal": statistics.mean(t_h),
+        "ms_kernel": tdom, "ms_rho_alone": statistics.mean(t_rho), "ms_vlocal_alone": statistics.mean(t_h),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": (launches * args.steps) if launches is not None else None,
+        "gpu_launches": launches * args.steps, "serving": serving,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -160,6 +160,13 @@ typedef struct gint_task {
  * otherwise GINT_EINVAL, as for a repeated handle or a missing input. */
 int gint_run_batch(const gint_task *tasks, int ntasks, int precision, void *stream);
 
+/* gint_run_batch that also records two caller-created CUDA events (cudaEvent_t, may be NULL) on
+ * `stream`: ev_start right before the first brick-kernel launch and ev_stop right after the
+ * last (FP64 / FP32: around all of the batch's kernels), so that the brick kernels can be timed
+ * without the per-call preparation and reduction launches. */
+int gint_run_batch_timed(const gint_task *tasks, int ntasks, int precision, void *stream, void *ev_start,
+                         void *ev_stop);
+
 /* Float64 reductions on the device, written to out_dev[0] (device):
  *   V != NULL: w * sum_g V_g rho_g  (the energy E);   V == NULL: w * sum_g rho_g (N_e = Tr(DS)). */
 int gint_grid_dot(gint_handle *h, const double *V, const double *rho, double *out_dev, void *stream);

@@ -431,6 +431,11 @@ int gint_force(gint_handle *h, int precision, const double *D_blocks, const doub
 }
 
 int gint_run_batch(const gint_task *tasks, int ntasks, int precision, void *stream) {
+  return gint_run_batch_timed(tasks, ntasks, precision, stream, nullptr, nullptr);
+}
+
+int gint_run_batch_timed(const gint_task *tasks, int ntasks, int precision, void *stream, void *ev_start,
+                         void *ev_stop) {
   if (ntasks < 0 || (ntasks > 0 && !tasks)) return GINT_EINVAL;
   if (check_precision(precision)) return GINT_EINVAL;
   for (int i = 0; i < ntasks; ++i) {
@@ -442,7 +447,9 @@ int gint_run_batch(const gint_task *tasks, int ntasks, int precision, void *stre
   if (ntasks == 0) return GINT_OK;
   DeviceGuard guard(tasks[0].h->device);
   cudaStream_t st = (cudaStream_t)stream;
-  if (precision == GINT_F16X3 || precision == GINT_F16X1) return gint_tc_batch(tasks, ntasks, precision, st);
+  if (precision == GINT_F16X3 || precision == GINT_F16X1)
+    return gint_tc_batch(tasks, ntasks, precision, st, (cudaEvent_t)ev_start, (cudaEvent_t)ev_stop);
+  if (ev_start && cudaEventRecord((cudaEvent_t)ev_start, st) != cudaSuccess) return GINT_ECUDA;
   for (int i = 0; i < ntasks; ++i) {
     const gint_task &T = tasks[i];
     gint_handle *h = T.h;
@@ -464,6 +471,7 @@ int gint_run_batch(const gint_task *tasks, int ntasks, int precision, void *stre
       if (rc) return rc;
     }
   }
+  if (ev_stop && cudaEventRecord((cudaEvent_t)ev_stop, st) != cudaSuccess) return GINT_ECUDA;
   return GINT_OK;
 }
 

@@ -105,7 +105,8 @@ int gint_reduce_dot(gint_handle *h, const double *a, const double *b, long long 
 int gint_tc_rho(gint_handle *h, int precision, const double *D, double *rho, const double *V, double *F,
                 cudaStream_t st);
 int gint_tc_vlocal(gint_handle *h, int precision, const double *V, double *H, cudaStream_t st);
-int gint_tc_batch(const gint_task *tasks, int n, int precision, cudaStream_t st);
+int gint_tc_batch(const gint_task *tasks, int n, int precision, cudaStream_t st, cudaEvent_t ev0,
+                  cudaEvent_t ev1);
 int gint_tc_check_capacity(const gint_handle *h);
 int gint_tc_prepare(gint_handle *h);  // layouts and scratch of the tensor-core path (after neighbours)
 void gint_tc_free(gint_handle *h);

@@ -144,6 +144,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 32 bit x 8 columns.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // x = hi + lo with both parts float16 (hi = round(x), lo = round(x - hi)).
 __device__ __forceinline__ void split_h(float x, __half &hi, __half &lo) {
   hi = __float2half_rn(x);
@@ -976,13 +988,24 @@ __global__ void __launch_bounds__(kT, 1)
         float rp = 0.f;
         for (int a = q; a < na; a += 4) {
           const int pc = sh.s_pcol[a], po = sh.s_po[a];
+          // the atom's own columns only (an 8-column atom may end the accumulator: a 16-column
+          // load there would reach past the tensor-memory allocation)
           float y[GINT_MAX_ORB_ATOM], yc[16];
           for (int h = 0; h < po; h += 16) {
-            tmem_ld16(tmem + lane_base + pc + h, y + h);
-            if (split3 && corr_base) {
-              tmem_ld16(tmem + lane_base + corr_base + pc + h, yc);
+            if (po - h >= 16) {
+              tmem_ld16(tmem + lane_base + pc + h, y + h);
+              if (split3 && corr_base) {
+                tmem_ld16(tmem + lane_base + corr_base + pc + h, yc);
 #pragma unroll
-              for (int i = 0; i < 16; ++i) y[h + i] += yc[i];
+                for (int i = 0; i < 16; ++i) y[h + i] += yc[i];
+              }
+            } else {
+              tmem_ld8(tmem + lane_base + pc + h, y + h);
+              if (split3 && corr_base) {
+                tmem_ld8(tmem + lane_base + corr_base + pc + h, yc);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) y[h + i] += yc[i];
+              }
             }
           }
           for (int i = 0; i < po; ++i) y[i] *= inv;
@@ -1556,8 +1579,9 @@ static_assert(sizeof(GTabs) + sizeof(GTile) <= 32764 && sizeof(GTabs) + sizeof(G
                   sizeof(GPrep) <= 32764,
               "batch kernel parameters exceed the launch limit");
 
-// One launch group (at most kMaxBatch tasks, validated by the caller).
-static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st) {
+// One launch group (at most kMaxBatch tasks, validated by the caller).  ev0 / ev1 (may be NULL)
+// are recorded on the stream right before / after the brick kernel.
+static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
   gint_handle *h0 = tk[0].h;
   const GTabs &tabs = h0->geom;
   GPrep P{};
@@ -1669,8 +1693,10 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st) {
     auto kern = force ? k_tc_fused<true> : k_tc_fused<false>;
     int rc = set_smem(kern, smem);
     if (rc) return rc;
+    if (ev0) TC_CHECK(cudaEventRecord(ev0, st));
     kern<<<grid, kT, smem, st>>>(tabs, B, h0->zero_dev, h0->work_ctr);
     TC_CHECK(cudaGetLastError());
+    if (ev1) TC_CHECK(cudaEventRecord(ev1, st));
   }
   if (uppers > 0) {
     k_h_reduce<<<(unsigned)uppers, 192, 0, st>>>(tabs, R);
@@ -1679,7 +1705,7 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st) {
   return GINT_OK;
 }
 
-int gint_tc_batch(const gint_task *tasks, int n, int precision, cudaStream_t st) {
+int gint_tc_batch(const gint_task *tasks, int n, int precision, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
   if (n <= 0) return GINT_OK;
   const gint_handle *h0 = tasks[0].h;
   for (int i = 0; i < n; ++i) {
@@ -1696,7 +1722,9 @@ int gint_tc_batch(const gint_task *tasks, int n, int precision, cudaStream_t st)
   }
   const int split3 = precision == GINT_F16X3 ? 1 : 0;
   for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
-    int rc = run_group(tasks + i0, std::min(kMaxBatch, n - i0), split3, st);
+    const bool first = i0 == 0, last = i0 + kMaxBatch >= n;
+    int rc = run_group(tasks + i0, std::min(kMaxBatch, n - i0), split3, st, first ? ev0 : nullptr,
+                       last ? ev1 : nullptr);
     if (rc) return rc;
   }
   return GINT_OK;
@@ -1705,12 +1733,12 @@ int gint_tc_batch(const gint_task *tasks, int n, int precision, cudaStream_t st)
 int gint_tc_rho(gint_handle *h, int precision, const double *D, double *rho, const double *V, double *F,
                 cudaStream_t st) {
   const gint_task t{h, D, V, rho, nullptr, F};
-  return gint_tc_batch(&t, 1, precision, st);
+  return gint_tc_batch(&t, 1, precision, st, nullptr, nullptr);
 }
 
 int gint_tc_vlocal(gint_handle *h, int precision, const double *V, double *H, cudaStream_t st) {
   const gint_task t{h, nullptr, V, nullptr, H, nullptr};
-  return gint_tc_batch(&t, 1, precision, st);
+  return gint_tc_batch(&t, 1, precision, st, nullptr, nullptr);
 }
 
 extern "C" int gint_tc_selftest(int n, double *max_err) {

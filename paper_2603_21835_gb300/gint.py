@@ -73,12 +73,13 @@ _lib.gint_sync.argtypes = [_vp, _vp]
 _lib.gint_tc_selftest.argtypes = [_i, ctypes.POINTER(_d)]
 _lib.gint_grid_dot_noalloc.argtypes = [_vp, _vp, _ll, _d, _vp, _vp]
 _lib.gint_run_batch.argtypes = [ctypes.POINTER(_Task), _i, _i, _vp]
+_lib.gint_run_batch_timed.argtypes = [ctypes.POINTER(_Task), _i, _i, _vp, _vp, _vp]
 _lib.gint_memory.argtypes = [_vp, ctypes.POINTER(_ll)]
 
 C_ABI_SYMBOLS = ("gint_create", "gint_destroy", "gint_layout", "gint_pairs", "gint_stats", "gint_set_positions",
                  "gint_rho", "gint_vlocal", "gint_force", "gint_grid_dot", "gint_block_dot", "gint_weight",
                  "gint_strerror", "gint_sync", "gint_tc_selftest", "gint_grid_dot_noalloc", "gint_run_batch",
-                 "gint_memory")
+                 "gint_run_batch_timed", "gint_memory")
 
 
 def tc_selftest(n: int = 256) -> float:
@@ -120,15 +121,24 @@ class Task:
     F: Optional[torch.Tensor] = None     # out: forces [natoms, 3]
 
 
-def run_batch(tasks: Sequence[Task], precision: int = F16X3, stream=None) -> None:
+def run_batch(tasks: Sequence[Task], precision: int = F16X3, stream=None, kernel_events=None) -> None:
     """All tasks' bricks in one persistent launch (tensor-core precisions; up to 32 systems per
-    launch), asynchronous on `stream`."""
+    launch), asynchronous on `stream`.  kernel_events: optional (start, stop) torch.cuda.Event
+    pair recorded around the brick kernel(s) (they must have been recorded once before, so that
+    the CUDA events exist)."""
     arr = (_Task * max(len(tasks), 1))()
     for i, t in enumerate(tasks):
         g = t.g
         arr[i] = _Task(g._h, _dptr(t.D, numel=g.nblock), _dptr(t.V, numel=g.ngrid), _dptr(t.rho, numel=g.ngrid),
                        _dptr(t.H, numel=g.nblock), _dptr(t.F, numel=3 * g.natoms))
-    _check(_lib.gint_run_batch(arr, len(tasks), int(precision), _stream(stream)), "gint_run_batch")
+    if kernel_events is None:
+        _check(_lib.gint_run_batch(arr, len(tasks), int(precision), _stream(stream)), "gint_run_batch")
+    else:
+        e0, e1 = (ctypes.c_void_p(e.cuda_event) for e in kernel_events)
+        if not e0.value or not e1.value:
+            raise ValueError("kernel_events must have been recorded once (CUDA events are created lazily)")
+        _check(_lib.gint_run_batch_timed(arr, len(tasks), int(precision), _stream(stream), e0, e1),
+               "gint_run_batch_timed")
 
 
 class Gint:
@@ -225,10 +235,10 @@ class Gint:
 
     def run(self, D_blocks: Optional[torch.Tensor], V: Optional[torch.Tensor], precision: int = F16X3,
             rho: Optional[torch.Tensor] = None, H: Optional[torch.Tensor] = None, F: Optional[torch.Tensor] = None,
-            stream=None) -> None:
+            stream=None, kernel_events=None) -> None:
         """Several passes of this system in one call (with the tensor-core precisions the density
         or force bricks and the local-H bricks share one persistent launch)."""
-        run_batch([Task(self, D_blocks, V, rho, H, F)], precision, stream)
+        run_batch([Task(self, D_blocks, V, rho, H, F)], precision, stream, kernel_events)
 
     def grid_dot(self, V: Optional[torch.Tensor], rho: torch.Tensor, out: Optional[torch.Tensor] = None,
                  stream=None) -> torch.Tensor:

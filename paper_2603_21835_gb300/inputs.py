@@ -311,6 +311,14 @@ def h2o_workload(nmol: int, seed: int, box: float = 30.0, grid: Tuple[int, int, 
                  cscale: float = 0.25, dense_D: bool = True) -> Workload:
     """Rigid water molecules placed in a central sphere of a cubic vacuum box."""
     rng = np.random.default_rng(seed)
+    sysm = _h2o_system(rng, nmol, box, grid)
+    V = draw_V(rng, sysm.cell, grid)
+    C = draw_C(rng, sysm.norb, 2 * nmol * 4 // 2, cscale)
+    D = density_matrix(C) if dense_D else None
+    return Workload(system=sysm, V=V, C=C, D=D)
+
+
+def _h2o_system(rng: np.random.Generator, nmol: int, box: float, grid: Tuple[int, int, int]) -> System:
     spO, spH = o_species(), h_species()
     Rs = (3.0 * nmol / (4.0 * math.pi * 0.00495)) ** (1.0 / 3.0)
     centre = np.full(3, box / 2)
@@ -337,8 +345,44 @@ def h2o_workload(nmol: int, seed: int, box: float = 30.0, grid: Tuple[int, int, 
     cell = np.diag([box, box, box]).astype(np.float64)
     pos = np.asarray(pos)
     species = np.asarray(spec, dtype=np.int32)
-    sysm = System(cell=cell, pos=pos, species=species, sp=[spO, spH], grid=grid, name=f"h2o{nmol}")
-    V = draw_V(rng, cell, grid)
-    C = draw_C(rng, sysm.norb, 2 * nmol * 4 // 2, cscale)
-    D = density_matrix(C) if dense_D else None
-    return Workload(system=sysm, V=V, C=C, D=D)
+    return System(cell=cell, pos=pos, species=species, sp=[spO, spH], grid=grid, name=f"h2o{nmol}")
+
+
+# --------------------------------------------------------------------------------------
+# Serving mix: Si supercells of 8-216 atoms (48 grid points per cubic-cell edge) and water
+# clusters of 8-64 molecules in 30 Bohr vacuum boxes (144^3), on one species list
+# --------------------------------------------------------------------------------------
+SERVING_SI_CELLS = ((1, 1, 1), (2, 1, 1), (2, 2, 1), (2, 2, 2), (3, 2, 2), (3, 3, 2), (3, 3, 3))
+SERVING_H2O = (8, 16, 32, 64)
+OCCUPIED_PAIRS = {"Si": 2.0, "O": 3.0, "H": 0.5}  # valence electron pairs per atom
+
+
+def serving_library() -> List[Species]:
+    return [si_species(), o_species(), h_species()]
+
+
+def serving_pool(seed: int = 0) -> List[System]:
+    """The geometries of the serving mix (Si with N(0, 0.05) Bohr displacements)."""
+    lib = serving_library()
+    out: List[System] = []
+    for k, n in enumerate(SERVING_SI_CELLS):
+        cell, pos = si_supercell(n)
+        rng = np.random.default_rng(seed + 1000 + k)
+        pos = wrap_positions(cell, pos + rng.normal(0.0, 0.05, pos.shape))
+        grid = tuple(48 * x for x in n)
+        sysm = System(cell=cell, pos=pos, species=np.zeros(pos.shape[0], dtype=np.int32), sp=[lib[0]], grid=grid,
+                      name=f"si{pos.shape[0]}")
+        out.append(on_species(sysm, lib))
+    for nmol in SERVING_H2O:
+        sysm = _h2o_system(np.random.default_rng(seed + 2000 + nmol), nmol, 30.0, (144, 144, 144))
+        out.append(on_species(sysm, lib))
+    return out
+
+
+def serving_inputs(system: System, seed: int, cscale: float = 0.25) -> Tuple[np.ndarray, np.ndarray]:
+    """One request's inputs: V (20 periodic Gaussians) and coefficients C (norb x occupied pairs)."""
+    rng = np.random.default_rng(seed)
+    V = draw_V(rng, system.cell, system.grid)
+    nb = int(round(sum(OCCUPIED_PAIRS[system.sp[s].name] for s in system.species)))
+    C = draw_C(rng, system.norb, max(nb, 1), cscale)
+    return V, C

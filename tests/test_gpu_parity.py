@@ -223,3 +223,26 @@ def test_si512_sampled_parity(si512, torch_cuda, prec):
         k = g.block_index(*bl)
         blk = H[g.pair_off[k]:g.pair_off[k + 1]].reshape(ref.shape)
         assert np.abs(blk - ref).max() <= TOL[prec] * hmax, bl
+
+
+def test_water_cluster_with_eight_column_atoms(torch_cuda):
+    """24 water molecules in a 20 Bohr box, 96^3: O atoms take 16 padded columns, H atoms 8, so
+    some bricks end on an 8-column atom (six bricks here have padded width 256 with an H atom at
+    columns 248-255, the layout whose force epilogue must read exactly 8 columns)."""
+    torch = torch_cuda
+    from paper_2603_21835_gb300 import gint as G
+
+    w = inputs.h2o_workload(24, seed=3, box=20.0, grid=(96, 96, 96))
+    o = Oracle(w.system)
+    g = G.Gint(w.system)
+    Db = g.dense_to_blocks(w.D)
+    ref_rho, ref_H, ref_F = o.rho(w.D), o.vlocal(w.V), o.force(w.D, w.V)
+    for prec in ("fp64", "f16x3"):
+        rho, H, F, rho2 = _run(G, g, Db, w.V, G.PRECISIONS[prec], torch)
+        g.sync()
+        assert _rel(rho, ref_rho) <= TOL[prec], prec
+        assert _rel(rho2, ref_rho) <= TOL[prec], prec
+        assert _rel(g.blocks_to_dense(H), ref_H) <= TOL[prec], prec
+        ftol = FTOL_ABS[prec] if FTOL_ABS[prec] is not None else 1e-11 * np.abs(ref_F).max()
+        assert np.abs(F - ref_F).max() <= ftol, prec
+    g.close()

@@ -1,0 +1,145 @@
+"""Serving loop on the GPU: continuous batching of mixed systems under an HBM budget.
+
+Each request's result must be the same in the mix as alone (rho and H bitwise: one owner brick
+per grid point and a fixed-order H reduction; forces to float64 rounding, as their atomic
+accumulation order varies) and match the FP64 oracle at the F16x3 tolerances (1e-6 max-norm
+relative for rho and H, 1e-5 Ha/Bohr for forces).
+"""
+import threading
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2603_21835_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+LIB = [inputs.si_species(), inputs.o_species(), inputs.h_species()]
+
+
+def _rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max())
+
+
+def _variant(w, j):
+    """Request j's inputs: the workload's V and D rescaled (D stays symmetric positive)."""
+    return w.D * (1.0 + 0.05 * j), w.V * (1.0 + 0.1 * j)
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    from paper_2603_21835_gb300 import gint as G
+    from paper_2603_21835_gb300 import serve
+
+    ws = [inputs.config_workload("si8_g48"),
+          inputs.h2o_workload(4, seed=3, box=20.0, grid=(96, 96, 96)),
+          inputs.si_workload((2, 1, 1), (96, 48, 48), seed=5, disp_sigma=0.05, name="si16")]
+    systems = [inputs.on_species(w.system, LIB) for w in ws]
+    alone = [G.Gint(s) for s in systems]
+    return dict(torch=torch, G=G, serve=serve, ws=ws, systems=systems, alone=alone)
+
+
+def _alone_result(env, i, j):
+    torch, G = env["torch"], env["G"]
+    g, w = env["alone"][i], env["ws"][i]
+    D, V = _variant(w, j)
+    Dd = torch.from_numpy(g.dense_to_blocks(D)).cuda()
+    Vd = torch.from_numpy(np.ascontiguousarray(V.reshape(-1))).cuda()
+    rho = torch.empty(g.ngrid, dtype=torch.float64, device="cuda")
+    H = torch.empty(g.nblock, dtype=torch.float64, device="cuda")
+    F = torch.empty((g.natoms, 3), dtype=torch.float64, device="cuda")
+    g.run(Dd, Vd, G.F16X3, rho=rho, H=H, F=F)
+    torch.cuda.synchronize()
+    g.sync()
+    return rho.cpu().numpy(), H.cpu().numpy(), F.cpu().numpy()
+
+
+def _submit_stream(srv, sessions, env, plan, gap_ms, seed, nburst):
+    """Submits (session index, variant) pairs from a client thread: the first `nburst` while the
+    server holds launches (so they queue together), then one every Poisson gap."""
+    import torch
+
+    futs = [None] * len(plan)
+    rng = np.random.default_rng(seed)
+    ready = threading.Event()
+    data = []
+    for i, j in plan:
+        w, g = env["ws"][i], env["alone"][i]
+        D, V = _variant(w, j)
+        data.append((torch.from_numpy(g.dense_to_blocks(D)).pin_memory(),
+                     torch.from_numpy(np.ascontiguousarray(V.reshape(-1))).pin_memory()))
+
+    def client():
+        srv.pause()
+        for k, (i, _) in enumerate(plan):
+            if k == nburst:
+                srv.resume()
+            if k >= nburst:
+                ready.wait(rng.exponential(gap_ms) * 1e-3)
+            futs[k] = srv.submit(sessions[i], *data[k])
+        srv.resume()
+
+    th = threading.Thread(target=client)
+    th.start()
+    th.join()
+    return [f.result(timeout=120) for f in futs]
+
+
+def test_mix_equals_alone_and_oracle(env):
+    serve = env["serve"]
+    plan = [(i, j) for j in range(4) for i in range(3)]
+    with serve.Server(LIB, budget_bytes=8 << 30) as srv:
+        sessions = [srv.open(s) for s in env["systems"]]
+        results = _submit_stream(srv, sessions, env, plan, gap_ms=1.0, seed=1, nburst=6)
+        sizes = list(srv.batch_sizes)
+        assert not srv.errors
+    assert sizes[0] == 3  # the queued burst: one request of each system in one launch (FIFO)
+    for (i, j), r in zip(plan, results):
+        rho, H, F = _alone_result(env, i, j)
+        assert np.array_equal(r.rho.reshape(-1), rho), (i, j)
+        assert np.array_equal(r.H, H), (i, j)
+        assert np.abs(r.F - F).max() <= 1e-12 * max(1.0, np.abs(F).max()), (i, j)
+        assert r.latency_ms > 0
+    for i in range(3):
+        w, g = env["ws"][i], env["alone"][i]
+        o = Oracle(env["systems"][i])
+        r = results[plan.index((i, 0))]
+        assert _rel(r.rho, o.rho(w.D)) <= 1e-6
+        assert _rel(r.H, g.dense_to_blocks(o.vlocal(w.V))) <= 1e-6
+        assert np.abs(r.F - o.force(w.D, w.V)).max() <= 1e-5
+    lat = serve.percentiles([r.latency_ms for r in results])
+    assert lat["p50"] <= lat["p99"]
+
+
+def test_budget_forces_eviction_and_recreation(env):
+    serve = env["serve"]
+    hb = max(g.memory() for g in env["alone"])
+    rb = max(8 * (2 * g.nblock + 2 * g.ngrid + 3 * g.natoms) for g in env["alone"])
+    budget = hb + rb + 4096  # the largest handle with the largest request, little else
+    plan = [(0, 1), (2, 1), (1, 2), (0, 3), (2, 2), (1, 1)]
+    with serve.Server(LIB, budget_bytes=budget) as srv:
+        sessions = [srv.open(s) for s in env["systems"]]
+        srv.budget.peak = srv.budget.used  # creation in open() may exceed by one handle (documented)
+        results = _submit_stream(srv, sessions, env, plan, gap_ms=0.5, seed=2, nburst=3)
+        print("handle", hb, "request", rb, "budget", budget, "peak", srv.budget.peak, "creations", srv.creations,
+              "batches", srv.batch_sizes)
+        assert srv.budget.peak <= budget
+        assert srv.creations >= 2  # handles were evicted and re-created to stay within the budget
+        assert not srv.errors
+    for (i, j), r in zip(plan, results):
+        rho, H, F = _alone_result(env, i, j)
+        assert np.array_equal(r.rho.reshape(-1), rho) and np.array_equal(r.H, H), (i, j)
+        assert np.abs(r.F - F).max() <= 1e-12 * max(1.0, np.abs(F).max()), (i, j)
+
+
+def test_request_beyond_budget_is_rejected(env):
+    serve = env["serve"]
+    with serve.Server(LIB, budget_bytes=1 << 20) as srv:
+        s = srv.open(env["systems"][0])
+        w, g = env["ws"][0], env["alone"][0]
+        fut = srv.submit(s, g.dense_to_blocks(w.D), w.V)
+        with pytest.raises(MemoryError):
+            fut.result(timeout=60)
