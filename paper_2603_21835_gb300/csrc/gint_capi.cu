@@ -216,6 +216,7 @@ int gint_create(const gint_desc *d, gint_handle **out) {
       GS.rcut = std::max(GS.rcut, R.rc);
     }
     GS.rcut2 = GS.rcut * GS.rcut;
+    GS.rcut2f = (float)GS.rcut2;
     GS.porb = (GS.norb + 7) / 8 * 8;
     {
       int cnt[3] = {0, 0, 0};

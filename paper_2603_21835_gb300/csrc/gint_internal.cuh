@@ -30,7 +30,8 @@ struct GRadial {
 struct GSpecies {
   int nrad, rad0, norb, porb;  // porb: orbitals padded to a multiple of 8 (tensor-core layouts)
   int shape;                   // (ns, np, nd) code 1 + ns + 8 np + 64 nd when the radials are l-sorted and
-  int pad;                     // share one knot grid (same npts and dr); 0 otherwise
+                               // share one knot grid (same npts and dr); 0 otherwise
+  float rcut2f;                // rcut2 rounded to float32 (coarse support test of the float32 kernels)
   double rcut, rcut2;          // largest rc of the species and its square
 };
 #define GINT_SHAPE(ns, np, nd) (1 + (ns) + 8 * (np) + 64 * (nd))

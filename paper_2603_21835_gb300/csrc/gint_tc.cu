@@ -17,7 +17,7 @@
 // diagonal block halved, rho = 2 sum_k P_k Y_k where Y_k accumulates P_j D_jk over the chunks
 // j <= chunk(k) only, so chunk c's columns are final right after chunk c's MMA: the epilogue of
 // chunk c overlaps the MMA of chunk c+1 and the MMA work is halved.  Within a brick a producer
-// warp (bulk copies), one MMA thread and four epilogue warps run decoupled by mbarriers.
+// warp (bulk copies), one MMA thread and twelve epilogue warps run decoupled by mbarriers.
 // Force: full Y = P D (all chunks, all columns), then per atom 2 w V grad(phi) . Y.
 // Local H: K = grid points (chunks of 32), M = N = orbitals (128-row tiles, upper block
 // triangle); each brick writes its float32 slot-pair tiles to a scratch area and a per-pair
@@ -47,6 +47,7 @@ constexpr uint32_t kHSBO = 576;  // 4 core matrices of K per 8-row group
 constexpr long long kWaitNs = 2000000000LL;  // bounded mbarrier waits: 2 s
 constexpr unsigned char kNoSlot = 255;
 constexpr int kProducerWarp = 4, kMmaWarp = 5;
+constexpr int kEpiGroups = 3, kEpiWarps = 4 * kEpiGroups;  // density epilogue: warps 0-3, 6-13
 
 // ------------------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -70,11 +71,12 @@ __device__ __forceinline__ long long globaltimer() {
   return t;
 }
 // Bounded wait: false (and the timeout bit in *err) if the phase did not complete within kWaitNs.
+// try_wait itself suspends the thread until the phase completes or a short hardware time limit
+// passes, so the loop needs no sleep of its own (a sleep would delay the wake-up).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = globaltimer();
   while (!mbar_try_wait(bar, parity)) {
-    __nanosleep(32);
     if (globaltimer() - t0 > kWaitNs) {
       atomicOr(err, GINT_ERRBIT_TIMEOUT);
       return false;
@@ -92,6 +94,8 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// Named barrier 1 over the density epilogue warps (barrier 0 is __syncthreads).
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -363,7 +367,7 @@ __device__ __forceinline__ void add_image_fast(const GTabs &g, const float2 *__r
 }
 
 // ------------------------------------------------------------------------------ brick metadata
-constexpr int kMaxStages = 4;
+constexpr int kMaxStages = 6;
 constexpr int kMaxChunks = kNPMAX / kRC;
 struct BrickSh {
   uint64_t full[kMaxStages];  // density: B stage loaded (bulk-copy transactions)
@@ -380,7 +384,10 @@ struct BrickSh {
   unsigned char col2slot[kNPMAX];
   double fpart[kMAXA][3];
   float rpart[4][128];
-  float sc[4];  // scales
+  float rpartl[4][128];  // density epilogue: compensation terms of the groups' partial sums
+  float wv[128];   // w V at the brick's points (local H, force)
+  double ob[3];    // brick origin (Cartesian)
+  float sc[4];     // scales
 };
 
 __device__ __forceinline__ void split2(double v, float &hi, float &lo) {
@@ -411,9 +418,10 @@ __host__ __device__ __forceinline__ int place_slot(int cur, int po) {
 __device__ void load_brick(const GCell &g, const GTabs &tb, const GNbr &nb, const long long *__restrict__ tile_off,
                            long long b, BrickSh &sh) {
   const int t = threadIdx.x;
-  const int bk = (int)(b % g.nbk), bj = (int)((b / g.nbk) % g.nbj), bi = (int)(b / ((long long)g.nbk * g.nbj));
-  double ob[3];
-  grid_point(g, bi * GINT_BI, bj * GINT_BJ, bk * GINT_BK, ob);
+  if (t == 0) {  // brick origin, once per brick (float64 division is slow on this GPU)
+    const int bk = (int)(b % g.nbk), bj = (int)((b / g.nbk) % g.nbj), bi = (int)(b / ((long long)g.nbk * g.nbj));
+    grid_point(g, bi * GINT_BI, bj * GINT_BJ, bk * GINT_BK, sh.ob);
+  }
   const long long s0 = nb.b_at_off[b];
   const int na = (int)(nb.b_at_off[b + 1] - s0);
   const long long e_begin = nb.s_ent[s0], e_end = nb.s_ent[s0 + na];
@@ -427,10 +435,13 @@ __device__ void load_brick(const GCell &g, const GTabs &tb, const GNbr &nb, cons
     sh.s_e0[a] = (int)(nb.s_ent[s0 + a] - e_begin);
     sh.fpart[a][0] = sh.fpart[a][1] = sh.fpart[a][2] = 0.0;
   }
-  for (int e = t; e < nent; e += blockDim.x)
-    for (int c = 0; c < 3; ++c) split2(nb.e_shift[3 * (e_begin + e) + c] - ob[c], sh.e_hi[e][c], sh.e_lo[e][c]);
   for (int k = t; k < kNPMAX; k += blockDim.x) sh.col2slot[k] = kNoSlot;
   __syncthreads();
+  // entry positions relative to the brick origin (one (entry, axis) per thread; thread 0 is busy below)
+  for (int u = t - 1; u >= 0 && u < 3 * nent; u += blockDim.x - 1) {
+    const int e = u / 3, c = u - 3 * (u / 3);
+    split2(nb.e_shift[3 * (e_begin + e) + c] - sh.ob[c], sh.e_hi[e][c], sh.e_lo[e][c]);
+  }
   if (t == 0) {
     sh.na = na;
     sh.nent = nent;
@@ -498,7 +509,7 @@ __device__ __forceinline__ void slot_values(const GTabs &g, const float2 *__rest
   }
   if (!valid) return;
   const GSpecies &S = g.sp[sh.s_sp[a]];
-  const float rc2 = (float)S.rcut2;
+  const float rc2 = S.rcut2f;
   for (int e = sh.s_e0[a]; e < sh.s_e0[a + 1]; ++e) {
     float dh[3], dl[3];
     rel_disp_df(sh, P, e, dh, dl);
@@ -619,7 +630,7 @@ __device__ __noinline__ void job_P_generic(const GTabs &g, const float2 *__restr
     for (int e = sh.s_e0[a]; e < sh.s_e0[a + 1]; ++e) {
       float dh[3], dl[3];
       rel_disp_df(sh, point_df(sh, p), e, dh, dl);
-      if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < (float)S.rcut2)
+      if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < S.rcut2f)
         add_image_generic<false>(g, tab, S, dh, dl, v, nullptr);
     }
   }
@@ -648,7 +659,7 @@ __device__ __noinline__ void job_H_generic(const GTabs &g, const float2 *__restr
     for (int e = sh.s_e0[a]; e < sh.s_e0[a + 1]; ++e) {
       float dh[3], dl[3];
       rel_disp_df(sh, point_df(sh, pt), e, dh, dl);
-      if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < (float)S.rcut2)
+      if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < S.rcut2f)
         add_image_generic<false>(g, tab, S, dh, dl, v, nullptr);
     }
   }
@@ -675,7 +686,7 @@ __device__ __noinline__ void job_F_generic(const GTabs &g, const float2 *__restr
     for (int e = sh.s_e0[a]; e < sh.s_e0[a + 1]; ++e) {
       float dh[3], dl[3];
       rel_disp_df(sh, point_df(sh, p), e, dh, dl);
-      if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < (float)S.rcut2)
+      if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < S.rcut2f)
         add_image_generic<true>(g, tab, S, dh, dl, v, gv);
     }
   }
@@ -837,6 +848,10 @@ __global__ void __launch_bounds__(kT, 1)
       }
       cur = sidx;
     }
+    if (t < 128 && S.V && (hitem || FORCE)) {  // w V at the brick's points
+      int gi, gj, gk;
+      sh.wv[t] = brick_point(S.c, b, t, gi, gj, gk) ? (float)(S.c.w * S.V[grid_index(S.c, gi, gj, gk)]) : 0.f;
+    }
     load_brick(S.c, g, S.nb, S.tile_off, b, sh);  // ends with a barrier: sh.item may be replaced now
     if (t == 0) sh.item = atomicAdd(work, 1);
     const int na = sh.na, NP = sh.np;
@@ -944,9 +959,12 @@ __global__ void __launch_bounds__(kT, 1)
           }
         }
         __syncwarp();
-      } else if (warp < 4 && !FORCE) {
-        double racc = 0.0;
-        for (int c = 0; c < nch; ++c) {
+      } else if (!FORCE && warp < kEpiWarps + 2) {
+        // three groups of four warps (warps 0-3, 6-9, 10-13; each group covers the 128 lanes)
+        // take chunks round robin; compensated float32 sums (two-sum) per point and group
+        const int grp = warp < 4 ? 0 : (warp - 2) >> 2;
+        float rhi = 0.f, rlo = 0.f;
+        for (int c = grp; c < nch; c += kEpiGroups) {
           if (!mbar_wait(&sh.done[c], (dpar >> c) & 1u, S.err)) ok = false;
           tc_fence_after();
           // chunk c's columns are final: rho += P_k Y_k
@@ -971,9 +989,26 @@ __global__ void __launch_bounds__(kT, 1)
               part += (hf.x + lf.x) * y[hseg * 8 + 2 * e] + (hf.y + lf.y) * y[hseg * 8 + 2 * e + 1];
             }
           }
-          racc += (double)part;
+          float sum, err;
+          two_sum(rhi, part, sum, err);
+          rhi = sum;
+          rlo += err;
         }
-        if (valid && S.rho) S.rho[gidx] = racc * (2.0 / ((double)Sphi * (double)Sphi * (double)SD));
+        if (grp > 0) {
+          sh.rpart[grp][p] = rhi;
+          sh.rpartl[grp][p] = rlo;
+        }
+        epi_barrier();
+        if (grp == 0) {
+          for (int g2 = 1; g2 < kEpiGroups; ++g2) {
+            float sum, err;
+            two_sum(rhi, sh.rpart[g2][p], sum, err);
+            rhi = sum;
+            rlo += err + sh.rpartl[g2][p];
+          }
+          if (valid && S.rho)
+            S.rho[gidx] = ((double)rhi + (double)rlo) * (2.0 / ((double)Sphi * (double)Sphi * (double)SD));
+        }
       }
       // all MMAs of the brick are complete once the last chunk's barrier has flipped (in order)
       if (!mbar_wait(&sh.done[nch - 1], (dpar >> (nch - 1)) & 1u, S.err)) ok = false;
@@ -984,7 +1019,7 @@ __global__ void __launch_bounds__(kT, 1)
         // full Y: per atom, rho and force from recomputed phi and grad phi (unscaled float32)
         const float2 *tab = S.tab;
         const float inv = 1.f / (Sphi * SD);
-        const float wv = (valid && S.V) ? (float)(S.c.w * S.V[gidx]) : 0.f;
+        const float wv = (valid && S.V) ? sh.wv[p] : 0.f;
         float rp = 0.f;
         for (int a = q; a < na; a += 4) {
           const int pc = sh.s_pcol[a], po = sh.s_po[a];
@@ -1067,7 +1102,7 @@ __global__ void __launch_bounds__(kT, 1)
         const int pt = c * kHP + pp;
         int gi, gj, gk;
         const bool valid = brick_point(S.c, b, pt, gi, gj, gk);
-        const float wvSA = valid ? (float)(S.c.w * S.V[grid_index(S.c, gi, gj, gk)]) * SA : 0.f;
+        const float wvSA = valid ? sh.wv[pt] * SA : 0.f;
         for (int a = q; a < na; a += 16) {
           const int pc = sh.s_pcol[a];
           const int gend = (a == na - 1) ? NP : 0;
