@@ -54,9 +54,32 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=256, help="Poisson serving run (0: skip)")
-    ap.add_argument("--serve-load", type=float, default=0.6, help="arrival rate / measured burst capacity")
+    ap.add_argument("--serve-load", type=float, default=0.75, help="arrival rate x mean service time alone")
     ap.add_argument("--serve-budget-gb", type=float, default=32.0)
     return ap.parse_args()
+
+
+def profiled_traffic(workload: str, precision: str):
+    """DRAM bytes per launch of the brick kernel from a committed ncu summary under profiles/,
+    if one was taken on this workload and precision with the current kernel source; else None."""
+    import glob
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_2603_21835_gb300", "csrc", "gint_tc.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                parts = line.strip().split(": ", 1)
+                if len(parts) == 2 and parts[0] in ("workload", "precision", "kernel_source_sha256",
+                                                    "traffic_bytes_per_launch"):
+                    kv[parts[0]] = parts[1].strip()
+        if (kv.get("workload") == workload and kv.get("precision") == precision
+                and kv.get("kernel_source_sha256") == sha and "traffic_bytes_per_launch" in kv):
+            return int(kv["traffic_bytes_per_launch"]), os.path.relpath(path, ROOT)
+    return None, None
 
 
 def load_peaks():
@@ -185,7 +208,9 @@ TENSOR_PRECISIONS = ("f16x3", "f16x1")
 
 
 def run_serving(args, prec, dev):
-    """Continuous batching: a Poisson stream of rho + H + F requests over the serving mix."""
+    """Continuous batching: rho + H + F requests over the serving mix (Si supercells and water
+    clusters, half each), first one at a time (service times alone), then a Poisson stream at
+    args.serve_load / (mean service time alone), then all at once (burst)."""
     import torch
 
     from paper_2603_21835_gb300 import inputs, serve
@@ -196,8 +221,7 @@ def run_serving(args, prec, dev):
     try:
         sessions = [srv.open(s) for s in pool]
         nvar = 4
-        rng = np.random.default_rng(5)
-        choice = rng.integers(0, len(pool), args.serve_requests)
+        plan_idx = inputs.serving_requests(args.serve_requests, seed=1)
         cache = {}
 
         def req(i, k):
@@ -207,45 +231,51 @@ def run_serving(args, prec, dev):
                                  torch.from_numpy(np.ascontiguousarray(V.reshape(-1))).pin_memory())
             return cache[(i, k)]
 
-        plan = [(int(i), n % nvar) for n, i in enumerate(choice)]
+        plan = [(i, n % nvar) for n, i in enumerate(plan_idx)]
         for i, k in plan:
             req(i, k)
-        # warm-up and burst capacity: every geometry twice, submitted at once
-        burst = [(i, k) for k in range(2) for i in range(len(pool))]
-        for _ in range(2):
+        # service time of each geometry alone (after one warm-up request each)
+        alone = {}
+        for rep in range(2):
+            for i in range(len(pool)):
+                r = srv.submit(sessions[i], *req(i, 0)).result(timeout=300)
+                if rep == 1:
+                    alone[i] = r.latency_ms
+        mean_alone = float(np.mean([alone[i] for i, _ in plan]))
+        rate = args.serve_load / (mean_alone * 1e-3)
+
+        def run(gaps):
+            nb0 = len(srv.batch_sizes)
+            futs = []
             t0 = time.perf_counter()
-            futs = [srv.submit(sessions[i], *req(i, k)) for i, k in burst]
-            res = [f.result(timeout=300) for f in futs]
-            t_burst = max(r.done_t for r in res) - t0
-        capacity = len(burst) / t_burst
-        rate = args.serve_load * capacity
-        gaps = rng.exponential(1.0 / rate, len(plan))
-        nb0 = len(srv.batch_sizes)
-        futs = []
-        t0 = time.perf_counter()
-        due = t0
-        for (i, k), gap in zip(plan, gaps):
-            due += gap
-            while True:
-                dt = due - time.perf_counter()
-                if dt <= 0:
-                    break
-                time.sleep(min(dt, 0.002))
-            futs.append(srv.submit(sessions[i], *req(i, k)))
-        res = [f.result(timeout=300) for f in futs]
-        t_end = max(r.done_t for r in res)
-        lat = serve.percentiles([r.latency_ms for r in res])
-        pairs = sum(2.0 * sessions[i].W for i, _ in plan)
-        sizes = srv.batch_sizes[nb0:]
+            due = t0
+            for (i, k), gap in zip(plan, gaps):
+                due += gap
+                while True:
+                    dt = due - time.perf_counter()
+                    if dt <= 0:
+                        break
+                    time.sleep(min(dt, 0.002))
+                futs.append(srv.submit(sessions[i], *req(i, k)))
+            res = [f.result(timeout=600) for f in futs]
+            wall = max(r.done_t for r in res) - t0
+            lat = serve.percentiles([r.latency_ms for r in res])
+            sizes = srv.batch_sizes[nb0:]
+            pairs = sum(2.0 * sessions[i].W for i, _ in plan)
+            return {"p50_ms": lat["p50"], "p99_ms": lat["p99"], "mean_ms": lat["mean"], "max_ms": lat["max"],
+                    "throughput_req_s": len(plan) / wall, "throughput_gpt_pair_s": pairs / wall / 1e9,
+                    "batches": len(sizes), "mean_batch": float(np.mean(sizes)), "max_batch": int(max(sizes))}
+
+        poisson = run(np.random.default_rng(1).exponential(1.0 / rate, len(plan)))
+        burst = run(np.zeros(len(plan)))
         out = {
             "requests": len(plan), "outputs": "rho+H+F", "pool": [s.name for s in pool],
-            "arrivals": f"Poisson, rate = {args.serve_load:g} x burst capacity",
-            "rate_hz": rate, "burst_capacity_req_s": capacity,
-            "p50_ms": lat["p50"], "p99_ms": lat["p99"], "mean_ms": lat["mean"], "max_ms": lat["max"],
-            "throughput_req_s": len(plan) / (t_end - t0),
-            "throughput_gpt_pair_s": pairs / (t_end - t0) / 1e9,
+            "mix": "Si supercells and water clusters with probability 1/2 each (seed 1)",
+            "mean_service_alone_ms": mean_alone,
+            "arrivals": f"Poisson, rate = {args.serve_load:g} / mean service time alone",
+            "rate_hz": rate, "poisson": poisson, "burst": burst,
+            "p50_ms": poisson["p50_ms"], "p99_ms": poisson["p99_ms"],
             "throughput_note": "2W per request (rho + H pair updates); the force pass is extra work not counted",
-            "batches": len(sizes), "mean_batch": float(np.mean(sizes)), "max_batch": int(max(sizes)),
             "budget_bytes": srv.budget.budget, "peak_bytes": srv.budget.peak, "errors": len(srv.errors),
         }
     finally:
@@ -370,8 +400,9 @@ def main():
         peak = FP32_SIMT_TFLOPS_PER_GHZ * mhz / 1e3
         bound, punit, pdesc = "alu", "TFLOP/s", "fp32 SIMT 152 SMs x 128 lanes x 2 flops x sampled SM clock"
     achieved = flops / (tdom * 1e-3) / 1e12
+    traffic, traffic_src = profiled_traffic(args.workload, args.precision) if tensor else (None, None)
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": punit,
-                "frac": achieved / peak, "traffic": None, "peak_source": pdesc,
+                "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_source": pdesc,
                 "algorithmic_flops_per_launch": flops}
 
     # end to end through the public API: pinned host in, pinned host out, copies in the timed region

@@ -352,7 +352,7 @@ def _h2o_system(rng: np.random.Generator, nmol: int, box: float, grid: Tuple[int
 # Serving mix: Si supercells of 8-216 atoms (48 grid points per cubic-cell edge) and water
 # clusters of 8-64 molecules in 30 Bohr vacuum boxes (144^3), on one species list
 # --------------------------------------------------------------------------------------
-SERVING_SI_CELLS = ((1, 1, 1), (2, 1, 1), (2, 2, 1), (2, 2, 2), (3, 2, 2), (3, 3, 2), (3, 3, 3))
+SERVING_SI_CELLS = tuple((a, b, c) for a in range(1, 4) for b in range(a, 4) for c in range(b, 4))  # n1<=n2<=n3
 SERVING_H2O = (8, 16, 32, 64)
 OCCUPIED_PAIRS = {"Si": 2.0, "O": 3.0, "H": 0.5}  # valence electron pairs per atom
 
@@ -362,7 +362,9 @@ def serving_library() -> List[Species]:
 
 
 def serving_pool(seed: int = 0) -> List[System]:
-    """The geometries of the serving mix (Si with N(0, 0.05) Bohr displacements)."""
+    """The geometries of the serving mix: the ten Si supercells n1 x n2 x n3 with
+    1 <= n1 <= n2 <= n3 <= 3 (N(0, 0.05) Bohr displacements, grid 48 n_i), then the four water
+    clusters.  serving_kinds() tells which entries are Si and which are water."""
     lib = serving_library()
     out: List[System] = []
     for k, n in enumerate(SERVING_SI_CELLS):
@@ -377,6 +379,19 @@ def serving_pool(seed: int = 0) -> List[System]:
         sysm = _h2o_system(np.random.default_rng(seed + 2000 + nmol), nmol, 30.0, (144, 144, 144))
         out.append(on_species(sysm, lib))
     return out
+
+
+def serving_kinds() -> Tuple[List[int], List[int]]:
+    """Indices of serving_pool() entries: (Si supercells, water clusters)."""
+    ns = len(SERVING_SI_CELLS)
+    return list(range(ns)), list(range(ns, ns + len(SERVING_H2O)))
+
+
+def serving_requests(n: int, seed: int = 1) -> List[int]:
+    """Pool indices of n requests: Si or water with probability 1/2 each, then a uniform size."""
+    rng = np.random.default_rng(seed)
+    si, h2o = serving_kinds()
+    return [int(rng.choice(si)) if rng.random() < 0.5 else int(rng.choice(h2o)) for _ in range(n)]
 
 
 def serving_inputs(system: System, seed: int, cscale: float = 0.25) -> Tuple[np.ndarray, np.ndarray]:
