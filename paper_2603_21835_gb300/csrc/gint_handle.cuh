@@ -68,6 +68,8 @@ struct gint_handle {
   int *hu_pair = nullptr;                 // [nupper] pair index
   long long *hu_off = nullptr;            // [nupper + 1] CSR into hu_src
   long long *hu_src = nullptr;            // scratch element offset of each contribution
+  uint4 *plan = nullptr;                  // per-brick plan records (brick metadata, prefetched by the kernel)
+  long long *plan_off_dev = nullptr;      // [nbricks + 1] record offsets, 16-byte units
   long long tc_bytes = 0;                 // device bytes of the tensor-core workspace above
   double *red = nullptr;      // reduction partials
   double *scal = nullptr;     // device scalars

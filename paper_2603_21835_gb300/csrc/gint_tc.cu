@@ -369,6 +369,7 @@ __device__ __forceinline__ void add_image_fast(const GTabs &g, const float2 *__r
 // ------------------------------------------------------------------------------ brick metadata
 constexpr int kMaxStages = 6;
 constexpr int kMaxChunks = kNPMAX / kRC;
+constexpr int kPlanWords = 1536;  // prefetch buffer of a brick plan record (6 KB); larger records take the slow path
 struct BrickSh {
   uint64_t full[kMaxStages];  // density: B stage loaded (bulk-copy transactions)
   uint64_t done[kMaxChunks];  // density: MMAs of chunk c complete (one use per brick)
@@ -388,6 +389,9 @@ struct BrickSh {
   float wv[128];   // w V at the brick's points (local H, force)
   double ob[3];    // brick origin (Cartesian)
   float sc[4];     // scales
+  uint64_t plan_bar;  // the next item's plan record has landed in planbuf
+  int plan_pref;      // 1 if planbuf is being filled for the next item
+  alignas(16) uint32_t planbuf[kPlanWords];
 };
 
 __device__ __forceinline__ void split2(double v, float &hi, float &lo) {
@@ -470,6 +474,56 @@ __device__ void load_brick(const GCell &g, const GTabs &tb, const GNbr &nb, cons
   }
   for (int a = t; a < na; a += blockDim.x)
     for (int i = 0; i < sh.s_po[a]; ++i) sh.col2slot[sh.s_pcol[a] + i] = (unsigned char)a;
+  __syncthreads();
+}
+
+// Plan record of a brick (built once per geometry from load_brick's result, 32-bit words):
+//   [0] na  [1] nent  [2] np  [3] cumulative porb of all slots
+//   [4 + 8a + k], k = 0..7: atom, species, norb, porb, pcol, first entry, cumpo, rowst of slot a
+//   [4 + 8 na + 6 e + c]: entry e, c < 3: hi part of axis c, c >= 3: lo part (float bits)
+//   then na * na tile offsets, then np bytes of the column -> slot map; padded to 16 bytes.
+__host__ __device__ __forceinline__ long long plan_words(int na, int nent, int np) {
+  const long long w = 4 + 8LL * na + 6LL * nent + (long long)na * na + (np + 3) / 4;
+  return (w + 3) & ~3LL;
+}
+
+// Unpacks the record in sh.planbuf into the brick metadata (all threads; ends with a barrier).
+__device__ void unpack_plan(BrickSh &sh) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  const uint32_t *w = sh.planbuf;
+  const int na = (int)w[0], nent = (int)w[1], np = (int)w[2];
+  for (int a = t; a < na; a += nt) {
+    const uint32_t *q = w + 4 + 8 * a;
+    sh.s_atom[a] = (int)q[0];
+    sh.s_sp[a] = (int)q[1];
+    sh.s_no[a] = (int)q[2];
+    sh.s_po[a] = (int)q[3];
+    sh.s_pcol[a] = (int)q[4];
+    sh.s_e0[a] = (int)q[5];
+    sh.s_cumpo[a] = (int)q[6];
+    sh.s_rowst[a] = (int)q[7];
+    sh.fpart[a][0] = sh.fpart[a][1] = sh.fpart[a][2] = 0.0;
+  }
+  if (t == 0) {
+    sh.na = na;
+    sh.nent = nent;
+    sh.np = np;
+    sh.s_e0[na] = nent;
+    sh.s_cumpo[na] = (int)w[3];
+  }
+  const int eb = 4 + 8 * na;
+  for (int u = t; u < 6 * nent; u += nt) {
+    const int e = u / 6, c = u - 6 * e;
+    const float v = __uint_as_float(w[eb + u]);
+    if (c < 3)
+      sh.e_hi[e][c] = v;
+    else
+      sh.e_lo[e][c - 3] = v;
+  }
+  const int tb = eb + 6 * nent;
+  for (int i = t; i < na * na; i += nt) sh.s_tile[i] = (int)w[tb + i];
+  const unsigned char *cb = reinterpret_cast<const unsigned char *>(w + tb + na * na);
+  for (int k = t; k < kNPMAX; k += nt) sh.col2slot[k] = k < np ? cb[k] : kNoSlot;
   __syncthreads();
 }
 
@@ -721,6 +775,8 @@ struct GSys {
   const long long *hs_brick_off;
   float *hs;                                 // local-H scratch tiles
   unsigned *err;                             // device error word of the handle
+  const uint4 *plan;                         // brick plan records (NULL: metadata built per item)
+  const long long *plan_off;                 // [nbricks + 1] record offsets in 16-byte units
   long long nrho, nh;                        // items of each kind: 0 or nbricks
 };
 
@@ -767,14 +823,36 @@ __global__ void __launch_bounds__(kT, 1)
   const uint32_t bop = (uint32_t)np_max * kRC * 2;  // one B operand (hi or lo) of one stage
   const uint32_t hop = (uint32_t)(np_max / 8) * kHSBO;
   const uint32_t hstage = 4 * hop;
+  const long long total = B.start[B.nsys];
+  // thread 0: fetches the next item and starts the bulk copy of its plan record into planbuf
+  // (the buffer is free: the current item's record was unpacked before the last barrier)
+  auto next_item = [&]() {
+    const long long nx = atomicAdd(work, 1);
+    sh.item = (int)nx;
+    sh.plan_pref = 0;
+    if (nx >= total) return;
+    const int s2 = batch_sys(B, nx);
+    const GSys &S2 = B.sys[s2];
+    if (!S2.plan) return;
+    const long long l2 = nx - B.start[s2];
+    const long long b2 = l2 >= S2.nrho ? l2 - S2.nrho : l2;
+    const long long o0 = S2.plan_off[b2], o1 = S2.plan_off[b2 + 1];
+    const uint32_t bytes = (uint32_t)((o1 - o0) * 16);
+    if (bytes > 4u * kPlanWords) return;
+    fence_async_smem();  // earlier generic reads of planbuf before the asynchronous write
+    mbar_arrive_tx(&sh.plan_bar, bytes);
+    bulk_g2s(sh.planbuf, S2.plan + o0, bytes, &sh.plan_bar);
+    sh.plan_pref = 1;
+  };
   if (t == 0) {
     for (int s = 0; s < kMaxStages; ++s) mbar_init(&sh.full[s], 1);
     for (int c = 0; c < kMaxChunks; ++c) mbar_init(&sh.done[c], 1);
     mbar_init(&sh.hdone[0], 1);
     mbar_init(&sh.hdone[1], 1);
+    mbar_init(&sh.plan_bar, 1);
     fence_mbar_init();
     sh.abort = 0;
-    sh.item = atomicAdd(work, 1);
+    next_item();
   }
   if (warp == 0) {
     tmem_alloc(&sh.tmem, 512);
@@ -784,7 +862,7 @@ __global__ void __launch_bounds__(kT, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sh.tmem;
-  const long long total = B.start[B.nsys];
+  uint32_t pphase = 0;  // plan records consumed by this CTA (phase parity of plan_bar)
   uint32_t G = 0;     // density chunks issued by this CTA (B-stage ring bookkeeping)
   uint32_t dpar = 0;  // bit c: phase parity of done[c] (used once per density brick that has a chunk c)
   uint32_t GH = 0;    // local-H stages issued by this CTA
@@ -833,7 +911,11 @@ __global__ void __launch_bounds__(kT, 1)
   for (;;) {
     __syncthreads();
     const long long it = sh.item;
-    if (it >= total || sh.abort) break;
+    const int pref = sh.plan_pref;
+    if (it >= total || sh.abort) {
+      if (pref) mbar_wait(&sh.plan_bar, pphase & 1u, B.sys[0].err);  // no copy may be in flight at exit
+      break;
+    }
     const int sidx = batch_sys(B, it);
     const GSys &S = B.sys[sidx];
     const long long local = it - B.start[sidx];
@@ -852,8 +934,14 @@ __global__ void __launch_bounds__(kT, 1)
       int gi, gj, gk;
       sh.wv[t] = brick_point(S.c, b, t, gi, gj, gk) ? (float)(S.c.w * S.V[grid_index(S.c, gi, gj, gk)]) : 0.f;
     }
-    load_brick(S.c, g, S.nb, S.tile_off, b, sh);  // ends with a barrier: sh.item may be replaced now
-    if (t == 0) sh.item = atomicAdd(work, 1);
+    if (pref) {  // prefetched plan record (the common case)
+      if (!mbar_wait(&sh.plan_bar, pphase & 1u, S.err)) ok = false;
+      ++pphase;
+      unpack_plan(sh);  // ends with a barrier
+    } else {
+      load_brick(S.c, g, S.nb, S.tile_off, b, sh);  // ends with a barrier
+    }
+    if (t == 0) next_item();  // every thread has read sh.item and sh.plan_pref
     const int na = sh.na, NP = sh.np;
     const float Sphi = sh.sc[0];
     if (!hitem) {
@@ -1377,6 +1465,59 @@ __global__ void k_build_tiles(const __grid_constant__ GTabs g, const __grid_cons
   }
 }
 
+// One CTA per brick: the brick's metadata exactly as the brick kernel's slow path builds it,
+// serialised into its plan record (see plan_words).  Record capacity mismatch: index error bit.
+__global__ void __launch_bounds__(128) k_build_plans(const __grid_constant__ GTabs g, GCell c, GNbr nb,
+                                                     const long long *__restrict__ tile_off,
+                                                     const long long *__restrict__ plan_off, uint32_t *plan,
+                                                     unsigned *err) {
+  __shared__ BrickSh sh;
+  const long long b = blockIdx.x;
+  const int t = threadIdx.x;
+  load_brick(c, g, nb, tile_off, b, sh);
+  const int na = sh.na, nent = sh.nent, np = sh.np;
+  const long long cap = (plan_off[b + 1] - plan_off[b]) * 4;
+  if (plan_words(na, nent, np) > cap) {
+    if (t == 0) atomicOr(err, GINT_ERRBIT_INDEX);
+    return;
+  }
+  uint32_t *w = plan + plan_off[b] * 4;
+  if (t == 0) {
+    w[0] = (uint32_t)na;
+    w[1] = (uint32_t)nent;
+    w[2] = (uint32_t)np;
+    w[3] = (uint32_t)sh.s_cumpo[na];
+  }
+  for (int a = t; a < na; a += blockDim.x) {
+    uint32_t *q = w + 4 + 8 * a;
+    q[0] = (uint32_t)sh.s_atom[a];
+    q[1] = (uint32_t)sh.s_sp[a];
+    q[2] = (uint32_t)sh.s_no[a];
+    q[3] = (uint32_t)sh.s_po[a];
+    q[4] = (uint32_t)sh.s_pcol[a];
+    q[5] = (uint32_t)sh.s_e0[a];
+    q[6] = (uint32_t)sh.s_cumpo[a];
+    q[7] = (uint32_t)sh.s_rowst[a];
+  }
+  const int eb = 4 + 8 * na;
+  for (int u = t; u < 6 * nent; u += blockDim.x) {
+    const int e = u / 6, k = u - 6 * e;
+    w[eb + u] = __float_as_uint(k < 3 ? sh.e_hi[e][k] : sh.e_lo[e][k - 3]);
+  }
+  const int tb = eb + 6 * nent;
+  for (int i = t; i < na * na; i += blockDim.x) w[tb + i] = (uint32_t)sh.s_tile[i];
+  // column -> slot bytes, packed four per word, zero padded to the record end
+  const long long cw0 = tb + (long long)na * na;
+  for (long long i = cw0 + t; i < cap; i += blockDim.x) {
+    uint32_t v = 0;
+    for (int k = 0; k < 4; ++k) {
+      const long long col = 4 * (i - cw0) + k;
+      if (col < np) v |= (uint32_t)sh.col2slot[col] << (8 * k);
+    }
+    w[i] = v;
+  }
+}
+
 // ------------------------------------------------------------------------------ self-test
 // One f16 MMA per operand layout on integer data; err_out[0] = max |D - exact|.
 __global__ void __launch_bounds__(128, 1) k_tc_selftest(int N, float *err_out, unsigned *status) {
@@ -1463,6 +1604,8 @@ void dfree(T *&p) {
 
 void gint_tc_free(gint_handle *h) {
   h->tc_bytes = 0;
+  dfree(h->plan);
+  dfree(h->plan_off_dev);
   dfree(h->Dt_hi);
   dfree(h->Dt_lo);
   dfree(h->Dt_hi2);
@@ -1521,6 +1664,9 @@ int gint_tc_prepare(gint_handle *h) {
     return (it != e && *it == J) ? (int)(it - h->pair_col.begin()) : -1;
   };
   std::vector<int> no;  // padded orbital counts (porb) of the brick's slots
+  std::vector<long long> ent_off(nb + 1);
+  TC_CHECK(cudaMemcpy(ent_off.data(), h->b_ent_off, (nb + 1) * sizeof(long long), cudaMemcpyDeviceToHost));
+  std::vector<long long> plan_off(nb + 1, 0);  // plan records, 16-byte units
   // pass 1: sizes and counts
   for (long long b = 0; b < nb; ++b) {
     const long long s0 = at_off[b], s1 = at_off[b + 1];
@@ -1534,6 +1680,7 @@ int gint_tc_prepare(gint_handle *h) {
       cum += S.porb;
     }
     npmax = std::max(npmax, (cur + 15) & ~15);
+    plan_off[b + 1] = plan_off[b] + plan_words((int)(s1 - s0), (int)(ent_off[b + 1] - ent_off[b]), (cur + 15) & ~15) / 4;
     long long tot = 0, rest = cum;
     for (long long a = 0; a < s1 - s0; ++a) {
       tot += (long long)no[a] * rest;
@@ -1599,6 +1746,25 @@ int gint_tc_prepare(gint_handle *h) {
     TC_CHECK(cudaMemcpy(h->hu_pair, upair.data(), upair.size() * sizeof(int), cudaMemcpyHostToDevice));
   TC_CHECK(cudaMemcpy(h->hu_off, uoff.data(), uoff.size() * sizeof(long long), cudaMemcpyHostToDevice));
   TC_CHECK(cudaMemcpy(h->hu_src, src.data(), src.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  // brick plan records, built on the device by the slow-path metadata code itself
+  if (cudaMalloc(&h->plan_off_dev, (nb + 1) * sizeof(long long)) != cudaSuccess ||
+      cudaMalloc(&h->plan, std::max<long long>(plan_off[nb], 1) * 16) != cudaSuccess) {
+    cudaGetLastError();
+    return GINT_ENOMEM;
+  }
+  h->tc_bytes += (nb + 1) * (long long)sizeof(long long) + std::max<long long>(plan_off[nb], 1) * 16;
+  TC_CHECK(cudaMemcpy(h->plan_off_dev, plan_off.data(), (nb + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+  // (bricks beyond the kernels' capacity get no records: compute calls report GINT_ECAPACITY)
+  if (nb > 0 && h->max_brick_atoms <= kMAXA && h->max_brick_ent <= kMAXE && h->max_brick_porb <= kNPMAX) {
+    TC_CHECK(cudaMemset(h->err_word, 0, sizeof(unsigned)));
+    k_build_plans<<<(unsigned)nb, 128>>>(h->geom, static_cast<const GCell &>(h->geom), h->nbr(), h->tile_off_dev,
+                                         h->plan_off_dev, reinterpret_cast<uint32_t *>(h->plan), h->err_word);
+    TC_CHECK(cudaGetLastError());
+    TC_CHECK(cudaDeviceSynchronize());
+    unsigned err = 0;
+    TC_CHECK(cudaMemcpy(&err, h->err_word, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (err) return GINT_EDEVICE;
+  }
   return GINT_OK;
 }
 
@@ -1679,6 +1845,8 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
     S.hs_brick_off = h->hs_brick_off;
     S.hs = h->hs;
     S.err = h->err_word;
+    S.plan = h->plan;
+    S.plan_off = h->plan_off_dev;
     S.nrho = dens ? h->geom.nbricks : 0;
     S.nh = loc ? h->geom.nbricks : 0;
     B.start[i] = items;
