@@ -10,14 +10,17 @@
 //
 // Layout: the orbitals of each atom occupy porb = roundup(norb, 8) columns of the brick's
 // orbital space (zero padded), no atom crosses a multiple of 128 columns, NP = padded total.
-// D is pre-tiled per atom pair into float16 (hi, lo) 128-byte core matrices, so a B operand
-// row group of 8 rows x 8 columns is one bulk (TMA) copy from global memory.
+// D is pre-tiled per atom pair into float16 (hi, lo) 128-byte core matrices, stored
+// column-atom-major, so the B operand of a chunk that is one 16-column atom arrives in a few bulk
+// (TMA) copies: one per run of row atoms that are adjacent in the brick and in the tile store.
 //
 // Density (D symmetric): columns are streamed in chunks of 16.  With the chunk's own
 // diagonal block halved, rho = 2 sum_k P_k Y_k where Y_k accumulates P_j D_jk over the chunks
 // j <= chunk(k) only, so chunk c's columns are final right after chunk c's MMA: the epilogue of
-// chunk c overlaps the MMA of chunk c+1 and the MMA work is halved.  Within a brick a producer
-// warp (bulk copies), one MMA thread and twelve epilogue warps run decoupled by mbarriers.
+// chunk c overlaps the MMA of chunk c+1 and the MMA work is halved.  Within a brick the first
+// stages arrive by bulk copies during the orbital evaluation; then every warp but the MMA warp
+// loads the chunk whose stage has just been freed, one MMA thread issues, and twelve epilogue
+// warps drain finished chunks, all decoupled by mbarriers.
 // Force: full Y = P D (all chunks, all columns), then per atom 2 w V grad(phi) . Y.
 // Local H: K = grid points (chunks of 32), M = N = orbitals (128-row tiles, upper block
 // triangle); each brick writes its float32 slot-pair tiles to a scratch area and a per-pair
@@ -46,8 +49,9 @@ constexpr uint32_t kHLBO = 144;  // local-H operands: padded K-direction core-ma
 constexpr uint32_t kHSBO = 576;  // 4 core matrices of K per 8-row group
 constexpr long long kWaitNs = 2000000000LL;  // bounded mbarrier waits: 2 s
 constexpr unsigned char kNoSlot = 255;
-constexpr int kProducerWarp = 4, kMmaWarp = 5;
+constexpr int kProducerWarp = 4, kMmaWarp = 5;  // producer: bulk-copy prefetch of the first stages
 constexpr int kEpiGroups = 3, kEpiWarps = 4 * kEpiGroups;  // density epilogue: warps 0-3, 6-13
+constexpr int kLoaderWarps = 15;                           // density chunk loads: every warp but the MMA warp
 
 // ------------------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -84,6 +88,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsign
   }
   return true;
 }
+__device__ __forceinline__ void mbar_arrive_cnt(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) { mbar_arrive_cnt(bar, 1u); }
 __device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
@@ -845,7 +853,7 @@ __global__ void __launch_bounds__(kT, 1)
     sh.plan_pref = 1;
   };
   if (t == 0) {
-    for (int s = 0; s < kMaxStages; ++s) mbar_init(&sh.full[s], 1);
+    for (int s = 0; s < kMaxStages; ++s) mbar_init(&sh.full[s], kLoaderWarps);
     for (int c = 0; c < kMaxChunks; ++c) mbar_init(&sh.done[c], 1);
     mbar_init(&sh.hdone[0], 1);
     mbar_init(&sh.hdone[1], 1);
@@ -872,40 +880,109 @@ __global__ void __launch_bounds__(kT, 1)
   auto issue_copies = [&](const GSys &S, int c, int s, int NP, int na) {
     const int rowbase = FORCE ? 0 : c * kRC;
     const int ngroups = (NP - rowbase) >> 3;
-    if (lane == 0) mbar_arrive_tx(&sh.full[s], (uint32_t)ngroups * 2 * 256);
+    if (lane == 0) {  // one arrival with the transaction count stands for the loader warps' arrivals
+      mbar_arrive_tx(&sh.full[s], (uint32_t)ngroups * 2 * 256);
+      mbar_arrive_cnt(&sh.full[s], kLoaderWarps - 1);
+    }
     __syncwarp();
     unsigned char *Bh = B0 + s * 2 * bop, *Bl = Bh + bop;
-    // a chunk that is exactly one 16-column atom a: the 16 x 16 tile (b, a) of a 16-row atom b
-    // is 512 contiguous bytes in global and in shared memory (rows gr, gr+1; both segments)
     const int ca = sh.col2slot[c * kRC];
-    const bool chunk16 = ca != kNoSlot && sh.s_po[ca] == 16 && sh.s_pcol[ca] == c * kRC;
+    if (ca != kNoSlot && sh.s_po[ca] == 16 && sh.s_pcol[ca] == c * kRC) {
+      // the chunk is one 16-column atom: a row group of the stage (256 bytes: segment-major 8 x 8
+      // blocks) is laid out like a row group of a 16-column tile, so whole tiles copy as they are,
+      // and slots that are adjacent in the brick's rows and in the column-atom-major tile store
+      // form one copy.  Gap rows and absent tiles are zero-filled per row group.
+      // one lane per slot (windows of 32 slots): a slot continues the previous slot's run if
+      // both have present, non-diagonal tiles that are adjacent in rows and in the tile store
+      auto zero_rows = [&](int r0, int r1) {
+        for (int r = r0; r < r1; r += 8) {
+          bulk_g2s(Bh + (r - rowbase) * 32, zero, 256, &sh.full[s]);
+          bulk_g2s(Bl + (r - rowbase) * 32, zero, 256, &sh.full[s]);
+        }
+      };
+      for (int base = 0; base < na; base += 32) {
+        const int bs = base + lane;
+        const bool in = bs < na && sh.s_pcol[bs] >= rowbase;
+        const int pc = in ? sh.s_pcol[bs] : 0, po = in ? sh.s_po[bs] : 0;
+        const int tile = in ? sh.s_tile[bs * na + ca] : -1;
+        const bool diag = !FORCE && bs == ca;
+        const bool pin = in && bs > 0 && sh.s_pcol[bs - 1] >= rowbase;  // previous slot in the chunk rows
+        const int ppc = pin ? sh.s_pcol[bs - 1] : 0, ppo = pin ? sh.s_po[bs - 1] : 0;
+        const int ptile = pin ? sh.s_tile[(bs - 1) * na + ca] : -1;
+        const bool pdiag = !FORCE && bs - 1 == ca;
+        const bool run_ok = in && tile >= 0 && !diag;
+        const bool cont = run_ok && lane > 0 && pin && ptile >= 0 && !pdiag && ppc + ppo == pc &&
+                          (long long)ptile + (long long)ppo * 16 == (long long)tile;
+        const unsigned brk = __ballot_sync(0xffffffffu, !cont);  // run boundaries (and non-slots)
+        const int endrow = pc + po;
+        if (in) {
+          const int gap0 = pin ? ppc + ppo : rowbase;  // rows of no slot in front of this one
+          if (pc > gap0) zero_rows(gap0, pc);
+          if (bs == na - 1 && endrow < NP) zero_rows(endrow, NP);  // tail rows
+          if (tile < 0) {
+            zero_rows(pc, endrow);
+          } else if (diag) {  // the chunk's own block: halved tiles
+            bulk_g2s(Bh + (pc - rowbase) * 32, S.Dhi2 + tile, (uint32_t)po * 32, &sh.full[s]);
+            bulk_g2s(Bl + (pc - rowbase) * 32, S.Dlo2 + tile, (uint32_t)po * 32, &sh.full[s]);
+          }
+        }
+        // the last slot of a run ends where the next boundary starts
+        const unsigned later = lane < 31 ? (brk >> (lane + 1)) : 0u;
+        const int last = later ? lane + __ffs(later) - 1 : 31;
+        const int run_end = __shfl_sync(0xffffffffu, endrow, last);
+        if (run_ok && !cont) {
+          const uint32_t bytes = (uint32_t)(run_end - pc) * 32;
+          bulk_g2s(Bh + (pc - rowbase) * 32, S.Dhi + tile, bytes, &sh.full[s]);
+          bulk_g2s(Bl + (pc - rowbase) * 32, S.Dlo + tile, bytes, &sh.full[s]);
+        }
+      }
+      __syncwarp();
+      return;
+    }
+    // general chunk (8-column atoms): one copy per row group and column segment
     for (int u = lane; u < ngroups * 2; u += 32) {
       const int gr = u >> 1, sg = u & 1;
       const int k0 = rowbase + 8 * gr, j0 = c * kRC + 8 * sg;
       const int bs = sh.col2slot[k0], as = sh.col2slot[j0];
-      const int kl0 = bs != kNoSlot ? k0 - sh.s_pcol[bs] : 0;
-      const bool merged = chunk16 && bs != kNoSlot && sh.s_po[bs] == 16 && (FORCE || gr - kl0 / 8 != 1);
-      if (merged && (kl0 != 0 || sg != 0)) continue;  // carried by the row group's first unit
       long long src = -1;
       if (bs != kNoSlot && as != kNoSlot) {
         const int tile = sh.s_tile[bs * na + as];
+        const int kl0 = k0 - sh.s_pcol[bs];
         if (tile >= 0)
           src = (long long)tile + (long long)((kl0 >> 3) * (sh.s_po[as] >> 3) + ((j0 - sh.s_pcol[as]) >> 3)) * 64;
       }
       const bool diag = !FORCE && gr < 2;
-      const __half *sh_hi = src < 0 ? zero : (diag ? S.Dhi2 : S.Dhi) + src;
-      const __half *sh_lo = src < 0 ? zero : (diag ? S.Dlo2 : S.Dlo) + src;
-      const uint32_t bytes = merged ? 512u : 128u;
-      const bool zsrc = src < 0;
-      if (zsrc && merged) {
-        for (int z = 0; z < 4; ++z) {
-          bulk_g2s(Bh + gr * 256 + z * 128, zero, 128, &sh.full[s]);
-          bulk_g2s(Bl + gr * 256 + z * 128, zero, 128, &sh.full[s]);
+      bulk_g2s(Bh + gr * 256 + sg * 128, src < 0 ? zero : (diag ? S.Dhi2 : S.Dhi) + src, 128u, &sh.full[s]);
+      bulk_g2s(Bl + gr * 256 + sg * 128, src < 0 ? zero : (diag ? S.Dlo2 : S.Dlo) + src, 128u, &sh.full[s]);
+    }
+  };
+  // chunk c's B panel into stage s by the loader threads (lt = 0 .. 32 kLoaderWarps - 1): 16-byte
+  // pieces through registers, rows on consecutive threads (eight threads read one core matrix)
+  auto load_chunk = [&](const GSys &S, int c, int s, int NP, int na, int lt) {
+    const int rowbase = FORCE ? 0 : c * kRC;
+    const int nrows = NP - rowbase;
+    unsigned char *Bh = B0 + s * 2 * bop;
+#pragma unroll 2
+    for (int u = lt; u < 4 * nrows; u += kLoaderWarps * 32) {
+      const int seg = (u >= nrows) + (u >= 2 * nrows) + (u >= 3 * nrows);  // 2 h + column segment
+      const int rr = u - seg * nrows, r = rowbase + rr;
+      const int h = seg >> 1, sg = seg & 1;
+      const int j0 = c * kRC + 8 * sg;
+      const int bs = sh.col2slot[r], as = sh.col2slot[j0];
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (bs != kNoSlot && as != kNoSlot) {
+        const int tile = sh.s_tile[bs * na + as];
+        if (tile >= 0) {
+          const int kl = r - sh.s_pcol[bs];
+          const long long src = (long long)tile +
+                                (long long)((kl >> 3) * (sh.s_po[as] >> 3) + ((j0 - sh.s_pcol[as]) >> 3)) * 64 +
+                                (kl & 7) * 8;
+          const bool diag = !FORCE && rr < kRC;
+          const __half *base = h ? (diag ? S.Dlo2 : S.Dlo) : (diag ? S.Dhi2 : S.Dhi);
+          v = __ldg(reinterpret_cast<const uint4 *>(base + src));
         }
-      } else {
-        bulk_g2s(Bh + gr * 256 + sg * 128, sh_hi, bytes, &sh.full[s]);
-        bulk_g2s(Bl + gr * 256 + sg * 128, sh_lo, bytes, &sh.full[s]);
       }
+      *reinterpret_cast<uint4 *>(Bh + h * bop + (rr >> 3) * 256 + sg * 128 + (rr & 7) * 16) = v;
     }
   };
   for (;;) {
@@ -1013,14 +1090,7 @@ __global__ void __launch_bounds__(kT, 1)
       __syncthreads();
       // ---- phase B: chunks of 16 columns, producer warp / MMA thread / epilogue warps
       const uint32_t corr_base = (NP <= 256) ? 256u : 0u;  // separate correction accumulator if it fits
-      if (warp == kProducerWarp) {
-        for (int c = nstages; c < nch; ++c) {
-          // stage (G + c) % nstages was last read by chunk c - nstages of this brick
-          if (lane == 0 && !mbar_wait(&sh.done[c - nstages], (dpar >> (c - nstages)) & 1u, S.err)) ok = false;
-          __syncwarp();
-          issue_copies(S, c, (G + c) % nstages, NP, na);
-        }
-      } else if (warp == kMmaWarp) {
+      if (warp == kMmaWarp) {
         if (lane == 0) {
           for (int c = 0; c < nch; ++c) {
             const uint32_t Gc = G + c, s = Gc % nstages;
@@ -1047,14 +1117,27 @@ __global__ void __launch_bounds__(kT, 1)
           }
         }
         __syncwarp();
-      } else if (!FORCE && warp < kEpiWarps + 2) {
-        // three groups of four warps (warps 0-3, 6-9, 10-13; each group covers the 128 lanes)
-        // take chunks round robin; compensated float32 sums (two-sum) per point and group
-        const int grp = warp < 4 ? 0 : (warp - 2) >> 2;
+      } else {
+        // every other warp: once chunk c's MMAs are done its stage is free, load chunk c + nstages
+        // into it; then the density epilogue groups (warps 0-3, 6-9, 10-13, each covering the 128
+        // lanes) drain their chunks round robin (compensated float32 sums per point and group)
+        const int lt = (warp < kMmaWarp ? warp : warp - 1) * 32 + lane;
+        const int grp = FORCE ? -1 : warp < 4 ? 0 : (warp >= 6 && warp < 6 + 4 * (kEpiGroups - 1)) ? (warp - 2) >> 2 : -1;
         float rhi = 0.f, rlo = 0.f;
-        for (int c = grp; c < nch; c += kEpiGroups) {
+        for (int c = 0; c < nch; ++c) {
+          const int cl = c + nstages;
+          const bool mine = grp >= 0 && c % kEpiGroups == grp;
+          if (cl >= nch && !mine) continue;
           if (!mbar_wait(&sh.done[c], (dpar >> c) & 1u, S.err)) ok = false;
           tc_fence_after();
+          if (cl < nch) {
+            const int sl = (G + cl) % nstages;
+            load_chunk(S, cl, sl, NP, na, lt);
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.full[sl]);
+          }
+          if (!mine) continue;
           // chunk c's columns are final: rho += P_k Y_k
           const int k0 = c * kRC;
           float y[16], yc[16];
@@ -1086,7 +1169,7 @@ __global__ void __launch_bounds__(kT, 1)
           sh.rpart[grp][p] = rhi;
           sh.rpartl[grp][p] = rlo;
         }
-        epi_barrier();
+        if (grp >= 0) epi_barrier();
         if (grp == 0) {
           for (int g2 = 1; g2 < kEpiGroups; ++g2) {
             float sum, err;
@@ -1628,13 +1711,26 @@ int gint_tc_prepare(gint_handle *h) {
   const GGeom &g = h->geom;
   const int na_tot = g.natoms;
   // D tiles: roundup(norb(I), 8) x porb(J) per pair
+  // D tiles: porb(I) x porb(J) per pair, stored column-atom-major (for each J its row atoms I in
+  // ascending order), so that a brick's consecutive row atoms of one chunk are one copy
+  auto find_pair = [&](int I, int J) -> int {
+    auto b = h->pair_col.begin() + h->pair_row[I], e = h->pair_col.begin() + h->pair_row[I + 1];
+    auto it = std::lower_bound(b, e, J);
+    return (it != e && *it == J) ? (int)(it - h->pair_col.begin()) : -1;
+  };
   h->tile_off.assign(h->npairs + 1, 0);
-  for (int I = 0; I < na_tot; ++I)
-    for (int p = h->pair_row[I]; p < h->pair_row[I + 1]; ++p) {
-      const int J = h->pair_col[p];
-      h->tile_off[p + 1] =
-          h->tile_off[p] + (long long)((h->atom_norb[I] + 7) & ~7) * g.sp[h->species_host[J]].porb;
-    }
+  {
+    long long off = 0;
+    for (int J = 0; J < na_tot; ++J)
+      for (int q = h->pair_row[J]; q < h->pair_row[J + 1]; ++q) {
+        const int I = h->pair_col[q];  // pair (J, I) exists, so (I, J) does too
+        const int p = find_pair(I, J);
+        if (p < 0) return GINT_EINVAL;
+        h->tile_off[p] = off;
+        off += (long long)g.sp[h->species_host[I]].porb * g.sp[h->species_host[J]].porb;
+      }
+    h->tile_off[h->npairs] = off;
+  }
   h->ntile_elems = h->tile_off[h->npairs];
   const size_t tbytes = std::max<long long>(h->ntile_elems, 64) * sizeof(__half);
   if (cudaMalloc(&h->Dt_hi, tbytes) != cudaSuccess || cudaMalloc(&h->Dt_lo, tbytes) != cudaSuccess ||
@@ -1658,11 +1754,6 @@ int gint_tc_prepare(gint_handle *h) {
   std::vector<long long> hs_off(nb + 1, 0);
   std::vector<long long> cnt(h->npairs + 1, 0);
   int npmax = 0;
-  auto find_pair = [&](int I, int J) -> int {
-    auto b = h->pair_col.begin() + h->pair_row[I], e = h->pair_col.begin() + h->pair_row[I + 1];
-    auto it = std::lower_bound(b, e, J);
-    return (it != e && *it == J) ? (int)(it - h->pair_col.begin()) : -1;
-  };
   std::vector<int> no;  // padded orbital counts (porb) of the brick's slots
   std::vector<long long> ent_off(nb + 1);
   TC_CHECK(cudaMemcpy(ent_off.data(), h->b_ent_off, (nb + 1) * sizeof(long long), cudaMemcpyDeviceToHost));
