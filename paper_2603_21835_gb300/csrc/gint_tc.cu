@@ -18,9 +18,9 @@
 // diagonal block halved, rho = 2 sum_k P_k Y_k where Y_k accumulates P_j D_jk over the chunks
 // j <= chunk(k) only, so chunk c's columns are final right after chunk c's MMA: the epilogue of
 // chunk c overlaps the MMA of chunk c+1 and the MMA work is halved.  Within a brick the first
-// stages arrive by bulk copies during the orbital evaluation; then every warp but the MMA warp
-// loads the chunk whose stage has just been freed, one MMA thread issues, and twelve epilogue
-// warps drain finished chunks, all decoupled by mbarriers.
+// stages arrive by bulk copies during the orbital evaluation; then seven loader warps load the
+// chunk whose stage has just been freed, one MMA thread issues, and eight epilogue warps drain
+// finished chunks, all decoupled by mbarriers.
 // Force: full Y = P D (all chunks, all columns), then per atom 2 w V grad(phi) . Y.
 // Local H: K = grid points (chunks of 32), M = N = orbitals (128-row tiles, upper block
 // triangle); each brick writes its float32 slot-pair tiles to a scratch area and a per-pair
@@ -50,8 +50,17 @@ constexpr uint32_t kHSBO = 576;  // 4 core matrices of K per 8-row group
 constexpr long long kWaitNs = 2000000000LL;  // bounded mbarrier waits: 2 s
 constexpr unsigned char kNoSlot = 255;
 constexpr int kProducerWarp = 4, kMmaWarp = 5;  // producer: bulk-copy prefetch of the first stages
-constexpr int kEpiGroups = 3, kEpiWarps = 4 * kEpiGroups;  // density epilogue: warps 0-3, 6-13
-constexpr int kLoaderWarps = 15;                           // density chunk loads: every warp but the MMA warp
+// density phase B roles: epilogue groups of four warps (warps 0-3, 6-9, ...), the MMA warp (5),
+// and the loader warps (4 and every warp after the epilogue groups)
+constexpr int kEpiGroups = 2, kEpiWarps = 4 * kEpiGroups;
+constexpr int kLoaderWarps = 16 - 1 - kEpiWarps;
+constexpr int kMaxPieces = (4 * kNPMAX + 32 * kLoaderWarps - 1) / (32 * kLoaderWarps);  // per loader thread
+__device__ __forceinline__ int loader_index(int warp) {  // -1: not a loader warp
+  return warp == 4 ? 0 : warp >= 6 + 4 * (kEpiGroups - 1) ? warp - (6 + 4 * (kEpiGroups - 1)) + 1 : -1;
+}
+__device__ __forceinline__ int epi_group(int warp) {  // -1: not an epilogue warp
+  return warp < 4 ? 0 : (warp >= 6 && warp < 6 + 4 * (kEpiGroups - 1)) ? 1 + ((warp - 6) >> 2) : -1;
+}
 
 // ------------------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -956,34 +965,45 @@ __global__ void __launch_bounds__(kT, 1)
       bulk_g2s(Bl + gr * 256 + sg * 128, src < 0 ? zero : (diag ? S.Dlo2 : S.Dlo) + src, 128u, &sh.full[s]);
     }
   };
-  // chunk c's B panel into stage s by the loader threads (lt = 0 .. 32 kLoaderWarps - 1): 16-byte
-  // pieces through registers, rows on consecutive threads (eight threads read one core matrix)
-  auto load_chunk = [&](const GSys &S, int c, int s, int NP, int na, int lt) {
+  // chunk c's B panel by the loader threads (lt = 0 .. 32 kLoaderWarps - 1), 16-byte pieces with
+  // rows on consecutive threads (eight threads read one core matrix): gather_chunk issues the global
+  // loads into registers (no stage needed yet), scatter_chunk stores them into the freed stage.
+  auto gather_chunk = [&](const GSys &S, int c, int NP, int na, int lt, uint4 (&v)[kMaxPieces],
+                          int (&dst)[kMaxPieces]) {
     const int rowbase = FORCE ? 0 : c * kRC;
     const int nrows = NP - rowbase;
-    unsigned char *Bh = B0 + s * 2 * bop;
-#pragma unroll 2
-    for (int u = lt; u < 4 * nrows; u += kLoaderWarps * 32) {
-      const int seg = (u >= nrows) + (u >= 2 * nrows) + (u >= 3 * nrows);  // 2 h + column segment
-      const int rr = u - seg * nrows, r = rowbase + rr;
-      const int h = seg >> 1, sg = seg & 1;
-      const int j0 = c * kRC + 8 * sg;
-      const int bs = sh.col2slot[r], as = sh.col2slot[j0];
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (bs != kNoSlot && as != kNoSlot) {
-        const int tile = sh.s_tile[bs * na + as];
-        if (tile >= 0) {
-          const int kl = r - sh.s_pcol[bs];
-          const long long src = (long long)tile +
-                                (long long)((kl >> 3) * (sh.s_po[as] >> 3) + ((j0 - sh.s_pcol[as]) >> 3)) * 64 +
-                                (kl & 7) * 8;
-          const bool diag = !FORCE && rr < kRC;
-          const __half *base = h ? (diag ? S.Dlo2 : S.Dlo) : (diag ? S.Dhi2 : S.Dhi);
-          v = __ldg(reinterpret_cast<const uint4 *>(base + src));
+#pragma unroll
+    for (int i = 0; i < kMaxPieces; ++i) {
+      const int u = lt + i * kLoaderWarps * 32;
+      v[i] = make_uint4(0u, 0u, 0u, 0u);
+      dst[i] = -1;
+      if (u < 4 * nrows) {
+        const int seg = (u >= nrows) + (u >= 2 * nrows) + (u >= 3 * nrows);  // 2 h + column segment
+        const int rr = u - seg * nrows, r = rowbase + rr;
+        const int h = seg >> 1, sg = seg & 1;
+        const int j0 = c * kRC + 8 * sg;
+        dst[i] = h * (int)bop + (rr >> 3) * 256 + sg * 128 + (rr & 7) * 16;
+        const int bs = sh.col2slot[r], as = sh.col2slot[j0];
+        if (bs != kNoSlot && as != kNoSlot) {
+          const int tile = sh.s_tile[bs * na + as];
+          if (tile >= 0) {
+            const int kl = r - sh.s_pcol[bs];
+            const long long src = (long long)tile +
+                                  (long long)((kl >> 3) * (sh.s_po[as] >> 3) + ((j0 - sh.s_pcol[as]) >> 3)) * 64 +
+                                  (kl & 7) * 8;
+            const bool diag = !FORCE && rr < kRC;
+            const __half *base = h ? (diag ? S.Dlo2 : S.Dlo) : (diag ? S.Dhi2 : S.Dhi);
+            v[i] = __ldg(reinterpret_cast<const uint4 *>(base + src));
+          }
         }
       }
-      *reinterpret_cast<uint4 *>(Bh + h * bop + (rr >> 3) * 256 + sg * 128 + (rr & 7) * 16) = v;
     }
+  };
+  auto scatter_chunk = [&](int s, const uint4 (&v)[kMaxPieces], const int (&dst)[kMaxPieces]) {
+    unsigned char *Bs = B0 + s * 2 * bop;
+#pragma unroll
+    for (int i = 0; i < kMaxPieces; ++i)
+      if (dst[i] >= 0) *reinterpret_cast<uint4 *>(Bs + dst[i]) = v[i];
   };
   for (;;) {
     __syncthreads();
@@ -1092,9 +1112,10 @@ __global__ void __launch_bounds__(kT, 1)
       const uint32_t corr_base = (NP <= 256) ? 256u : 0u;  // separate correction accumulator if it fits
       if (warp == kMmaWarp) {
         if (lane == 0) {
+          unsigned *errp = S.err;
+          uint32_t s = G % nstages, fph = (G / nstages) & 1u;  // stage and phase parity of chunk 0
           for (int c = 0; c < nch; ++c) {
-            const uint32_t Gc = G + c, s = Gc % nstages;
-            if (!mbar_wait(&sh.full[s], (Gc / nstages) & 1, S.err)) ok = false;
+            if (!mbar_wait(&sh.full[s], fph, errp)) ok = false;
             tc_fence_after();
             unsigned char *Bh = B0 + s * 2 * bop, *Bl = Bh + bop;
             const int rowbase = FORCE ? 0 : c * kRC;
@@ -1114,30 +1135,38 @@ __global__ void __launch_bounds__(kT, 1)
               }
             }
             mma_commit(&sh.done[c]);
+            if (++s == (uint32_t)nstages) {
+              s = 0;
+              fph ^= 1u;
+            }
           }
         }
         __syncwarp();
-      } else {
-        // every other warp: once chunk c's MMAs are done its stage is free, load chunk c + nstages
-        // into it; then the density epilogue groups (warps 0-3, 6-9, 10-13, each covering the 128
-        // lanes) drain their chunks round robin (compensated float32 sums per point and group)
-        const int lt = (warp < kMmaWarp ? warp : warp - 1) * 32 + lane;
-        const int grp = FORCE ? -1 : warp < 4 ? 0 : (warp >= 6 && warp < 6 + 4 * (kEpiGroups - 1)) ? (warp - 2) >> 2 : -1;
+      } else if (loader_index(warp) >= 0) {
+        // loader warps: gather chunk c + nstages into registers, then once chunk c's MMAs are done
+        // (its stage is free) store it there
+        const int lt = loader_index(warp) * 32 + lane;
+        unsigned *errp = S.err;
+        int sl = (int)(G % nstages);  // stage of chunk c (and of chunk c + nstages)
+        uint4 v[kMaxPieces];
+        int dst[kMaxPieces];
+        for (int c = 0; c + nstages < nch; ++c) {
+          gather_chunk(S, c + nstages, NP, na, lt, v, dst);
+          if (!mbar_wait(&sh.done[c], (dpar >> c) & 1u, errp)) ok = false;
+          scatter_chunk(sl, v, dst);
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh.full[sl]);
+          if (++sl == nstages) sl = 0;
+        }
+      } else if (!FORCE) {
+        // density epilogue groups (each covers the 128 lanes) drain finished chunks round robin
+        // (compensated float32 sums per point and group)
+        const int grp = epi_group(warp);
         float rhi = 0.f, rlo = 0.f;
-        for (int c = 0; c < nch; ++c) {
-          const int cl = c + nstages;
-          const bool mine = grp >= 0 && c % kEpiGroups == grp;
-          if (cl >= nch && !mine) continue;
+        for (int c = grp; c < nch; c += kEpiGroups) {
           if (!mbar_wait(&sh.done[c], (dpar >> c) & 1u, S.err)) ok = false;
           tc_fence_after();
-          if (cl < nch) {
-            const int sl = (G + cl) % nstages;
-            load_chunk(S, cl, sl, NP, na, lt);
-            fence_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sh.full[sl]);
-          }
-          if (!mine) continue;
           // chunk c's columns are final: rho += P_k Y_k
           const int k0 = c * kRC;
           float y[16], yc[16];
@@ -1169,7 +1198,7 @@ __global__ void __launch_bounds__(kT, 1)
           sh.rpart[grp][p] = rhi;
           sh.rpartl[grp][p] = rlo;
         }
-        if (grp >= 0) epi_barrier();
+        epi_barrier();
         if (grp == 0) {
           for (int g2 = 1; g2 < kEpiGroups; ++g2) {
             float sum, err;
