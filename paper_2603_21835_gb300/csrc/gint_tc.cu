@@ -22,9 +22,12 @@
 // chunk whose stage has just been freed, one MMA thread issues, and eight epilogue warps drain
 // finished chunks, all decoupled by mbarriers.
 // Force: full Y = P D (all chunks, all columns), then per atom 2 w V grad(phi) . Y.
-// Local H: K = grid points (chunks of 32), M = N = orbitals (128-row tiles, upper block
-// triangle); each brick writes its float32 slot-pair tiles to a scratch area and a per-pair
-// float64 reduction (fixed order, no atomics) produces both H(I,J) and H(J,I).
+// Local H from the same orbital tile P: H = (W P)^T P with K = grid points (blocks of 16-32),
+// M = N = orbitals (128-row tiles, upper block triangle); both operands are MN-major views of
+// [point][orbital] buffers, W P built per block in the freed chunk stages.  Each brick writes its
+// float32 slot-pair tiles to a scratch area and a per-pair float64 reduction (fixed order, no
+// atomics) produces both H(I,J) and H(J,I).  One work item per brick runs every requested pass,
+// so the orbitals are evaluated once per brick.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -44,9 +47,6 @@ constexpr int kNPMAXH = 288;     // padded orbitals of a brick (local H: tensor-
 constexpr int kMAXA = 40;        // atoms of a brick
 constexpr int kMAXE = 160;       // (atom, image) entries of a brick
 constexpr int kRC = 16;          // density chunk width (one f16 K step)
-constexpr int kHP = 32;          // local-H chunk: grid points (two K steps)
-constexpr uint32_t kHLBO = 144;  // local-H operands: padded K-direction core-matrix stride
-constexpr uint32_t kHSBO = 576;  // 4 core matrices of K per 8-row group
 constexpr long long kWaitNs = 2000000000LL;  // bounded mbarrier waits: 2 s
 constexpr unsigned char kNoSlot = 255;
 constexpr int kProducerWarp = 4, kMmaWarp = 5;  // producer: bulk-copy prefetch of the first stages
@@ -140,6 +140,9 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 __device__ __forceinline__ uint32_t idesc_f16(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// Both operands MN-major (transposed): core-matrix rows run along M (or N); the descriptors then
+// take LBO = stride between core matrices along K, SBO = stride along M (or N).
+__device__ __forceinline__ uint32_t idesc_f16_mn(int M, int N) { return idesc_f16(M, N) | (1u << 15) | (1u << 16); }
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -652,28 +655,6 @@ __device__ __forceinline__ void job_P(const GTabs &g, const float2 *__restrict__
   }
 }
 
-// Local H: A = w V phi (scaled), B = phi (scaled), rows [pcol, pcol + PO), K = point pp.
-template <int NS, int NPR, int ND, int PO>
-__device__ __forceinline__ void job_H(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a, int pt,
-                                      int pp, bool valid, float Sphi, float wvSA, unsigned char *Ah,
-                                      unsigned char *Al, unsigned char *Bh, unsigned char *Bl) {
-  float v[PO];
-  slot_values<NS, NPR, ND, false>(g, tab, sh, a, point_df(sh, pt), valid, v, nullptr);
-  const int pc = sh.s_pcol[a];
-#pragma unroll
-  for (int i = 0; i < PO; ++i) {
-    const int r = pc + i;
-    __half bh, bl, ah, al;
-    split_h(v[i] * Sphi, bh, bl);
-    split_h(v[i] * wvSA, ah, al);
-    const uint32_t off = (r >> 3) * kHSBO + (pp >> 3) * kHLBO + (r & 7) * 16 + (pp & 7) * 2;
-    *reinterpret_cast<__half *>(Bh + off) = bh;
-    *reinterpret_cast<__half *>(Bl + off) = bl;
-    *reinterpret_cast<__half *>(Ah + off) = ah;
-    *reinterpret_cast<__half *>(Al + off) = al;
-  }
-}
-
 // Force epilogue: y[PO] (true Y values of slot a's columns) -> rho part and force components.
 template <int NS, int NPR, int ND, int PO>
 __device__ __forceinline__ void job_F(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a, int p,
@@ -719,33 +700,6 @@ __device__ __noinline__ void job_P_generic(const GTabs &g, const float2 *__restr
     *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
   }
 }
-__device__ __noinline__ void job_H_generic(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
-                                           int pt, int pp, bool valid, float Sphi, float wvSA, unsigned char *Ah,
-                                           unsigned char *Al, unsigned char *Bh, unsigned char *Bl) {
-  float v[GINT_MAX_ORB_ATOM];
-  const int po = sh.s_po[a], pc = sh.s_pcol[a];
-  for (int i = 0; i < po; ++i) v[i] = 0.f;
-  if (valid) {
-    const GSpecies &S = g.sp[sh.s_sp[a]];
-    for (int e = sh.s_e0[a]; e < sh.s_e0[a + 1]; ++e) {
-      float dh[3], dl[3];
-      rel_disp_df(sh, point_df(sh, pt), e, dh, dl);
-      if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < S.rcut2f)
-        add_image_generic<false>(g, tab, S, dh, dl, v, nullptr);
-    }
-  }
-  for (int i = 0; i < po; ++i) {
-    const int r = pc + i;
-    __half bh, bl, ah, al;
-    split_h(v[i] * Sphi, bh, bl);
-    split_h(v[i] * wvSA, ah, al);
-    const uint32_t off = (r >> 3) * kHSBO + (pp >> 3) * kHLBO + (r & 7) * 16 + (pp & 7) * 2;
-    *reinterpret_cast<__half *>(Bh + off) = bh;
-    *reinterpret_cast<__half *>(Bl + off) = bl;
-    *reinterpret_cast<__half *>(Ah + off) = ah;
-    *reinterpret_cast<__half *>(Al + off) = al;
-  }
-}
 __device__ __noinline__ void job_F_generic(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
                                            int p, bool valid, const float *y, float &rp, float &fx, float &fy,
                                            float &fz) {
@@ -776,8 +730,8 @@ __device__ __forceinline__ int gap_begin(const BrickSh &sh, int a) {
 
 // ------------------------------------------------------------------------------ batch descriptors
 // Several systems share one persistent launch.  They must have identical species/radial
-// metadata (GTabs, a kernel parameter); everything else is per system.  Work items are the
-// density (or force) bricks of system 0, then its local-H bricks, then those of system 1, ...
+// metadata (GTabs, a kernel parameter); everything else is per system.  Work items are the bricks
+// of system 0, then those of system 1, ...; an item runs every pass its system asks for.
 constexpr int kMaxBatch = 32;
 
 struct GSys {
@@ -794,11 +748,12 @@ struct GSys {
   unsigned *err;                             // device error word of the handle
   const uint4 *plan;                         // brick plan records (NULL: metadata built per item)
   const long long *plan_off;                 // [nbricks + 1] record offsets in 16-byte units
-  long long nrho, nh;                        // items of each kind: 0 or nbricks
+  int do_rho, do_h;                          // passes of this system's brick items
 };
 
 struct GBatch {
   int nsys, np_max, nstages, split3;
+  int hkb, pad;                    // local-H K-block (points) of the W P ping-pong buffers
   long long start[kMaxBatch + 1];  // first item of each system; start[nsys] = total
   GSys sys[kMaxBatch];
 };
@@ -838,8 +793,6 @@ __global__ void __launch_bounds__(kT, 1)
   unsigned char *Ph = smem, *Pl = smem + 128u * np_max * 2;
   unsigned char *B0 = smem + 128u * np_max * 4;
   const uint32_t bop = (uint32_t)np_max * kRC * 2;  // one B operand (hi or lo) of one stage
-  const uint32_t hop = (uint32_t)(np_max / 8) * kHSBO;
-  const uint32_t hstage = 4 * hop;
   const long long total = B.start[B.nsys];
   // thread 0: fetches the next item and starts the bulk copy of its plan record into planbuf
   // (the buffer is free: the current item's record was unpacked before the last barrier)
@@ -851,8 +804,7 @@ __global__ void __launch_bounds__(kT, 1)
     const int s2 = batch_sys(B, nx);
     const GSys &S2 = B.sys[s2];
     if (!S2.plan) return;
-    const long long l2 = nx - B.start[s2];
-    const long long b2 = l2 >= S2.nrho ? l2 - S2.nrho : l2;
+    const long long b2 = nx - B.start[s2];
     const long long o0 = S2.plan_off[b2], o1 = S2.plan_off[b2 + 1];
     const uint32_t bytes = (uint32_t)((o1 - o0) * 16);
     if (bytes > 4u * kPlanWords) return;
@@ -1015,9 +967,8 @@ __global__ void __launch_bounds__(kT, 1)
     }
     const int sidx = batch_sys(B, it);
     const GSys &S = B.sys[sidx];
-    const long long local = it - B.start[sidx];
-    const bool hitem = local >= S.nrho;
-    const long long b = hitem ? local - S.nrho : local;
+    const long long b = it - B.start[sidx];
+    const bool do_rho = S.do_rho != 0, do_h = S.do_h != 0;
     if (sidx != cur) {  // the previous item is finished (barrier above): replace points and scales
       init_points(S.c, sh);
       if (t == 0) {
@@ -1027,7 +978,7 @@ __global__ void __launch_bounds__(kT, 1)
       }
       cur = sidx;
     }
-    if (t < 128 && S.V && (hitem || FORCE)) {  // w V at the brick's points
+    if (t < 128 && S.V && (do_h || FORCE)) {  // w V at the brick's points
       int gi, gj, gk;
       sh.wv[t] = brick_point(S.c, b, t, gi, gj, gk) ? (float)(S.c.w * S.V[grid_index(S.c, gi, gj, gk)]) : 0.f;
     }
@@ -1041,8 +992,8 @@ __global__ void __launch_bounds__(kT, 1)
     if (t == 0) next_item();  // every thread has read sh.item and sh.plan_pref
     const int na = sh.na, NP = sh.np;
     const float Sphi = sh.sc[0];
-    if (!hitem) {
-      // ================================================================ density / force brick
+    {
+      // ================================================================ orbitals, density / force
       const float SD = sh.sc[1];
       const int p = t & 127, q = t >> 7;  // grid point, slot slice (0..3)
       const uint32_t lane_base = (uint32_t)((p >> 5) * 32) << 16;
@@ -1050,12 +1001,12 @@ __global__ void __launch_bounds__(kT, 1)
       const bool valid = brick_point(S.c, b, p, gi, gj, gk);
       const long long gidx = valid ? grid_index(S.c, gi, gj, gk) : 0;
       if (na == 0) {
-        if (q == 0 && valid && S.rho) S.rho[gidx] = 0.0;
+        if (do_rho && q == 0 && valid && S.rho) S.rho[gidx] = 0.0;
         continue;
       }
       const int nch = NP / kRC;
-      // the previous density item's MMAs are complete: every stage is free, prefetch the first chunks
-      if (warp == kProducerWarp)
+      // the previous item's MMAs are complete: every stage is free, prefetch the first density chunks
+      if (do_rho && warp == kProducerWarp)
         for (int c = 0; c < nch && c < nstages; ++c) issue_copies(S, c, (G + c) % nstages, NP, na);
       // ---- phase A: scaled orbitals of all atoms at every point -> P (hi, lo), zero padding
       for (int a = q; a < na; a += 4) {
@@ -1108,7 +1059,8 @@ __global__ void __launch_bounds__(kT, 1)
       }
       fence_async_smem();
       __syncthreads();
-      // ---- phase B: chunks of 16 columns, producer warp / MMA thread / epilogue warps
+      if (do_rho) {
+      // ---- phase B: chunks of 16 columns, loader warps / MMA thread / epilogue warps
       const uint32_t corr_base = (NP <= 256) ? 256u : 0u;  // separate correction accumulator if it fits
       if (warp == kMmaWarp) {
         if (lane == 0) {
@@ -1282,90 +1234,88 @@ __global__ void __launch_bounds__(kT, 1)
             atomicAdd(S.F + 3 * I + 2, sh.fpart[a][2]);
           }
       }
-    } else {
-      // ================================================================ local-H brick
-      if (na == 0) continue;
-      const float SA = sh.sc[2];
-      const float out_scale = 1.f / (Sphi * SA);
-      const int pp = t & (kHP - 1), q = t >> 5;  // point within the chunk, slot slice (0..15)
-      const int ntile = (NP + 127) / 128;
-      int tb[3] = {0, 0, 0}, T = 0;
-      for (int m = 0; m < ntile; ++m) {
-        tb[m] = T;
-        T += NP - 128 * m;
-      }
-      const uint32_t corr_base = (2 * T <= 512) ? (uint32_t)T : 0u;
-      for (int c = 0; c < 128 / kHP; ++c, ++GH) {
-        const int s = GH & 1;
-        unsigned char *Ah = smem + s * hstage, *Al = Ah + hop, *Bh = Al + hop, *Bl = Bh + hop;
-        if (GH >= 2 && !mbar_wait(&sh.hdone[s], ((GH - 2) >> 1) & 1, S.err)) ok = false;
-        const int pt = c * kHP + pp;
-        int gi, gj, gk;
-        const bool valid = brick_point(S.c, b, pt, gi, gj, gk);
-        const float wvSA = valid ? sh.wv[pt] * SA : 0.f;
-        for (int a = q; a < na; a += 16) {
-          const int pc = sh.s_pcol[a];
-          const int gend = (a == na - 1) ? NP : 0;
-          for (int r = gap_begin(sh, a); r < pc; ++r) {
-            const uint32_t off = (r >> 3) * kHSBO + (pp >> 3) * kHLBO + (r & 7) * 16 + (pp & 7) * 2;
-            *reinterpret_cast<uint16_t *>(Bh + off) = 0;
-            *reinterpret_cast<uint16_t *>(Bl + off) = 0;
-            *reinterpret_cast<uint16_t *>(Ah + off) = 0;
-            *reinterpret_cast<uint16_t *>(Al + off) = 0;
-          }
-          for (int r = pc + sh.s_po[a]; r < gend; ++r) {
-            const uint32_t off = (r >> 3) * kHSBO + (pp >> 3) * kHLBO + (r & 7) * 16 + (pp & 7) * 2;
-            *reinterpret_cast<uint16_t *>(Bh + off) = 0;
-            *reinterpret_cast<uint16_t *>(Bl + off) = 0;
-            *reinterpret_cast<uint16_t *>(Ah + off) = 0;
-            *reinterpret_cast<uint16_t *>(Al + off) = 0;
-          }
-          const float2 *tab = S.tab;
-          switch (g.sp[sh.s_sp[a]].shape) {
-#define CASE_H(ns, np_, nd)                                                                                    \
-  case GINT_SHAPE(ns, np_, nd):                                                                              \
-    job_H<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tab, sh, a, pt, pp, valid, Sphi, wvSA, Ah, Al, \
-                                                            Bh, Bl);                                         \
-    break;
-            GINT_FOR_SHAPES(CASE_H)
-#undef CASE_H
-            default:
-              job_H_generic(g, tab, sh, a, pt, pp, valid, Sphi, wvSA, Ah, Al, Bh, Bl);
-          }
-        }
-        fence_async_smem();
+      }  // do_rho
+      if (do_h) {
+        // ================================================================ local H from P
+        // H_mu,nu = sum_g (w V_g P_g,mu) P_g,nu: K = grid points in blocks of hkb, both operands
+        // MN-major views of [point][orbital] buffers (P itself, and W P built per block in one of
+        // two halves of the stage region, ping-pong with the MMAs of the previous block).
+        tc_fence_before();  // the density part's tensor-memory reads are finished
         __syncthreads();
-        if (t == 0) {
-          tc_fence_after();
-          for (int ks = 0; ks < kHP / 16; ++ks) {
-            for (int m = 0; m < ntile; ++m) {
-              const uint64_t dah = sdesc(smem_u32(Ah) + m * 16 * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
-              const uint64_t dal = sdesc(smem_u32(Al) + m * 16 * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
-              const int N = NP - 128 * m;
-              for (int n0 = 0; n0 < N; n0 += 256) {
-                const int nn = min(256, N - n0);
-                const uint32_t id = idesc_f16(128, nn);
-                const uint32_t brow = (uint32_t)(128 * m + n0);
-                const uint64_t dbh = sdesc(smem_u32(Bh) + (brow >> 3) * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
-                const uint64_t dbl = sdesc(smem_u32(Bl) + (brow >> 3) * kHSBO + ks * 2 * kHLBO, kHLBO, kHSBO);
-                const uint32_t dm = tmem + tb[m] + n0, dc = tmem + corr_base + tb[m] + n0;
-                const bool first = (c == 0 && ks == 0);
-                mma_f16(dm, dah, dbh, id, first ? 0u : 1u);
-                if (split3) {
-                  mma_f16(dc, dah, dbl, id, (first && corr_base) ? 0u : 1u);
-                  mma_f16(dc, dal, dbh, id, 1u);
+        tc_fence_after();
+        const float SA = sh.sc[2];
+        const float out_scale = 1.f / (Sphi * SA);
+        const float wscale = SA / Sphi;
+        const int hkb = B.hkb, ng = NP >> 3;
+        const uint32_t whalf = (uint32_t)hkb * 4u * (uint32_t)np_max;  // hi and lo of one block
+        const int ntile = (NP + 127) / 128;
+        int tb[3] = {0, 0, 0}, T = 0;
+        for (int m = 0; m < ntile; ++m) {
+          tb[m] = T;
+          T += NP - 128 * m;
+        }
+        const uint32_t corr_base = (2 * T <= 512) ? (uint32_t)T : 0u;
+        for (int j = 0; j < 128 / hkb; ++j, ++GH) {
+          const int hh = GH & 1;
+          unsigned char *Wh = B0 + hh * whalf, *Wl = Wh + whalf / 2;
+          // the MMAs that last read this half (two blocks ago) are complete
+          if (GH >= 2 && !mbar_wait(&sh.hdone[hh], ((GH - 2) >> 1) & 1, S.err)) ok = false;
+          const int p0 = j * hkb;
+          for (int u = t; u < hkb * ng; u += kT) {
+            const int pl = u / ng, gg = u - pl * ng, pt = p0 + pl;
+            const uint32_t so = (pt >> 3) * sboP + gg * 128 + (pt & 7) * 16;
+            const uint32_t dso = (pl >> 3) * sboP + gg * 128 + (pl & 7) * 16;
+            const float f = sh.wv[pt] * wscale;
+            const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + so), wl = *reinterpret_cast<const uint4 *>(Pl + so);
+            const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
+            uint32_t oh[4], ol[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
+              const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
+              __half h0, l0, h1, l1;
+              split_h((hf.x + lf.x) * f, h0, l0);
+              split_h((hf.y + lf.y) * f, h1, l1);
+              oh[e] = pack2(h0, h1);
+              ol[e] = pack2(l0, l1);
+            }
+            *reinterpret_cast<uint4 *>(Wh + dso) = make_uint4(oh[0], oh[1], oh[2], oh[3]);
+            *reinterpret_cast<uint4 *>(Wl + dso) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
+          }
+          fence_async_smem();
+          __syncthreads();
+          if (t == 0) {
+            tc_fence_after();
+            for (int ks = 0; ks < hkb / 16; ++ks) {
+              const uint32_t kw = (uint32_t)(2 * ks) * sboP, kp = (uint32_t)((p0 >> 3) + 2 * ks) * sboP;
+              for (int m = 0; m < ntile; ++m) {
+                const uint64_t dah = sdesc(smem_u32(Wh) + kw + m * 16 * 128, sboP, 128);
+                const uint64_t dal = sdesc(smem_u32(Wl) + kw + m * 16 * 128, sboP, 128);
+                const int N = NP - 128 * m;
+                for (int n0 = 0; n0 < N; n0 += 256) {
+                  const int nn = min(256, N - n0);
+                  const uint32_t id = idesc_f16_mn(128, nn);
+                  const uint32_t col = (uint32_t)(128 * m + n0);
+                  const uint64_t dbh = sdesc(smem_u32(Ph) + kp + (col >> 3) * 128, sboP, 128);
+                  const uint64_t dbl = sdesc(smem_u32(Pl) + kp + (col >> 3) * 128, sboP, 128);
+                  const uint32_t dm = tmem + tb[m] + n0, dc = tmem + corr_base + tb[m] + n0;
+                  const bool first = (j == 0 && ks == 0);
+                  mma_f16(dm, dah, dbh, id, first ? 0u : 1u);
+                  if (split3) {
+                    mma_f16(dc, dah, dbl, id, (first && corr_base) ? 0u : 1u);
+                    mma_f16(dc, dal, dbh, id, 1u);
+                  }
                 }
               }
             }
+            mma_commit(&sh.hdone[hh]);
           }
-          mma_commit(&sh.hdone[s]);
         }
-      }
-      {
-        const uint32_t Gp = GH - 1;
-        if (!mbar_wait(&sh.hdone[Gp & 1], (Gp >> 1) & 1, S.err)) ok = false;
-        tc_fence_after();
-      }
+        {
+          const uint32_t Gp = GH - 1;
+          if (!mbar_wait(&sh.hdone[Gp & 1], (Gp >> 1) & 1, S.err)) ok = false;
+          tc_fence_after();
+        }
       // epilogue: upper slot-pair tiles -> scratch (float32, unscaled), 8-column runs per row:
       // tile (a, c), a <= c, is porb(a) x porb(c) at rowst(a) + porb(a) (cumpo(c) - cumpo(a))
       {
@@ -1406,6 +1356,7 @@ __global__ void __launch_bounds__(kT, 1)
           }
         }
       }
+      }  // do_h
     }
     tc_fence_before();
     if (!ok) sh.abort = 1;
@@ -1631,7 +1582,9 @@ __global__ void __launch_bounds__(128) k_build_plans(const __grid_constant__ GTa
 }
 
 // ------------------------------------------------------------------------------ self-test
-// One f16 MMA per operand layout on integer data; err_out[0] = max |D - exact|.
+// One f16 MMA per operand layout the brick kernels use, on integer data; err_out[0] = max |D - exact|.
+//   layout 0, 1: K-major, LBO 128 (K), SBO 256 / 512 (8-row groups) -- density P and B stages
+//   layout 2: both operands MN-major, LBO = K-direction stride, SBO = 128 -- local H from P
 __global__ void __launch_bounds__(128, 1) k_tc_selftest(int N, float *err_out, unsigned *status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t bar;
@@ -1650,25 +1603,31 @@ __global__ void __launch_bounds__(128, 1) k_tc_selftest(int N, float *err_out, u
   tc_fence_after();
   const uint32_t tmem = tmem_s;
   float maxerr = 0.f;
-  const uint32_t lbos[3] = {128, 128, kHLBO}, sbos[3] = {256, 512, kHSBO};
   for (int layout = 0; layout < 3; ++layout) {
-    const uint32_t lbo = lbos[layout], sbo = sbos[layout];
-    unsigned char *A = smem, *B = smem + 16 * sbo;
+    const bool mn = layout == 2;
+    const uint32_t sbo = layout == 0 ? 256u : 512u;
+    unsigned char *A = smem, *B = smem + 8192;
+    const uint32_t ksa = 16 * 128, ksb = (uint32_t)(N / 8) * 128;  // MN-major K strides
     for (int e = t; e < 128 * 16; e += 128) {
       const int i = e >> 4, k = e & 15;
-      *reinterpret_cast<__half *>(A + (i >> 3) * sbo + (k >> 3) * lbo + (i & 7) * 16 + (k & 7) * 2) =
-          __float2half((float)(((i * 7 + k * 3) % 9) - 4));
+      const uint32_t off = mn ? (k >> 3) * ksa + (i >> 3) * 128 + (k & 7) * 16 + (i & 7) * 2
+                              : (i >> 3) * sbo + (k >> 3) * 128 + (i & 7) * 16 + (k & 7) * 2;
+      *reinterpret_cast<__half *>(A + off) = __float2half((float)(((i * 7 + k * 3) % 9) - 4));
     }
     for (int e = t; e < N * 16; e += 128) {
       const int n = e >> 4, k = e & 15;
-      *reinterpret_cast<__half *>(B + (n >> 3) * sbo + (k >> 3) * lbo + (n & 7) * 16 + (k & 7) * 2) =
-          __float2half((float)(((n * 5 + k * 11) % 9) - 4));
+      const uint32_t off = mn ? (k >> 3) * ksb + (n >> 3) * 128 + (k & 7) * 16 + (n & 7) * 2
+                              : (n >> 3) * sbo + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+      *reinterpret_cast<__half *>(B + off) = __float2half((float)(((n * 5 + k * 11) % 9) - 4));
     }
     fence_async_smem();
     __syncthreads();
     if (t == 0) {
       tc_fence_after();
-      mma_f16(tmem, sdesc(smem_u32(A), lbo, sbo), sdesc(smem_u32(B), lbo, sbo), idesc_f16(128, N), 0u);
+      if (mn)
+        mma_f16(tmem, sdesc(smem_u32(A), ksa, 128), sdesc(smem_u32(B), ksb, 128), idesc_f16_mn(128, N), 0u);
+      else
+        mma_f16(tmem, sdesc(smem_u32(A), 128, sbo), sdesc(smem_u32(B), 128, sbo), idesc_f16(128, N), 0u);
       mma_commit(&bar);
     }
     if (!mbar_wait(&bar, (uint32_t)layout & 1, status)) break;
@@ -1692,7 +1651,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_selftest(int N, float *err_out, u
 }
 
 inline uint32_t rho_smem_bytes(int np, int nstages) { return 128u * np * 4 + (uint32_t)nstages * np * kRC * 4; }
-inline uint32_t h_smem_bytes(int np) { return 2u * 4 * (uint32_t)(np / 8) * kHSBO + 16 * kHSBO; }
+constexpr uint32_t kHTail = 2048;  // >= 15 core matrices of 128 bytes
 
 template <typename K>
 int set_smem(K kern, uint32_t bytes) {
@@ -1911,7 +1870,7 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
   GRed R{};
   P.nsys = n;
   P.work = h0->work_ctr;
-  bool force = false, any_rho = false, any_h = false;
+  bool force = false;
   int np = kRC;
   long long items = 0, pairs = 0, uppers = 0;
   int nt = 0, nr = 0;
@@ -1920,8 +1879,6 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
     gint_handle *h = T.h;
     const bool dens = T.rho || T.F, loc = T.H_blocks != nullptr;
     force |= T.F != nullptr;
-    any_rho |= dens;
-    any_h |= loc;
     GPrepSys &ps = P.sys[i];
     ps.D = dens ? T.D_blocks : nullptr;
     ps.nblock = h->nblock;
@@ -1967,10 +1924,10 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
     S.err = h->err_word;
     S.plan = h->plan;
     S.plan_off = h->plan_off_dev;
-    S.nrho = dens ? h->geom.nbricks : 0;
-    S.nh = loc ? h->geom.nbricks : 0;
+    S.do_rho = dens ? 1 : 0;
+    S.do_h = loc ? 1 : 0;
     B.start[i] = items;
-    items += S.nrho + S.nh;
+    items += (dens || loc) ? h->geom.nbricks : 0;
     if (dens || loc) np = std::max(np, h->max_brick_porb);
     if (loc && h->nupper > 0) {
       R.start[nr] = uppers;
@@ -1995,14 +1952,16 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
   R.nsys = nr;
   R.start[nr] = uppers;
   np = (np + 15) & ~15;
+  // dynamic shared memory: P (hi, lo) | stage region (density chunk stages; afterwards the two W P
+  // halves of the local-H pass) | tail pad read by the last 128-row A tile above NP
   int nstages = kMaxStages;
-  if (any_rho)
-    while (nstages > 2 && rho_smem_bytes(np, nstages) + sizeof(BrickSh) > 227 * 1024) --nstages;
-  const uint32_t smem = std::max(any_rho ? rho_smem_bytes(np, nstages) : 0u, any_h ? h_smem_bytes(np) : 0u);
+  while (nstages > 2 && rho_smem_bytes(np, nstages) + kHTail + sizeof(BrickSh) > 227 * 1024) --nstages;
+  const uint32_t smem = rho_smem_bytes(np, nstages) + kHTail;
   if (smem + sizeof(BrickSh) > 227 * 1024) return GINT_ECAPACITY;
   B.np_max = np;
   B.nstages = nstages;
   B.split3 = split3;
+  B.hkb = nstages >= 4 ? 32 : 16;  // two halves of hkb x np_max (hi, lo) fit the stage region
   const int bx = std::max(8, 2 * h0->num_sms / n);
   k_prep<<<dim3(bx, n), 256, 0, st>>>(P);
   k_prep_scales<<<1, kMaxBatch, 0, st>>>(P);
@@ -2076,7 +2035,7 @@ extern "C" int gint_tc_selftest(int n, double *max_err) {
   int rc = GINT_OK;
   cudaMemset(d_err, 0, sizeof(float));
   cudaMemset(d_status, 0, sizeof(unsigned));
-  const uint32_t smem = 48 * kHSBO;
+  const uint32_t smem = 24 * 1024;  // A in [0, 8 KB), B in [8 KB, 24 KB) for every layout
   if (set_smem(k_tc_selftest, smem) != GINT_OK) rc = GINT_ECUDA;
   if (!rc) {
     k_tc_selftest<<<1, 128, smem>>>(n, d_err, d_status);
