@@ -1382,9 +1382,12 @@ struct GRed {
   GRedSys sys[kMaxBatch];
 };
 
-// One CTA per upper pair (I <= J) of any system: H_IJ = sum over the bricks containing both
-// (fixed order; float32 partials of eight contributions, float64 total); H_JI = H_IJ^T.
-__global__ void k_h_reduce(const __grid_constant__ GTabs g, const __grid_constant__ GRed R) {
+// One CTA per upper pair (I <= J) of any system: H_IJ = sum over the bricks containing both, in
+// a fixed (brick) order with a compensated float32 sum (two-sum: error-free additions into a
+// hi + lo pair, as accurate as a float64 sum of the float32 tiles); H_JI = H_IJ^T.  Sixteen
+// contributions are in flight per thread, the next sixteen scratch offsets loading meanwhile.
+__global__ void __launch_bounds__(192) k_h_reduce(const __grid_constant__ GTabs g, const __grid_constant__ GRed R) {
+  constexpr int kB = 16;
   const long long gu = blockIdx.x;
   int lo = 0, hi = R.nsys - 1;
   while (lo < hi) {
@@ -1405,15 +1408,36 @@ __global__ void k_h_reduce(const __grid_constant__ GTabs g, const __grid_constan
   for (int e = threadIdx.x; e < nI * nJ; e += blockDim.x) {
     const int i = e / nJ, j = e - (e / nJ) * nJ;
     const int se = i * pJ + j;
-    double acc = 0.0;
+    float ah = 0.f, al = 0.f;
     long long k = k0;
-    for (; k + 8 <= k1; k += 8) {
-      float v[8];
+    long long o[kB];
+    if (k + kB <= k1) {
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) v[jj] = hs[src[k + jj] + se];
-      acc += (double)(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
+      for (int jj = 0; jj < kB; ++jj) o[jj] = __ldg(src + k + jj);
     }
-    for (; k < k1; ++k) acc += (double)hs[src[k] + se];
+    for (; k + kB <= k1; k += kB) {
+      float v[kB];
+#pragma unroll
+      for (int jj = 0; jj < kB; ++jj) v[jj] = __ldg(hs + o[jj] + se);
+      if (k + 2 * kB <= k1) {
+#pragma unroll
+        for (int jj = 0; jj < kB; ++jj) o[jj] = __ldg(src + k + kB + jj);
+      }
+#pragma unroll
+      for (int jj = 0; jj < kB; ++jj) {
+        float sum, err;
+        two_sum(ah, v[jj], sum, err);
+        ah = sum;
+        al += err;
+      }
+    }
+    for (; k < k1; ++k) {
+      float sum, err;
+      two_sum(ah, __ldg(hs + src[k] + se), sum, err);
+      ah = sum;
+      al += err;
+    }
+    const double acc = (double)ah + (double)al;
     S.H[S.pair_off[p] + e] = acc;
     if (I != J) S.H[S.pair_off[S.pair_T[p]] + (long long)j * nI + i] = acc;
   }
