@@ -15,6 +15,8 @@ struct gint_handle {
   // radial tables, (f, f') per knot
   double2 *tab64 = nullptr;
   float2 *tab32 = nullptr;
+  float2 *tab32i = nullptr;  // interleaved per-species copy of tab32 ([knot][radial]) for shaped species
+  long long nknots_i = 0;
   long long nknots = 0;
   // atoms
   double *pos_dev = nullptr;

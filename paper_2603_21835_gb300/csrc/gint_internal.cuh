@@ -32,6 +32,8 @@ struct GSpecies {
   int shape;                   // (ns, np, nd) code 1 + ns + 8 np + 64 nd when the radials are l-sorted and
                                // share one knot grid (same npts and dr); 0 otherwise
   float rcut2f;                // rcut2 rounded to float32 (coarse support test of the float32 kernels)
+  int ioff, kslot;             // shaped species: interleaved float32 table [knot][kslot] of (f, f') at
+                               // float2 offset ioff, kslot = radials rounded up to even; 0 otherwise
   double rcut, rcut2;          // largest rc of the species and its square
 };
 #define GINT_SHAPE(ns, np, nd) (1 + (ns) + 8 * (np) + 64 * (nd))

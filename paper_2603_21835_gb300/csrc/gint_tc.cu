@@ -303,10 +303,12 @@ __device__ void add_image_generic(const GTabs &g, const float2 *__restrict__ tab
 }
 
 // Fast path for l-sorted species (NS s, NP p, ND d radials) on one knot grid: one knot/basis
-// computation per image, all column indices static (register arrays).
+// computation per image, the knot pair of every radial from the interleaved table (tabi: a few
+// 16-byte loads), all column indices static (register arrays).
 template <int NS, int NPR, int ND, bool GRAD>
-__device__ __forceinline__ void add_image_fast(const GTabs &g, const float2 *__restrict__ tab, const GSpecies &S,
+__device__ __forceinline__ void add_image_fast(const GTabs &g, const float2 *__restrict__ tabi, const GSpecies &S,
                                                const float dh[3], const float dl[3], float *v, float *gv) {
+  constexpr int NR = NS + NPR + ND, KS = (NR + 1) & ~1;
   float r, rl, ir;
   bool at0;
   dist_df(dh, dl, r, rl, ir, at0);
@@ -315,6 +317,28 @@ __device__ __forceinline__ void add_image_fast(const GTabs &g, const float2 *__r
   float t;
   if (!knot_df(R0, r, rl, i, t)) return;
   const Basis B = hermite_basis(t);
+  // (f, f') at knots i and i + 1: preloaded for values only; with gradients (more live registers)
+  // each radial's pair is loaded where it is used
+  const float2 *q2 = tabi + S.ioff + (long long)i * KS;
+  float2 ka[GRAD ? 1 : KS], kb[GRAD ? 1 : KS];
+  if (!GRAD) {
+    const float4 *q = reinterpret_cast<const float4 *>(q2);
+#pragma unroll
+    for (int h = 0; h < KS / 2; ++h) {
+      const float4 x = __ldg(q + h), y = __ldg(q + KS / 2 + h);
+      ka[2 * h] = make_float2(x.x, x.y);
+      ka[2 * h + 1] = make_float2(x.z, x.w);
+      kb[2 * h] = make_float2(y.x, y.y);
+      kb[2 * h + 1] = make_float2(y.z, y.w);
+    }
+  }
+  const float drf = R0.dr_f, idr = R0.idr_hi;  // shared knot grid
+  auto radial_k = [&](int k, float &f, float &df) {
+    const float2 a = GRAD ? __ldg(q2 + k) : ka[GRAD ? 0 : k], b = GRAD ? __ldg(q2 + KS + k) : kb[GRAD ? 0 : k];
+    const float dlt = b.x - a.x;
+    f = a.x + dlt * B.s + drf * (a.y * B.c0 + b.y * B.c1);
+    df = (dlt * B.ds + drf * (a.y * B.d0 + b.y * B.d1)) * idr;
+  };
   const float ux = dh[0] * ir, uy = dh[1] * ir, uz = dh[2] * ir;
   const float Y0 = 0.28209479177387814347f;
   float y1[3], gy1[3][3], y2[5], gy2[5][3];
@@ -325,7 +349,7 @@ __device__ __forceinline__ void add_image_fast(const GTabs &g, const float2 *__r
     const GRadial &R = g.rad[S.rad0 + k];
     if (r < R.rc_f) {
       float f, df;
-      radial_at(tab, R, i, B, f, df);
+      radial_k(k, f, df);
       v[k] += f * Y0;
       if (GRAD && !at0) {
         const float a = df * Y0;
@@ -341,7 +365,7 @@ __device__ __forceinline__ void add_image_fast(const GTabs &g, const float2 *__r
     const int col = NS + 3 * k;
     if (r < R.rc_f) {
       float f, df;
-      radial_at(tab, R, i, B, f, df);
+      radial_k(NS + k, f, df);
       if (at0) {
         if (GRAD) {
           const float c = 0.48860251190291992159f * df;
@@ -370,7 +394,7 @@ __device__ __forceinline__ void add_image_fast(const GTabs &g, const float2 *__r
     const int col = NS + 3 * NPR + 5 * k;
     if (r < R.rc_f && !at0) {
       float f, df;
-      radial_at(tab, R, i, B, f, df);
+      radial_k(NS + NPR + k, f, df);
       const float fr = f * ir;
 #pragma unroll
       for (int m = 0; m < 5; ++m) {
@@ -738,6 +762,7 @@ struct GSys {
   GCell c;
   GNbr nb;
   const float2 *tab;                         // float32 knot table of this system's handle
+  const float2 *tabi;                        // its interleaved copy (shaped species)
   const __half *Dhi, *Dlo, *Dhi2, *Dlo2;     // D tiles (density / force items)
   const long long *tile_off;
   const float *scales;                       // [0] S_phi, [1] S_D, [2] S_Q
@@ -1024,7 +1049,7 @@ __global__ void __launch_bounds__(kT, 1)
           }
       }
       {
-        const float2 *tab = S.tab;
+        const float2 *tab = S.tab, *tabi = S.tabi;
         const PointDF P = point_df(sh, p);
         for (int a = q; a < na; a += 8) {
           const int a1 = a + 4;
@@ -1034,9 +1059,9 @@ __global__ void __launch_bounds__(kT, 1)
 #define CASE_P(ns, np_, nd)                                                                                      \
   case GINT_SHAPE(ns, np_, nd):                                                                                \
     if (pair)                                                                                                  \
-      job_P2<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tab, sh, a, a1, P, p, valid, Sphi, Ph, Pl, sboP); \
+      job_P2<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tabi, sh, a, a1, P, p, valid, Sphi, Ph, Pl, sboP); \
     else                                                                                                       \
-      job_P<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tab, sh, a, P, p, valid, Sphi, Ph, Pl, sboP);     \
+      job_P<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tabi, sh, a, P, p, valid, Sphi, Ph, Pl, sboP);    \
     break;
             GINT_FOR_SHAPES(CASE_P)
 #undef CASE_P
@@ -1047,7 +1072,7 @@ __global__ void __launch_bounds__(kT, 1)
             switch (g.sp[sh.s_sp[a1]].shape) {
 #define CASE_P1(ns, np_, nd)                                                                                      \
   case GINT_SHAPE(ns, np_, nd):                                                                                 \
-    job_P<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tab, sh, a1, P, p, valid, Sphi, Ph, Pl, sboP);     \
+    job_P<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tabi, sh, a1, P, p, valid, Sphi, Ph, Pl, sboP);    \
     break;
               GINT_FOR_SHAPES(CASE_P1)
 #undef CASE_P1
@@ -1169,7 +1194,7 @@ __global__ void __launch_bounds__(kT, 1)
       dpar ^= (nch >= 32) ? 0xffffffffu : ((1u << nch) - 1u);
       if (FORCE) {
         // full Y: per atom, rho and force from recomputed phi and grad phi (unscaled float32)
-        const float2 *tab = S.tab;
+        const float2 *tab = S.tab, *tabi = S.tabi;
         const float inv = 1.f / (Sphi * SD);
         const float wv = (valid && S.V) ? sh.wv[p] : 0.f;
         float rp = 0.f;
@@ -1200,7 +1225,7 @@ __global__ void __launch_bounds__(kT, 1)
           switch (g.sp[sh.s_sp[a]].shape) {
 #define CASE_F(ns, np_, nd)                                                                          \
   case GINT_SHAPE(ns, np_, nd):                                                                    \
-    job_F<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tab, sh, a, p, valid, y, rp, fx, fy, fz); \
+    job_F<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tabi, sh, a, p, valid, y, rp, fx, fy, fz); \
     break;
             GINT_FOR_SHAPES(CASE_F)
 #undef CASE_F
@@ -1935,6 +1960,7 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
     S.c = static_cast<const GCell &>(h->geom);
     S.nb = h->nbr();
     S.tab = h->tab32;
+    S.tabi = h->tab32i;
     S.Dhi = h->Dt_hi;
     S.Dlo = h->Dt_lo;
     S.Dhi2 = h->Dt_hi2;
