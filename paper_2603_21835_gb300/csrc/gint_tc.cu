@@ -180,13 +180,15 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// x = hi + lo with both parts float16 (hi = round(x), lo = round(x - hi)).
-__device__ __forceinline__ void split_h(float x, __half &hi, __half &lo) {
-  hi = __float2half_rn(x);
-  lo = __float2half_rn(x - __half2float(hi));
-}
-__device__ __forceinline__ uint32_t pack2(__half a, __half b) {
-  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+// x = hi + lo with both parts float16 (hi = round(x), lo = round(x - hi)), two values at once
+// (packed float32x2 -> float16x2 round-to-nearest conversions): hw, lw hold the hi and lo halves
+// of a (low 16 bits) and b (high 16 bits).
+__device__ __forceinline__ void split_h2(float a, float b, uint32_t &hw, uint32_t &lw) {
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+  hw = *reinterpret_cast<const uint32_t *>(&h);
+  lw = *reinterpret_cast<const uint32_t *>(&l);
 }
 
 // ------------------------------------------------------------------------------ orbital evaluation
@@ -633,11 +635,7 @@ __device__ __forceinline__ void store_P(const float *v, int pc, int p, float Sph
     uint32_t wh[4], wl[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      __half h0, l0, h1, l1;
-      split_h(v[k + 2 * e] * Sphi, h0, l0);
-      split_h(v[k + 2 * e + 1] * Sphi, h1, l1);
-      wh[e] = pack2(h0, h1);
-      wl[e] = pack2(l0, l1);
+      split_h2(v[k + 2 * e] * Sphi, v[k + 2 * e + 1] * Sphi, wh[e], wl[e]);
     }
     const uint32_t off = (p >> 3) * sboP + ((pc + k) >> 3) * 128 + (p & 7) * 16;
     *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
@@ -667,11 +665,7 @@ __device__ __forceinline__ void job_P(const GTabs &g, const float2 *__restrict__
     uint32_t wh[4], wl[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      __half h0, l0, h1, l1;
-      split_h(v[k + 2 * e] * Sphi, h0, l0);
-      split_h(v[k + 2 * e + 1] * Sphi, h1, l1);
-      wh[e] = pack2(h0, h1);
-      wl[e] = pack2(l0, l1);
+      split_h2(v[k + 2 * e] * Sphi, v[k + 2 * e + 1] * Sphi, wh[e], wl[e]);
     }
     const uint32_t off = (p >> 3) * sboP + ((pc + k) >> 3) * 128 + (p & 7) * 16;
     *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
@@ -713,11 +707,7 @@ __device__ __noinline__ void job_P_generic(const GTabs &g, const float2 *__restr
   for (int k = 0; k < po; k += 8) {
     uint32_t wh[4], wl[4];
     for (int e = 0; e < 4; ++e) {
-      __half h0, l0, h1, l1;
-      split_h(v[k + 2 * e] * Sphi, h0, l0);
-      split_h(v[k + 2 * e + 1] * Sphi, h1, l1);
-      wh[e] = pack2(h0, h1);
-      wl[e] = pack2(l0, l1);
+      split_h2(v[k + 2 * e] * Sphi, v[k + 2 * e + 1] * Sphi, wh[e], wl[e]);
     }
     const uint32_t off = (p >> 3) * sboP + ((pc + k) >> 3) * 128 + (p & 7) * 16;
     *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
@@ -1299,11 +1289,7 @@ __global__ void __launch_bounds__(kT, 1)
             for (int e = 0; e < 4; ++e) {
               const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
               const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
-              __half h0, l0, h1, l1;
-              split_h((hf.x + lf.x) * f, h0, l0);
-              split_h((hf.y + lf.y) * f, h1, l1);
-              oh[e] = pack2(h0, h1);
-              ol[e] = pack2(l0, l1);
+              split_h2((hf.x + lf.x) * f, (hf.y + lf.y) * f, oh[e], ol[e]);
             }
             *reinterpret_cast<uint4 *>(Wh + dso) = make_uint4(oh[0], oh[1], oh[2], oh[3]);
             *reinterpret_cast<uint4 *>(Wl + dso) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
