@@ -82,6 +82,18 @@ def profiled_traffic(workload: str, precision: str):
     return None, None
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest value over all ranks (timings: the slowest rank sets the job's time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -372,10 +384,7 @@ def main():
             b.record(stream)
             torch.cuda.synchronize()
             lst.append(a.elapsed_time(b))
-    tot = torch.tensor([sum(t_steps)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    ms_per_step = tot.item() / args.steps
+    ms_per_step = max_over_ranks(sum(t_steps), world, dev) / args.steps
     value = world * 2.0 * W / (ms_per_step * 1e-3) / 1e9
 
     # roofline of the dominant kernel (per-launch mean over the timed region, CUDA events on its stream)
@@ -432,10 +441,7 @@ def main():
             e1.synchronize()
             if k > 0:
                 te.append(e0.elapsed_time(e1))
-        tt = torch.tensor([sum(te)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_e2e = tt.item() / len(te)
+        ms_e2e = max_over_ranks(sum(te), world, dev) / len(te)
         e2e = {"value": world * 2.0 * W / (ms_e2e * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": int(Db.numel() * 8 + V.numel() * 8),
                "d2h_bytes_per_step": int(rho.numel() * 8 + H.numel() * 8)}
