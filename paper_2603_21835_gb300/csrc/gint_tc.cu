@@ -1276,9 +1276,12 @@ __global__ void __launch_bounds__(kT, 1)
           // the MMAs that last read this half (two blocks ago) are complete
           if (GH >= 2 && !mbar_wait(&sh.hdone[hh], ((GH - 2) >> 1) & 1, S.err)) ok = false;
           const int p0 = j * hkb;
-          // warps 1-15 build the block while thread 0 may still be issuing the previous block's MMAs
+          // warps 1-15 build the block while thread 0 may still be issuing the previous block's MMAs.
+          // Unit u = (point octet, orbital group, point in octet) with the point fastest: eight
+          // consecutive threads touch one 128-byte core-matrix row block (no bank conflicts).
           for (int u = t - 32; u >= 0 && u < hkb * ng; u += kT - 32) {
-            const int pl = u / ng, gg = u - pl * ng, pt = p0 + pl;
+            const int v8 = u >> 3, po8 = v8 / ng, gg = v8 - po8 * ng;
+            const int pl = po8 * 8 + (u & 7), pt = p0 + pl;
             const uint32_t so = (pt >> 3) * sboP + gg * 128 + (pt & 7) * 16;
             const uint32_t dso = (pl >> 3) * sboP + gg * 128 + (pl & 7) * 16;
             const float f = sh.wv[pt] * wscale;
