@@ -49,7 +49,7 @@ constexpr int kMAXE = 160;       // (atom, image) entries of a brick
 constexpr int kRC = 16;          // density chunk width (one f16 K step)
 constexpr long long kWaitNs = 2000000000LL;  // bounded mbarrier waits: 2 s
 constexpr unsigned char kNoSlot = 255;
-constexpr int kProducerWarp = 4, kMmaWarp = 5;  // producer: bulk-copy prefetch of the first stages
+constexpr int kMmaWarp = 5;  // lane 0 issues the density MMAs
 // density phase B roles: epilogue groups of four warps (warps 0-3, 6-9, ...), the MMA warp (5),
 // and the loader warps (4 and every warp after the epilogue groups)
 constexpr int kEpiGroups = 2, kEpiWarps = 4 * kEpiGroups;
@@ -414,6 +414,7 @@ __device__ __forceinline__ void add_image_fast(const GTabs &g, const float2 *__r
 
 // ------------------------------------------------------------------------------ brick metadata
 constexpr int kMaxStages = 6;
+static_assert(kLoaderWarps >= kMaxStages, "one loader warp per prefetched stage");
 constexpr int kMaxChunks = kNPMAX / kRC;
 constexpr int kPlanWords = 1536;  // prefetch buffer of a brick plan record (6 KB); larger records take the slow path
 struct BrickSh {
@@ -1021,8 +1022,12 @@ __global__ void __launch_bounds__(kT, 1)
       }
       const int nch = NP / kRC;
       // the previous item's MMAs are complete: every stage is free, prefetch the first density chunks
-      if (do_rho && warp == kProducerWarp)
-        for (int c = 0; c < nch && c < nstages; ++c) issue_copies(S, c, (G + c) % nstages, NP, na);
+      // (one chunk per loader warp: a warp issuing a chunk's bulk copies spends about as long as
+      // a quarter of the orbital evaluation)
+      if (do_rho) {
+        const int li = loader_index(warp);
+        if (li >= 0 && li < nch && li < nstages) issue_copies(S, li, (G + li) % nstages, NP, na);
+      }
       // ---- phase A: scaled orbitals of all atoms at every point -> P (hi, lo), zero padding
       for (int a = q; a < na; a += 4) {
         const int gap0 = gap_begin(sh, a), pc = sh.s_pcol[a];
