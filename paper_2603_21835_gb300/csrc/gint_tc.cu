@@ -1389,8 +1389,10 @@ __global__ void __launch_bounds__(kT, 1)
           if (!mbar_wait(&sh.hdone[Gp & 1], (Gp >> 1) & 1, S.err)) ok = false;
           tc_fence_after();
         }
-      // epilogue: upper slot-pair tiles -> scratch (float32, unscaled), 8-column runs per row:
-      // tile (a, c), a <= c, is porb(a) x porb(c) at rowst(a) + porb(a) (cumpo(c) - cumpo(a))
+      // epilogue: upper slot-pair tiles -> scratch (float32, unscaled), stored column-major so that
+      // the lanes of a warp (consecutive rows) write contiguous runs: tile (a, c), a <= c, holds
+      // porb(c) columns of porb(a) rows at rowst(a) + porb(a) (cumpo(c) - cumpo(a)); element (i, j)
+      // at j porb(a) + i (the row-major porb(c) x porb(a) block (c, a) of the symmetric brick H)
       {
         const int ln = t & 127, qq = t >> 7;
         const uint32_t lane_base = (uint32_t)((ln >> 5) * 32) << 16;
@@ -1401,7 +1403,7 @@ __global__ void __launch_bounds__(kT, 1)
           const int il = as != kNoSlot ? mu - sh.s_pcol[as] : 0;
           const bool rowok = as != kNoSlot && il < sh.s_no[as];
           const int po_a = rowok ? sh.s_po[as] : 0, cum_a = rowok ? sh.s_cumpo[as] : 0;
-          float *rowp = S.hs + base + (rowok ? sh.s_rowst[as] : 0);
+          float *rowp = S.hs + base + (rowok ? sh.s_rowst[as] : 0) + il;
           const int N = NP - 128 * m;
           for (int gcol = qq; gcol < N / 16; gcol += 4) {
             float y[16], yc[16];
@@ -1417,14 +1419,9 @@ __global__ void __launch_bounds__(kT, 1)
               const int nu = 128 * m + gcol * 16 + 8 * hh;
               const int cs = sh.col2slot[nu];
               if (cs == kNoSlot || cs < as) continue;
-              const int po_c = sh.s_po[cs];
-              float *dst = rowp + (long long)po_a * (sh.s_cumpo[cs] - cum_a) + il * po_c + (nu - sh.s_pcol[cs]);
-              reinterpret_cast<float4 *>(dst)[0] =
-                  make_float4(y[8 * hh] * out_scale, y[8 * hh + 1] * out_scale, y[8 * hh + 2] * out_scale,
-                              y[8 * hh + 3] * out_scale);
-              reinterpret_cast<float4 *>(dst)[1] =
-                  make_float4(y[8 * hh + 4] * out_scale, y[8 * hh + 5] * out_scale, y[8 * hh + 6] * out_scale,
-                              y[8 * hh + 7] * out_scale);
+              float *dst = rowp + (long long)po_a * (sh.s_cumpo[cs] - cum_a + (nu - sh.s_pcol[cs]));
+#pragma unroll
+              for (int i = 0; i < 8; ++i) dst[(long long)i * po_a] = y[8 * hh + i] * out_scale;
             }
           }
         }
@@ -1454,8 +1451,8 @@ struct GRed {
   GRedSys sys[kMaxBatch];
 };
 
-// One CTA per upper pair (I <= J) of any system: H_IJ = sum over the bricks containing both, in
-// a fixed (brick) order with a compensated float32 sum (two-sum: error-free additions into a
+// One CTA per upper pair (I <= J) of any system: H_IJ = sum over the bricks containing both (their
+// scratch tiles are column-major, element (i, j) at j porb(I) + i), in a fixed (brick) order with a compensated float32 sum (two-sum: error-free additions into a
 // hi + lo pair, as accurate as a float64 sum of the float32 tiles); H_JI = H_IJ^T.  Sixteen
 // contributions are in flight per thread, the next sixteen scratch offsets loading meanwhile.
 __global__ void __launch_bounds__(192) k_h_reduce(const __grid_constant__ GTabs g, const __grid_constant__ GRed R) {
@@ -1473,13 +1470,13 @@ __global__ void __launch_bounds__(192) k_h_reduce(const __grid_constant__ GTabs 
   const int u = (int)(gu - R.start[lo]);
   const int p = S.hu_pair[u];
   const int I = S.pair_I[p], J = S.pair_J[p];
-  const int nI = g.sp[S.species[I]].norb, nJ = g.sp[S.species[J]].norb, pJ = g.sp[S.species[J]].porb;
+  const int nI = g.sp[S.species[I]].norb, nJ = g.sp[S.species[J]].norb, pI = g.sp[S.species[I]].porb;
   const long long k0 = S.hu_off[u], k1 = S.hu_off[u + 1];
   const float *__restrict__ hs = S.hs;
   const long long *__restrict__ src = S.hu_src;
   for (int e = threadIdx.x; e < nI * nJ; e += blockDim.x) {
-    const int i = e / nJ, j = e - (e / nJ) * nJ;
-    const int se = i * pJ + j;
+    const int j = e / nI, i = e - (e / nI) * nI;
+    const int se = j * pI + i;
     float ah = 0.f, al = 0.f;
     long long k = k0;
     long long o[kB];
@@ -1510,8 +1507,8 @@ __global__ void __launch_bounds__(192) k_h_reduce(const __grid_constant__ GTabs 
       al += err;
     }
     const double acc = (double)ah + (double)al;
-    S.H[S.pair_off[p] + e] = acc;
-    if (I != J) S.H[S.pair_off[S.pair_T[p]] + (long long)j * nI + i] = acc;
+    S.H[S.pair_off[p] + (long long)i * nJ + j] = acc;
+    if (I != J) S.H[S.pair_off[S.pair_T[p]] + e] = acc;
   }
 }
 
