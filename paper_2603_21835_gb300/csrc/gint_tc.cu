@@ -1401,7 +1401,8 @@ __global__ void __launch_bounds__(kT, 1)
           const int mu = 128 * m + ln;
           const int as = mu < NP ? sh.col2slot[mu] : kNoSlot;
           const int il = as != kNoSlot ? mu - sh.s_pcol[as] : 0;
-          const bool rowok = as != kNoSlot && il < sh.s_no[as];
+          // padding rows are stored too (zeros; never read): whole 32-byte sectors per column
+          const bool rowok = as != kNoSlot;
           const int po_a = rowok ? sh.s_po[as] : 0, cum_a = rowok ? sh.s_cumpo[as] : 0;
           float *rowp = S.hs + base + (rowok ? sh.s_rowst[as] : 0) + il;
           const int N = NP - 128 * m;
@@ -1452,11 +1453,15 @@ struct GRed {
 };
 
 // One CTA per upper pair (I <= J) of any system: H_IJ = sum over the bricks containing both (their
-// scratch tiles are column-major, element (i, j) at j porb(I) + i), in a fixed (brick) order with a compensated float32 sum (two-sum: error-free additions into a
-// hi + lo pair, as accurate as a float64 sum of the float32 tiles); H_JI = H_IJ^T.  Sixteen
-// contributions are in flight per thread, the next sixteen scratch offsets loading meanwhile.
-__global__ void __launch_bounds__(192) k_h_reduce(const __grid_constant__ GTabs g, const __grid_constant__ GRed R) {
-  constexpr int kB = 16;
+// scratch tiles are column-major, porb(J) columns of porb(I) rows, padding rows included, every tile
+// 16-byte aligned), with compensated float32 sums (two-sum: error-free additions into a hi + lo pair,
+// as accurate as a float64 sum of the float32 tiles); H_JI = H_IJ^T.  A thread sums four rows of one
+// column (16-byte loads, eight in flight) over one of kRedGroups contiguous parts of the brick list;
+// the parts' sums are then combined in part order (the result does not depend on scheduling).
+constexpr int kRedLanes = 64, kRedGroups = 4, kRedThreads = kRedLanes * kRedGroups;
+__global__ void __launch_bounds__(kRedThreads, 4) k_h_reduce(const __grid_constant__ GTabs g, const __grid_constant__ GRed R) {
+  constexpr int kB = 8;
+  __shared__ float4 part_hi[kRedGroups - 1][kRedLanes], part_lo[kRedGroups - 1][kRedLanes];
   const long long gu = blockIdx.x;
   int lo = 0, hi = R.nsys - 1;
   while (lo < hi) {
@@ -1470,45 +1475,76 @@ __global__ void __launch_bounds__(192) k_h_reduce(const __grid_constant__ GTabs 
   const int u = (int)(gu - R.start[lo]);
   const int p = S.hu_pair[u];
   const int I = S.pair_I[p], J = S.pair_J[p];
-  const int nI = g.sp[S.species[I]].norb, nJ = g.sp[S.species[J]].norb, pI = g.sp[S.species[I]].porb;
-  const long long k0 = S.hu_off[u], k1 = S.hu_off[u + 1];
+  const int nI = g.sp[S.species[I]].norb, nJ = g.sp[S.species[J]].norb;
+  const int pI = g.sp[S.species[I]].porb, pJ = g.sp[S.species[J]].porb;
+  const int ln = threadIdx.x % kRedLanes, grp = threadIdx.x / kRedLanes;
+  const long long kk0 = S.hu_off[u], kk1 = S.hu_off[u + 1];
+  const long long per = (kk1 - kk0 + kRedGroups - 1) / kRedGroups;
+  const long long k0 = min(kk1, kk0 + grp * per), k1 = min(kk1, k0 + per);
   const float *__restrict__ hs = S.hs;
   const long long *__restrict__ src = S.hu_src;
-  for (int e = threadIdx.x; e < nI * nJ; e += blockDim.x) {
-    const int j = e / nI, i = e - (e / nI) * nI;
-    const int se = j * pI + i;
-    float ah = 0.f, al = 0.f;
-    long long k = k0;
-    long long o[kB];
-    if (k + kB <= k1) {
+  const int n4 = (pI * pJ) >> 2;
+  for (int base = 0; base < n4; base += kRedLanes) {  // block-uniform trip count
+    const int e4 = base + ln, f = 4 * e4, j = f / pI, i0 = f - j * pI;  // rows i0 .. i0 + 3 of column j
+    const bool act = e4 < n4 && j < nJ && i0 < nI;
+    float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
+    auto add = [&](const float4 v) {
+      const float x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int jj = 0; jj < kB; ++jj) o[jj] = __ldg(src + k + jj);
-    }
-    for (; k + kB <= k1; k += kB) {
-      float v[kB];
-#pragma unroll
-      for (int jj = 0; jj < kB; ++jj) v[jj] = __ldg(hs + o[jj] + se);
-      if (k + 2 * kB <= k1) {
-#pragma unroll
-        for (int jj = 0; jj < kB; ++jj) o[jj] = __ldg(src + k + kB + jj);
-      }
-#pragma unroll
-      for (int jj = 0; jj < kB; ++jj) {
+      for (int q = 0; q < 4; ++q) {
         float sum, err;
-        two_sum(ah, v[jj], sum, err);
-        ah = sum;
-        al += err;
+        two_sum(ah[q], x[q], sum, err);
+        ah[q] = sum;
+        al[q] += err;
+      }
+    };
+    if (act) {
+      long long k = k0;
+      long long o[kB];
+      if (k + kB <= k1) {
+#pragma unroll
+        for (int jj = 0; jj < kB; ++jj) o[jj] = __ldg(src + k + jj);
+      }
+      for (; k + kB <= k1; k += kB) {
+        float4 v[kB];
+#pragma unroll
+        for (int jj = 0; jj < kB; ++jj) v[jj] = __ldg(reinterpret_cast<const float4 *>(hs + o[jj] + f));
+        if (k + 2 * kB <= k1) {
+#pragma unroll
+          for (int jj = 0; jj < kB; ++jj) o[jj] = __ldg(src + k + kB + jj);
+        }
+#pragma unroll
+        for (int jj = 0; jj < kB; ++jj) add(v[jj]);
+      }
+      for (; k < k1; ++k) add(__ldg(reinterpret_cast<const float4 *>(hs + src[k] + f)));
+    }
+    if (grp > 0) {
+      part_hi[grp - 1][ln] = make_float4(ah[0], ah[1], ah[2], ah[3]);
+      part_lo[grp - 1][ln] = make_float4(al[0], al[1], al[2], al[3]);
+    }
+    __syncthreads();
+    if (grp == 0 && act) {
+      for (int g2 = 0; g2 < kRedGroups - 1; ++g2) {
+        const float4 h4 = part_hi[g2][ln], l4 = part_lo[g2][ln];
+        const float hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float sum, err;
+          two_sum(ah[q], hv[q], sum, err);
+          ah[q] = sum;
+          al[q] += err + lv[q];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + q;
+        if (i >= nI) break;
+        const double acc = (double)ah[q] + (double)al[q];
+        S.H[S.pair_off[p] + (long long)i * nJ + j] = acc;
+        if (I != J) S.H[S.pair_off[S.pair_T[p]] + (long long)j * nI + i] = acc;
       }
     }
-    for (; k < k1; ++k) {
-      float sum, err;
-      two_sum(ah, __ldg(hs + src[k] + se), sum, err);
-      ah = sum;
-      al += err;
-    }
-    const double acc = (double)ah + (double)al;
-    S.H[S.pair_off[p] + (long long)i * nJ + j] = acc;
-    if (I != J) S.H[S.pair_off[S.pair_T[p]] + e] = acc;
+    __syncthreads();
   }
 }
 
@@ -2076,7 +2112,7 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
     if (ev1) TC_CHECK(cudaEventRecord(ev1, st));
   }
   if (uppers > 0) {
-    k_h_reduce<<<(unsigned)uppers, 192, 0, st>>>(tabs, R);
+    k_h_reduce<<<(unsigned)uppers, kRedThreads, 0, st>>>(tabs, R);
     TC_CHECK(cudaGetLastError());
   }
   return GINT_OK;
