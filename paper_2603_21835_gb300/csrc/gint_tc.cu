@@ -58,6 +58,12 @@ constexpr int kMaxPieces = (4 * kNPMAX + 32 * kLoaderWarps - 1) / (32 * kLoaderW
 __device__ __forceinline__ int loader_index(int warp) {  // -1: not a loader warp
   return warp == 4 ? 0 : warp >= 6 + 4 * (kEpiGroups - 1) ? warp - (6 + 4 * (kEpiGroups - 1)) + 1 : -1;
 }
+// Orbital slots go to four slices of warps (warps 4q .. 4q+3 take slots q, q+4, ...), so the last
+// slices have the fewest; the first density chunks' bulk copies are issued by warps of those slices
+// (10-15, then 4): chunk i by the warp of prefetch index i.
+__device__ __forceinline__ int prefetch_index(int warp) {  // -1: no prefetch chunk
+  return warp >= 10 ? warp - 10 : warp == 4 ? 6 : -1;
+}
 __device__ __forceinline__ int epi_group(int warp) {  // -1: not an epilogue warp
   return warp < 4 ? 0 : (warp >= 6 && warp < 6 + 4 * (kEpiGroups - 1)) ? 1 + ((warp - 6) >> 2) : -1;
 }
@@ -414,7 +420,7 @@ __device__ __forceinline__ void add_image_fast(const GTabs &g, const float2 *__r
 
 // ------------------------------------------------------------------------------ brick metadata
 constexpr int kMaxStages = 6;
-static_assert(kLoaderWarps >= kMaxStages, "one loader warp per prefetched stage");
+static_assert(kMaxStages <= 7, "one prefetch warp per prefetched stage");
 constexpr int kMaxChunks = kNPMAX / kRC;
 constexpr int kPlanWords = 1536;  // prefetch buffer of a brick plan record (6 KB); larger records take the slow path
 struct BrickSh {
@@ -1025,7 +1031,7 @@ __global__ void __launch_bounds__(kT, 1)
       // (one chunk per loader warp: a warp issuing a chunk's bulk copies spends about as long as
       // a quarter of the orbital evaluation)
       if (do_rho) {
-        const int li = loader_index(warp);
+        const int li = prefetch_index(warp);
         if (li >= 0 && li < nch && li < nstages) issue_copies(S, li, (G + li) % nstages, NP, na);
       }
       // ---- phase A: scaled orbitals of all atoms at every point -> P (hi, lo), zero padding
