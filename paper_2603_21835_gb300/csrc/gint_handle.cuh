@@ -57,8 +57,8 @@ struct gint_handle {
   long long ntile_elems = 0;
   // D tiles in 128-byte core-matrix order: rows roundup(norb(I), 8), K = porb(J) (zero padded);
   // *_h2 hold the same tiles halved (diagonal chunk of the density pass)
-  __half *Dt_hi = nullptr, *Dt_lo = nullptr, *Dt_hi2 = nullptr, *Dt_lo2 = nullptr;
-  __half *zero_dev = nullptr;  // 256 zero bytes: source of the bulk copies for absent tiles
+  __half *Dt_hl = nullptr, *Dt_hl2 = nullptr;  // D tiles (hi, lo interleaved per 8 x 8 block), halved copy
+  __half *zero_dev = nullptr;  // 512 zero bytes: source of the bulk copies for absent tiles
   long long *tile_off_dev = nullptr;
   float *scales = nullptr;    // device: [0] S_phi, [1] S_D (density), [2] S_Q (local H)
   int max_brick_porb = 0;     // largest padded (aligned) orbital count of a brick

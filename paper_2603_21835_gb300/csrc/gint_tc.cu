@@ -760,7 +760,7 @@ struct GSys {
   GNbr nb;
   const float2 *tab;                         // float32 knot table of this system's handle
   const float2 *tabi;                        // its interleaved copy (shaped species)
-  const __half *Dhi, *Dlo, *Dhi2, *Dlo2;     // D tiles (density / force items)
+  const __half *Dhl, *Dhl2;                 // D tiles, hi and lo 8 x 8 blocks interleaved (and halved)
   const long long *tile_off;
   const float *scales;                       // [0] S_phi, [1] S_D, [2] S_Q
   const double *V;                           // NULL: no local-H items, zero force weight
@@ -796,9 +796,10 @@ __device__ __forceinline__ int batch_sys(const GBatch &B, long long it) {
 // ------------------------------------------------------------------------------ brick kernel
 // One persistent CTA per SM walks the batch's items.  Dynamic shared memory is used by either
 // kind of item:
-//   density: P (hi, lo) [128 x np_max] | nstages x B stage (hi, lo) [np_max x 16]
+//   density: P (hi, lo) [128 x np_max] | nstages x B stage [np_max x 16] (hi and lo interleaved)
 //     P element (p, k): (p/8)*16*np_max + (k/8)*128 + (p%8)*16 + (k%8)*2
-//     B element (r, j): (r/8)*256 + (j/8)*128 + (r%8)*16 + (j%8)*2
+//     B element (r, j) of part h (0 hi, 1 lo): (r/8)*512 + (j/8)*256 + h*128 + (r%8)*16 + (j%8)*2
+//     (the layout of a row group of a 16-column tile in the interleaved tile store)
 //   local H: 2 stages of A hi, A lo, B hi, B lo, each [np_max rows x 32 points]
 //     element (r, p): (r/8)*576 + (p/8)*144 + (r%8)*16 + (p%8)*2, plus a tail pad for the rows
 //     above NP that the last 128-row A tile reads (they only feed output rows that are ignored).
@@ -868,20 +869,18 @@ __global__ void __launch_bounds__(kT, 1)
       mbar_arrive_cnt(&sh.full[s], kLoaderWarps - 1);
     }
     __syncwarp();
-    unsigned char *Bh = B0 + s * 2 * bop, *Bl = Bh + bop;
+    unsigned char *Bs = B0 + s * 2 * bop;
     const int ca = sh.col2slot[c * kRC];
     if (ca != kNoSlot && sh.s_po[ca] == 16 && sh.s_pcol[ca] == c * kRC) {
-      // the chunk is one 16-column atom: a row group of the stage (256 bytes: segment-major 8 x 8
-      // blocks) is laid out like a row group of a 16-column tile, so whole tiles copy as they are,
+      // the chunk is one 16-column atom: a row group of the stage (512 bytes: segment-major pairs of
+      // hi and lo 8 x 8 blocks) is laid out like a row group of a 16-column tile in the interleaved
+      // store, so whole tiles copy as they are (hi and lo in one copy),
       // and slots that are adjacent in the brick's rows and in the column-atom-major tile store
       // form one copy.  Gap rows and absent tiles are zero-filled per row group.
       // one lane per slot (windows of 32 slots): a slot continues the previous slot's run if
       // both have present, non-diagonal tiles that are adjacent in rows and in the tile store
       auto zero_rows = [&](int r0, int r1) {
-        for (int r = r0; r < r1; r += 8) {
-          bulk_g2s(Bh + (r - rowbase) * 32, zero, 256, &sh.full[s]);
-          bulk_g2s(Bl + (r - rowbase) * 32, zero, 256, &sh.full[s]);
-        }
+        for (int r = r0; r < r1; r += 8) bulk_g2s(Bs + (r - rowbase) * 64, zero, 512, &sh.full[s]);
       };
       for (int base = 0; base < na; base += 32) {
         const int bs = base + lane;
@@ -905,8 +904,7 @@ __global__ void __launch_bounds__(kT, 1)
           if (tile < 0) {
             zero_rows(pc, endrow);
           } else if (diag) {  // the chunk's own block: halved tiles
-            bulk_g2s(Bh + (pc - rowbase) * 32, S.Dhi2 + tile, (uint32_t)po * 32, &sh.full[s]);
-            bulk_g2s(Bl + (pc - rowbase) * 32, S.Dlo2 + tile, (uint32_t)po * 32, &sh.full[s]);
+            bulk_g2s(Bs + (pc - rowbase) * 64, S.Dhl2 + 2 * (long long)tile, (uint32_t)po * 64, &sh.full[s]);
           }
         }
         // the last slot of a run ends where the next boundary starts
@@ -914,15 +912,13 @@ __global__ void __launch_bounds__(kT, 1)
         const int last = later ? lane + __ffs(later) - 1 : 31;
         const int run_end = __shfl_sync(0xffffffffu, endrow, last);
         if (run_ok && !cont) {
-          const uint32_t bytes = (uint32_t)(run_end - pc) * 32;
-          bulk_g2s(Bh + (pc - rowbase) * 32, S.Dhi + tile, bytes, &sh.full[s]);
-          bulk_g2s(Bl + (pc - rowbase) * 32, S.Dlo + tile, bytes, &sh.full[s]);
+          bulk_g2s(Bs + (pc - rowbase) * 64, S.Dhl + 2 * (long long)tile, (uint32_t)(run_end - pc) * 64, &sh.full[s]);
         }
       }
       __syncwarp();
       return;
     }
-    // general chunk (8-column atoms): one copy per row group and column segment
+    // general chunk (8-column atoms): one copy (hi and lo block) per row group and column segment
     for (int u = lane; u < ngroups * 2; u += 32) {
       const int gr = u >> 1, sg = u & 1;
       const int k0 = rowbase + 8 * gr, j0 = c * kRC + 8 * sg;
@@ -935,8 +931,7 @@ __global__ void __launch_bounds__(kT, 1)
           src = (long long)tile + (long long)((kl0 >> 3) * (sh.s_po[as] >> 3) + ((j0 - sh.s_pcol[as]) >> 3)) * 64;
       }
       const bool diag = !FORCE && gr < 2;
-      bulk_g2s(Bh + gr * 256 + sg * 128, src < 0 ? zero : (diag ? S.Dhi2 : S.Dhi) + src, 128u, &sh.full[s]);
-      bulk_g2s(Bl + gr * 256 + sg * 128, src < 0 ? zero : (diag ? S.Dlo2 : S.Dlo) + src, 128u, &sh.full[s]);
+      bulk_g2s(Bs + gr * 512 + sg * 256, src < 0 ? zero : (diag ? S.Dhl2 : S.Dhl) + 2 * src, 256u, &sh.full[s]);
     }
   };
   // chunk c's B panel by the loader threads (lt = 0 .. 32 kLoaderWarps - 1), 16-byte pieces with
@@ -956,17 +951,17 @@ __global__ void __launch_bounds__(kT, 1)
         const int rr = u - seg * nrows, r = rowbase + rr;
         const int h = seg >> 1, sg = seg & 1;
         const int j0 = c * kRC + 8 * sg;
-        dst[i] = h * (int)bop + (rr >> 3) * 256 + sg * 128 + (rr & 7) * 16;
+        dst[i] = (rr >> 3) * 512 + sg * 256 + h * 128 + (rr & 7) * 16;
         const int bs = sh.col2slot[r], as = sh.col2slot[j0];
         if (bs != kNoSlot && as != kNoSlot) {
           const int tile = sh.s_tile[bs * na + as];
           if (tile >= 0) {
             const int kl = r - sh.s_pcol[bs];
-            const long long src = (long long)tile +
-                                  (long long)((kl >> 3) * (sh.s_po[as] >> 3) + ((j0 - sh.s_pcol[as]) >> 3)) * 64 +
-                                  (kl & 7) * 8;
+            const long long src =
+                2 * ((long long)tile + (long long)((kl >> 3) * (sh.s_po[as] >> 3) + ((j0 - sh.s_pcol[as]) >> 3)) * 64) +
+                h * 64 + (kl & 7) * 8;
             const bool diag = !FORCE && rr < kRC;
-            const __half *base = h ? (diag ? S.Dlo2 : S.Dlo) : (diag ? S.Dhi2 : S.Dhi);
+            const __half *base = diag ? S.Dhl2 : S.Dhl;
             v[i] = __ldg(reinterpret_cast<const uint4 *>(base + src));
           }
         }
@@ -1098,8 +1093,8 @@ __global__ void __launch_bounds__(kT, 1)
           unsigned *errp = S.err;
           uint32_t s = G % nstages, fph = (G / nstages) & 1u;
           const uint64_t dah0 = sdesc(smem_u32(Ph), 128, sboP), dal0 = sdesc(smem_u32(Pl), 128, sboP);
-          const uint64_t dbh0 = sdesc(smem_u32(B0), 128, 256);
-          const uint32_t sstep = (2 * bop) >> 4, lstep = bop >> 4;
+          const uint64_t dbh0 = sdesc(smem_u32(B0), 256, 512);
+          const uint32_t sstep = (2 * bop) >> 4, lstep = 128 >> 4;
           tc_fence_after();  // after the barrier that ended the previous item's tensor-memory reads
           for (int c = 0; c < nch; ++c) {
             if (!mbar_wait(&sh.full[s], fph, errp)) ok = false;
@@ -1122,7 +1117,7 @@ __global__ void __launch_bounds__(kT, 1)
           for (int c = 0; c < nch; ++c) {
             if (!mbar_wait(&sh.full[s], fph, errp)) ok = false;
             tc_fence_after();
-            unsigned char *Bh = B0 + s * 2 * bop, *Bl = Bh + bop;
+            unsigned char *Bh = B0 + s * 2 * bop, *Bl = Bh + 128;
             const int rowbase = FORCE ? 0 : c * kRC;
             const int N = NP - rowbase;
             const uint64_t dah = sdesc(smem_u32(Ph) + (c * kRC / 8) * 128, 128, sboP);
@@ -1130,8 +1125,8 @@ __global__ void __launch_bounds__(kT, 1)
             for (int n0 = 0; n0 < N; n0 += 256) {
               const int nn = min(256, N - n0);
               const uint32_t id = idesc_f16(128, nn);
-              const uint64_t dbh = sdesc(smem_u32(Bh) + (n0 >> 3) * 256, 128, 256);
-              const uint64_t dbl = sdesc(smem_u32(Bl) + (n0 >> 3) * 256, 128, 256);
+              const uint64_t dbh = sdesc(smem_u32(Bh) + (n0 >> 3) * 512, 256, 512);
+              const uint64_t dbl = sdesc(smem_u32(Bl) + (n0 >> 3) * 512, 256, 512);
               const uint32_t dm = tmem + rowbase + n0, dc = tmem + corr_base + rowbase + n0;
               mma_f16(dm, dah, dbh, id, c > 0 ? 1u : 0u);
               if (split3) {
@@ -1620,7 +1615,7 @@ struct GTileSys {
   const long long *pair_off, *tile_off;
   const int *species;
   const float *scales;
-  __half *Dhi, *Dlo, *Dhi2, *Dlo2;
+  __half *Dhl, *Dhl2;  // interleaved: 8 x 8 block b of the tile has hi at 128 b, lo at 128 b + 64
 };
 struct GTile {
   int nsys;
@@ -1651,15 +1646,16 @@ __global__ void k_build_tiles(const __grid_constant__ GTabs g, const __grid_cons
   for (int e = threadIdx.x; e < rI * pJ; e += blockDim.x) {
     const int cm = e >> 6, w = e & 63;
     const int i = (cm / sJ) * 8 + (w >> 3), j = (cm % sJ) * 8 + (w & 7);
+    const long long q = 2 * to + (long long)cm * 128 + w;  // hi element; lo 64 halves later
     if (i < nI && j < nJ) {
       const double x = S.D[o + (long long)i * nJ + j] * sc;
       const __half h = __float2half_rn((float)x), h2 = __float2half_rn((float)(0.5 * x));
-      S.Dhi[to + e] = h;
-      S.Dlo[to + e] = __float2half_rn((float)(x - (double)__half2float(h)));
-      S.Dhi2[to + e] = h2;
-      S.Dlo2[to + e] = __float2half_rn((float)(0.5 * x - (double)__half2float(h2)));
+      S.Dhl[q] = h;
+      S.Dhl[q + 64] = __float2half_rn((float)(x - (double)__half2float(h)));
+      S.Dhl2[q] = h2;
+      S.Dhl2[q + 64] = __float2half_rn((float)(0.5 * x - (double)__half2float(h2)));
     } else {
-      S.Dhi[to + e] = S.Dlo[to + e] = S.Dhi2[to + e] = S.Dlo2[to + e] = __float2half(0.f);
+      S.Dhl[q] = S.Dhl[q + 64] = S.Dhl2[q] = S.Dhl2[q + 64] = __float2half(0.f);
     }
   }
 }
@@ -1813,10 +1809,8 @@ void gint_tc_free(gint_handle *h) {
   h->tc_bytes = 0;
   dfree(h->plan);
   dfree(h->plan_off_dev);
-  dfree(h->Dt_hi);
-  dfree(h->Dt_lo);
-  dfree(h->Dt_hi2);
-  dfree(h->Dt_lo2);
+  dfree(h->Dt_hl);
+  dfree(h->Dt_hl2);
   dfree(h->zero_dev);
   dfree(h->tile_off_dev);
   dfree(h->scales);
@@ -1857,15 +1851,14 @@ int gint_tc_prepare(gint_handle *h) {
   }
   h->ntile_elems = h->tile_off[h->npairs];
   const size_t tbytes = std::max<long long>(h->ntile_elems, 64) * sizeof(__half);
-  if (cudaMalloc(&h->Dt_hi, tbytes) != cudaSuccess || cudaMalloc(&h->Dt_lo, tbytes) != cudaSuccess ||
-      cudaMalloc(&h->Dt_hi2, tbytes) != cudaSuccess || cudaMalloc(&h->Dt_lo2, tbytes) != cudaSuccess ||
-      cudaMalloc(&h->zero_dev, 256) != cudaSuccess ||
+  if (cudaMalloc(&h->Dt_hl, 2 * tbytes) != cudaSuccess || cudaMalloc(&h->Dt_hl2, 2 * tbytes) != cudaSuccess ||
+      cudaMalloc(&h->zero_dev, 512) != cudaSuccess ||
       cudaMalloc(&h->tile_off_dev, (h->npairs + 1) * sizeof(long long)) != cudaSuccess ||
       cudaMalloc(&h->scales, 8 * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
     return GINT_ENOMEM;
   }
-  TC_CHECK(cudaMemset(h->zero_dev, 0, 256));
+  TC_CHECK(cudaMemset(h->zero_dev, 0, 512));
   TC_CHECK(cudaMemset(h->scales, 0, 8 * sizeof(float)));
   TC_CHECK(cudaMemcpy(h->tile_off_dev, h->tile_off.data(), (h->npairs + 1) * sizeof(long long),
                       cudaMemcpyHostToDevice));
@@ -1952,7 +1945,7 @@ int gint_tc_prepare(gint_handle *h) {
     cudaGetLastError();
     return GINT_ENOMEM;
   }
-  h->tc_bytes = 4 * (long long)tbytes + 256 + (h->npairs + 1) * (long long)sizeof(long long) + 8 * sizeof(float) +
+  h->tc_bytes = 4 * (long long)tbytes + 512 + (h->npairs + 1) * (long long)sizeof(long long) + 8 * sizeof(float) +
                 (nb + 1) * (long long)sizeof(long long) + std::max<long long>(h->hs_elems, 1) * (long long)sizeof(float) +
                 (long long)std::max<size_t>(upair.size(), 1) * (long long)sizeof(int) +
                 (long long)(uoff.size() + src.size()) * (long long)sizeof(long long);
@@ -1985,7 +1978,7 @@ int gint_tc_prepare(gint_handle *h) {
 
 int gint_tc_check_capacity(const gint_handle *h) {
   if (h->max_brick_porb > kNPMAX || h->max_brick_atoms > kMAXA || h->max_brick_ent > kMAXE ||
-      h->max_species_norb > GINT_MAX_ORB_ATOM || h->ntile_elems > 0x7fffffffLL || !h->Dt_hi)
+      h->max_species_norb > GINT_MAX_ORB_ATOM || h->ntile_elems > 0x7fffffffLL || !h->Dt_hl)
     return GINT_ECAPACITY;
   return GINT_OK;
 }
@@ -2036,10 +2029,8 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
       ts.tile_off = h->tile_off_dev;
       ts.species = h->species_dev;
       ts.scales = h->scales;
-      ts.Dhi = h->Dt_hi;
-      ts.Dlo = h->Dt_lo;
-      ts.Dhi2 = h->Dt_hi2;
-      ts.Dlo2 = h->Dt_lo2;
+      ts.Dhl = h->Dt_hl;
+      ts.Dhl2 = h->Dt_hl2;
       pairs += h->npairs;
     }
     GSys &S = B.sys[i];
@@ -2047,10 +2038,8 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
     S.nb = h->nbr();
     S.tab = h->tab32;
     S.tabi = h->tab32i;
-    S.Dhi = h->Dt_hi;
-    S.Dlo = h->Dt_lo;
-    S.Dhi2 = h->Dt_hi2;
-    S.Dlo2 = h->Dt_lo2;
+    S.Dhl = h->Dt_hl;
+    S.Dhl2 = h->Dt_hl2;
     S.tile_off = h->tile_off_dev;
     S.scales = h->scales;
     S.V = T.V;
