@@ -11,16 +11,17 @@
 // Layout: the orbitals of each atom occupy porb = roundup(norb, 8) columns of the brick's
 // orbital space (zero padded), no atom crosses a multiple of 128 columns, NP = padded total.
 // D is pre-tiled per atom pair into float16 (hi, lo) 128-byte core matrices, stored
-// column-atom-major, so the B operand of a chunk that is one 16-column atom arrives in a few bulk
-// (TMA) copies: one per run of row atoms that are adjacent in the brick and in the tile store.
+// column-atom-major with the hi and lo 8 x 8 blocks interleaved, so the B operand of a chunk that is
+// one 16-column atom arrives in a few bulk (TMA) copies: one per run of row atoms that are adjacent
+// in the brick and in the tile store.
 //
 // Density (D symmetric): columns are streamed in chunks of 16.  With the chunk's own
 // diagonal block halved, rho = 2 sum_k P_k Y_k where Y_k accumulates P_j D_jk over the chunks
 // j <= chunk(k) only, so chunk c's columns are final right after chunk c's MMA: the epilogue of
-// chunk c overlaps the MMA of chunk c+1 and the MMA work is halved.  Within a brick the first
-// stages arrive by bulk copies during the orbital evaluation; then seven loader warps load the
-// chunk whose stage has just been freed, one MMA thread issues, and eight epilogue warps drain
-// finished chunks, all decoupled by mbarriers.
+// chunk c overlaps the MMA of chunk c+1 and the MMA work is halved.  Seven prefetch warps issue
+// the chunks' bulk copies, chunk k by warp k mod 7 (the first stages during the orbital evaluation,
+// each later chunk as soon as its stage is freed), one MMA thread issues, and eight epilogue warps
+// drain finished chunks, all decoupled by mbarriers.
 // Force: full Y = P D (all chunks, all columns), then per atom 2 w V grad(phi) . Y.
 // Local H from the same orbital tile P: H = (W P)^T P with K = grid points (blocks of 16-32),
 // M = N = orbitals (128-row tiles, upper block triangle); both operands are MN-major views of
@@ -50,17 +51,12 @@ constexpr int kRC = 16;          // density chunk width (one f16 K step)
 constexpr long long kWaitNs = 2000000000LL;  // bounded mbarrier waits: 2 s
 constexpr unsigned char kNoSlot = 255;
 constexpr int kMmaWarp = 5;  // lane 0 issues the density MMAs
-// density phase B roles: epilogue groups of four warps (warps 0-3, 6-9, ...), the MMA warp (5),
-// and the loader warps (4 and every warp after the epilogue groups)
+// density phase B roles: epilogue groups of four warps (warps 0-3, 6-9), the MMA warp (5), and the
+// prefetch warps (10-15, 4) that issue the bulk copies of the D chunks.  Orbital slots go to four
+// slices of warps (warps 4q .. 4q+3 take slots q, q+4, ...), so the last slices have the fewest: the
+// prefetch warps are taken from those.  Chunk k goes to the warp of prefetch index k mod 7 (the
+// first chunks during the orbital evaluation, the others once their stage is free).
 constexpr int kEpiGroups = 2, kEpiWarps = 4 * kEpiGroups;
-constexpr int kLoaderWarps = 16 - 1 - kEpiWarps;
-constexpr int kMaxPieces = (4 * kNPMAX + 32 * kLoaderWarps - 1) / (32 * kLoaderWarps);  // per loader thread
-__device__ __forceinline__ int loader_index(int warp) {  // -1: not a loader warp
-  return warp == 4 ? 0 : warp >= 6 + 4 * (kEpiGroups - 1) ? warp - (6 + 4 * (kEpiGroups - 1)) + 1 : -1;
-}
-// Orbital slots go to four slices of warps (warps 4q .. 4q+3 take slots q, q+4, ...), so the last
-// slices have the fewest; the first density chunks' bulk copies are issued by warps of those slices
-// (10-15, then 4): chunk i by the warp of prefetch index i.
 __device__ __forceinline__ int prefetch_index(int warp) {  // -1: no prefetch chunk
   return warp >= 10 ? warp - 10 : warp == 4 ? 6 : -1;
 }
@@ -103,10 +99,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsign
   }
   return true;
 }
-__device__ __forceinline__ void mbar_arrive_cnt(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) { mbar_arrive_cnt(bar, 1u); }
 __device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
@@ -420,7 +412,8 @@ __device__ __forceinline__ void add_image_fast(const GTabs &g, const float2 *__r
 
 // ------------------------------------------------------------------------------ brick metadata
 constexpr int kMaxStages = 6;
-static_assert(kMaxStages <= 7, "one prefetch warp per prefetched stage");
+constexpr int kPrefetchWarps = 7;  // warps 10-15 and 4
+static_assert(kMaxStages <= kPrefetchWarps, "one prefetch warp per prefetched stage");
 constexpr int kMaxChunks = kNPMAX / kRC;
 constexpr int kPlanWords = 1536;  // prefetch buffer of a brick plan record (6 KB); larger records take the slow path
 struct BrickSh {
@@ -837,7 +830,7 @@ __global__ void __launch_bounds__(kT, 1)
     sh.plan_pref = 1;
   };
   if (t == 0) {
-    for (int s = 0; s < kMaxStages; ++s) mbar_init(&sh.full[s], kLoaderWarps);
+    for (int s = 0; s < kMaxStages; ++s) mbar_init(&sh.full[s], 1);
     for (int c = 0; c < kMaxChunks; ++c) mbar_init(&sh.done[c], 1);
     mbar_init(&sh.hdone[0], 1);
     mbar_init(&sh.hdone[1], 1);
@@ -864,10 +857,7 @@ __global__ void __launch_bounds__(kT, 1)
   auto issue_copies = [&](const GSys &S, int c, int s, int NP, int na) {
     const int rowbase = FORCE ? 0 : c * kRC;
     const int ngroups = (NP - rowbase) >> 3;
-    if (lane == 0) {  // one arrival with the transaction count stands for the loader warps' arrivals
-      mbar_arrive_tx(&sh.full[s], (uint32_t)ngroups * 2 * 256);
-      mbar_arrive_cnt(&sh.full[s], kLoaderWarps - 1);
-    }
+    if (lane == 0) mbar_arrive_tx(&sh.full[s], (uint32_t)ngroups * 512);  // the stage's one arrival
     __syncwarp();
     unsigned char *Bs = B0 + s * 2 * bop;
     const int ca = sh.col2slot[c * kRC];
@@ -934,46 +924,6 @@ __global__ void __launch_bounds__(kT, 1)
       bulk_g2s(Bs + gr * 512 + sg * 256, src < 0 ? zero : (diag ? S.Dhl2 : S.Dhl) + 2 * src, 256u, &sh.full[s]);
     }
   };
-  // chunk c's B panel by the loader threads (lt = 0 .. 32 kLoaderWarps - 1), 16-byte pieces with
-  // rows on consecutive threads (eight threads read one core matrix): gather_chunk issues the global
-  // loads into registers (no stage needed yet), scatter_chunk stores them into the freed stage.
-  auto gather_chunk = [&](const GSys &S, int c, int NP, int na, int lt, uint4 (&v)[kMaxPieces],
-                          int (&dst)[kMaxPieces]) {
-    const int rowbase = FORCE ? 0 : c * kRC;
-    const int nrows = NP - rowbase;
-#pragma unroll
-    for (int i = 0; i < kMaxPieces; ++i) {
-      const int u = lt + i * kLoaderWarps * 32;
-      v[i] = make_uint4(0u, 0u, 0u, 0u);
-      dst[i] = -1;
-      if (u < 4 * nrows) {
-        const int seg = (u >= nrows) + (u >= 2 * nrows) + (u >= 3 * nrows);  // 2 h + column segment
-        const int rr = u - seg * nrows, r = rowbase + rr;
-        const int h = seg >> 1, sg = seg & 1;
-        const int j0 = c * kRC + 8 * sg;
-        dst[i] = (rr >> 3) * 512 + sg * 256 + h * 128 + (rr & 7) * 16;
-        const int bs = sh.col2slot[r], as = sh.col2slot[j0];
-        if (bs != kNoSlot && as != kNoSlot) {
-          const int tile = sh.s_tile[bs * na + as];
-          if (tile >= 0) {
-            const int kl = r - sh.s_pcol[bs];
-            const long long src =
-                2 * ((long long)tile + (long long)((kl >> 3) * (sh.s_po[as] >> 3) + ((j0 - sh.s_pcol[as]) >> 3)) * 64) +
-                h * 64 + (kl & 7) * 8;
-            const bool diag = !FORCE && rr < kRC;
-            const __half *base = diag ? S.Dhl2 : S.Dhl;
-            v[i] = __ldg(reinterpret_cast<const uint4 *>(base + src));
-          }
-        }
-      }
-    }
-  };
-  auto scatter_chunk = [&](int s, const uint4 (&v)[kMaxPieces], const int (&dst)[kMaxPieces]) {
-    unsigned char *Bs = B0 + s * 2 * bop;
-#pragma unroll
-    for (int i = 0; i < kMaxPieces; ++i)
-      if (dst[i] >= 0) *reinterpret_cast<uint4 *>(Bs + dst[i]) = v[i];
-  };
   for (;;) {
     __syncthreads();
     const long long it = sh.item;
@@ -1023,8 +973,8 @@ __global__ void __launch_bounds__(kT, 1)
       }
       const int nch = NP / kRC;
       // the previous item's MMAs are complete: every stage is free, prefetch the first density chunks
-      // (one chunk per loader warp: a warp issuing a chunk's bulk copies spends about as long as
-      // a quarter of the orbital evaluation)
+      // (one chunk per prefetch warp: a warp issuing a chunk's bulk copies spends a sizeable part of
+      // the orbital evaluation on it)
       if (do_rho) {
         const int li = prefetch_index(warp);
         if (li >= 0 && li < nch && li < nstages) issue_copies(S, li, (G + li) % nstages, NP, na);
@@ -1081,7 +1031,7 @@ __global__ void __launch_bounds__(kT, 1)
       fence_async_smem();
       __syncthreads();
       if (do_rho) {
-      // ---- phase B: chunks of 16 columns, loader warps / MMA thread / epilogue warps
+      // ---- phase B: chunks of 16 columns, prefetch warps / MMA thread / epilogue warps
       const uint32_t corr_base = (NP <= 256) ? 256u : 0u;  // separate correction accumulator if it fits
       if (warp == kMmaWarp) {
         if (lane == 0 && NP <= 256 && split3 && corr_base) {
@@ -1142,22 +1092,15 @@ __global__ void __launch_bounds__(kT, 1)
           }
         }
         __syncwarp();
-      } else if (loader_index(warp) >= 0) {
-        // loader warps: gather chunk c + nstages into registers, then once chunk c's MMAs are done
-        // (its stage is free) store it there
-        const int lt = loader_index(warp) * 32 + lane;
+      } else if (prefetch_index(warp) >= 0) {
+        // prefetch warps, later chunks: chunk k (k mod kPrefetchWarps = the warp's prefetch index),
+        // its bulk copies issued once chunk k - nstages's MMAs are done (the stage is free)
         unsigned *errp = S.err;
-        int sl = (int)(G % nstages);  // stage of chunk c (and of chunk c + nstages)
-        uint4 v[kMaxPieces];
-        int dst[kMaxPieces];
-        for (int c = 0; c + nstages < nch; ++c) {
-          gather_chunk(S, c + nstages, NP, na, lt, v, dst);
-          if (!mbar_wait(&sh.done[c], (dpar >> c) & 1u, errp)) ok = false;
-          scatter_chunk(sl, v, dst);
-          fence_async_smem();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sh.full[sl]);
-          if (++sl == nstages) sl = 0;
+        const int li = prefetch_index(warp);
+        for (int k = nstages + ((li - nstages) % kPrefetchWarps + kPrefetchWarps) % kPrefetchWarps; k < nch;
+             k += kPrefetchWarps) {
+          if (!mbar_wait(&sh.done[k - nstages], (dpar >> (k - nstages)) & 1u, errp)) ok = false;
+          issue_copies(S, k, (int)((G + k) % nstages), NP, na);
         }
       } else if (!FORCE) {
         // density epilogue groups (each covers the 128 lanes) drain finished chunks round robin
