@@ -14,6 +14,11 @@
  *                  (the density formula of Sec. 3.3.1 with rho_{mu nu}(R) summed over R)
  *   local H        H_{mu nu} = sum_g w V(r_g) Phi_mu(r_g) Phi_nu(r_g)
  *                  (the local-potential matrix element formula of Sec. 3.3.1, w = Delta V)
+ *   local H(R)     H_{mu nu}(R) = sum over grid points of all space of w V phi_mu(r - tau_I)
+ *                  phi_nu(r - tau_J - R) (the same formula with the lattice vector R kept apart,
+ *                  Sec. 2 H(R) and its Bloch sum H(k) = sum_R e^{ik.R} H(R)); by the periodicity of
+ *                  V: sum over cell points g and image pairs (I at tau_I + n_I A, J at tau_J + n_J A)
+ *                  with n_J - n_I = R
  *   local Pulay    F_I = - dE/dtau_I, E = sum_g w V(r_g) rho(r_g) at fixed V, which is the
  *   force          local Pulay force formula of Sec. 3.3.1:
  *                  F_I = sum_g w V_g sum_{mu in I} grad Phi_mu(r_g) sum_nu (D_mu nu + D_nu mu) Phi_nu(r_g)
@@ -377,6 +382,93 @@ int orc_vlocal_block(const orc_sys *s, const double *V, int I, int J, double *ou
     for (int e = 0; e < nI * nJ; ++e) out[e] += acc[e];
     free(acc);
   }
+  return 0;
+}
+
+/* The lattice images of atom a whose support covers r: n_out[k] (image at tau_a + n A) and the
+ * image's orbitals phi_out[k][norb(a)], k < returned count (at most ORC_MAXIMG). */
+#define ORC_MAXIMG 64
+static int atom_images(const orc_sys *s, const double inv[9], int a, const double r[3], int n_out[][3],
+                       double *phi_out) {
+  int sp = s->species[a];
+  int no = orc_species_norb(s, sp);
+  double rc = species_rcut(s, sp);
+  double d0[3], u[3], reach[3], tmpg[64 * 3];
+  for (int c = 0; c < 3; ++c) d0[c] = r[c] - s->pos[3 * a + c];
+  for (int c = 0; c < 3; ++c) {
+    u[c] = d0[0] * inv[0 * 3 + c] + d0[1] * inv[1 * 3 + c] + d0[2] * inv[2 * 3 + c];
+    reach[c] = rc * sqrt(inv[0 * 3 + c] * inv[0 * 3 + c] + inv[1 * 3 + c] * inv[1 * 3 + c] +
+                         inv[2 * 3 + c] * inv[2 * 3 + c]);
+  }
+  int cnt = 0;
+  for (int n0 = (int)ceil(u[0] - reach[0]); n0 <= (int)floor(u[0] + reach[0]); ++n0)
+    for (int n1 = (int)ceil(u[1] - reach[1]); n1 <= (int)floor(u[1] + reach[1]); ++n1)
+      for (int n2 = (int)ceil(u[2] - reach[2]); n2 <= (int)floor(u[2] + reach[2]); ++n2) {
+        double d[3];
+        for (int c = 0; c < 3; ++c) d[c] = d0[c] - (n0 * s->cell[c] + n1 * s->cell[3 + c] + n2 * s->cell[6 + c]);
+        if (sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) >= rc || cnt == ORC_MAXIMG) continue;
+        double *ph = phi_out + (size_t)cnt * no;
+        memset(ph, 0, sizeof(double) * no);
+        memset(tmpg, 0, sizeof(tmpg));
+        add_species_orbitals(s, sp, d, ph, tmpg);
+        n_out[cnt][0] = n0;
+        n_out[cnt][1] = n1;
+        n_out[cnt][2] = n2;
+        ++cnt;
+      }
+  return cnt;
+}
+
+/* Blocks H_IJ(R) [nR][norb(I)][norb(J)] for the listed lattice vectors R (integer triplets in units
+ * of a1, a2, a3): every cell grid point, every pair of images (I at tau_I + n_I A, J at
+ * tau_J + n_J A) adds w V_g phi_I phi_J^T to R = n_J - n_I.  Products that belong to an R outside
+ * the list are summed in absolute value into *missed (zero when the list is complete). */
+int orc_vlocal_block_R(const orc_sys *s, const double *V, int I, int J, int nR, const int *R, double *out,
+                       double *missed) {
+  double inv[9], det;
+  inverse3(s->cell, inv, &det);
+  int nI = orc_species_norb(s, s->species[I]), nJ = orc_species_norb(s, s->species[J]);
+  double w = orc_weight(s);
+  long long ng = (long long)s->n1 * s->n2 * s->n3;
+  size_t blk = (size_t)nI * nJ;
+  memset(out, 0, sizeof(double) * blk * nR);
+  double miss = 0.0;
+#pragma omp parallel reduction(+ : miss)
+  {
+    double *pI = (double *)malloc(sizeof(double) * ORC_MAXIMG * 64);
+    double *pJ = (double *)malloc(sizeof(double) * ORC_MAXIMG * 64);
+    int (*nIm)[3] = malloc(sizeof(int[3]) * ORC_MAXIMG), (*nJm)[3] = malloc(sizeof(int[3]) * ORC_MAXIMG);
+    double *acc = (double *)calloc(blk * nR, sizeof(double));
+#pragma omp for schedule(static)
+    for (long long g = 0; g < ng; ++g) {
+      double r[3];
+      grid_point(s, g, r);
+      int ci = atom_images(s, inv, I, r, nIm, pI);
+      if (!ci) continue;
+      int cj = atom_images(s, inv, J, r, nJm, pJ);
+      if (!cj) continue;
+      double wv = w * V[g];
+      for (int a = 0; a < ci; ++a)
+        for (int b = 0; b < cj; ++b) {
+          int d0 = nJm[b][0] - nIm[a][0], d1 = nJm[b][1] - nIm[a][1], d2 = nJm[b][2] - nIm[a][2];
+          int k = 0;
+          while (k < nR && !(R[3 * k] == d0 && R[3 * k + 1] == d1 && R[3 * k + 2] == d2)) ++k;
+          const double *fa = pI + (size_t)a * nI, *fb = pJ + (size_t)b * nJ;
+          if (k == nR) {
+            for (int i = 0; i < nI; ++i)
+              for (int j = 0; j < nJ; ++j) miss += fabs(wv * fa[i] * fb[j]);
+            continue;
+          }
+          double *o = acc + (size_t)k * blk;
+          for (int i = 0; i < nI; ++i)
+            for (int j = 0; j < nJ; ++j) o[i * nJ + j] += wv * fa[i] * fb[j];
+        }
+    }
+#pragma omp critical
+    for (size_t e = 0; e < blk * nR; ++e) out[e] += acc[e];
+    free(pI); free(pJ); free(nIm); free(nJm); free(acc);
+  }
+  *missed = miss;
   return 0;
 }
 

@@ -74,6 +74,7 @@ def _load():
             lib.orc_rho.argtypes = [P, vp, ll, vp, vp]
             lib.orc_vlocal.argtypes = [P, vp, ll, vp, vp]
             lib.orc_vlocal_block.argtypes = [P, vp, ctypes.c_int, ctypes.c_int, vp]
+            lib.orc_vlocal_block_R.argtypes = [P, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp]
             lib.orc_force.argtypes = [P, vp, vp, ll, vp, vp, vp]
             lib.orc_count_pairs.argtypes = [P, ll, vp, vp, vp]
             lib.orc_num_threads.argtypes = []
@@ -177,6 +178,20 @@ class Oracle:
         out = np.zeros((nI, nJ))
         self.lib.orc_vlocal_block(ctypes.byref(self.s), _ptr(V), int(I), int(J), _ptr(out))
         return out
+
+    def vlocal_block_R(self, V: np.ndarray, I: int, J: int, R) -> tuple:
+        """H_IJ(R) for the listed lattice vectors R (integer triplets, units of the cell vectors):
+        the local-H block between atom I at tau_I and atom J at tau_J + R (paper Sec. 2, H(R)).
+        Returns (blocks [len(R), norb(I), norb(J)], missed): missed sums the absolute values of
+        products that belong to an R outside the list (zero when the list is complete)."""
+        V = np.ascontiguousarray(V, dtype=np.float64).reshape(-1)
+        R = np.ascontiguousarray(np.asarray(R, dtype=np.int32).reshape(-1, 3))
+        nI, nJ = self._norb_atom(I), self._norb_atom(J)
+        out = np.zeros((R.shape[0], nI, nJ))
+        missed = ctypes.c_double()
+        self.lib.orc_vlocal_block_R(ctypes.byref(self.s), _ptr(V), int(I), int(J), int(R.shape[0]), _ptr(R),
+                                    _ptr(out), ctypes.byref(missed))
+        return out, missed.value
 
     def force(self, D: np.ndarray, V: np.ndarray, idx: Optional[np.ndarray] = None,
               atoms: Optional[np.ndarray] = None) -> np.ndarray:
