@@ -295,6 +295,46 @@ def run_serving(args, prec, dev):
     return out
 
 
+def run_per_R(g, V, prec, steps, stream, flush, hbm_gbs):
+    """Local H per lattice vector, H_IJ(R), and its Bloch sum H(k) on the same workload (tensor-core
+    precisions): mean times of gint_vlocal_R (the brick pass and the per-(I, J, R) reduction) and of
+    gint_bloch (one k point), L2 flushed between steps."""
+    import torch
+
+    from paper_2603_21835_gb300 import gint as G
+
+    try:
+        keys, _ = g.layout_R()
+    except G.GintError as e:
+        return {"unavailable": str(e)}
+    HR = torch.empty(g.nblock_R, dtype=torch.float64, device=V.device)
+    Hk = torch.empty(2 * g.nblock, dtype=torch.float64, device=V.device)
+    kf = (0.25, 0.1, -0.3)
+    for _ in range(3):
+        g.vlocal_R(V, prec, out=HR, stream=stream)
+        g.bloch(HR, kf, out=Hk, stream=stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tr, tb = [], []
+    for k in range(steps):
+        flush.fill_(float(k))
+        ev[0].record(stream)
+        g.vlocal_R(V, prec, out=HR, stream=stream)
+        ev[1].record(stream)
+        g.bloch(HR, kf, out=Hk, stream=stream)
+        ev[2].record(stream)
+        ev[2].synchronize()
+        tr.append(ev[0].elapsed_time(ev[1]))
+        tb.append(ev[1].elapsed_time(ev[2]))
+    mr, mb = statistics.mean(tr), statistics.mean(tb)
+    W = g.stats()["W"]
+    bloch_bytes = 8 * (g.nblock_R + 2 * g.nblock)  # H(R) read once, H(k) (complex) written once
+    gbs = bloch_bytes / (mb * 1e-3) / 1e9
+    return {"keys": int(len(keys)), "elements": int(g.nblock_R), "kfrac": list(kf),
+            "ms_vlocal_R": mr, "vlocal_R_gpt_pair_s": W / (mr * 1e-3) / 1e9,
+            "ms_bloch": mb, "bloch_bytes": bloch_bytes, "bloch_gb_s": gbs,
+            "bloch_frac_of_hbm": gbs / hbm_gbs if hbm_gbs else None}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -455,6 +495,10 @@ def main():
     if rank == 0 and world == 1 and args.serve_requests > 0:
         serving = run_serving(args, prec, dev)
 
+    per_R = None
+    if rank == 0 and tensor:
+        per_R = run_per_R(g, V, prec, args.steps, stream, flush, peaks.get("hbm_gbs"))
+
     launches = KERNEL_LAUNCHES.get(args.precision)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -468,7 +512,7 @@ def main():
                    "parallelism": f"replicas{world}"},
         "ms_kernel": tdom, "ms_rho_alone": statistics.mean(t_rho), "ms_vlocal_alone": statistics.mean(t_h),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": launches * args.steps, "serving": serving,
+        "gpu_launches": launches * args.steps, "serving": serving, "per_R": per_R,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

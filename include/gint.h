@@ -127,6 +127,31 @@ int gint_rho(gint_handle *h, int precision, const double *D_blocks, double *rho,
 /* Local-Hamiltonian pass: H blocks (device, overwritten) from V [n1 n2 n3] (device). */
 int gint_vlocal(gint_handle *h, int precision, const double *V, double *H_blocks, void *stream);
 
+/* Local H per lattice vector (paper Sec. 2, H_{mu nu}(R); Sec. 3.3.1, the local-potential matrix
+ * element between phi_mu at tau_I and phi_nu at tau_J + R): keys (I, J, R) with
+ * R = n1 a1 + n2 a2 + n3 a3, one norb(I) x norb(J) row-major block per key, keys sorted by
+ * (I, J, n1, n2, n3); for each key (I, J, R) the key (J, I, -R) exists and H_JI(-R) = H_IJ(R)^T.
+ * Summed over R, the blocks of (I, J) give the Gamma-point block of gint_vlocal.
+ *
+ * gint_layout_R: host outputs (any may be NULL): the number of keys, the float64 elements of an
+ * H(R) array, and pointers to library-owned host arrays keys [nkeys][5] (I, J, n1, n2, n3) and
+ * key_off [nkeys + 1] (element offset of each block), valid until the positions change or the
+ * handle is destroyed.  The tables are built on the first call (synchronous).
+ * Returns GINT_EUNSUPPORTED when some brick sees two lattice images of one atom (a cell shorter
+ * than about twice the orbital cutoff plus a brick): there the brick tiles mix several R. */
+int gint_layout_R(gint_handle *h, int *nkeys, long long *nblock_elems, const int **keys, const long long **key_off);
+
+/* Local-Hamiltonian pass per lattice vector: H_R [nblock_elems of gint_layout_R] (device,
+ * overwritten) from V [n1 n2 n3] (device).  Tensor-core precisions only (GINT_F16X3, GINT_F16X1;
+ * others: GINT_EUNSUPPORTED): the same brick pass as gint_vlocal, reduced per (I, J, R). */
+int gint_vlocal_R(gint_handle *h, int precision, const double *V, double *H_R, void *stream);
+
+/* Bloch sum (paper Sec. 2): H_k = sum_R e^{i k.R} H(R) in the Gamma-point block layout of gint_vlocal,
+ * complex float64 interleaved (re, im): H_k [2 nblock] (device, overwritten), from H_R (device, as
+ * written by gint_vlocal_R).  kfrac [3] (host) is k in reciprocal-lattice units (k = kf1 b1 + kf2 b2 +
+ * kf3 b3, a_i . b_j = 2 pi delta_ij), so k.R = 2 pi (kf . n).  At kfrac = 0 it is the Gamma block. */
+int gint_bloch(gint_handle *h, const double *H_R, const double *kfrac, double *H_k, void *stream);
+
 /* Local Pulay forces F [natoms][3] (device, overwritten) = -dE/dtau for E = sum_g w V rho.
  * If rho is not NULL the density is written as well (same pass). */
 int gint_force(gint_handle *h, int precision, const double *D_blocks, const double *V, double *F, double *rho,

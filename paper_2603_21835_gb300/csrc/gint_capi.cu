@@ -55,6 +55,7 @@ void free_all(gint_handle *h) {
   dfree(h->s_atom); dfree(h->s_col); dfree(h->s_ent); dfree(h->e_shift); dfree(h->b_pair);
   dfree(h->D32); dfree(h->work_ctr); dfree(h->red); dfree(h->scal); dfree(h->err_word);
   gint_tc_free(h);
+  gint_hr_free(h);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   h->own_stream = nullptr;
 }
@@ -387,7 +388,7 @@ int gint_memory(const gint_handle *h, long long *device_bytes) {
   b += h->cap_slots * 8 + (h->cap_slots + 1) * L + h->cap_ent * 3 * (long long)sizeof(double) +
        h->cap_pairtab * 4;                                                                  // neighbours
   b += 1024 * (long long)sizeof(double) + 16 * (long long)sizeof(double) + 16 + h->nblock * 4 + 16;  // workspace
-  *device_bytes = b + h->tc_bytes;
+  *device_bytes = b + h->tc_bytes + h->r_bytes;
   return GINT_OK;
 }
 
@@ -402,6 +403,7 @@ int gint_set_positions(gint_handle *h, const double *pos_dev, void *stream) {
   if (rc) return rc;
   rc = gint_tc_prepare(h);
   if (rc) return rc;
+  gint_hr_free(h);  // H(R) keys follow the new images (rebuilt on first use)
   if (cudaMemcpyAsync(h->pos_host.data(), h->pos_dev, 3 * sizeof(double) * h->geom.natoms, cudaMemcpyDeviceToHost,
                       st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
@@ -435,6 +437,39 @@ int gint_vlocal(gint_handle *h, int precision, const double *V, double *H_blocks
     return gint_simt_vlocal(h, precision == GINT_FP64, V, H_blocks, st);
   }
   return gint_tc_vlocal(h, precision, V, H_blocks, st);  // every block element is written
+}
+
+int gint_layout_R(gint_handle *h, int *nkeys, long long *nblock_elems, const int **keys, const long long **key_off) {
+  if (!h) return GINT_EINVAL;
+  DeviceGuard guard(h->device);
+  const int rc = gint_hr_prepare(h);
+  if (rc) return rc;
+  if (nkeys) *nkeys = h->r_nkeys;
+  if (nblock_elems) *nblock_elems = h->r_nblock;
+  if (keys) *keys = h->r_keys_host.data();
+  if (key_off) *key_off = h->r_off_host.data();
+  return GINT_OK;
+}
+
+int gint_vlocal_R(gint_handle *h, int precision, const double *V, double *H_R, void *stream) {
+  if (!h || !V || !H_R) return GINT_EINVAL;
+  if (check_precision(precision)) return GINT_EINVAL;
+  if (precision != GINT_F16X3 && precision != GINT_F16X1) return GINT_EUNSUPPORTED;
+  DeviceGuard guard(h->device);
+  int rc = gint_hr_prepare(h);
+  if (rc) return rc;
+  h->reduce_R = true;
+  rc = gint_tc_vlocal(h, precision, V, H_R, (cudaStream_t)stream);  // every H(R) element is written
+  h->reduce_R = false;
+  return rc;
+}
+
+int gint_bloch(gint_handle *h, const double *H_R, const double *kfrac, double *H_k, void *stream) {
+  if (!h || !H_R || !kfrac || !H_k) return GINT_EINVAL;
+  DeviceGuard guard(h->device);
+  const int rc = gint_hr_prepare(h);
+  if (rc) return rc;
+  return gint_hr_bloch(h, H_R, kfrac, H_k, (cudaStream_t)stream);
 }
 
 int gint_force(gint_handle *h, int precision, const double *D_blocks, const double *V, double *F, double *rho,

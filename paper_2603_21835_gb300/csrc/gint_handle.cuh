@@ -73,6 +73,19 @@ struct gint_handle {
   uint4 *plan = nullptr;                  // per-brick plan records (brick metadata, prefetched by the kernel)
   long long *plan_off_dev = nullptr;      // [nbricks + 1] record offsets, 16-byte units
   long long tc_bytes = 0;                 // device bytes of the tensor-core workspace above
+  // local H per lattice vector (keys (I, J, R); built on first use by gint_hr_prepare)
+  bool r_ready = false;
+  int r_status = 0;           // GINT_OK, or why per-R output is unavailable for this geometry
+  bool reduce_R = false;      // the next local-H reduction writes H(R) blocks (set around one call)
+  int r_nkeys = 0, r_nupper = 0;
+  long long r_nblock = 0, r_bytes = 0;
+  std::vector<int> r_keys_host;         // [nkeys][5]: I, J, n1, n2, n3 (R = n1 a1 + n2 a2 + n3 a3)
+  std::vector<long long> r_off_host;    // [nkeys + 1] element offset of each H(R) block
+  int *r_kI = nullptr, *r_kJ = nullptr, *r_kT = nullptr, *r_kn = nullptr;
+  long long *r_koff = nullptr;
+  int *r_hu_key = nullptr;              // upper keys, each with its contributions:
+  long long *r_hu_off = nullptr, *r_hu_src = nullptr;
+  int *r_gk_off = nullptr;              // [npairs + 1]: keys of pair p are [gk_off[p], gk_off[p + 1])
   double *red = nullptr;      // reduction partials
   double *scal = nullptr;     // device scalars
   unsigned *err_word = nullptr;
@@ -114,3 +127,7 @@ int gint_tc_batch(const gint_task *tasks, int n, int precision, cudaStream_t st,
 int gint_tc_check_capacity(const gint_handle *h);
 int gint_tc_prepare(gint_handle *h);  // layouts and scratch of the tensor-core path (after neighbours)
 void gint_tc_free(gint_handle *h);
+// gint_hr.cu
+int gint_hr_prepare(gint_handle *h);  // key tables of H(R) (GINT_EUNSUPPORTED if tiles mix R)
+void gint_hr_free(gint_handle *h);
+int gint_hr_bloch(gint_handle *h, const double *HR, const double kf[3], double *Hk, cudaStream_t st);

@@ -1998,20 +1998,31 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
     B.start[i] = items;
     items += (dens || loc) ? h->geom.nbricks : 0;
     if (dens || loc) np = std::max(np, h->max_brick_porb);
-    if (loc && h->nupper > 0) {
+    if (loc && (h->reduce_R ? h->r_nupper : h->nupper) > 0) {
       R.start[nr] = uppers;
       GRedSys &rs = R.sys[nr++];
-      rs.hu_pair = h->hu_pair;
-      rs.hu_off = h->hu_off;
-      rs.hu_src = h->hu_src;
       rs.hs = h->hs;
-      rs.pair_I = h->pair_I_dev;
-      rs.pair_J = h->pair_col_dev;
-      rs.pair_T = h->pair_T_dev;
-      rs.pair_off = h->pair_off_dev;
       rs.species = h->species_dev;
       rs.H = T.H_blocks;
-      uppers += h->nupper;
+      if (h->reduce_R) {  // the same tiles keyed by (I, J, R): H(R) blocks
+        rs.hu_pair = h->r_hu_key;
+        rs.hu_off = h->r_hu_off;
+        rs.hu_src = h->r_hu_src;
+        rs.pair_I = h->r_kI;
+        rs.pair_J = h->r_kJ;
+        rs.pair_T = h->r_kT;
+        rs.pair_off = h->r_koff;
+        uppers += h->r_nupper;
+      } else {
+        rs.hu_pair = h->hu_pair;
+        rs.hu_off = h->hu_off;
+        rs.hu_src = h->hu_src;
+        rs.pair_I = h->pair_I_dev;
+        rs.pair_J = h->pair_col_dev;
+        rs.pair_T = h->pair_T_dev;
+        rs.pair_off = h->pair_off_dev;
+        uppers += h->nupper;
+      }
     }
   }
   B.nsys = n;

@@ -75,11 +75,15 @@ _lib.gint_grid_dot_noalloc.argtypes = [_vp, _vp, _ll, _d, _vp, _vp]
 _lib.gint_run_batch.argtypes = [ctypes.POINTER(_Task), _i, _i, _vp]
 _lib.gint_run_batch_timed.argtypes = [ctypes.POINTER(_Task), _i, _i, _vp, _vp, _vp]
 _lib.gint_memory.argtypes = [_vp, ctypes.POINTER(_ll)]
+_lib.gint_layout_R.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_ll), ctypes.POINTER(ctypes.POINTER(_i)),
+                               ctypes.POINTER(ctypes.POINTER(_ll))]
+_lib.gint_vlocal_R.argtypes = [_vp, _i, _vp, _vp, _vp]
+_lib.gint_bloch.argtypes = [_vp, _vp, _vp, _vp, _vp]
 
 C_ABI_SYMBOLS = ("gint_create", "gint_destroy", "gint_layout", "gint_pairs", "gint_stats", "gint_set_positions",
                  "gint_rho", "gint_vlocal", "gint_force", "gint_grid_dot", "gint_block_dot", "gint_weight",
                  "gint_strerror", "gint_sync", "gint_tc_selftest", "gint_grid_dot_noalloc", "gint_run_batch",
-                 "gint_run_batch_timed", "gint_memory")
+                 "gint_run_batch_timed", "gint_memory", "gint_layout_R", "gint_vlocal_R", "gint_bloch")
 
 
 def tc_selftest(n: int = 256) -> float:
@@ -222,6 +226,44 @@ class Gint:
         _check(_lib.gint_vlocal(self._h, int(precision), _dptr(V, numel=self.ngrid), _dptr(out, numel=self.nblock),
                                 _stream(stream)), "gint_vlocal")
         return out
+
+    def layout_R(self):
+        """Keys of the local H per lattice vector (paper Sec. 2, H(R)): (keys [nkeys, 5] int32 rows
+        (I, J, n1, n2, n3) with R = n1 a1 + n2 a2 + n3 a3, sorted; key_off [nkeys + 1] element offsets
+        of the norb(I) x norb(J) row-major blocks).  Raises GintError (GINT_EUNSUPPORTED) when some
+        brick sees two images of one atom."""
+        nk, nel = _i(), _ll()
+        kp, op = ctypes.POINTER(_i)(), ctypes.POINTER(_ll)()
+        _check(_lib.gint_layout_R(self._h, ctypes.byref(nk), ctypes.byref(nel), ctypes.byref(kp), ctypes.byref(op)),
+               "gint_layout_R")
+        keys = np.ctypeslib.as_array(kp, shape=(nk.value * 5,)).reshape(-1, 5).copy() if nk.value else \
+            np.zeros((0, 5), np.int32)
+        off = np.ctypeslib.as_array(op, shape=(nk.value + 1,)).copy()
+        self.nblock_R = int(nel.value)
+        return keys, off
+
+    def vlocal_R(self, V: torch.Tensor, precision: int = F16X3, out: Optional[torch.Tensor] = None,
+                 stream=None) -> torch.Tensor:
+        """H(R) blocks (float64, device) in the layout of layout_R (tensor-core precisions)."""
+        if not hasattr(self, "nblock_R"):
+            self.layout_R()
+        if out is None:
+            out = torch.empty(self.nblock_R, dtype=torch.float64, device=V.device)
+        _check(_lib.gint_vlocal_R(self._h, int(precision), _dptr(V, numel=self.ngrid),
+                                  _dptr(out, numel=self.nblock_R), _stream(stream)), "gint_vlocal_R")
+        return out
+
+    def bloch(self, H_R: torch.Tensor, kfrac, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """H(k) = sum_R e^{ik.R} H(R) in the Gamma block layout (complex128, device); kfrac is k in
+        reciprocal-lattice units."""
+        if not hasattr(self, "nblock_R"):
+            self.layout_R()
+        kf = (ctypes.c_double * 3)(*[float(x) for x in kfrac])
+        if out is None:
+            out = torch.empty(2 * self.nblock, dtype=torch.float64, device=H_R.device)
+        _check(_lib.gint_bloch(self._h, _dptr(H_R, numel=self.nblock_R), kf, _dptr(out, numel=2 * self.nblock),
+                               _stream(stream)), "gint_bloch")
+        return torch.view_as_complex(out.view(self.nblock, 2))
 
     def force(self, D_blocks: torch.Tensor, V: torch.Tensor, precision: int = FP64,
               out: Optional[torch.Tensor] = None, rho_out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:

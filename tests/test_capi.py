@@ -25,7 +25,7 @@ def _declared_symbols():
         if fn.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", fn)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names |= set(re.findall(r"\b(gint_[a-z0-9_]+)\s*\(", txt))
+            names |= set(re.findall(r"\b(gint_[A-Za-z0-9_]+)\s*\(", txt))
     return names
 
 
