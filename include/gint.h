@@ -146,11 +146,13 @@ int gint_layout_R(gint_handle *h, int *nkeys, long long *nblock_elems, const int
  * others: GINT_EUNSUPPORTED): the same brick pass as gint_vlocal, reduced per (I, J, R). */
 int gint_vlocal_R(gint_handle *h, int precision, const double *V, double *H_R, void *stream);
 
-/* Bloch sum (paper Sec. 2): H_k = sum_R e^{i k.R} H(R) in the Gamma-point block layout of gint_vlocal,
- * complex float64 interleaved (re, im): H_k [2 nblock] (device, overwritten), from H_R (device, as
- * written by gint_vlocal_R).  kfrac [3] (host) is k in reciprocal-lattice units (k = kf1 b1 + kf2 b2 +
- * kf3 b3, a_i . b_j = 2 pi delta_ij), so k.R = 2 pi (kf . n).  At kfrac = 0 it is the Gamma block. */
-int gint_bloch(gint_handle *h, const double *H_R, const double *kfrac, double *H_k, void *stream);
+/* Bloch sums (paper Sec. 2): H(k) = sum_R e^{i k.R} H(R) for nk k points, each in the Gamma-point
+ * block layout of gint_vlocal, complex float64 interleaved (re, im): H_k [nk][2 nblock] (device,
+ * overwritten), from H_R (device, as written by gint_vlocal_R).  kfrac [nk][3] (host) is each k in
+ * reciprocal-lattice units (k = kf1 b1 + kf2 b2 + kf3 b3, a_i . b_j = 2 pi delta_ij), so
+ * k.R = 2 pi (kf . n).  Up to 8 k points share one pass over H(R).  At kfrac = 0 it is the Gamma
+ * block. */
+int gint_bloch(gint_handle *h, const double *H_R, int nk, const double *kfrac, double *H_k, void *stream);
 
 /* Local Pulay forces F [natoms][3] (device, overwritten) = -dE/dtau for E = sum_g w V rho.
  * If rho is not NULL the density is written as well (same pass). */

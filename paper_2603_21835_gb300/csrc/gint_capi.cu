@@ -464,12 +464,12 @@ int gint_vlocal_R(gint_handle *h, int precision, const double *V, double *H_R, v
   return rc;
 }
 
-int gint_bloch(gint_handle *h, const double *H_R, const double *kfrac, double *H_k, void *stream) {
-  if (!h || !H_R || !kfrac || !H_k) return GINT_EINVAL;
+int gint_bloch(gint_handle *h, const double *H_R, int nk, const double *kfrac, double *H_k, void *stream) {
+  if (!h || !H_R || !kfrac || !H_k || nk < 0) return GINT_EINVAL;
   DeviceGuard guard(h->device);
   const int rc = gint_hr_prepare(h);
   if (rc) return rc;
-  return gint_hr_bloch(h, H_R, kfrac, H_k, (cudaStream_t)stream);
+  return gint_hr_bloch(h, H_R, nk, kfrac, H_k, (cudaStream_t)stream);
 }
 
 int gint_force(gint_handle *h, int precision, const double *D_blocks, const double *V, double *F, double *rho,

@@ -130,4 +130,4 @@ void gint_tc_free(gint_handle *h);
 // gint_hr.cu
 int gint_hr_prepare(gint_handle *h);  // key tables of H(R) (GINT_EUNSUPPORTED if tiles mix R)
 void gint_hr_free(gint_handle *h);
-int gint_hr_bloch(gint_handle *h, const double *HR, const double kf[3], double *Hk, cudaStream_t st);
+int gint_hr_bloch(gint_handle *h, const double *HR, int nk, const double *kf, double *Hk, cudaStream_t st);

@@ -48,39 +48,54 @@ void hfree(T *&p) {
 }
 
 // H_k (complex, interleaved re / im, Gamma-pair layout) = sum over the keys (I, J, n) of pair p of
-// e^{2 pi i kf.n} H_R[key]: one CTA per pair, the phases of up to 64 keys at a time in shared memory.
+// e^{2 pi i kf.n} H_R[key], for up to kMaxK k points at once (each H(R) element is read once for all
+// of them): one CTA per pair, the phases of up to 32 keys at a time in shared memory.
+constexpr int kMaxK = 8;
+struct GKpts {
+  int nk;
+  double kf[kMaxK][3];
+};
 __global__ void __launch_bounds__(128) k_bloch(const long long *__restrict__ pair_off, const int *__restrict__ gk_off,
                                                const int *__restrict__ kn, const long long *__restrict__ koff,
-                                               const double *__restrict__ HR, double k0, double k1, double k2,
-                                               double *__restrict__ Hk) {
-  __shared__ double cs[64], sn[64];
-  const int p = blockIdx.x;
+                                               const double *__restrict__ HR, const __grid_constant__ GKpts K,
+                                               long long nblock, double *__restrict__ Hk) {
+  __shared__ double cs[32][kMaxK], sn[32][kMaxK];
+  const int p = blockIdx.x, nk = K.nk;
   const long long o = pair_off[p], blk = pair_off[p + 1] - o;
   const int q0 = gk_off[p], q1 = gk_off[p + 1];
   for (long long e0 = 0; e0 < blk; e0 += blockDim.x) {
     const long long e = e0 + threadIdx.x;
-    double re = 0.0, im = 0.0;
-    for (int qb = q0; qb < q1; qb += 64) {
-      const int nq = min(64, q1 - qb);
+    double re[kMaxK], im[kMaxK];
+#pragma unroll
+    for (int j = 0; j < kMaxK; ++j) re[j] = im[j] = 0.0;
+    for (int qb = q0; qb < q1; qb += 32) {
+      const int nq = min(32, q1 - qb);
       __syncthreads();
-      if ((int)threadIdx.x < nq) {
-        const int q = qb + threadIdx.x;
+      for (int u = threadIdx.x; u < nq * nk; u += blockDim.x) {
+        const int i = u / nk, j = u - i * nk, q = qb + i;
         // k.R = 2 pi (kf . n) for R = n1 a1 + n2 a2 + n3 a3 and k in reciprocal-lattice units
-        sincospi(2.0 * (k0 * kn[3 * q] + k1 * kn[3 * q + 1] + k2 * kn[3 * q + 2]), &sn[threadIdx.x],
-                 &cs[threadIdx.x]);
+        sincospi(2.0 * (K.kf[j][0] * kn[3 * q] + K.kf[j][1] * kn[3 * q + 1] + K.kf[j][2] * kn[3 * q + 2]), &sn[i][j],
+                 &cs[i][j]);
       }
       __syncthreads();
       if (e < blk)
         for (int i = 0; i < nq; ++i) {
           const double h = HR[koff[qb + i] + e];
-          re += cs[i] * h;
-          im += sn[i] * h;
+#pragma unroll
+          for (int j = 0; j < kMaxK; ++j)
+            if (j < nk) {
+              re[j] += cs[i][j] * h;
+              im[j] += sn[i][j] * h;
+            }
         }
     }
-    if (e < blk) {
-      Hk[2 * (o + e)] = re;
-      Hk[2 * (o + e) + 1] = im;
-    }
+    if (e < blk)
+#pragma unroll
+      for (int j = 0; j < kMaxK; ++j)
+        if (j < nk) {
+          Hk[2 * (j * nblock + o + e)] = re[j];
+          Hk[2 * (j * nblock + o + e) + 1] = im[j];
+        }
   }
 }
 
@@ -230,9 +245,16 @@ int gint_hr_prepare(gint_handle *h) {
   return GINT_OK;
 }
 
-int gint_hr_bloch(gint_handle *h, const double *HR, const double kf[3], double *Hk, cudaStream_t st) {
+int gint_hr_bloch(gint_handle *h, const double *HR, int nk, const double *kf, double *Hk, cudaStream_t st) {
   if (h->npairs == 0) return GINT_OK;
-  k_bloch<<<(unsigned)h->npairs, 128, 0, st>>>(h->pair_off_dev, h->r_gk_off, h->r_kn, h->r_koff, HR, kf[0], kf[1],
-                                               kf[2], Hk);
-  return cudaGetLastError() == cudaSuccess ? GINT_OK : GINT_ECUDA;
+  for (int k0 = 0; k0 < nk; k0 += kMaxK) {
+    GKpts K{};
+    K.nk = std::min(kMaxK, nk - k0);
+    for (int j = 0; j < K.nk; ++j)
+      for (int c = 0; c < 3; ++c) K.kf[j][c] = kf[3 * (k0 + j) + c];
+    k_bloch<<<(unsigned)h->npairs, 128, 0, st>>>(h->pair_off_dev, h->r_gk_off, h->r_kn, h->r_koff, HR, K, h->nblock,
+                                                 Hk + 2 * (long long)k0 * h->nblock);
+    if (cudaGetLastError() != cudaSuccess) return GINT_ECUDA;
+  }
+  return GINT_OK;
 }

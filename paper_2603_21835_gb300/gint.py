@@ -78,7 +78,7 @@ _lib.gint_memory.argtypes = [_vp, ctypes.POINTER(_ll)]
 _lib.gint_layout_R.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_ll), ctypes.POINTER(ctypes.POINTER(_i)),
                                ctypes.POINTER(ctypes.POINTER(_ll))]
 _lib.gint_vlocal_R.argtypes = [_vp, _i, _vp, _vp, _vp]
-_lib.gint_bloch.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.gint_bloch.argtypes = [_vp, _vp, _i, _vp, _vp, _vp]
 
 C_ABI_SYMBOLS = ("gint_create", "gint_destroy", "gint_layout", "gint_pairs", "gint_stats", "gint_set_positions",
                  "gint_rho", "gint_vlocal", "gint_force", "gint_grid_dot", "gint_block_dot", "gint_weight",
@@ -254,16 +254,20 @@ class Gint:
         return out
 
     def bloch(self, H_R: torch.Tensor, kfrac, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
-        """H(k) = sum_R e^{ik.R} H(R) in the Gamma block layout (complex128, device); kfrac is k in
-        reciprocal-lattice units."""
+        """H(k) = sum_R e^{ik.R} H(R) in the Gamma block layout (complex128, device); kfrac is one k
+        ([3]) or several ([nk, 3]) in reciprocal-lattice units; the result is [nblock] or [nk, nblock]."""
         if not hasattr(self, "nblock_R"):
             self.layout_R()
-        kf = (ctypes.c_double * 3)(*[float(x) for x in kfrac])
+        kf = np.ascontiguousarray(np.asarray(kfrac, dtype=np.float64))
+        single = kf.ndim == 1
+        kf = kf.reshape(-1, 3)
+        nk = kf.shape[0]
         if out is None:
-            out = torch.empty(2 * self.nblock, dtype=torch.float64, device=H_R.device)
-        _check(_lib.gint_bloch(self._h, _dptr(H_R, numel=self.nblock_R), kf, _dptr(out, numel=2 * self.nblock),
-                               _stream(stream)), "gint_bloch")
-        return torch.view_as_complex(out.view(self.nblock, 2))
+            out = torch.empty(nk * 2 * self.nblock, dtype=torch.float64, device=H_R.device)
+        _check(_lib.gint_bloch(self._h, _dptr(H_R, numel=self.nblock_R), nk, kf.ctypes.data,
+                               _dptr(out, numel=nk * 2 * self.nblock), _stream(stream)), "gint_bloch")
+        z = torch.view_as_complex(out.view(nk, self.nblock, 2))
+        return z[0] if single else z
 
     def force(self, D_blocks: torch.Tensor, V: torch.Tensor, precision: int = FP64,
               out: Optional[torch.Tensor] = None, rho_out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:

@@ -109,6 +109,17 @@ def test_bloch_sum(si64):
         assert np.abs(A - refk).max() <= len(qs) * TOL * hmax
 
 
+def test_several_k_points_in_one_call(si64):
+    """Nine k points (two launches of up to eight) equal nine single-k calls."""
+    s = si64
+    g = s["g"]
+    kf = np.random.default_rng(4).uniform(-0.5, 0.5, size=(9, 3))
+    many = g.bloch(s["HR_dev"], kf).cpu().numpy()
+    for j in range(9):
+        one = g.bloch(s["HR_dev"], kf[j]).cpu().numpy()
+        assert np.array_equal(many[j], one)
+
+
 def test_folded_cell_is_unsupported():
     """8-atom Si cell: a brick sees two images of an atom, so its tiles mix R."""
     from paper_2603_21835_gb300 import gint as G
