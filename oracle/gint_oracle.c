@@ -19,6 +19,12 @@
  *                  Sec. 2 H(R) and its Bloch sum H(k) = sum_R e^{ik.R} H(R)); by the periodicity of
  *                  V: sum over cell points g and image pairs (I at tau_I + n_I A, J at tau_J + n_J A)
  *                  with n_J - n_I = R
+ *   projector      P_{j mu}^{IJ}(A) = int beta_{I j}(r - tau_I) e^{-i A.r} Phi_{J mu}(r) dr, the
+ *   overlaps       velocity-gauge nonlocal matrix element of Sec. 3.3.2 ("Spherical Grid Integration
+ *                  for Nonlocal Potentials"), on an atom-centred grid around tau_I (radial nodes on
+ *                  [0, rc_beta] times r^2, angular points with weights summing to 4 pi); beta_{I j} =
+ *                  f(|x|) Y_lm from a projector radial table (cubic Hermite, like the orbitals), Phi the
+ *                  periodised orbital (Gamma point)
  *   local Pulay    F_I = - dE/dtau_I, E = sum_g w V(r_g) rho(r_g) at fixed V, which is the
  *   force          local Pulay force formula of Sec. 3.3.1:
  *                  F_I = sum_g w V_g sum_{mu in I} grad Phi_mu(r_g) sum_nu (D_mu nu + D_nu mu) Phi_nu(r_g)
@@ -469,6 +475,42 @@ int orc_vlocal_block_R(const orc_sys *s, const double *V, int I, int J, int nR, 
     free(pI); free(pJ); free(nIm); free(nJm); free(acc);
   }
   *missed = miss;
+  return 0;
+}
+
+/* Projector overlaps with the velocity-gauge phase: out [nbeta(I)][norb(J)][2] (re, im) =
+ * sum_{k,a} W_ka beta_{I j}(x) e^{-i A.(tau_I + x)} Phi_{J mu}(tau_I + x), x = r_k e_a, r_k = rc t_k,
+ * W_ka = rc rw_k r_k^2 w_a.  `p` describes the projectors as the "orbitals" of a system with the same
+ * cell and atoms (its radial tables, l and rc); rt / rw are nodes and weights on [0, 1], ang [na][4]
+ * holds the angular points (x, y, z) and weights. */
+int orc_psibeta(const orc_sys *s, const orc_sys *p, const double A[3], int I, int J, int nr, const double *rt,
+                const double *rw, int na, const double *ang, double *out) {
+  double inv[9], det;
+  inverse3(s->cell, inv, &det);
+  int nb = orc_species_norb(p, p->species[I]), no = orc_species_norb(s, s->species[J]);
+  double rcb = species_rcut(p, p->species[I]);
+  memset(out, 0, sizeof(double) * 2 * nb * no);
+  double *beta = (double *)malloc(sizeof(double) * nb), *gb = (double *)malloc(sizeof(double) * nb * 3);
+  double *phi = (double *)malloc(sizeof(double) * no);
+  for (int k = 0; k < nr; ++k) {
+    double r = rcb * rt[k], wk = rcb * rw[k] * r * r;
+    for (int a = 0; a < na; ++a) {
+      double x[3] = {r * ang[4 * a], r * ang[4 * a + 1], r * ang[4 * a + 2]}, pt[3];
+      for (int c = 0; c < 3; ++c) pt[c] = s->pos[3 * I + c] + x[c];
+      memset(beta, 0, sizeof(double) * nb);
+      memset(gb, 0, sizeof(double) * nb * 3);
+      add_species_orbitals(p, p->species[I], x, beta, gb);
+      if (!atom_orbitals(s, inv, J, pt, phi, NULL)) continue;
+      double ph = -(A[0] * pt[0] + A[1] * pt[1] + A[2] * pt[2]);
+      double w = wk * ang[4 * a + 3], cr = w * cos(ph), ci = w * sin(ph);
+      for (int j = 0; j < nb; ++j)
+        for (int m = 0; m < no; ++m) {
+          out[2 * (j * no + m)] += cr * beta[j] * phi[m];
+          out[2 * (j * no + m) + 1] += ci * beta[j] * phi[m];
+        }
+    }
+  }
+  free(beta); free(gb); free(phi);
   return 0;
 }
 

@@ -75,6 +75,8 @@ def _load():
             lib.orc_vlocal.argtypes = [P, vp, ll, vp, vp]
             lib.orc_vlocal_block.argtypes = [P, vp, ctypes.c_int, ctypes.c_int, vp]
             lib.orc_vlocal_block_R.argtypes = [P, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+            lib.orc_psibeta.argtypes = [P, P, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp,
+                                        vp]
             lib.orc_force.argtypes = [P, vp, vp, ll, vp, vp, vp]
             lib.orc_count_pairs.argtypes = [P, ll, vp, vp, vp]
             lib.orc_num_threads.argtypes = []
@@ -192,6 +194,22 @@ class Oracle:
         self.lib.orc_vlocal_block_R(ctypes.byref(self.s), _ptr(V), int(I), int(J), int(R.shape[0]), _ptr(R),
                                     _ptr(out), ctypes.byref(missed))
         return out, missed.value
+
+    def psibeta(self, projectors: "Oracle", A, I: int, J: int, radial, angular) -> np.ndarray:
+        """Velocity-gauge projector overlaps (paper Sec. 3.3.2): [nbeta(I), norb(J)] complex,
+        sum over the atom-centred grid around tau_I of beta_{I j}(x) e^{-i A.r} Phi_{J mu}(r), r = tau_I + x.
+        ``projectors`` is an Oracle of the same cell and atoms whose radials are the projectors;
+        ``radial`` = (nodes, weights) on [0, 1] (scaled to [0, rc_beta], times r^2); ``angular`` =
+        [n, 4] points (x, y, z) and weights (summing to 4 pi)."""
+        rt = np.ascontiguousarray(radial[0], dtype=np.float64)
+        rw = np.ascontiguousarray(radial[1], dtype=np.float64)
+        ang = np.ascontiguousarray(angular, dtype=np.float64).reshape(-1, 4)
+        A = np.ascontiguousarray(A, dtype=np.float64).reshape(3)
+        nb, no = projectors._norb_atom(I), self._norb_atom(J)
+        out = np.zeros((nb, no, 2))
+        self.lib.orc_psibeta(ctypes.byref(self.s), ctypes.byref(projectors.s), _ptr(A), int(I), int(J), rt.shape[0],
+                             _ptr(rt), _ptr(rw), ang.shape[0], _ptr(ang), _ptr(out))
+        return out[..., 0] + 1j * out[..., 1]
 
     def force(self, D: np.ndarray, V: np.ndarray, idx: Optional[np.ndarray] = None,
               atoms: Optional[np.ndarray] = None) -> np.ndarray:

@@ -137,6 +137,12 @@ def si_species(rc: float = 7.0, dr: float = 0.01) -> Species:
     return species_dzp("Si", rc, [(0, 2), (1, 2), (2, 1)], dr)
 
 
+def si_projectors(rc: float = 2.5, dr: float = 0.01) -> Species:
+    """Nonlocal projectors of Si (one s and one p channel, 4 functions per atom), localised like
+    pseudopotential projectors: r^l exp(-6 r^2) (1 - (r/rc)^2)^3 within rc = 2.5 Bohr."""
+    return Species(name="Si-proj", radials=[make_radial(0, 6.0, rc, dr), make_radial(1, 6.0, rc, dr)])
+
+
 def o_species(rc: float = 6.0, dr: float = 0.01) -> Species:
     return species_dzp("O", rc, [(0, 2), (1, 2), (2, 1)], dr)
 
