@@ -337,6 +337,35 @@ def run_per_R(g, V, prec, steps, stream, flush, hbm_gbs):
             "bloch_frac_of_hbm": gbs / hbm_gbs if hbm_gbs else None}
 
 
+def run_psibeta(g, system, steps, stream):
+    """Velocity-gauge projector overlaps <beta| e^{-i A.r} |Phi> (float64, spherical grids of 140 x 162
+    points around every projector atom) for every (projector atom, orbital atom) pair of the workload:
+    mean time of gint_psibeta with Si projectors (one s and one p channel)."""
+    import torch
+
+    from paper_2603_21835_gb300 import inputs
+
+    if any(sp.name != "Si" for sp in system.sp):
+        return None
+    g.set_projectors([inputs.si_projectors()])
+    A = (0.12, -0.07, 0.05)
+    out = torch.empty(2 * g.pb_nelems, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        g.psibeta(A, out=out, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        g.psibeta(A, out=out, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    npairs = int(len(g.pb_pairs))
+    points = npairs * 140 * 162
+    return {"pairs": npairs, "elements": int(g.pb_nelems), "ms": ms, "pairs_per_s": npairs / (ms * 1e-3),
+            "grid_points_per_s": points / (ms * 1e-3), "precision": "f64",
+            "quadrature": "140 Gauss-Legendre radial x 162-point degree-17 product angular rule"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -501,6 +530,10 @@ def main():
     if rank == 0 and tensor:
         per_R = run_per_R(g, V, prec, args.steps, stream, flush, peaks.get("hbm_gbs"))
 
+    psibeta = None
+    if rank == 0 and tensor:
+        psibeta = run_psibeta(g, w.system, 3, stream)
+
     launches = KERNEL_LAUNCHES.get(args.precision)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -514,7 +547,7 @@ def main():
                    "parallelism": f"replicas{world}"},
         "ms_kernel": tdom, "ms_rho_alone": statistics.mean(t_rho), "ms_vlocal_alone": statistics.mean(t_h),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": launches * args.steps, "serving": serving, "per_R": per_R,
+        "gpu_launches": launches * args.steps, "serving": serving, "per_R": per_R, "psibeta": psibeta,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

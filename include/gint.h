@@ -154,6 +154,28 @@ int gint_vlocal_R(gint_handle *h, int precision, const double *V, double *H_R, v
  * block. */
 int gint_bloch(gint_handle *h, const double *H_R, int nk, const double *kfrac, double *H_k, void *stream);
 
+/* Velocity-gauge nonlocal projector overlaps (paper Sec. 3.3.2, "Spherical Grid Integration for
+ * Nonlocal Potentials"): P_{j mu}^{IJ}(A) = <beta_{I j}| e^{-i A.r} |Phi_{J mu}>, the integral of
+ * beta_{I j}(r - tau_I) e^{-i A.r} Phi_{J mu}(r) on a grid centred on tau_I (140 Gauss-Legendre radial
+ * nodes on [0, rc_beta] and a degree-17 angular rule: 9 Gauss-Legendre nodes in cos(theta) x 18
+ * azimuths, standing in for the paper's 110-point Lebedev-Laikov rule).  Phi is the orbital summed over
+ * the lattice images of J (Gamma point); r is the Cartesian position (the phase is not periodic).
+ *
+ * gint_set_projectors: projector radial tables per species (host, same species order as the
+ * descriptor; a species may have none), f including r^l, l <= 2, beta_j = f(r) Y_lm in the orbitals'
+ * convention.  Builds the pair list (I, J) of atoms whose orbitals reach I's projectors.  Synchronous.
+ * GINT_EUNSUPPORTED if an orbital species has more than 16 orbitals.
+ * gint_psibeta_layout: host outputs (any may be NULL): number of pairs, complex elements, and pointers
+ * to library-owned host arrays pairs [npairs][2] (I, J) and off [npairs + 1]; pair p's block is
+ * nbeta(I) x norb(J) row-major at off[p] (projector functions in the order of the radials, m as for
+ * orbitals).  GINT_EINVAL before gint_set_projectors.
+ * gint_psibeta: A [3] (host, atomic units), out [2 nelems] (device, overwritten, re / im interleaved),
+ * float64 throughout. */
+int gint_set_projectors(gint_handle *h, int nspecies, const gint_species *proj);
+int gint_psibeta_layout(const gint_handle *h, int *npairs, long long *nelems, const int **pairs,
+                        const long long **off);
+int gint_psibeta(gint_handle *h, const double *A, double *out, void *stream);
+
 /* Local Pulay forces F [natoms][3] (device, overwritten) = -dE/dtau for E = sum_g w V rho.
  * If rho is not NULL the density is written as well (same pass). */
 int gint_force(gint_handle *h, int precision, const double *D_blocks, const double *V, double *F, double *rho,

@@ -56,6 +56,7 @@ void free_all(gint_handle *h) {
   dfree(h->D32); dfree(h->work_ctr); dfree(h->red); dfree(h->scal); dfree(h->err_word);
   gint_tc_free(h);
   gint_hr_free(h);
+  gint_pb_free(h);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   h->own_stream = nullptr;
 }
@@ -388,7 +389,7 @@ int gint_memory(const gint_handle *h, long long *device_bytes) {
   b += h->cap_slots * 8 + (h->cap_slots + 1) * L + h->cap_ent * 3 * (long long)sizeof(double) +
        h->cap_pairtab * 4;                                                                  // neighbours
   b += 1024 * (long long)sizeof(double) + 16 * (long long)sizeof(double) + 16 + h->nblock * 4 + 16;  // workspace
-  *device_bytes = b + h->tc_bytes + h->r_bytes;
+  *device_bytes = b + h->tc_bytes + h->r_bytes + h->pb_bytes;
   return GINT_OK;
 }
 
@@ -470,6 +471,28 @@ int gint_bloch(gint_handle *h, const double *H_R, int nk, const double *kfrac, d
   const int rc = gint_hr_prepare(h);
   if (rc) return rc;
   return gint_hr_bloch(h, H_R, nk, kfrac, H_k, (cudaStream_t)stream);
+}
+
+int gint_set_projectors(gint_handle *h, int nspecies, const gint_species *proj) {
+  if (!h) return GINT_EINVAL;
+  DeviceGuard guard(h->device);
+  return gint_pb_set(h, nspecies, proj);
+}
+
+int gint_psibeta_layout(const gint_handle *h, int *npairs, long long *nelems, const int **pairs,
+                        const long long **off) {
+  if (!h || !h->pb_ready) return GINT_EINVAL;
+  if (npairs) *npairs = h->pb_npairs;
+  if (nelems) *nelems = h->pb_nelems;
+  if (pairs) *pairs = h->pb_pairs_host.data();
+  if (off) *off = h->pb_off_host.data();
+  return GINT_OK;
+}
+
+int gint_psibeta(gint_handle *h, const double *A, double *out, void *stream) {
+  if (!h || !A || !out) return GINT_EINVAL;
+  DeviceGuard guard(h->device);
+  return gint_pb_run(h, A, out, (cudaStream_t)stream);
 }
 
 int gint_force(gint_handle *h, int precision, const double *D_blocks, const double *V, double *F, double *rho,

@@ -86,6 +86,17 @@ struct gint_handle {
   int *r_hu_key = nullptr;              // upper keys, each with its contributions:
   long long *r_hu_off = nullptr, *r_hu_src = nullptr;
   int *r_gk_off = nullptr;              // [npairs + 1]: keys of pair p are [gk_off[p], gk_off[p + 1])
+  // velocity-gauge projector overlaps (set by gint_set_projectors)
+  bool pb_ready = false;
+  GTabs pb_tabs{};                      // projector radial metadata per species
+  double2 *pb_tab64 = nullptr;          // projector tables, (f, f') per knot
+  int pb_npairs = 0;
+  long long pb_nelems = 0, pb_bytes = 0;
+  std::vector<int> pb_pairs_host;       // [npairs][2]: projector atom I, orbital atom J
+  std::vector<long long> pb_off_host;   // [npairs + 1] complex-element offset of each block
+  int *pb_I = nullptr, *pb_J = nullptr, *pb_img_off = nullptr;
+  long long *pb_off = nullptr;
+  double *pb_img = nullptr;             // image positions of J per pair
   double *red = nullptr;      // reduction partials
   double *scal = nullptr;     // device scalars
   unsigned *err_word = nullptr;
@@ -131,3 +142,7 @@ void gint_tc_free(gint_handle *h);
 int gint_hr_prepare(gint_handle *h);  // key tables of H(R) (GINT_EUNSUPPORTED if tiles mix R)
 void gint_hr_free(gint_handle *h);
 int gint_hr_bloch(gint_handle *h, const double *HR, int nk, const double *kf, double *Hk, cudaStream_t st);
+// gint_pb.cu
+int gint_pb_set(gint_handle *h, int nspecies, const gint_species *proj);
+int gint_pb_run(gint_handle *h, const double A[3], double *out, cudaStream_t st);
+void gint_pb_free(gint_handle *h);

@@ -79,11 +79,16 @@ _lib.gint_layout_R.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_ll), cty
                                ctypes.POINTER(ctypes.POINTER(_ll))]
 _lib.gint_vlocal_R.argtypes = [_vp, _i, _vp, _vp, _vp]
 _lib.gint_bloch.argtypes = [_vp, _vp, _i, _vp, _vp, _vp]
+_lib.gint_set_projectors.argtypes = [_vp, _i, _vp]
+_lib.gint_psibeta_layout.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_ll), ctypes.POINTER(ctypes.POINTER(_i)),
+                                     ctypes.POINTER(ctypes.POINTER(_ll))]
+_lib.gint_psibeta.argtypes = [_vp, _vp, _vp, _vp]
 
 C_ABI_SYMBOLS = ("gint_create", "gint_destroy", "gint_layout", "gint_pairs", "gint_stats", "gint_set_positions",
                  "gint_rho", "gint_vlocal", "gint_force", "gint_grid_dot", "gint_block_dot", "gint_weight",
                  "gint_strerror", "gint_sync", "gint_tc_selftest", "gint_grid_dot_noalloc", "gint_run_batch",
-                 "gint_run_batch_timed", "gint_memory", "gint_layout_R", "gint_vlocal_R", "gint_bloch")
+                 "gint_run_batch_timed", "gint_memory", "gint_layout_R", "gint_vlocal_R", "gint_bloch",
+                 "gint_set_projectors", "gint_psibeta_layout", "gint_psibeta")
 
 
 def tc_selftest(n: int = 256) -> float:
@@ -145,20 +150,26 @@ def run_batch(tasks: Sequence[Task], precision: int = F16X3, stream=None, kernel
                "gint_run_batch_timed")
 
 
+def _species_array(species_list):
+    """gint_species[] (and the arrays it points into, which must stay alive) from Species records."""
+    keep, sp_arr = [], (_Species * len(species_list))()
+    for s, sp in enumerate(species_list):
+        arr = (_Radial * max(len(sp.radials), 1))()
+        for k, r in enumerate(sp.radials):
+            f = np.ascontiguousarray(r.f, dtype=np.float64)
+            df = np.ascontiguousarray(r.df, dtype=np.float64)
+            keep += [f, df]
+            arr[k] = _Radial(int(r.l), int(f.shape[0]), float(r.dr), float(r.rc), f.ctypes.data, df.ctypes.data)
+        keep.append(arr)
+        sp_arr[s] = _Species(len(sp.radials), arr)
+    return sp_arr, keep
+
+
 class Gint:
     """One geometry (cell, atoms, species radial tables, grid) resident on the current GPU."""
 
     def __init__(self, system, skin: float = 0.0):
-        rad_keep, sp_arr = [], (_Species * len(system.sp))()
-        for s, sp in enumerate(system.sp):
-            arr = (_Radial * len(sp.radials))()
-            for k, r in enumerate(sp.radials):
-                f = np.ascontiguousarray(r.f, dtype=np.float64)
-                df = np.ascontiguousarray(r.df, dtype=np.float64)
-                rad_keep += [f, df]
-                arr[k] = _Radial(int(r.l), int(f.shape[0]), float(r.dr), float(r.rc), f.ctypes.data, df.ctypes.data)
-            rad_keep.append(arr)
-            sp_arr[s] = _Species(len(sp.radials), arr)
+        sp_arr, rad_keep = _species_array(system.sp)
         pos = np.ascontiguousarray(system.pos, dtype=np.float64)
         spc = np.ascontiguousarray(system.species, dtype=np.int32)
         d = _Desc()
@@ -268,6 +279,28 @@ class Gint:
                                _dptr(out, numel=nk * 2 * self.nblock), _stream(stream)), "gint_bloch")
         z = torch.view_as_complex(out.view(nk, self.nblock, 2))
         return z[0] if single else z
+
+    def set_projectors(self, species_list):
+        """Nonlocal projector radials per species (Species records, same order as the system's)."""
+        sp_arr, keep = _species_array(species_list)
+        _check(_lib.gint_set_projectors(self._h, len(species_list), ctypes.cast(sp_arr, _vp)), "gint_set_projectors")
+        n, ne = _i(), _ll()
+        pp, op = ctypes.POINTER(_i)(), ctypes.POINTER(_ll)()
+        _check(_lib.gint_psibeta_layout(self._h, ctypes.byref(n), ctypes.byref(ne), ctypes.byref(pp), ctypes.byref(op)),
+               "gint_psibeta_layout")
+        self.pb_pairs = np.ctypeslib.as_array(pp, shape=(2 * n.value,)).reshape(-1, 2).copy() if n.value else \
+            np.zeros((0, 2), np.int32)
+        self.pb_off = np.ctypeslib.as_array(op, shape=(n.value + 1,)).copy()
+        self.pb_nelems = int(ne.value)
+
+    def psibeta(self, A, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """<beta_{I j}| e^{-i A.r} |Phi_{J mu}> blocks (complex128, device) in the layout of
+        set_projectors (pb_pairs, pb_off): pair p's block is nbeta(I) x norb(J) at pb_off[p]."""
+        a = (ctypes.c_double * 3)(*[float(x) for x in A])
+        if out is None:
+            out = torch.empty(2 * self.pb_nelems, dtype=torch.float64, device="cuda")
+        _check(_lib.gint_psibeta(self._h, a, _dptr(out, numel=2 * self.pb_nelems), _stream(stream)), "gint_psibeta")
+        return torch.view_as_complex(out.view(self.pb_nelems, 2))
 
     def force(self, D_blocks: torch.Tensor, V: torch.Tensor, precision: int = FP64,
               out: Optional[torch.Tensor] = None, rho_out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:

@@ -120,6 +120,34 @@ def test_several_k_points_in_one_call(si64):
         assert np.array_equal(many[j], one)
 
 
+def test_water_cluster_two_species():
+    """Water molecules in a 20 Bohr box (O: 13 orbitals, H: 5; blocks of different shapes): every R
+    of a few pairs against the oracle."""
+    import torch
+
+    from paper_2603_21835_gb300 import gint as G
+
+    w = inputs.h2o_workload(6, seed=3, box=20.0, grid=(64, 64, 64))
+    g = G.Gint(w.system)
+    keys, off = g.layout_R()
+    V = torch.from_numpy(np.ascontiguousarray(w.V.reshape(-1))).cuda()
+    HR = g.vlocal_R(V, G.F16X3).cpu().numpy()
+    g.sync()
+    o = Oracle(w.system)
+    hmax = np.abs(HR).max()
+    for I, J in [(0, 1), (1, 2), (0, 3), (2, 2)]:
+        qs = [q for q, k in enumerate(keys) if k[0] == I and k[1] == J]
+        if not qs:
+            continue
+        R = keys[qs, 2:]
+        ref, missed = o.vlocal_block_R(w.V, I, J, R)
+        assert missed <= 1e-12 * hmax
+        for i, q in enumerate(qs):
+            blk = HR[off[q]:off[q + 1]].reshape(ref[i].shape)
+            assert np.abs(blk - ref[i]).max() <= TOL * hmax, (I, J, tuple(R[i]))
+    g.close()
+
+
 def test_folded_cell_is_unsupported():
     """8-atom Si cell: a brick sees two images of an atom, so its tiles mix R."""
     from paper_2603_21835_gb300 import gint as G
