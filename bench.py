@@ -366,6 +366,50 @@ def run_psibeta(g, system, steps, stream):
             "quadrature": "140 Gauss-Legendre radial x 162-point degree-17 product angular rule"}
 
 
+def run_cn(n, nocc, steps, stream):
+    """Density-matrix build and one Crank-Nicolson step (complex float64 GEMMs and LU through the
+    libraries) for an n x n basis and nocc states: mean times over `steps` calls."""
+    import numpy as np
+    import torch
+
+    from paper_2603_21835_gb300 import gint as G
+
+    try:
+        cn = G.CrankNicolson(n, nocc)
+    except G.GintError as e:
+        return {"unavailable": str(e)}
+    rng = np.random.default_rng(0)
+    S = torch.eye(n, dtype=torch.float64, device="cuda") + 1e-3 * torch.from_numpy(rng.normal(size=(n, n))).cuda()
+    S = 0.5 * (S + S.T)
+    H = torch.from_numpy(rng.normal(size=(n, n))).cuda()
+    H = 0.5 * (H + H.T)
+    psi = torch.from_numpy(rng.normal(size=(nocc, n)) + 1j * rng.normal(size=(nocc, n))).cuda()
+    f = torch.full((nocc,), 2.0, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(psi)
+    D = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    cn.step(S, H, 0.05, psi, out=out, stream=stream)
+    cn.density_matrix(out, f, out=D, stream=stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ts, td = [], []
+    for _ in range(steps):
+        ev[0].record(stream)
+        cn.step(S, H, 0.05, psi, out=out, stream=stream)
+        ev[1].record(stream)
+        cn.density_matrix(out, f, out=D, stream=stream)
+        ev[2].record(stream)
+        ev[2].synchronize()
+        ts.append(ev[0].elapsed_time(ev[1]))
+        td.append(ev[1].elapsed_time(ev[2]))
+    info = cn.info()
+    cn.close()
+    ms_s, ms_d = statistics.mean(ts), statistics.mean(td)
+    # complex float64 flops: ZGEMM 8 n^2 nocc, LU 8/3 n^3, triangular solves 8 n^2 nocc; D: 8 n^2 nocc
+    fl_step = 8.0 * n * n * nocc + 8.0 / 3.0 * n ** 3 + 8.0 * n * n * nocc
+    return {"n": n, "nocc": nocc, "ms_step": ms_s, "step_tflops": fl_step / (ms_s * 1e-3) / 1e12,
+            "ms_density_matrix": ms_d, "dm_tflops": 8.0 * n * n * nocc / (ms_d * 1e-3) / 1e12, "lu_info": info,
+            "precision": "c128"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -534,6 +578,10 @@ def main():
     if rank == 0 and tensor:
         psibeta = run_psibeta(g, w.system, 3, stream)
 
+    cn = None
+    if rank == 0 and tensor:
+        cn = run_cn(g.norb, 128 if g.norb < 2048 else 1024, 3 if g.norb < 2048 else 2, stream)
+
     launches = KERNEL_LAUNCHES.get(args.precision)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -548,6 +596,7 @@ def main():
         "ms_kernel": tdom, "ms_rho_alone": statistics.mean(t_rho), "ms_vlocal_alone": statistics.mean(t_h),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches * args.steps, "serving": serving, "per_R": per_R, "psibeta": psibeta,
+        "crank_nicolson": cn,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -176,6 +176,28 @@ int gint_psibeta_layout(const gint_handle *h, int *npairs, long long *nelems, co
                         const long long **off);
 int gint_psibeta(gint_handle *h, const double *A, double *out, void *stream);
 
+/* Dense steps of real-time propagation around the grid passes (paper Sec. 2): the density matrix
+ * from coefficients and occupations, and one Crank-Nicolson step of the coefficients.  Plain library
+ * operations (complex GEMMs and an LU factorisation with partial pivoting, cuBLAS / cuSOLVER loaded
+ * on first use; GINT_EUNSUPPORTED from gint_cn_create if they cannot be loaded).  A context holds all
+ * buffers for an n x n problem with nocc states (allocated by gint_cn_create on the current device),
+ * so the compute calls allocate nothing.  Matrices are float64 n x n, symmetric (any order); psi is
+ * complex float64 n x nocc column-major (state j is psi[j n .. j n + n)), re / im interleaved; all
+ * device pointers, caller-owned; the calls are asynchronous on `stream` and must not run
+ * concurrently on one context.
+ *
+ * gint_cn_step: psi_out = (S + i dt/2 H)^{-1} (S - i dt/2 H) psi (psi_out must not alias psi).
+ * gint_dm_build: D = Re(psi diag(f) psi^dagger), f [nocc] (device) occupations.
+ * gint_cn_info: the LAPACK-style info of the last factorisation (0: success; i > 0: U(i, i) = 0);
+ * synchronous. */
+typedef struct gint_cn gint_cn;
+int gint_cn_create(int n, int nocc, gint_cn **out);
+int gint_cn_destroy(gint_cn *c);
+int gint_cn_step(gint_cn *c, const double *S, const double *H, double dt, const double *psi, double *psi_out,
+                 void *stream);
+int gint_dm_build(gint_cn *c, const double *psi, const double *f, double *D, void *stream);
+int gint_cn_info(gint_cn *c, int *info);
+
 /* Local Pulay forces F [natoms][3] (device, overwritten) = -dE/dtau for E = sum_g w V rho.
  * If rho is not NULL the density is written as well (same pass). */
 int gint_force(gint_handle *h, int precision, const double *D_blocks, const double *V, double *F, double *rho,

@@ -83,12 +83,69 @@ _lib.gint_set_projectors.argtypes = [_vp, _i, _vp]
 _lib.gint_psibeta_layout.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_ll), ctypes.POINTER(ctypes.POINTER(_i)),
                                      ctypes.POINTER(ctypes.POINTER(_ll))]
 _lib.gint_psibeta.argtypes = [_vp, _vp, _vp, _vp]
+_lib.gint_cn_create.argtypes = [_i, _i, ctypes.POINTER(_vp)]
+_lib.gint_cn_destroy.argtypes = [_vp]
+_lib.gint_cn_step.argtypes = [_vp, _vp, _vp, _d, _vp, _vp, _vp]
+_lib.gint_dm_build.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.gint_cn_info.argtypes = [_vp, ctypes.POINTER(_i)]
 
 C_ABI_SYMBOLS = ("gint_create", "gint_destroy", "gint_layout", "gint_pairs", "gint_stats", "gint_set_positions",
                  "gint_rho", "gint_vlocal", "gint_force", "gint_grid_dot", "gint_block_dot", "gint_weight",
                  "gint_strerror", "gint_sync", "gint_tc_selftest", "gint_grid_dot_noalloc", "gint_run_batch",
                  "gint_run_batch_timed", "gint_memory", "gint_layout_R", "gint_vlocal_R", "gint_bloch",
-                 "gint_set_projectors", "gint_psibeta_layout", "gint_psibeta")
+                 "gint_set_projectors", "gint_psibeta_layout", "gint_psibeta", "gint_cn_create", "gint_cn_destroy",
+                 "gint_cn_step", "gint_dm_build", "gint_cn_info")
+
+
+class CrankNicolson:
+    """Density-matrix build and Crank-Nicolson steps for n x n matrices and nocc states on the current
+    GPU (buffers held by the context).  States are rows of a complex128 [nocc, n] tensor."""
+
+    def __init__(self, n: int, nocc: int):
+        c = _vp()
+        _check(_lib.gint_cn_create(int(n), int(nocc), ctypes.byref(c)), "gint_cn_create")
+        self._c, self.n, self.nocc = c, int(n), int(nocc)
+
+    def _cplx(self, psi: torch.Tensor):
+        if psi.dtype != torch.complex128 or not psi.is_cuda or not psi.is_contiguous() or \
+                tuple(psi.shape) != (self.nocc, self.n):
+            raise ValueError(f"expected a contiguous CUDA complex128 tensor [{self.nocc}, {self.n}]")
+        return ctypes.c_void_p(psi.data_ptr())
+
+    def step(self, S: torch.Tensor, H: torch.Tensor, dt: float, psi: torch.Tensor,
+             out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """(S + i dt/2 H)^{-1} (S - i dt/2 H) psi."""
+        if out is None:
+            out = torch.empty_like(psi)
+        nn = self.n * self.n
+        _check(_lib.gint_cn_step(self._c, _dptr(S, numel=nn), _dptr(H, numel=nn), float(dt), self._cplx(psi),
+                                 self._cplx(out), _stream(stream)), "gint_cn_step")
+        return out
+
+    def density_matrix(self, psi: torch.Tensor, f: torch.Tensor, out: Optional[torch.Tensor] = None,
+                       stream=None) -> torch.Tensor:
+        """Re(psi^T diag(f) conj(psi)) as [n, n] float64 (rows of psi are the states)."""
+        if out is None:
+            out = torch.empty((self.n, self.n), dtype=torch.float64, device=psi.device)
+        _check(_lib.gint_dm_build(self._c, self._cplx(psi), _dptr(f, numel=self.nocc), _dptr(out, numel=self.n * self.n),
+                                  _stream(stream)), "gint_dm_build")
+        return out
+
+    def info(self) -> int:
+        i = _i()
+        _check(_lib.gint_cn_info(self._c, ctypes.byref(i)), "gint_cn_info")
+        return i.value
+
+    def close(self):
+        if self._c:
+            _lib.gint_cn_destroy(self._c)
+            self._c = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tc_selftest(n: int = 256) -> float:
