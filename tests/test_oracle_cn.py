@@ -4,7 +4,7 @@ solver, explicit loops)."""
 import numpy as np
 import scipy.linalg
 
-from oracle.dense import crank_nicolson, density_matrix
+from oracle.dense import crank_nicolson, density_matrix, energy_density_matrix
 
 
 def _matrices(n=60, seed=0):
@@ -62,3 +62,27 @@ def test_density_matrix_by_explicit_sum_and_trace():
     e, C = scipy.linalg.eigh(H, S)
     D2 = density_matrix(C[:, :k], f)
     assert abs(np.trace(D2 @ S) - f.sum()) <= 1e-12 * f.sum()
+
+
+def test_edm_of_eigenstates_is_the_textbook_form():
+    """For S-orthonormal eigenstates (H c = e S c) and D = C f C^T: E = C f e C^T."""
+    S, H = _matrices(seed=7)
+    e, C = scipy.linalg.eigh(H, S)
+    k = 11
+    f = np.random.default_rng(8).uniform(0, 2, size=k)
+    D = (C[:, :k] * f) @ C[:, :k].T
+    E = energy_density_matrix(S, H, D)
+    ref = (C[:, :k] * (f * e[:k])) @ C[:, :k].T
+    assert np.abs(E - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_edm_identities():
+    S, H = _matrices(seed=9)
+    rng = np.random.default_rng(10)
+    G = rng.normal(size=S.shape)
+    D = 0.5 * (G + G.T)
+    E = energy_density_matrix(S, H, D)
+    assert np.abs(E - E.T).max() == 0.0
+    assert abs(np.trace(E @ S) - np.trace(H @ D)) <= 1e-12 * np.abs(H @ D).sum()
+    E1 = energy_density_matrix(np.eye(S.shape[0]), H, D)
+    assert np.abs(E1 - 0.5 * (H @ D + D @ H)).max() <= 1e-13 * np.abs(H @ D).max()
