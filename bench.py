@@ -367,8 +367,9 @@ def run_psibeta(g, system, steps, stream):
 
 
 def run_cn(n, nocc, steps, stream):
-    """Density-matrix build and one Crank-Nicolson step (complex float64 GEMMs and LU through the
-    libraries) for an n x n basis and nocc states: mean times over `steps` calls."""
+    """Density-matrix build, one Crank-Nicolson step (complex float64 GEMMs and LU through the
+    libraries) for an n x n basis and nocc states, and the energy-density matrix (real float64 GEMM and
+    Cholesky solve): mean times over `steps` calls."""
     import numpy as np
     import torch
 
@@ -400,14 +401,25 @@ def run_cn(n, nocc, steps, stream):
         ev[2].synchronize()
         ts.append(ev[0].elapsed_time(ev[1]))
         td.append(ev[1].elapsed_time(ev[2]))
+    te = []
+    E = torch.empty_like(D)
+    cn.energy_density_matrix(S, H, D, out=E, stream=stream)
+    for _ in range(steps):
+        ev[0].record(stream)
+        cn.energy_density_matrix(S, H, D, out=E, stream=stream)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        te.append(ev[0].elapsed_time(ev[1]))
     info = cn.info()
     cn.close()
-    ms_s, ms_d = statistics.mean(ts), statistics.mean(td)
+    ms_s, ms_d, ms_e = statistics.mean(ts), statistics.mean(td), statistics.mean(te)
     # complex float64 flops: ZGEMM 8 n^2 nocc, LU 8/3 n^3, triangular solves 8 n^2 nocc; D: 8 n^2 nocc
     fl_step = 8.0 * n * n * nocc + 8.0 / 3.0 * n ** 3 + 8.0 * n * n * nocc
     return {"n": n, "nocc": nocc, "ms_step": ms_s, "step_tflops": fl_step / (ms_s * 1e-3) / 1e12,
-            "ms_density_matrix": ms_d, "dm_tflops": 8.0 * n * n * nocc / (ms_d * 1e-3) / 1e12, "lu_info": info,
-            "precision": "c128"}
+            "ms_density_matrix": ms_d, "dm_tflops": 8.0 * n * n * nocc / (ms_d * 1e-3) / 1e12,
+            # real float64: DGEMM 2 n^3, Cholesky n^3 / 3, two triangular solves 2 n^3
+            "ms_energy_density_matrix": ms_e, "edm_tflops": (4.0 + 1.0 / 3.0) * n ** 3 / (ms_e * 1e-3) / 1e12,
+            "solver_info": info, "precision": "c128 / f64"}
 
 
 def main():

@@ -198,6 +198,11 @@ int gint_cn_step(gint_cn *c, const double *S, const double *H, double dt, const 
 int gint_dm_build(gint_cn *c, const double *psi, const double *f, double *D, void *stream);
 int gint_cn_info(gint_cn *c, int *info);
 
+/* Energy-density matrix E = (S^{-1} H D + D H S^{-1}) / 2 (the overlap part of the forces needs it):
+ * S (positive definite), H, D real symmetric n x n (device), E (device, overwritten); a Cholesky
+ * solve with the context's buffers (gint_cn_info reports a non-positive pivot as i > 0). */
+int gint_edm(gint_cn *c, const double *S, const double *H, const double *D, double *E, void *stream);
+
 /* Local Pulay forces F [natoms][3] (device, overwritten) = -dE/dtau for E = sum_g w V rho.
  * If rho is not NULL the density is written as well (same pass). */
 int gint_force(gint_handle *h, int precision, const double *D_blocks, const double *V, double *F, double *rho,

@@ -1,7 +1,8 @@
 // gint_cn.cu -- the dense steps of real-time propagation around the grid passes: the density matrix
-// from coefficients and occupations, D = Re(psi diag(f) psi^dagger), and one Crank-Nicolson step of
-// the coefficients, (S + i dt/2 H) psi(t + dt) = (S - i dt/2 H) psi(t), by LU factorisation (paper
-// Sec. 2: the density matrix and the time propagation of the coefficients with the overlap matrix).
+// from coefficients and occupations, D = Re(psi diag(f) psi^dagger), one Crank-Nicolson step of the
+// coefficients, (S + i dt/2 H) psi(t + dt) = (S - i dt/2 H) psi(t), by LU factorisation (paper Sec. 2:
+// the density matrix and the time propagation of the coefficients with the overlap matrix), and the
+// energy-density matrix E = (S^{-1} H D + D H S^{-1}) / 2 by a Cholesky solve.
 //
 // Both are plain library operations: complex GEMMs (cuBLAS) and an LU factorisation with partial
 // pivoting and its solve (cuSOLVER).  The libraries are loaded on first use (dlopen), so the grid
@@ -41,6 +42,12 @@ struct Libs {
                             int *) = nullptr;
   cusolverStatus_t (*getrs)(cusolverDnHandle_t, cublasOperation_t, int, int, const cuDoubleComplex *, int,
                             const int *, cuDoubleComplex *, int, int *) = nullptr;
+  cublasStatus_t (*dgemm)(cublasHandle_t, cublasOperation_t, cublasOperation_t, int, int, int, const double *,
+                          const double *, int, const double *, int, const double *, double *, int) = nullptr;
+  cusolverStatus_t (*potrf_size)(cusolverDnHandle_t, cublasFillMode_t, int, double *, int, int *) = nullptr;
+  cusolverStatus_t (*potrf)(cusolverDnHandle_t, cublasFillMode_t, int, double *, int, double *, int, int *) = nullptr;
+  cusolverStatus_t (*potrs)(cusolverDnHandle_t, cublasFillMode_t, int, int, const double *, int, double *, int,
+                            int *) = nullptr;
 };
 
 void *open_first(const char *const *names) {
@@ -70,8 +77,12 @@ const Libs &libs() {
     L.getrf_size = (decltype(L.getrf_size))dlsym(hs, "cusolverDnZgetrf_bufferSize");
     L.getrf = (decltype(L.getrf))dlsym(hs, "cusolverDnZgetrf");
     L.getrs = (decltype(L.getrs))dlsym(hs, "cusolverDnZgetrs");
+    L.dgemm = (decltype(L.dgemm))dlsym(hb, "cublasDgemm_v2");
+    L.potrf_size = (decltype(L.potrf_size))dlsym(hs, "cusolverDnDpotrf_bufferSize");
+    L.potrf = (decltype(L.potrf))dlsym(hs, "cusolverDnDpotrf");
+    L.potrs = (decltype(L.potrs))dlsym(hs, "cusolverDnDpotrs");
     L.ok = L.blas_create && L.blas_destroy && L.blas_stream && L.zgemm && L.sol_create && L.sol_destroy &&
-           L.sol_stream && L.getrf_size && L.getrf && L.getrs;
+           L.sol_stream && L.getrf_size && L.getrf && L.getrs && L.dgemm && L.potrf_size && L.potrf && L.potrs;
   });
   return L;
 }
@@ -101,12 +112,21 @@ __global__ void k_real_part(long long nn, const cuDoubleComplex *__restrict__ C,
     D[e] = cuCreal(C[e]);
 }
 
+// E = (X + X^T) / 2 (n x n)
+__global__ void k_sym_half(int n, const double *__restrict__ X, double *__restrict__ E) {
+  const long long nn = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / n, j = e - i * n;
+    E[e] = 0.5 * (X[e] + X[j * n + i]);
+  }
+}
+
 unsigned blocks_for(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 4096); }
 
 }  // namespace
 
 struct gint_cn {
-  int n = 0, nocc = 0, device = 0, lwork = 0;
+  int n = 0, nocc = 0, device = 0, lwork = 0, lwork_r = 0;
   cuDoubleComplex *A = nullptr, *W = nullptr, *Y = nullptr, *work = nullptr;
   int *ipiv = nullptr, *info = nullptr;
   cublasHandle_t blas = nullptr;
@@ -150,10 +170,14 @@ int gint_cn_create(int n, int nocc, gint_cn **out) {
     return GINT_ENOMEM;
   }
   if (L.blas_create(&c->blas) != CUBLAS_STATUS_SUCCESS || L.sol_create(&c->sol) != CUSOLVER_STATUS_SUCCESS ||
-      L.getrf_size(c->sol, n, n, c->A, n, &c->lwork) != CUSOLVER_STATUS_SUCCESS) {
+      L.getrf_size(c->sol, n, n, c->A, n, &c->lwork) != CUSOLVER_STATUS_SUCCESS ||
+      L.potrf_size(c->sol, CUBLAS_FILL_MODE_LOWER, n, reinterpret_cast<double *>(c->A), n, &c->lwork_r) !=
+          CUSOLVER_STATUS_SUCCESS) {
     gint_cn_destroy(c);
     return GINT_ECUDA;
   }
+  // one workspace for both factorisations (complex elements; the real one needs lwork_r doubles)
+  c->lwork = std::max(c->lwork, (c->lwork_r + 1) / 2);
   if (cudaMalloc(&c->work, (size_t)std::max(c->lwork, 1) * sizeof(cuDoubleComplex)) != cudaSuccess ||
       cudaMemset(c->info, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -201,6 +225,29 @@ int gint_dm_build(gint_cn *c, const double *psi, const double *f, double *D, voi
       CUBLAS_STATUS_SUCCESS)
     return GINT_ECUDA;
   k_real_part<<<blocks_for(nn), 256, 0, st>>>(nn, c->W, D);
+  return cudaGetLastError() == cudaSuccess ? GINT_OK : GINT_ECUDA;
+}
+
+int gint_edm(gint_cn *c, const double *S, const double *H, const double *D, double *E, void *stream) {
+  if (!c || !S || !H || !D || !E) return GINT_EINVAL;
+  const Libs &L = libs();
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = c->n;
+  // the n x n complex buffers hold two real n x n matrices each: A -> Cholesky factor of S, W -> X
+  double *F = reinterpret_cast<double *>(c->A), *X = reinterpret_cast<double *>(c->W);
+  if (cudaMemcpyAsync(F, S, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return GINT_ECUDA;
+  if (L.blas_stream(c->blas, st) != CUBLAS_STATUS_SUCCESS || L.sol_stream(c->sol, st) != CUSOLVER_STATUS_SUCCESS)
+    return GINT_ECUDA;
+  const double one = 1.0, zero = 0.0;
+  // X = H D, then X <- S^{-1} X (S = L L^T), E = (X + X^T) / 2
+  if (L.dgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, H, n, D, n, &zero, X, n) != CUBLAS_STATUS_SUCCESS)
+    return GINT_ECUDA;
+  if (L.potrf(c->sol, CUBLAS_FILL_MODE_LOWER, n, F, n, reinterpret_cast<double *>(c->work), 2 * c->lwork, c->info) !=
+      CUSOLVER_STATUS_SUCCESS)
+    return GINT_ECUDA;
+  if (L.potrs(c->sol, CUBLAS_FILL_MODE_LOWER, n, n, F, n, X, n, c->info) != CUSOLVER_STATUS_SUCCESS) return GINT_ECUDA;
+  k_sym_half<<<blocks_for((long long)n * n), 256, 0, st>>>(n, X, E);
   return cudaGetLastError() == cudaSuccess ? GINT_OK : GINT_ECUDA;
 }
 

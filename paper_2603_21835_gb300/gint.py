@@ -88,13 +88,14 @@ _lib.gint_cn_destroy.argtypes = [_vp]
 _lib.gint_cn_step.argtypes = [_vp, _vp, _vp, _d, _vp, _vp, _vp]
 _lib.gint_dm_build.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.gint_cn_info.argtypes = [_vp, ctypes.POINTER(_i)]
+_lib.gint_edm.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
 
 C_ABI_SYMBOLS = ("gint_create", "gint_destroy", "gint_layout", "gint_pairs", "gint_stats", "gint_set_positions",
                  "gint_rho", "gint_vlocal", "gint_force", "gint_grid_dot", "gint_block_dot", "gint_weight",
                  "gint_strerror", "gint_sync", "gint_tc_selftest", "gint_grid_dot_noalloc", "gint_run_batch",
                  "gint_run_batch_timed", "gint_memory", "gint_layout_R", "gint_vlocal_R", "gint_bloch",
                  "gint_set_projectors", "gint_psibeta_layout", "gint_psibeta", "gint_cn_create", "gint_cn_destroy",
-                 "gint_cn_step", "gint_dm_build", "gint_cn_info")
+                 "gint_cn_step", "gint_dm_build", "gint_cn_info", "gint_edm")
 
 
 class CrankNicolson:
@@ -129,6 +130,16 @@ class CrankNicolson:
             out = torch.empty((self.n, self.n), dtype=torch.float64, device=psi.device)
         _check(_lib.gint_dm_build(self._c, self._cplx(psi), _dptr(f, numel=self.nocc), _dptr(out, numel=self.n * self.n),
                                   _stream(stream)), "gint_dm_build")
+        return out
+
+    def energy_density_matrix(self, S: torch.Tensor, H: torch.Tensor, D: torch.Tensor,
+                              out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """(S^{-1} H D + D H S^{-1}) / 2 as [n, n] float64."""
+        if out is None:
+            out = torch.empty((self.n, self.n), dtype=torch.float64, device=S.device)
+        nn = self.n * self.n
+        _check(_lib.gint_edm(self._c, _dptr(S, numel=nn), _dptr(H, numel=nn), _dptr(D, numel=nn),
+                             _dptr(out, numel=nn), _stream(stream)), "gint_edm")
         return out
 
     def info(self) -> int:

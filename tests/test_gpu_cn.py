@@ -1,10 +1,11 @@
-"""GPU parity of the density-matrix build and the Crank-Nicolson step (paper Sec. 2) against the
-LAPACK oracle (oracle/dense.py), both in complex float64: 1e-12 of the largest entry; and the loop
-rho -> H -> psi -> rho closed on the 8-atom Si cell with the grid library's own passes."""
+"""GPU parity of the density-matrix build, the Crank-Nicolson step (paper Sec. 2) and the energy-
+density matrix against the LAPACK oracle (oracle/dense.py), all in float64: 1e-12 of the largest
+entry; and the loop rho -> H -> psi -> rho closed on the 8-atom Si cell with the grid library's own
+passes."""
 import numpy as np
 import pytest
 
-from oracle.dense import crank_nicolson, density_matrix
+from oracle.dense import crank_nicolson, density_matrix, energy_density_matrix
 from oracle.oracle import Oracle
 from paper_2603_21835_gb300 import inputs
 
@@ -39,6 +40,24 @@ def test_step_and_density_matrix_match_the_oracle():
     assert np.abs(out - ref).max() <= 1e-12 * np.abs(ref).max()
     Dref = density_matrix(psi, f)
     assert np.abs(D - Dref).max() <= 1e-12 * np.abs(Dref).max()
+    cn.close()
+
+
+def test_energy_density_matrix_matches_the_oracle():
+    import torch
+
+    from paper_2603_21835_gb300 import gint as G
+
+    n = 832
+    S, H = _matrices(n, 2)
+    G_ = np.random.default_rng(3).normal(size=(n, n))
+    D = 0.5 * (G_ + G_.T)
+    cn = G.CrankNicolson(n, 8)
+    E = cn.energy_density_matrix(*(torch.from_numpy(x).cuda() for x in (S, H, D))).cpu().numpy()
+    assert cn.info() == 0
+    ref = energy_density_matrix(S, H, D)
+    assert np.abs(E - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert np.abs(E - E.T).max() == 0.0
     cn.close()
 
 
