@@ -401,6 +401,15 @@ def run_cn(n, nocc, steps, stream):
         ev[2].synchronize()
         ts.append(ev[0].elapsed_time(ev[1]))
         td.append(ev[1].elapsed_time(ev[2]))
+    tt = []
+    D16 = torch.empty_like(D)
+    cn.density_matrix(psi, f, out=D16, stream=stream, precision="f16x3")
+    for _ in range(max(steps, 5)):
+        ev[0].record(stream)
+        cn.density_matrix(psi, f, out=D16, stream=stream, precision="f16x3")
+        ev[1].record(stream)
+        ev[1].synchronize()
+        tt.append(ev[0].elapsed_time(ev[1]))
     te = []
     E = torch.empty_like(D)
     cn.energy_density_matrix(S, H, D, out=E, stream=stream)
@@ -412,14 +421,19 @@ def run_cn(n, nocc, steps, stream):
         te.append(ev[0].elapsed_time(ev[1]))
     info = cn.info()
     cn.close()
-    ms_s, ms_d, ms_e = statistics.mean(ts), statistics.mean(td), statistics.mean(te)
+    ms_s, ms_d, ms_e, ms_t = statistics.mean(ts), statistics.mean(td), statistics.mean(te), statistics.mean(tt)
+    # tensor-core build: tiles I <= J of 128 x 128, K padded to 64, three float16 products per term
+    T, kp = (n + 127) // 128, (2 * nocc + 63) // 64 * 64
+    tc_flops = 3 * 2.0 * 128 * 128 * kp * (T * (T + 1) // 2)
     # complex float64 flops: ZGEMM 8 n^2 nocc, LU 8/3 n^3, triangular solves 8 n^2 nocc; D: 8 n^2 nocc
     fl_step = 8.0 * n * n * nocc + 8.0 / 3.0 * n ** 3 + 8.0 * n * n * nocc
     return {"n": n, "nocc": nocc, "ms_step": ms_s, "step_tflops": fl_step / (ms_s * 1e-3) / 1e12,
             "ms_density_matrix": ms_d, "dm_tflops": 8.0 * n * n * nocc / (ms_d * 1e-3) / 1e12,
             # real float64: DGEMM 2 n^3, Cholesky n^3 / 3, two triangular solves 2 n^3
             "ms_energy_density_matrix": ms_e, "edm_tflops": (4.0 + 1.0 / 3.0) * n ** 3 / (ms_e * 1e-3) / 1e12,
-            "solver_info": info, "precision": "c128 / f64"}
+            "ms_density_matrix_f16x3": ms_t, "dm_f16x3_tflops_real_part": 4.0 * n * n * nocc / (ms_t * 1e-3) / 1e12,
+            "dm_f16x3_tensor_tflops": tc_flops / (ms_t * 1e-3) / 1e12,
+            "solver_info": info, "precision": "c128 / f64; f16x3 tensor-core D build"}
 
 
 def main():

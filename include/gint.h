@@ -188,14 +188,20 @@ int gint_psibeta(gint_handle *h, const double *A, double *out, void *stream);
  *
  * gint_cn_step: psi_out = (S + i dt/2 H)^{-1} (S - i dt/2 H) psi (psi_out must not alias psi).
  * gint_dm_build: D = Re(psi diag(f) psi^dagger), f [nocc] (device) occupations.
+ * gint_dm_build_f16x3: the same D on the tensor cores: D = A B^T with A_ik = f_s psi_is, B_ik = psi_is
+ * (k = 2 s + real / imaginary part), each operand scaled by a power of two and split into float16
+ * hi + lo, three float16 products per term with float32 accumulation over chunks of 64 k and a
+ * float64 sum of four partial accumulators; D is symmetric bit for bit, and its error is about
+ * 2^-21 of max_i sum_s |f_s| |psi_is|^2.  Occupations of any sign; no allocation.
  * gint_cn_info: the LAPACK-style info of the last factorisation (0: success; i > 0: U(i, i) = 0);
- * synchronous. */
+ * synchronous; returns GINT_ETIMEDOUT (once) when a bounded wait of the tensor-core build gave up. */
 typedef struct gint_cn gint_cn;
 int gint_cn_create(int n, int nocc, gint_cn **out);
 int gint_cn_destroy(gint_cn *c);
 int gint_cn_step(gint_cn *c, const double *S, const double *H, double dt, const double *psi, double *psi_out,
                  void *stream);
 int gint_dm_build(gint_cn *c, const double *psi, const double *f, double *D, void *stream);
+int gint_dm_build_f16x3(gint_cn *c, const double *psi, const double *f, double *D, void *stream);
 int gint_cn_info(gint_cn *c, int *info);
 
 /* Energy-density matrix E = (S^{-1} H D + D H S^{-1}) / 2 (the overlap part of the forces needs it):

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libgint.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gint_capi.cu", "gint_nbr.cu", "gint_simt.cu", "gint_tc.cu", "gint_noalloc.cu", "gint_hr.cu", "gint_pb.cu", "gint_cn.cu"]
+SOURCES = ["gint_capi.cu", "gint_nbr.cu", "gint_simt.cu", "gint_tc.cu", "gint_noalloc.cu", "gint_hr.cu", "gint_pb.cu", "gint_cn.cu", "gint_dm.cu"]
 
 
 def nvcc() -> str:

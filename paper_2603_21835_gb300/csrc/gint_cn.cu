@@ -2,7 +2,8 @@
 // from coefficients and occupations, D = Re(psi diag(f) psi^dagger), one Crank-Nicolson step of the
 // coefficients, (S + i dt/2 H) psi(t + dt) = (S - i dt/2 H) psi(t), by LU factorisation (paper Sec. 2:
 // the density matrix and the time propagation of the coefficients with the overlap matrix), and the
-// energy-density matrix E = (S^{-1} H D + D H S^{-1}) / 2 by a Cholesky solve.
+// energy-density matrix E = (S^{-1} H D + D H S^{-1}) / 2 by a Cholesky solve.  The density matrix
+// also has a tensor-core build (float16 three-term split, gint_dm.cu).
 //
 // Both are plain library operations: complex GEMMs (cuBLAS) and an LU factorisation with partial
 // pivoting and its solve (cuSOLVER).  The libraries are loaded on first use (dlopen), so the grid
@@ -19,6 +20,7 @@
 #include <string>
 
 #include "gint.h"
+#include "gint_dm.cuh"
 
 #ifndef GINT_CUDA_LIB_DIR
 #define GINT_CUDA_LIB_DIR "/usr/local/cuda/lib64"
@@ -129,6 +131,8 @@ struct gint_cn {
   int n = 0, nocc = 0, device = 0, lwork = 0, lwork_r = 0;
   cuDoubleComplex *A = nullptr, *W = nullptr, *Y = nullptr, *work = nullptr;
   int *ipiv = nullptr, *info = nullptr;
+  void *dmw = nullptr;         // tensor-core density-matrix build: packed operands and scales
+  unsigned *status = nullptr;  // its device error word
   cublasHandle_t blas = nullptr;
   cusolverDnHandle_t sol = nullptr;
 };
@@ -145,6 +149,8 @@ int gint_cn_destroy(gint_cn *c) {
   cudaFree(c->work);
   cudaFree(c->ipiv);
   cudaFree(c->info);
+  cudaFree(c->dmw);
+  cudaFree(c->status);
   if (c->blas) L.blas_destroy(c->blas);
   if (c->sol) L.sol_destroy(c->sol);
   delete c;
@@ -164,7 +170,9 @@ int gint_cn_create(int n, int nocc, gint_cn **out) {
   if (cudaMalloc(&c->A, nn * sizeof(cuDoubleComplex)) != cudaSuccess ||
       cudaMalloc(&c->W, nn * sizeof(cuDoubleComplex)) != cudaSuccess ||
       cudaMalloc(&c->Y, (size_t)n * nocc * sizeof(cuDoubleComplex)) != cudaSuccess ||
-      cudaMalloc(&c->ipiv, (size_t)n * sizeof(int)) != cudaSuccess || cudaMalloc(&c->info, sizeof(int)) != cudaSuccess) {
+      cudaMalloc(&c->ipiv, (size_t)n * sizeof(int)) != cudaSuccess || cudaMalloc(&c->info, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->dmw, gint_dm_tc_bytes(n, nocc)) != cudaSuccess ||
+      cudaMalloc(&c->status, sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
     gint_cn_destroy(c);
     return GINT_ENOMEM;
@@ -179,7 +187,7 @@ int gint_cn_create(int n, int nocc, gint_cn **out) {
   // one workspace for both factorisations (complex elements; the real one needs lwork_r doubles)
   c->lwork = std::max(c->lwork, (c->lwork_r + 1) / 2);
   if (cudaMalloc(&c->work, (size_t)std::max(c->lwork, 1) * sizeof(cuDoubleComplex)) != cudaSuccess ||
-      cudaMemset(c->info, 0, sizeof(int)) != cudaSuccess) {
+      cudaMemset(c->info, 0, sizeof(int)) != cudaSuccess || cudaMemset(c->status, 0, sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
     gint_cn_destroy(c);
     return GINT_ENOMEM;
@@ -228,6 +236,11 @@ int gint_dm_build(gint_cn *c, const double *psi, const double *f, double *D, voi
   return cudaGetLastError() == cudaSuccess ? GINT_OK : GINT_ECUDA;
 }
 
+int gint_dm_build_f16x3(gint_cn *c, const double *psi, const double *f, double *D, void *stream) {
+  if (!c || !psi || !f || !D) return GINT_EINVAL;
+  return gint_dm_tc(c->n, c->nocc, psi, f, D, c->dmw, c->status, (cudaStream_t)stream);
+}
+
 int gint_edm(gint_cn *c, const double *S, const double *H, const double *D, double *E, void *stream) {
   if (!c || !S || !H || !D || !E) return GINT_EINVAL;
   const Libs &L = libs();
@@ -253,7 +266,15 @@ int gint_edm(gint_cn *c, const double *S, const double *H, const double *D, doub
 
 int gint_cn_info(gint_cn *c, int *info) {
   if (!c || !info) return GINT_EINVAL;
-  return cudaMemcpy(info, c->info, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess ? GINT_OK : GINT_ECUDA;
+  unsigned st = 0;
+  if (cudaMemcpy(info, c->info, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&st, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return GINT_ECUDA;
+  if (st != 0) {
+    cudaMemset(c->status, 0, sizeof(unsigned));
+    return GINT_ETIMEDOUT;
+  }
+  return GINT_OK;
 }
 
 }  // extern "C"

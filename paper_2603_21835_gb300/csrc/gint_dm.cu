@@ -1,0 +1,309 @@
+// gint_dm.cu -- the density matrix D = Re(psi diag(f) psi^dagger) (paper Sec. 2: rho_{mu nu} =
+// sum_n f_n c_{mu n} c*_{nu n}, real part at the Gamma point) on the tcgen05 tensor cores.
+//
+// With k = 2 s + (0: real part, 1: imaginary part) the build is one real product D = A B^T,
+// A_ik = f_s psi_is and B_ik = psi_is (parts), K = 2 nocc.  Each operand is scaled by one power of
+// two (its largest magnitude lands in [2^14, 2^15)) and split into float16 hi + lo, and
+//   A B^T ~ Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T
+// runs as kind::f16 MMAs with float32 accumulators in tensor memory (lo lo, ~2^-22 of a product,
+// is dropped).  The tensor core's float32 accumulation does not round to nearest, so its error grows
+// with the number of MMAs added into one accumulator: the hi hi products of each K chunk of 64 (four
+// MMAs) go to a fresh accumulator of a 3-deep ring, which drain warps add into float32 Kahan sums in
+// registers; the cross products, 2^-11 smaller, stay in one accumulator for the whole K range.
+//
+// k_dm_absmax: the two scales' maxima (float64 bits, atomicMax).
+// k_dm_pack: operands -> hi/lo core-matrix blocks: block (row tile t, chunk q) is 32 KB,
+//   [hi 16 KB | lo 16 KB], each 128 rows x 64 k float16, core matrix (row group g, k group h) at
+//   byte (g * 8 + h) * 128 (K-major, no swizzle: LBO 128, SBO 1024).  Rows >= n, k >= 2 nocc: 0.
+// k_dm_mma: one CTA of 16 warps per tile pair I <= J of D (128 x 128).  Lane 0 of warp 0 streams
+//   the A (tile I) and B (tile J) blocks of each chunk by two bulk copies into a 3-stage ring and
+//   issues 12 MMAs per chunk (4 K steps x 3 products); all 16 warps drain the hi hi accumulators
+//   (row = TMEM lane, 32 columns a warp) and write D[i, j] and D[j, i] from one value, so D is
+//   symmetric bit for bit.  (Sixteen warps keep the register cap at 128 for the Kahan sums.)
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "gint.h"
+#include "gint_dm.cuh"
+#include "gint_ptx.cuh"
+
+namespace {
+using namespace gptx;
+
+constexpr int kTile = 128;                        // rows (and columns) of a D tile: M = N = 128
+constexpr int kKC = 64;                           // k values per chunk: 4 MMA K steps of 16
+constexpr int kStages = 3;                        // chunks in flight
+constexpr int kHH = 3;                            // ring of hi hi accumulators (128 TMEM columns each)
+constexpr uint32_t kCrossCol = kHH * 128;         // the hi lo + lo hi accumulator
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kHalfBytes = kTile * kKC * 2;  // one float16 part of a block: 16 KB
+constexpr uint32_t kBlockBytes = 2 * kHalfBytes;  // hi then lo
+constexpr uint32_t kStageBytes = 2 * kBlockBytes;  // A block then B block
+constexpr uint32_t kSmemBytes = kStages * kStageBytes;
+constexpr int kDrainWarps = 16;                   // four per TMEM lane quarter, 32 columns each
+constexpr int kDrainCols = kTile / (kDrainWarps / 4);
+constexpr int kDmThreads = 32 * kDrainWarps;
+static_assert(kCrossCol + 128 <= kTmemCols, "tensor memory columns");
+constexpr long long kWaitNs = 2000000000LL;  // bounded waits: 2 s
+constexpr unsigned kErrTimeout = 1u;
+
+// Scale exponent of an operand: 2^sigma * max lands in [2^14, 2^15) (float16 max 65504).
+__device__ __forceinline__ int dm_sigma(unsigned long long bits) {
+  const double m = __longlong_as_double((long long)bits);
+  return m > 0.0 ? 14 - ilogb(m) : 0;
+}
+
+// m[0] = max |f_s psi_is| and m[1] = max |psi_is| over real and imaginary parts (float64 bits of
+// non-negative values order like the unsigned integers).
+__global__ void k_dm_absmax(int n, int nocc, const double2 *__restrict__ psi, const double *__restrict__ f,
+                            unsigned long long *m) {
+  double a = 0.0, b = 0.0;
+  const long long tot = (long long)n * nocc;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const double2 p = psi[e];
+    const double x = fmax(fabs(p.x), fabs(p.y));
+    b = fmax(b, x);
+    a = fmax(a, fabs(f[e / n]) * x);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&m[0], (unsigned long long)__double_as_longlong(a));
+    atomicMax(&m[1], (unsigned long long)__double_as_longlong(b));
+  }
+}
+
+__device__ __forceinline__ void split_f16(double x, __half &hi, __half &lo) {
+  hi = __double2half(x);
+  lo = __double2half(x - (double)__half2float(hi));
+}
+
+// One thread per (row i, group of 8 k = 4 states): reads psi[s][i] (coalesced over i) and writes one
+// 16-byte core-matrix row of hi and of lo, for A and for B.
+__global__ void k_dm_pack(int n, int nocc, int T, int nq, const double2 *__restrict__ psi, const double *__restrict__ f,
+                          const unsigned long long *__restrict__ m, unsigned char *__restrict__ PA,
+                          unsigned char *__restrict__ PB) {
+  const double sa = ldexp(1.0, dm_sigma(m[0])), sb = ldexp(1.0, dm_sigma(m[1]));
+  const long long np = (long long)T * kTile, tot = np * (nq * (kKC / 8));
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % np), kg = (int)(e / np);
+    __align__(16) __half ah[8], al[8], bh[8], bl[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int s = kg * 4 + j;
+      double2 p = make_double2(0.0, 0.0);
+      double fs = 0.0;
+      if (i < n && s < nocc) {
+        p = psi[(long long)s * n + i];
+        fs = f[s];
+      }
+      split_f16(fs * p.x * sa, ah[2 * j], al[2 * j]);
+      split_f16(fs * p.y * sa, ah[2 * j + 1], al[2 * j + 1]);
+      split_f16(p.x * sb, bh[2 * j], bl[2 * j]);
+      split_f16(p.y * sb, bh[2 * j + 1], bl[2 * j + 1]);
+    }
+    const int t = i / kTile, r = i % kTile, q = kg / (kKC / 8), h = kg % (kKC / 8);
+    const size_t off = ((size_t)t * nq + q) * kBlockBytes + (size_t)((r >> 3) * 8 + h) * 128 + (r & 7) * 16;
+    *reinterpret_cast<uint4 *>(PA + off) = *reinterpret_cast<const uint4 *>(ah);
+    *reinterpret_cast<uint4 *>(PA + off + kHalfBytes) = *reinterpret_cast<const uint4 *>(al);
+    *reinterpret_cast<uint4 *>(PB + off) = *reinterpret_cast<const uint4 *>(bh);
+    *reinterpret_cast<uint4 *>(PB + off + kHalfBytes) = *reinterpret_cast<const uint4 *>(bl);
+  }
+}
+
+// Kahan step: (s, c) += x, the running sum s and its lost low part c (true sum ~ s - c).
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+struct DmShared {
+  uint64_t full[kStages], empty[kStages], hfull[kHH], hfree[kHH], done;
+  uint32_t tmem;
+};
+
+// Copies of chunk c (A tile I, B tile J) into its stage.
+__device__ __forceinline__ void dm_load(DmShared &sh, unsigned char *smem, const unsigned char *PA,
+                                        const unsigned char *PB, int I, int J, int nq, int c) {
+  const int s = c % kStages;
+  mbar_arrive_tx(&sh.full[s], kStageBytes);
+  bulk_g2s(smem + s * kStageBytes, PA + ((size_t)I * nq + c) * kBlockBytes, kBlockBytes, &sh.full[s]);
+  bulk_g2s(smem + s * kStageBytes + kBlockBytes, PB + ((size_t)J * nq + c) * kBlockBytes, kBlockBytes, &sh.full[s]);
+}
+
+// One warp adds its 32 rows x kDrainCols columns of the hi hi accumulator of chunk c into the
+// Kahan sums and releases the accumulator; false if the wait gave up.
+__device__ __forceinline__ bool dm_drain(DmShared &sh, uint32_t lane_base, int c, float *sum, float *cmp,
+                                         unsigned *status) {
+  const int a = c % kHH;
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(&sh.hfull[a], (uint32_t)(c / kHH) & 1u, status, kErrTimeout,
+                                                     kWaitNs));
+  if (!ok) return false;
+  tc_fence_after();
+#pragma unroll
+  for (int g = 0; g < kDrainCols / 16; ++g) {
+    float y[16];
+    tmem_ld16(lane_base + (uint32_t)a * 128u + (uint32_t)g * 16u, y);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) kahan_add(sum[g * 16 + j], cmp[g * 16 + j], y[j]);
+  }
+  tc_fence_before();
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(&sh.hfree[a]);
+  return true;
+}
+
+__global__ void __launch_bounds__(kDmThreads, 1)
+    k_dm_mma(int n, int nq, const unsigned char *__restrict__ PA, const unsigned char *__restrict__ PB,
+             const unsigned long long *__restrict__ m, double *__restrict__ D, unsigned *status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ DmShared sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // tile pair p -> (I, J), I <= J, p = J (J + 1) / 2 + I
+  const long long p = blockIdx.x;
+  int J = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
+  while ((long long)J * (J + 1) / 2 > p) --J;
+  while ((long long)(J + 1) * (J + 2) / 2 <= p) ++J;
+  const int I = (int)(p - (long long)J * (J + 1) / 2);
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&sh.full[s], 1);
+      mbar_init(&sh.empty[s], 1);
+    }
+    for (int a = 0; a < kHH; ++a) {
+      mbar_init(&sh.hfull[a], 1);
+      mbar_init(&sh.hfree[a], kDrainWarps);
+    }
+    mbar_init(&sh.done, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&sh.tmem, kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sh.tmem;
+
+  // warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its rows) and kDrainCols columns from kDrainCols (w / 4)
+  const int r = (warp & 3) * 32 + lane, c0 = (warp >> 2) * kDrainCols;
+  const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
+  float sum[kDrainCols], cmp[kDrainCols];
+#pragma unroll
+  for (int j = 0; j < kDrainCols; ++j) sum[j] = cmp[j] = 0.f;
+  bool ok = true;
+
+  if (warp == 0) {
+    // lane 0 issues: chunk c's MMAs (hi hi into ring slot c mod kHH, hi lo + lo hi into the cross
+    // slot), then the refill of chunk c - 1's stage once its MMAs are done; the warp drains chunk
+    // c - 2 (the slot the MMAs of chunk c + 1 will take).
+    const uint32_t idesc = idesc_f16(kTile, kTile), sbase = smem_u32(smem), dx = tmem + kCrossCol;
+    int issued = 0, consumed = 0;
+    if (lane == 0)
+      for (; issued < min(kStages, nq); ++issued) dm_load(sh, smem, PA, PB, I, J, nq, issued);
+    for (int c = 0; c < nq && ok; ++c) {
+      bool lok = true;
+      if (lane == 0) {
+        const int s = c % kStages, a = c % kHH;
+        lok = mbar_wait(&sh.full[s], (uint32_t)(c / kStages) & 1u, status, kErrTimeout, kWaitNs);
+        if (lok) consumed = c + 1;
+        if (lok && c >= kHH)
+          lok = mbar_wait(&sh.hfree[a], (uint32_t)((c / kHH) - 1) & 1u, status, kErrTimeout, kWaitNs);
+        if (lok) {
+          tc_fence_after();
+          const uint32_t sa = sbase + s * kStageBytes, sb = sa + kBlockBytes;
+          const uint32_t dh = tmem + (uint32_t)a * 128u;
+#pragma unroll
+          for (int ks = 0; ks < kKC / 16; ++ks) {
+            const uint32_t o = ks * 256;  // two core matrices along K per step
+            const uint64_t ah = sdesc(sa + o, 128, 1024), al = sdesc(sa + kHalfBytes + o, 128, 1024);
+            const uint64_t bh = sdesc(sb + o, 128, 1024), bl = sdesc(sb + kHalfBytes + o, 128, 1024);
+            mma_f16(dh, ah, bh, idesc, ks > 0 ? 1u : 0u);
+            mma_f16(dx, ah, bl, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+            mma_f16(dx, al, bh, idesc, 1u);
+          }
+          mma_commit(&sh.empty[s]);
+          mma_commit(&sh.hfull[a]);
+          if (c >= 1 && issued < nq) {
+            lok = mbar_wait(&sh.empty[(c - 1) % kStages], (uint32_t)((c - 1) / kStages) & 1u, status, kErrTimeout,
+                            kWaitNs);
+            if (lok) dm_load(sh, smem, PA, PB, I, J, nq, issued++);
+          }
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, lok, 0);
+      if (ok && c >= 2) ok = dm_drain(sh, lane_base, c - 2, sum, cmp, status);
+    }
+    if (lane == 0) {
+      mma_commit(&sh.done);
+      // no copy may still be landing in shared memory when the CTA exits
+      for (int c = consumed; c < issued; ++c)
+        mbar_wait(&sh.full[c % kStages], (uint32_t)(c / kStages) & 1u, status, kErrTimeout, kWaitNs);
+    }
+    for (int c = max(0, nq - 2); c < nq && ok; ++c) ok = dm_drain(sh, lane_base, c, sum, cmp, status);
+  } else {
+    for (int c = 0; c < nq && ok; ++c) ok = dm_drain(sh, lane_base, c, sum, cmp, status);
+  }
+
+  ok = __all_sync(0xffffffffu, ok && mbar_wait(&sh.done, 0u, status, kErrTimeout, kWaitNs));
+  tc_fence_after();
+  if (ok) {
+    const double scale = ldexp(1.0, -(dm_sigma(m[0]) + dm_sigma(m[1])));
+    const long long i = (long long)I * kTile + r;
+#pragma unroll
+    for (int g = 0; g < kDrainCols / 16; ++g) {
+      float x[16];
+      tmem_ld16(lane_base + kCrossCol + (uint32_t)g * 16u, x);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const long long jj = (long long)J * kTile + c0 + g * 16 + j;
+        if (i < n && jj < n && (I != J || jj >= i)) {
+          const double v = (((double)sum[g * 16 + j] - (double)cmp[g * 16 + j]) + (double)x[j]) * scale;
+          D[i * n + jj] = v;
+          D[jj * n + i] = v;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+unsigned grid_for(long long work) { return (unsigned)std::max<long long>(1, std::min<long long>((work + 255) / 256, 152 * 16)); }
+
+}  // namespace
+
+size_t gint_dm_tc_bytes(int n, int nocc) {
+  const long long T = (n + kTile - 1) / kTile, nq = (2LL * nocc + kKC - 1) / kKC;
+  return (size_t)(2 * T * nq) * kBlockBytes + 2 * sizeof(unsigned long long);
+}
+
+int gint_dm_tc(int n, int nocc, const double *psi, const double *f, double *D, void *work, unsigned *status,
+               cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_dm_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess)
+      return GINT_ECUDA;
+    attr = true;
+  }
+  const int T = (n + kTile - 1) / kTile, nq = (2 * nocc + kKC - 1) / kKC;
+  unsigned char *PA = static_cast<unsigned char *>(work), *PB = PA + (size_t)T * nq * kBlockBytes;
+  unsigned long long *m = reinterpret_cast<unsigned long long *>(PB + (size_t)T * nq * kBlockBytes);
+  if (cudaMemsetAsync(m, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) return GINT_ECUDA;
+  const double2 *P = reinterpret_cast<const double2 *>(psi);
+  k_dm_absmax<<<grid_for((long long)n * nocc), 256, 0, st>>>(n, nocc, P, f, m);
+  k_dm_pack<<<grid_for((long long)T * kTile * nq * (kKC / 8)), 256, 0, st>>>(n, nocc, T, nq, P, f, m, PA, PB);
+  k_dm_mma<<<(unsigned)((long long)T * (T + 1) / 2), kDmThreads, kSmemBytes, st>>>(n, nq, PA, PB, m, D, status);
+  return cudaGetLastError() == cudaSuccess ? GINT_OK : GINT_ECUDA;
+}

@@ -87,6 +87,7 @@ _lib.gint_cn_create.argtypes = [_i, _i, ctypes.POINTER(_vp)]
 _lib.gint_cn_destroy.argtypes = [_vp]
 _lib.gint_cn_step.argtypes = [_vp, _vp, _vp, _d, _vp, _vp, _vp]
 _lib.gint_dm_build.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.gint_dm_build_f16x3.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.gint_cn_info.argtypes = [_vp, ctypes.POINTER(_i)]
 _lib.gint_edm.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
 
@@ -95,7 +96,7 @@ C_ABI_SYMBOLS = ("gint_create", "gint_destroy", "gint_layout", "gint_pairs", "gi
                  "gint_strerror", "gint_sync", "gint_tc_selftest", "gint_grid_dot_noalloc", "gint_run_batch",
                  "gint_run_batch_timed", "gint_memory", "gint_layout_R", "gint_vlocal_R", "gint_bloch",
                  "gint_set_projectors", "gint_psibeta_layout", "gint_psibeta", "gint_cn_create", "gint_cn_destroy",
-                 "gint_cn_step", "gint_dm_build", "gint_cn_info", "gint_edm")
+                 "gint_cn_step", "gint_dm_build", "gint_dm_build_f16x3", "gint_cn_info", "gint_edm")
 
 
 class CrankNicolson:
@@ -124,12 +125,14 @@ class CrankNicolson:
         return out
 
     def density_matrix(self, psi: torch.Tensor, f: torch.Tensor, out: Optional[torch.Tensor] = None,
-                       stream=None) -> torch.Tensor:
-        """Re(psi^T diag(f) conj(psi)) as [n, n] float64 (rows of psi are the states)."""
+                       stream=None, precision: str = "fp64") -> torch.Tensor:
+        """Re(psi^T diag(f) conj(psi)) as [n, n] float64 (rows of psi are the states); precision "fp64"
+        (complex float64 GEMM) or "f16x3" (tensor cores, float16 three-term split)."""
         if out is None:
             out = torch.empty((self.n, self.n), dtype=torch.float64, device=psi.device)
-        _check(_lib.gint_dm_build(self._c, self._cplx(psi), _dptr(f, numel=self.nocc), _dptr(out, numel=self.n * self.n),
-                                  _stream(stream)), "gint_dm_build")
+        fn = {"fp64": _lib.gint_dm_build, "f16x3": _lib.gint_dm_build_f16x3}[precision]
+        _check(fn(self._c, self._cplx(psi), _dptr(f, numel=self.nocc), _dptr(out, numel=self.n * self.n),
+                  _stream(stream)), "gint_dm_build")
         return out
 
     def energy_density_matrix(self, S: torch.Tensor, H: torch.Tensor, D: torch.Tensor,

@@ -1,7 +1,8 @@
 """GPU parity of the density-matrix build, the Crank-Nicolson step (paper Sec. 2) and the energy-
 density matrix against the LAPACK oracle (oracle/dense.py), all in float64: 1e-12 of the largest
-entry; and the loop rho -> H -> psi -> rho closed on the 8-atom Si cell with the grid library's own
-passes."""
+entry; the tensor-core density-matrix build (float16 three-term split) within 1e-6 of
+max_i sum_s |f_s| |psi_is|^2; and the loop rho -> H -> psi -> rho closed on the 8-atom Si cell with
+the grid library's own passes."""
 import numpy as np
 import pytest
 
@@ -93,3 +94,42 @@ def test_loop_rho_H_psi_rho_on_the_grid():
     assert np.abs(rho - rref).max() <= 1e-8 * np.abs(rref).max(), cond
     cn.close()
     g.close()
+
+
+@pytest.mark.parametrize("n,nocc,signed", [(832, 64, False), (700, 37, True), (130, 3, False), (6656, 1024, False)])
+def test_tensor_core_density_matrix(n, nocc, signed):
+    """Ragged n (tiles of 128) and K = 2 nocc (chunks of 64), fewer chunks than accumulators (nocc 3),
+    occupations of both signs, and the 512-atom size (6656 orbitals, 1024 states) on sampled rows."""
+    import torch
+
+    from paper_2603_21835_gb300 import gint as G
+
+    rng = np.random.default_rng(n + nocc)
+    psi = (rng.normal(size=(n, nocc)) + 1j * rng.normal(size=(n, nocc))) / 32
+    f = rng.uniform(-1, 2, size=nocc) if signed else rng.uniform(0, 2, size=nocc)
+    cn = G.CrankNicolson(n, nocc)
+    pd = torch.from_numpy(np.ascontiguousarray(psi.T)).cuda()
+    D = cn.density_matrix(pd, torch.from_numpy(f).cuda(), precision="f16x3").cpu().numpy()
+    assert cn.info() == 0
+    cn.close()
+    assert np.array_equal(D, D.T)
+    bound = (np.abs(psi) ** 2 @ np.abs(f)).max()
+    idx = np.arange(n) if n <= 1024 else np.unique(np.r_[rng.choice(n, 300, replace=False), 0, n - 1])
+    ref = density_matrix(psi[idx], f)
+    err = np.abs(D[np.ix_(idx, idx)] - ref).max()
+    print(f"n={n} nocc={nocc}: max error {err / bound:.3g} of max_i sum_s |f_s| |psi_is|^2")
+    assert err <= 1e-6 * bound, (err, bound)
+    assert err > 0.0  # the float16 path ran, not a float64 one
+
+
+def test_tensor_core_density_matrix_of_zero_states_is_zero():
+    import torch
+
+    from paper_2603_21835_gb300 import gint as G
+
+    cn = G.CrankNicolson(200, 5)
+    D = cn.density_matrix(torch.zeros((5, 200), dtype=torch.complex128, device="cuda"),
+                          torch.ones(5, dtype=torch.float64, device="cuda"), precision="f16x3")
+    assert cn.info() == 0
+    assert torch.count_nonzero(D).item() == 0
+    cn.close()
