@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dense-only", action="store_true",
+                    help="time only the dense steps (Crank-Nicolson, density matrices) at the workload's basis size")
     ap.add_argument("--serve-requests", type=int, default=256, help="Poisson serving run (0: skip)")
     ap.add_argument("--serve-load", type=float, default=0.75, help="arrival rate x mean service time alone")
     ap.add_argument("--serve-budget-gb", type=float, default=32.0)
@@ -458,6 +460,13 @@ def main():
     prec = G.PRECISIONS[args.precision]
     w = inputs.config_workload(args.workload, dense_D=False)
     g = G.Gint(w.system)
+    if args.dense_only:
+        n = g.norb
+        g.close()
+        cn = run_cn(n, 128 if n < 2048 else 1024, 3 if n < 2048 else 2, torch.cuda.current_stream())
+        if rank == 0:
+            print(json.dumps({"workload": args.workload, "crank_nicolson": cn}), flush=True)
+        return
     st = g.stats()
     W = st["W"]
     Db_host = g.blocks_from_coefficients(w.C)
