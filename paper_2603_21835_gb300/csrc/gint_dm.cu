@@ -11,7 +11,7 @@
 // MMAs) go to a fresh accumulator of a 3-deep ring, which drain warps add into float32 Kahan sums in
 // registers; the cross products, 2^-11 smaller, stay in one accumulator for the whole K range.
 //
-// k_dm_absmax: the two scales' maxima (float64 bits, atomicMax).
+// k_dm_absmax: the two scales' maxima (bit patterns of |x|, integer compares, atomicMax).
 // k_dm_pack: operands -> hi/lo core-matrix blocks: block (row tile t, chunk q) is 32 KB,
 //   [hi 16 KB | lo 16 KB], each 128 rows x 64 k float16, core matrix (row group g, k group h) at
 //   byte (g * 8 + h) * 128 (K-major, no swizzle: LBO 128, SBO 1024).  Rows >= n, k >= 2 nocc: 0.
@@ -56,59 +56,83 @@ __device__ __forceinline__ int dm_sigma(unsigned long long bits) {
   return m > 0.0 ? 14 - ilogb(m) : 0;
 }
 
-// m[0] = max |f_s psi_is| and m[1] = max |psi_is| over real and imaginary parts (float64 bits of
-// non-negative values order like the unsigned integers).
-__global__ void k_dm_absmax(int n, int nocc, const double2 *__restrict__ psi, const double *__restrict__ f,
-                            unsigned long long *m) {
-  double a = 0.0, b = 0.0;
-  const long long tot = (long long)n * nocc;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const double2 p = psi[e];
-    const double x = fmax(fabs(p.x), fabs(p.y));
-    b = fmax(b, x);
-    a = fmax(a, fabs(f[e / n]) * x);
+// Bit pattern of |x|: for non-negative doubles it orders like the value.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// m[0] = max |f_s psi_is| and m[1] = max |psi_is| over real and imaginary parts, as the bit
+// patterns of non-negative doubles.  Blocks along y take states, along x orbitals (coalesced); the
+// maxima over psi are integer compares, one multiply by |f_s| per thread and state.
+__global__ void __launch_bounds__(256) k_dm_absmax(int n, int nocc, const double2 *__restrict__ psi,
+                                                   const double *__restrict__ f, unsigned long long *m) {
+  unsigned long long a = 0, b = 0;
+  for (int s = blockIdx.y; s < nocc; s += gridDim.y) {
+    const double2 *row = psi + (long long)s * n;
+    unsigned long long x = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const double2 p = row[i];
+      x = max(x, max(abs_bits(p.x), abs_bits(p.y)));
+    }
+    b = max(b, x);
+    a = max(a, abs_bits(f[s] * __longlong_as_double((long long)x)));
   }
+  __shared__ unsigned long long ra[8], rb[8];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
-    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
   }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(&m[0], (unsigned long long)__double_as_longlong(a));
-    atomicMax(&m[1], (unsigned long long)__double_as_longlong(b));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    ra[warp] = a;
+    rb[warp] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      a = max(a, ra[w]);
+      b = max(b, rb[w]);
+    }
+    atomicMax(&m[0], a);
+    atomicMax(&m[1], b);
   }
 }
 
-__device__ __forceinline__ void split_f16(double x, __half &hi, __half &lo) {
-  hi = __double2half(x);
-  lo = __double2half(x - (double)__half2float(hi));
+__device__ __forceinline__ void split_f16(float x, __half &hi, __half &lo) {
+  hi = __float2half_rn(x);
+  lo = __float2half_rn(x - __half2float(hi));
 }
 
-// One thread per (row i, group of 8 k = 4 states): reads psi[s][i] (coalesced over i) and writes one
-// 16-byte core-matrix row of hi and of lo, for A and for B.
-__global__ void k_dm_pack(int n, int nocc, int T, int nq, const double2 *__restrict__ psi, const double *__restrict__ f,
-                          const unsigned long long *__restrict__ m, unsigned char *__restrict__ PA,
-                          unsigned char *__restrict__ PB) {
-  const double sa = ldexp(1.0, dm_sigma(m[0])), sb = ldexp(1.0, dm_sigma(m[1]));
-  const long long np = (long long)T * kTile, tot = np * (nq * (kKC / 8));
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % np), kg = (int)(e / np);
+// Block (x, y): rows i = 128 x + t of the operands, groups of 8 k (4 states) kg = y, y + gridDim.y,
+// ...; each thread reads psi[s][i] (coalesced over i) and writes one 16-byte core-matrix row of hi
+// and of lo, for A and for B.  B = 2^sigmaB psi is scaled in float64 (exact) and rounded to float32
+// once; A = B (f_s 2^(sigmaA - sigmaB)) is formed in float32 (relative error 2^-24, below the
+// split's 2^-23); the hi / lo split is float32 arithmetic.
+__global__ void __launch_bounds__(kTile) k_dm_pack(int n, int nocc, int nq, const double2 *__restrict__ psi,
+                                                   const double *__restrict__ f, const unsigned long long *__restrict__ m,
+                                                   unsigned char *__restrict__ PA, unsigned char *__restrict__ PB) {
+  const int sa = dm_sigma(m[0]), sb = dm_sigma(m[1]);
+  const double scb = ldexp(1.0, sb), rab = ldexp(1.0, sa - sb);
+  const int t = blockIdx.x, r = threadIdx.x, i = t * kTile + r;
+  for (int kg = blockIdx.y; kg < nq * (kKC / 8); kg += gridDim.y) {
     __align__(16) __half ah[8], al[8], bh[8], bl[8];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int s = kg * 4 + j;
-      double2 p = make_double2(0.0, 0.0);
-      double fs = 0.0;
+      float bx = 0.f, by = 0.f, fa = 0.f;
       if (i < n && s < nocc) {
-        p = psi[(long long)s * n + i];
-        fs = f[s];
+        const double2 p = psi[(long long)s * n + i];
+        bx = (float)(p.x * scb);
+        by = (float)(p.y * scb);
+        fa = (float)(f[s] * rab);
       }
-      split_f16(fs * p.x * sa, ah[2 * j], al[2 * j]);
-      split_f16(fs * p.y * sa, ah[2 * j + 1], al[2 * j + 1]);
-      split_f16(p.x * sb, bh[2 * j], bl[2 * j]);
-      split_f16(p.y * sb, bh[2 * j + 1], bl[2 * j + 1]);
+      split_f16(bx * fa, ah[2 * j], al[2 * j]);
+      split_f16(by * fa, ah[2 * j + 1], al[2 * j + 1]);
+      split_f16(bx, bh[2 * j], bl[2 * j]);
+      split_f16(by, bh[2 * j + 1], bl[2 * j + 1]);
     }
-    const int t = i / kTile, r = i % kTile, q = kg / (kKC / 8), h = kg % (kKC / 8);
+    const int q = kg / (kKC / 8), h = kg % (kKC / 8);
     const size_t off = ((size_t)t * nq + q) * kBlockBytes + (size_t)((r >> 3) * 8 + h) * 128 + (r & 7) * 16;
     *reinterpret_cast<uint4 *>(PA + off) = *reinterpret_cast<const uint4 *>(ah);
     *reinterpret_cast<uint4 *>(PA + off + kHalfBytes) = *reinterpret_cast<const uint4 *>(al);
@@ -280,8 +304,6 @@ __global__ void __launch_bounds__(kDmThreads, 1)
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-unsigned grid_for(long long work) { return (unsigned)std::max<long long>(1, std::min<long long>((work + 255) / 256, 152 * 16)); }
-
 }  // namespace
 
 size_t gint_dm_tc_bytes(int n, int nocc) {
@@ -302,8 +324,10 @@ int gint_dm_tc(int n, int nocc, const double *psi, const double *f, double *D, v
   unsigned long long *m = reinterpret_cast<unsigned long long *>(PB + (size_t)T * nq * kBlockBytes);
   if (cudaMemsetAsync(m, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) return GINT_ECUDA;
   const double2 *P = reinterpret_cast<const double2 *>(psi);
-  k_dm_absmax<<<grid_for((long long)n * nocc), 256, 0, st>>>(n, nocc, P, f, m);
-  k_dm_pack<<<grid_for((long long)T * kTile * nq * (kKC / 8)), 256, 0, st>>>(n, nocc, T, nq, P, f, m, PA, PB);
+  const dim3 ga((unsigned)std::max(1, std::min((n + 1023) / 1024, 64)), (unsigned)std::min(nocc, 256));
+  k_dm_absmax<<<ga, 256, 0, st>>>(n, nocc, P, f, m);
+  const dim3 gp((unsigned)T, (unsigned)std::min(nq * (kKC / 8), 256));
+  k_dm_pack<<<gp, kTile, 0, st>>>(n, nocc, nq, P, f, m, PA, PB);
   k_dm_mma<<<(unsigned)((long long)T * (T + 1) / 2), kDmThreads, kSmemBytes, st>>>(n, nq, PA, PB, m, D, status);
   return cudaGetLastError() == cudaSuccess ? GINT_OK : GINT_ECUDA;
 }
