@@ -192,7 +192,8 @@ int gint_psibeta(gint_handle *h, const double *A, double *out, void *stream);
  * (k = 2 s + real / imaginary part), each operand scaled by a power of two and split into float16
  * hi + lo, three float16 products per term with float32 accumulation over chunks of 64 k and a
  * float64 sum of four partial accumulators; D is symmetric bit for bit, and its error is about
- * 2^-21 of max_i sum_s |f_s| |psi_is|^2.  Occupations of any sign; no allocation.
+ * 2^-21 of max_i sum_s |f_s| |psi_is|^2.  Occupations of any sign; psi 16-byte aligned (as for
+ * every complex128 array here); no allocation.
  * gint_cn_info: the LAPACK-style info of the last factorisation (0: success; i > 0: U(i, i) = 0);
  * synchronous; returns GINT_ETIMEDOUT (once) when a bounded wait of the tensor-core build gave up. */
 typedef struct gint_cn gint_cn;

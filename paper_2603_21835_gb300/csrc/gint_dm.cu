@@ -313,12 +313,9 @@ size_t gint_dm_tc_bytes(int n, int nocc) {
 
 int gint_dm_tc(int n, int nocc, const double *psi, const double *f, double *D, void *work, unsigned *status,
                cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_dm_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess)
-      return GINT_ECUDA;
-    attr = true;
-  }
+  // set on every call: the attribute is per device and the call is cheap next to the build
+  if (cudaFuncSetAttribute(k_dm_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess)
+    return GINT_ECUDA;
   const int T = (n + kTile - 1) / kTile, nq = (2 * nocc + kKC - 1) / kKC;
   unsigned char *PA = static_cast<unsigned char *>(work), *PB = PA + (size_t)T * nq * kBlockBytes;
   unsigned long long *m = reinterpret_cast<unsigned long long *>(PB + (size_t)T * nq * kBlockBytes);
