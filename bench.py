@@ -466,6 +466,8 @@ def main():
         cn = run_cn(n, 128 if n < 2048 else 1024, 3 if n < 2048 else 2, torch.cuda.current_stream())
         if rank == 0:
             print(json.dumps({"workload": args.workload, "crank_nicolson": cn}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
         return
     st = g.stats()
     W = st["W"]
