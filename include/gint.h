@@ -190,10 +190,12 @@ int gint_psibeta(gint_handle *h, const double *A, double *out, void *stream);
  * gint_dm_build: D = Re(psi diag(f) psi^dagger), f [nocc] (device) occupations.
  * gint_dm_build_f16x3: the same D on the tensor cores: D = A B^T with A_ik = f_s psi_is, B_ik = psi_is
  * (k = 2 s + real / imaginary part), each operand scaled by a power of two and split into float16
- * hi + lo, three float16 products per term with float32 accumulation over chunks of 64 k and a
- * float64 sum of four partial accumulators; D is symmetric bit for bit, and its error is about
- * 2^-21 of max_i sum_s |f_s| |psi_is|^2.  Occupations of any sign; psi 16-byte aligned (as for
- * every complex128 array here); no allocation.
+ * hi + lo, three float16 products per term (lo lo dropped).  The hi hi products of each chunk of 64 k
+ * go to a fresh float32 tensor-memory accumulator, which is added into float32 Kahan sums; the
+ * cross products share one accumulator; the parts are combined in float64.  D is symmetric bit for
+ * bit; its error stays within about 3 * 2^-22 of max_i sum_s |f_s| |psi_is|^2 (measured up to
+ * 2.8e-7).  Occupations of any sign; psi 16-byte aligned (as for every complex128 array here); no
+ * allocation.
  * gint_cn_info: the LAPACK-style info of the last factorisation (0: success; i > 0: U(i, i) = 0);
  * synchronous; returns GINT_ETIMEDOUT (once) when a bounded wait of the tensor-core build gave up. */
 typedef struct gint_cn gint_cn;
