@@ -69,6 +69,29 @@ def test_s_type_with_phase_is_the_closed_form():
     assert abs(got - ref) <= 1e-11 * abs(ref)
 
 
+def test_p_type_with_phase_is_the_closed_form():
+    """beta = (r - tau_I)_c e^{-6 |r - tau_I|^2} (real solid harmonic, l = 1), phi = e^{-0.8 x^2} Y00 at
+    tau_J: with the Gaussian product K e^{-p |r - P|^2}, the integral of (r - tau_I)_c times it and
+    e^{-i A.r} is K (pi/p)^{3/2} e^{-|A|^2 / 4p} e^{-i A.P} [(P - tau_I)_c - i A_c / 2p] (the moment
+    from the derivative of the s-type result in A); a wrong phase centre or sign for l > 0 fails."""
+    tI, tJ = np.array([3.0, 4.0, 5.0]), np.array([4.1, 5.3, 3.9])
+    o, op = _pair_systems([_gauss_radial(0, 0.8, 7.5)], [_gauss_radial(1, 6.0, 2.5)], tI, tJ)
+    A = np.array([0.45, -0.3, 0.6])
+    got = o.psibeta(op, A, 0, 1, radial_rule(), angular_rule())[:, 0]
+    a, b = 6.0, 0.8
+    p = a + b
+    P = (a * tI + b * tJ) / p
+    K = math.exp(-a * b * np.sum((tI - tJ) ** 2) / p)
+    F = K * (math.pi / p) ** 1.5 * math.exp(-A @ A / (4 * p)) * np.exp(-1j * (A @ P)) / math.sqrt(4 * math.pi)
+    ref = np.zeros(3, dtype=np.complex128)
+    for m, poly in enumerate(_SOLID[1]):
+        for e, coef in poly.items():
+            c = e.index(1)
+            ref[m] += coef * F * ((P - tI)[c] - 0.5j * A[c] / p)
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+    assert np.abs(ref.imag).max() > 1e-3 * np.abs(ref).max()  # the field term is not negligible
+
+
 def test_zero_field_is_the_two_centre_overlap():
     """A = 0: a p-type projector against s and d orbitals equals the two-centre Gaussian overlap
     (product theorem with the real solid harmonics, the same Y_lm convention)."""
