@@ -543,12 +543,14 @@ def main():
     peaks, peak_kind = load_peaks()
     if tensor:
         dom, tdom = "k_tc_fused (density + local-H bricks)", statistics.mean(a.elapsed_time(b) for a, b in evk)
-        flops = 2.0 * W  # per pass one FMA per unordered orbital pair per grid point (D, H symmetric)
+        # 2 flops (one multiply-add) per ordered orbital pair per grid point per pass, both passes in
+        # this launch; the kernels use the symmetry of D and H and execute about half of it
+        flops = 4.0 * W
     else:
         mr = statistics.mean(a.elapsed_time(b) for a, b in evr)
         mh = statistics.mean(a.elapsed_time(b) for a, b in evh)
         dom, tdom = ("k_simt_rho", mr) if mr >= mh else ("k_simt_vlocal", mh)
-        flops = W
+        flops = 2.0 * W  # one pass per launch, 2 flops per ordered orbital pair per grid point
     if tensor:
         peak = peaks.get("bf16_tflops")
         bound, punit = "tensor", "TFLOP/s"
