@@ -525,10 +525,12 @@ def main():
     if world > 1:
         dist.barrier()
     t_steps = [a.elapsed_time(b) for a, b in ev]
-    # the passes one at a time (informational, outside the timed steps)
-    t_rho, t_h = [], []
+    # the passes one at a time, and the force pass (informational, outside the timed steps)
+    t_rho, t_h, t_f = [], [], []
+    F = torch.empty((g.natoms, 3), dtype=torch.float64, device=dev)
     for k in range(3):
-        for fn, lst in ((lambda: g.rho(Db, prec, out=rho), t_rho), (lambda: g.vlocal(V, prec, out=H), t_h)):
+        for fn, lst in ((lambda: g.rho(Db, prec, out=rho), t_rho), (lambda: g.vlocal(V, prec, out=H), t_h),
+                        (lambda: g.force(Db, V, prec, out=F), t_f)):
             flush.fill_(float(k))
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -633,6 +635,7 @@ def main():
                    "nbricks": st["nbricks"], "max_brick_orb": st["max_brick_orb"], "l2": "flushed (256 MB write)",
                    "parallelism": f"replicas{world}"},
         "ms_kernel": tdom, "ms_rho_alone": statistics.mean(t_rho), "ms_vlocal_alone": statistics.mean(t_h),
+        "ms_force_alone": statistics.mean(t_f),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches * args.steps, "serving": serving, "per_R": per_R, "psibeta": psibeta,
         "crank_nicolson": cn,
