@@ -72,3 +72,29 @@ def test_strerror_and_invalid_descriptors(lib):
     nanpos[0, 0] = np.nan
     with pytest.raises(G.GintError):
         G.Gint(inputs.System(cell=sysm.cell, pos=nanpos, species=sysm.species, sp=sysm.sp, grid=(8, 8, 8)))
+
+
+def test_entry_points_reject_null_arguments_on_the_host(lib):
+    """NULL handles, contexts and buffers come back as GINT_EINVAL before any CUDA call."""
+    EINVAL = -1
+    i, ll = ctypes.c_int(), ctypes.c_longlong()
+    assert lib.gint_layout_R(None, ctypes.byref(i), ctypes.byref(ll), None, None) == EINVAL
+    assert lib.gint_vlocal_R(None, 2, None, None, None) == EINVAL
+    assert lib.gint_bloch(None, None, 1, None, None, None) == EINVAL
+    assert lib.gint_set_projectors(None, 1, None) == EINVAL
+    assert lib.gint_psibeta_layout(None, ctypes.byref(i), ctypes.byref(ll), None, None) == EINVAL
+    assert lib.gint_psibeta(None, None, None, None) == EINVAL
+    c = ctypes.c_void_p()
+    assert lib.gint_cn_create(0, 4, ctypes.byref(c)) == EINVAL
+    assert lib.gint_cn_create(4, 0, ctypes.byref(c)) == EINVAL
+    assert lib.gint_cn_create(4, 4, None) == EINVAL
+    assert lib.gint_cn_step(None, None, None, ctypes.c_double(0.1), None, None, None) == EINVAL
+    assert lib.gint_dm_build(None, None, None, None, None) == EINVAL
+    assert lib.gint_dm_build_f16x3(None, None, None, None, None) == EINVAL
+    assert lib.gint_edm(None, None, None, None, None, None) == EINVAL
+    assert lib.gint_cn_info(None, ctypes.byref(i)) == EINVAL
+    assert lib.gint_cn_destroy(None) == 0
+    lib.gint_strerror.restype = ctypes.c_char_p
+    msgs = {code: lib.gint_strerror(code) for code in range(-8, 1)}
+    assert len(set(msgs.values())) == len(msgs) and all(msgs.values())
+    assert lib.gint_strerror(-99) == b"unknown error"
