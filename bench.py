@@ -6,9 +6,11 @@ workload (inputs resident in HBM).  Work unit: ordered orbital pairs per grid po
 W = sum_g n_g^2 per pass, so one step is 2W pair updates; the metric is Gpt-pair/s.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f16x3|fp64|fp32|f16x1]
-                  [--workload si64_g96|si8_g48|si512_g192] [--impl ours|reference]
+                  [--workload si512_g192|si64_g96|si8_g48] [--impl ours|reference]
 
-With the tensor-core precisions both passes' bricks run in one persistent launch per step.
+The default workload is the 512-atom Si supercell (4x4x4, 6656 orbitals, 192^3 grid).  With the
+tensor-core precisions both passes' bricks run in one persistent launch per step; the float64 GPU
+path is timed on the same workload in the same run (fp64_gpu), and the line reports the ratio.
 After the timed steps (rank 0, N = 1) a serving run submits a Poisson stream of density +
 local-H + force requests over a mix of Si supercells (8-216 atoms) and water clusters (8-64
 molecules) to the continuous-batching server and reports p50/p99 latency and throughput.
@@ -49,10 +51,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f16x3", choices=["f16x3", "fp64", "fp32", "f16x1"])
-    ap.add_argument("--workload", default="si64_g96")
+    ap.add_argument("--workload", default="si512_g192")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the float64 GPU comparator (0: skip)")
     ap.add_argument("--dense-only", action="store_true",
                     help="time only the dense steps (Crank-Nicolson, density matrices) at the workload's basis size")
     ap.add_argument("--serve-requests", type=int, default=256, help="Poisson serving run (0: skip)")
@@ -161,6 +164,19 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ oracle (CPU) baseline
+# the oracle's region of a workload: the 512-atom case is checked on the grid sub-volume [0, n/2)^3
+ORACLE_REGION = {"si512_g192": "sub-volume [0,96)^3 of the 192^3 grid"}
+
+
+def oracle_region(workload_name: str, grid):
+    """Grid indices the oracle baseline samples from (None: the whole grid)."""
+    if workload_name not in ORACLE_REGION:
+        return None
+    n1, n2, n3 = grid
+    i, j, k = np.meshgrid(np.arange(n1 // 2), np.arange(n2 // 2), np.arange(n3 // 2), indexing="ij")
+    return ((i * n2 + j) * n3 + k).reshape(-1)
+
+
 def oracle_sample(workload_name: str, target_s: float, seed: int = 7):
     """Times the FP64 oracle (rho + H over a random subset of grid points) on the host cores.
     Returns (Gpt-pair/s, threads, description)."""
@@ -170,20 +186,25 @@ def oracle_sample(workload_name: str, target_s: float, seed: int = 7):
     w = inputs.config_workload(workload_name, dense_D=True)
     o = Oracle(w.system)
     rng = np.random.default_rng(seed)
+    region = oracle_region(workload_name, o.grid)
+    pool = region if region is not None else np.arange(o.ngrid)
     n = 4000
     while True:
-        idx = np.sort(rng.choice(o.ngrid, n, replace=False))
+        idx = np.sort(rng.choice(pool, min(n, pool.size), replace=False))
         t0 = time.perf_counter()
         o.rho(w.D, idx)
         o.vlocal(w.V, idx)
         dt = time.perf_counter() - t0
-        if dt >= 0.5 * target_s or n >= o.ngrid:
+        if dt >= 0.5 * target_s or n >= pool.size:
             break
-        n = int(min(o.ngrid, n * max(2.0, 0.9 * target_s / max(dt, 1e-3))))
+        n = int(min(pool.size, n * max(2.0, 0.9 * target_s / max(dt, 1e-3))))
+    n = idx.size
     Wsample, _ = o.count_pairs(idx)
     value = 2.0 * Wsample / dt / 1e9
-    desc = (f"FP64 oracle rho + H_loc over {n} random grid points of {workload_name} "
-            f"({n / o.ngrid:.3%} of the grid, 2W = {2 * Wsample:.3e} pair updates) in {dt:.1f} s")
+    where = f"the {ORACLE_REGION[workload_name]}" if region is not None else "the grid"
+    desc = (f"FP64 oracle rho + H_loc over {n} random grid points of {workload_name}, drawn from {where} "
+            f"({n / o.ngrid:.3%} of the grid, 2W = {2 * Wsample:.3e} pair updates) in {dt:.1f} s; "
+            f"no extrapolation")
     return value, Oracle.num_threads(), desc, dt
 
 
@@ -541,6 +562,29 @@ def main():
     ms_per_step = max_over_ranks(sum(t_steps), world, dev) / args.steps
     value = world * 2.0 * W / (ms_per_step * 1e-3) / 1e9
 
+    # the float64 GPU path on the same workload and inputs (CUDA cores; the comparator of the
+    # mixed-precision path), timed the same way: density + local-H passes, L2 flushed
+    fp64_gpu = None
+    if args.precision != "fp64" and args.fp64_steps > 0:
+        g.rho(Db, G.FP64, out=rho)
+        g.vlocal(V, G.FP64, out=H)
+        torch.cuda.synchronize()
+        t64 = []
+        for k in range(args.fp64_steps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.rho(Db, G.FP64, out=rho)
+            g.vlocal(V, G.FP64, out=H)
+            b.record(stream)
+            b.synchronize()
+            t64.append(a.elapsed_time(b))
+        ms64 = max_over_ranks(statistics.mean(t64), world, dev)
+        v64 = world * 2.0 * W / (ms64 * 1e-3) / 1e9
+        fp64_gpu = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": args.fp64_steps,
+                    "kernels": "k_simt_rho, k_simt_vlocal (float64 CUDA cores)",
+                    "mixed_over_fp64": value / v64}
+
     # roofline of the dominant kernel (per-launch mean over the timed region, CUDA events on its stream)
     peaks, peak_kind = load_peaks()
     if tensor:
@@ -636,7 +680,8 @@ def main():
                    "parallelism": f"replicas{world}"},
         "ms_kernel": tdom, "ms_rho_alone": statistics.mean(t_rho), "ms_vlocal_alone": statistics.mean(t_h),
         "ms_force_alone": statistics.mean(t_f),
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "fp64_gpu": fp64_gpu,
+        "mixed_over_fp64": fp64_gpu["mixed_over_fp64"] if fp64_gpu else None,
         "gpu_launches": launches * args.steps, "serving": serving, "per_R": per_R, "psibeta": psibeta,
         "crank_nicolson": cn,
     }

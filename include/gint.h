@@ -51,8 +51,14 @@ extern "C" {
 #define GINT_ESKIN (-7)      /* atoms moved so that a pair outside the block set now overlaps */
 #define GINT_EUNSUPPORTED (-8) /* precision mode or feature not available on this device */
 
-/* Precision of the brick contractions.  Cross-brick reductions, the charge and energy
- * reductions and the per-atom force reduction are float64 in every mode. */
+/* Precision of the brick contractions.  The charge and energy reductions and the per-atom force
+ * reduction are float64 in every mode.  The cross-brick reduction of H is float64 in the FP64 mode;
+ * with the tensor-core modes the per-brick float32 tiles are summed as double-float pairs (error-free
+ * two-sum into a float32 hi + lo pair, relative error about n^2 2^-48 for n bricks) and the pair is
+ * combined in float64.
+ * GINT_F16X3 forces (gint_force, and force tasks of gint_run_batch) split orbitals and D in fixed point
+ * instead: hi = the nearest integer at a common scale (so the tensor core's float32 accumulation of
+ * hi * hi is exact), lo = the float16 remainder, and four products hi*hi + hi*lo + lo*hi + lo*lo. */
 #define GINT_FP64 0  /* float64 everywhere (CUDA cores) */
 #define GINT_FP32 1  /* float32 orbitals and CUDA-core contractions */
 #define GINT_F16X3 2 /* float32 orbitals; tensor-core contractions on operands split into two float16

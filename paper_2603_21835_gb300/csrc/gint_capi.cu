@@ -47,7 +47,7 @@ void dfree(T *&p) {
 }
 
 void free_all(gint_handle *h) {
-  dfree(h->tab64); dfree(h->tab32); dfree(h->tab32i);
+  dfree(h->tab64); dfree(h->tab32); dfree(h->tab32i); dfree(h->dtab32); dfree(h->dtab32i);
   dfree(h->pos_dev); dfree(h->species_dev);
   dfree(h->pair_row_dev); dfree(h->pair_col_dev); dfree(h->pair_off_dev); dfree(h->pair_T_dev); dfree(h->pair_I_dev);
   dfree(h->n_at); dfree(h->n_ent); dfree(h->n_orb);
@@ -241,22 +241,37 @@ int gint_create(const gint_desc *d, gint_handle **out) {
   h->nknots = (long long)t64.size();
   std::vector<float2> t32(t64.size());
   for (size_t i = 0; i < t64.size(); ++i) t32[i] = make_float2((float)t64[i].x, (float)t64[i].y);
+  std::vector<float> d32(t64.size(), 0.f);  // knot differences in float64, rounded once
+  for (int k = 0; k < r; ++k)
+    for (int i = 0; i + 1 < g.rad[k].npts; ++i) {
+      const long long o = g.rad[k].off + i;
+      d32[o] = (float)(t64[o + 1].x - t64[o].x);
+    }
   // shaped species (radials on one knot grid): (f, f') of all radials at a knot side by side, so a
   // knot pair is a few 16-byte loads in the orbital kernels
   std::vector<float2> t32i;
+  std::vector<float> d32i;
   for (int s = 0; s < d->nspecies; ++s) {
     GSpecies &GS = g.sp[s];
     GS.ioff = GS.kslot = 0;
     if (!GS.shape) continue;
     GS.kslot = (GS.nrad + 1) & ~1;
-    if (t32i.size() & 1) t32i.push_back(make_float2(0.f, 0.f));
+    if (t32i.size() & 1) {
+      t32i.push_back(make_float2(0.f, 0.f));
+      d32i.push_back(0.f);
+    }
     GS.ioff = (int)t32i.size();
     const int npts = g.rad[GS.rad0].npts;
     for (int i = 0; i < npts; ++i)
-      for (int k = 0; k < GS.kslot; ++k)
+      for (int k = 0; k < GS.kslot; ++k) {
         t32i.push_back(k < GS.nrad ? t32[g.rad[GS.rad0 + k].off + i] : make_float2(0.f, 0.f));
+        d32i.push_back(k < GS.nrad ? d32[g.rad[GS.rad0 + k].off + i] : 0.f);
+      }
   }
-  if (t32i.empty()) t32i.push_back(make_float2(0.f, 0.f));
+  if (t32i.empty()) {
+    t32i.push_back(make_float2(0.f, 0.f));
+    d32i.push_back(0.f);
+  }
   h->nknots_i = (long long)t32i.size();
   TRY(dalloc(&h->tab64, t64.size()));
   TRY(dalloc(&h->tab32, t32.size()));
@@ -264,6 +279,10 @@ int gint_create(const gint_desc *d, gint_handle **out) {
   TRYCU(cudaMemcpy(h->tab32i, t32i.data(), t32i.size() * sizeof(float2), cudaMemcpyHostToDevice));
   TRYCU(cudaMemcpy(h->tab64, t64.data(), t64.size() * sizeof(double2), cudaMemcpyHostToDevice));
   TRYCU(cudaMemcpy(h->tab32, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  TRY(dalloc(&h->dtab32, d32.size()));
+  TRY(dalloc(&h->dtab32i, d32i.size()));
+  TRYCU(cudaMemcpy(h->dtab32, d32.data(), d32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  TRYCU(cudaMemcpy(h->dtab32i, d32i.data(), d32i.size() * sizeof(float), cudaMemcpyHostToDevice));
   // atoms
   h->pos_host.assign(d->pos, d->pos + 3 * (size_t)d->natoms);
   h->species_host.assign(d->species, d->species + d->natoms);
@@ -382,7 +401,7 @@ int gint_stats(const gint_handle *h, double *W, double *W_exec, long long *nbric
 int gint_memory(const gint_handle *h, long long *device_bytes) {
   if (!h || !device_bytes) return GINT_EINVAL;
   const long long nb = h->geom.nbricks, na = h->geom.natoms, np = h->npairs, L = sizeof(long long);
-  long long b = h->nknots * (long long)(sizeof(double2) + sizeof(float2)) + h->nknots_i * 8;  // tables
+  long long b = h->nknots * (long long)(sizeof(double2) + sizeof(float2) + sizeof(float)) + h->nknots_i * 12;  // tables
   b += na * (3 * (long long)sizeof(double) + 4);                                            // atoms
   b += (na + 1) * 4 + np * 4 + (np + 1) * L + 2 * np * 4;                                  // pair set
   b += nb * 3 * 4 + (nb + 1) * 3 * L + 8 * L;                                               // brick counts

@@ -16,6 +16,11 @@ struct gint_handle {
   double2 *tab64 = nullptr;
   float2 *tab32 = nullptr;
   float2 *tab32i = nullptr;  // interleaved per-species copy of tab32 ([knot][radial]) for shaped species
+  // float32 knot differences f_{k+1} - f_k formed in float64 (parallel to tab32 / tab32i): the
+  // radial derivative of the float32 evaluators divides this difference by the knot spacing, and
+  // a difference of two float32-rounded knot values would lose about two digits there
+  float *dtab32 = nullptr;
+  float *dtab32i = nullptr;
   long long nknots_i = 0;
   long long nknots = 0;
   // atoms

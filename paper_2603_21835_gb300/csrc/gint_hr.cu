@@ -166,7 +166,7 @@ int gint_hr_prepare(gint_handle *h) {
     po.assign(s1 - s0, 0);
     long long cum = 0;
     for (long long s = s0; s < s1; ++s) {
-      po[s - s0] = g.sp[h->species_host[satom[s]]].porb;
+      po[s - s0] = g.sp[h->species_host[satom[s]]].norb;  // scratch tiles hold no padding
       cum += po[s - s0];
     }
     long long rowst = 0, cum_a = 0;

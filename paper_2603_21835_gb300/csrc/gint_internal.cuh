@@ -112,9 +112,10 @@ struct Tab2<double> { typedef double2 type; };
 template <>
 struct Tab2<float> { typedef float2 type; };
 
+// dtab (may be NULL): f_{k+1} - f_k per knot formed in float64 (for float32 tables; see the handle)
 template <typename T>
 __device__ __forceinline__ void radial_eval(const typename Tab2<T>::type *__restrict__ tab, const GRadial &R, T r,
-                                            T &f, T &df) {
+                                            T &f, T &df, const float *__restrict__ dtab = nullptr) {
   T x = r * (T)R.inv_dr;
   int i = (int)x;
   if (i >= R.npts - 1) {
@@ -127,13 +128,14 @@ __device__ __forceinline__ void radial_eval(const typename Tab2<T>::type *__rest
   T dr = (T)R.dr;
   T g0 = a.y * dr, g1 = b.y * dr;
   T t2 = t * t;
+  const T dlt = dtab ? (T)dtab[R.off + i] : b.x - a.x;
   // Hermite basis in nested form: h00 = 1 - t^2 (3 - 2t), h01 = t^2 (3 - 2t),
   // h10 = t (1 - t)^2, h11 = t^2 (t - 1)
   T s = t2 * ((T)3 - (T)2 * t);
   T u = (T)1 - t;
-  f = a.x + (b.x - a.x) * s + g0 * t * u * u + g1 * t2 * (t - (T)1);
+  f = a.x + dlt * s + g0 * t * u * u + g1 * t2 * (t - (T)1);
   // derivatives: dh01 = 6 t (1 - t) = -dh00, dh10 = (1 - t)(1 - 3t), dh11 = t (3t - 2)
-  df = ((b.x - a.x) * (T)6 * t * u + g0 * u * ((T)1 - (T)3 * t) + g1 * t * ((T)3 * t - (T)2)) * (T)R.inv_dr;
+  df = (dlt * (T)6 * t * u + g0 * u * ((T)1 - (T)3 * t) + g1 * t * ((T)3 * t - (T)2)) * (T)R.inv_dr;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -173,7 +175,8 @@ __device__ __forceinline__ float gsqrt<float>(float x) { return sqrtf(x); }
 // grad phi = u (f' Y - l f Y / r) + (f / r) grad_u y(u), with Y = y(u), u = d / r.
 template <typename T, bool PHI, bool GRAD>
 __device__ __forceinline__ void add_orbitals(const GTabs &g, const typename Tab2<T>::type *__restrict__ tab, int sp,
-                                             T dx, T dy, T dz, T *phi, T (*grad)[3]) {
+                                             T dx, T dy, T dz, T *phi, T (*grad)[3],
+                                             const float *__restrict__ dtab = nullptr) {
   const GSpecies &S = g.sp[sp];
   T r2 = dx * dx + dy * dy + dz * dz;
   T r = gsqrt<T>(r2);
@@ -186,7 +189,7 @@ __device__ __forceinline__ void add_orbitals(const GTabs &g, const typename Tab2
     const int l = R.l, nm = 2 * l + 1;
     if (r < (T)R.rc) {
       T f, df;
-      radial_eval<T>(tab, R, r, f, df);
+      radial_eval<T>(tab, R, r, f, df, dtab);
       if (at0) {
         if (PHI && l == 0) phi[col] += f * (T)0.28209479177387814347;
         if (GRAD && l == 1) {

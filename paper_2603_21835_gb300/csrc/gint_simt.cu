@@ -34,8 +34,8 @@ struct SlabShared {
 // (and chi = w V phi if CHI), and builds the coverage list.  Returns the number of slots.
 template <typename T, bool CHI>
 __device__ int slab_orbitals(const GGeom &g, const GNbr &nb, const typename Tab2<T>::type *__restrict__ tab,
-                             long long b, int lane, int warp, const double rp[3], bool valid, T wv, T *phi, T *chi,
-                             int ld, SlabShared &sh) {
+                             const float *__restrict__ dtab, long long b, int lane, int warp, const double rp[3],
+                             bool valid, T wv, T *phi, T *chi, int ld, SlabShared &sh) {
   const long long s0 = nb.b_at_off[b];
   const int na = (int)(nb.b_at_off[b + 1] - s0);
   for (int a = threadIdx.x; a < na; a += blockDim.x) {
@@ -61,7 +61,7 @@ __device__ int slab_orbitals(const GGeom &g, const GNbr &nb, const typename Tab2
         double dx = rp[0] - nb.e_shift[3 * e], dy = rp[1] - nb.e_shift[3 * e + 1], dz = rp[2] - nb.e_shift[3 * e + 2];
         if (dx * dx + dy * dy + dz * dz < rc2) {
           cov = true;
-          add_orbitals<T, true, false>(g, tab, sp, (T)dx, (T)dy, (T)dz, myphi + col, nullptr);
+          add_orbitals<T, true, false>(g, tab, sp, (T)dx, (T)dy, (T)dz, myphi + col, nullptr, dtab);
         }
       }
     }
@@ -83,8 +83,9 @@ __device__ int slab_orbitals(const GGeom &g, const GNbr &nb, const typename Tab2
 
 template <typename T, int MAXO, bool FORCE>
 __global__ void __launch_bounds__(kThreads) k_simt_rho(GGeom g, GNbr nb, const typename Tab2<T>::type *__restrict__ tab,
-                                                        const T *__restrict__ D, const double *__restrict__ V,
-                                                        double *__restrict__ rho, double *__restrict__ F, int ld) {
+                                                        const float *__restrict__ dtab, const T *__restrict__ D,
+                                                        const double *__restrict__ V, double *__restrict__ rho,
+                                                        double *__restrict__ F, int ld) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SlabShared sh;
   __shared__ double rpart[kWarps][32];
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(kThreads) k_simt_rho(GGeom g, GNbr nb, const t
   double rp[3];
   grid_point(g, gi, gj, gk, rp);
   const long long gidx = valid ? grid_index(g, gi, gj, gk) : 0;
-  const int na = slab_orbitals<T, false>(g, nb, tab, b, lane, warp, rp, valid, (T)0, phi, nullptr, ld, sh);
+  const int na = slab_orbitals<T, false>(g, nb, tab, dtab, b, lane, warp, rp, valid, (T)0, phi, nullptr, ld, sh);
   const T *myphi = phi + lane * ld;
   const long long pbase = nb.b_pair_off[b];
   const double wv = (FORCE && valid) ? g.w * V[gidx] : 0.0;
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(kThreads) k_simt_rho(GGeom g, GNbr nb, const t
         for (long long e = sh.s_e0[a]; e < sh.s_e0[a + 1]; ++e) {
           double dx = rp[0] - nb.e_shift[3 * e], dy = rp[1] - nb.e_shift[3 * e + 1], dz = rp[2] - nb.e_shift[3 * e + 2];
           if (dx * dx + dy * dy + dz * dz < rc2)
-            add_orbitals<T, false, true>(g, tab, sp, (T)dx, (T)dy, (T)dz, nullptr, gs);
+            add_orbitals<T, false, true>(g, tab, sp, (T)dx, (T)dy, (T)dz, nullptr, gs, dtab);
         }
       }
       T fx = 0, fy = 0, fz = 0;
@@ -166,8 +167,8 @@ __global__ void __launch_bounds__(kThreads) k_simt_rho(GGeom g, GNbr nb, const t
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_simt_vlocal(GGeom g, GNbr nb, const typename Tab2<T>::type *__restrict__ tab,
-                                                           const int *__restrict__ pair_T, const double *__restrict__ V,
-                                                           double *__restrict__ H, int ld) {
+                                                           const float *__restrict__ dtab, const int *__restrict__ pair_T,
+                                                           const double *__restrict__ V, double *__restrict__ H, int ld) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SlabShared sh;
   T *phi = reinterpret_cast<T *>(smem);
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) k_simt_vlocal(GGeom g, GNbr nb, cons
   double rp[3];
   grid_point(g, gi, gj, gk, rp);
   const T wv = valid ? (T)(g.w * V[grid_index(g, gi, gj, gk)]) : (T)0;
-  const int na = slab_orbitals<T, true>(g, nb, tab, b, lane, warp, rp, valid, wv, phi, chi, ld, sh);
+  const int na = slab_orbitals<T, true>(g, nb, tab, dtab, b, lane, warp, rp, valid, wv, phi, chi, ld, sh);
   const long long pbase = nb.b_pair_off[b];
   const int nc = sh.ncov;
   int k = 0;
@@ -274,13 +275,15 @@ static int run_rho(gint_handle *h, const T *D, double *rho, const double *V, dou
     auto kern = k_simt_rho<T, MAXO, true>;
     int rc = launch_cfg(kern, smem);
     if (rc) return rc;
-    kern<<<grid, kThreads, smem, st>>>(h->geom, h->nbr(), (const typename Tab2<T>::type *)(sizeof(T) == 8 ? (void *)h->tab64 : (void *)h->tab32), D, V, rho, F, ld);
+    kern<<<grid, kThreads, smem, st>>>(h->geom, h->nbr(), (const typename Tab2<T>::type *)(sizeof(T) == 8 ? (void *)h->tab64 : (void *)h->tab32),
+                                       sizeof(T) == 8 ? nullptr : h->dtab32, D, V, rho, F, ld);
   } else {
     size_t smem = sizeof(T) * 32 * (size_t)ld;
     auto kern = k_simt_rho<T, MAXO, false>;
     int rc = launch_cfg(kern, smem);
     if (rc) return rc;
-    kern<<<grid, kThreads, smem, st>>>(h->geom, h->nbr(), (const typename Tab2<T>::type *)(sizeof(T) == 8 ? (void *)h->tab64 : (void *)h->tab32), D, V, rho, F, ld);
+    kern<<<grid, kThreads, smem, st>>>(h->geom, h->nbr(), (const typename Tab2<T>::type *)(sizeof(T) == 8 ? (void *)h->tab64 : (void *)h->tab32),
+                                       sizeof(T) == 8 ? nullptr : h->dtab32, D, V, rho, F, ld);
   }
   SIMT_CHECK(cudaGetLastError());
   return GINT_OK;
@@ -305,7 +308,7 @@ static int run_vlocal(gint_handle *h, const double *V, double *H, cudaStream_t s
   if (rc) return rc;
   kern<<<(unsigned)(h->geom.nbricks * 4), kThreads, smem, st>>>(
       h->geom, h->nbr(), (const typename Tab2<T>::type *)(sizeof(T) == 8 ? (void *)h->tab64 : (void *)h->tab32),
-      h->pair_T_dev, V, H, ld);
+      sizeof(T) == 8 ? nullptr : h->dtab32, h->pair_T_dev, V, H, ld);
   SIMT_CHECK(cudaGetLastError());
   return GINT_OK;
 }

@@ -51,6 +51,7 @@ constexpr int kRC = 16;          // density chunk width (one f16 K step)
 constexpr long long kWaitNs = 2000000000LL;  // bounded mbarrier waits: 2 s
 constexpr unsigned char kNoSlot = 255;
 constexpr int kMmaWarp = 5;  // lane 0 issues the density MMAs
+constexpr float kFxScaleD = 1.f / 16.f;  // fixed-point D scale relative to the floating split's
 // density phase B roles: epilogue groups of four warps (warps 0-3, 6-9), the MMA warp (5), and the
 // prefetch warps (10-15, 4) that issue the bulk copies of the D chunks.  Orbital slots go to four
 // slices of warps (warps 4q .. 4q+3 take slots q, q+4, ...), so the last slices have the fewest: the
@@ -189,6 +190,20 @@ __device__ __forceinline__ void split_h2(float a, float b, uint32_t &hw, uint32_
   lw = *reinterpret_cast<const uint32_t *>(&l);
 }
 
+// Fixed-point split (force pass): hi = the nearest integer (|x| <= 2048, exact in float16), lo =
+// round(x - hi), |lo| <= 1/2.  Every hi * hi product is then an integer, so as long as the partial
+// sums stay below 2^24 the tensor core's float32 accumulation of the hi * hi products is exact (no
+// bits fall below the accumulator's last place, whatever its rounding).  The lo parts carry the rest
+// to float16 precision; all three products with a lo factor go to a separate accumulator whose
+// values are about 2^-10 of the main one, where rounding is negligible.
+__device__ __forceinline__ void split_fx2(float a, float b, uint32_t &hw, uint32_t &lw) {
+  const float ha = rintf(a), hb = rintf(b);
+  const __half2 h = __floats2half2_rn(ha, hb);
+  const __half2 l = __floats2half2_rn(a - ha, b - hb);
+  hw = *reinterpret_cast<const uint32_t *>(&h);
+  lw = *reinterpret_cast<const uint32_t *>(&l);
+}
+
 // ------------------------------------------------------------------------------ orbital evaluation
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   s = a + b;
@@ -250,18 +265,19 @@ __device__ __forceinline__ Basis hermite_basis(float t) {
   B.d1 = t * (3.f * t - 2.f);
   return B;
 }
-__device__ __forceinline__ void radial_at(const float2 *__restrict__ tab, const GRadial &R, int i, const Basis &B,
-                                          float &f, float &df) {
+// dtab (may be NULL): knot differences formed in float64 (accurate derivatives; see the handle)
+__device__ __forceinline__ void radial_at(const float2 *__restrict__ tab, const float *__restrict__ dtab,
+                                          const GRadial &R, int i, const Basis &B, float &f, float &df) {
   const float2 a = tab[R.off + i], b = tab[R.off + i + 1];
-  const float dlt = b.x - a.x;
+  const float dlt = dtab ? dtab[R.off + i] : b.x - a.x;
   f = a.x + dlt * B.s + R.dr_f * (a.y * B.c0 + b.y * B.c1);
   df = (dlt * B.ds + R.dr_f * (a.y * B.d0 + b.y * B.d1)) * R.idr_hi;
 }
 
 // Generic path (any radial order or knot grids): adds one image to v[col] (+ gv[3 col + c]).
 template <bool GRAD>
-__device__ void add_image_generic(const GTabs &g, const float2 *__restrict__ tab, const GSpecies &S, const float dh[3],
-                                  const float dl[3], float *v, float *gv) {
+__device__ void add_image_generic(const GTabs &g, const float2 *__restrict__ tab, const float *__restrict__ dtab,
+                                  const GSpecies &S, const float dh[3], const float dl[3], float *v, float *gv) {
   float r, rl, ir;
   bool at0;
   dist_df(dh, dl, r, rl, ir, at0);
@@ -274,7 +290,7 @@ __device__ void add_image_generic(const GTabs &g, const float2 *__restrict__ tab
     float t;
     if (r < R.rc_f && knot_df(R, r, rl, i, t)) {
       float f, df;
-      radial_at(tab, R, i, hermite_basis(t), f, df);
+      radial_at(tab, GRAD ? dtab : nullptr, R, i, hermite_basis(t), f, df);
       if (at0) {
         if (l == 0) v[col] += f * 0.28209479177387814347f;
         if (GRAD && l == 1) {
@@ -306,8 +322,9 @@ __device__ void add_image_generic(const GTabs &g, const float2 *__restrict__ tab
 // computation per image, the knot pair of every radial from the interleaved table (tabi: a few
 // 16-byte loads), all column indices static (register arrays).
 template <int NS, int NPR, int ND, bool GRAD>
-__device__ __forceinline__ void add_image_fast(const GTabs &g, const float2 *__restrict__ tabi, const GSpecies &S,
-                                               const float dh[3], const float dl[3], float *v, float *gv) {
+__device__ __forceinline__ void add_image_fast(const GTabs &g, const float2 *__restrict__ tabi,
+                                               const float *__restrict__ dtabi, const GSpecies &S, const float dh[3],
+                                               const float dl[3], float *v, float *gv) {
   constexpr int NR = NS + NPR + ND, KS = (NR + 1) & ~1;
   float r, rl, ir;
   bool at0;
@@ -333,9 +350,12 @@ __device__ __forceinline__ void add_image_fast(const GTabs &g, const float2 *__r
     }
   }
   const float drf = R0.dr_f, idr = R0.idr_hi;  // shared knot grid
+  // with gradients the knot difference comes from the float64-formed table (values alone: the
+  // difference of the two float32 knot values is accurate enough)
+  const float *qd = GRAD ? dtabi + S.ioff + (long long)i * KS : nullptr;
   auto radial_k = [&](int k, float &f, float &df) {
     const float2 a = GRAD ? __ldg(q2 + k) : ka[GRAD ? 0 : k], b = GRAD ? __ldg(q2 + KS + k) : kb[GRAD ? 0 : k];
-    const float dlt = b.x - a.x;
+    const float dlt = GRAD ? __ldg(qd + k) : b.x - a.x;
     f = a.x + dlt * B.s + drf * (a.y * B.c0 + b.y * B.c1);
     df = (dlt * B.ds + drf * (a.y * B.d0 + b.y * B.d1)) * idr;
   };
@@ -423,7 +443,7 @@ struct BrickSh {
   uint32_t tmem;
   int item, na, np, nent, abort;
   int s_atom[kMAXA], s_no[kMAXA], s_po[kMAXA], s_sp[kMAXA], s_pcol[kMAXA], s_e0[kMAXA + 1];
-  int s_cumpo[kMAXA + 1];       // prefix of porb over slots
+  int s_cumno[kMAXA + 1];       // prefix of norb over slots (local-H scratch layout)
   int s_rowst[kMAXA];           // local-H scratch: first element of slot a's row of tiles
   int s_tile[kMAXA * kMAXA];    // D tile element offset of (row slot b, K slot a), -1 if none
   float e_hi[kMAXE][3], e_lo[kMAXE][3];  // entry positions relative to the brick origin
@@ -433,6 +453,7 @@ struct BrickSh {
   float rpart[4][128];
   float rpartl[4][128];  // density epilogue: compensation terms of the groups' partial sums
   float wv[128];   // w V at the brick's points (local H, force)
+  float rsc[128];  // force launches: power-of-two scale of each row of P (fixed-point split)
   double ob[3];    // brick origin (Cartesian)
   float sc[4];     // scales
   uint64_t plan_bar;  // the next item's plan record has landed in planbuf
@@ -501,15 +522,15 @@ __device__ void load_brick(const GCell &g, const GTabs &tb, const GNbr &nb, cons
       const int pc = place_slot(cur, sh.s_po[a]);
       sh.s_pcol[a] = pc;
       cur = pc + sh.s_po[a];
-      sh.s_cumpo[a] = cum;
-      cum += sh.s_po[a];
+      sh.s_cumno[a] = cum;
+      cum += sh.s_no[a];
     }
-    sh.s_cumpo[na] = cum;
+    sh.s_cumno[na] = cum;
     sh.np = (cur + 15) & ~15;
     int rs = 0;
     for (int a = 0; a < na; ++a) {
       sh.s_rowst[a] = rs;
-      rs += sh.s_po[a] * (cum - sh.s_cumpo[a]);
+      rs += sh.s_no[a] * (cum - sh.s_cumno[a]);
     }
   }
   __syncthreads();
@@ -524,8 +545,8 @@ __device__ void load_brick(const GCell &g, const GTabs &tb, const GNbr &nb, cons
 }
 
 // Plan record of a brick (built once per geometry from load_brick's result, 32-bit words):
-//   [0] na  [1] nent  [2] np  [3] cumulative porb of all slots
-//   [4 + 8a + k], k = 0..7: atom, species, norb, porb, pcol, first entry, cumpo, rowst of slot a
+//   [0] na  [1] nent  [2] np  [3] cumulative norb of all slots
+//   [4 + 8a + k], k = 0..7: atom, species, norb, porb, pcol, first entry, cumno, rowst of slot a
 //   [4 + 8 na + 6 e + c]: entry e, c < 3: hi part of axis c, c >= 3: lo part (float bits)
 //   then na * na tile offsets, then np bytes of the column -> slot map; padded to 16 bytes.
 __host__ __device__ __forceinline__ long long plan_words(int na, int nent, int np) {
@@ -546,7 +567,7 @@ __device__ void unpack_plan(BrickSh &sh) {
     sh.s_po[a] = (int)q[3];
     sh.s_pcol[a] = (int)q[4];
     sh.s_e0[a] = (int)q[5];
-    sh.s_cumpo[a] = (int)q[6];
+    sh.s_cumno[a] = (int)q[6];
     sh.s_rowst[a] = (int)q[7];
     sh.fpart[a][0] = sh.fpart[a][1] = sh.fpart[a][2] = 0.0;
   }
@@ -555,7 +576,7 @@ __device__ void unpack_plan(BrickSh &sh) {
     sh.nent = nent;
     sh.np = np;
     sh.s_e0[na] = nent;
-    sh.s_cumpo[na] = (int)w[3];
+    sh.s_cumno[na] = (int)w[3];
   }
   const int eb = 4 + 8 * na;
   for (int u = t; u < 6 * nent; u += nt) {
@@ -599,7 +620,8 @@ __device__ __forceinline__ void rel_disp_df(const BrickSh &sh, const PointDF &P,
 
 // Periodised orbitals (all images) of slot a at local point p: v[PO] (+ gv[3 PO]), zero based.
 template <int NS, int NPR, int ND, bool GRAD>
-__device__ __forceinline__ void slot_values(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
+__device__ __forceinline__ void slot_values(const GTabs &g, const float2 *__restrict__ tab,
+                                            const float *__restrict__ dtab, const BrickSh &sh, int a,
                                             const PointDF &P, bool valid, float *v, float *gv) {
   constexpr int PO = (NS + 3 * NPR + 5 * ND + 7) / 8 * 8;
 #pragma unroll
@@ -615,9 +637,9 @@ __device__ __forceinline__ void slot_values(const GTabs &g, const float2 *__rest
     rel_disp_df(sh, P, e, dh, dl);
     if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < rc2) {
       if (NS + NPR + ND > 0)
-        add_image_fast<NS, NPR, ND, GRAD>(g, tab, S, dh, dl, v, gv);
+        add_image_fast<NS, NPR, ND, GRAD>(g, tab, dtab, S, dh, dl, v, gv);
       else
-        add_image_generic<GRAD>(g, tab, S, dh, dl, v, gv);
+        add_image_generic<GRAD>(g, tab, dtab, S, dh, dl, v, gv);
     }
   }
 }
@@ -648,8 +670,8 @@ __device__ __forceinline__ void job_P2(const GTabs &g, const float2 *__restrict_
                                        int a1, const PointDF &P, int p, bool valid, float Sphi, unsigned char *Ph,
                                        unsigned char *Pl, uint32_t sboP) {
   float v0[PO], v1[PO];
-  slot_values<NS, NPR, ND, false>(g, tab, sh, a0, P, valid, v0, nullptr);
-  slot_values<NS, NPR, ND, false>(g, tab, sh, a1, P, valid, v1, nullptr);
+  slot_values<NS, NPR, ND, false>(g, tab, nullptr, sh, a0, P, valid, v0, nullptr);
+  slot_values<NS, NPR, ND, false>(g, tab, nullptr, sh, a1, P, valid, v1, nullptr);
   store_P<PO>(v0, sh.s_pcol[a0], p, Sphi, Ph, Pl, sboP);
   store_P<PO>(v1, sh.s_pcol[a1], p, Sphi, Ph, Pl, sboP);
 }
@@ -658,27 +680,17 @@ __device__ __forceinline__ void job_P(const GTabs &g, const float2 *__restrict__
                                       const PointDF &P, int p, bool valid, float Sphi, unsigned char *Ph,
                                       unsigned char *Pl, uint32_t sboP) {
   float v[PO];
-  slot_values<NS, NPR, ND, false>(g, tab, sh, a, P, valid, v, nullptr);
-  const int pc = sh.s_pcol[a];
-#pragma unroll
-  for (int k = 0; k < PO; k += 8) {
-    uint32_t wh[4], wl[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      split_h2(v[k + 2 * e] * Sphi, v[k + 2 * e + 1] * Sphi, wh[e], wl[e]);
-    }
-    const uint32_t off = (p >> 3) * sboP + ((pc + k) >> 3) * 128 + (p & 7) * 16;
-    *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
-    *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
-  }
+  slot_values<NS, NPR, ND, false>(g, tab, nullptr, sh, a, P, valid, v, nullptr);
+  store_P<PO>(v, sh.s_pcol[a], p, Sphi, Ph, Pl, sboP);
 }
 
 // Force epilogue: y[PO] (true Y values of slot a's columns) -> rho part and force components.
 template <int NS, int NPR, int ND, int PO>
-__device__ __forceinline__ void job_F(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a, int p,
-                                      bool valid, const float *y, float &rp, float &fx, float &fy, float &fz) {
+__device__ __forceinline__ void job_F(const GTabs &g, const float2 *__restrict__ tab, const float *__restrict__ dtab,
+                                      const BrickSh &sh, int a, int p, bool valid, const float *y, float &rp, float &fx,
+                                      float &fy, float &fz) {
   float v[PO], gv[3 * PO];
-  slot_values<NS, NPR, ND, true>(g, tab, sh, a, point_df(sh, p), valid, v, gv);
+  slot_values<NS, NPR, ND, true>(g, tab, dtab, sh, a, point_df(sh, p), valid, v, gv);
 #pragma unroll
   for (int i = 0; i < PO; ++i) {
     rp += v[i] * y[i];
@@ -690,8 +702,8 @@ __device__ __forceinline__ void job_F(const GTabs &g, const float2 *__restrict__
 
 // Generic-shape jobs (any species up to GINT_MAX_ORB_ATOM orbitals).
 __device__ __noinline__ void job_P_generic(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
-                                           int p, bool valid, float Sphi, unsigned char *Ph, unsigned char *Pl,
-                                           uint32_t sboP) {
+                                           int p, bool valid, float Sphi, unsigned char *Ph,
+                                           unsigned char *Pl, uint32_t sboP) {
   float v[GINT_MAX_ORB_ATOM];
   const int po = sh.s_po[a], pc = sh.s_pcol[a];
   for (int i = 0; i < po; ++i) v[i] = 0.f;
@@ -701,7 +713,7 @@ __device__ __noinline__ void job_P_generic(const GTabs &g, const float2 *__restr
       float dh[3], dl[3];
       rel_disp_df(sh, point_df(sh, p), e, dh, dl);
       if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < S.rcut2f)
-        add_image_generic<false>(g, tab, S, dh, dl, v, nullptr);
+        add_image_generic<false>(g, tab, nullptr, S, dh, dl, v, nullptr);
     }
   }
   for (int k = 0; k < po; k += 8) {
@@ -714,9 +726,9 @@ __device__ __noinline__ void job_P_generic(const GTabs &g, const float2 *__restr
     *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
   }
 }
-__device__ __noinline__ void job_F_generic(const GTabs &g, const float2 *__restrict__ tab, const BrickSh &sh, int a,
-                                           int p, bool valid, const float *y, float &rp, float &fx, float &fy,
-                                           float &fz) {
+__device__ __noinline__ void job_F_generic(const GTabs &g, const float2 *__restrict__ tab,
+                                           const float *__restrict__ dtab, const BrickSh &sh, int a, int p, bool valid,
+                                           const float *y, float &rp, float &fx, float &fy, float &fz) {
   float v[GINT_MAX_ORB_ATOM], gv[3 * GINT_MAX_ORB_ATOM];
   const int no = sh.s_no[a];
   for (int i = 0; i < no; ++i) v[i] = gv[3 * i] = gv[3 * i + 1] = gv[3 * i + 2] = 0.f;
@@ -726,7 +738,7 @@ __device__ __noinline__ void job_F_generic(const GTabs &g, const float2 *__restr
       float dh[3], dl[3];
       rel_disp_df(sh, point_df(sh, p), e, dh, dl);
       if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] < S.rcut2f)
-        add_image_generic<true>(g, tab, S, dh, dl, v, gv);
+        add_image_generic<true>(g, tab, dtab, S, dh, dl, v, gv);
     }
   }
   for (int i = 0; i < no; ++i) {
@@ -753,6 +765,7 @@ struct GSys {
   GNbr nb;
   const float2 *tab;                         // float32 knot table of this system's handle
   const float2 *tabi;                        // its interleaved copy (shaped species)
+  const float *dtab, *dtabi;                 // knot differences formed in float64 (gradients)
   const __half *Dhl, *Dhl2;                 // D tiles, hi and lo 8 x 8 blocks interleaved (and halved)
   const long long *tile_off;
   const float *scales;                       // [0] S_phi, [1] S_D, [2] S_Q
@@ -958,10 +971,15 @@ __global__ void __launch_bounds__(kT, 1)
     }
     if (t == 0) next_item();  // every thread has read sh.item and sh.plan_pref
     const int na = sh.na, NP = sh.np;
+    // force launches with the three-term split use a fixed-point split of P and D (exact hi * hi
+    // accumulation, four products): D at 2^-4 of the floating split's scale (|hi| < 2048), and each
+    // row of P (grid point) rescaled by its own power of two s_p so that its largest |value| lies in
+    // [512, 1024)
+    const bool fixp = FORCE && split3;
     const float Sphi = sh.sc[0];
     {
       // ================================================================ orbitals, density / force
-      const float SD = sh.sc[1];
+      const float SD = fixp ? sh.sc[1] * kFxScaleD : sh.sc[1];
       const int p = t & 127, q = t >> 7;  // grid point, slot slice (0..3)
       const uint32_t lane_base = (uint32_t)((p >> 5) * 32) << 16;
       int gi, gj, gk;
@@ -1028,6 +1046,45 @@ __global__ void __launch_bounds__(kT, 1)
           }
         }
       }
+      if (fixp) {
+        // ---- fixed-point rows: s_p from the row's largest |value| (the four slices' maxima), then
+        // every element x = (hi + lo) s_p re-split as hi = rint(x), lo = x - hi (float16)
+        float m = 0.f;
+        for (int a = q; a < na; a += 4)
+          for (int k = sh.s_pcol[a]; k < sh.s_pcol[a] + sh.s_po[a]; k += 8) {
+            const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
+            const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + off), wl = *reinterpret_cast<const uint4 *>(Pl + off);
+            const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
+              const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
+              m = fmaxf(m, fmaxf(fabsf(hf.x + lf.x), fabsf(hf.y + lf.y)));
+            }
+          }
+        sh.rpart[q][p] = m;
+        __syncthreads();
+        const float rm = fmaxf(fmaxf(sh.rpart[0][p], sh.rpart[1][p]), fmaxf(sh.rpart[2][p], sh.rpart[3][p]));
+        int ex = 0;
+        frexpf(rm, &ex);  // rm = f 2^ex, f in [0.5, 1)
+        const float sp = rm > 0.f ? ldexpf(1.f, 10 - ex) : 1.f;
+        if (q == 0) sh.rsc[p] = sp;
+        for (int a = q; a < na; a += 4)
+          for (int k = sh.s_pcol[a]; k < sh.s_pcol[a] + sh.s_po[a]; k += 8) {
+            const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
+            const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + off), wl = *reinterpret_cast<const uint4 *>(Pl + off);
+            const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
+            uint32_t oh[4], ol[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
+              const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
+              split_fx2((hf.x + lf.x) * sp, (hf.y + lf.y) * sp, oh[e], ol[e]);
+            }
+            *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(oh[0], oh[1], oh[2], oh[3]);
+            *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
+          }
+      }
       fence_async_smem();
       __syncthreads();
       if (do_rho) {
@@ -1055,6 +1112,7 @@ __global__ void __launch_bounds__(kT, 1)
             mma_f16(tmem + rowbase, dah, dbh, id, acc);
             mma_f16(tmem + 256u + rowbase, dah, dbl, id, acc);
             mma_f16(tmem + 256u + rowbase, dal, dbh, id, 1u);
+            if (FORCE) mma_f16(tmem + 256u + rowbase, dal, dbl, id, 1u);  // fixed-point split: lo * lo too
             mma_commit(&sh.done[c]);
             if (++s == (uint32_t)nstages) {
               s = 0;
@@ -1082,6 +1140,7 @@ __global__ void __launch_bounds__(kT, 1)
               if (split3) {
                 mma_f16(dc, dah, dbl, id, (c > 0 || corr_base == 0) ? 1u : 0u);
                 mma_f16(dc, dal, dbh, id, 1u);
+                if (fixp) mma_f16(dc, dal, dbl, id, 1u);
               }
             }
             mma_commit(&sh.done[c]);
@@ -1161,7 +1220,7 @@ __global__ void __launch_bounds__(kT, 1)
       if (FORCE) {
         // full Y: per atom, rho and force from recomputed phi and grad phi (unscaled float32)
         const float2 *tab = S.tab, *tabi = S.tabi;
-        const float inv = 1.f / (Sphi * SD);
+        const float inv = 1.f / (Sphi * SD * (fixp ? sh.rsc[p] : 1.f));
         const float wv = (valid && S.V) ? sh.wv[p] : 0.f;
         float rp = 0.f;
         for (int a = q; a < na; a += 4) {
@@ -1191,12 +1250,12 @@ __global__ void __launch_bounds__(kT, 1)
           switch (g.sp[sh.s_sp[a]].shape) {
 #define CASE_F(ns, np_, nd)                                                                          \
   case GINT_SHAPE(ns, np_, nd):                                                                    \
-    job_F<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tabi, sh, a, p, valid, y, rp, fx, fy, fz); \
+    job_F<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tabi, S.dtabi, sh, a, p, valid, y, rp, fx, fy, fz); \
     break;
             GINT_FOR_SHAPES(CASE_F)
 #undef CASE_F
             default:
-              job_F_generic(g, tab, sh, a, p, valid, y, rp, fx, fy, fz);
+              job_F_generic(g, tab, S.dtab, sh, a, p, valid, y, rp, fx, fy, fz);
           }
           fx *= 2.f * wv;
           fy *= 2.f * wv;
@@ -1260,7 +1319,7 @@ __global__ void __launch_bounds__(kT, 1)
             const int pl = po8 * 8 + (u & 7), pt = p0 + pl;
             const uint32_t so = (pt >> 3) * sboP + gg * 128 + (pt & 7) * 16;
             const uint32_t dso = (pl >> 3) * sboP + gg * 128 + (pl & 7) * 16;
-            const float f = sh.wv[pt] * wscale;
+            const float f = fixp ? sh.wv[pt] * wscale / (sh.rsc[pt] * sh.rsc[pt]) : sh.wv[pt] * wscale;
             const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + so), wl = *reinterpret_cast<const uint4 *>(Pl + so);
             const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
             uint32_t oh[4], ol[4];
@@ -1335,8 +1394,10 @@ __global__ void __launch_bounds__(kT, 1)
         }
       // epilogue: upper slot-pair tiles -> scratch (float32, unscaled), stored column-major so that
       // the lanes of a warp (consecutive rows) write contiguous runs: tile (a, c), a <= c, holds
-      // porb(c) columns of porb(a) rows at rowst(a) + porb(a) (cumpo(c) - cumpo(a)); element (i, j)
-      // at j porb(a) + i (the row-major porb(c) x porb(a) block (c, a) of the symmetric brick H)
+      // norb(c) columns of norb(a) rows at rowst(a) + norb(a) (cumno(c) - cumno(a)); element (i, j)
+      // at j norb(a) + i (the row-major norb(c) x norb(a) block (c, a) of the symmetric brick H).
+      // Only the orbitals themselves are stored (no padding rows or columns): the tiles of a brick
+      // are one dense, fully written range.
       {
         const int ln = t & 127, qq = t >> 7;
         const uint32_t lane_base = (uint32_t)((ln >> 5) * 32) << 16;
@@ -1345,9 +1406,9 @@ __global__ void __launch_bounds__(kT, 1)
           const int mu = 128 * m + ln;
           const int as = mu < NP ? sh.col2slot[mu] : kNoSlot;
           const int il = as != kNoSlot ? mu - sh.s_pcol[as] : 0;
-          // padding rows are stored too (zeros; never read): whole 32-byte sectors per column
-          const bool rowok = as != kNoSlot;
-          const int po_a = rowok ? sh.s_po[as] : 0, cum_a = rowok ? sh.s_cumpo[as] : 0;
+          const int no_a = as != kNoSlot ? sh.s_no[as] : 0;
+          const bool rowok = as != kNoSlot && il < no_a;
+          const int cum_a = rowok ? sh.s_cumno[as] : 0;
           float *rowp = S.hs + base + (rowok ? sh.s_rowst[as] : 0) + il;
           const int N = NP - 128 * m;
           for (int gcol = qq; gcol < N / 16; gcol += 4) {
@@ -1364,9 +1425,11 @@ __global__ void __launch_bounds__(kT, 1)
               const int nu = 128 * m + gcol * 16 + 8 * hh;
               const int cs = sh.col2slot[nu];
               if (cs == kNoSlot || cs < as) continue;
-              float *dst = rowp + (long long)po_a * (sh.s_cumpo[cs] - cum_a + (nu - sh.s_pcol[cs]));
+              const int j0 = nu - sh.s_pcol[cs], nj = min(8, sh.s_no[cs] - j0);
+              float *dst = rowp + (long long)no_a * (sh.s_cumno[cs] - cum_a + j0);
 #pragma unroll
-              for (int i = 0; i < 8; ++i) dst[(long long)i * po_a] = y[8 * hh + i] * out_scale;
+              for (int i = 0; i < 8; ++i)
+                if (i < nj) dst[(long long)i * no_a] = y[8 * hh + i] * out_scale;
             }
           }
         }
@@ -1397,15 +1460,17 @@ struct GRed {
 };
 
 // One CTA per upper pair (I <= J) of any system: H_IJ = sum over the bricks containing both (their
-// scratch tiles are column-major, porb(J) columns of porb(I) rows, padding rows included, every tile
-// 16-byte aligned), with compensated float32 sums (two-sum: error-free additions into a hi + lo pair,
-// as accurate as a float64 sum of the float32 tiles); H_JI = H_IJ^T.  A thread sums four rows of one
-// column (16-byte loads, eight in flight) over one of kRedGroups contiguous parts of the brick list;
-// the parts' sums are then combined in part order (the result does not depend on scheduling).
-constexpr int kRedLanes = 64, kRedGroups = 4, kRedThreads = kRedLanes * kRedGroups;
+// scratch tiles are column-major, norb(J) columns of norb(I) rows, element e = j norb(I) + i), summed
+// as double-float pairs (two-sum: error-free additions into a hi + lo pair of float32, relative error
+// about n^2 2^-48 for n bricks, far below the float32 rounding of the tiles themselves) and combined
+// in float64; H_JI = H_IJ^T.  A thread sums kRedE elements of the block (stride kRedLanes) over one of
+// kRedGroups contiguous parts of the pair's brick list, kRedB bricks' loads in flight; the parts'
+// sums are then combined in part order (the result does not depend on scheduling).  A float64 sum
+// of every tile value would cost more than the brick pass itself on this GPU (float64 runs at about
+// 1/64 of the float32 rate), so the float64 step is the final combination only.
+constexpr int kRedLanes = 64, kRedGroups = 4, kRedThreads = kRedLanes * kRedGroups, kRedE = 3, kRedB = 8;
 __global__ void __launch_bounds__(kRedThreads, 4) k_h_reduce(const __grid_constant__ GTabs g, const __grid_constant__ GRed R) {
-  constexpr int kB = 8;
-  __shared__ float4 part_hi[kRedGroups - 1][kRedLanes], part_lo[kRedGroups - 1][kRedLanes];
+  __shared__ float part_hi[kRedGroups - 1][kRedE][kRedLanes], part_lo[kRedGroups - 1][kRedE][kRedLanes];
   const long long gu = blockIdx.x;
   int lo = 0, hi = R.nsys - 1;
   while (lo < hi) {
@@ -1420,70 +1485,65 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_h_reduce(const __grid_consta
   const int p = S.hu_pair[u];
   const int I = S.pair_I[p], J = S.pair_J[p];
   const int nI = g.sp[S.species[I]].norb, nJ = g.sp[S.species[J]].norb;
-  const int pI = g.sp[S.species[I]].porb, pJ = g.sp[S.species[J]].porb;
   const int ln = threadIdx.x % kRedLanes, grp = threadIdx.x / kRedLanes;
   const long long kk0 = S.hu_off[u], kk1 = S.hu_off[u + 1];
   const long long per = (kk1 - kk0 + kRedGroups - 1) / kRedGroups;
   const long long k0 = min(kk1, kk0 + grp * per), k1 = min(kk1, k0 + per);
   const float *__restrict__ hs = S.hs;
   const long long *__restrict__ src = S.hu_src;
-  const int n4 = (pI * pJ) >> 2;
-  for (int base = 0; base < n4; base += kRedLanes) {  // block-uniform trip count
-    const int e4 = base + ln, f = 4 * e4, j = f / pI, i0 = f - j * pI;  // rows i0 .. i0 + 3 of column j
-    const bool act = e4 < n4 && j < nJ && i0 < nI;
-    float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
-    auto add = [&](const float4 v) {
-      const float x[4] = {v.x, v.y, v.z, v.w};
+  const int ne = nI * nJ;
+  for (int base = 0; base < ne; base += kRedLanes * kRedE) {  // block-uniform trip count
+    int e[kRedE];
+    bool act[kRedE];
+    float ah[kRedE], al[kRedE];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float sum, err;
-        two_sum(ah[q], x[q], sum, err);
-        ah[q] = sum;
-        al[q] += err;
-      }
+    for (int q = 0; q < kRedE; ++q) {
+      e[q] = base + q * kRedLanes + ln;
+      act[q] = e[q] < ne;
+      if (!act[q]) e[q] = 0;  // a valid address; its loads are discarded
+      ah[q] = al[q] = 0.f;
+    }
+    auto add = [&](int q, float x) {
+      float sum, err;
+      two_sum(ah[q], x, sum, err);
+      ah[q] = sum;
+      al[q] += err;
     };
-    if (act) {
-      long long k = k0;
-      long long o[kB];
-      if (k + kB <= k1) {
+    long long k = k0;
+    for (; k + kRedB <= k1; k += kRedB) {
+      long long o[kRedB];
 #pragma unroll
-        for (int jj = 0; jj < kB; ++jj) o[jj] = __ldg(src + k + jj);
-      }
-      for (; k + kB <= k1; k += kB) {
-        float4 v[kB];
+      for (int jj = 0; jj < kRedB; ++jj) o[jj] = __ldg(src + k + jj);
+      float v[kRedB][kRedE];
 #pragma unroll
-        for (int jj = 0; jj < kB; ++jj) v[jj] = __ldg(reinterpret_cast<const float4 *>(hs + o[jj] + f));
-        if (k + 2 * kB <= k1) {
+      for (int jj = 0; jj < kRedB; ++jj)
 #pragma unroll
-          for (int jj = 0; jj < kB; ++jj) o[jj] = __ldg(src + k + kB + jj);
-        }
+        for (int q = 0; q < kRedE; ++q) v[jj][q] = __ldg(hs + o[jj] + e[q]);
 #pragma unroll
-        for (int jj = 0; jj < kB; ++jj) add(v[jj]);
-      }
-      for (; k < k1; ++k) add(__ldg(reinterpret_cast<const float4 *>(hs + src[k] + f)));
+      for (int jj = 0; jj < kRedB; ++jj)
+#pragma unroll
+        for (int q = 0; q < kRedE; ++q) add(q, v[jj][q]);
+    }
+    for (; k < k1; ++k) {
+      const long long o = __ldg(src + k);
+#pragma unroll
+      for (int q = 0; q < kRedE; ++q) add(q, __ldg(hs + o + e[q]));
     }
     if (grp > 0) {
-      part_hi[grp - 1][ln] = make_float4(ah[0], ah[1], ah[2], ah[3]);
-      part_lo[grp - 1][ln] = make_float4(al[0], al[1], al[2], al[3]);
+#pragma unroll
+      for (int q = 0; q < kRedE; ++q) {
+        part_hi[grp - 1][q][ln] = ah[q];
+        part_lo[grp - 1][q][ln] = al[q];
+      }
     }
     __syncthreads();
-    if (grp == 0 && act) {
-      for (int g2 = 0; g2 < kRedGroups - 1; ++g2) {
-        const float4 h4 = part_hi[g2][ln], l4 = part_lo[g2][ln];
-        const float hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
+    if (grp == 0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float sum, err;
-          two_sum(ah[q], hv[q], sum, err);
-          ah[q] = sum;
-          al[q] += err + lv[q];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = i0 + q;
-        if (i >= nI) break;
-        const double acc = (double)ah[q] + (double)al[q];
+      for (int q = 0; q < kRedE; ++q) {
+        if (!act[q]) continue;
+        double acc = (double)ah[q] + (double)al[q];
+        for (int g2 = 0; g2 < kRedGroups - 1; ++g2) acc += (double)part_hi[g2][q][ln] + (double)part_lo[g2][q][ln];
+        const int j = e[q] / nI, i = e[q] - j * nI;
         S.H[S.pair_off[p] + (long long)i * nJ + j] = acc;
         if (I != J) S.H[S.pair_off[S.pair_T[p]] + (long long)j * nI + i] = acc;
       }
@@ -1562,6 +1622,7 @@ struct GTileSys {
 };
 struct GTile {
   int nsys;
+  int fixed;  // 1: fixed-point split at 2^-4 of the floating split's scale (force launches)
   long long start[kMaxBatch + 1];  // first pair of each system
   GTileSys sys[kMaxBatch];
 };
@@ -1584,7 +1645,8 @@ __global__ void k_build_tiles(const __grid_constant__ GTabs g, const __grid_cons
   const int I = S.pair_I[p], J = S.pair_J[p];
   const int nI = g.sp[S.species[I]].norb, nJ = g.sp[S.species[J]].norb, pJ = g.sp[S.species[J]].porb;
   const int rI = (nI + 7) & ~7, sJ = pJ >> 3;
-  const double sc = (double)S.scales[1];
+  const bool fixed = TB.fixed != 0;
+  const double sc = (double)S.scales[1] * (fixed ? (double)kFxScaleD : 1.0);
   const long long o = S.pair_off[p], to = S.tile_off[p];
   for (int e = threadIdx.x; e < rI * pJ; e += blockDim.x) {
     const int cm = e >> 6, w = e & 63;
@@ -1592,6 +1654,13 @@ __global__ void k_build_tiles(const __grid_constant__ GTabs g, const __grid_cons
     const long long q = 2 * to + (long long)cm * 128 + w;  // hi element; lo 64 halves later
     if (i < nI && j < nJ) {
       const double x = S.D[o + (long long)i * nJ + j] * sc;
+      if (fixed) {  // hi: the nearest integer (exact in float16: |x| < 2048); the halved tiles are unused
+        const double hx = rint(x);
+        S.Dhl[q] = __float2half_rn((float)hx);
+        S.Dhl[q + 64] = __float2half_rn((float)(x - hx));
+        S.Dhl2[q] = S.Dhl2[q + 64] = __float2half(0.f);
+        continue;
+      }
       const __half h = __float2half_rn((float)x), h2 = __float2half_rn((float)(0.5 * x));
       S.Dhl[q] = h;
       S.Dhl[q + 64] = __float2half_rn((float)(x - (double)__half2float(h)));
@@ -1624,7 +1693,7 @@ __global__ void __launch_bounds__(128) k_build_plans(const __grid_constant__ GTa
     w[0] = (uint32_t)na;
     w[1] = (uint32_t)nent;
     w[2] = (uint32_t)np;
-    w[3] = (uint32_t)sh.s_cumpo[na];
+    w[3] = (uint32_t)sh.s_cumno[na];
   }
   for (int a = t; a < na; a += blockDim.x) {
     uint32_t *q = w + 4 + 8 * a;
@@ -1634,7 +1703,7 @@ __global__ void __launch_bounds__(128) k_build_plans(const __grid_constant__ GTa
     q[3] = (uint32_t)sh.s_po[a];
     q[4] = (uint32_t)sh.s_pcol[a];
     q[5] = (uint32_t)sh.s_e0[a];
-    q[6] = (uint32_t)sh.s_cumpo[a];
+    q[6] = (uint32_t)sh.s_cumno[a];
     q[7] = (uint32_t)sh.s_rowst[a];
   }
   const int eb = 4 + 8 * na;
@@ -1814,7 +1883,7 @@ int gint_tc_prepare(gint_handle *h) {
   std::vector<long long> hs_off(nb + 1, 0);
   std::vector<long long> cnt(h->npairs + 1, 0);
   int npmax = 0;
-  std::vector<int> no;  // padded orbital counts (porb) of the brick's slots
+  std::vector<int> no;  // orbital counts (norb) of the brick's slots (local-H scratch tiles hold no padding)
   std::vector<long long> ent_off(nb + 1);
   TC_CHECK(cudaMemcpy(ent_off.data(), h->b_ent_off, (nb + 1) * sizeof(long long), cudaMemcpyDeviceToHost));
   std::vector<long long> plan_off(nb + 1, 0);  // plan records, 16-byte units
@@ -1827,8 +1896,8 @@ int gint_tc_prepare(gint_handle *h) {
     for (long long s = s0; s < s1; ++s) {
       const GSpecies &S = g.sp[h->species_host[satom[s]]];
       cur = place_slot(cur, S.porb) + S.porb;
-      no[s - s0] = S.porb;
-      cum += S.porb;
+      no[s - s0] = S.norb;
+      cum += S.norb;
     }
     npmax = std::max(npmax, (cur + 15) & ~15);
     plan_off[b + 1] = plan_off[b] + plan_words((int)(s1 - s0), (int)(ent_off[b + 1] - ent_off[b]), (cur + 15) & ~15) / 4;
@@ -1864,7 +1933,7 @@ int gint_tc_prepare(gint_handle *h) {
     no.assign(s1 - s0, 0);
     long long cum = 0;
     for (long long s = s0; s < s1; ++s) {
-      no[s - s0] = g.sp[h->species_host[satom[s]]].porb;
+      no[s - s0] = g.sp[h->species_host[satom[s]]].norb;
       cum += no[s - s0];
     }
     long long rowst = 0, cumno_a = 0;
@@ -1981,6 +2050,8 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
     S.nb = h->nbr();
     S.tab = h->tab32;
     S.tabi = h->tab32i;
+    S.dtab = h->dtab32;
+    S.dtabi = h->dtab32i;
     S.Dhl = h->Dt_hl;
     S.Dhl2 = h->Dt_hl2;
     S.tile_off = h->tile_off_dev;
@@ -2029,6 +2100,7 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
   B.start[n] = items;
   TB.nsys = nt;
   TB.start[nt] = pairs;
+  TB.fixed = (force && split3) ? 1 : 0;
   R.nsys = nr;
   R.start[nr] = uppers;
   np = (np + 15) & ~15;

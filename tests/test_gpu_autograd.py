@@ -83,7 +83,19 @@ def test_forces_vs_central_differences_and_oracle(mods, si64d, prec):
             fd = -(Es[0] - Es[1]) / (2 * h)
             assert abs(F[I, c] - fd) <= 1e-5, (prec, I, c, F[I, c], fd)
     g.ensure_positions(pos0)
-    # the oracle's local Pulay force for the same atoms
-    o = Oracle(w.system)
-    Fo = o.force(w.D, w.V, atoms=np.array(atoms))
-    assert np.abs(F[atoms] - Fo[atoms]).max() <= 1e-5
+    # the oracle's local Pulay force on all 64 atoms
+    Fo = _oracle_forces(w)
+    err = np.abs(F - Fo).max()
+    worst = np.argsort(-np.abs(F - Fo).max(1))[:4]
+    print(prec, "forces of all 64 atoms vs the oracle:", err, "Ha/Bohr; worst atoms",
+          [(int(a), float(np.abs(F - Fo)[a].max())) for a in worst])
+    assert err <= (1e-11 * np.abs(Fo).max() if prec == "fp64" else 1e-5)
+
+
+_FO = {}
+
+
+def _oracle_forces(w):
+    if "F" not in _FO:
+        _FO["F"] = Oracle(w.system).force(w.D, w.V)
+    return _FO["F"]
