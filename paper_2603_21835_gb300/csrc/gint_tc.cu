@@ -52,6 +52,7 @@ constexpr long long kWaitNs = 2000000000LL;  // bounded mbarrier waits: 2 s
 constexpr unsigned char kNoSlot = 255;
 constexpr int kMmaWarp = 5;  // lane 0 issues the density MMAs
 constexpr float kFxScaleD = 1.f / 16.f;  // fixed-point D scale relative to the floating split's
+constexpr uint32_t kHTail = 2048;  // >= 15 core matrices of 128 bytes read above the last local-H operand rows
 // density phase B roles: epilogue groups of four warps (warps 0-3, 6-9), the MMA warp (5), and the
 // prefetch warps (10-15, 4) that issue the bulk copies of the D chunks.  Orbital slots go to four
 // slices of warps (warps 4q .. 4q+3 take slots q, q+4, ...), so the last slices have the fewest: the
@@ -110,6 +111,16 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// 1-D bulk copy shared -> global (bulk-group completion), and the waits on this thread's groups:
+// .read = the shared-memory source may be overwritten; plain = the global writes are done.
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // Named barrier 1 over the density epilogue warps (barrier 0 is __syncthreads).
 __device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -444,7 +455,7 @@ struct BrickSh {
   int item, na, np, nent, abort;
   int s_atom[kMAXA], s_no[kMAXA], s_po[kMAXA], s_sp[kMAXA], s_pcol[kMAXA], s_e0[kMAXA + 1];
   int s_cumno[kMAXA + 1];       // prefix of norb over slots (local-H scratch layout)
-  int s_rowst[kMAXA];           // local-H scratch: first element of slot a's row of tiles
+  int s_rowst[kMAXA + 1];       // local-H scratch: first element of slot a's row of tiles; [na]: the total
   int s_tile[kMAXA * kMAXA];    // D tile element offset of (row slot b, K slot a), -1 if none
   float e_hi[kMAXE][3], e_lo[kMAXE][3];  // entry positions relative to the brick origin
   float pt_hi[128][3], pt_lo[128][3];    // grid point positions relative to the brick origin
@@ -532,6 +543,7 @@ __device__ void load_brick(const GCell &g, const GTabs &tb, const GNbr &nb, cons
       sh.s_rowst[a] = rs;
       rs += sh.s_no[a] * (cum - sh.s_cumno[a]);
     }
+    sh.s_rowst[na] = rs;
   }
   __syncthreads();
   const long long pbase = nb.b_pair_off[b];
@@ -577,6 +589,7 @@ __device__ void unpack_plan(BrickSh &sh) {
     sh.np = np;
     sh.s_e0[na] = nent;
     sh.s_cumno[na] = (int)w[3];
+    sh.s_rowst[na] = na > 0 ? (int)w[4 + 8 * (na - 1) + 7] + (int)w[4 + 8 * (na - 1) + 2] * ((int)w[3] - (int)w[4 + 8 * (na - 1) + 6]) : 0;
   }
   const int eb = 4 + 8 * na;
   for (int u = t; u < 6 * nent; u += nt) {
@@ -780,8 +793,8 @@ struct GSys {
 };
 
 struct GBatch {
-  int nsys, np_max, nstages, split3;
-  int hkb, pad;                    // local-H K-block (points) of the W P ping-pong buffers
+  int nsys, np_max, split3;
+  int dsmem;                       // dynamic shared memory of the launch (bytes)
   long long start[kMaxBatch + 1];  // first item of each system; start[nsys] = total
   GSys sys[kMaxBatch];
 };
@@ -800,15 +813,16 @@ __device__ __forceinline__ int batch_sys(const GBatch &B, long long it) {
 }
 
 // ------------------------------------------------------------------------------ brick kernel
-// One persistent CTA per SM walks the batch's items.  Dynamic shared memory is used by either
-// kind of item:
-//   density: P (hi, lo) [128 x np_max] | nstages x B stage [np_max x 16] (hi and lo interleaved)
-//     P element (p, k): (p/8)*16*np_max + (k/8)*128 + (p%8)*16 + (k%8)*2
+// One persistent CTA per SM walks the batch's items.  Dynamic shared memory, laid out per item for
+// the item's padded width NP:
+//   density: P (hi, lo) [128 x NP] | nst x B stage [NP x 16] (hi and lo interleaved), nst = as many as
+//     fit, up to kMaxStages
+//     P element (p, k): (p/8)*16*NP + (k/8)*128 + (p%8)*16 + (k%8)*2
 //     B element (r, j) of part h (0 hi, 1 lo): (r/8)*512 + (j/8)*256 + h*128 + (r%8)*16 + (j%8)*2
 //     (the layout of a row group of a 16-column tile in the interleaved tile store)
-//   local H: 2 stages of A hi, A lo, B hi, B lo, each [np_max rows x 32 points]
-//     element (r, p): (r/8)*576 + (p/8)*144 + (r%8)*16 + (p%8)*2, plus a tail pad for the rows
-//     above NP that the last 128-row A tile reads (they only feed output rows that are ignored).
+//   local H: two blocks of W P (hi, lo), hkb points x NP each, in the stage region, with the P layout;
+//     the last 128-row A tile reads up to kHTail bytes above them (rows above NP, whose outputs are
+//     ignored); afterwards the whole region stages the brick's scratch tiles for one bulk store.
 // FORCE: density items produce rho and forces (full Y); a system without F only gets rho.
 template <bool FORCE>
 __global__ void __launch_bounds__(kT, 1)
@@ -817,11 +831,13 @@ __global__ void __launch_bounds__(kT, 1)
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ BrickSh sh;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int np_max = B.np_max, nstages = B.nstages, split3 = B.split3;
-  const uint32_t sboP = 16u * np_max;
-  unsigned char *Ph = smem, *Pl = smem + 128u * np_max * 2;
-  unsigned char *B0 = smem + 128u * np_max * 4;
-  const uint32_t bop = (uint32_t)np_max * kRC * 2;  // one B operand (hi or lo) of one stage
+  const int split3 = B.split3;
+  // dynamic shared memory of an item, laid out for its own padded width NP: P (hi, lo), then as many
+  // density stages (hi and lo of an NP x 16 panel each) as fit, up to kMaxStages (narrower bricks get
+  // more chunks in flight), then at least kHTail bytes
+  uint32_t sboP = 0, bop = 0;  // P row-group stride; one B operand (hi or lo) of one stage
+  unsigned char *Ph = smem, *Pl = smem, *B0 = smem;
+  int nst = 2;  // density stages of the item
   const long long total = B.start[B.nsys];
   // thread 0: fetches the next item and starts the bulk copy of its plan record into planbuf
   // (the buffer is free: the current item's record was unpacked before the last barrier)
@@ -861,7 +877,7 @@ __global__ void __launch_bounds__(kT, 1)
   tc_fence_after();
   const uint32_t tmem = sh.tmem;
   uint32_t pphase = 0;  // plan records consumed by this CTA (phase parity of plan_bar)
-  uint32_t G = 0;     // density chunks issued by this CTA (B-stage ring bookkeeping)
+  uint32_t fpar = 0;  // bit s: phase parity of the next use of stage s (full[s])
   uint32_t dpar = 0;  // bit c: phase parity of done[c] (used once per density brick that has a chunk c)
   uint32_t GH = 0;    // local-H stages issued by this CTA
   int cur = -1;       // system whose points and scales are in shared memory
@@ -962,6 +978,9 @@ __global__ void __launch_bounds__(kT, 1)
       int gi, gj, gk;
       sh.wv[t] = brick_point(S.c, b, t, gi, gj, gk) ? (float)(S.c.w * S.V[grid_index(S.c, gi, gj, gk)]) : 0.f;
     }
+    // the previous item's local-H tiles have left shared memory (its bulk store has read them)
+    // before this item writes any dynamic shared memory (the barriers of the unpack order it)
+    if (t == 0) bulk_wait_read();
     if (pref) {  // prefetched plan record (the common case)
       if (!mbar_wait(&sh.plan_bar, pphase & 1u, S.err)) ok = false;
       ++pphase;
@@ -990,12 +1009,19 @@ __global__ void __launch_bounds__(kT, 1)
         continue;
       }
       const int nch = NP / kRC;
+      sboP = 16u * (uint32_t)NP;
+      Pl = smem + 128u * (uint32_t)NP * 2u;
+      B0 = smem + 128u * (uint32_t)NP * 4u;
+      bop = (uint32_t)NP * kRC * 2u;
+      nst = min(kMaxStages, (int)(((uint32_t)B.dsmem - 128u * (uint32_t)NP * 4u - kHTail) / (2u * bop)));
+      // chunk c uses stage c mod nst; its phase parity is that stage's next parity, flipped once per
+      // earlier use of the stage in this item
       // the previous item's MMAs are complete: every stage is free, prefetch the first density chunks
       // (one chunk per prefetch warp: a warp issuing a chunk's bulk copies spends a sizeable part of
       // the orbital evaluation on it)
       if (do_rho) {
         const int li = prefetch_index(warp);
-        if (li >= 0 && li < nch && li < nstages) issue_copies(S, li, (G + li) % nstages, NP, na);
+        if (li >= 0 && li < nch && li < nst) issue_copies(S, li, li, NP, na);
       }
       // ---- phase A: scaled orbitals of all atoms at every point -> P (hi, lo), zero padding
       for (int a = q; a < na; a += 4) {
@@ -1098,13 +1124,13 @@ __global__ void __launch_bounds__(kT, 1)
           // orders the copies before the MMAs; the epilogue's tensor-memory reads touch finished
           // columns only, so one tcgen05 fence per item suffices.
           unsigned *errp = S.err;
-          uint32_t s = G % nstages, fph = (G / nstages) & 1u;
+          uint32_t s = 0, wrap = 0;
           const uint64_t dah0 = sdesc(smem_u32(Ph), 128, sboP), dal0 = sdesc(smem_u32(Pl), 128, sboP);
           const uint64_t dbh0 = sdesc(smem_u32(B0), 256, 512);
           const uint32_t sstep = (2 * bop) >> 4, lstep = 128 >> 4;
           tc_fence_after();  // after the barrier that ended the previous item's tensor-memory reads
           for (int c = 0; c < nch; ++c) {
-            if (!mbar_wait(&sh.full[s], fph, errp)) ok = false;
+            if (!mbar_wait(&sh.full[s], ((fpar >> s) & 1u) ^ wrap, errp)) ok = false;
             const uint32_t rowbase = FORCE ? 0u : (uint32_t)c * kRC;
             const uint32_t id = idesc_f16(128, NP - (int)rowbase), acc = c > 0 ? 1u : 0u;
             const uint64_t dah = dah0 + (uint64_t)(16 * c), dal = dal0 + (uint64_t)(16 * c);
@@ -1114,16 +1140,16 @@ __global__ void __launch_bounds__(kT, 1)
             mma_f16(tmem + 256u + rowbase, dal, dbh, id, 1u);
             if (FORCE) mma_f16(tmem + 256u + rowbase, dal, dbl, id, 1u);  // fixed-point split: lo * lo too
             mma_commit(&sh.done[c]);
-            if (++s == (uint32_t)nstages) {
+            if (++s == (uint32_t)nst) {
               s = 0;
-              fph ^= 1u;
+              wrap ^= 1u;
             }
           }
         } else if (lane == 0) {
           unsigned *errp = S.err;
-          uint32_t s = G % nstages, fph = (G / nstages) & 1u;  // stage and phase parity of chunk 0
+          uint32_t s = 0, wrap = 0;  // stage of chunk c, and 1 once the stages have wrapped an odd number of times
           for (int c = 0; c < nch; ++c) {
-            if (!mbar_wait(&sh.full[s], fph, errp)) ok = false;
+            if (!mbar_wait(&sh.full[s], ((fpar >> s) & 1u) ^ wrap, errp)) ok = false;
             tc_fence_after();
             unsigned char *Bh = B0 + s * 2 * bop, *Bl = Bh + 128;
             const int rowbase = FORCE ? 0 : c * kRC;
@@ -1144,22 +1170,22 @@ __global__ void __launch_bounds__(kT, 1)
               }
             }
             mma_commit(&sh.done[c]);
-            if (++s == (uint32_t)nstages) {
+            if (++s == (uint32_t)nst) {
               s = 0;
-              fph ^= 1u;
+              wrap ^= 1u;
             }
           }
         }
         __syncwarp();
       } else if (prefetch_index(warp) >= 0) {
         // prefetch warps, later chunks: chunk k (k mod kPrefetchWarps = the warp's prefetch index),
-        // its bulk copies issued once chunk k - nstages's MMAs are done (the stage is free)
+        // its bulk copies issued once chunk k - nst's MMAs are done (the stage is free)
         unsigned *errp = S.err;
         const int li = prefetch_index(warp);
-        for (int k = nstages + ((li - nstages) % kPrefetchWarps + kPrefetchWarps) % kPrefetchWarps; k < nch;
+        for (int k = nst + ((li - nst) % kPrefetchWarps + kPrefetchWarps) % kPrefetchWarps; k < nch;
              k += kPrefetchWarps) {
-          if (!mbar_wait(&sh.done[k - nstages], (dpar >> (k - nstages)) & 1u, errp)) ok = false;
-          issue_copies(S, k, (int)((G + k) % nstages), NP, na);
+          if (!mbar_wait(&sh.done[k - nst], (dpar >> (k - nst)) & 1u, errp)) ok = false;
+          issue_copies(S, k, k % nst, NP, na);
         }
       } else if (!FORCE) {
         // density epilogue groups (each covers the 128 lanes) drain finished chunks round robin
@@ -1215,7 +1241,8 @@ __global__ void __launch_bounds__(kT, 1)
       // all MMAs of the brick are complete once the last chunk's barrier has flipped (in order)
       if (!mbar_wait(&sh.done[nch - 1], (dpar >> (nch - 1)) & 1u, S.err)) ok = false;
       tc_fence_after();
-      G += nch;
+      for (int st = 0; st < nst && st < nch; ++st)  // stage st served chunks st, st + nst, ...
+        if ((((nch - 1 - st) / nst) & 1) == 0) fpar ^= 1u << st;
       dpar ^= (nch >= 32) ? 0xffffffffu : ((1u << nch) - 1u);
       if (FORCE) {
         // full Y: per atom, rho and force from recomputed phi and grad phi (unscaled float32)
@@ -1296,8 +1323,8 @@ __global__ void __launch_bounds__(kT, 1)
         const float SA = sh.sc[2];
         const float out_scale = 1.f / (Sphi * SA);
         const float wscale = SA / Sphi;
-        const int hkb = B.hkb, ng = NP >> 3;
-        const uint32_t whalf = (uint32_t)hkb * 4u * (uint32_t)np_max;  // hi and lo of one block
+        const int hkb = nst >= 4 ? 32 : 16, ng = NP >> 3;  // two halves of hkb x NP (hi, lo) fit the stages
+        const uint32_t whalf = (uint32_t)hkb * 4u * (uint32_t)NP;  // hi and lo of one block
         const int ntile = (NP + 127) / 128;
         int tb[3] = {0, 0, 0}, T = 0;
         for (int m = 0; m < ntile; ++m) {
@@ -1392,16 +1419,22 @@ __global__ void __launch_bounds__(kT, 1)
           if (!mbar_wait(&sh.hdone[Gp & 1], (Gp >> 1) & 1, S.err)) ok = false;
           tc_fence_after();
         }
-      // epilogue: upper slot-pair tiles -> scratch (float32, unscaled), stored column-major so that
-      // the lanes of a warp (consecutive rows) write contiguous runs: tile (a, c), a <= c, holds
-      // norb(c) columns of norb(a) rows at rowst(a) + norb(a) (cumno(c) - cumno(a)); element (i, j)
-      // at j norb(a) + i (the row-major norb(c) x norb(a) block (c, a) of the symmetric brick H).
-      // Only the orbitals themselves are stored (no padding rows or columns): the tiles of a brick
-      // are one dense, fully written range.
+      // epilogue: upper slot-pair tiles -> scratch (float32, unscaled), column-major: tile (a, c),
+      // a <= c, holds norb(c) columns of norb(a) rows at rowst(a) + norb(a) (cumno(c) - cumno(a));
+      // element (i, j) at j norb(a) + i (the row-major norb(c) x norb(a) block (c, a) of the
+      // symmetric brick H).  Only the orbitals themselves are stored (no padding rows or columns),
+      // so the brick's tiles are one dense range of rowst(na) values (padded to 16 bytes).  The range
+      // is assembled in shared memory (the orbital tile and the stage region are free once the MMAs
+      // are done: consecutive rows of a column land in consecutive words, no bank conflicts) and
+      // leaves in one bulk copy that overlaps the next item's set-up; a range larger than the
+      // dynamic shared memory is stored directly.
       {
         const int ln = t & 127, qq = t >> 7;
         const uint32_t lane_base = (uint32_t)((ln >> 5) * 32) << 16;
         const long long base = S.hs_brick_off[b];
+        const int total = sh.s_rowst[na], padded = (total + 3) & ~3;
+        const bool staged = padded * 4 <= B.dsmem;
+        float *const stg = staged ? reinterpret_cast<float *>(smem) : S.hs + base;
         for (int m = 0; m < ntile; ++m) {
           const int mu = 128 * m + ln;
           const int as = mu < NP ? sh.col2slot[mu] : kNoSlot;
@@ -1409,7 +1442,7 @@ __global__ void __launch_bounds__(kT, 1)
           const int no_a = as != kNoSlot ? sh.s_no[as] : 0;
           const bool rowok = as != kNoSlot && il < no_a;
           const int cum_a = rowok ? sh.s_cumno[as] : 0;
-          float *rowp = S.hs + base + (rowok ? sh.s_rowst[as] : 0) + il;
+          float *rowp = stg + (rowok ? sh.s_rowst[as] : 0) + il;
           const int N = NP - 128 * m;
           for (int gcol = qq; gcol < N / 16; gcol += 4) {
             float y[16], yc[16];
@@ -1426,12 +1459,18 @@ __global__ void __launch_bounds__(kT, 1)
               const int cs = sh.col2slot[nu];
               if (cs == kNoSlot || cs < as) continue;
               const int j0 = nu - sh.s_pcol[cs], nj = min(8, sh.s_no[cs] - j0);
-              float *dst = rowp + (long long)no_a * (sh.s_cumno[cs] - cum_a + j0);
+              float *dst = rowp + no_a * (sh.s_cumno[cs] - cum_a + j0);
 #pragma unroll
               for (int i = 0; i < 8; ++i)
-                if (i < nj) dst[(long long)i * no_a] = y[8 * hh + i] * out_scale;
+                if (i < nj) dst[i * no_a] = y[8 * hh + i] * out_scale;
             }
           }
+        }
+        for (int k = total + t; k < padded; k += kT) stg[k] = 0.f;
+        if (staged) {
+          fence_async_smem();  // the generic writes above before the bulk copy reads them
+          __syncthreads();
+          if (t == 0 && padded > 0) bulk_s2g(S.hs + base, stg, (uint32_t)padded * 4u);
         }
       }
       }  // do_h
@@ -1439,6 +1478,7 @@ __global__ void __launch_bounds__(kT, 1)
     tc_fence_before();
     if (!ok) sh.abort = 1;
   }
+  if (t == 0) bulk_wait_all();  // the last item's bulk store is complete
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 512);
 }
@@ -1795,7 +1835,6 @@ __global__ void __launch_bounds__(128, 1) k_tc_selftest(int N, float *err_out, u
 }
 
 inline uint32_t rho_smem_bytes(int np, int nstages) { return 128u * np * 4 + (uint32_t)nstages * np * kRC * 4; }
-constexpr uint32_t kHTail = 2048;  // >= 15 core matrices of 128 bytes
 
 template <typename K>
 int set_smem(K kern, uint32_t bytes) {
@@ -1906,7 +1945,7 @@ int gint_tc_prepare(gint_handle *h) {
       tot += (long long)no[a] * rest;
       rest -= no[a];
     }
-    hs_off[b + 1] = hs_off[b] + tot;
+    hs_off[b + 1] = hs_off[b] + ((tot + 3) & ~3LL);  // 16-byte aligned ranges (one bulk copy each)
     for (long long a = s0; a < s1; ++a)
       for (long long c = a; c < s1; ++c) {
         const int p = find_pair(satom[a], satom[c]);
@@ -2106,14 +2145,13 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
   np = (np + 15) & ~15;
   // dynamic shared memory: P (hi, lo) | stage region (density chunk stages; afterwards the two W P
   // halves of the local-H pass) | tail pad read by the last 128-row A tile above NP
-  int nstages = kMaxStages;
-  while (nstages > 2 && rho_smem_bytes(np, nstages) + kHTail + sizeof(BrickSh) > 227 * 1024) --nstages;
-  const uint32_t smem = rho_smem_bytes(np, nstages) + kHTail;
-  if (smem + sizeof(BrickSh) > 227 * 1024) return GINT_ECAPACITY;
+  // all the shared memory a CTA may have: items lay out P and as many stages as fit for their own
+  // width (at least two stages at the widest brick of the launch)
+  const uint32_t smem = (uint32_t)(227 * 1024 - sizeof(BrickSh)) & ~1023u;
+  if (rho_smem_bytes(np, 2) + kHTail > smem) return GINT_ECAPACITY;
   B.np_max = np;
-  B.nstages = nstages;
   B.split3 = split3;
-  B.hkb = nstages >= 4 ? 32 : 16;  // two halves of hkb x np_max (hi, lo) fit the stage region
+  B.dsmem = (int)smem;
   const int bx = std::max(8, 2 * h0->num_sms / n);
   k_prep<<<dim3(bx, n), 256, 0, st>>>(P);
   k_prep_scales<<<1, kMaxBatch, 0, st>>>(P);
