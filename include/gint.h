@@ -118,6 +118,29 @@ int gint_pairs(const gint_handle *h, int *pair_IJ, long long *pair_off);
 int gint_stats(const gint_handle *h, double *W, double *W_exec, long long *nbricks, int *max_brick_orb,
                int *max_brick_atoms);
 
+/* Diagnostic: the grid-brick -> atom neighbour lists of the current geometry (the paper's BigGrid
+ * neighbour relation, Sec. 3.3.1 and Fig. 2), copied to host arrays.  Brick b = (bi nb2 + bj) nb3 + bk
+ * (nb_i = ceil(n_i / brick_i), bricks of 4 x 4 x 8 points) covers grid points [4 bi, 4 bi + 4) x
+ * [4 bj, 4 bj + 4) x [8 bk, 8 bk + 8) (clipped to the grid).  An entry is a lattice image tau_I + R of an
+ * atom whose support sphere (|r - tau_I - R| < rcut(I)) strictly contains at least one grid point of
+ * the brick; the entries of one atom form a slot, the slots of a brick are sorted by atom.  Outputs
+ * (host, any may be NULL; pass NULL arrays first to learn the counts):
+ *   nslots, nentries;  b_off [nbricks + 1]: slots of brick b are [b_off[b], b_off[b + 1]);
+ *   slot_atom [nslots];  slot_ent [nslots + 1]: entries of slot s are [slot_ent[s], slot_ent[s + 1]);
+ *   ent_pos [nentries][3]: Cartesian tau_I + R of each entry.
+ * Synchronous.  GINT_ECUDA if a copy fails. */
+int gint_brick_lists(const gint_handle *h, long long *nslots, long long *nentries, long long *b_off, int *slot_atom,
+                     long long *slot_ent, double *ent_pos);
+
+/* Diagnostic: the periodised orbitals Phi_mu (Eqs. 1-2 at k = 0, all lattice images within the support)
+ * and their gradients at arbitrary points, evaluated by the brick kernels' own evaluators:
+ * GINT_FP64 (the float64 CUDA-core evaluator) or GINT_F16X3 (the tensor-core path's float32 evaluator:
+ * double-float distance and knot parameter, float32 Hermite interpolation with derivative differences
+ * formed in float64, float32 Y_lm).  pts [npts][3] (host, Cartesian Bohr); phi [npts][norb] and grad
+ * [npts][norb][3] (host outputs, grad may be NULL).  Synchronous; allocates temporary device memory.
+ * GINT_EUNSUPPORTED for other precisions. */
+int gint_orbitals(gint_handle *h, int precision, long long npts, const double *pts, double *phi, double *grad);
+
 /* Device memory held by the handle (tables, neighbour lists, workspace), in bytes (host
  * output).  The footprint that a serving loop counts against its HBM budget. */
 int gint_memory(const gint_handle *h, long long *device_bytes);
@@ -203,7 +226,10 @@ int gint_psibeta(gint_handle *h, const double *A, double *out, void *stream);
  * 2.8e-7).  Occupations of any sign; psi 16-byte aligned (as for every complex128 array here); no
  * allocation.
  * gint_cn_info: the LAPACK-style info of the last factorisation (0: success; i > 0: U(i, i) = 0);
- * synchronous; returns GINT_ETIMEDOUT (once) when a bounded wait of the tensor-core build gave up. */
+ * synchronous; returns GINT_ETIMEDOUT (once) when a bounded wait of the tensor-core build gave up.  The
+ * D of that call is then undefined; and since a CTA whose final completion wait also gave up releases
+ * its tensor memory with MMAs possibly still in flight, destroy the context after GINT_ETIMEDOUT rather
+ * than reuse it. */
 typedef struct gint_cn gint_cn;
 int gint_cn_create(int n, int nocc, gint_cn **out);
 int gint_cn_destroy(gint_cn *c);

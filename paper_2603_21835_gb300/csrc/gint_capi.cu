@@ -398,6 +398,22 @@ int gint_stats(const gint_handle *h, double *W, double *W_exec, long long *nbric
   return GINT_OK;
 }
 
+int gint_brick_lists(const gint_handle *h, long long *nslots, long long *nentries, long long *b_off, int *slot_atom,
+                     long long *slot_ent, double *ent_pos) {
+  if (!h) return GINT_EINVAL;
+  long long ns = h->nslots, ne = 0;
+  if (cudaMemcpy(&ne, h->s_ent + ns, sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess) return GINT_ECUDA;
+  if (nslots) *nslots = ns;
+  if (nentries) *nentries = ne;
+  const long long nb = h->geom.nbricks;
+  if ((b_off && cudaMemcpy(b_off, h->b_at_off, (nb + 1) * sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      (slot_atom && ns && cudaMemcpy(slot_atom, h->s_atom, ns * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      (slot_ent && cudaMemcpy(slot_ent, h->s_ent, (ns + 1) * sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      (ent_pos && ne && cudaMemcpy(ent_pos, h->e_shift, 3 * ne * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess))
+    return GINT_ECUDA;
+  return GINT_OK;
+}
+
 int gint_memory(const gint_handle *h, long long *device_bytes) {
   if (!h || !device_bytes) return GINT_EINVAL;
   const long long nb = h->geom.nbricks, na = h->geom.natoms, np = h->npairs, L = sizeof(long long);

@@ -49,6 +49,9 @@ constexpr int kDmThreads = 32 * kDrainWarps;
 static_assert(kCrossCol + 128 <= kTmemCols, "tensor memory columns");
 constexpr long long kWaitNs = 2000000000LL;  // bounded waits: 2 s
 constexpr unsigned kErrTimeout = 1u;
+// the final completion wait gave up too: MMAs issued by the CTA may still have been running when it
+// released its tensor memory (the call's result and later tensor-core results are unreliable)
+constexpr unsigned kErrInflight = 2u;
 
 // Scale exponent of an operand: 2^sigma * max lands in [2^14, 2^15) (float16 max 65504).
 __device__ __forceinline__ int dm_sigma(unsigned long long bits) {
@@ -298,6 +301,11 @@ __global__ void __launch_bounds__(kDmThreads, 1)
         }
       }
     }
+  }
+  if (!ok && warp == 0 && lane == 0) {
+    // before the tensor memory is released: once more (bounded) for the MMAs issued so far, which
+    // complete by themselves; if they still have not, say so
+    if (!mbar_wait(&sh.done, 0u, status, kErrTimeout, 4 * kWaitNs)) atomicOr(status, kErrInflight);
   }
   tc_fence_before();
   __syncthreads();

@@ -1,5 +1,6 @@
-// gint_ptx.cuh -- inline-PTX wrappers for sm_103a kernels: mbarriers with bounded waits, 1-D bulk
-// copies, tcgen05 tensor memory, shared-memory matrix descriptors, kind::f16 MMAs and TMEM loads.
+// gint_ptx.cuh -- inline-PTX wrappers for the sm_103a kernels (brick kernels and the tensor-core
+// density matrix): mbarriers with bounded waits, 1-D bulk copies in both directions, tcgen05 tensor
+// memory, shared-memory matrix descriptors, kind::f16 MMAs and TMEM loads.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -91,6 +92,34 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b,
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+// Both operands MN-major (transposed): core-matrix rows run along M (or N); the descriptors then
+// take LBO = stride between core matrices along K, SBO = stride along M (or N).
+__device__ __forceinline__ uint32_t idesc_f16_mn(int M, int N) { return idesc_f16(M, N) | (1u << 15) | (1u << 16); }
+// Orders this thread's generic-proxy shared-memory accesses before later async-proxy ones (bulk
+// copies, MMA operand reads) once a barrier has been passed.
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 1-D bulk copy shared -> global (bulk-group completion, 16-byte aligned, size a multiple of 16),
+// and the waits on this thread's groups: .read = the shared-memory source may be overwritten;
+// plain = the global writes are done.
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// 32 lanes x 32 bit x 8 columns.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 // 32 lanes x 32 bit x 16 columns: thread i of the warp receives its lane's 16 values.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {

@@ -39,8 +39,10 @@
 #include <vector>
 
 #include "gint_handle.cuh"
+#include "gint_ptx.cuh"
 
 namespace {
+using namespace gptx;
 
 constexpr int kT = 512;          // threads of the brick kernels (16 warps)
 constexpr int kNPMAX = 320;      // padded orbitals of a brick (density / force)
@@ -67,128 +69,12 @@ __device__ __forceinline__ int epi_group(int warp) {  // -1: not an epilogue war
 }
 
 // ------------------------------------------------------------------------------ PTX wrappers
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ long long globaltimer() {
-  long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Bounded wait: false (and the timeout bit in *err) if the phase did not complete within kWaitNs.
-// try_wait itself suspends the thread until the phase completes or a short hardware time limit
-// passes, so the loop needs no sleep of its own (a sleep would delay the wake-up).
+// (gint_ptx.cuh) with this file's bounded-wait limit and error bit
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = globaltimer();
-  while (!mbar_try_wait(bar, parity)) {
-    if (globaltimer() - t0 > kWaitNs) {
-      atomicOr(err, GINT_ERRBIT_TIMEOUT);
-      return false;
-    }
-  }
-  return true;
+  return gptx::mbar_wait(bar, parity, err, GINT_ERRBIT_TIMEOUT, kWaitNs);
 }
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-// 1-D bulk copy global -> shared, completing `bytes` of transactions on the mbarrier.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-// 1-D bulk copy shared -> global (bulk-group completion), and the waits on this thread's groups:
-// .read = the shared-memory source may be overwritten; plain = the global writes are done.
-__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
-               "r"(bytes)
-               : "memory");
-  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // Named barrier 1 over the density epilogue warps (barrier 0 is __syncthreads).
 __device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-// Shared-memory matrix descriptor, no swizzle, K-major core matrices of 8 rows x 16 bytes:
-// lbo = byte stride between core matrices along K, sbo = byte stride between 8-row groups.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-  return d;                // base offset 0, no swizzle
-}
-// Instruction descriptor of kind::f16: f32 accumulator, f16 A and B, both K-major.
-__device__ __forceinline__ uint32_t idesc_f16(int M, int N) {
-  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-// Both operands MN-major (transposed): core-matrix rows run along M (or N); the descriptors then
-// take LBO = stride between core matrices along K, SBO = stride along M (or N).
-__device__ __forceinline__ uint32_t idesc_f16_mn(int M, int N) { return idesc_f16(M, N) | (1u << 15) | (1u << 16); }
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-// 32 lanes x 32 bit x 16 columns: thread i of the warp receives its lane's 16 values.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 32 lanes x 32 bit x 8 columns.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr)
-               : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // x = hi + lo with both parts float16 (hi = round(x), lo = round(x - hi)), two values at once
 // (packed float32x2 -> float16x2 round-to-nearest conversions): hw, lw hold the hi and lo halves
@@ -1765,6 +1651,65 @@ __global__ void __launch_bounds__(128) k_build_plans(const __grid_constant__ GTa
   }
 }
 
+// ------------------------------------------------------------------------------ orbital diagnostic
+// One thread per (point, atom): the periodised orbitals of the atom and their gradients at an
+// arbitrary point, summed over the lattice images whose support covers it, by the brick kernels'
+// own evaluators: float64 (the CUDA-core path's add_orbitals) or float32 (the tensor-core path's
+// double-float distance, knot and Hermite evaluation, difference tables for the derivatives).
+__global__ void k_orbitals(const __grid_constant__ GGeom g, const double2 *__restrict__ tab64,
+                           const float2 *__restrict__ tab, const float2 *__restrict__ tabi,
+                           const float *__restrict__ dtab, const float *__restrict__ dtabi, const double *__restrict__ pos,
+                           const int *__restrict__ species, const int *__restrict__ aoff, long long npts, int norb,
+                           const double *__restrict__ pts, int fp64, double *__restrict__ phi, double *__restrict__ grad) {
+  const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= npts * g.natoms) return;
+  const long long q = u / g.natoms;
+  const int I = (int)(u - q * g.natoms), sp = species[I];
+  const GSpecies &S = g.sp[sp];
+  const int no = S.norb, o = aoff[I];
+  double v64[GINT_MAX_ORB_ATOM], gv64[GINT_MAX_ORB_ATOM][3];
+  float v32[GINT_MAX_ORB_ATOM], gv32[3 * GINT_MAX_ORB_ATOM];
+  for (int i = 0; i < no; ++i) {
+    v64[i] = gv64[i][0] = gv64[i][1] = gv64[i][2] = 0.0;
+    v32[i] = gv32[3 * i] = gv32[3 * i + 1] = gv32[3 * i + 2] = 0.f;
+  }
+  double d0[3], uf[3];
+  for (int d = 0; d < 3; ++d) d0[d] = pts[3 * q + d] - pos[3 * I + d];
+  for (int d = 0; d < 3; ++d) uf[d] = d0[0] * g.inv[0 * 3 + d] + d0[1] * g.inv[1 * 3 + d] + d0[2] * g.inv[2 * 3 + d];
+  int lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = (int)ceil(uf[d] - S.rcut * g.reach[d]);
+    hi[d] = (int)floor(uf[d] + S.rcut * g.reach[d]);
+  }
+  for (int n0 = lo[0]; n0 <= hi[0]; ++n0)
+    for (int n1 = lo[1]; n1 <= hi[1]; ++n1)
+      for (int n2 = lo[2]; n2 <= hi[2]; ++n2) {
+        double dd[3];
+        for (int d = 0; d < 3; ++d) dd[d] = d0[d] - (n0 * g.cell[d] + n1 * g.cell[3 + d] + n2 * g.cell[6 + d]);
+        if (dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2] >= S.rcut2) continue;
+        if (fp64) {
+          add_orbitals<double, true, true>(g, tab64, sp, dd[0], dd[1], dd[2], v64, gv64);
+        } else {
+          float dh[3], dl[3];
+          for (int d = 0; d < 3; ++d) split2(dd[d], dh[d], dl[d]);
+          if (dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2] >= S.rcut2f) continue;  // the brick kernels' test
+          switch (S.shape) {
+#define CASE_O(ns, np_, nd) \
+  case GINT_SHAPE(ns, np_, nd): add_image_fast<ns, np_, nd, true>(g, tabi, dtabi, S, dh, dl, v32, gv32); break;
+            GINT_FOR_SHAPES(CASE_O)
+#undef CASE_O
+            default:
+              add_image_generic<true>(g, tab, dtab, S, dh, dl, v32, gv32);
+          }
+        }
+      }
+  for (int i = 0; i < no; ++i) {
+    phi[q * norb + o + i] = fp64 ? v64[i] : (double)v32[i];
+    if (grad)
+      for (int d = 0; d < 3; ++d) grad[(q * norb + o + i) * 3 + d] = fp64 ? gv64[i][d] : (double)gv32[3 * i + d];
+  }
+}
+
 // ------------------------------------------------------------------------------ self-test
 // One f16 MMA per operand layout the brick kernels use, on integer data; err_out[0] = max |D - exact|.
 //   layout 0, 1: K-major, LBO 128 (K), SBO 256 / 512 (8-row groups) -- density P and B stages
@@ -2211,6 +2156,43 @@ int gint_tc_rho(gint_handle *h, int precision, const double *D, double *rho, con
 int gint_tc_vlocal(gint_handle *h, int precision, const double *V, double *H, cudaStream_t st) {
   const gint_task t{h, nullptr, V, nullptr, H, nullptr};
   return gint_tc_batch(&t, 1, precision, st, nullptr, nullptr);
+}
+
+extern "C" int gint_orbitals(gint_handle *h, int precision, long long npts, const double *pts, double *phi,
+                             double *grad) {
+  if (!h || npts < 0 || (npts > 0 && (!pts || !phi))) return GINT_EINVAL;
+  if (precision != GINT_FP64 && precision != GINT_F16X3) return GINT_EUNSUPPORTED;
+  if (h->max_species_norb > GINT_MAX_ORB_ATOM) return GINT_ECAPACITY;
+  if (npts == 0) return GINT_OK;
+  const int norb = h->norb, na = h->geom.natoms;
+  double *dp = nullptr, *dphi = nullptr, *dgrad = nullptr;
+  int *daoff = nullptr;
+  int rc = GINT_OK;
+  if (cudaMalloc(&dp, 3 * npts * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dphi, npts * norb * sizeof(double)) != cudaSuccess ||
+      (grad && cudaMalloc(&dgrad, 3 * npts * norb * sizeof(double)) != cudaSuccess) ||
+      cudaMalloc(&daoff, (na + 1) * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    rc = GINT_ENOMEM;
+  }
+  if (!rc && (cudaMemcpy(dp, pts, 3 * npts * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+              cudaMemcpy(daoff, h->atom_off.data(), (na + 1) * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess))
+    rc = GINT_ECUDA;
+  if (!rc) {
+    const long long nt = npts * na;
+    k_orbitals<<<(unsigned)((nt + 127) / 128), 128>>>(h->geom, h->tab64, h->tab32, h->tab32i, h->dtab32, h->dtab32i,
+                                                      h->pos_dev, h->species_dev, daoff, npts, norb, dp,
+                                                      precision == GINT_FP64 ? 1 : 0, dphi, dgrad);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) rc = GINT_ECUDA;
+  }
+  if (!rc && (cudaMemcpy(phi, dphi, npts * norb * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+              (grad && cudaMemcpy(grad, dgrad, 3 * npts * norb * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)))
+    rc = GINT_ECUDA;
+  cudaFree(dp);
+  cudaFree(dphi);
+  cudaFree(dgrad);
+  cudaFree(daoff);
+  return rc;
 }
 
 extern "C" int gint_tc_selftest(int n, double *max_err) {

@@ -90,13 +90,16 @@ _lib.gint_dm_build.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.gint_dm_build_f16x3.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.gint_cn_info.argtypes = [_vp, ctypes.POINTER(_i)]
 _lib.gint_edm.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+_lib.gint_brick_lists.argtypes = [_vp, ctypes.POINTER(_ll), ctypes.POINTER(_ll), _vp, _vp, _vp, _vp]
+_lib.gint_orbitals.argtypes = [_vp, _i, _ll, _vp, _vp, _vp]
 
 C_ABI_SYMBOLS = ("gint_create", "gint_destroy", "gint_layout", "gint_pairs", "gint_stats", "gint_set_positions",
                  "gint_rho", "gint_vlocal", "gint_force", "gint_grid_dot", "gint_block_dot", "gint_weight",
                  "gint_strerror", "gint_sync", "gint_tc_selftest", "gint_grid_dot_noalloc", "gint_run_batch",
                  "gint_run_batch_timed", "gint_memory", "gint_layout_R", "gint_vlocal_R", "gint_bloch",
                  "gint_set_projectors", "gint_psibeta_layout", "gint_psibeta", "gint_cn_create", "gint_cn_destroy",
-                 "gint_cn_step", "gint_dm_build", "gint_dm_build_f16x3", "gint_cn_info", "gint_edm")
+                 "gint_cn_step", "gint_dm_build", "gint_dm_build_f16x3", "gint_cn_info", "gint_edm",
+                 "gint_brick_lists", "gint_orbitals")
 
 
 class CrankNicolson:
@@ -274,6 +277,32 @@ class Gint:
         _check(_lib.gint_stats(self._h, ctypes.byref(W), ctypes.byref(Wx), ctypes.byref(nb), ctypes.byref(mo),
                                ctypes.byref(ma)), "gint_stats")
         return dict(W=W.value, W_exec=Wx.value, nbricks=nb.value, max_brick_orb=mo.value, max_brick_atoms=ma.value)
+
+    def brick_lists(self):
+        """The grid-brick -> atom neighbour lists (host copies): b_off [nbricks + 1], slot_atom [nslots],
+        slot_ent [nslots + 1], ent_pos [nentries, 3] (Cartesian tau_I + R of each entry)."""
+        ns, ne = _ll(), _ll()
+        _check(_lib.gint_brick_lists(self._h, ctypes.byref(ns), ctypes.byref(ne), None, None, None, None),
+               "gint_brick_lists")
+        nb = self.stats()["nbricks"]
+        b_off = np.zeros(nb + 1, dtype=np.int64)
+        atom = np.zeros(max(ns.value, 1), dtype=np.int32)
+        ent = np.zeros(ns.value + 1, dtype=np.int64)
+        epos = np.zeros((max(ne.value, 1), 3))
+        _check(_lib.gint_brick_lists(self._h, ctypes.byref(ns), ctypes.byref(ne), b_off.ctypes.data, atom.ctypes.data,
+                                     ent.ctypes.data, epos.ctypes.data), "gint_brick_lists")
+        return b_off, atom[:ns.value], ent, epos[:ne.value]
+
+    def orbitals(self, pts: np.ndarray, precision: int = FP64):
+        """Periodised orbitals and gradients at the points [n, 3] by the kernels' evaluators (FP64 or
+        F16X3): (phi [n, norb], grad [n, norb, 3])."""
+        pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+        n = pts.shape[0]
+        phi = np.zeros((n, self.norb))
+        grad = np.zeros((n, self.norb, 3))
+        _check(_lib.gint_orbitals(self._h, int(precision), n, pts.ctypes.data, phi.ctypes.data, grad.ctypes.data),
+               "gint_orbitals")
+        return phi, grad
 
     def memory(self) -> int:
         """Device bytes held by the handle (tables, neighbour lists, workspace)."""
