@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the float64 GPU comparator (0: skip)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the serving run and the per-R, projector and Crank-Nicolson timings")
     ap.add_argument("--dense-only", action="store_true",
                     help="time only the dense steps (Crank-Nicolson, density matrices) at the workload's basis size")
     ap.add_argument("--serve-requests", type=int, default=256, help="Poisson serving run (0: skip)")
@@ -652,19 +654,19 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
     serving = None
-    if rank == 0 and world == 1 and args.serve_requests > 0:
+    if rank == 0 and world == 1 and args.serve_requests > 0 and not args.no_extras:
         serving = run_serving(args, prec, dev)
 
     per_R = None
-    if rank == 0 and tensor:
+    if rank == 0 and tensor and not args.no_extras:
         per_R = run_per_R(g, V, prec, args.steps, stream, flush, peaks.get("hbm_gbs"))
 
     psibeta = None
-    if rank == 0 and tensor:
+    if rank == 0 and tensor and not args.no_extras:
         psibeta = run_psibeta(g, w.system, 3, stream)
 
     cn = None
-    if rank == 0 and tensor:
+    if rank == 0 and tensor and not args.no_extras:
         cn = run_cn(g.norb, 128 if g.norb < 2048 else 1024, 3 if g.norb < 2048 else 2, stream)
 
     launches = KERNEL_LAUNCHES.get(args.precision)
