@@ -50,6 +50,7 @@ extern "C" {
 #define GINT_ECAPACITY (-6)  /* a brick holds more orbitals/atoms than the kernels support */
 #define GINT_ESKIN (-7)      /* atoms moved so that a pair outside the block set now overlaps */
 #define GINT_EUNSUPPORTED (-8) /* precision mode or feature not available on this device */
+#define GINT_EBUSY (-9)      /* the serving queue is full or the task's handle has a job in flight */
 
 /* Precision of the brick contractions.  The charge and energy reductions and the per-atom force
  * reduction are float64 in every mode.  The cross-brick reduction of H is float64 in the FP64 mode;
@@ -283,6 +284,37 @@ int gint_run_batch(const gint_task *tasks, int ntasks, int precision, void *stre
  * without the per-call preparation and reduction launches. */
 int gint_run_batch_timed(const gint_task *tasks, int ntasks, int precision, void *stream, void *ev_start,
                          void *ev_stop);
+
+/* Continuous-batching server: ONE resident launch of the brick kernels drains a device work queue to
+ * which jobs are appended while it runs, so a request that arrives while others are on the GPU starts
+ * as soon as it is published, in the same residency, and its work overlaps theirs on the device.  A
+ * job is one task (rho, H and, with forces, F of one system, as for gint_run_batch); its per-call
+ * preparation (maxima and scales), D tiles, bricks and H reduction are all items of the resident
+ * kernel, each waiting (bounded) for the items of its job that it depends on.  The kernel leaves after
+ * idle_s seconds without work (or on gint_server_stop); submit and test relaunch it when needed.
+ *
+ * gint_server_create: precision GINT_F16X3 or GINT_F16X1; forces != 0 runs the force variant of the
+ *   brick items (jobs may then ask for F; tasks without F get rho from the same pass).  Allocates its
+ *   queue and host-mapped completion words on the current device.
+ * gint_server_submit: publishes one task.  Its device inputs (D, V) must be complete in stream order
+ *   on `stream` (the job starts after that stream's work submitted so far); outputs are written
+ *   asynchronously.  Every task's handle must be on the server's device with the same species list.
+ *   At most 64 jobs in flight and one job per handle at a time: GINT_EBUSY otherwise (test the
+ *   earlier jobs and submit again).  *ticket identifies the job.  Does not block.
+ * gint_server_test: *done = 1 once the job's results are in device memory (then read them on any
+ *   stream); relaunches the resident kernel if it left with work outstanding; GINT_ETIMEDOUT /
+ *   GINT_EDEVICE if an item's bounded wait gave up (the server cannot be used any more).
+ * gint_server_stats: kernel launches so far and jobs submitted.
+ * gint_server_stop: makes the resident kernel leave once idle and waits for it.
+ * gint_server_destroy: stop, then free.
+ * The paper has no serving layer; this is the serving pattern around its grid passes. */
+typedef struct gint_server gint_server;
+int gint_server_create(int precision, int forces, double idle_s, gint_server **out);
+int gint_server_submit(gint_server *s, const gint_task *task, void *stream, long long *ticket);
+int gint_server_test(gint_server *s, long long ticket, int *done);
+int gint_server_stats(const gint_server *s, long long *launches, long long *jobs);
+int gint_server_stop(gint_server *s);
+int gint_server_destroy(gint_server *s);
 
 /* Float64 reductions on the device, written to out_dev[0] (device):
  *   V != NULL: w * sum_g V_g rho_g  (the energy E);   V == NULL: w * sum_g rho_g (N_e = Tr(DS)). */

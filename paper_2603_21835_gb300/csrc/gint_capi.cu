@@ -631,6 +631,7 @@ const char *gint_strerror(int code) {
     case GINT_ECAPACITY: return "brick exceeds kernel capacity";
     case GINT_ESKIN: return "atoms moved beyond the pair-set skin";
     case GINT_EUNSUPPORTED: return "unsupported precision or feature";
+    case GINT_EBUSY: return "serving queue full, or the handle has a job in flight";
     default: return "unknown error";
   }
 }

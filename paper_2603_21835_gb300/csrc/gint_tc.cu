@@ -710,64 +710,49 @@ __device__ __forceinline__ int batch_sys(const GBatch &B, long long it) {
 //     the last 128-row A tile reads up to kHTail bytes above them (rows above NP, whose outputs are
 //     ignored); afterwards the whole region stages the brick's scratch tiles for one bulk store.
 // FORCE: density items produce rho and forces (full Y); a system without F only gets rho.
+// One brick item of the persistent kernels (its metadata already unpacked into sh, the per-point
+// potential in sh.wv): orbitals, the density / force chunk stream and the local-H pass.  Dynamic
+// shared memory, laid out for the item's padded width NP: P (hi, lo), then as many density stages
+// (hi and lo of an NP x 16 panel each) as fit, up to kMaxStages (narrower bricks get more chunks in
+// flight), then at least kHTail bytes.  cx carries the CTA's barrier phases across items.
+struct ItemCtx {
+  uint32_t fpar;  // bit s: phase parity of the next use of stage s (full[s])
+  uint32_t dpar;  // bit c: phase parity of done[c] (used once per density brick that has a chunk c)
+  uint32_t GH;    // local-H stages issued by this CTA
+  bool ok;        // no bounded wait has given up
+};
 template <bool FORCE>
-__global__ void __launch_bounds__(kT, 1)
-    k_tc_fused(const __grid_constant__ GTabs g, const __grid_constant__ GBatch B, const __half *__restrict__ zero,
-               int *work) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ BrickSh sh;
+__device__ __forceinline__ void brick_body(const GTabs &g, const GSys &S, long long b, bool do_rho, bool do_h,
+                                           int split3, int dsmem, const __half *__restrict__ zero, uint32_t tmem,
+                                           BrickSh &sh, unsigned char *smem, ItemCtx &cx) {
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int split3 = B.split3;
-  // dynamic shared memory of an item, laid out for its own padded width NP: P (hi, lo), then as many
-  // density stages (hi and lo of an NP x 16 panel each) as fit, up to kMaxStages (narrower bricks get
-  // more chunks in flight), then at least kHTail bytes
-  uint32_t sboP = 0, bop = 0;  // P row-group stride; one B operand (hi or lo) of one stage
-  unsigned char *Ph = smem, *Pl = smem, *B0 = smem;
-  int nst = 2;  // density stages of the item
-  const long long total = B.start[B.nsys];
-  // thread 0: fetches the next item and starts the bulk copy of its plan record into planbuf
-  // (the buffer is free: the current item's record was unpacked before the last barrier)
-  auto next_item = [&]() {
-    const long long nx = atomicAdd(work, 1);
-    sh.item = (int)nx;
-    sh.plan_pref = 0;
-    if (nx >= total) return;
-    const int s2 = batch_sys(B, nx);
-    const GSys &S2 = B.sys[s2];
-    if (!S2.plan) return;
-    const long long b2 = nx - B.start[s2];
-    const long long o0 = S2.plan_off[b2], o1 = S2.plan_off[b2 + 1];
-    const uint32_t bytes = (uint32_t)((o1 - o0) * 16);
-    if (bytes > 4u * kPlanWords) return;
-    fence_async_smem();  // earlier generic reads of planbuf before the asynchronous write
-    mbar_arrive_tx(&sh.plan_bar, bytes);
-    bulk_g2s(sh.planbuf, S2.plan + o0, bytes, &sh.plan_bar);
-    sh.plan_pref = 1;
-  };
-  if (t == 0) {
-    for (int s = 0; s < kMaxStages; ++s) mbar_init(&sh.full[s], 1);
-    for (int c = 0; c < kMaxChunks; ++c) mbar_init(&sh.done[c], 1);
-    mbar_init(&sh.hdone[0], 1);
-    mbar_init(&sh.hdone[1], 1);
-    mbar_init(&sh.plan_bar, 1);
-    fence_mbar_init();
-    sh.abort = 0;
-    next_item();
-  }
-  if (warp == 0) {
-    tmem_alloc(&sh.tmem, 512);
-    tmem_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = sh.tmem;
-  uint32_t pphase = 0;  // plan records consumed by this CTA (phase parity of plan_bar)
-  uint32_t fpar = 0;  // bit s: phase parity of the next use of stage s (full[s])
-  uint32_t dpar = 0;  // bit c: phase parity of done[c] (used once per density brick that has a chunk c)
-  uint32_t GH = 0;    // local-H stages issued by this CTA
-  int cur = -1;       // system whose points and scales are in shared memory
-  bool ok = true;
+  uint32_t &fpar = cx.fpar, &dpar = cx.dpar, &GH = cx.GH;
+  bool &ok = cx.ok;
+  const int na = sh.na, NP = sh.np;
+  // force launches with the three-term split use a fixed-point split of P and D (exact hi * hi
+  // accumulation, four products): D at 2^-4 of the floating split's scale (|hi| < 2048), and each
+  // row of P (grid point) rescaled by its own power of two s_p so that its largest |value| lies in
+  // [512, 1024)
+  const bool fixp = FORCE && split3;
+  const float Sphi = sh.sc[0];
+  {
+    // ================================================================ orbitals, density / force
+    const float SD = fixp ? sh.sc[1] * kFxScaleD : sh.sc[1];
+    const int p = t & 127, q = t >> 7;  // grid point, slot slice (0..3)
+    const uint32_t lane_base = (uint32_t)((p >> 5) * 32) << 16;
+    int gi, gj, gk;
+    const bool valid = brick_point(S.c, b, p, gi, gj, gk);
+    const long long gidx = valid ? grid_index(S.c, gi, gj, gk) : 0;
+    if (na == 0) {
+      if (do_rho && q == 0 && valid && S.rho) S.rho[gidx] = 0.0;
+      return;
+    }
+    const int nch = NP / kRC;
+    const uint32_t sboP = 16u * (uint32_t)NP;  // P row-group stride
+    unsigned char *const Ph = smem, *const Pl = smem + 128u * (uint32_t)NP * 2u;
+    unsigned char *const B0 = smem + 128u * (uint32_t)NP * 4u;
+    const uint32_t bop = (uint32_t)NP * kRC * 2u;  // one B operand (hi or lo) of one stage
+    const int nst = min(kMaxStages, (int)(((uint32_t)dsmem - 128u * (uint32_t)NP * 4u - kHTail) / (2u * bop)));
   // bulk copies of chunk c's B tile (rows [rowbase, NP) x columns [16c, 16c+16)) into stage s
   auto issue_copies = [&](const GSys &S, int c, int s, int NP, int na) {
     const int rowbase = FORCE ? 0 : c * kRC;
@@ -839,6 +824,521 @@ __global__ void __launch_bounds__(kT, 1)
       bulk_g2s(Bs + gr * 512 + sg * 256, src < 0 ? zero : (diag ? S.Dhl2 : S.Dhl) + 2 * src, 256u, &sh.full[s]);
     }
   };
+    // chunk c uses stage c mod nst; its phase parity is that stage's next parity, flipped once per
+    // earlier use of the stage in this item
+    // the previous item's MMAs are complete: every stage is free, prefetch the first density chunks
+    // (one chunk per prefetch warp: a warp issuing a chunk's bulk copies spends a sizeable part of
+    // the orbital evaluation on it)
+    if (do_rho) {
+      const int li = prefetch_index(warp);
+      if (li >= 0 && li < nch && li < nst) issue_copies(S, li, li, NP, na);
+    }
+    // ---- phase A: scaled orbitals of all atoms at every point -> P (hi, lo), zero padding
+    for (int a = q; a < na; a += 4) {
+      const int gap0 = gap_begin(sh, a), pc = sh.s_pcol[a];
+      for (int k = gap0; k < pc; k += 8) {
+        const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
+        *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(0u, 0u, 0u, 0u);
+      }
+      if (a == na - 1)
+        for (int k = pc + sh.s_po[a]; k < NP; k += 8) {
+          const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
+          *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(0u, 0u, 0u, 0u);
+          *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    {
+      const float2 *tab = S.tab, *tabi = S.tabi;
+      const PointDF P = point_df(sh, p);
+      for (int a = q; a < na; a += 8) {
+        const int a1 = a + 4;
+        const int shp = g.sp[sh.s_sp[a]].shape;
+        const bool pair = a1 < na && g.sp[sh.s_sp[a1]].shape == shp;
+        switch (shp) {
+#define CASE_P(ns, np_, nd)                                                                                      \
+case GINT_SHAPE(ns, np_, nd):                                                                                \
+  if (pair)                                                                                                  \
+    job_P2<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tabi, sh, a, a1, P, p, valid, Sphi, Ph, Pl, sboP); \
+  else                                                                                                       \
+    job_P<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tabi, sh, a, P, p, valid, Sphi, Ph, Pl, sboP);    \
+  break;
+          GINT_FOR_SHAPES(CASE_P)
+#undef CASE_P
+          default:
+            job_P_generic(g, tab, sh, a, p, valid, Sphi, Ph, Pl, sboP);
+        }
+        if (a1 < na && !(pair && shp != 0)) {
+          switch (g.sp[sh.s_sp[a1]].shape) {
+#define CASE_P1(ns, np_, nd)                                                                                      \
+case GINT_SHAPE(ns, np_, nd):                                                                                 \
+  job_P<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tabi, sh, a1, P, p, valid, Sphi, Ph, Pl, sboP);    \
+  break;
+            GINT_FOR_SHAPES(CASE_P1)
+#undef CASE_P1
+            default:
+              job_P_generic(g, tab, sh, a1, p, valid, Sphi, Ph, Pl, sboP);
+          }
+        }
+      }
+    }
+    if (fixp) {
+      // ---- fixed-point rows: s_p from the row's largest |value| (the four slices' maxima), then
+      // every element x = (hi + lo) s_p re-split as hi = rint(x), lo = x - hi (float16)
+      float m = 0.f;
+      for (int a = q; a < na; a += 4)
+        for (int k = sh.s_pcol[a]; k < sh.s_pcol[a] + sh.s_po[a]; k += 8) {
+          const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
+          const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + off), wl = *reinterpret_cast<const uint4 *>(Pl + off);
+          const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
+            const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
+            m = fmaxf(m, fmaxf(fabsf(hf.x + lf.x), fabsf(hf.y + lf.y)));
+          }
+        }
+      sh.rpart[q][p] = m;
+      __syncthreads();
+      const float rm = fmaxf(fmaxf(sh.rpart[0][p], sh.rpart[1][p]), fmaxf(sh.rpart[2][p], sh.rpart[3][p]));
+      int ex = 0;
+      frexpf(rm, &ex);  // rm = f 2^ex, f in [0.5, 1)
+      const float sp = rm > 0.f ? ldexpf(1.f, 10 - ex) : 1.f;
+      if (q == 0) sh.rsc[p] = sp;
+      for (int a = q; a < na; a += 4)
+        for (int k = sh.s_pcol[a]; k < sh.s_pcol[a] + sh.s_po[a]; k += 8) {
+          const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
+          const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + off), wl = *reinterpret_cast<const uint4 *>(Pl + off);
+          const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
+          uint32_t oh[4], ol[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
+            const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
+            split_fx2((hf.x + lf.x) * sp, (hf.y + lf.y) * sp, oh[e], ol[e]);
+          }
+          *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(oh[0], oh[1], oh[2], oh[3]);
+          *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
+        }
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (do_rho) {
+    // ---- phase B: chunks of 16 columns, prefetch warps / MMA thread / epilogue warps
+    const uint32_t corr_base = (NP <= 256) ? 256u : 0u;  // separate correction accumulator if it fits
+    if (warp == kMmaWarp) {
+      if (lane == 0 && NP <= 256 && split3 && corr_base) {
+        // common case, straight-line issue (branches and descriptor rebuilds in this loop cost more
+        // issue time than the MMAs take to run): the descriptors' start-address field (bytes / 16)
+        // advances by constants, 256 bytes of P per chunk and 2 bop per stage.  The stage barrier
+        // orders the copies before the MMAs; the epilogue's tensor-memory reads touch finished
+        // columns only, so one tcgen05 fence per item suffices.
+        unsigned *errp = S.err;
+        uint32_t s = 0, wrap = 0;
+        const uint64_t dah0 = sdesc(smem_u32(Ph), 128, sboP), dal0 = sdesc(smem_u32(Pl), 128, sboP);
+        const uint64_t dbh0 = sdesc(smem_u32(B0), 256, 512);
+        const uint32_t sstep = (2 * bop) >> 4, lstep = 128 >> 4;
+        tc_fence_after();  // after the barrier that ended the previous item's tensor-memory reads
+        for (int c = 0; c < nch; ++c) {
+          if (!mbar_wait(&sh.full[s], ((fpar >> s) & 1u) ^ wrap, errp)) ok = false;
+          const uint32_t rowbase = FORCE ? 0u : (uint32_t)c * kRC;
+          const uint32_t id = idesc_f16(128, NP - (int)rowbase), acc = c > 0 ? 1u : 0u;
+          const uint64_t dah = dah0 + (uint64_t)(16 * c), dal = dal0 + (uint64_t)(16 * c);
+          const uint64_t dbh = dbh0 + (uint64_t)(s * sstep), dbl = dbh + lstep;
+          mma_f16(tmem + rowbase, dah, dbh, id, acc);
+          mma_f16(tmem + 256u + rowbase, dah, dbl, id, acc);
+          mma_f16(tmem + 256u + rowbase, dal, dbh, id, 1u);
+          if (FORCE) mma_f16(tmem + 256u + rowbase, dal, dbl, id, 1u);  // fixed-point split: lo * lo too
+          mma_commit(&sh.done[c]);
+          if (++s == (uint32_t)nst) {
+            s = 0;
+            wrap ^= 1u;
+          }
+        }
+      } else if (lane == 0) {
+        unsigned *errp = S.err;
+        uint32_t s = 0, wrap = 0;  // stage of chunk c, and 1 once the stages have wrapped an odd number of times
+        for (int c = 0; c < nch; ++c) {
+          if (!mbar_wait(&sh.full[s], ((fpar >> s) & 1u) ^ wrap, errp)) ok = false;
+          tc_fence_after();
+          unsigned char *Bh = B0 + s * 2 * bop, *Bl = Bh + 128;
+          const int rowbase = FORCE ? 0 : c * kRC;
+          const int N = NP - rowbase;
+          const uint64_t dah = sdesc(smem_u32(Ph) + (c * kRC / 8) * 128, 128, sboP);
+          const uint64_t dal = sdesc(smem_u32(Pl) + (c * kRC / 8) * 128, 128, sboP);
+          for (int n0 = 0; n0 < N; n0 += 256) {
+            const int nn = min(256, N - n0);
+            const uint32_t id = idesc_f16(128, nn);
+            const uint64_t dbh = sdesc(smem_u32(Bh) + (n0 >> 3) * 512, 256, 512);
+            const uint64_t dbl = sdesc(smem_u32(Bl) + (n0 >> 3) * 512, 256, 512);
+            const uint32_t dm = tmem + rowbase + n0, dc = tmem + corr_base + rowbase + n0;
+            mma_f16(dm, dah, dbh, id, c > 0 ? 1u : 0u);
+            if (split3) {
+              mma_f16(dc, dah, dbl, id, (c > 0 || corr_base == 0) ? 1u : 0u);
+              mma_f16(dc, dal, dbh, id, 1u);
+              if (fixp) mma_f16(dc, dal, dbl, id, 1u);
+            }
+          }
+          mma_commit(&sh.done[c]);
+          if (++s == (uint32_t)nst) {
+            s = 0;
+            wrap ^= 1u;
+          }
+        }
+      }
+      __syncwarp();
+    } else if (prefetch_index(warp) >= 0) {
+      // prefetch warps, later chunks: chunk k (k mod kPrefetchWarps = the warp's prefetch index),
+      // its bulk copies issued once chunk k - nst's MMAs are done (the stage is free)
+      unsigned *errp = S.err;
+      const int li = prefetch_index(warp);
+      for (int k = nst + ((li - nst) % kPrefetchWarps + kPrefetchWarps) % kPrefetchWarps; k < nch;
+           k += kPrefetchWarps) {
+        if (!mbar_wait(&sh.done[k - nst], (dpar >> (k - nst)) & 1u, errp)) ok = false;
+        issue_copies(S, k, k % nst, NP, na);
+      }
+    } else if (!FORCE) {
+      // density epilogue groups (each covers the 128 lanes) drain finished chunks round robin
+      // (compensated float32 sums per point and group)
+      const int grp = epi_group(warp);
+      float rhi = 0.f, rlo = 0.f;
+      for (int c = grp; c < nch; c += kEpiGroups) {
+        if (!mbar_wait(&sh.done[c], (dpar >> c) & 1u, S.err)) ok = false;
+        tc_fence_after();
+        // chunk c's columns are final: rho += P_k Y_k
+        const int k0 = c * kRC;
+        float y[16], yc[16];
+        tmem_ld16(tmem + lane_base + k0, y);
+        if (split3 && corr_base) {
+          tmem_ld16(tmem + lane_base + corr_base + k0, yc);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) y[i] += yc[i];
+        }
+        float part = 0.f;
+#pragma unroll
+        for (int hseg = 0; hseg < 2; ++hseg) {
+          const uint32_t off = (p >> 3) * sboP + ((k0 >> 3) + hseg) * 128 + (p & 7) * 16;
+          const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + off), wl = *reinterpret_cast<const uint4 *>(Pl + off);
+          const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
+            const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
+            part += (hf.x + lf.x) * y[hseg * 8 + 2 * e] + (hf.y + lf.y) * y[hseg * 8 + 2 * e + 1];
+          }
+        }
+        float sum, err;
+        two_sum(rhi, part, sum, err);
+        rhi = sum;
+        rlo += err;
+      }
+      if (grp > 0) {
+        sh.rpart[grp][p] = rhi;
+        sh.rpartl[grp][p] = rlo;
+      }
+      epi_barrier();
+      if (grp == 0) {
+        for (int g2 = 1; g2 < kEpiGroups; ++g2) {
+          float sum, err;
+          two_sum(rhi, sh.rpart[g2][p], sum, err);
+          rhi = sum;
+          rlo += err + sh.rpartl[g2][p];
+        }
+        if (valid && S.rho)
+          S.rho[gidx] = ((double)rhi + (double)rlo) * (2.0 / ((double)Sphi * (double)Sphi * (double)SD));
+      }
+    }
+    // all MMAs of the brick are complete once the last chunk's barrier has flipped (in order)
+    if (!mbar_wait(&sh.done[nch - 1], (dpar >> (nch - 1)) & 1u, S.err)) ok = false;
+    tc_fence_after();
+    for (int st = 0; st < nst && st < nch; ++st)  // stage st served chunks st, st + nst, ...
+      if ((((nch - 1 - st) / nst) & 1) == 0) fpar ^= 1u << st;
+    dpar ^= (nch >= 32) ? 0xffffffffu : ((1u << nch) - 1u);
+    if (FORCE) {
+      // full Y: per atom, rho and force from recomputed phi and grad phi (unscaled float32)
+      const float2 *tab = S.tab, *tabi = S.tabi;
+      const float inv = 1.f / (Sphi * SD * (fixp ? sh.rsc[p] : 1.f));
+      const float wv = (valid && S.V) ? sh.wv[p] : 0.f;
+      float rp = 0.f;
+      for (int a = q; a < na; a += 4) {
+        const int pc = sh.s_pcol[a], po = sh.s_po[a];
+        // the atom's own columns only (an 8-column atom may end the accumulator: a 16-column
+        // load there would reach past the tensor-memory allocation)
+        float y[GINT_MAX_ORB_ATOM], yc[16];
+        for (int h = 0; h < po; h += 16) {
+          if (po - h >= 16) {
+            tmem_ld16(tmem + lane_base + pc + h, y + h);
+            if (split3 && corr_base) {
+              tmem_ld16(tmem + lane_base + corr_base + pc + h, yc);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) y[h + i] += yc[i];
+            }
+          } else {
+            tmem_ld8(tmem + lane_base + pc + h, y + h);
+            if (split3 && corr_base) {
+              tmem_ld8(tmem + lane_base + corr_base + pc + h, yc);
+#pragma unroll
+              for (int i = 0; i < 8; ++i) y[h + i] += yc[i];
+            }
+          }
+        }
+        for (int i = 0; i < po; ++i) y[i] *= inv;
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        switch (g.sp[sh.s_sp[a]].shape) {
+#define CASE_F(ns, np_, nd)                                                                          \
+case GINT_SHAPE(ns, np_, nd):                                                                    \
+  job_F<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tabi, S.dtabi, sh, a, p, valid, y, rp, fx, fy, fz); \
+  break;
+          GINT_FOR_SHAPES(CASE_F)
+#undef CASE_F
+          default:
+            job_F_generic(g, tab, S.dtab, sh, a, p, valid, y, rp, fx, fy, fz);
+        }
+        fx *= 2.f * wv;
+        fy *= 2.f * wv;
+        fz *= 2.f * wv;
+        for (int o = 16; o > 0; o >>= 1) {
+          fx += __shfl_xor_sync(0xffffffffu, fx, o);
+          fy += __shfl_xor_sync(0xffffffffu, fy, o);
+          fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        }
+        if (lane == 0) {
+          atomicAdd(&sh.fpart[a][0], (double)fx);
+          atomicAdd(&sh.fpart[a][1], (double)fy);
+          atomicAdd(&sh.fpart[a][2], (double)fz);
+        }
+      }
+      sh.rpart[q][p] = rp;
+      __syncthreads();
+      if (q == 0 && valid && S.rho)
+        S.rho[gidx] =
+            (double)sh.rpart[0][p] + (double)sh.rpart[1][p] + (double)sh.rpart[2][p] + (double)sh.rpart[3][p];
+      if (S.F)
+        for (int a = t; a < na; a += kT) {
+          const int I = sh.s_atom[a];
+          atomicAdd(S.F + 3 * I + 0, sh.fpart[a][0]);
+          atomicAdd(S.F + 3 * I + 1, sh.fpart[a][1]);
+          atomicAdd(S.F + 3 * I + 2, sh.fpart[a][2]);
+        }
+    }
+    }  // do_rho
+    if (do_h) {
+      // ================================================================ local H from P
+      // H_mu,nu = sum_g (w V_g P_g,mu) P_g,nu: K = grid points in blocks of hkb, both operands
+      // MN-major views of [point][orbital] buffers (P itself, and W P built per block in one of
+      // two halves of the stage region, ping-pong with the MMAs of the previous block).
+      tc_fence_before();  // the density part's tensor-memory reads are finished
+      __syncthreads();
+      tc_fence_after();
+      const float SA = sh.sc[2];
+      const float out_scale = 1.f / (Sphi * SA);
+      const float wscale = SA / Sphi;
+      const int hkb = nst >= 4 ? 32 : 16, ng = NP >> 3;  // two halves of hkb x NP (hi, lo) fit the stages
+      const uint32_t whalf = (uint32_t)hkb * 4u * (uint32_t)NP;  // hi and lo of one block
+      const int ntile = (NP + 127) / 128;
+      int tb[3] = {0, 0, 0}, T = 0;
+      for (int m = 0; m < ntile; ++m) {
+        tb[m] = T;
+        T += NP - 128 * m;
+      }
+      const uint32_t corr_base = (2 * T <= 512) ? (uint32_t)T : 0u;
+      for (int j = 0; j < 128 / hkb; ++j, ++GH) {
+        const int hh = GH & 1;
+        unsigned char *Wh = B0 + hh * whalf, *Wl = Wh + whalf / 2;
+        // the MMAs that last read this half (two blocks ago) are complete
+        if (GH >= 2 && !mbar_wait(&sh.hdone[hh], ((GH - 2) >> 1) & 1, S.err)) ok = false;
+        const int p0 = j * hkb;
+        // warps 1-15 build the block while thread 0 may still be issuing the previous block's MMAs.
+        // Unit u = (point octet, orbital group, point in octet) with the point fastest: eight
+        // consecutive threads touch one 128-byte core-matrix row block (no bank conflicts).
+        for (int u = t - 32; u >= 0 && u < hkb * ng; u += kT - 32) {
+          const int v8 = u >> 3, po8 = v8 / ng, gg = v8 - po8 * ng;
+          const int pl = po8 * 8 + (u & 7), pt = p0 + pl;
+          const uint32_t so = (pt >> 3) * sboP + gg * 128 + (pt & 7) * 16;
+          const uint32_t dso = (pl >> 3) * sboP + gg * 128 + (pl & 7) * 16;
+          const float f = fixp ? sh.wv[pt] * wscale / (sh.rsc[pt] * sh.rsc[pt]) : sh.wv[pt] * wscale;
+          const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + so), wl = *reinterpret_cast<const uint4 *>(Pl + so);
+          const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
+          uint32_t oh[4], ol[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
+            const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
+            split_h2((hf.x + lf.x) * f, (hf.y + lf.y) * f, oh[e], ol[e]);
+          }
+          *reinterpret_cast<uint4 *>(Wh + dso) = make_uint4(oh[0], oh[1], oh[2], oh[3]);
+          *reinterpret_cast<uint4 *>(Wl + dso) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (t == 0 && NP <= 256 && split3) {
+          // common case, straight-line issue: at most two 128-row tiles of one N <= 256 each; the
+          // descriptors' start-address field advances by 2 sboP / 16 per K step of 16 points, and by
+          // 2048 / 16 from the first to the second tile (orbitals 128-255, rows of A and columns of B)
+          tc_fence_after();
+          const uint64_t wh0 = sdesc(smem_u32(Wh), sboP, 128), wl0 = sdesc(smem_u32(Wl), sboP, 128);
+          const uint32_t pofs = (uint32_t)(p0 >> 3) * sboP;
+          const uint64_t ph0 = sdesc(smem_u32(Ph) + pofs, sboP, 128), pl0 = sdesc(smem_u32(Pl) + pofs, sboP, 128);
+          const uint32_t kstep = (2u * sboP) >> 4;
+          const uint32_t id0 = idesc_f16_mn(128, NP), id1 = idesc_f16_mn(128, NP > 128 ? NP - 128 : 16);
+          const uint32_t m0 = tmem + (uint32_t)tb[0], m1 = tmem + (uint32_t)tb[1];
+          const uint32_t c0 = m0 + corr_base, c1 = m1 + corr_base;
+          for (int ks = 0; ks < hkb / 16; ++ks) {
+            const uint64_t ko = (uint64_t)ks * kstep;
+            const bool first = (j == 0 && ks == 0);
+            const uint32_t am = first ? 0u : 1u, ac = (first && corr_base) ? 0u : 1u;
+            mma_f16(m0, wh0 + ko, ph0 + ko, id0, am);
+            mma_f16(c0, wh0 + ko, pl0 + ko, id0, ac);
+            mma_f16(c0, wl0 + ko, ph0 + ko, id0, 1u);
+            if (NP > 128) {
+              mma_f16(m1, wh0 + ko + 128u, ph0 + ko + 128u, id1, am);
+              mma_f16(c1, wh0 + ko + 128u, pl0 + ko + 128u, id1, ac);
+              mma_f16(c1, wl0 + ko + 128u, ph0 + ko + 128u, id1, 1u);
+            }
+          }
+          mma_commit(&sh.hdone[hh]);
+        } else if (t == 0) {
+          tc_fence_after();
+          for (int ks = 0; ks < hkb / 16; ++ks) {
+            const uint32_t kw = (uint32_t)(2 * ks) * sboP, kp = (uint32_t)((p0 >> 3) + 2 * ks) * sboP;
+            for (int m = 0; m < ntile; ++m) {
+              const uint64_t dah = sdesc(smem_u32(Wh) + kw + m * 16 * 128, sboP, 128);
+              const uint64_t dal = sdesc(smem_u32(Wl) + kw + m * 16 * 128, sboP, 128);
+              const int N = NP - 128 * m;
+              for (int n0 = 0; n0 < N; n0 += 256) {
+                const int nn = min(256, N - n0);
+                const uint32_t id = idesc_f16_mn(128, nn);
+                const uint32_t col = (uint32_t)(128 * m + n0);
+                const uint64_t dbh = sdesc(smem_u32(Ph) + kp + (col >> 3) * 128, sboP, 128);
+                const uint64_t dbl = sdesc(smem_u32(Pl) + kp + (col >> 3) * 128, sboP, 128);
+                const uint32_t dm = tmem + tb[m] + n0, dc = tmem + corr_base + tb[m] + n0;
+                const bool first = (j == 0 && ks == 0);
+                mma_f16(dm, dah, dbh, id, first ? 0u : 1u);
+                if (split3) {
+                  mma_f16(dc, dah, dbl, id, (first && corr_base) ? 0u : 1u);
+                  mma_f16(dc, dal, dbh, id, 1u);
+                }
+              }
+            }
+          }
+          mma_commit(&sh.hdone[hh]);
+        }
+      }
+      {
+        const uint32_t Gp = GH - 1;
+        if (!mbar_wait(&sh.hdone[Gp & 1], (Gp >> 1) & 1, S.err)) ok = false;
+        tc_fence_after();
+      }
+    // epilogue: upper slot-pair tiles -> scratch (float32, unscaled), column-major: tile (a, c),
+    // a <= c, holds norb(c) columns of norb(a) rows at rowst(a) + norb(a) (cumno(c) - cumno(a));
+    // element (i, j) at j norb(a) + i (the row-major norb(c) x norb(a) block (c, a) of the
+    // symmetric brick H).  Only the orbitals themselves are stored (no padding rows or columns),
+    // so the brick's tiles are one dense range of rowst(na) values (padded to 16 bytes).  The range
+    // is assembled in shared memory (the orbital tile and the stage region are free once the MMAs
+    // are done: consecutive rows of a column land in consecutive words, no bank conflicts) and
+    // leaves in one bulk copy that overlaps the next item's set-up; a range larger than the
+    // dynamic shared memory is stored directly.
+    {
+      const int ln = t & 127, qq = t >> 7;
+      const uint32_t lane_base = (uint32_t)((ln >> 5) * 32) << 16;
+      const long long base = S.hs_brick_off[b];
+      const int total = sh.s_rowst[na], padded = (total + 3) & ~3;
+      const bool staged = padded * 4 <= dsmem;
+      float *const stg = staged ? reinterpret_cast<float *>(smem) : S.hs + base;
+      for (int m = 0; m < ntile; ++m) {
+        const int mu = 128 * m + ln;
+        const int as = mu < NP ? sh.col2slot[mu] : kNoSlot;
+        const int il = as != kNoSlot ? mu - sh.s_pcol[as] : 0;
+        const int no_a = as != kNoSlot ? sh.s_no[as] : 0;
+        const bool rowok = as != kNoSlot && il < no_a;
+        const int cum_a = rowok ? sh.s_cumno[as] : 0;
+        float *rowp = stg + (rowok ? sh.s_rowst[as] : 0) + il;
+        const int N = NP - 128 * m;
+        for (int gcol = qq; gcol < N / 16; gcol += 4) {
+          float y[16], yc[16];
+          tmem_ld16(tmem + lane_base + tb[m] + gcol * 16, y);
+          if (split3 && corr_base) {
+            tmem_ld16(tmem + lane_base + corr_base + tb[m] + gcol * 16, yc);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) y[i] += yc[i];
+          }
+          if (!rowok) continue;
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            const int nu = 128 * m + gcol * 16 + 8 * hh;
+            const int cs = sh.col2slot[nu];
+            if (cs == kNoSlot || cs < as) continue;
+            const int j0 = nu - sh.s_pcol[cs], nj = min(8, sh.s_no[cs] - j0);
+            float *dst = rowp + no_a * (sh.s_cumno[cs] - cum_a + j0);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              if (i < nj) dst[i * no_a] = y[8 * hh + i] * out_scale;
+          }
+        }
+      }
+      for (int k = total + t; k < padded; k += kT) stg[k] = 0.f;
+      if (staged) {
+        fence_async_smem();  // the generic writes above before the bulk copy reads them
+        __syncthreads();
+        if (t == 0 && padded > 0) bulk_s2g(S.hs + base, stg, (uint32_t)padded * 4u);
+      }
+    }
+    }  // do_h
+  }
+}
+
+template <bool FORCE>
+__global__ void __launch_bounds__(kT, 1)
+    k_tc_fused(const __grid_constant__ GTabs g, const __grid_constant__ GBatch B, const __half *__restrict__ zero,
+               int *work) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ BrickSh sh;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int split3 = B.split3;
+  const long long total = B.start[B.nsys];
+  // thread 0: fetches the next item and starts the bulk copy of its plan record into planbuf
+  // (the buffer is free: the current item's record was unpacked before the last barrier)
+  auto next_item = [&]() {
+    const long long nx = atomicAdd(work, 1);
+    sh.item = (int)nx;
+    sh.plan_pref = 0;
+    if (nx >= total) return;
+    const int s2 = batch_sys(B, nx);
+    const GSys &S2 = B.sys[s2];
+    if (!S2.plan) return;
+    const long long b2 = nx - B.start[s2];
+    const long long o0 = S2.plan_off[b2], o1 = S2.plan_off[b2 + 1];
+    const uint32_t bytes = (uint32_t)((o1 - o0) * 16);
+    if (bytes > 4u * kPlanWords) return;
+    fence_async_smem();  // earlier generic reads of planbuf before the asynchronous write
+    mbar_arrive_tx(&sh.plan_bar, bytes);
+    bulk_g2s(sh.planbuf, S2.plan + o0, bytes, &sh.plan_bar);
+    sh.plan_pref = 1;
+  };
+  if (t == 0) {
+    for (int s = 0; s < kMaxStages; ++s) mbar_init(&sh.full[s], 1);
+    for (int c = 0; c < kMaxChunks; ++c) mbar_init(&sh.done[c], 1);
+    mbar_init(&sh.hdone[0], 1);
+    mbar_init(&sh.hdone[1], 1);
+    mbar_init(&sh.plan_bar, 1);
+    fence_mbar_init();
+    sh.abort = 0;
+    next_item();
+  }
+  if (warp == 0) {
+    tmem_alloc(&sh.tmem, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sh.tmem;
+  uint32_t pphase = 0;  // plan records consumed by this CTA (phase parity of plan_bar)
+  uint32_t fpar = 0;  // bit s: phase parity of the next use of stage s (full[s])
+  uint32_t dpar = 0;  // bit c: phase parity of done[c] (used once per density brick that has a chunk c)
+  uint32_t GH = 0;    // local-H stages issued by this CTA
+  int cur = -1;       // system whose points and scales are in shared memory
+  bool ok = true;
   for (;;) {
     __syncthreads();
     const long long it = sh.item;
@@ -875,492 +1375,12 @@ __global__ void __launch_bounds__(kT, 1)
       load_brick(S.c, g, S.nb, S.tile_off, b, sh);  // ends with a barrier
     }
     if (t == 0) next_item();  // every thread has read sh.item and sh.plan_pref
-    const int na = sh.na, NP = sh.np;
-    // force launches with the three-term split use a fixed-point split of P and D (exact hi * hi
-    // accumulation, four products): D at 2^-4 of the floating split's scale (|hi| < 2048), and each
-    // row of P (grid point) rescaled by its own power of two s_p so that its largest |value| lies in
-    // [512, 1024)
-    const bool fixp = FORCE && split3;
-    const float Sphi = sh.sc[0];
-    {
-      // ================================================================ orbitals, density / force
-      const float SD = fixp ? sh.sc[1] * kFxScaleD : sh.sc[1];
-      const int p = t & 127, q = t >> 7;  // grid point, slot slice (0..3)
-      const uint32_t lane_base = (uint32_t)((p >> 5) * 32) << 16;
-      int gi, gj, gk;
-      const bool valid = brick_point(S.c, b, p, gi, gj, gk);
-      const long long gidx = valid ? grid_index(S.c, gi, gj, gk) : 0;
-      if (na == 0) {
-        if (do_rho && q == 0 && valid && S.rho) S.rho[gidx] = 0.0;
-        continue;
-      }
-      const int nch = NP / kRC;
-      sboP = 16u * (uint32_t)NP;
-      Pl = smem + 128u * (uint32_t)NP * 2u;
-      B0 = smem + 128u * (uint32_t)NP * 4u;
-      bop = (uint32_t)NP * kRC * 2u;
-      nst = min(kMaxStages, (int)(((uint32_t)B.dsmem - 128u * (uint32_t)NP * 4u - kHTail) / (2u * bop)));
-      // chunk c uses stage c mod nst; its phase parity is that stage's next parity, flipped once per
-      // earlier use of the stage in this item
-      // the previous item's MMAs are complete: every stage is free, prefetch the first density chunks
-      // (one chunk per prefetch warp: a warp issuing a chunk's bulk copies spends a sizeable part of
-      // the orbital evaluation on it)
-      if (do_rho) {
-        const int li = prefetch_index(warp);
-        if (li >= 0 && li < nch && li < nst) issue_copies(S, li, li, NP, na);
-      }
-      // ---- phase A: scaled orbitals of all atoms at every point -> P (hi, lo), zero padding
-      for (int a = q; a < na; a += 4) {
-        const int gap0 = gap_begin(sh, a), pc = sh.s_pcol[a];
-        for (int k = gap0; k < pc; k += 8) {
-          const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
-          *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(0u, 0u, 0u, 0u);
-          *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(0u, 0u, 0u, 0u);
-        }
-        if (a == na - 1)
-          for (int k = pc + sh.s_po[a]; k < NP; k += 8) {
-            const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
-            *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(0u, 0u, 0u, 0u);
-            *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(0u, 0u, 0u, 0u);
-          }
-      }
-      {
-        const float2 *tab = S.tab, *tabi = S.tabi;
-        const PointDF P = point_df(sh, p);
-        for (int a = q; a < na; a += 8) {
-          const int a1 = a + 4;
-          const int shp = g.sp[sh.s_sp[a]].shape;
-          const bool pair = a1 < na && g.sp[sh.s_sp[a1]].shape == shp;
-          switch (shp) {
-#define CASE_P(ns, np_, nd)                                                                                      \
-  case GINT_SHAPE(ns, np_, nd):                                                                                \
-    if (pair)                                                                                                  \
-      job_P2<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tabi, sh, a, a1, P, p, valid, Sphi, Ph, Pl, sboP); \
-    else                                                                                                       \
-      job_P<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tabi, sh, a, P, p, valid, Sphi, Ph, Pl, sboP);    \
-    break;
-            GINT_FOR_SHAPES(CASE_P)
-#undef CASE_P
-            default:
-              job_P_generic(g, tab, sh, a, p, valid, Sphi, Ph, Pl, sboP);
-          }
-          if (a1 < na && !(pair && shp != 0)) {
-            switch (g.sp[sh.s_sp[a1]].shape) {
-#define CASE_P1(ns, np_, nd)                                                                                      \
-  case GINT_SHAPE(ns, np_, nd):                                                                                 \
-    job_P<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tabi, sh, a1, P, p, valid, Sphi, Ph, Pl, sboP);    \
-    break;
-              GINT_FOR_SHAPES(CASE_P1)
-#undef CASE_P1
-              default:
-                job_P_generic(g, tab, sh, a1, p, valid, Sphi, Ph, Pl, sboP);
-            }
-          }
-        }
-      }
-      if (fixp) {
-        // ---- fixed-point rows: s_p from the row's largest |value| (the four slices' maxima), then
-        // every element x = (hi + lo) s_p re-split as hi = rint(x), lo = x - hi (float16)
-        float m = 0.f;
-        for (int a = q; a < na; a += 4)
-          for (int k = sh.s_pcol[a]; k < sh.s_pcol[a] + sh.s_po[a]; k += 8) {
-            const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
-            const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + off), wl = *reinterpret_cast<const uint4 *>(Pl + off);
-            const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
-              const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
-              m = fmaxf(m, fmaxf(fabsf(hf.x + lf.x), fabsf(hf.y + lf.y)));
-            }
-          }
-        sh.rpart[q][p] = m;
-        __syncthreads();
-        const float rm = fmaxf(fmaxf(sh.rpart[0][p], sh.rpart[1][p]), fmaxf(sh.rpart[2][p], sh.rpart[3][p]));
-        int ex = 0;
-        frexpf(rm, &ex);  // rm = f 2^ex, f in [0.5, 1)
-        const float sp = rm > 0.f ? ldexpf(1.f, 10 - ex) : 1.f;
-        if (q == 0) sh.rsc[p] = sp;
-        for (int a = q; a < na; a += 4)
-          for (int k = sh.s_pcol[a]; k < sh.s_pcol[a] + sh.s_po[a]; k += 8) {
-            const uint32_t off = (p >> 3) * sboP + (k >> 3) * 128 + (p & 7) * 16;
-            const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + off), wl = *reinterpret_cast<const uint4 *>(Pl + off);
-            const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
-            uint32_t oh[4], ol[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
-              const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
-              split_fx2((hf.x + lf.x) * sp, (hf.y + lf.y) * sp, oh[e], ol[e]);
-            }
-            *reinterpret_cast<uint4 *>(Ph + off) = make_uint4(oh[0], oh[1], oh[2], oh[3]);
-            *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
-          }
-      }
-      fence_async_smem();
-      __syncthreads();
-      if (do_rho) {
-      // ---- phase B: chunks of 16 columns, prefetch warps / MMA thread / epilogue warps
-      const uint32_t corr_base = (NP <= 256) ? 256u : 0u;  // separate correction accumulator if it fits
-      if (warp == kMmaWarp) {
-        if (lane == 0 && NP <= 256 && split3 && corr_base) {
-          // common case, straight-line issue (branches and descriptor rebuilds in this loop cost more
-          // issue time than the MMAs take to run): the descriptors' start-address field (bytes / 16)
-          // advances by constants, 256 bytes of P per chunk and 2 bop per stage.  The stage barrier
-          // orders the copies before the MMAs; the epilogue's tensor-memory reads touch finished
-          // columns only, so one tcgen05 fence per item suffices.
-          unsigned *errp = S.err;
-          uint32_t s = 0, wrap = 0;
-          const uint64_t dah0 = sdesc(smem_u32(Ph), 128, sboP), dal0 = sdesc(smem_u32(Pl), 128, sboP);
-          const uint64_t dbh0 = sdesc(smem_u32(B0), 256, 512);
-          const uint32_t sstep = (2 * bop) >> 4, lstep = 128 >> 4;
-          tc_fence_after();  // after the barrier that ended the previous item's tensor-memory reads
-          for (int c = 0; c < nch; ++c) {
-            if (!mbar_wait(&sh.full[s], ((fpar >> s) & 1u) ^ wrap, errp)) ok = false;
-            const uint32_t rowbase = FORCE ? 0u : (uint32_t)c * kRC;
-            const uint32_t id = idesc_f16(128, NP - (int)rowbase), acc = c > 0 ? 1u : 0u;
-            const uint64_t dah = dah0 + (uint64_t)(16 * c), dal = dal0 + (uint64_t)(16 * c);
-            const uint64_t dbh = dbh0 + (uint64_t)(s * sstep), dbl = dbh + lstep;
-            mma_f16(tmem + rowbase, dah, dbh, id, acc);
-            mma_f16(tmem + 256u + rowbase, dah, dbl, id, acc);
-            mma_f16(tmem + 256u + rowbase, dal, dbh, id, 1u);
-            if (FORCE) mma_f16(tmem + 256u + rowbase, dal, dbl, id, 1u);  // fixed-point split: lo * lo too
-            mma_commit(&sh.done[c]);
-            if (++s == (uint32_t)nst) {
-              s = 0;
-              wrap ^= 1u;
-            }
-          }
-        } else if (lane == 0) {
-          unsigned *errp = S.err;
-          uint32_t s = 0, wrap = 0;  // stage of chunk c, and 1 once the stages have wrapped an odd number of times
-          for (int c = 0; c < nch; ++c) {
-            if (!mbar_wait(&sh.full[s], ((fpar >> s) & 1u) ^ wrap, errp)) ok = false;
-            tc_fence_after();
-            unsigned char *Bh = B0 + s * 2 * bop, *Bl = Bh + 128;
-            const int rowbase = FORCE ? 0 : c * kRC;
-            const int N = NP - rowbase;
-            const uint64_t dah = sdesc(smem_u32(Ph) + (c * kRC / 8) * 128, 128, sboP);
-            const uint64_t dal = sdesc(smem_u32(Pl) + (c * kRC / 8) * 128, 128, sboP);
-            for (int n0 = 0; n0 < N; n0 += 256) {
-              const int nn = min(256, N - n0);
-              const uint32_t id = idesc_f16(128, nn);
-              const uint64_t dbh = sdesc(smem_u32(Bh) + (n0 >> 3) * 512, 256, 512);
-              const uint64_t dbl = sdesc(smem_u32(Bl) + (n0 >> 3) * 512, 256, 512);
-              const uint32_t dm = tmem + rowbase + n0, dc = tmem + corr_base + rowbase + n0;
-              mma_f16(dm, dah, dbh, id, c > 0 ? 1u : 0u);
-              if (split3) {
-                mma_f16(dc, dah, dbl, id, (c > 0 || corr_base == 0) ? 1u : 0u);
-                mma_f16(dc, dal, dbh, id, 1u);
-                if (fixp) mma_f16(dc, dal, dbl, id, 1u);
-              }
-            }
-            mma_commit(&sh.done[c]);
-            if (++s == (uint32_t)nst) {
-              s = 0;
-              wrap ^= 1u;
-            }
-          }
-        }
-        __syncwarp();
-      } else if (prefetch_index(warp) >= 0) {
-        // prefetch warps, later chunks: chunk k (k mod kPrefetchWarps = the warp's prefetch index),
-        // its bulk copies issued once chunk k - nst's MMAs are done (the stage is free)
-        unsigned *errp = S.err;
-        const int li = prefetch_index(warp);
-        for (int k = nst + ((li - nst) % kPrefetchWarps + kPrefetchWarps) % kPrefetchWarps; k < nch;
-             k += kPrefetchWarps) {
-          if (!mbar_wait(&sh.done[k - nst], (dpar >> (k - nst)) & 1u, errp)) ok = false;
-          issue_copies(S, k, k % nst, NP, na);
-        }
-      } else if (!FORCE) {
-        // density epilogue groups (each covers the 128 lanes) drain finished chunks round robin
-        // (compensated float32 sums per point and group)
-        const int grp = epi_group(warp);
-        float rhi = 0.f, rlo = 0.f;
-        for (int c = grp; c < nch; c += kEpiGroups) {
-          if (!mbar_wait(&sh.done[c], (dpar >> c) & 1u, S.err)) ok = false;
-          tc_fence_after();
-          // chunk c's columns are final: rho += P_k Y_k
-          const int k0 = c * kRC;
-          float y[16], yc[16];
-          tmem_ld16(tmem + lane_base + k0, y);
-          if (split3 && corr_base) {
-            tmem_ld16(tmem + lane_base + corr_base + k0, yc);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) y[i] += yc[i];
-          }
-          float part = 0.f;
-#pragma unroll
-          for (int hseg = 0; hseg < 2; ++hseg) {
-            const uint32_t off = (p >> 3) * sboP + ((k0 >> 3) + hseg) * 128 + (p & 7) * 16;
-            const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + off), wl = *reinterpret_cast<const uint4 *>(Pl + off);
-            const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
-              const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
-              part += (hf.x + lf.x) * y[hseg * 8 + 2 * e] + (hf.y + lf.y) * y[hseg * 8 + 2 * e + 1];
-            }
-          }
-          float sum, err;
-          two_sum(rhi, part, sum, err);
-          rhi = sum;
-          rlo += err;
-        }
-        if (grp > 0) {
-          sh.rpart[grp][p] = rhi;
-          sh.rpartl[grp][p] = rlo;
-        }
-        epi_barrier();
-        if (grp == 0) {
-          for (int g2 = 1; g2 < kEpiGroups; ++g2) {
-            float sum, err;
-            two_sum(rhi, sh.rpart[g2][p], sum, err);
-            rhi = sum;
-            rlo += err + sh.rpartl[g2][p];
-          }
-          if (valid && S.rho)
-            S.rho[gidx] = ((double)rhi + (double)rlo) * (2.0 / ((double)Sphi * (double)Sphi * (double)SD));
-        }
-      }
-      // all MMAs of the brick are complete once the last chunk's barrier has flipped (in order)
-      if (!mbar_wait(&sh.done[nch - 1], (dpar >> (nch - 1)) & 1u, S.err)) ok = false;
-      tc_fence_after();
-      for (int st = 0; st < nst && st < nch; ++st)  // stage st served chunks st, st + nst, ...
-        if ((((nch - 1 - st) / nst) & 1) == 0) fpar ^= 1u << st;
-      dpar ^= (nch >= 32) ? 0xffffffffu : ((1u << nch) - 1u);
-      if (FORCE) {
-        // full Y: per atom, rho and force from recomputed phi and grad phi (unscaled float32)
-        const float2 *tab = S.tab, *tabi = S.tabi;
-        const float inv = 1.f / (Sphi * SD * (fixp ? sh.rsc[p] : 1.f));
-        const float wv = (valid && S.V) ? sh.wv[p] : 0.f;
-        float rp = 0.f;
-        for (int a = q; a < na; a += 4) {
-          const int pc = sh.s_pcol[a], po = sh.s_po[a];
-          // the atom's own columns only (an 8-column atom may end the accumulator: a 16-column
-          // load there would reach past the tensor-memory allocation)
-          float y[GINT_MAX_ORB_ATOM], yc[16];
-          for (int h = 0; h < po; h += 16) {
-            if (po - h >= 16) {
-              tmem_ld16(tmem + lane_base + pc + h, y + h);
-              if (split3 && corr_base) {
-                tmem_ld16(tmem + lane_base + corr_base + pc + h, yc);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) y[h + i] += yc[i];
-              }
-            } else {
-              tmem_ld8(tmem + lane_base + pc + h, y + h);
-              if (split3 && corr_base) {
-                tmem_ld8(tmem + lane_base + corr_base + pc + h, yc);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) y[h + i] += yc[i];
-              }
-            }
-          }
-          for (int i = 0; i < po; ++i) y[i] *= inv;
-          float fx = 0.f, fy = 0.f, fz = 0.f;
-          switch (g.sp[sh.s_sp[a]].shape) {
-#define CASE_F(ns, np_, nd)                                                                          \
-  case GINT_SHAPE(ns, np_, nd):                                                                    \
-    job_F<ns, np_, nd, (ns + 3 * np_ + 5 * nd + 7) / 8 * 8>(g, tabi, S.dtabi, sh, a, p, valid, y, rp, fx, fy, fz); \
-    break;
-            GINT_FOR_SHAPES(CASE_F)
-#undef CASE_F
-            default:
-              job_F_generic(g, tab, S.dtab, sh, a, p, valid, y, rp, fx, fy, fz);
-          }
-          fx *= 2.f * wv;
-          fy *= 2.f * wv;
-          fz *= 2.f * wv;
-          for (int o = 16; o > 0; o >>= 1) {
-            fx += __shfl_xor_sync(0xffffffffu, fx, o);
-            fy += __shfl_xor_sync(0xffffffffu, fy, o);
-            fz += __shfl_xor_sync(0xffffffffu, fz, o);
-          }
-          if (lane == 0) {
-            atomicAdd(&sh.fpart[a][0], (double)fx);
-            atomicAdd(&sh.fpart[a][1], (double)fy);
-            atomicAdd(&sh.fpart[a][2], (double)fz);
-          }
-        }
-        sh.rpart[q][p] = rp;
-        __syncthreads();
-        if (q == 0 && valid && S.rho)
-          S.rho[gidx] =
-              (double)sh.rpart[0][p] + (double)sh.rpart[1][p] + (double)sh.rpart[2][p] + (double)sh.rpart[3][p];
-        if (S.F)
-          for (int a = t; a < na; a += kT) {
-            const int I = sh.s_atom[a];
-            atomicAdd(S.F + 3 * I + 0, sh.fpart[a][0]);
-            atomicAdd(S.F + 3 * I + 1, sh.fpart[a][1]);
-            atomicAdd(S.F + 3 * I + 2, sh.fpart[a][2]);
-          }
-      }
-      }  // do_rho
-      if (do_h) {
-        // ================================================================ local H from P
-        // H_mu,nu = sum_g (w V_g P_g,mu) P_g,nu: K = grid points in blocks of hkb, both operands
-        // MN-major views of [point][orbital] buffers (P itself, and W P built per block in one of
-        // two halves of the stage region, ping-pong with the MMAs of the previous block).
-        tc_fence_before();  // the density part's tensor-memory reads are finished
-        __syncthreads();
-        tc_fence_after();
-        const float SA = sh.sc[2];
-        const float out_scale = 1.f / (Sphi * SA);
-        const float wscale = SA / Sphi;
-        const int hkb = nst >= 4 ? 32 : 16, ng = NP >> 3;  // two halves of hkb x NP (hi, lo) fit the stages
-        const uint32_t whalf = (uint32_t)hkb * 4u * (uint32_t)NP;  // hi and lo of one block
-        const int ntile = (NP + 127) / 128;
-        int tb[3] = {0, 0, 0}, T = 0;
-        for (int m = 0; m < ntile; ++m) {
-          tb[m] = T;
-          T += NP - 128 * m;
-        }
-        const uint32_t corr_base = (2 * T <= 512) ? (uint32_t)T : 0u;
-        for (int j = 0; j < 128 / hkb; ++j, ++GH) {
-          const int hh = GH & 1;
-          unsigned char *Wh = B0 + hh * whalf, *Wl = Wh + whalf / 2;
-          // the MMAs that last read this half (two blocks ago) are complete
-          if (GH >= 2 && !mbar_wait(&sh.hdone[hh], ((GH - 2) >> 1) & 1, S.err)) ok = false;
-          const int p0 = j * hkb;
-          // warps 1-15 build the block while thread 0 may still be issuing the previous block's MMAs.
-          // Unit u = (point octet, orbital group, point in octet) with the point fastest: eight
-          // consecutive threads touch one 128-byte core-matrix row block (no bank conflicts).
-          for (int u = t - 32; u >= 0 && u < hkb * ng; u += kT - 32) {
-            const int v8 = u >> 3, po8 = v8 / ng, gg = v8 - po8 * ng;
-            const int pl = po8 * 8 + (u & 7), pt = p0 + pl;
-            const uint32_t so = (pt >> 3) * sboP + gg * 128 + (pt & 7) * 16;
-            const uint32_t dso = (pl >> 3) * sboP + gg * 128 + (pl & 7) * 16;
-            const float f = fixp ? sh.wv[pt] * wscale / (sh.rsc[pt] * sh.rsc[pt]) : sh.wv[pt] * wscale;
-            const uint4 wh = *reinterpret_cast<const uint4 *>(Ph + so), wl = *reinterpret_cast<const uint4 *>(Pl + so);
-            const uint32_t hw[4] = {wh.x, wh.y, wh.z, wh.w}, lw[4] = {wl.x, wl.y, wl.z, wl.w};
-            uint32_t oh[4], ol[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[e]));
-              const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[e]));
-              split_h2((hf.x + lf.x) * f, (hf.y + lf.y) * f, oh[e], ol[e]);
-            }
-            *reinterpret_cast<uint4 *>(Wh + dso) = make_uint4(oh[0], oh[1], oh[2], oh[3]);
-            *reinterpret_cast<uint4 *>(Wl + dso) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
-          }
-          fence_async_smem();
-          __syncthreads();
-          if (t == 0 && NP <= 256 && split3) {
-            // common case, straight-line issue: at most two 128-row tiles of one N <= 256 each; the
-            // descriptors' start-address field advances by 2 sboP / 16 per K step of 16 points, and by
-            // 2048 / 16 from the first to the second tile (orbitals 128-255, rows of A and columns of B)
-            tc_fence_after();
-            const uint64_t wh0 = sdesc(smem_u32(Wh), sboP, 128), wl0 = sdesc(smem_u32(Wl), sboP, 128);
-            const uint32_t pofs = (uint32_t)(p0 >> 3) * sboP;
-            const uint64_t ph0 = sdesc(smem_u32(Ph) + pofs, sboP, 128), pl0 = sdesc(smem_u32(Pl) + pofs, sboP, 128);
-            const uint32_t kstep = (2u * sboP) >> 4;
-            const uint32_t id0 = idesc_f16_mn(128, NP), id1 = idesc_f16_mn(128, NP > 128 ? NP - 128 : 16);
-            const uint32_t m0 = tmem + (uint32_t)tb[0], m1 = tmem + (uint32_t)tb[1];
-            const uint32_t c0 = m0 + corr_base, c1 = m1 + corr_base;
-            for (int ks = 0; ks < hkb / 16; ++ks) {
-              const uint64_t ko = (uint64_t)ks * kstep;
-              const bool first = (j == 0 && ks == 0);
-              const uint32_t am = first ? 0u : 1u, ac = (first && corr_base) ? 0u : 1u;
-              mma_f16(m0, wh0 + ko, ph0 + ko, id0, am);
-              mma_f16(c0, wh0 + ko, pl0 + ko, id0, ac);
-              mma_f16(c0, wl0 + ko, ph0 + ko, id0, 1u);
-              if (NP > 128) {
-                mma_f16(m1, wh0 + ko + 128u, ph0 + ko + 128u, id1, am);
-                mma_f16(c1, wh0 + ko + 128u, pl0 + ko + 128u, id1, ac);
-                mma_f16(c1, wl0 + ko + 128u, ph0 + ko + 128u, id1, 1u);
-              }
-            }
-            mma_commit(&sh.hdone[hh]);
-          } else if (t == 0) {
-            tc_fence_after();
-            for (int ks = 0; ks < hkb / 16; ++ks) {
-              const uint32_t kw = (uint32_t)(2 * ks) * sboP, kp = (uint32_t)((p0 >> 3) + 2 * ks) * sboP;
-              for (int m = 0; m < ntile; ++m) {
-                const uint64_t dah = sdesc(smem_u32(Wh) + kw + m * 16 * 128, sboP, 128);
-                const uint64_t dal = sdesc(smem_u32(Wl) + kw + m * 16 * 128, sboP, 128);
-                const int N = NP - 128 * m;
-                for (int n0 = 0; n0 < N; n0 += 256) {
-                  const int nn = min(256, N - n0);
-                  const uint32_t id = idesc_f16_mn(128, nn);
-                  const uint32_t col = (uint32_t)(128 * m + n0);
-                  const uint64_t dbh = sdesc(smem_u32(Ph) + kp + (col >> 3) * 128, sboP, 128);
-                  const uint64_t dbl = sdesc(smem_u32(Pl) + kp + (col >> 3) * 128, sboP, 128);
-                  const uint32_t dm = tmem + tb[m] + n0, dc = tmem + corr_base + tb[m] + n0;
-                  const bool first = (j == 0 && ks == 0);
-                  mma_f16(dm, dah, dbh, id, first ? 0u : 1u);
-                  if (split3) {
-                    mma_f16(dc, dah, dbl, id, (first && corr_base) ? 0u : 1u);
-                    mma_f16(dc, dal, dbh, id, 1u);
-                  }
-                }
-              }
-            }
-            mma_commit(&sh.hdone[hh]);
-          }
-        }
-        {
-          const uint32_t Gp = GH - 1;
-          if (!mbar_wait(&sh.hdone[Gp & 1], (Gp >> 1) & 1, S.err)) ok = false;
-          tc_fence_after();
-        }
-      // epilogue: upper slot-pair tiles -> scratch (float32, unscaled), column-major: tile (a, c),
-      // a <= c, holds norb(c) columns of norb(a) rows at rowst(a) + norb(a) (cumno(c) - cumno(a));
-      // element (i, j) at j norb(a) + i (the row-major norb(c) x norb(a) block (c, a) of the
-      // symmetric brick H).  Only the orbitals themselves are stored (no padding rows or columns),
-      // so the brick's tiles are one dense range of rowst(na) values (padded to 16 bytes).  The range
-      // is assembled in shared memory (the orbital tile and the stage region are free once the MMAs
-      // are done: consecutive rows of a column land in consecutive words, no bank conflicts) and
-      // leaves in one bulk copy that overlaps the next item's set-up; a range larger than the
-      // dynamic shared memory is stored directly.
-      {
-        const int ln = t & 127, qq = t >> 7;
-        const uint32_t lane_base = (uint32_t)((ln >> 5) * 32) << 16;
-        const long long base = S.hs_brick_off[b];
-        const int total = sh.s_rowst[na], padded = (total + 3) & ~3;
-        const bool staged = padded * 4 <= B.dsmem;
-        float *const stg = staged ? reinterpret_cast<float *>(smem) : S.hs + base;
-        for (int m = 0; m < ntile; ++m) {
-          const int mu = 128 * m + ln;
-          const int as = mu < NP ? sh.col2slot[mu] : kNoSlot;
-          const int il = as != kNoSlot ? mu - sh.s_pcol[as] : 0;
-          const int no_a = as != kNoSlot ? sh.s_no[as] : 0;
-          const bool rowok = as != kNoSlot && il < no_a;
-          const int cum_a = rowok ? sh.s_cumno[as] : 0;
-          float *rowp = stg + (rowok ? sh.s_rowst[as] : 0) + il;
-          const int N = NP - 128 * m;
-          for (int gcol = qq; gcol < N / 16; gcol += 4) {
-            float y[16], yc[16];
-            tmem_ld16(tmem + lane_base + tb[m] + gcol * 16, y);
-            if (split3 && corr_base) {
-              tmem_ld16(tmem + lane_base + corr_base + tb[m] + gcol * 16, yc);
-#pragma unroll
-              for (int i = 0; i < 16; ++i) y[i] += yc[i];
-            }
-            if (!rowok) continue;
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-              const int nu = 128 * m + gcol * 16 + 8 * hh;
-              const int cs = sh.col2slot[nu];
-              if (cs == kNoSlot || cs < as) continue;
-              const int j0 = nu - sh.s_pcol[cs], nj = min(8, sh.s_no[cs] - j0);
-              float *dst = rowp + no_a * (sh.s_cumno[cs] - cum_a + j0);
-#pragma unroll
-              for (int i = 0; i < 8; ++i)
-                if (i < nj) dst[i * no_a] = y[8 * hh + i] * out_scale;
-            }
-          }
-        }
-        for (int k = total + t; k < padded; k += kT) stg[k] = 0.f;
-        if (staged) {
-          fence_async_smem();  // the generic writes above before the bulk copy reads them
-          __syncthreads();
-          if (t == 0 && padded > 0) bulk_s2g(S.hs + base, stg, (uint32_t)padded * 4u);
-        }
-      }
-      }  // do_h
-    }
+    ItemCtx cx{fpar, dpar, GH, ok};
+    brick_body<FORCE>(g, S, b, do_rho, do_h, split3, B.dsmem, zero, tmem, sh, smem, cx);
+    fpar = cx.fpar;
+    dpar = cx.dpar;
+    GH = cx.GH;
+    ok = cx.ok;
     tc_fence_before();
     if (!ok) sh.abort = 1;
   }
@@ -1395,30 +1415,25 @@ struct GRed {
 // of every tile value would cost more than the brick pass itself on this GPU (float64 runs at about
 // 1/64 of the float32 rate), so the float64 step is the final combination only.
 constexpr int kRedLanes = 64, kRedGroups = 4, kRedThreads = kRedLanes * kRedGroups, kRedE = 3, kRedB = 8;
-__global__ void __launch_bounds__(kRedThreads, 4) k_h_reduce(const __grid_constant__ GTabs g, const __grid_constant__ GRed R) {
-  __shared__ float part_hi[kRedGroups - 1][kRedE][kRedLanes], part_lo[kRedGroups - 1][kRedE][kRedLanes];
-  const long long gu = blockIdx.x;
-  int lo = 0, hi = R.nsys - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (R.start[mid] <= gu)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  const GRedSys &S = R.sys[lo];
-  const int u = (int)(gu - R.start[lo]);
+__device__ __forceinline__ void bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+// Upper pair u of system S by NG groups of kRedLanes threads (tid in [0, NG kRedLanes)); part_hi and
+// part_lo hold (NG - 1) kRedE kRedLanes floats each; the groups synchronise on barrier `bar`.
+template <int NG>
+__device__ __forceinline__ void reduce_pair(const GTabs &g, const GRedSys &S, int u, int tid, float *part_hi,
+                                            float *part_lo, int bar) {
   const int p = S.hu_pair[u];
   const int I = S.pair_I[p], J = S.pair_J[p];
   const int nI = g.sp[S.species[I]].norb, nJ = g.sp[S.species[J]].norb;
-  const int ln = threadIdx.x % kRedLanes, grp = threadIdx.x / kRedLanes;
+  const int ln = tid % kRedLanes, grp = tid / kRedLanes;
   const long long kk0 = S.hu_off[u], kk1 = S.hu_off[u + 1];
-  const long long per = (kk1 - kk0 + kRedGroups - 1) / kRedGroups;
+  const long long per = (kk1 - kk0 + NG - 1) / NG;
   const long long k0 = min(kk1, kk0 + grp * per), k1 = min(kk1, k0 + per);
   const float *__restrict__ hs = S.hs;
   const long long *__restrict__ src = S.hu_src;
   const int ne = nI * nJ;
-  for (int base = 0; base < ne; base += kRedLanes * kRedE) {  // block-uniform trip count
+  for (int base = 0; base < ne; base += kRedLanes * kRedE) {  // uniform trip count within the groups
     int e[kRedE];
     bool act[kRedE];
     float ah[kRedE], al[kRedE];
@@ -1444,7 +1459,7 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_h_reduce(const __grid_consta
 #pragma unroll
       for (int jj = 0; jj < kRedB; ++jj)
 #pragma unroll
-        for (int q = 0; q < kRedE; ++q) v[jj][q] = __ldg(hs + o[jj] + e[q]);
+        for (int q = 0; q < kRedE; ++q) v[jj][q] = __ldcg(hs + o[jj] + e[q]);  // written by this or another launch
 #pragma unroll
       for (int jj = 0; jj < kRedB; ++jj)
 #pragma unroll
@@ -1453,29 +1468,44 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_h_reduce(const __grid_consta
     for (; k < k1; ++k) {
       const long long o = __ldg(src + k);
 #pragma unroll
-      for (int q = 0; q < kRedE; ++q) add(q, __ldg(hs + o + e[q]));
+      for (int q = 0; q < kRedE; ++q) add(q, __ldcg(hs + o + e[q]));
     }
     if (grp > 0) {
 #pragma unroll
       for (int q = 0; q < kRedE; ++q) {
-        part_hi[grp - 1][q][ln] = ah[q];
-        part_lo[grp - 1][q][ln] = al[q];
+        part_hi[((grp - 1) * kRedE + q) * kRedLanes + ln] = ah[q];
+        part_lo[((grp - 1) * kRedE + q) * kRedLanes + ln] = al[q];
       }
     }
-    __syncthreads();
+    bar_sync(bar, NG * kRedLanes);
     if (grp == 0) {
 #pragma unroll
       for (int q = 0; q < kRedE; ++q) {
         if (!act[q]) continue;
         double acc = (double)ah[q] + (double)al[q];
-        for (int g2 = 0; g2 < kRedGroups - 1; ++g2) acc += (double)part_hi[g2][q][ln] + (double)part_lo[g2][q][ln];
+        for (int g2 = 0; g2 < NG - 1; ++g2)
+          acc += (double)part_hi[(g2 * kRedE + q) * kRedLanes + ln] + (double)part_lo[(g2 * kRedE + q) * kRedLanes + ln];
         const int j = e[q] / nI, i = e[q] - j * nI;
         S.H[S.pair_off[p] + (long long)i * nJ + j] = acc;
         if (I != J) S.H[S.pair_off[S.pair_T[p]] + (long long)j * nI + i] = acc;
       }
     }
-    __syncthreads();
+    bar_sync(bar, NG * kRedLanes);
   }
+}
+
+__global__ void __launch_bounds__(kRedThreads, 4) k_h_reduce(const __grid_constant__ GTabs g, const __grid_constant__ GRed R) {
+  __shared__ float part_hi[(kRedGroups - 1) * kRedE * kRedLanes], part_lo[(kRedGroups - 1) * kRedE * kRedLanes];
+  const long long gu = blockIdx.x;
+  int lo = 0, hi = R.nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (R.start[mid] <= gu)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  reduce_pair<kRedGroups>(g, R.sys[lo], (int)(gu - R.start[lo]), threadIdx.x, part_hi, part_lo, 0);
 }
 
 // ------------------------------------------------------------------------------ batched preparation
@@ -1496,17 +1526,17 @@ struct GPrep {
   GPrepSys sys[kMaxBatch];
 };
 
-// blockIdx.y = system: max |D|, max |V| (float32, rounded), zero F; also resets the work counter.
-__global__ void k_prep(const __grid_constant__ GPrep P) {
-  const GPrepSys &S = P.sys[blockIdx.y];
-  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+// Elements [i0, i1) of the system's D blocks, grid and force arrays, by nt threads (this one t):
+// max |D| and max |V| (float32, rounded; atomicMax into S.mx), F zeroed.
+__device__ __forceinline__ void prep_range(const GPrepSys &S, long long i0, long long i1, long long t, long long nt) {
   float mD = 0.f, mV = 0.f;
+  // inputs read through L2 (__ldcg): a resident launch may see them rewritten between its jobs
   if (S.D)
-    for (long long i = i0; i < S.nblock; i += stride) mD = fmaxf(mD, (float)fabs(S.D[i]));
+    for (long long i = i0 + t; i < min(i1, S.nblock); i += nt) mD = fmaxf(mD, (float)fabs(__ldcg(S.D + i)));
   if (S.V)
-    for (long long i = i0; i < S.ngrid; i += stride) mV = fmaxf(mV, (float)fabs(S.V[i]));
+    for (long long i = i0 + t; i < min(i1, S.ngrid); i += nt) mV = fmaxf(mV, (float)fabs(__ldcg(S.V + i)));
   if (S.F)
-    for (long long i = i0; i < 3 * S.natoms; i += stride) S.F[i] = 0.0;
+    for (long long i = i0 + t; i < min(i1, 3 * S.natoms); i += nt) S.F[i] = 0.0;
   for (int o = 16; o > 0; o >>= 1) {
     mD = fmaxf(mD, __shfl_xor_sync(0xffffffffu, mD, o));
     mV = fmaxf(mV, __shfl_xor_sync(0xffffffffu, mV, o));
@@ -1515,6 +1545,12 @@ __global__ void k_prep(const __grid_constant__ GPrep P) {
     if (mD > 0.f) atomicMax(S.mx, __float_as_uint(mD));
     if (mV > 0.f) atomicMax(S.mx + 1, __float_as_uint(mV));
   }
+}
+
+// blockIdx.y = system: prep_range over the whole arrays; also resets the work counter.
+__global__ void k_prep(const __grid_constant__ GPrep P) {
+  prep_range(P.sys[blockIdx.y], 0, 0x7fffffffffffffffLL, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+             (long long)gridDim.x * blockDim.x);
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *P.work = 0;
 }
 
@@ -1523,19 +1559,21 @@ __device__ double pow2_scale(double lim, double m) {
   return exp2(floor(log2(lim / m)));
 }
 
-// Thread s: power-of-two scales of system s ([0] orbitals, [1] D, [2] w V orbitals), with the
-// largest scaled magnitudes below 2^15 (float16 max 65504; a zero input gets 2^20); then clears
-// the maxima for the next call.
-__global__ void k_prep_scales(const __grid_constant__ GPrep P) {
-  const int s = threadIdx.x;
-  if (s >= P.nsys) return;
-  const GPrepSys &S = P.sys[s];
+// Power-of-two scales of a system ([0] orbitals, [1] D, [2] w V orbitals), with the largest scaled
+// magnitudes below 2^15 (float16 max 65504; a zero input gets 2^20); then clears the maxima for the
+// next call.  One thread.
+__device__ __forceinline__ void prep_scales(const GPrepSys &S) {
   const double pb = 4.0 * S.phi_bound;
   S.scales[0] = (float)pow2_scale(30000.0, pb);
   S.scales[1] = (float)pow2_scale(30000.0, (double)__uint_as_float(S.mx[0]));
   S.scales[2] = (float)pow2_scale(30000.0, pb * S.w * (double)__uint_as_float(S.mx[1]));
   S.mx[0] = 0u;
   S.mx[1] = 0u;
+}
+
+// Thread s: the scales of system s.
+__global__ void k_prep_scales(const __grid_constant__ GPrep P) {
+  if (threadIdx.x < P.nsys) prep_scales(P.sys[threadIdx.x]);
 }
 
 struct GTileSys {
@@ -1553,33 +1591,21 @@ struct GTile {
   GTileSys sys[kMaxBatch];
 };
 
-// One CTA per pair of any system: D blocks (float64, row-major norb(I) x norb(J)) -> scaled
-// float16 (hi, lo) tiles of roundup(norb(I), 8) x porb(J) in core-matrix order
-// [row group][K group][8][8], plus the same tiles halved.
-__global__ void k_build_tiles(const __grid_constant__ GTabs g, const __grid_constant__ GTile TB) {
-  const long long gp = blockIdx.x;
-  int lo = 0, hi = TB.nsys - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (TB.start[mid] <= gp)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  const GTileSys &S = TB.sys[lo];
-  const int p = (int)(gp - TB.start[lo]);
+// Pair p of a system by nt threads (this one t): D block (float64, row-major norb(I) x norb(J)) ->
+// scaled float16 (hi, lo) tile of roundup(norb(I), 8) x porb(J) in core-matrix order
+// [row group][K group][8][8], plus the same tile halved (floating split), or the fixed-point split.
+__device__ __forceinline__ void build_tile(const GTabs &g, const GTileSys &S, int p, bool fixed, int t, int nt) {
   const int I = S.pair_I[p], J = S.pair_J[p];
   const int nI = g.sp[S.species[I]].norb, nJ = g.sp[S.species[J]].norb, pJ = g.sp[S.species[J]].porb;
   const int rI = (nI + 7) & ~7, sJ = pJ >> 3;
-  const bool fixed = TB.fixed != 0;
-  const double sc = (double)S.scales[1] * (fixed ? (double)kFxScaleD : 1.0);
+  const double sc = (double)__ldcg(S.scales + 1) * (fixed ? (double)kFxScaleD : 1.0);
   const long long o = S.pair_off[p], to = S.tile_off[p];
-  for (int e = threadIdx.x; e < rI * pJ; e += blockDim.x) {
+  for (int e = t; e < rI * pJ; e += nt) {
     const int cm = e >> 6, w = e & 63;
     const int i = (cm / sJ) * 8 + (w >> 3), j = (cm % sJ) * 8 + (w & 7);
     const long long q = 2 * to + (long long)cm * 128 + w;  // hi element; lo 64 halves later
     if (i < nI && j < nJ) {
-      const double x = S.D[o + (long long)i * nJ + j] * sc;
+      const double x = __ldcg(S.D + o + (long long)i * nJ + j) * sc;
       if (fixed) {  // hi: the nearest integer (exact in float16: |x| < 2048); the halved tiles are unused
         const double hx = rint(x);
         S.Dhl[q] = __float2half_rn((float)hx);
@@ -1596,6 +1622,20 @@ __global__ void k_build_tiles(const __grid_constant__ GTabs g, const __grid_cons
       S.Dhl[q] = S.Dhl[q + 64] = S.Dhl2[q] = S.Dhl2[q + 64] = __float2half(0.f);
     }
   }
+}
+
+// One CTA per pair of any system.
+__global__ void k_build_tiles(const __grid_constant__ GTabs g, const __grid_constant__ GTile TB) {
+  const long long gp = blockIdx.x;
+  int lo = 0, hi = TB.nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (TB.start[mid] <= gp)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  build_tile(g, TB.sys[lo], (int)(gp - TB.start[lo]), TB.fixed != 0, threadIdx.x, blockDim.x);
 }
 
 // One CTA per brick: the brick's metadata exactly as the brick kernel's slow path builds it,
@@ -1649,6 +1689,231 @@ __global__ void __launch_bounds__(128) k_build_plans(const __grid_constant__ GTa
     }
     w[i] = v;
   }
+}
+
+// ------------------------------------------------------------------------------ resident serving kernel
+// Continuous batching: one resident launch drains a device work queue to which the host appends jobs
+// (one task: the density / force and local-H passes of one system) while it runs.  A job's items, in
+// the global item order: kServePrep max-reduction chunks, one scales item, tile items (kServeTilePairs
+// pairs each), one item per brick, reduction items (kServeRedPairs upper pairs each).  A CTA claims
+// items one at a time, in order, by a compare-and-swap on the claim counter that never passes the
+// published count; an item waits (bounded) for the items of its job it depends on (scales after the
+// chunks, tiles after the scales, bricks after the tiles, reductions after the bricks), which were
+// all claimed earlier, so the wait always ends.  The last item of a job to complete writes the job's
+// completion word into host-mapped memory.  A CTA with nothing to claim for idle_ns (or on the stop
+// flag, or when a wait gave up anywhere) leaves; the host relaunches when it has unclaimed work.
+constexpr int kServeRing = 64;                  // jobs in flight at most (descriptor ring)
+constexpr long long kServePrep = 1LL << 20;     // elements per max-reduction item
+constexpr int kServeTilePairs = 32;             // pairs per tile item (four at a time, 128 threads each)
+constexpr int kServeRedPairs = 2;               // upper pairs per reduction item (256 threads each)
+constexpr long long kServeMaxJobs = 1LL << 20;  // jobs over a server's lifetime (completion-order table)
+
+struct GJob {
+  GSys sys;
+  GPrepSys prep;
+  GTileSys tile;
+  GRedSys red;
+  int npairs, nupper, fixed, pad;
+  long long nbricks;
+  long long n_prep, n_tile, n_red;  // items of each kind (plus one scales item)
+  long long item0, nitems;          // first item and item count of the job
+  unsigned long long seq;
+};
+struct GJobState {  // completed items of the job per kind, and in total (zeroed at publication)
+  int prep, scales, tiles, bricks, red, all, pad[2];
+};
+struct GServeCtl {
+  unsigned long long head;       // claimed items
+  unsigned long long tail;       // published items (written by the host)
+  unsigned long long first_seq;  // claims never go to jobs before this one (cursor start, host hint)
+  int stop;                      // host: leave as soon as idle
+  unsigned err;                  // GINT_ERRBIT_* of any item; every CTA leaves
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ long long ld_acquire_s64(const long long *p) {
+  long long v;
+  asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_acquire_s32(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// Bounded wait (thread 0) until *cnt >= target; false after kWaitNs (timeout bit in *err).
+__device__ __forceinline__ bool wait_count(const int *cnt, long long target, unsigned *err) {
+  if (ld_acquire_s32(cnt) >= target) return true;
+  const long long t0 = globaltimer();
+  while (ld_acquire_s32(cnt) < target) {
+    if (globaltimer() - t0 > kWaitNs) {
+      atomicOr(err, GINT_ERRBIT_TIMEOUT);
+      return false;
+    }
+    __nanosleep(256);
+  }
+  return true;
+}
+
+template <bool FORCE>
+__global__ void __launch_bounds__(kT, 1)
+    k_serve(const __grid_constant__ GTabs g, GServeCtl *ctl, const GJob *__restrict__ jobs, GJobState *st,
+            const long long *__restrict__ job_end, volatile unsigned long long *done, const __half *__restrict__ zero,
+            int split3, int dsmem, long long idle_ns) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ BrickSh sh;
+  __shared__ GJob sj;    // the item's job (copied through L2 for every item: a ring slot is rewritten
+                         // by the host for later jobs while this launch runs)
+  __shared__ long long s_item, s_seq;
+  const int t = threadIdx.x, warp = t >> 5;
+  if (t == 0) {
+    for (int s2 = 0; s2 < kMaxStages; ++s2) mbar_init(&sh.full[s2], 1);
+    for (int c = 0; c < kMaxChunks; ++c) mbar_init(&sh.done[c], 1);
+    mbar_init(&sh.hdone[0], 1);
+    mbar_init(&sh.hdone[1], 1);
+    mbar_init(&sh.plan_bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&sh.tmem, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sh.tmem;
+  ItemCtx cx{0u, 0u, 0u, true};
+  uint32_t pphase = 0;
+  unsigned long long cursor = 0, cur_sys = ~0ull;
+  if (t == 0) cursor = ld_acquire_u64(&ctl->first_seq);
+  for (;;) {
+    if (t == 0) {
+      // claim the next item (never past the published count), or leave
+      long long item = -1;
+      const long long t0 = globaltimer();
+      for (;;) {
+        if (*(volatile unsigned *)&ctl->err) break;
+        const unsigned long long h = *(volatile unsigned long long *)&ctl->head;
+        const unsigned long long tl = ld_acquire_u64(&ctl->tail);
+        if (h < tl) {
+          if (atomicCAS(&ctl->head, h, h + 1) == h) {
+            item = (long long)h;
+            break;
+          }
+          continue;
+        }
+        if (*(volatile int *)&ctl->stop || globaltimer() - t0 > idle_ns) break;
+        __nanosleep(1000);
+      }
+      if (item >= 0)  // job_end of every published job is written before the tail
+        while (ld_acquire_s64(job_end + cursor) <= item) ++cursor;
+      s_item = item;
+      s_seq = (long long)cursor;
+      bulk_wait_read();  // a previous brick item's tiles have left shared memory
+    }
+    __syncthreads();
+    const long long item = s_item;
+    if (item < 0) break;
+    const unsigned long long seq = (unsigned long long)s_seq;
+    {
+      const int *src = reinterpret_cast<const int *>(jobs + seq % kServeRing);
+      int *dst = reinterpret_cast<int *>(&sj);
+      for (int k = t; k < (int)(sizeof(GJob) / sizeof(int)); k += kT) dst[k] = __ldcg(src + k);
+    }
+    __syncthreads();
+    const GJob &J = sj;
+    GJobState &JS = st[seq % kServeRing];
+    unsigned *err = &ctl->err;
+    const long long li = item - J.item0;
+    const long long b0 = J.n_prep + 1 + J.n_tile, r0 = b0 + J.nbricks;
+    int *counter;
+    if (li < J.n_prep) {  // max-reduction chunk
+      prep_range(J.prep, li * kServePrep, (li + 1) * kServePrep, t, kT);
+      counter = &JS.prep;
+    } else if (li == J.n_prep) {  // scales
+      if (t == 0 && wait_count(&JS.prep, J.n_prep, err)) prep_scales(J.prep);
+      counter = &JS.scales;
+    } else if (li < b0) {  // D tiles
+      bool go = true;
+      if (t == 0) go = wait_count(&JS.scales, 1, err);
+      __syncthreads();
+      if (go && !*(volatile unsigned *)err) {
+        const long long p0 = (li - J.n_prep - 1) * kServeTilePairs;
+        for (long long p = p0 + (t >> 7); p < min((long long)J.npairs, p0 + kServeTilePairs); p += kT / 128)
+          build_tile(g, J.tile, (int)p, J.fixed != 0, t & 127, 128);
+      }
+      counter = &JS.tiles;
+    } else if (li < r0) {  // a brick
+      const long long b = li - b0;
+      cx.ok = true;
+      if (t == 0) wait_count(&JS.tiles, J.n_tile, err);
+      __syncthreads();
+      if (!*(volatile unsigned *)err) {  // the same decision in every thread (read after the barrier)
+        const GSys &S = sj.sys;
+        if (seq != cur_sys) {  // a new job: points and scales into shared memory
+          init_points(S.c, sh);
+          if (t == 0) {
+            sh.sc[0] = __ldcg(S.scales + 0);
+            sh.sc[1] = __ldcg(S.scales + 1);
+            sh.sc[2] = __ldcg(S.scales + 2);
+          }
+          cur_sys = seq;
+        }
+        const bool do_rho = S.do_rho != 0, do_h = S.do_h != 0;
+        if (t < 128 && S.V && (do_h || FORCE)) {
+          int gi, gj, gk;
+          sh.wv[t] = brick_point(S.c, b, t, gi, gj, gk) ? (float)(S.c.w * __ldcg(S.V + grid_index(S.c, gi, gj, gk))) : 0.f;
+        }
+        const long long o0 = S.plan_off[b], o1 = S.plan_off[b + 1];
+        const uint32_t bytes = (uint32_t)((o1 - o0) * 16);
+        if (S.plan && bytes <= 4u * kPlanWords) {
+          if (t == 0) {
+            fence_async_smem();
+            mbar_arrive_tx(&sh.plan_bar, bytes);
+            bulk_g2s(sh.planbuf, S.plan + o0, bytes, &sh.plan_bar);
+          }
+          if (!mbar_wait(&sh.plan_bar, pphase & 1u, err)) cx.ok = false;
+          ++pphase;
+          unpack_plan(sh);  // ends with a barrier
+        } else {
+          load_brick(S.c, g, S.nb, S.tile_off, b, sh);  // ends with a barrier
+        }
+        brick_body<FORCE>(g, S, b, do_rho, do_h, split3, dsmem, zero, tmem, sh, smem, cx);
+        tc_fence_before();
+      }
+      counter = &JS.bricks;
+    } else {  // H reduction: two upper pairs, one per 256 threads (named barriers 2, 3), split into parts
+      // exactly as k_h_reduce splits them, so the blocks equal those of the batched call bit for bit
+      bool go = true;
+      if (t == 0) go = wait_count(&JS.bricks, J.nbricks, err);
+      __syncthreads();
+      if (go && !*(volatile unsigned *)err) {
+        const int sg = t / kRedThreads, u = (int)((li - r0) * kServeRedPairs) + sg;
+        float *part = reinterpret_cast<float *>(smem) + sg * 2 * (kRedGroups - 1) * kRedE * kRedLanes;
+        if (u < J.nupper)
+          reduce_pair<kRedGroups>(g, J.red, u, t % kRedThreads, part, part + (kRedGroups - 1) * kRedE * kRedLanes,
+                                  2 + sg);
+      }
+      counter = &JS.red;
+    }
+    if (!cx.ok) atomicOr(err, GINT_ERRBIT_TIMEOUT);  // the next claim sees it: every CTA leaves
+    __syncthreads();
+    if (t == 0) {
+      __threadfence();  // this item's results before its count
+      atomicAdd(counter, 1);
+      if (atomicAdd(&JS.all, 1) == (int)J.nitems - 1) {
+        __threadfence_system();
+        done[seq % kServeRing] = seq + 1;  // the job's results are in device memory
+      }
+    }
+  }
+  if (t == 0) bulk_wait_all();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 // ------------------------------------------------------------------------------ orbital diagnostic
@@ -1986,6 +2251,71 @@ static_assert(sizeof(GTabs) + sizeof(GTile) <= 32764 && sizeof(GTabs) + sizeof(G
 
 // One launch group (at most kMaxBatch tasks, validated by the caller).  ev0 / ev1 (may be NULL)
 // are recorded on the stream right before / after the brick kernel.
+// Per-system descriptors of one task (density / force bricks need D, local H needs V).
+static void fill_prep(GPrepSys &ps, const gint_task &T) {
+  gint_handle *h = T.h;
+  const bool dens = T.rho || T.F, loc = T.H_blocks != nullptr;
+  ps.D = dens ? T.D_blocks : nullptr;
+  ps.nblock = h->nblock;
+  ps.V = (loc || T.F) ? T.V : nullptr;
+  ps.ngrid = h->geom.ngrid;
+  ps.F = T.F;
+  ps.natoms = h->geom.natoms;
+  ps.mx = reinterpret_cast<unsigned *>(h->scales + 4);
+  ps.scales = h->scales;
+  ps.phi_bound = h->phi_bound;
+  ps.w = h->geom.w;
+}
+static void fill_tile(GTileSys &ts, const gint_task &T) {
+  gint_handle *h = T.h;
+  ts.D = T.D_blocks;
+  ts.pair_I = h->pair_I_dev;
+  ts.pair_J = h->pair_col_dev;
+  ts.pair_off = h->pair_off_dev;
+  ts.tile_off = h->tile_off_dev;
+  ts.species = h->species_dev;
+  ts.scales = h->scales;
+  ts.Dhl = h->Dt_hl;
+  ts.Dhl2 = h->Dt_hl2;
+}
+static void fill_sys(GSys &S, const gint_task &T) {
+  gint_handle *h = T.h;
+  const bool dens = T.rho || T.F, loc = T.H_blocks != nullptr;
+  S.c = static_cast<const GCell &>(h->geom);
+  S.nb = h->nbr();
+  S.tab = h->tab32;
+  S.tabi = h->tab32i;
+  S.dtab = h->dtab32;
+  S.dtabi = h->dtab32i;
+  S.Dhl = h->Dt_hl;
+  S.Dhl2 = h->Dt_hl2;
+  S.tile_off = h->tile_off_dev;
+  S.scales = h->scales;
+  S.V = T.V;
+  S.rho = T.rho;
+  S.F = T.F;
+  S.hs_brick_off = h->hs_brick_off;
+  S.hs = h->hs;
+  S.err = h->err_word;
+  S.plan = h->plan;
+  S.plan_off = h->plan_off_dev;
+  S.do_rho = dens ? 1 : 0;
+  S.do_h = loc ? 1 : 0;
+}
+static void fill_red_gamma(GRedSys &rs, const gint_task &T) {
+  gint_handle *h = T.h;
+  rs.hs = h->hs;
+  rs.species = h->species_dev;
+  rs.H = T.H_blocks;
+  rs.hu_pair = h->hu_pair;
+  rs.hu_off = h->hu_off;
+  rs.hu_src = h->hu_src;
+  rs.pair_I = h->pair_I_dev;
+  rs.pair_J = h->pair_col_dev;
+  rs.pair_T = h->pair_T_dev;
+  rs.pair_off = h->pair_off_dev;
+}
+
 static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
   gint_handle *h0 = tk[0].h;
   const GTabs &tabs = h0->geom;
@@ -2004,52 +2334,13 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
     gint_handle *h = T.h;
     const bool dens = T.rho || T.F, loc = T.H_blocks != nullptr;
     force |= T.F != nullptr;
-    GPrepSys &ps = P.sys[i];
-    ps.D = dens ? T.D_blocks : nullptr;
-    ps.nblock = h->nblock;
-    ps.V = (loc || T.F) ? T.V : nullptr;
-    ps.ngrid = h->geom.ngrid;
-    ps.F = T.F;
-    ps.natoms = h->geom.natoms;
-    ps.mx = reinterpret_cast<unsigned *>(h->scales + 4);
-    ps.scales = h->scales;
-    ps.phi_bound = h->phi_bound;
-    ps.w = h->geom.w;
+    fill_prep(P.sys[i], T);
     if (dens && h->npairs > 0) {
       TB.start[nt] = pairs;
-      GTileSys &ts = TB.sys[nt++];
-      ts.D = T.D_blocks;
-      ts.pair_I = h->pair_I_dev;
-      ts.pair_J = h->pair_col_dev;
-      ts.pair_off = h->pair_off_dev;
-      ts.tile_off = h->tile_off_dev;
-      ts.species = h->species_dev;
-      ts.scales = h->scales;
-      ts.Dhl = h->Dt_hl;
-      ts.Dhl2 = h->Dt_hl2;
+      fill_tile(TB.sys[nt++], T);
       pairs += h->npairs;
     }
-    GSys &S = B.sys[i];
-    S.c = static_cast<const GCell &>(h->geom);
-    S.nb = h->nbr();
-    S.tab = h->tab32;
-    S.tabi = h->tab32i;
-    S.dtab = h->dtab32;
-    S.dtabi = h->dtab32i;
-    S.Dhl = h->Dt_hl;
-    S.Dhl2 = h->Dt_hl2;
-    S.tile_off = h->tile_off_dev;
-    S.scales = h->scales;
-    S.V = T.V;
-    S.rho = T.rho;
-    S.F = T.F;
-    S.hs_brick_off = h->hs_brick_off;
-    S.hs = h->hs;
-    S.err = h->err_word;
-    S.plan = h->plan;
-    S.plan_off = h->plan_off_dev;
-    S.do_rho = dens ? 1 : 0;
-    S.do_h = loc ? 1 : 0;
+    fill_sys(B.sys[i], T);
     B.start[i] = items;
     items += (dens || loc) ? h->geom.nbricks : 0;
     if (dens || loc) np = std::max(np, h->max_brick_porb);
@@ -2156,6 +2447,235 @@ int gint_tc_rho(gint_handle *h, int precision, const double *D, double *rho, con
 int gint_tc_vlocal(gint_handle *h, int precision, const double *V, double *H, cudaStream_t st) {
   const gint_task t{h, nullptr, V, nullptr, H, nullptr};
   return gint_tc_batch(&t, 1, precision, st, nullptr, nullptr);
+}
+
+
+// ------------------------------------------------------------------------------ serving API (host)
+struct gint_server {
+  int device = 0, forces = 1, split3 = 1, num_sms = 0, dsmem = 0;
+  long long idle_ns = 0;
+  GTabs tabs{};
+  bool have_tabs = false, launched = false;
+  GServeCtl *ctl = nullptr;
+  GJob *jobs = nullptr;
+  GJobState *st = nullptr;
+  long long *job_end = nullptr;
+  unsigned long long *done_h = nullptr, *done_d = nullptr;  // host-mapped completion words
+  GJob *stage = nullptr;                                     // pinned staging, one per ring slot
+  long long *stage_end = nullptr;
+  unsigned long long *stage_tail = nullptr, *stage_misc = nullptr;
+  __half *zero = nullptr;
+  cudaStream_t kstream = nullptr, cstream = nullptr;
+  cudaEvent_t kdone = nullptr, ev_in = nullptr;
+  unsigned long long next_seq = 0, next_item = 0;
+  gint_handle *slot_h[kServeRing] = {};
+  long long launches = 0;
+};
+
+static int server_free(gint_server *v) {
+  if (!v) return GINT_OK;
+  if (v->ctl) cudaFree(v->ctl);
+  if (v->jobs) cudaFree(v->jobs);
+  if (v->st) cudaFree(v->st);
+  if (v->job_end) cudaFree(v->job_end);
+  if (v->zero) cudaFree(v->zero);
+  if (v->done_h) cudaFreeHost(v->done_h);
+  if (v->stage) cudaFreeHost(v->stage);
+  if (v->stage_end) cudaFreeHost(v->stage_end);
+  if (v->stage_tail) cudaFreeHost(v->stage_tail);
+  if (v->stage_misc) cudaFreeHost(v->stage_misc);
+  if (v->kstream) cudaStreamDestroy(v->kstream);
+  if (v->cstream) cudaStreamDestroy(v->cstream);
+  if (v->kdone) cudaEventDestroy(v->kdone);
+  if (v->ev_in) cudaEventDestroy(v->ev_in);
+  delete v;
+  return GINT_OK;
+}
+
+static bool slot_done(const gint_server *v, unsigned long long seq) {
+  return *(volatile unsigned long long *)&v->done_h[seq % kServeRing] == seq + 1;
+}
+
+// (Re)launches the resident kernel if it is not running; claims start at the oldest unfinished job.
+static int server_launch(gint_server *v) {
+  if (v->launched && cudaEventQuery(v->kdone) == cudaErrorNotReady) return GINT_OK;
+  cudaGetLastError();
+  unsigned long long first = v->next_seq;
+  for (unsigned long long q = v->next_seq > kServeRing ? v->next_seq - kServeRing : 0; q < v->next_seq; ++q)
+    if (!slot_done(v, q)) {
+      first = q;
+      break;
+    }
+  v->stage_misc[0] = first;
+  if (cudaMemcpyAsync(&v->ctl->first_seq, v->stage_misc, sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                      v->kstream) != cudaSuccess)
+    return GINT_ECUDA;
+  auto kern = v->forces ? k_serve<true> : k_serve<false>;
+  kern<<<v->num_sms, kT, v->dsmem, v->kstream>>>(v->tabs, v->ctl, v->jobs, v->st, v->job_end, v->done_d, v->zero,
+                                                  v->split3, v->dsmem, v->idle_ns);
+  if (cudaGetLastError() != cudaSuccess || cudaEventRecord(v->kdone, v->kstream) != cudaSuccess) return GINT_ECUDA;
+  v->launched = true;
+  ++v->launches;
+  return GINT_OK;
+}
+
+extern "C" int gint_server_create(int precision, int forces, double idle_s, gint_server **out) {
+  if (!out) return GINT_EINVAL;
+  *out = nullptr;
+  if (precision != GINT_F16X3 && precision != GINT_F16X1) return GINT_EUNSUPPORTED;
+  if (!(idle_s > 0) || idle_s > 10.0) return GINT_EINVAL;
+  gint_server *v = new gint_server();
+  v->forces = forces ? 1 : 0;
+  v->split3 = precision == GINT_F16X3 ? 1 : 0;
+  v->idle_ns = (long long)(idle_s * 1e9);
+  if (cudaGetDevice(&v->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v->num_sms, cudaDevAttrMultiProcessorCount, v->device) != cudaSuccess) {
+    server_free(v);
+    return GINT_ECUDA;
+  }
+  const size_t stat = sizeof(BrickSh) + sizeof(GJob) + 64;
+  v->dsmem = (int)((227 * 1024 - stat) & ~(size_t)1023);
+  bool okm = cudaMalloc(&v->ctl, sizeof(GServeCtl)) == cudaSuccess &&
+             cudaMalloc(&v->jobs, kServeRing * sizeof(GJob)) == cudaSuccess &&
+             cudaMalloc(&v->st, kServeRing * sizeof(GJobState)) == cudaSuccess &&
+             cudaMalloc(&v->job_end, kServeMaxJobs * sizeof(long long)) == cudaSuccess &&
+             cudaMalloc(&v->zero, 512) == cudaSuccess &&
+             cudaHostAlloc(&v->done_h, kServeRing * sizeof(unsigned long long), cudaHostAllocMapped) == cudaSuccess &&
+             cudaHostAlloc(&v->stage, kServeRing * sizeof(GJob), cudaHostAllocDefault) == cudaSuccess &&
+             cudaHostAlloc(&v->stage_end, kServeRing * sizeof(long long), cudaHostAllocDefault) == cudaSuccess &&
+             cudaHostAlloc(&v->stage_tail, kServeRing * sizeof(unsigned long long), cudaHostAllocDefault) == cudaSuccess &&
+             cudaHostAlloc(&v->stage_misc, 8 * sizeof(unsigned long long), cudaHostAllocDefault) == cudaSuccess;
+  if (!okm) {
+    cudaGetLastError();
+    server_free(v);
+    return GINT_ENOMEM;
+  }
+  std::memset(v->done_h, 0, kServeRing * sizeof(unsigned long long));
+  if (cudaHostGetDevicePointer((void **)&v->done_d, v->done_h, 0) != cudaSuccess ||
+      cudaMemset(v->ctl, 0, sizeof(GServeCtl)) != cudaSuccess || cudaMemset(v->zero, 0, 512) != cudaSuccess ||
+      cudaMemset(v->st, 0, kServeRing * sizeof(GJobState)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&v->kstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&v->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&v->kdone, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&v->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      set_smem(k_serve<true>, (uint32_t)v->dsmem) != GINT_OK || set_smem(k_serve<false>, (uint32_t)v->dsmem) != GINT_OK) {
+    cudaGetLastError();
+    server_free(v);
+    return GINT_ECUDA;
+  }
+  *out = v;
+  return GINT_OK;
+}
+
+extern "C" int gint_server_submit(gint_server *v, const gint_task *T, void *stream, long long *ticket) {
+  if (!v || !T || !T->h || !ticket) return GINT_EINVAL;
+  gint_handle *h = T->h;
+  const bool dens = T->rho || T->F, loc = T->H_blocks != nullptr;
+  if ((!dens && !loc) || (dens && !T->D_blocks) || ((loc || T->F) && !T->V)) return GINT_EINVAL;
+  if (T->F && !v->forces) return GINT_EINVAL;
+  if (h->device != v->device) return GINT_EINVAL;
+  int rc = gint_tc_check_capacity(h);
+  if (rc) return rc;
+  if (loc && h->max_brick_porb > kNPMAXH) return GINT_ECAPACITY;
+  if (h->max_brick_porb + 0 > kNPMAX || rho_smem_bytes(std::max(h->max_brick_porb, kRC), 2) + kHTail > (uint32_t)v->dsmem)
+    return GINT_ECAPACITY;
+  if (!v->have_tabs) {
+    v->tabs = h->geom;
+    v->have_tabs = true;
+  } else if (std::memcmp(static_cast<const GTabs *>(&h->geom), &v->tabs, sizeof(GTabs))) {
+    return GINT_EINVAL;
+  }
+  if (v->next_seq >= (unsigned long long)kServeMaxJobs) return GINT_ECAPACITY;
+  const unsigned long long seq = v->next_seq;
+  const int slot = (int)(seq % kServeRing);
+  if (seq >= (unsigned long long)kServeRing && !slot_done(v, seq - kServeRing)) return GINT_EBUSY;
+  for (unsigned long long q = seq > kServeRing ? seq - kServeRing : 0; q < seq; ++q)
+    if (v->slot_h[q % kServeRing] == h && !slot_done(v, q)) return GINT_EBUSY;  // one job per handle
+  GJob &J = v->stage[slot];
+  std::memset(&J, 0, sizeof(GJob));
+  fill_sys(J.sys, *T);
+  fill_prep(J.prep, *T);
+  if (dens && h->npairs > 0) fill_tile(J.tile, *T);
+  if (loc) fill_red_gamma(J.red, *T);
+  J.npairs = dens ? h->npairs : 0;
+  J.nupper = loc ? h->nupper : 0;
+  J.fixed = (v->forces && v->split3) ? 1 : 0;
+  J.nbricks = h->geom.nbricks;
+  const long long span = std::max(std::max(h->nblock, h->geom.ngrid), 3LL * h->geom.natoms);
+  J.n_prep = std::max(1LL, (span + kServePrep - 1) / kServePrep);
+  J.n_tile = (J.npairs + kServeTilePairs - 1) / kServeTilePairs;
+  J.n_red = (J.nupper + kServeRedPairs - 1) / kServeRedPairs;
+  J.item0 = (long long)v->next_item;
+  J.nitems = J.n_prep + 1 + J.n_tile + J.nbricks + J.n_red;
+  J.seq = seq;
+  cudaStream_t cs = (cudaStream_t)stream;
+  v->done_h[slot] = 0;
+  v->stage_end[slot] = J.item0 + J.nitems;
+  v->stage_tail[slot] = (unsigned long long)(J.item0 + J.nitems);
+  // inputs copied on the caller's stream first; then descriptor, counters, job end and the new tail
+  if (cudaEventRecord(v->ev_in, cs) != cudaSuccess || cudaStreamWaitEvent(v->cstream, v->ev_in, 0) != cudaSuccess ||
+      cudaMemcpyAsync(v->jobs + slot, &J, sizeof(GJob), cudaMemcpyHostToDevice, v->cstream) != cudaSuccess ||
+      cudaMemsetAsync(v->st + slot, 0, sizeof(GJobState), v->cstream) != cudaSuccess ||
+      cudaMemcpyAsync(v->job_end + seq, v->stage_end + slot, sizeof(long long), cudaMemcpyHostToDevice, v->cstream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(&v->ctl->tail, v->stage_tail + slot, sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                      v->cstream) != cudaSuccess)
+    return GINT_ECUDA;
+  v->slot_h[slot] = h;
+  v->next_item += (unsigned long long)J.nitems;
+  v->next_seq = seq + 1;
+  *ticket = (long long)seq;
+  return server_launch(v);
+}
+
+extern "C" int gint_server_test(gint_server *v, long long ticket, int *done) {
+  if (!v || !done || ticket < 0 || (unsigned long long)ticket >= v->next_seq) return GINT_EINVAL;
+  if ((unsigned long long)ticket + kServeRing < v->next_seq) {
+    *done = 1;  // its slot has been reused: it completed
+    return GINT_OK;
+  }
+  *done = slot_done(v, (unsigned long long)ticket) ? 1 : 0;
+  if (*done) return GINT_OK;
+  if (v->launched && cudaEventQuery(v->kdone) == cudaErrorNotReady) return GINT_OK;  // still resident
+  cudaGetLastError();
+  // the kernel has left: an error, or it went idle while this job's copies were still on their way
+  GServeCtl c;
+  if (cudaStreamSynchronize(v->cstream) != cudaSuccess ||
+      cudaMemcpy(&c, v->ctl, sizeof(GServeCtl), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return GINT_ECUDA;
+  if (c.err) return (c.err & GINT_ERRBIT_TIMEOUT) ? GINT_ETIMEDOUT : GINT_EDEVICE;
+  *done = slot_done(v, (unsigned long long)ticket) ? 1 : 0;
+  if (*done) return GINT_OK;
+  return c.head < c.tail ? server_launch(v) : GINT_OK;
+}
+
+extern "C" int gint_server_stats(const gint_server *v, long long *launches, long long *jobs) {
+  if (!v) return GINT_EINVAL;
+  if (launches) *launches = v->launches;
+  if (jobs) *jobs = (long long)v->next_seq;
+  return GINT_OK;
+}
+
+extern "C" int gint_server_stop(gint_server *v) {
+  if (!v) return GINT_EINVAL;
+  if (!v->launched) return GINT_OK;
+  v->stage_misc[1] = 1;
+  if (cudaMemcpyAsync(&v->ctl->stop, v->stage_misc + 1, sizeof(int), cudaMemcpyHostToDevice, v->cstream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(v->cstream) != cudaSuccess || cudaEventSynchronize(v->kdone) != cudaSuccess)
+    return GINT_ECUDA;
+  v->stage_misc[1] = 0;
+  if (cudaMemcpy(&v->ctl->stop, v->stage_misc + 1, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    return GINT_ECUDA;
+  v->launched = false;
+  return GINT_OK;
+}
+
+extern "C" int gint_server_destroy(gint_server *v) {
+  if (!v) return GINT_OK;
+  const int rc = gint_server_stop(v);
+  server_free(v);
+  return rc;
 }
 
 extern "C" int gint_orbitals(gint_handle *h, int precision, long long npts, const double *pts, double *phi,

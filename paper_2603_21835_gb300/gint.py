@@ -91,6 +91,12 @@ _lib.gint_dm_build_f16x3.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.gint_cn_info.argtypes = [_vp, ctypes.POINTER(_i)]
 _lib.gint_edm.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
 _lib.gint_brick_lists.argtypes = [_vp, ctypes.POINTER(_ll), ctypes.POINTER(_ll), _vp, _vp, _vp, _vp]
+_lib.gint_server_create.argtypes = [_i, _i, _d, ctypes.POINTER(_vp)]
+_lib.gint_server_submit.argtypes = [_vp, ctypes.POINTER(_Task), _vp, ctypes.POINTER(_ll)]
+_lib.gint_server_test.argtypes = [_vp, _ll, ctypes.POINTER(_i)]
+_lib.gint_server_stats.argtypes = [_vp, ctypes.POINTER(_ll), ctypes.POINTER(_ll)]
+_lib.gint_server_stop.argtypes = [_vp]
+_lib.gint_server_destroy.argtypes = [_vp]
 _lib.gint_orbitals.argtypes = [_vp, _i, _ll, _vp, _vp, _vp]
 
 C_ABI_SYMBOLS = ("gint_create", "gint_destroy", "gint_layout", "gint_pairs", "gint_stats", "gint_set_positions",
@@ -99,7 +105,8 @@ C_ABI_SYMBOLS = ("gint_create", "gint_destroy", "gint_layout", "gint_pairs", "gi
                  "gint_run_batch_timed", "gint_memory", "gint_layout_R", "gint_vlocal_R", "gint_bloch",
                  "gint_set_projectors", "gint_psibeta_layout", "gint_psibeta", "gint_cn_create", "gint_cn_destroy",
                  "gint_cn_step", "gint_dm_build", "gint_dm_build_f16x3", "gint_cn_info", "gint_edm",
-                 "gint_brick_lists", "gint_orbitals")
+                 "gint_brick_lists", "gint_orbitals", "gint_server_create", "gint_server_submit", "gint_server_test",
+                 "gint_server_stats", "gint_server_stop", "gint_server_destroy")
 
 
 class CrankNicolson:
@@ -222,6 +229,57 @@ def run_batch(tasks: Sequence[Task], precision: int = F16X3, stream=None, kernel
             raise ValueError("kernel_events must have been recorded once (CUDA events are created lazily)")
         _check(_lib.gint_run_batch_timed(arr, len(tasks), int(precision), _stream(stream), e0, e1),
                "gint_run_batch_timed")
+
+
+EBUSY = -9
+
+
+class DeviceQueue:
+    """The library's continuous-batching server (gint_server_*): one resident launch of the brick
+    kernels drains a device work queue; jobs (Task) are published while it runs."""
+
+    def __init__(self, precision: int = F16X3, forces: bool = True, idle_s: float = 0.2):
+        q = _vp()
+        _check(_lib.gint_server_create(int(precision), 1 if forces else 0, float(idle_s), ctypes.byref(q)),
+               "gint_server_create")
+        self._q = q
+
+    def submit(self, t: Task, stream=None) -> Optional[int]:
+        """Publishes the task (its D and V complete in order on `stream`); the ticket, or None when the
+        queue is full or the task's handle has a job in flight (GINT_EBUSY)."""
+        g = t.g
+        arr = _Task(g._h, _dptr(t.D, numel=g.nblock), _dptr(t.V, numel=g.ngrid), _dptr(t.rho, numel=g.ngrid),
+                    _dptr(t.H, numel=g.nblock), _dptr(t.F, numel=3 * g.natoms))
+        tk = _ll()
+        rc = _lib.gint_server_submit(self._q, ctypes.byref(arr), _stream(stream), ctypes.byref(tk))
+        if rc == EBUSY:
+            return None
+        _check(rc, "gint_server_submit")
+        return tk.value
+
+    def done(self, ticket: int) -> bool:
+        d = _i()
+        _check(_lib.gint_server_test(self._q, int(ticket), ctypes.byref(d)), "gint_server_test")
+        return bool(d.value)
+
+    def stats(self) -> dict:
+        la, jo = _ll(), _ll()
+        _check(_lib.gint_server_stats(self._q, ctypes.byref(la), ctypes.byref(jo)), "gint_server_stats")
+        return dict(launches=la.value, jobs=jo.value)
+
+    def stop(self):
+        _check(_lib.gint_server_stop(self._q), "gint_server_stop")
+
+    def close(self):
+        if getattr(self, "_q", None):
+            _lib.gint_server_destroy(self._q)
+            self._q = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _species_array(species_list):
