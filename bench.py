@@ -282,7 +282,7 @@ def run_serving(args, prec, dev):
         rate = args.serve_load / (mean_alone * 1e-3)
 
         def run(gaps):
-            nb0 = len(srv.batch_sizes)
+            nb0 = len(srv.concurrency)
             futs = []
             t0 = time.perf_counter()
             due = t0
@@ -297,11 +297,11 @@ def run_serving(args, prec, dev):
             res = [f.result(timeout=600) for f in futs]
             wall = max(r.done_t for r in res) - t0
             lat = serve.percentiles([r.latency_ms for r in res])
-            sizes = srv.batch_sizes[nb0:]
+            conc = srv.concurrency[nb0:]
             pairs = sum(2.0 * sessions[i].W for i, _ in plan)
             return {"p50_ms": lat["p50"], "p99_ms": lat["p99"], "mean_ms": lat["mean"], "max_ms": lat["max"],
                     "throughput_req_s": len(plan) / wall, "throughput_gpt_pair_s": pairs / wall / 1e9,
-                    "batches": len(sizes), "mean_batch": float(np.mean(sizes)), "max_batch": int(max(sizes))}
+                    "mean_jobs_in_flight_at_publication": float(np.mean(conc)), "max_jobs_in_flight": int(max(conc))}
 
         poisson = run(np.random.default_rng(1).exponential(1.0 / rate, len(plan)))
         burst = run(np.zeros(len(plan)))
@@ -314,6 +314,8 @@ def run_serving(args, prec, dev):
             "p50_ms": poisson["p50_ms"], "p99_ms": poisson["p99_ms"],
             "throughput_note": "2W per request (rho + H pair updates); the force pass is extra work not counted",
             "budget_bytes": srv.budget.budget, "peak_bytes": srv.budget.peak, "errors": len(srv.errors),
+            "resident_launches": srv.stats()["resident_launches"],
+            "design": "device work queue: one resident launch drains jobs published while it runs",
         }
     finally:
         srv.close()

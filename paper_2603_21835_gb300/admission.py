@@ -1,19 +1,17 @@
 """Admission policy of the serving loop (host logic only, no GPU needed).
 
-Device memory counted against the HBM budget:
-  * resident handles: per geometry, the radial tables, grid-brick neighbour lists, atom-pair
-    layout and workspace of the library handle (gint_memory);
-  * in-flight buffers: per admitted request, its device inputs and outputs (D and H blocks,
-    V and rho on the grid, F).
+Device memory counted against the HBM budget, per resident replica (one library handle of a
+geometry with its own device input/output buffers): the radial tables, grid-brick neighbour
+lists, atom-pair layout and workspace of the handle (gint_memory), plus D and H blocks, V and rho
+on the grid and F.  A replica runs one job at a time.
 
-A batch takes the queue's requests in arrival order (FIFO, no overtaking) while
-  * it has fewer than ``max_batch`` requests,
-  * the request's geometry is not already in the batch (one task per handle and launch),
-  * the request's bytes (plus its handle's, if the handle is not resident) fit the budget after
-    evicting idle resident handles, least recently used first (never one the batch uses).
-The first request that does not fit ends the batch; it waits for memory that batches on the
-GPU will release.  A request that cannot fit even when nothing else is admitted, nothing is on
-the GPU and every idle handle is evicted is rejected.
+Publication order (publish_order): in arrival order, a queued request is published when its
+geometry has an idle replica left and no earlier request of the same geometry is still waiting;
+requests of other geometries may overtake a waiting one (so one busy geometry does not hold up the
+others), while each geometry's requests run in arrival order.  A geometry without a resident
+replica gets one re-created, after evicting idle replicas least recently used first (Budget.plan);
+a request that cannot fit even when every idle replica is evicted and nothing is on the GPU is
+rejected.
 """
 from __future__ import annotations
 
@@ -78,43 +76,18 @@ class Budget:
             r.last_used = now
 
 
-@dataclasses.dataclass
-class Plan:
-    admit: List = dataclasses.field(default_factory=list)    # requests of the batch, in order
-    reject: List = dataclasses.field(default_factory=list)   # requests that can never fit
-    evict: List[Hashable] = dataclasses.field(default_factory=list)   # handles to free first
-    create: List[Hashable] = dataclasses.field(default_factory=list)  # handles to (re)create
-
-    @property
-    def consumed(self) -> int:
-        """Length of the queue prefix the plan takes (rejections come first, then admissions)."""
-        return len(self.reject) + len(self.admit)
-
-
-def select_batch(pending: Sequence, budget: Budget, max_batch: int, any_inflight: bool, now: float) -> Plan:
-    """Plans the next batch from the FIFO `pending` (items with .key, .request_bytes and
-    .handle_bytes) and applies it to `budget`: evictions, residents for created handles,
-    in-flight bytes and busy counts of the admitted requests."""
-    plan = Plan()
-    keys = set()
-    for r in pending:
-        if len(plan.admit) >= max_batch or r.key in keys:
-            break
-        resident = r.key in budget.resident
-        need = r.request_bytes + (0 if resident else r.handle_bytes)
-        ev = budget.plan(need, tuple(keys) + (r.key,))
-        if ev is None:
-            if plan.admit or any_inflight:
-                break
-            plan.reject.append(r)
+def publish_order(pending_keys: Sequence[Hashable], idle: Dict[Hashable, int]) -> List[int]:
+    """Indices (into the queue, in order) of the requests to publish now, given each geometry's
+    count of idle replicas: per-geometry FIFO, other geometries may overtake."""
+    left = dict(idle)
+    blocked = set()
+    out = []
+    for i, k in enumerate(pending_keys):
+        if k in blocked:
             continue
-        for k in ev:
-            budget.evict(k)
-        plan.evict += ev
-        if not resident:
-            budget.add_resident(r.key, r.handle_bytes, now)
-            plan.create.append(r.key)
-        budget.acquire(r.key, r.request_bytes)
-        keys.add(r.key)
-        plan.admit.append(r)
-    return plan
+        if left.get(k, 0) > 0:
+            left[k] -= 1
+            out.append(i)
+        else:
+            blocked.add(k)
+    return out

@@ -1529,18 +1529,37 @@ struct GPrep {
 // Elements [i0, i1) of the system's D blocks, grid and force arrays, by nt threads (this one t):
 // max |D| and max |V| (float32, rounded; atomicMax into S.mx), F zeroed.
 __device__ __forceinline__ void prep_range(const GPrepSys &S, long long i0, long long i1, long long t, long long nt) {
-  float mD = 0.f, mV = 0.f;
-  // inputs read through L2 (__ldcg): a resident launch may see them rewritten between its jobs
-  if (S.D)
-    for (long long i = i0 + t; i < min(i1, S.nblock); i += nt) mD = fmaxf(mD, (float)fabs(__ldcg(S.D + i)));
-  if (S.V)
-    for (long long i = i0 + t; i < min(i1, S.ngrid); i += nt) mV = fmaxf(mV, (float)fabs(__ldcg(S.V + i)));
+  // |x| of a float64 orders like its bit pattern without the sign, so the maxima are integer maxima
+  // (no float64 arithmetic, which runs at a small fraction of the integer rate on this GPU); the
+  // largest one is rounded to float32 once (rounding is monotonic: the same value as the largest
+  // rounded element).  Inputs are read through L2 (__ldcg): a resident launch may see them
+  // rewritten between its jobs.
+  unsigned long long bD = 0, bV = 0;
+  const unsigned long long mag = 0x7fffffffffffffffull;
+  // eight loads in flight per thread
+  auto absmax = [&](const double *x, long long n) {
+    unsigned long long b = 0;
+    const long long e = min(i1, n);
+    long long i = i0 + t;
+    for (; i + 7 * nt < e; i += 8 * nt) {
+      long long v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = __double_as_longlong(__ldcg(x + i + k * nt));
+#pragma unroll
+      for (int k = 0; k < 8; ++k) b = max(b, (unsigned long long)v[k] & mag);
+    }
+    for (; i < e; i += nt) b = max(b, (unsigned long long)__double_as_longlong(__ldcg(x + i)) & mag);
+    return b;
+  };
+  if (S.D) bD = absmax(S.D, S.nblock);
+  if (S.V) bV = absmax(S.V, S.ngrid);
   if (S.F)
     for (long long i = i0 + t; i < min(i1, 3 * S.natoms); i += nt) S.F[i] = 0.0;
   for (int o = 16; o > 0; o >>= 1) {
-    mD = fmaxf(mD, __shfl_xor_sync(0xffffffffu, mD, o));
-    mV = fmaxf(mV, __shfl_xor_sync(0xffffffffu, mV, o));
+    bD = max(bD, __shfl_xor_sync(0xffffffffu, bD, o));
+    bV = max(bV, __shfl_xor_sync(0xffffffffu, bV, o));
   }
+  const float mD = (float)__longlong_as_double((long long)bD), mV = (float)__longlong_as_double((long long)bV);
   if ((threadIdx.x & 31) == 0) {
     if (mD > 0.f) atomicMax(S.mx, __float_as_uint(mD));
     if (mV > 0.f) atomicMax(S.mx + 1, __float_as_uint(mV));
@@ -1703,7 +1722,8 @@ __global__ void __launch_bounds__(128) k_build_plans(const __grid_constant__ GTa
 // completion word into host-mapped memory.  A CTA with nothing to claim for idle_ns (or on the stop
 // flag, or when a wait gave up anywhere) leaves; the host relaunches when it has unclaimed work.
 constexpr int kServeRing = 64;                  // jobs in flight at most (descriptor ring)
-constexpr long long kServePrep = 1LL << 20;     // elements per max-reduction item
+constexpr long long kServePrep = 1LL << 16;     // elements per max-reduction item
+constexpr int kServeRange = 16;                 // most items one claim takes
 constexpr int kServeTilePairs = 32;             // pairs per tile item (four at a time, 128 threads each)
 constexpr int kServeRedPairs = 2;               // upper pairs per reduction item (256 threads each)
 constexpr long long kServeMaxJobs = 1LL << 20;  // jobs over a server's lifetime (completion-order table)
@@ -1768,7 +1788,20 @@ __global__ void __launch_bounds__(kT, 1)
   __shared__ BrickSh sh;
   __shared__ GJob sj;    // the item's job (copied through L2 for every item: a ring slot is rewritten
                          // by the host for later jobs while this launch runs)
-  __shared__ long long s_item, s_seq;
+  __shared__ long long s_item, s_seq, s_plan_next;  // s_plan_next: the item whose plan record is in flight
+  // thread 0's bookkeeping, kept in shared memory (not registers) so that it does not add to the
+  // register pressure of the brick items: the claim still to run, the job cursor, the current job,
+  // and completed items not yet counted (one job and kind; counted before this CTA waits for
+  // anything, a dependency or a new claim, and when the job or kind changes)
+  struct ServeState {
+    unsigned long long range_next, range_end, cursor, cur_sys, cur_job, pseq;
+    int *pc;
+    GJobState *pjs;
+    int pn, pitems;
+    unsigned long long bseq;           // the job whose stage bounds follow (claims)
+    long long b_i0, b_bb, b_rr, b_ee;  // its first item, first brick, first reduction, end
+  };
+  __shared__ ServeState ss;
   const int t = threadIdx.x, warp = t >> 5;
   if (t == 0) {
     for (int s2 = 0; s2 < kMaxStages; ++s2) mbar_init(&sh.full[s2], 1);
@@ -1788,80 +1821,143 @@ __global__ void __launch_bounds__(kT, 1)
   const uint32_t tmem = sh.tmem;
   ItemCtx cx{0u, 0u, 0u, true};
   uint32_t pphase = 0;
-  unsigned long long cursor = 0, cur_sys = ~0ull;
-  if (t == 0) cursor = ld_acquire_u64(&ctl->first_seq);
+  auto flush = [&]() {  // thread 0
+    if (!ss.pn) return;
+    __threadfence();  // the items' results before their counts
+    atomicAdd(ss.pc, ss.pn);
+    if (atomicAdd(&ss.pjs->all, ss.pn) + ss.pn == ss.pitems) {
+      __threadfence_system();
+      done[ss.pseq % kServeRing] = ss.pseq + 1;  // the job's results are in device memory
+    }
+    ss.pn = 0;
+  };
+  if (t == 0) {
+    ss.cursor = ld_acquire_u64(&ctl->first_seq);
+    ss.range_next = ss.range_end = 0;
+    ss.cur_sys = ss.cur_job = ~0ull;
+    ss.pc = nullptr;
+    ss.pjs = nullptr;
+    ss.pn = ss.pitems = 0;
+    ss.pseq = 0;
+    ss.bseq = ~0ull;
+    s_plan_next = -1;
+  }
   for (;;) {
     if (t == 0) {
-      // claim the next item (never past the published count), or leave
+      // the next item of the current claim, or a new claim of up to kServeRange published items
+      // (fewer as the published work runs low: a few items per CTA at most), or leave
       long long item = -1;
-      const long long t0 = globaltimer();
-      for (;;) {
-        if (*(volatile unsigned *)&ctl->err) break;
-        const unsigned long long h = *(volatile unsigned long long *)&ctl->head;
-        const unsigned long long tl = ld_acquire_u64(&ctl->tail);
-        if (h < tl) {
-          if (atomicCAS(&ctl->head, h, h + 1) == h) {
-            item = (long long)h;
+      if (ss.range_next < ss.range_end) {
+        item = (long long)ss.range_next++;
+      } else {
+        flush();
+        const long long t0 = globaltimer();
+        for (;;) {
+          if (*(volatile unsigned *)&ctl->err) break;
+          const unsigned long long h = *(volatile unsigned long long *)&ctl->head;
+          const unsigned long long tl = ld_acquire_u64(&ctl->tail);
+          if (h < tl) {
+            // the claim's size from the stage of item h (bounds of its job cached): up to kServeRange
+            // bricks or kServeRange / 2 reduction items, clipped to the stage; the short preparation
+            // and tile stages one item at a time so that every CTA helps with them
+            unsigned long long c = ss.cursor;
+            while (ld_acquire_s64(job_end + c) <= (long long)h) ++c;
+            ss.cursor = c;
+            if (ss.bseq != c) {
+              const GJob *jc = jobs + c % kServeRing;
+              ss.b_i0 = __ldcg(&jc->item0);
+              ss.b_bb = ss.b_i0 + __ldcg(&jc->n_prep) + 1 + __ldcg(&jc->n_tile);
+              ss.b_rr = ss.b_bb + __ldcg(&jc->nbricks);
+              ss.b_ee = ss.b_i0 + __ldcg(&jc->nitems);
+              ss.bseq = c;
+            }
+            const long long hi = (long long)h;
+            const long long lim = hi < ss.b_bb ? 1
+                                  : hi < ss.b_rr ? min((long long)kServeRange, ss.b_rr - hi)
+                                                 : min((long long)kServeRange / 2, ss.b_ee - hi);
+            const unsigned long long r = (unsigned long long)max(
+                1LL, min(lim, (long long)((tl - h) / (4ull * gridDim.x))));
+            unsigned long long got;
+            if (tl - h >= 2ull * gridDim.x * kServeRange) {
+              // plenty published: a plain fetch-and-add cannot pass the tail (at most one claim of
+              // at most kServeRange items per CTA is in progress), so no retry is needed
+              got = atomicAdd(&ctl->head, r);
+            } else {
+              got = atomicCAS(&ctl->head, h, h + r);
+              if (got != h) continue;
+            }
+            item = (long long)got;
+            ss.range_next = got + 1;
+            ss.range_end = got + r;
             break;
           }
-          continue;
+          if (*(volatile int *)&ctl->stop || globaltimer() - t0 > idle_ns) break;
+          __nanosleep(1000);
         }
-        if (*(volatile int *)&ctl->stop || globaltimer() - t0 > idle_ns) break;
-        __nanosleep(1000);
       }
-      if (item >= 0)  // job_end of every published job is written before the tail
-        while (ld_acquire_s64(job_end + cursor) <= item) ++cursor;
+      if (item >= 0) {  // job_end of every published job is written before the tail
+        unsigned long long c = ss.cursor;
+        while (ld_acquire_s64(job_end + c) <= item) ++c;
+        ss.cursor = c;
+      }
       s_item = item;
-      s_seq = (long long)cursor;
+      s_seq = (long long)ss.cursor;
       bulk_wait_read();  // a previous brick item's tiles have left shared memory
     }
     __syncthreads();
     const long long item = s_item;
     if (item < 0) break;
     const unsigned long long seq = (unsigned long long)s_seq;
-    {
+    if (seq != ss.cur_job) {  // a job's descriptor does not change while it is in flight
       const int *src = reinterpret_cast<const int *>(jobs + seq % kServeRing);
       int *dst = reinterpret_cast<int *>(&sj);
       for (int k = t; k < (int)(sizeof(GJob) / sizeof(int)); k += kT) dst[k] = __ldcg(src + k);
+      __syncthreads();
+      if (t == 0) ss.cur_job = seq;
     }
-    __syncthreads();
     const GJob &J = sj;
     GJobState &JS = st[seq % kServeRing];
     unsigned *err = &ctl->err;
     const long long li = item - J.item0;
     const long long b0 = J.n_prep + 1 + J.n_tile, r0 = b0 + J.nbricks;
-    int *counter;
     if (li < J.n_prep) {  // max-reduction chunk
       prep_range(J.prep, li * kServePrep, (li + 1) * kServePrep, t, kT);
-      counter = &JS.prep;
     } else if (li == J.n_prep) {  // scales
-      if (t == 0 && wait_count(&JS.prep, J.n_prep, err)) prep_scales(J.prep);
-      counter = &JS.scales;
+      if (t == 0) {
+        flush();
+        if (wait_count(&JS.prep, J.n_prep, err)) prep_scales(J.prep);
+      }
     } else if (li < b0) {  // D tiles
       bool go = true;
-      if (t == 0) go = wait_count(&JS.scales, 1, err);
+      if (t == 0) {
+        flush();
+        go = wait_count(&JS.scales, 1, err);
+      }
       __syncthreads();
       if (go && !*(volatile unsigned *)err) {
         const long long p0 = (li - J.n_prep - 1) * kServeTilePairs;
         for (long long p = p0 + (t >> 7); p < min((long long)J.npairs, p0 + kServeTilePairs); p += kT / 128)
           build_tile(g, J.tile, (int)p, J.fixed != 0, t & 127, 128);
       }
-      counter = &JS.tiles;
     } else if (li < r0) {  // a brick
       const long long b = li - b0;
       cx.ok = true;
-      if (t == 0) wait_count(&JS.tiles, J.n_tile, err);
+      if (t == 0 && ld_acquire_s32(&JS.tiles) < J.n_tile) {
+        flush();
+        wait_count(&JS.tiles, J.n_tile, err);
+      }
       __syncthreads();
       if (!*(volatile unsigned *)err) {  // the same decision in every thread (read after the barrier)
         const GSys &S = sj.sys;
-        if (seq != cur_sys) {  // a new job: points and scales into shared memory
+        if (seq != ss.cur_sys) {  // a new job: points and scales into shared memory
           init_points(S.c, sh);
+          __syncthreads();  // every thread has read ss.cur_sys
           if (t == 0) {
             sh.sc[0] = __ldcg(S.scales + 0);
             sh.sc[1] = __ldcg(S.scales + 1);
             sh.sc[2] = __ldcg(S.scales + 2);
+            ss.cur_sys = seq;
           }
-          cur_sys = seq;
         }
         const bool do_rho = S.do_rho != 0, do_h = S.do_h != 0;
         if (t < 128 && S.V && (do_h || FORCE)) {
@@ -1871,7 +1967,7 @@ __global__ void __launch_bounds__(kT, 1)
         const long long o0 = S.plan_off[b], o1 = S.plan_off[b + 1];
         const uint32_t bytes = (uint32_t)((o1 - o0) * 16);
         if (S.plan && bytes <= 4u * kPlanWords) {
-          if (t == 0) {
+          if (s_plan_next != item && t == 0) {  // not prefetched by the previous item
             fence_async_smem();
             mbar_arrive_tx(&sh.plan_bar, bytes);
             bulk_g2s(sh.planbuf, S.plan + o0, bytes, &sh.plan_bar);
@@ -1882,14 +1978,32 @@ __global__ void __launch_bounds__(kT, 1)
         } else {
           load_brick(S.c, g, S.nb, S.tile_off, b, sh);  // ends with a barrier
         }
+        if (t == 0) {
+          // the plan record of the next item of this claim, if it is a brick of this job, while this
+          // one runs (the buffer is free: unpacked before the barrier above)
+          s_plan_next = -1;
+          const long long li2 = (long long)ss.range_next - J.item0;
+          if (ss.range_next < ss.range_end && li2 >= b0 && li2 < r0 && S.plan) {
+            const long long p0 = S.plan_off[li2 - b0], p1 = S.plan_off[li2 - b0 + 1];
+            const uint32_t nb2 = (uint32_t)((p1 - p0) * 16);
+            if (nb2 <= 4u * kPlanWords) {
+              fence_async_smem();
+              mbar_arrive_tx(&sh.plan_bar, nb2);
+              bulk_g2s(sh.planbuf, S.plan + p0, nb2, &sh.plan_bar);
+              s_plan_next = (long long)ss.range_next;
+            }
+          }
+        }
         brick_body<FORCE>(g, S, b, do_rho, do_h, split3, dsmem, zero, tmem, sh, smem, cx);
         tc_fence_before();
       }
-      counter = &JS.bricks;
     } else {  // H reduction: two upper pairs, one per 256 threads (named barriers 2, 3), split into parts
       // exactly as k_h_reduce splits them, so the blocks equal those of the batched call bit for bit
       bool go = true;
-      if (t == 0) go = wait_count(&JS.bricks, J.nbricks, err);
+      if (t == 0 && ld_acquire_s32(&JS.bricks) < J.nbricks) {
+        flush();
+        go = wait_count(&JS.bricks, J.nbricks, err);
+      }
       __syncthreads();
       if (go && !*(volatile unsigned *)err) {
         const int sg = t / kRedThreads, u = (int)((li - r0) * kServeRedPairs) + sg;
@@ -1898,20 +2012,32 @@ __global__ void __launch_bounds__(kT, 1)
           reduce_pair<kRedGroups>(g, J.red, u, t % kRedThreads, part, part + (kRedGroups - 1) * kRedE * kRedLanes,
                                   2 + sg);
       }
-      counter = &JS.red;
     }
     if (!cx.ok) atomicOr(err, GINT_ERRBIT_TIMEOUT);  // the next claim sees it: every CTA leaves
     __syncthreads();
-    if (t == 0) {
-      __threadfence();  // this item's results before its count
-      atomicAdd(counter, 1);
-      if (atomicAdd(&JS.all, 1) == (int)J.nitems - 1) {
-        __threadfence_system();
-        done[seq % kServeRing] = seq + 1;  // the job's results are in device memory
-      }
+    if (t == 0) {  // everything from shared memory: nothing of the item stays live in registers
+      const unsigned long long sq = (unsigned long long)s_seq;
+      GJobState *js = st + sq % kServeRing;
+      const long long l2 = s_item - sj.item0, bb = sj.n_prep + 1 + sj.n_tile, rr = bb + sj.nbricks;
+      int *counter = l2 < sj.n_prep ? &js->prep
+                   : l2 == sj.n_prep ? &js->scales
+                   : l2 < bb ? &js->tiles
+                   : l2 < rr ? &js->bricks
+                             : &js->red;
+      if (ss.pn && (ss.pc != counter || ss.pjs != js)) flush();
+      ss.pc = counter;
+      ss.pjs = js;
+      ss.pitems = (int)sj.nitems;
+      ss.pseq = sq;
+      ++ss.pn;
     }
   }
-  if (t == 0) bulk_wait_all();
+  if (t == 0) {
+    flush();
+    // a plan record still in flight (the claim ended on an error): wait for it, bounded
+    if (s_plan_next >= 0) mbar_wait(&sh.plan_bar, pphase & 1u, &ctl->err);
+    bulk_wait_all();
+  }
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 512);
 }

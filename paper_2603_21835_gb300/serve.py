@@ -1,28 +1,28 @@
 """Serving loop: continuous batching of grid-integration requests on one GPU.
 
-A *session* is one geometry (cell, atoms, grid) registered with the server; its handle (radial
-tables, grid-brick neighbour lists, atom-pair layout and workspace) stays resident on the device
-between requests, so repeated requests on one geometry pay for none of that set-up.  A *request*
-is (session, D blocks, V) and returns rho, the local-H blocks and the local Pulay forces (the
-three passes of the paper's Sec. 3.3.1) as host arrays.
+A *session* is one geometry (cell, atoms, grid) registered with the server.  Its *replicas* are
+library handles (radial tables, grid-brick neighbour lists, atom-pair layout, workspace) with their
+own device input/output buffers; they stay resident between requests, so repeated requests on one
+geometry pay for none of that set-up.  A *request* is (session, D blocks, V) and returns rho, the
+local-H blocks and the local Pulay forces (the three passes of the paper's Sec. 3.3.1) as host
+arrays.
 
-Scheduling (one scheduler thread):
-  * requests wait in a FIFO queue; a batch takes queued requests in order while there is a free
-    slot (at most ``max_batch`` systems, one request per session) and their device footprint fits
-    the HBM budget, evicting idle resident handles (least recently used) when it would not;
-  * up to ``depth`` batches are on the GPU at once: a request that arrives while a batch runs is
-    admitted into the next one as soon as slots and memory allow, its inputs are copied on a
-    side stream while the running batch computes, and its batch is queued behind it, so the
-    device does not idle between batches;
-  * each batch is ONE call of gint_run_batch: every system's density/force bricks and local-H
-    bricks are items of one persistent launch (plus the per-batch preparation and H-reduction
-    launches);
-  * a batch's results are read back when its completion event fires and the futures resolve.
-
-The budget counts resident handles (gint_memory) plus the device buffers of admitted requests
-(D, V, rho, H, F).  A new geometry's handle is measured when it is created; until then its
-footprint is unknown, so creation may exceed the budget by that one handle before idle handles
-are evicted.  A request that cannot fit even in an empty server fails with MemoryError.
+The GPU side is the library's device work queue (gint_server_*): ONE resident launch of the brick
+kernels drains a queue of jobs, and a job published while others are on the GPU starts as soon as
+CTAs free up, in the same residency, its items interleaving with theirs.  The host side here (one
+scheduler thread) decides what to publish:
+  * requests wait in a FIFO queue; the scheduler publishes a request as soon as its session has an
+    idle replica (a replica runs one job at a time: its workspace is the job's), overtaking earlier
+    requests only of other sessions, so each session's requests run in arrival order;
+  * publishing a request = copying D and V into the replica's device buffers (copy stream) and
+    submitting the job; at most 64 jobs are in flight;
+  * when a job's completion word arrives, its outputs are copied to pinned host memory and its
+    future resolves; the replica is idle again.
+Device memory is counted against the HBM budget per replica (gint_memory of the handle plus its
+input/output buffers).  A session without a resident replica (evicted earlier) gets one re-created
+when it is next needed: the queue is drained first (handle creation and release synchronise the
+device), idle replicas are evicted least recently used first until it fits, and a request that
+cannot fit even on an empty server fails with MemoryError.
 """
 from __future__ import annotations
 
@@ -37,39 +37,58 @@ import numpy as np
 import torch
 
 from . import gint as G
-from .admission import Budget, select_batch
+from .admission import Budget, publish_order
 
 
 # ----------------------------------------------------------------------------------------------
-# Sessions, requests, results
+# Sessions, replicas, requests, results
 # ----------------------------------------------------------------------------------------------
+class Replica:
+    """One resident handle of a session with its device buffers and pinned host outputs."""
+
+    def __init__(self, session: "Session", index: int, device: torch.device):
+        self.session, self.index = session, index
+        self.g = G.Gint(session.system)
+        s = session
+        self.D = torch.empty(s.nblock, dtype=torch.float64, device=device)
+        self.V = torch.empty(s.ngrid, dtype=torch.float64, device=device)
+        self.rho = torch.empty(s.ngrid, dtype=torch.float64, device=device)
+        self.H = torch.empty(s.nblock, dtype=torch.float64, device=device)
+        self.F = torch.empty((s.natoms, 3), dtype=torch.float64, device=device)
+        self.nbytes = self.g.memory() + s.request_bytes
+        self.busy = False
+
+    @property
+    def key(self) -> Tuple[int, int]:
+        return (self.session.key, self.index)
+
+    def drop(self):
+        self.g.close()
+        self.D = self.V = self.rho = self.H = self.F = None
+
+
 class Session:
     """A geometry registered with a server.  Layout arrays (pair list, block offsets, orbital
-    offsets) stay on the host; the handle may be evicted and re-created (same layout)."""
+    offsets) stay on the host; replicas may be evicted and re-created (same layout)."""
 
     def __init__(self, server: "Server", key: int, system):
         self.server, self.key, self.system = server, key, system
-        self.g: Optional[G.Gint] = None
-        self.handle_bytes = 0
-
-    def _create(self):
-        self.g = G.Gint(self.system)
-        self.handle_bytes = self.g.memory()
-        g = self.g
+        self.replicas: Dict[int, Replica] = {}
+        g = G.Gint(system)
         self.nblock, self.ngrid, self.natoms, self.norb = g.nblock, g.ngrid, g.natoms, g.norb
         self.pair_IJ, self.pair_off, self.atom_off = g.pair_IJ, g.pair_off, g.atom_off
-        st = g.stats()
-        self.W = st["W"]
-
-    def _drop(self):
-        if self.g is not None:
-            self.g.close()
-            self.g = None
+        self.W = g.stats()["W"]
+        self.handle_bytes = g.memory()
+        g.close()
 
     @property
     def request_bytes(self) -> int:
-        """Device bytes of one request's buffers: D, H blocks; V, rho; F."""
+        """Device bytes of one replica's input/output buffers: D, H blocks; V, rho; F."""
         return 8 * (2 * self.nblock + 2 * self.ngrid + 3 * self.natoms)
+
+    @property
+    def replica_bytes(self) -> int:
+        return self.handle_bytes + self.request_bytes
 
     def blocks_from_coefficients(self, C: np.ndarray) -> np.ndarray:
         """D = C C^T in this session's block layout (host, no dense D)."""
@@ -95,10 +114,9 @@ class Result:
     H: np.ndarray
     F: np.ndarray
     submit_t: float
-    launch_t: float
+    launch_t: float   # published to the device queue
     done_t: float
-    batch: int
-    batch_size: int
+    concurrency: int  # jobs in flight (this one included) when it was published
 
     @property
     def latency_ms(self) -> float:
@@ -112,28 +130,12 @@ class _Request:
     V: torch.Tensor  # pinned host
     future: Future
     submit_t: float
-    dev: Tuple = ()
-    host_out: Tuple = ()
-
-    @property
-    def key(self) -> int:
-        return self.session.key
-
-    @property
-    def request_bytes(self) -> int:
-        return self.session.request_bytes
-
-    @property
-    def handle_bytes(self) -> int:
-        return self.session.handle_bytes
-
-
-@dataclasses.dataclass
-class _Batch:
-    index: int
-    requests: List[_Request]
-    event: torch.cuda.Event
-    launch_t: float
+    replica: Optional[Replica] = None
+    ticket: int = -1
+    launch_t: float = 0.0
+    concurrency: int = 0
+    copied: Optional[torch.cuda.Event] = None
+    host: Tuple = ()  # pinned host outputs (the result's arrays: no copy on the host)
 
 
 def _pinned(x) -> torch.Tensor:
@@ -147,50 +149,47 @@ def _pinned(x) -> torch.Tensor:
 class Server:
     """Continuous-batching gint server on one GPU (see the module docstring)."""
 
-    def __init__(self, species: Sequence, budget_bytes: int, precision: int = G.F16X3, max_batch: int = 32,
-                 depth: int = 2, device: Optional[torch.device] = None, poll_s: float = 1e-4):
+    def __init__(self, species: Sequence, budget_bytes: int, precision: int = G.F16X3, replicas: int = 1,
+                 device: Optional[torch.device] = None, idle_s: float = 0.2, poll_s: float = 5e-5):
         self.species = list(species)
         self.precision = int(precision)
-        self.max_batch = int(max_batch)
-        self.depth = int(depth)
+        self.replicas = max(1, int(replicas))
         self.device = torch.device(device if device is not None else "cuda")
         self.poll_s = poll_s
         self.budget = Budget(budget_bytes)
         self._sessions: Dict[int, Session] = {}
         self._queue: Deque[_Request] = collections.deque()  # guarded by _cv
-        self._inflight: Deque[_Batch] = collections.deque()  # scheduler thread only
+        self._inflight: List[_Request] = []   # published jobs (scheduler thread only)
+        self._draining: List[_Request] = []   # completed jobs whose outputs are being copied
         self._cv = threading.Condition(threading.Lock())
-        self._state = threading.RLock()  # budget and sessions (scheduler and open())
+        self._state = threading.RLock()
         self._stop = False
-        self._failed: Optional[BaseException] = None  # a CUDA error: the context cannot be used any more
         self._paused = False
-        self._nbatch = 0
-        self.batch_sizes: List[int] = []
-        self.creations = 0  # handles re-created after an eviction
+        self._failed: Optional[BaseException] = None
+        self.creations = 0  # replicas re-created after an eviction
+        self.concurrency: List[int] = []  # jobs in flight at each publication
         self.errors: List[BaseException] = []
         with torch.cuda.device(self.device):
-            self._compute = torch.cuda.Stream()
             self._copy = torch.cuda.Stream()
-            self._check = torch.cuda.Stream()
+            self.queue = G.DeviceQueue(self.precision, forces=True, idle_s=idle_s)
         self._thread = threading.Thread(target=self._loop, name="gint-serve", daemon=True)
         self._thread.start()
 
     # -- client API
     def open(self, system) -> Session:
-        """Registers a geometry (species indices refer to the server's species list) and makes
-        its handle resident now (counted against the budget; idle handles may be evicted)."""
+        """Registers a geometry (species indices refer to the server's species list) and makes its
+        replicas resident now (counted against the budget; idle replicas may be evicted)."""
         names = [sp.name for sp in system.sp]
         lib = [sp.name for sp in self.species]
         if names != lib:
             raise ValueError(f"system species {names} differ from the server's list {lib}")
         with self._state:
-            key = len(self._sessions)
-            s = Session(self, key, system)
             with torch.cuda.device(self.device):
-                s._create()
-            self._sessions[key] = s
-            self.budget.add_resident(key, s.handle_bytes, time.perf_counter())
-            self._evict_for(0, protect=(key,))
+                key = len(self._sessions)
+                s = Session(self, key, system)
+                self._sessions[key] = s
+                for r in range(self.replicas):
+                    self._make_replica(s, r, protect=())
         return s
 
     def submit(self, session: Session, D_blocks, V) -> Future:
@@ -211,7 +210,7 @@ class Server:
         return fut
 
     def pause(self):
-        """Holds new launches (batches already on the GPU complete); requests keep queuing."""
+        """Holds new publications (jobs already on the GPU complete); requests keep queuing."""
         with self._cv:
             self._paused = True
 
@@ -220,6 +219,13 @@ class Server:
             self._paused = False
             self._cv.notify()
 
+    def stats(self) -> dict:
+        with self._state:
+            q = self.queue.stats()
+        c = np.asarray(self.concurrency) if self.concurrency else np.zeros(1)
+        return dict(resident_launches=q["launches"], jobs=q["jobs"], mean_concurrency=float(c.mean()),
+                    max_concurrency=int(c.max()))
+
     def close(self):
         with self._cv:
             self._paused = False
@@ -227,8 +233,11 @@ class Server:
             self._cv.notify()
         self._thread.join()
         with self._state:
+            self.queue.close()
             for s in self._sessions.values():
-                s._drop()
+                for r in list(s.replicas.values()):
+                    r.drop()
+                s.replicas.clear()
             self._sessions.clear()
 
     def __enter__(self):
@@ -237,93 +246,112 @@ class Server:
     def __exit__(self, *exc):
         self.close()
 
-    # -- scheduler (everything below runs on the scheduler thread)
-    def _evict_for(self, need: int, protect=()) -> bool:
+    # -- replicas and memory (scheduler thread, or open())
+    def _make_replica(self, s: Session, index: int, protect) -> bool:
+        """Evicts idle replicas (LRU) until one more of `s` fits, then creates it; False if it cannot
+        fit.  Creating and releasing handles synchronise the device: the queue is drained first."""
+        need = s.replica_bytes
         plan = self.budget.plan(need, protect)
         if plan is None:
             return False
+        self.queue.stop()
         for key in plan:
-            self._sessions[key]._drop()
+            sk, ri = key
+            self._sessions[sk].replicas.pop(ri).drop()
             self.budget.evict(key)
+        r = Replica(s, index, self.device)
+        s.replicas[index] = r
+        self.budget.add_resident(r.key, r.nbytes, time.perf_counter())
         return True
 
-    def _admit(self) -> List[_Request]:
-        """The next batch (FIFO prefix of the queue, see admission.select_batch)."""
+    # -- scheduler (everything below runs on the scheduler thread)
+    def _publish(self, req: _Request, r: Replica):
+        req.replica = r
+        r.busy = True
+        now = time.perf_counter()
+        with self._state:  # the queue and the budget are shared with open()
+            self.budget.acquire(r.key, 0)
+            with torch.cuda.device(self.device), torch.cuda.stream(self._copy):
+                r.D.copy_(req.D, non_blocking=True)
+                r.V.copy_(req.V, non_blocking=True)
+            ticket = self.queue.submit(G.Task(r.g, r.D, r.V, rho=r.rho, H=r.H, F=r.F), stream=self._copy)
+            if ticket is None:  # the queue's ring is full: try again later
+                r.busy = False
+                self.budget.release(r.key, 0, now)
+                req.replica = None
+                return False
+        req.ticket, req.launch_t = ticket, now
+        req.host = tuple(torch.empty(t.shape, dtype=torch.float64, pin_memory=True) for t in (r.rho, r.H, r.F))
+        req.concurrency = len(self._inflight) + 1
+        self.concurrency.append(req.concurrency)
+        self._inflight.append(req)
+        return True
+
+    def _admit(self):
+        """Publishes queued requests whose geometry has an idle replica (admission.publish_order),
+        re-creating a replica first for a geometry that has none resident."""
         with self._cv:
-            pending = [self._queue[i] for i in range(min(len(self._queue), self.max_batch + 1))]
-        with self._state:
-            plan = select_batch(pending, self.budget, self.max_batch, bool(self._inflight), time.perf_counter())
-            for key in plan.evict:
-                self._sessions[key]._drop()
-            with torch.cuda.device(self.device):
-                for key in plan.create:
-                    self._sessions[key]._create()
+            if self._paused:
+                return
+            pending = list(self._queue)
+        if not pending:
+            return
+        taken = []
+        for s in {req.session.key: req.session for req in pending}.values():
+            if s.replicas:
+                continue
+            with self._state:  # evicted earlier: re-create one replica
+                busy = tuple(x.key for ss in self._sessions.values() for x in ss.replicas.values() if x.busy)
+                if self._make_replica(s, 0, protect=busy):
                     self.creations += 1
-        with self._cv:
-            for _ in range(plan.consumed):
-                self._queue.popleft()
-        for r in plan.reject:
-            r.future.set_exception(MemoryError(
-                f"request needs {r.request_bytes + r.handle_bytes} device bytes; the budget is {self.budget.budget}"))
-        return plan.admit
+                elif not busy:
+                    err = MemoryError(f"request needs {s.replica_bytes} device bytes; the budget is "
+                                      f"{self.budget.budget}")
+                    for req in pending:
+                        if req.session is s:
+                            req.future.set_exception(err)
+                            taken.append(req)
+        pending = [req for req in pending if req not in taken]
+        idle = {s.key: [x for x in s.replicas.values() if not x.busy] for s in {r.session for r in pending}}
+        for i in publish_order([req.session.key for req in pending], {k: len(v) for k, v in idle.items()}):
+            req = pending[i]
+            if not self._publish(req, idle[req.session.key].pop(0)):
+                break  # the queue's ring is full
+            taken.append(req)
+        if taken:
+            with self._cv:
+                for req in taken:
+                    self._queue.remove(req)
 
-    def _launch(self, reqs: List[_Request]) -> _Batch:
-        dev = self.device
-        with torch.cuda.device(dev):
-            with torch.cuda.stream(self._copy):
-                for r in reqs:
-                    s = r.session
-                    Dd = torch.empty(s.nblock, dtype=torch.float64, device=dev)
-                    Vd = torch.empty(s.ngrid, dtype=torch.float64, device=dev)
-                    Dd.copy_(r.D, non_blocking=True)
-                    Vd.copy_(r.V, non_blocking=True)
-                    Dd.record_stream(self._compute)
-                    Vd.record_stream(self._compute)
-                    r.dev = (Dd, Vd)
-                copied = torch.cuda.Event()
-                copied.record(self._copy)
-            self._compute.wait_event(copied)
-            with torch.cuda.stream(self._compute):
-                tasks = []
-                for r in reqs:
-                    s = r.session
-                    rho = torch.empty(s.ngrid, dtype=torch.float64, device=dev)
-                    H = torch.empty(s.nblock, dtype=torch.float64, device=dev)
-                    F = torch.empty((s.natoms, 3), dtype=torch.float64, device=dev)
-                    r.dev = r.dev + (rho, H, F)
-                    tasks.append(G.Task(s.g, r.dev[0], r.dev[1], rho=rho, H=H, F=F))
-                G.run_batch(tasks, self.precision, stream=self._compute)
-                for r in reqs:
-                    outs = r.dev[2:5]
-                    r.host_out = tuple(torch.empty(d.shape, dtype=torch.float64, pin_memory=True) for d in outs)
-                    for h, d in zip(r.host_out, outs):
+    def _collect(self):
+        for req in list(self._inflight):
+            with self._state:
+                finished = self.queue.done(req.ticket)
+            if finished:
+                self._inflight.remove(req)
+                r = req.replica
+                with torch.cuda.device(self.device), torch.cuda.stream(self._copy):
+                    for h, d in zip(req.host, (r.rho, r.H, r.F)):
                         h.copy_(d, non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(self._compute)
-        b = _Batch(self._nbatch, reqs, ev, time.perf_counter())
-        self._nbatch += 1
-        self.batch_sizes.append(len(reqs))
-        return b
-
-    def _release(self, r: _Request, now: float):
-        r.dev = ()
-        with self._state:
-            self.budget.release(r.key, r.request_bytes, now)
-
-    def _finish(self, b: _Batch):
-        done = time.perf_counter()
-        for r in b.requests:
-            s = r.session
-            try:
-                s.g.sync(stream=self._check)  # the handle's device error word (does not wait for later batches)
-                rho, H, F = (x.numpy() for x in r.host_out)
-                r.future.set_result(Result(rho.reshape(s.system.grid), H, F, r.submit_t, b.launch_t, done, b.index,
-                                           len(b.requests)))
-            except BaseException as e:  # noqa: BLE001 - delivered to the caller's future
-                self.errors.append(e)
-                r.future.set_exception(e)
-            r.host_out = ()
-            self._release(r, done)
+                    req.copied = torch.cuda.Event()
+                    req.copied.record(self._copy)
+                self._draining.append(req)
+        for req in list(self._draining):
+            if req.copied.query():
+                self._draining.remove(req)
+                r, s = req.replica, req.session
+                done = time.perf_counter()
+                try:
+                    r.g.sync(stream=self._copy)  # the handle's device error word
+                    rho, H, F = (x.numpy() for x in req.host)
+                    req.future.set_result(Result(rho.reshape(s.system.grid), H, F, req.submit_t, req.launch_t, done,
+                                                 req.concurrency))
+                except BaseException as e:  # noqa: BLE001 - delivered to the caller's future
+                    self.errors.append(e)
+                    req.future.set_exception(e)
+                r.busy = False
+                with self._state:
+                    self.budget.release(r.key, 0, done)
 
     def _loop(self):
         try:
@@ -334,36 +362,24 @@ class Server:
                 self._failed = e
                 pending = list(self._queue)
                 self._queue.clear()
-            for b in self._inflight:
-                pending += b.requests
-            self._inflight.clear()
+            pending += self._inflight + self._draining
+            self._inflight, self._draining = [], []
             for r in pending:
                 if not r.future.done():
                     r.future.set_exception(e)
 
     def _serve(self):
         while True:
-            while self._inflight and self._inflight[0].event.query():
-                self._finish(self._inflight.popleft())
+            self._collect()
             with self._cv:
-                if self._stop and not self._queue and not self._inflight:
+                if self._stop and not self._queue and not self._inflight and not self._draining:
                     return
-                ready = bool(self._queue) and len(self._inflight) < self.depth and not self._paused
-                if not ready:
-                    self._cv.wait(self.poll_s if self._inflight else 0.05)
+                idle = not self._queue and not self._inflight and not self._draining
+                if idle:
+                    self._cv.wait(0.05)
                     continue
-            reqs = self._admit()
-            if not reqs:
-                time.sleep(self.poll_s)  # memory is held by batches on the GPU
-                continue
-            try:
-                self._inflight.append(self._launch(reqs))
-            except BaseException as e:  # noqa: BLE001 - fail this batch, keep serving
-                self.errors.append(e)
-                now = time.perf_counter()
-                for r in reqs:
-                    r.future.set_exception(e)
-                    self._release(r, now)
+            self._admit()
+            time.sleep(self.poll_s)
 
 
 def percentiles(latencies_ms: Sequence[float]) -> Dict[str, float]:

@@ -1,4 +1,5 @@
-"""Serving loop on the GPU: continuous batching of mixed systems under an HBM budget.
+"""Serving loop on the GPU: continuous batching of mixed systems under an HBM budget, on the
+library's device work queue (one resident launch drains the jobs the scheduler publishes).
 
 Each request's result must be the same in the mix as alone (rho and H bitwise: one owner brick
 per grid point and a fixed-order H reduction; forces to float64 rounding, as their atomic
@@ -42,19 +43,20 @@ def env():
     return dict(torch=torch, G=G, serve=serve, ws=ws, systems=systems, alone=alone)
 
 
+_ALONE = {}
+
+
 def _alone_result(env, i, j):
-    torch, G = env["torch"], env["G"]
-    g, w = env["alone"][i], env["ws"][i]
-    D, V = _variant(w, j)
-    Dd = torch.from_numpy(g.dense_to_blocks(D)).cuda()
-    Vd = torch.from_numpy(np.ascontiguousarray(V.reshape(-1))).cuda()
-    rho = torch.empty(g.ngrid, dtype=torch.float64, device="cuda")
-    H = torch.empty(g.nblock, dtype=torch.float64, device="cuda")
-    F = torch.empty((g.natoms, 3), dtype=torch.float64, device="cuda")
-    g.run(Dd, Vd, G.F16X3, rho=rho, H=H, F=F)
-    torch.cuda.synchronize()
-    g.sync()
-    return rho.cpu().numpy(), H.cpu().numpy(), F.cpu().numpy()
+    """Request (i, j) served alone: a fresh server, one request, nothing else on the GPU."""
+    if (i, j) not in _ALONE:
+        serve = env["serve"]
+        w, g = env["ws"][i], env["alone"][i]
+        D, V = _variant(w, j)
+        with serve.Server(LIB, budget_bytes=8 << 30) as srv:
+            s = srv.open(env["systems"][i])
+            r = srv.submit(s, g.dense_to_blocks(D), np.ascontiguousarray(V.reshape(-1))).result(timeout=120)
+        _ALONE[(i, j)] = (r.rho.reshape(-1), r.H, r.F)
+    return _ALONE[(i, j)]
 
 
 def _submit_stream(srv, sessions, env, plan, gap_ms, seed, nburst):
@@ -94,9 +96,11 @@ def test_mix_equals_alone_and_oracle(env):
     with serve.Server(LIB, budget_bytes=8 << 30) as srv:
         sessions = [srv.open(s) for s in env["systems"]]
         results = _submit_stream(srv, sessions, env, plan, gap_ms=1.0, seed=1, nburst=6)
-        sizes = list(srv.batch_sizes)
+        st = srv.stats()
         assert not srv.errors
-    assert sizes[0] == 3  # the queued burst: one request of each system in one launch (FIFO)
+    # the queued burst: one request of each system on the GPU at once (the second request of a
+    # system waits for that system's replica), published into the resident launch
+    assert st["max_concurrency"] >= 3 and st["jobs"] == len(plan)
     for (i, j), r in zip(plan, results):
         rho, H, F = _alone_result(env, i, j)
         assert np.array_equal(r.rho.reshape(-1), rho), (i, j)
@@ -125,7 +129,7 @@ def test_budget_forces_eviction_and_recreation(env):
         srv.budget.peak = srv.budget.used  # creation in open() may exceed by one handle (documented)
         results = _submit_stream(srv, sessions, env, plan, gap_ms=0.5, seed=2, nburst=3)
         print("handle", hb, "request", rb, "budget", budget, "peak", srv.budget.peak, "creations", srv.creations,
-              "batches", srv.batch_sizes)
+              "stats", srv.stats())
         assert srv.budget.peak <= budget
         assert srv.creations >= 2  # handles were evicted and re-created to stay within the budget
         assert not srv.errors
