@@ -680,7 +680,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "natoms": g.natoms, "norb": g.norb, "grid": list(g.grid),
                    "precision": args.precision, "W_pairs_per_pass": W, "W_exec_padded": st["W_exec"],
-                   "nbricks": st["nbricks"], "max_brick_orb": st["max_brick_orb"], "l2": "flushed (256 MB write)",
+                   "nbricks": st["nbricks"], "max_brick_orb": st["max_brick_orb"], "handle_bytes": g.memory(),
+                   "l2": "flushed (256 MB write)",
                    "parallelism": f"replicas{world}"},
         "ms_kernel": tdom, "ms_rho_alone": statistics.mean(t_rho), "ms_vlocal_alone": statistics.mean(t_h),
         "ms_force_alone": statistics.mean(t_f),
