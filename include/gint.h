@@ -167,8 +167,12 @@ int gint_vlocal(gint_handle *h, int precision, const double *V, double *H_blocks
  * H(R) array, and pointers to library-owned host arrays keys [nkeys][5] (I, J, n1, n2, n3) and
  * key_off [nkeys + 1] (element offset of each block), valid until the positions change or the
  * handle is destroyed.  The tables are built on the first call (synchronous).
- * Returns GINT_EUNSUPPORTED when some brick sees two lattice images of one atom (a cell shorter
- * than about twice the orbital cutoff plus a brick): there the brick tiles mix several R. */
+ * Where some brick sees two lattice images of one atom (a cell shorter than about twice the orbital
+ * cutoff plus a brick), the handle's brick tiles mix several R; there the first call also builds an
+ * unfolded twin of the handle (same descriptor and pair layout, one brick slot per atom image;
+ * counted by gint_memory, moved by gint_set_positions), and the per-R calls run on it.
+ * GINT_ECAPACITY if the twin's bricks exceed the local-H kernel's limit of 288 padded orbital columns
+ * (18 images of 13-orbital atoms per brick; the 8-atom cubic Si cell needs 16). */
 int gint_layout_R(gint_handle *h, int *nkeys, long long *nblock_elems, const int **keys, const long long **key_off);
 
 /* Local-Hamiltonian pass per lattice vector: H_R [nblock_elems of gint_layout_R] (device,

@@ -59,6 +59,11 @@ void free_all(gint_handle *h) {
   gint_pb_free(h);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   h->own_stream = nullptr;
+  if (h->twin) {
+    free_all(h->twin);
+    delete h->twin;
+    h->twin = nullptr;
+  }
 }
 
 void inverse3(const double a[9], double inv[9], double *det) {
@@ -161,16 +166,40 @@ int gint_reserve_nbr(gint_handle *h) {
   return GINT_OK;
 }
 
-extern "C" {
+namespace {
 
-int gint_create(const gint_desc *d, gint_handle **out) {
+// The handle's set-up; `unfold` gives every (atom, image) entry of a brick a slot of its own.
+int create_impl(const gint_desc *d, bool unfold, gint_handle **out) {
   if (!out) return GINT_EINVAL;
   *out = nullptr;
   int v = validate(d);
   if (v) return v;
   gint_handle *h = new (std::nothrow) gint_handle();
   if (!h) return GINT_ENOMEM;
+  h->unfold = unfold;
   std::memset(static_cast<void *>(&h->geom), 0, sizeof(GGeom));  // batched launches compare GTabs bytes
+  // host copy of the descriptor's species (an unfolded twin is built from it on demand)
+  {
+    int nr = 0;
+    for (int s = 0; s < d->nspecies; ++s) nr += d->sp[s].nradial;
+    h->d_sp.assign(d->sp, d->sp + d->nspecies);
+    h->d_rad.resize(nr);
+    h->d_tab.resize(2 * (size_t)nr);
+    h->d_skin = d->skin;
+    h->d_pos0.assign(d->pos, d->pos + 3 * (size_t)d->natoms);
+    int r = 0;
+    for (int s = 0; s < d->nspecies; ++s) {
+      h->d_sp[s].radial = h->d_rad.data() + r;
+      for (int k = 0; k < d->sp[s].nradial; ++k, ++r) {
+        const gint_radial &R = d->sp[s].radial[k];
+        h->d_tab[2 * r].assign(R.f, R.f + R.npts);
+        h->d_tab[2 * r + 1].assign(R.df, R.df + R.npts);
+        h->d_rad[r] = R;
+        h->d_rad[r].f = h->d_tab[2 * r].data();
+        h->d_rad[r].df = h->d_tab[2 * r + 1].data();
+      }
+    }
+  }
   TRYCU(cudaGetDevice(&h->device));
   TRYCU(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
   cudaStream_t st = h->own_stream;
@@ -357,6 +386,57 @@ int gint_create(const gint_desc *d, gint_handle **out) {
   return GINT_OK;
 }
 
+// The unfolded twin of h: the creation-time descriptor (so the pair set and block layout are h's),
+// moved to h's current positions.
+int make_twin(gint_handle *h) {
+  if (h->twin) return GINT_OK;
+  gint_desc d{};
+  std::memcpy(d.cell, h->geom.cell, sizeof(d.cell));
+  d.natoms = h->geom.natoms;
+  d.pos = h->d_pos0.data();
+  d.species = h->species_host.data();
+  d.nspecies = h->geom.nspecies;
+  d.sp = h->d_sp.data();
+  d.n1 = h->geom.n1;
+  d.n2 = h->geom.n2;
+  d.n3 = h->geom.n3;
+  d.skin = h->d_skin;
+  gint_handle *t = nullptr;
+  int rc = create_impl(&d, true, &t);
+  if (rc) return rc;
+  if (h->pos_host != h->d_pos0) {
+    rc = gint_set_positions(t, h->pos_dev, h->own_stream);
+    if (rc) {
+      gint_destroy(t);
+      return rc;
+    }
+  }
+  if (t->nblock != h->nblock || t->npairs != h->npairs) {
+    gint_destroy(t);
+    return GINT_EDEVICE;
+  }
+  h->twin = t;
+  return GINT_OK;
+}
+
+// The handle whose local-H tiles give H(R), with its key tables built: h itself, or, when some
+// brick of h sees two images of one atom (its tiles mix several R), h's unfolded twin.
+int hr_handle(gint_handle *h, gint_handle **t) {
+  *t = h;
+  if (h->folded && !h->unfold) {
+    const int rc = make_twin(h);
+    if (rc) return rc;
+    *t = h->twin;
+  }
+  return gint_hr_prepare(*t);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gint_create(const gint_desc *d, gint_handle **out) { return create_impl(d, false, out); }
+
 int gint_destroy(gint_handle *h) {
   if (!h) return GINT_OK;
   DeviceGuard guard(h->device);
@@ -424,7 +504,9 @@ int gint_memory(const gint_handle *h, long long *device_bytes) {
   b += h->cap_slots * 8 + (h->cap_slots + 1) * L + h->cap_ent * 3 * (long long)sizeof(double) +
        h->cap_pairtab * 4;                                                                  // neighbours
   b += 1024 * (long long)sizeof(double) + 16 * (long long)sizeof(double) + 16 + h->nblock * 4 + 16;  // workspace
-  *device_bytes = b + h->tc_bytes + h->r_bytes + h->pb_bytes;
+  long long twin = 0;
+  if (h->twin) gint_memory(h->twin, &twin);
+  *device_bytes = b + h->tc_bytes + h->r_bytes + h->pb_bytes + twin;
   return GINT_OK;
 }
 
@@ -444,6 +526,7 @@ int gint_set_positions(gint_handle *h, const double *pos_dev, void *stream) {
                       st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return GINT_ECUDA;
+  if (h->twin) return gint_set_positions(h->twin, pos_dev, stream);
   return GINT_OK;
 }
 
@@ -478,12 +561,13 @@ int gint_vlocal(gint_handle *h, int precision, const double *V, double *H_blocks
 int gint_layout_R(gint_handle *h, int *nkeys, long long *nblock_elems, const int **keys, const long long **key_off) {
   if (!h) return GINT_EINVAL;
   DeviceGuard guard(h->device);
-  const int rc = gint_hr_prepare(h);
+  gint_handle *t;
+  const int rc = hr_handle(h, &t);
   if (rc) return rc;
-  if (nkeys) *nkeys = h->r_nkeys;
-  if (nblock_elems) *nblock_elems = h->r_nblock;
-  if (keys) *keys = h->r_keys_host.data();
-  if (key_off) *key_off = h->r_off_host.data();
+  if (nkeys) *nkeys = t->r_nkeys;
+  if (nblock_elems) *nblock_elems = t->r_nblock;
+  if (keys) *keys = t->r_keys_host.data();
+  if (key_off) *key_off = t->r_off_host.data();
   return GINT_OK;
 }
 
@@ -492,20 +576,22 @@ int gint_vlocal_R(gint_handle *h, int precision, const double *V, double *H_R, v
   if (check_precision(precision)) return GINT_EINVAL;
   if (precision != GINT_F16X3 && precision != GINT_F16X1) return GINT_EUNSUPPORTED;
   DeviceGuard guard(h->device);
-  int rc = gint_hr_prepare(h);
+  gint_handle *t;
+  int rc = hr_handle(h, &t);
   if (rc) return rc;
-  h->reduce_R = true;
-  rc = gint_tc_vlocal(h, precision, V, H_R, (cudaStream_t)stream);  // every H(R) element is written
-  h->reduce_R = false;
+  t->reduce_R = true;
+  rc = gint_tc_vlocal(t, precision, V, H_R, (cudaStream_t)stream);  // every H(R) element is written
+  t->reduce_R = false;
   return rc;
 }
 
 int gint_bloch(gint_handle *h, const double *H_R, int nk, const double *kfrac, double *H_k, void *stream) {
   if (!h || !H_R || !kfrac || !H_k || nk < 0) return GINT_EINVAL;
   DeviceGuard guard(h->device);
-  const int rc = gint_hr_prepare(h);
+  gint_handle *t;
+  const int rc = hr_handle(h, &t);
   if (rc) return rc;
-  return gint_hr_bloch(h, H_R, nk, kfrac, H_k, (cudaStream_t)stream);
+  return gint_hr_bloch(t, H_R, nk, kfrac, H_k, (cudaStream_t)stream);
 }
 
 int gint_set_projectors(gint_handle *h, int nspecies, const gint_species *proj) {

@@ -51,6 +51,20 @@ struct gint_handle {
   long long cap_slots = 0, cap_ent = 0, cap_pairtab = 0;
   long long nslots = 0, nent = 0, npairtab = 0;
   int max_brick_orb = 0, max_brick_atoms = 0, max_brick_ent = 0;
+  // Slots and lattice images.  Normally a slot is an atom with every image of it that reaches the
+  // brick (the images share one set of columns: Gamma point).  With `unfold` each (atom, image)
+  // entry is a slot of its own, ordered by atom and then by the image's lattice vector, so that a
+  // local-H tile of two slots belongs to one R.  `folded`: some slot of the current lists has
+  // several images.
+  bool unfold = false;
+  bool folded = false;
+  gint_handle *twin = nullptr;  // unfolded twin of a folded handle (built on first per-R use)
+  // host copy of the descriptor's species and radial tables (to build the twin)
+  std::vector<gint_species> d_sp;
+  std::vector<gint_radial> d_rad;
+  std::vector<std::vector<double>> d_tab;
+  std::vector<double> d_pos0;  // positions at creation (they fixed the pair set)
+  double d_skin = 0;
   double W = 0, W_exec = 0;
   // workspace
   float *D32 = nullptr;       // float32 copy of D blocks (FP32 SIMT mode)

@@ -7,8 +7,12 @@
 // image, the tile of slots a, c is entirely the contribution of the image pair (tau_I + n_a A,
 // tau_J + n_c A) and so belongs to H_IJ(R) with R = n_c - n_a.  These tables key the tiles by
 // (I, J, R) instead of (I, J); the per-pair reduction kernel then sums them in the same fixed brick
-// order into H(R) blocks.  A geometry where some brick sees two images of one atom (a cell shorter
-// than about 2 rc plus a brick) has tiles that mix several R: per-R output is not available there.
+// order into H(R) blocks.  Where some brick sees two images of one atom (a cell shorter than about
+// 2 rc plus a brick) the folded tiles mix several R; such a handle computes H(R) on its unfolded
+// twin, whose slots are single (atom, image) entries ordered by atom and then by lattice vector.
+// There a tile of two images of one atom (slots a < c) has R = n_c - n_a > 0 in lexicographic
+// order, so every tile still maps to an upper key: I < J, or I == J with R >= 0; the key (I, I, -R)
+// gets the transpose.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -176,6 +180,9 @@ int gint_hr_prepare(gint_handle *h) {
         const int I = satom[s0 + a], J = satom[s0 + c];
         if (find_pair(I, J) >= 0) {
           const Key k{I, J, sn[s0 + c][0] - sn[s0 + a][0], sn[s0 + c][1] - sn[s0 + a][1], sn[s0 + c][2] - sn[s0 + a][2]};
+          // slots are ordered by atom, then by lattice vector: an upper key by construction
+          if (I > J || (I == J && std::array<int, 3>{k[2], k[3], k[4]} < std::array<int, 3>{0, 0, 0}))
+            return GINT_EDEVICE;
           contrib[k].push_back(hs_off[b] + rowst + (long long)po[a] * (cum_c - cum_a));
         }
         cum_c += po[c];
@@ -189,7 +196,7 @@ int gint_hr_prepare(gint_handle *h) {
   for (const auto &kv : contrib) {
     const Key &k = kv.first;
     index[k] = 0;
-    if (k[0] != k[1]) index[Key{k[1], k[0], -k[2], -k[3], -k[4]}] = 0;
+    if (k[0] != k[1] || k[2] || k[3] || k[4]) index[Key{k[1], k[0], -k[2], -k[3], -k[4]}] = 0;
   }
   const int nk = (int)index.size();
   std::vector<int> kI(nk), kJ(nk), kT(nk), kn(3 * (size_t)nk), gk_off(h->npairs + 1, 0);

@@ -4,7 +4,9 @@
 // The grid is cut into bricks of 4 x 4 x 8 points.  An (atom, lattice image) entry belongs
 // to a brick when at least one of the brick's grid points lies strictly inside the atom's
 // support sphere (exact per-point test, float64).  Entries of one atom form a "slot": its
-// orbitals occupy one set of columns in the brick (periodic images folded, Gamma point).
+// orbitals occupy one set of columns in the brick (periodic images folded, Gamma point).  In the
+// unfolded layout (the per-R twin of a folded handle) every entry is a slot of its own, in the same
+// order (atom, then lattice vector (n1, n2, n3) ascending).
 // Each brick also gets an n_a x n_a table of global pair indices for its slots.
 #include <cuda_runtime.h>
 
@@ -112,7 +114,8 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
 }
 
 // One warp per brick: number of slots, entries and orbitals.
-__global__ void k_brick_count(GGeom g, const double *pos, const int *species, int *n_at, int *n_ent, int *n_orb) {
+__global__ void k_brick_count(GGeom g, const double *pos, const int *species, int unfold, int *n_at, int *n_ent,
+                              int *n_orb) {
   const int lane = threadIdx.x & 31;
   const long long b = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (b >= g.nbricks) return;
@@ -125,9 +128,10 @@ __global__ void k_brick_count(GGeom g, const double *pos, const int *species, in
     int I = a0 + lane;
     int cnt = 0;
     if (I < g.natoms) cnt = brick_atom_images(g, pos, species, I, lo, hi, c, rad, NoEmit());
-    at += __popc(__ballot_sync(0xffffffffu, cnt > 0));
+    const int slots = unfold ? cnt : (cnt > 0);
+    at += (int)warp_sum_ll(slots);
     ent += (int)warp_sum_ll(cnt);
-    orb += (int)warp_sum_ll(cnt > 0 ? g.sp[species[I < g.natoms ? I : 0]].norb : 0);
+    orb += (int)warp_sum_ll(slots * g.sp[species[I < g.natoms ? I : 0]].norb);
   }
   if (lane == 0) {
     n_at[b] = at;
@@ -185,7 +189,7 @@ __global__ void k_brick_scan(long long nb, const int *n_at, const int *n_ent, co
 }
 
 // One warp per brick: writes slots (atom, column, first entry) and entries (image shifts).
-__global__ void k_brick_fill(GGeom g, const double *pos, const int *species, const long long *at_off,
+__global__ void k_brick_fill(GGeom g, const double *pos, const int *species, int unfold, const long long *at_off,
                              const long long *ent_off, int *s_atom, int *s_col, long long *s_ent, double *e_shift,
                              unsigned *err) {
   const int lane = threadIdx.x & 31;
@@ -202,19 +206,20 @@ __global__ void k_brick_fill(GGeom g, const double *pos, const int *species, con
     int I = a0 + lane;
     int cnt = 0;
     if (I < g.natoms) cnt = brick_atom_images(g, pos, species, I, lo, hi, c, rad, NoEmit());
-    unsigned bal = __ballot_sync(0xffffffffu, cnt > 0);
-    int my_slot = __popc(bal & ((1u << lane) - 1u));
+    const int nsl = unfold ? cnt : (cnt > 0);  // slots of this atom
+    int my_slot = warp_excl_scan(nsl, lane);
     int my_ent = warp_excl_scan(cnt, lane);
     int no = (cnt > 0) ? g.sp[species[I]].norb : 0;
-    int my_col = warp_excl_scan(no, lane);
+    int my_col = warp_excl_scan(nsl * no, lane);
     if (cnt > 0) {
       long long k = slot + my_slot;
       long long e0 = ent + my_ent;
-      if (k < slot_end) {
-        s_atom[k] = I;
-        s_col[k] = col + my_col;
-        s_ent[k] = e0;
-      }
+      for (int j = 0; j < nsl; ++j)
+        if (k + j < slot_end) {
+          s_atom[k + j] = I;
+          s_col[k + j] = col + my_col + j * no;
+          s_ent[k + j] = e0 + j;
+        }
       long long e = e0;
       brick_atom_images(g, pos, species, I, lo, hi, c, rad, [&](const double *T) {
         if (e < ent_end) {
@@ -225,9 +230,9 @@ __global__ void k_brick_fill(GGeom g, const double *pos, const int *species, con
         ++e;
       });
     }
-    slot += __popc(bal);
+    slot += warp_sum_ll(nsl);
     ent += warp_sum_ll(cnt);
-    col += (int)warp_sum_ll(no);
+    col += (int)warp_sum_ll(nsl * no);
   }
   if (lane == 0 && (slot != slot_end || ent != ent_end)) atomicOr(err, GINT_ERRBIT_INDEX);
 }
@@ -326,7 +331,8 @@ int gint_build_neighbours(gint_handle *h, cudaStream_t st) {
   const long long nb = g.nbricks;
   const int wpb = 4;  // warps (bricks) per CTA
   const unsigned nblk = (unsigned)((nb + wpb - 1) / wpb);
-  k_brick_count<<<nblk, 32 * wpb, 0, st>>>(g, h->pos_dev, h->species_dev, h->n_at, h->n_ent, h->n_orb);
+  k_brick_count<<<nblk, 32 * wpb, 0, st>>>(g, h->pos_dev, h->species_dev, h->unfold ? 1 : 0, h->n_at, h->n_ent,
+                                           h->n_orb);
   NBR_CHECK(cudaGetLastError());
   k_brick_scan<<<1, 1024, 0, st>>>(nb, h->n_at, h->n_ent, h->n_orb, h->b_at_off, h->b_ent_off, h->b_pair_off,
                                    h->scan_out);
@@ -341,12 +347,13 @@ int gint_build_neighbours(gint_handle *h, cudaStream_t st) {
   h->max_brick_atoms = (int)tot[4];
   h->W_exec = (double)tot[5];
   h->max_brick_ent = (int)tot[6];
+  h->folded = h->nent != h->nslots;  // some slot holds several images
   if (h->max_brick_atoms > GINT_MAX_ATOMS_BRICK) return GINT_ECAPACITY;
   int rc = gint_reserve_nbr(h);
   if (rc) return rc;
   NBR_CHECK(cudaMemsetAsync(h->err_word, 0, sizeof(unsigned), st));
-  k_brick_fill<<<nblk, 32 * wpb, 0, st>>>(g, h->pos_dev, h->species_dev, h->b_at_off, h->b_ent_off, h->s_atom,
-                                          h->s_col, h->s_ent, h->e_shift, h->err_word);
+  k_brick_fill<<<nblk, 32 * wpb, 0, st>>>(g, h->pos_dev, h->species_dev, h->unfold ? 1 : 0, h->b_at_off,
+                                          h->b_ent_off, h->s_atom, h->s_col, h->s_ent, h->e_shift, h->err_word);
   NBR_CHECK(cudaGetLastError());
   // sentinel: s_ent[nslots] = nent
   NBR_CHECK(cudaMemcpyAsync(h->s_ent + h->nslots, h->b_ent_off + nb, sizeof(long long), cudaMemcpyDeviceToDevice, st));

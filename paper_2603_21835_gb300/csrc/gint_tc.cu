@@ -1409,8 +1409,9 @@ struct GRed {
 // scratch tiles are column-major, norb(J) columns of norb(I) rows, element e = j norb(I) + i), summed
 // as double-float pairs (two-sum: error-free additions into a hi + lo pair of float32, relative error
 // about n^2 2^-48 for n bricks, far below the float32 rounding of the tiles themselves) and combined
-// in float64; H_JI = H_IJ^T.  A thread sums kRedE elements of the block (stride kRedLanes) over one of
-// kRedGroups contiguous parts of the pair's brick list, kRedB bricks' loads in flight; the parts'
+// in float64; H_JI = H_IJ^T (per R: H_JI(-R) = H_IJ(R)^T, also for I == J, R != 0).  A thread
+// sums kRedE elements of the block (stride kRedLanes) over one of kRedGroups contiguous parts of
+// the pair's brick list, kRedB bricks' loads in flight; the parts'
 // sums are then combined in part order (the result does not depend on scheduling).  A float64 sum
 // of every tile value would cost more than the brick pass itself on this GPU (float64 runs at about
 // 1/64 of the float32 rate), so the float64 step is the final combination only.
@@ -1487,7 +1488,7 @@ __device__ __forceinline__ void reduce_pair(const GTabs &g, const GRedSys &S, in
           acc += (double)part_hi[(g2 * kRedE + q) * kRedLanes + ln] + (double)part_lo[(g2 * kRedE + q) * kRedLanes + ln];
         const int j = e[q] / nI, i = e[q] - j * nI;
         S.H[S.pair_off[p] + (long long)i * nJ + j] = acc;
-        if (I != J) S.H[S.pair_off[S.pair_T[p]] + (long long)j * nI + i] = acc;
+        if (S.pair_T[p] != p) S.H[S.pair_off[S.pair_T[p]] + (long long)j * nI + i] = acc;  // (J, I, -R)
       }
     }
     bar_sync(bar, NG * kRedLanes);

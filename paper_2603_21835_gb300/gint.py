@@ -399,8 +399,8 @@ class Gint:
     def layout_R(self):
         """Keys of the local H per lattice vector (paper Sec. 2, H(R)): (keys [nkeys, 5] int32 rows
         (I, J, n1, n2, n3) with R = n1 a1 + n2 a2 + n3 a3, sorted; key_off [nkeys + 1] element offsets
-        of the norb(I) x norb(J) row-major blocks).  Raises GintError (GINT_EUNSUPPORTED) when some
-        brick sees two images of one atom."""
+        of the norb(I) x norb(J) row-major blocks).  Where some brick sees two images of one atom, the
+        library computes H(R) on an unfolded twin of the handle (built here on first use)."""
         nk, nel = _i(), _ll()
         kp, op = ctypes.POINTER(_i)(), ctypes.POINTER(_ll)()
         _check(_lib.gint_layout_R(self._h, ctypes.byref(nk), ctypes.byref(nel), ctypes.byref(kp), ctypes.byref(op)),
@@ -503,6 +503,7 @@ class Gint:
         _check(_lib.gint_set_positions(self._h, _dptr(pos, numel=3 * self.natoms), _stream(stream)),
                "gint_set_positions")
         self._pos_dev = pos.clone()
+        self.__dict__.pop("nblock_R", None)  # H(R) keys follow the new images
 
     def ensure_positions(self, pos: torch.Tensor, stream=None):
         """Rebuilds the neighbour lists only if pos differs from the current geometry."""
