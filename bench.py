@@ -42,6 +42,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # nominal float64 rate of GB300 (no fast float64 tensor path)
 FP64_NOMINAL_TFLOPS = 1.25
 FP32_SIMT_TFLOPS_PER_GHZ = 152 * 128 * 2 / 1e3  # 152 SMs x 128 FP32 lanes x 2 flops per clock
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 float64 (CUDA cores), nominal
 
 
 def parse():
@@ -452,12 +453,20 @@ def run_cn(n, nocc, steps, stream):
     # tensor-core build: tiles I <= J of 128 x 128, K padded to 64, three float16 products per term
     T, kp = (n + 127) // 128, (2 * nocc + 63) // 64 * 64
     tc_flops = 3 * 2.0 * 128 * 128 * kp * (T * (T + 1) // 2)
-    # complex float64 flops: ZGEMM 8 n^2 nocc, LU 8/3 n^3, triangular solves 8 n^2 nocc; D: 8 n^2 nocc
-    fl_step = 8.0 * n * n * nocc + 8.0 / 3.0 * n ** 3 + 8.0 * n * n * nocc
-    return {"n": n, "nocc": nocc, "ms_step": ms_s, "step_tflops": fl_step / (ms_s * 1e-3) / 1e12,
-            "ms_density_matrix": ms_d, "dm_tflops": 8.0 * n * n * nocc / (ms_d * 1e-3) / 1e12,
-            # real float64: DGEMM 2 n^3, Cholesky n^3 / 3, two triangular solves 2 n^3
-            "ms_energy_density_matrix": ms_e, "edm_tflops": (4.0 + 1.0 / 3.0) * n ** 3 / (ms_e * 1e-3) / 1e12,
+    # float64 flops executed by the library's kernels: step = S psi (two real GEMMs, 4 n^2 nocc),
+    # complex L D L^T (n^3 / 6 complex multiply-adds = 4/3 n^3), two triangular solves (8 n^2 nocc);
+    # D = lower triangle of a real GEMM with K = 2 nocc (2 n^2 nocc); E = H D (2 n^3), real L D L^T
+    # (n^3 / 3), solves with n right-hand sides (2 n^3)
+    fl_step = 12.0 * n * n * nocc + 4.0 / 3.0 * n ** 3
+    fl_d, fl_e = 2.0 * n * n * nocc, (4.0 + 1.0 / 3.0) * n ** 3
+    step_tf, dm_tf, edm_tf = (fl / (ms * 1e-3) / 1e12 for fl, ms in ((fl_step, ms_s), (fl_d, ms_d), (fl_e, ms_e)))
+    return {"n": n, "nocc": nocc, "ms_step": ms_s, "step_tflops": step_tf,
+            "ms_density_matrix": ms_d, "dm_tflops": dm_tf,
+            "ms_energy_density_matrix": ms_e, "edm_tflops": edm_tf,
+            "fp64": {"kernels": "k_gemm, k_ldl_diag, k_trsv (hand-written float64 on the CUDA cores)",
+                     "bound": "fp64", "peak_tflops": FP64_NOMINAL_TFLOPS, "peak_source": "nominal (none measured)",
+                     "step_frac": step_tf / FP64_NOMINAL_TFLOPS, "dm_frac": dm_tf / FP64_NOMINAL_TFLOPS,
+                     "edm_frac": edm_tf / FP64_NOMINAL_TFLOPS},
             "ms_density_matrix_f16x3": ms_t, "dm_f16x3_tflops_real_part": 4.0 * n * n * nocc / (ms_t * 1e-3) / 1e12,
             "dm_f16x3_tensor_tflops": tc_flops / (ms_t * 1e-3) / 1e12,
             "solver_info": info, "precision": "c128 / f64; f16x3 tensor-core D build"}

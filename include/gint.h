@@ -211,17 +211,20 @@ int gint_psibeta_layout(const gint_handle *h, int *npairs, long long *nelems, co
 int gint_psibeta(gint_handle *h, const double *A, double *out, void *stream);
 
 /* Dense steps of real-time propagation around the grid passes (paper Sec. 2): the density matrix
- * from coefficients and occupations, and one Crank-Nicolson step of the coefficients.  Plain library
- * operations (complex GEMMs and an LU factorisation with partial pivoting, cuBLAS / cuSOLVER loaded
- * on first use; GINT_EUNSUPPORTED from gint_cn_create if they cannot be loaded).  A context holds all
+ * from coefficients and occupations, and one Crank-Nicolson step of the coefficients, in float64 on
+ * the library's own kernels (a tiled GEMM, a blocked L D L^T factorisation without pivoting and its
+ * triangular solves).  A context holds all
  * buffers for an n x n problem with nocc states (allocated by gint_cn_create on the current device),
  * so the compute calls allocate nothing.  Matrices are float64 n x n, symmetric (any order); psi is
  * complex float64 n x nocc column-major (state j is psi[j n .. j n + n)), re / im interleaved; all
  * device pointers, caller-owned; the calls are asynchronous on `stream` and must not run
  * concurrently on one context.
  *
- * gint_cn_step: psi_out = (S + i dt/2 H)^{-1} (S - i dt/2 H) psi (psi_out must not alias psi).
- * gint_dm_build: D = Re(psi diag(f) psi^dagger), f [nocc] (device) occupations.
+ * gint_cn_step: psi_out = (S + i dt/2 H)^{-1} (S - i dt/2 H) psi (psi_out must not alias psi),
+ * computed as 2 X - psi with (S + i dt/2 H) X = S psi; S + i dt/2 H (complex symmetric, positive
+ * definite Hermitian part S) is factored as L D L^T without pivoting.
+ * gint_dm_build: D = Re(psi diag(f) psi^dagger), f [nocc] (device) occupations; D is symmetric bit
+ * for bit.
  * gint_dm_build_f16x3: the same D on the tensor cores: D = A B^T with A_ik = f_s psi_is, B_ik = psi_is
  * (k = 2 s + real / imaginary part), each operand scaled by a power of two and split into float16
  * hi + lo, three float16 products per term (lo lo dropped).  The hi hi products of each chunk of 64 k
@@ -230,7 +233,8 @@ int gint_psibeta(gint_handle *h, const double *A, double *out, void *stream);
  * bit; its error stays within about 3 * 2^-22 of max_i sum_s |f_s| |psi_is|^2 (measured up to
  * 2.8e-7).  Occupations of any sign; psi 16-byte aligned (as for every complex128 array here); no
  * allocation.
- * gint_cn_info: the LAPACK-style info of the last factorisation (0: success; i > 0: U(i, i) = 0);
+ * gint_cn_info: the LAPACK-style info of the last factorisation (0: success; i > 0: the pivot d_i of
+ * L D L^T is zero or not finite, or for gint_edm not positive);
  * synchronous; returns GINT_ETIMEDOUT (once) when a bounded wait of the tensor-core build gave up.  The
  * D of that call is then undefined; and since a CTA whose final completion wait also gave up releases
  * its tensor memory with MMAs possibly still in flight, destroy the context after GINT_ETIMEDOUT rather
@@ -245,8 +249,9 @@ int gint_dm_build_f16x3(gint_cn *c, const double *psi, const double *f, double *
 int gint_cn_info(gint_cn *c, int *info);
 
 /* Energy-density matrix E = (S^{-1} H D + D H S^{-1}) / 2 (the overlap part of the forces needs it):
- * S (positive definite), H, D real symmetric n x n (device), E (device, overwritten); a Cholesky
- * solve with the context's buffers (gint_cn_info reports a non-positive pivot as i > 0). */
+ * S (positive definite), H, D real symmetric n x n (device), E (device, overwritten); X = H D, then
+ * S X' = X by L D L^T of S, E = (X' + X'^T) / 2 (bit-for-bit symmetric), with the context's buffers
+ * (gint_cn_info reports a non-positive pivot as i > 0). */
 int gint_edm(gint_cn *c, const double *S, const double *H, const double *D, double *E, void *stream);
 
 /* Local Pulay forces F [natoms][3] (device, overwritten) = -dE/dtau for E = sum_g w V rho.

@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libgint.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gint_capi.cu", "gint_nbr.cu", "gint_simt.cu", "gint_tc.cu", "gint_noalloc.cu", "gint_hr.cu", "gint_pb.cu", "gint_cn.cu", "gint_dm.cu"]
+SOURCES = ["gint_capi.cu", "gint_nbr.cu", "gint_simt.cu", "gint_tc.cu", "gint_noalloc.cu", "gint_hr.cu", "gint_pb.cu", "gint_cn.cu", "gint_dm.cu",
+           "gint_la.cu"]
 
 
 def nvcc() -> str:
@@ -28,13 +29,9 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _cuda_lib_dir() -> str:
-    return os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc()))), "lib64")
-
-
 def _flags(verbose: bool):
     f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--extended-lambda", "-Xcompiler", "-fPIC",
-                "-I", INCLUDE, "-I", CSRC, f'-DGINT_CUDA_LIB_DIR="{_cuda_lib_dir()}"']
+                "-I", INCLUDE, "-I", CSRC]
     if verbose:
         f += ["-Xptxas", "-v"]
     return f
@@ -66,7 +63,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if verbose and err:
                 sys.stderr.write(err)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart", "-ldl"]
+    cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

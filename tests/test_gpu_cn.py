@@ -1,5 +1,6 @@
 """GPU parity of the density-matrix build, the Crank-Nicolson step (paper Sec. 2) and the energy-
-density matrix against the LAPACK oracle (oracle/dense.py), all in float64: 1e-12 of the largest
+density matrix (the library's own float64 GEMM and blocked L D L^T kernels) against the LAPACK oracle
+(oracle/dense.py, LU with partial pivoting and Cholesky), all in float64: 1e-12 of the largest
 entry; the tensor-core density-matrix build (float16 three-term split) within 1e-6 of
 max_i sum_s |f_s| |psi_is|^2; and the loop rho -> H -> psi -> rho closed on the 8-atom Si cell with
 the grid library's own passes."""
@@ -21,12 +22,13 @@ def _matrices(n, seed):
     return S, 0.5 * (G + G.T)
 
 
-def test_step_and_density_matrix_match_the_oracle():
+@pytest.mark.parametrize("n,k", [(832, 64), (130, 3), (1601, 33)])
+def test_step_and_density_matrix_match_the_oracle(n, k):
+    """Sizes on and off the 64-wide blocks of the factorisation and of the GEMM tiles."""
     import torch
 
     from paper_2603_21835_gb300 import gint as G
 
-    n, k = 832, 64
     S, H = _matrices(n, 0)
     rng = np.random.default_rng(1)
     psi = rng.normal(size=(n, k)) + 1j * rng.normal(size=(n, k))
@@ -41,15 +43,16 @@ def test_step_and_density_matrix_match_the_oracle():
     assert np.abs(out - ref).max() <= 1e-12 * np.abs(ref).max()
     Dref = density_matrix(psi, f)
     assert np.abs(D - Dref).max() <= 1e-12 * np.abs(Dref).max()
+    assert np.array_equal(D, D.T)  # lower triangle computed and mirrored
     cn.close()
 
 
-def test_energy_density_matrix_matches_the_oracle():
+@pytest.mark.parametrize("n", [832, 130, 1601])
+def test_energy_density_matrix_matches_the_oracle(n):
     import torch
 
     from paper_2603_21835_gb300 import gint as G
 
-    n = 832
     S, H = _matrices(n, 2)
     G_ = np.random.default_rng(3).normal(size=(n, n))
     D = 0.5 * (G_ + G_.T)
@@ -59,6 +62,27 @@ def test_energy_density_matrix_matches_the_oracle():
     ref = energy_density_matrix(S, H, D)
     assert np.abs(E - ref).max() <= 1e-12 * np.abs(ref).max()
     assert np.abs(E - E.T).max() == 0.0
+    cn.close()
+
+
+def test_energy_density_matrix_reports_a_non_positive_pivot():
+    """S with a negative eigenvalue in its 70th leading block: the factorisation's info names the
+    first non-positive pivot (the 70th, in the second 64-wide block)."""
+    import torch
+
+    from paper_2603_21835_gb300 import gint as G
+
+    n = 100
+    S = np.eye(n)
+    S[69, 69] = -1.0
+    H, D = np.eye(n), np.eye(n)
+    cn = G.CrankNicolson(n, 4)
+    cn.energy_density_matrix(*(torch.from_numpy(x).cuda() for x in (S, H, D)))
+    assert cn.info() == 70
+    # the next call starts from a clean info word
+    S[69, 69] = 2.0
+    cn.energy_density_matrix(*(torch.from_numpy(x).cuda() for x in (S, H, D)))
+    assert cn.info() == 0
     cn.close()
 
 
