@@ -67,13 +67,13 @@ def parse():
     return ap.parse_args()
 
 
-def profiled_traffic(workload: str, precision: str):
-    """DRAM bytes per launch of the brick kernel from a committed ncu summary under profiles/,
-    if one was taken on this workload and precision with the current kernel source; else None."""
+def profiled(workload: str, precision: str, source: str, key: str):
+    """A figure (`key`) from a committed ncu summary under profiles/, if one was taken on this workload
+    (None: any) and precision with the current source of the kernel (csrc/`source`); else None."""
     import glob
     import hashlib
 
-    src = os.path.join(ROOT, "paper_2603_21835_gb300", "csrc", "gint_tc.cu")
+    src = os.path.join(ROOT, "paper_2603_21835_gb300", "csrc", source)
     with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
@@ -81,13 +81,19 @@ def profiled_traffic(workload: str, precision: str):
         with open(path) as f:
             for line in f:
                 parts = line.strip().split(": ", 1)
-                if len(parts) == 2 and parts[0] in ("workload", "precision", "kernel_source_sha256",
-                                                    "traffic_bytes_per_launch"):
+                if len(parts) == 2 and parts[0] in ("workload", "precision", "kernel_source", "kernel_source_sha256", key):
                     kv[parts[0]] = parts[1].strip()
-        if (kv.get("workload") == workload and kv.get("precision") == precision
-                and kv.get("kernel_source_sha256") == sha and "traffic_bytes_per_launch" in kv):
-            return int(kv["traffic_bytes_per_launch"]), os.path.relpath(path, ROOT)
+        if ((workload is None or kv.get("workload") == workload) and kv.get("precision") == precision
+                and kv.get("kernel_source", "gint_tc.cu") == source
+                and kv.get("kernel_source_sha256") == sha and key in kv):
+            return float(kv[key]), os.path.relpath(path, ROOT)
     return None, None
+
+
+def profiled_traffic(workload: str, precision: str):
+    """DRAM bytes per launch of the brick kernel (ncu), if profiled with the current source."""
+    v, path = profiled(workload, precision, "gint_tc.cu", "traffic_bytes_per_launch")
+    return (int(v) if v is not None else None), path
 
 
 def max_over_ranks(value: float, world: int, device=None) -> float:
@@ -365,7 +371,7 @@ def run_per_R(g, V, prec, steps, stream, flush, hbm_gbs):
             "bloch_frac_of_hbm": gbs / hbm_gbs if hbm_gbs else None}
 
 
-def run_psibeta(g, system, steps, stream):
+def run_psibeta(g, system, steps, stream, workload):
     """Velocity-gauge projector overlaps <beta| e^{-i A.r} |Phi> (float64, spherical grids of 140 x 162
     points around every projector atom) for every (projector atom, orbital atom) pair of the workload:
     mean time of gint_psibeta with Si projectors (one s and one p channel)."""
@@ -389,8 +395,17 @@ def run_psibeta(g, system, steps, stream):
     ms = e0.elapsed_time(e1) / steps
     npairs = int(len(g.pb_pairs))
     points = npairs * 140 * 162
+    # float64 roofline: the kernel's executed float64 flops (2 DFMA + DADD + DMUL), as the mean per pair
+    # counted by ncu with the current source on the 64-atom Si crystal (the same distribution of pair
+    # distances as any Si supercell), times the pairs, over the CUDA-event time, against the nominal rate
+    fpp, src = profiled(None, "f64", "gint_pb.cu", "fp64_flops_per_pair")
+    fl = None if fpp is None else fpp * npairs
+    roof = {"bound": "fp64", "kernel": "k_psibeta", "unit": "TFLOP/s", "peak": FP64_NOMINAL_TFLOPS,
+            "peak_source": "nominal (none measured)", "flops_source": src,
+            "achieved": None if fl is None else fl / (ms * 1e-3) / 1e12}
+    roof["frac"] = None if fl is None else roof["achieved"] / FP64_NOMINAL_TFLOPS
     return {"pairs": npairs, "elements": int(g.pb_nelems), "ms": ms, "pairs_per_s": npairs / (ms * 1e-3),
-            "grid_points_per_s": points / (ms * 1e-3), "precision": "f64",
+            "grid_points_per_s": points / (ms * 1e-3), "precision": "f64", "roofline": roof,
             "quadrature": "140 Gauss-Legendre radial x 162-point degree-17 product angular rule"}
 
 
@@ -674,7 +689,7 @@ def main():
 
     psibeta = None
     if rank == 0 and tensor and not args.no_extras:
-        psibeta = run_psibeta(g, w.system, 3, stream)
+        psibeta = run_psibeta(g, w.system, 3, stream, args.workload)
 
     cn = None
     if rank == 0 and tensor and not args.no_extras:
