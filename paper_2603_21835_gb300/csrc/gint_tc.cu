@@ -348,7 +348,10 @@ struct BrickSh {
   unsigned char col2slot[kNPMAX];
   double fpart[kMAXA][3];
   float rpart[4][128];
-  float rpartl[4][128];  // density epilogue: compensation terms of the groups' partial sums
+  union {
+    float rpartl[4][128];  // density epilogue: compensation terms of the groups' partial sums
+    double vd[128];        // force items: V at the brick's points, copied asynchronously (see wv)
+  };
   float wv[128];   // w V at the brick's points (local H, force)
   float rsc[128];  // force launches: power-of-two scale of each row of P (fixed-point split)
   double ob[3];    // brick origin (Cartesian)
@@ -720,6 +723,7 @@ struct ItemCtx {
   uint32_t dpar;  // bit c: phase parity of done[c] (used once per density brick that has a chunk c)
   uint32_t GH;    // local-H stages issued by this CTA
   bool ok;        // no bounded wait has given up
+  bool vpend;     // V of the brick's points is in flight to sh.vd (threads 0-127 each copy one value)
 };
 template <bool FORCE>
 __device__ __forceinline__ void brick_body(const GTabs &g, const GSys &S, long long b, bool do_rho, bool do_h,
@@ -744,6 +748,7 @@ __device__ __forceinline__ void brick_body(const GTabs &g, const GSys &S, long l
     const bool valid = brick_point(S.c, b, p, gi, gj, gk);
     const long long gidx = valid ? grid_index(S.c, gi, gj, gk) : 0;
     if (na == 0) {
+      if (cx.vpend && t < 128) cp_async_wait_all();  // no copy into sh.vd outlives the item
       if (do_rho && q == 0 && valid && S.rho) S.rho[gidx] = 0.0;
       return;
     }
@@ -921,6 +926,10 @@ case GINT_SHAPE(ns, np_, nd):                                                   
           *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
         }
     }
+    if (cx.vpend && t < 128) {  // the copy has had the orbital phase to land
+      cp_async_wait_all();
+      sh.wv[t] = (float)(S.c.w * sh.vd[t]);
+    }
     fence_async_smem();
     __syncthreads();
     if (do_rho) {
@@ -1008,11 +1017,12 @@ case GINT_SHAPE(ns, np_, nd):                                                   
         // chunk c's columns are final: rho += P_k Y_k
         const int k0 = c * kRC;
         float y[16], yc[16];
-        tmem_ld16(tmem + lane_base + k0, y);
         if (split3 && corr_base) {
-          tmem_ld16(tmem + lane_base + corr_base + k0, yc);
+          tmem_ld16x2(tmem + lane_base + k0, tmem + lane_base + corr_base + k0, y, yc);
 #pragma unroll
           for (int i = 0; i < 16; ++i) y[i] += yc[i];
+        } else {
+          tmem_ld16(tmem + lane_base + k0, y);
         }
         float part = 0.f;
 #pragma unroll
@@ -1067,11 +1077,12 @@ case GINT_SHAPE(ns, np_, nd):                                                   
         float y[GINT_MAX_ORB_ATOM], yc[16];
         for (int h = 0; h < po; h += 16) {
           if (po - h >= 16) {
-            tmem_ld16(tmem + lane_base + pc + h, y + h);
             if (split3 && corr_base) {
-              tmem_ld16(tmem + lane_base + corr_base + pc + h, yc);
+              tmem_ld16x2(tmem + lane_base + pc + h, tmem + lane_base + corr_base + pc + h, y + h, yc);
 #pragma unroll
               for (int i = 0; i < 16; ++i) y[h + i] += yc[i];
+            } else {
+              tmem_ld16(tmem + lane_base + pc + h, y + h);
             }
           } else {
             tmem_ld8(tmem + lane_base + pc + h, y + h);
@@ -1256,11 +1267,13 @@ case GINT_SHAPE(ns, np_, nd):                                                   
         const int N = NP - 128 * m;
         for (int gcol = qq; gcol < N / 16; gcol += 4) {
           float y[16], yc[16];
-          tmem_ld16(tmem + lane_base + tb[m] + gcol * 16, y);
           if (split3 && corr_base) {
-            tmem_ld16(tmem + lane_base + corr_base + tb[m] + gcol * 16, yc);
+            tmem_ld16x2(tmem + lane_base + tb[m] + gcol * 16, tmem + lane_base + corr_base + tb[m] + gcol * 16, y,
+                        yc);
 #pragma unroll
             for (int i = 0; i < 16; ++i) y[i] += yc[i];
+          } else {
+            tmem_ld16(tmem + lane_base + tb[m] + gcol * 16, y);
           }
           if (!rowok) continue;
 #pragma unroll
@@ -1360,7 +1373,16 @@ __global__ void __launch_bounds__(kT, 1)
       }
       cur = sidx;
     }
-    if (t < 128 && S.V && (do_h || FORCE)) {  // w V at the brick's points
+    // w V at the brick's points: force items copy V asynchronously (w V is formed after the
+    // orbitals; the force pass reads it only in its epilogue), the others load it here
+    const bool vpend = FORCE && S.V;
+    if (t < 128 && vpend) {
+      int gi, gj, gk;
+      if (brick_point(S.c, b, t, gi, gj, gk))
+        cp_async8(&sh.vd[t], S.V + grid_index(S.c, gi, gj, gk));
+      else
+        sh.vd[t] = 0.0;
+    } else if (t < 128 && S.V && do_h) {
       int gi, gj, gk;
       sh.wv[t] = brick_point(S.c, b, t, gi, gj, gk) ? (float)(S.c.w * S.V[grid_index(S.c, gi, gj, gk)]) : 0.f;
     }
@@ -1375,7 +1397,7 @@ __global__ void __launch_bounds__(kT, 1)
       load_brick(S.c, g, S.nb, S.tile_off, b, sh);  // ends with a barrier
     }
     if (t == 0) next_item();  // every thread has read sh.item and sh.plan_pref
-    ItemCtx cx{fpar, dpar, GH, ok};
+    ItemCtx cx{fpar, dpar, GH, ok, vpend};
     brick_body<FORCE>(g, S, b, do_rho, do_h, split3, B.dsmem, zero, tmem, sh, smem, cx);
     fpar = cx.fpar;
     dpar = cx.dpar;
