@@ -347,10 +347,16 @@ struct BrickSh {
   float pt_hi[128][3], pt_lo[128][3];    // grid point positions relative to the brick origin
   unsigned char col2slot[kNPMAX];
   double fpart[kMAXA][3];
-  float rpart[4][128];
+  union alignas(8) {
+    float rpart[4][128];  // density / force epilogues, fixed-point rows: per-slice partials of a point
+    // local-H epilogue (after those): per 8-column group h of the padded columns, (dense index of
+    // its first column among the brick's orbitals) << 4 | (its real columns), or -1 for padding
+    int hcol[kNPMAX / 8];
+  };
   union {
     float rpartl[4][128];  // density epilogue: compensation terms of the groups' partial sums
-    double vd[128];        // force items: V at the brick's points, copied asynchronously (see wv)
+    double vd[128];        // V at the brick's points, copied asynchronously (formed into wv after the
+                           // orbitals, before the density epilogue uses rpartl)
   };
   float wv[128];   // w V at the brick's points (local H, force)
   float rsc[128];  // force launches: power-of-two scale of each row of P (fixed-point split)
@@ -456,7 +462,9 @@ __host__ __device__ __forceinline__ long long plan_words(int na, int nent, int n
 }
 
 // Unpacks the record in sh.planbuf into the brick metadata (all threads; ends with a barrier).
-__device__ void unpack_plan(BrickSh &sh) {
+// wait_store: thread 0 also waits, before the closing barrier, until the previous item's bulk store
+// of local-H tiles has read shared memory (overlapping that store with the unpack).
+__device__ void unpack_plan(BrickSh &sh, bool wait_store = false) {
   const int t = threadIdx.x, nt = blockDim.x;
   const uint32_t *w = sh.planbuf;
   const int na = (int)w[0], nent = (int)w[1], np = (int)w[2];
@@ -493,6 +501,7 @@ __device__ void unpack_plan(BrickSh &sh) {
   for (int i = t; i < na * na; i += nt) sh.s_tile[i] = (int)w[tb + i];
   const unsigned char *cb = reinterpret_cast<const unsigned char *>(w + tb + na * na);
   for (int k = t; k < kNPMAX; k += nt) sh.col2slot[k] = k < np ? cb[k] : kNoSlot;
+  if (wait_store && t == 0) bulk_wait_read();
   __syncthreads();
 }
 
@@ -1141,6 +1150,15 @@ case GINT_SHAPE(ns, np_, nd):                                                   
       tc_fence_before();  // the density part's tensor-memory reads are finished
       __syncthreads();
       tc_fence_after();
+      for (int h8 = t; h8 < NP / 8; h8 += kT) {  // the epilogue's column table (read after the barriers below)
+        const int cs = sh.col2slot[8 * h8];
+        int v = -1;
+        if (cs != kNoSlot) {
+          const int j0 = 8 * h8 - sh.s_pcol[cs];
+          if (j0 < sh.s_no[cs]) v = ((sh.s_cumno[cs] + j0) << 4) | min(8, sh.s_no[cs] - j0);
+        }
+        sh.hcol[h8] = v;
+      }
       const float SA = sh.sc[2];
       const float out_scale = 1.f / (Sphi * SA);
       const float wscale = SA / Sphi;
@@ -1266,6 +1284,7 @@ case GINT_SHAPE(ns, np_, nd):                                                   
         float *rowp = stg + (rowok ? sh.s_rowst[as] : 0) + il;
         const int N = NP - 128 * m;
         for (int gcol = qq; gcol < N / 16; gcol += 4) {
+          const int2 hc = *reinterpret_cast<const int2 *>(&sh.hcol[16 * m + 2 * gcol]);
           float y[16], yc[16];
           if (split3 && corr_base) {
             tmem_ld16x2(tmem + lane_base + tb[m] + gcol * 16, tmem + lane_base + corr_base + tb[m] + gcol * 16, y,
@@ -1278,11 +1297,11 @@ case GINT_SHAPE(ns, np_, nd):                                                   
           if (!rowok) continue;
 #pragma unroll
           for (int hh = 0; hh < 2; ++hh) {
-            const int nu = 128 * m + gcol * 16 + 8 * hh;
-            const int cs = sh.col2slot[nu];
-            if (cs == kNoSlot || cs < as) continue;
-            const int j0 = nu - sh.s_pcol[cs], nj = min(8, sh.s_no[cs] - j0);
-            float *dst = rowp + no_a * (sh.s_cumno[cs] - cum_a + j0);
+            const int v = hh ? hc.y : hc.x;
+            const int cc = (v >> 4) - cum_a;  // < 0: a column slot before the row slot (lower triangle)
+            if (v < 0 || cc < 0) continue;
+            const int nj = v & 15;
+            float *dst = rowp + no_a * cc;
 #pragma unroll
             for (int i = 0; i < 8; ++i)
               if (i < nj) dst[i * no_a] = y[8 * hh + i] * out_scale;
@@ -1373,27 +1392,25 @@ __global__ void __launch_bounds__(kT, 1)
       }
       cur = sidx;
     }
-    // w V at the brick's points: force items copy V asynchronously (w V is formed after the
-    // orbitals; the force pass reads it only in its epilogue), the others load it here
-    const bool vpend = FORCE && S.V;
+    // w V at the brick's points: V is copied asynchronously (its DRAM latency would stall the set-up)
+    // and w V formed after the orbitals; the local-H pass and the force epilogue read it later
+    const bool vpend = S.V && (do_h || FORCE);
     if (t < 128 && vpend) {
       int gi, gj, gk;
       if (brick_point(S.c, b, t, gi, gj, gk))
         cp_async8(&sh.vd[t], S.V + grid_index(S.c, gi, gj, gk));
       else
         sh.vd[t] = 0.0;
-    } else if (t < 128 && S.V && do_h) {
-      int gi, gj, gk;
-      sh.wv[t] = brick_point(S.c, b, t, gi, gj, gk) ? (float)(S.c.w * S.V[grid_index(S.c, gi, gj, gk)]) : 0.f;
     }
     // the previous item's local-H tiles have left shared memory (its bulk store has read them)
-    // before this item writes any dynamic shared memory (the barriers of the unpack order it)
-    if (t == 0) bulk_wait_read();
+    // before this item writes any dynamic shared memory: thread 0 waits for that store before the
+    // closing barrier of the unpack (the unpack itself writes static shared memory only)
     if (pref) {  // prefetched plan record (the common case)
       if (!mbar_wait(&sh.plan_bar, pphase & 1u, S.err)) ok = false;
       ++pphase;
-      unpack_plan(sh);  // ends with a barrier
+      unpack_plan(sh, true);  // ends with a barrier
     } else {
+      if (t == 0) bulk_wait_read();
       load_brick(S.c, g, S.nb, S.tile_off, b, sh);  // ends with a barrier
     }
     if (t == 0) next_item();  // every thread has read sh.item and sh.plan_pref
@@ -2195,6 +2212,21 @@ __global__ void __launch_bounds__(128, 1) k_tc_selftest(int N, float *err_out, u
 
 inline uint32_t rho_smem_bytes(int np, int nstages) { return 128u * np * 4 + (uint32_t)nstages * np * kRC * 4; }
 
+// The dynamic shared memory a kernel can have next to its static shared memory (the static part
+// rounded up to the 1024-byte alignment of the dynamic region), in whole KB.
+template <typename K>
+uint32_t dyn_smem_limit(K kern) {
+  cudaFuncAttributes fa{};
+  int dev = 0, optin = 227 * 1024;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const size_t stat = (fa.sharedSizeBytes + 1023) & ~(size_t)1023;
+  return stat >= (size_t)optin ? 0u : (uint32_t)(((size_t)optin - stat) & ~(size_t)1023);
+}
+
 template <typename K>
 int set_smem(K kern, uint32_t bytes) {
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
@@ -2532,7 +2564,7 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
   // halves of the local-H pass) | tail pad read by the last 128-row A tile above NP
   // all the shared memory a CTA may have: items lay out P and as many stages as fit for their own
   // width (at least two stages at the widest brick of the launch)
-  const uint32_t smem = (uint32_t)(227 * 1024 - sizeof(BrickSh)) & ~1023u;
+  static const uint32_t smem = std::min(dyn_smem_limit(k_tc_fused<false>), dyn_smem_limit(k_tc_fused<true>));
   if (rho_smem_bytes(np, 2) + kHTail > smem) return GINT_ECAPACITY;
   B.np_max = np;
   B.split3 = split3;
@@ -2682,8 +2714,7 @@ extern "C" int gint_server_create(int precision, int forces, double idle_s, gint
     server_free(v);
     return GINT_ECUDA;
   }
-  const size_t stat = sizeof(BrickSh) + sizeof(GJob) + 64;
-  v->dsmem = (int)((227 * 1024 - stat) & ~(size_t)1023);
+  v->dsmem = (int)std::min(dyn_smem_limit(k_serve<false>), dyn_smem_limit(k_serve<true>));
   bool okm = cudaMalloc(&v->ctl, sizeof(GServeCtl)) == cudaSuccess &&
              cudaMalloc(&v->jobs, kServeRing * sizeof(GJob)) == cudaSuccess &&
              cudaMalloc(&v->st, kServeRing * sizeof(GJobState)) == cudaSuccess &&
