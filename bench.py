@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=256, help="Poisson serving run (0: skip)")
     ap.add_argument("--serve-load", type=float, default=0.75, help="arrival rate x mean service time alone")
     ap.add_argument("--serve-budget-gb", type=float, default=32.0)
+    ap.add_argument("--serve-replicas", type=int, default=2,
+                    help="resident handles per geometry (each runs one job at a time)")
     return ap.parse_args()
 
 
@@ -261,7 +263,7 @@ def run_serving(args, prec, dev):
 
     pool = inputs.serving_pool()
     srv = serve.Server(inputs.serving_library(), budget_bytes=int(args.serve_budget_gb * (1 << 30)), precision=prec,
-                       device=dev)
+                       replicas=args.serve_replicas, device=dev)
     try:
         sessions = [srv.open(s) for s in pool]
         nvar = 4
@@ -320,6 +322,7 @@ def run_serving(args, prec, dev):
             "rate_hz": rate, "poisson": poisson, "burst": burst,
             "p50_ms": poisson["p50_ms"], "p99_ms": poisson["p99_ms"],
             "throughput_note": "2W per request (rho + H pair updates); the force pass is extra work not counted",
+            "replicas_per_geometry": args.serve_replicas,
             "budget_bytes": srv.budget.budget, "peak_bytes": srv.budget.peak, "errors": len(srv.errors),
             "resident_launches": srv.stats()["resident_launches"],
             "design": "device work queue: one resident launch drains jobs published while it runs",

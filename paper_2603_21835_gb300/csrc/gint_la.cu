@@ -84,7 +84,7 @@ struct GemmK<double2> {
 // ty + 16 b (a, b < 4), so a warp reads 16 consecutive elements of each shared operand row.  The
 // next K slab is loaded into registers while the current one is multiplied.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kGT) k_gemm(int M, int N, int K, double alpha, View<T> A, View<T> B, double beta,
+__global__ void __launch_bounds__(kGT, 2) k_gemm(int M, int N, int K, double alpha, View<T> A, View<T> B, double beta,
                                               T *__restrict__ C, long long cr, long long cc) {
   constexpr int BK = GemmK<T>::BK, NL = BK * kBM / kGT;
   const int tm = blockIdx.x, tn = blockIdx.y;
@@ -188,49 +188,59 @@ __global__ void __launch_bounds__(kGT) k_ldl_diag(int nb, T *__restrict__ A, lon
 }
 
 // ------------------------------------------------------------- unit-triangular multi-vector solves
-// Vectors v < nv, element j < nb at X[v vs + j es], one per thread (its values in shared memory,
-// [j][thread], conflict-free), the nb x nb block L (element (i, j) at L[i + j ldl]) in shared memory:
+// Vectors v < nv, element j < nb at X[v vs + j es]; the nb x nb block L (element (i, j) at
+// L[i + j ldl]) in shared memory:
 //   TRANS = false: L y = x (unit lower; forward), TRANS = true: L^T y = x (backward).
 // PANEL (forward only): the panel of the factorisation, W = y (work, element (v, j) at W[v + j ldw])
 // and x = y / d_j (d_j = the factor's diagonal, L[j + j ldl]).
-constexpr int kSV = 64;  // vectors per CTA
+// A CTA takes kSV vectors with one thread per (element, vector) and eliminates column by column (at
+// step j, y_j is final and every later element subtracts its multiple): the float64 work of a block
+// is spread over many CTAs and all four schedulers of an SM, where one thread per vector would leave
+// most of the GPU's float64 units idle (a float64 warp instruction occupies a scheduler's unit for
+// many cycles).
+constexpr int kSV = 8;                 // vectors per CTA
+constexpr int kSVT = kSV * 64;         // threads: (element < 64) x (vector < kSV)
 template <typename T, bool TRANS, bool PANEL>
-__global__ void __launch_bounds__(kSV) k_trsv(int nb, const T *__restrict__ L, long long ldl, int nv, T *__restrict__ X,
-                                              long long vs, long long es, T *__restrict__ W, long long ldw) {
+__global__ void __launch_bounds__(kSVT) k_trsv(int nb, const T *__restrict__ L, long long ldl, int nv, T *__restrict__ X,
+                                               long long vs, long long es, T *__restrict__ W, long long ldw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *Ls = reinterpret_cast<T *>(smem_raw);  // nb x nb, column-major
-  T *ys = Ls + nb * nb;                     // [j][thread]
-  const int tid = threadIdx.x, v = blockIdx.x * kSV + tid;
-  for (int e = tid; e < nb * nb; e += kSV) {
-    const int i = e % nb, j = e / nb;
-    Ls[e] = L[i + j * ldl];
+  T *Ls = reinterpret_cast<T *>(smem_raw);  // nb x nb: Ls[i + j nb] = L(i, j), or L(j, i) for TRANS
+  T *xs = Ls + nb * nb;                     // [vector][element]
+  const int tid = threadIdx.x, i = tid & 63, vl = tid >> 6, v = blockIdx.x * kSV + vl;
+  for (int e = tid; e < nb * nb; e += kSVT) {
+    const int r = e % nb, c = e / nb;
+    Ls[e] = TRANS ? L[c + (long long)r * ldl] : L[r + (long long)c * ldl];
   }
-  const bool act = v < nv;
-  T *x = X + (long long)(act ? v : 0) * vs;
-  for (int j = 0; j < nb; ++j) ys[j * kSV + tid] = act ? x[j * es] : Ar<T>::zero();
-  __syncthreads();
+  const bool act = v < nv && i < nb;
+  T *x = X + (long long)(v < nv ? v : 0) * vs;
+  T xi = act ? x[(long long)i * es] : Ar<T>::zero();
+  xs[vl * 64 + i] = xi;
+  // step j reads element j (final after the previous step's barrier) and writes elements != j only
   if (!TRANS) {
-    for (int j = 1; j < nb; ++j) {
-      T acc = ys[j * kSV + tid];
-      for (int k = 0; k < j; ++k) acc = Ar<T>::fms(Ls[j + k * nb], ys[k * kSV + tid], acc);
-      ys[j * kSV + tid] = acc;
+    for (int j = 0; j + 1 < nb; ++j) {
+      __syncthreads();
+      const T yj = xs[vl * 64 + j];
+      if (i > j && i < nb) {
+        xi = Ar<T>::fms(Ls[i + j * nb], yj, xi);
+        xs[vl * 64 + i] = xi;
+      }
     }
   } else {
-    for (int j = nb - 2; j >= 0; --j) {
-      T acc = ys[j * kSV + tid];
-      for (int k = j + 1; k < nb; ++k) acc = Ar<T>::fms(Ls[k + j * nb], ys[k * kSV + tid], acc);
-      ys[j * kSV + tid] = acc;
+    for (int j = nb - 1; j > 0; --j) {
+      __syncthreads();
+      const T yj = xs[vl * 64 + j];
+      if (i < j) {
+        xi = Ar<T>::fms(Ls[i + j * nb], yj, xi);
+        xs[vl * 64 + i] = xi;
+      }
     }
   }
   if (!act) return;
-  for (int j = 0; j < nb; ++j) {
-    const T y = ys[j * kSV + tid];
-    if (PANEL) {
-      W[v + j * ldw] = y;
-      x[j * es] = Ar<T>::mul(y, Ar<T>::inv(Ls[j + j * nb]));
-    } else {
-      x[j * es] = y;
-    }
+  if (PANEL) {
+    W[v + (long long)i * ldw] = xi;
+    x[(long long)i * es] = Ar<T>::mul(xi, Ar<T>::inv(Ls[i + i * nb]));
+  } else {
+    x[(long long)i * es] = xi;
   }
 }
 
@@ -278,7 +288,7 @@ int gemm(int mode, int M, int N, int K, double alpha, View<T> A, View<T> B, doub
 template <typename T>
 int ldl_factor(int n, T *A, long long lda, T *work, int *info, bool spd, cudaStream_t st) {
   const size_t diag_smem = (size_t)(kNB * (kNB + 1) + kNB) * sizeof(T);
-  const size_t trsv_smem = (size_t)(kNB * kNB + kNB * kSV) * sizeof(T);
+  const size_t trsv_smem = (size_t)(kNB * kNB + 64 * kSV) * sizeof(T);
   int rc;
   if ((rc = set_smem(k_ldl_diag<T>, diag_smem)) || (rc = set_smem(k_trsv<T, false, true>, trsv_smem))) return rc;
   for (int j0 = 0; j0 < n; j0 += kNB) {
@@ -290,7 +300,7 @@ int ldl_factor(int n, T *A, long long lda, T *work, int *info, bool spd, cudaStr
     if (m == 0) break;
     T *A21 = A11 + nb;
     // panel: W21 = A21 L11^-T, L21 = W21 D1^-1 (rows of A21 are the vectors)
-    k_trsv<T, false, true><<<(unsigned)((m + kSV - 1) / kSV), kSV, (size_t)(nb * nb + nb * kSV) * sizeof(T), st>>>(
+    k_trsv<T, false, true><<<(unsigned)((m + kSV - 1) / kSV), kSVT, (size_t)(nb * nb + 64 * kSV) * sizeof(T), st>>>(
         nb, A11, lda, m, A21, 1, lda, work, n);
     LA_CHECK();
     // trailing update of the lower triangle: A22 -= W21 L21^T
@@ -304,7 +314,7 @@ int ldl_factor(int n, T *A, long long lda, T *work, int *info, bool spd, cudaStr
 template <typename T>
 int ldl_solve(int n, int nrhs, const T *A, long long lda, T *B, long long ldb, cudaStream_t st) {
   if (n <= 0 || nrhs <= 0) return GINT_OK;
-  const size_t trsv_smem = (size_t)(kNB * kNB + kNB * kSV) * sizeof(T);
+  const size_t trsv_smem = (size_t)(kNB * kNB + 64 * kSV) * sizeof(T);
   int rc;
   if ((rc = set_smem(k_trsv<T, false, false>, trsv_smem)) || (rc = set_smem(k_trsv<T, true, false>, trsv_smem)))
     return rc;
@@ -313,7 +323,7 @@ int ldl_solve(int n, int nrhs, const T *A, long long lda, T *B, long long ldb, c
   for (int k0 = 0; k0 < n; k0 += kNB) {
     const int nb = std::min(kNB, n - k0);
     const T *Lkk = A + k0 + (long long)k0 * lda;
-    k_trsv<T, false, false><<<nvb, kSV, (size_t)(nb * nb + nb * kSV) * sizeof(T), st>>>(nb, Lkk, lda, nrhs, B + k0,
+    k_trsv<T, false, false><<<nvb, kSVT, (size_t)(nb * nb + 64 * kSV) * sizeof(T), st>>>(nb, Lkk, lda, nrhs, B + k0,
                                                                                         ldb, 1, nullptr, 0);
     LA_CHECK();
     const int m = n - k0 - nb;
@@ -330,7 +340,7 @@ int ldl_solve(int n, int nrhs, const T *A, long long lda, T *B, long long ldb, c
   for (int k0 = ((n - 1) / kNB) * kNB; k0 >= 0; k0 -= kNB) {
     const int nb = std::min(kNB, n - k0);
     const T *Lkk = A + k0 + (long long)k0 * lda;
-    k_trsv<T, true, false><<<nvb, kSV, (size_t)(nb * nb + nb * kSV) * sizeof(T), st>>>(nb, Lkk, lda, nrhs, B + k0, ldb,
+    k_trsv<T, true, false><<<nvb, kSVT, (size_t)(nb * nb + 64 * kSV) * sizeof(T), st>>>(nb, Lkk, lda, nrhs, B + k0, ldb,
                                                                                        1, nullptr, 0);
     LA_CHECK();
     // rows i < k0: B_i -= sum_k L[k0 + k, i] X[k0 + k]
