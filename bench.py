@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the float64 GPU comparator (0: skip)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the serving run and the per-R, projector and Crank-Nicolson timings")
+    ap.add_argument("--no-dense", action="store_true", help="skip the dense propagation steps among the extras")
     ap.add_argument("--dense-only", action="store_true",
                     help="time only the dense steps (Crank-Nicolson, density matrices) at the workload's basis size")
     ap.add_argument("--serve-requests", type=int, default=256, help="Poisson serving run (0: skip)")
@@ -413,9 +414,9 @@ def run_psibeta(g, system, steps, stream, workload):
 
 
 def run_cn(n, nocc, steps, stream):
-    """Density-matrix build, one Crank-Nicolson step (complex float64 GEMMs and LU through the
-    libraries) for an n x n basis and nocc states, and the energy-density matrix (real float64 GEMM and
-    Cholesky solve): mean times over `steps` calls."""
+    """Density-matrix build, one Crank-Nicolson step (float64 GEMMs and the complex symmetric L D L^T
+    factorisation and solves, the library's own kernels) for an n x n basis and nocc states, and the
+    energy-density matrix (real GEMM, L D L^T and solves): mean times over `steps` calls."""
     import numpy as np
     import torch
 
@@ -695,7 +696,7 @@ def main():
         psibeta = run_psibeta(g, w.system, 3, stream, args.workload)
 
     cn = None
-    if rank == 0 and tensor and not args.no_extras:
+    if rank == 0 and tensor and not args.no_extras and not args.no_dense:
         cn = run_cn(g.norb, 128 if g.norb < 2048 else 1024, 3 if g.norb < 2048 else 2, stream)
 
     launches = KERNEL_LAUNCHES.get(args.precision)
