@@ -399,15 +399,16 @@ def run_psibeta(g, system, steps, stream, workload):
     ms = e0.elapsed_time(e1) / steps
     npairs = int(len(g.pb_pairs))
     points = npairs * 140 * 162
-    # float64 roofline: the kernel's executed float64 flops (2 DFMA + DADD + DMUL), as the mean per pair
-    # counted by ncu with the current source on the 64-atom Si crystal (the same distribution of pair
-    # distances as any Si supercell), times the pairs, over the CUDA-event time, against the nominal rate
-    fpp, src = profiled(None, "f64", "gint_pb.cu", "fp64_flops_per_pair")
-    fl = None if fpp is None else fpp * npairs
+    # float64 roofline: the kernel's executed float64 flops per launch (2 DFMA + DADD + DMUL, counted by
+    # ncu on this workload with the current source; a cell short enough to bring several images of an
+    # atom into a projector sphere does more work per pair) over the CUDA-event time, against the
+    # nominal rate
+    fl, src = profiled(workload, "f64", "gint_pb.cu", "fp64_flops_per_launch")
     roof = {"bound": "fp64", "kernel": "k_psibeta", "unit": "TFLOP/s", "peak": FP64_NOMINAL_TFLOPS,
             "peak_source": "nominal (none measured)", "flops_source": src,
             "achieved": None if fl is None else fl / (ms * 1e-3) / 1e12}
     roof["frac"] = None if fl is None else roof["achieved"] / FP64_NOMINAL_TFLOPS
+    roof["fp64_pipe_active_ncu"] = profiled(workload, "f64", "gint_pb.cu", "fp64_pipe_active")[0]
     return {"pairs": npairs, "elements": int(g.pb_nelems), "ms": ms, "pairs_per_s": npairs / (ms * 1e-3),
             "grid_points_per_s": points / (ms * 1e-3), "precision": "f64", "roofline": roof,
             "quadrature": "140 Gauss-Legendre radial x 162-point degree-17 product angular rule"}
