@@ -400,9 +400,7 @@ def run_psibeta(g, system, steps, stream, workload):
     npairs = int(len(g.pb_pairs))
     points = npairs * 140 * 162
     # float64 roofline: the kernel's executed float64 flops per launch (2 DFMA + DADD + DMUL, counted by
-    # ncu on this workload with the current source; a cell short enough to bring several images of an
-    # atom into a projector sphere does more work per pair) over the CUDA-event time, against the
-    # nominal rate
+    # ncu on this workload with the current source) over the CUDA-event time, against the nominal rate
     fl, src = profiled(workload, "f64", "gint_pb.cu", "fp64_flops_per_launch")
     roof = {"bound": "fp64", "kernel": "k_psibeta", "unit": "TFLOP/s", "peak": FP64_NOMINAL_TFLOPS,
             "peak_source": "nominal (none measured)", "flops_source": src,
