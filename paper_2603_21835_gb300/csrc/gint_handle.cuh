@@ -105,6 +105,7 @@ struct gint_handle {
   int *r_hu_key = nullptr;              // upper keys, each with its contributions:
   long long *r_hu_off = nullptr, *r_hu_src = nullptr;
   int *r_gk_off = nullptr;              // [npairs + 1]: keys of pair p are [gk_off[p], gk_off[p + 1])
+  bool r_group_ok = false;              // every group of 8 consecutive pairs has at most 64 keys
   // velocity-gauge projector overlaps (set by gint_set_projectors)
   bool pb_ready = false;
   GTabs pb_tabs{};                      // projector radial metadata per species

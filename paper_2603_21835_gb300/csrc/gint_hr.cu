@@ -103,6 +103,58 @@ __global__ void __launch_bounds__(128) k_bloch(const long long *__restrict__ pai
   }
 }
 
+// The same sums for groups of kGP consecutive pairs per CTA (one or a few keys per pair, as in a cell
+// where no brick sees two images of one atom): the phases of the group's keys (at most kGK) in shared
+// memory, then one thread per element of the group's blocks (flattened), each H(R) element read once
+// and every H(k) element written as one 16-byte store.  Small blocks no longer leave most of a CTA
+// idle, and one CTA covers kGP pairs instead of one.
+constexpr int kGP = 8, kGK = 64, kGT = 256;
+__global__ void __launch_bounds__(kGT) k_bloch_grouped(int npairs, const long long *__restrict__ pair_off,
+                                                      const int *__restrict__ gk_off, const int *__restrict__ kn,
+                                                      const long long *__restrict__ koff, const double *__restrict__ HR,
+                                                      const __grid_constant__ GKpts K, long long nblock,
+                                                      double2 *__restrict__ Hk) {
+  __shared__ double cs[kGK][kMaxK], sn[kGK][kMaxK];
+  __shared__ long long poff[kGP + 1];
+  __shared__ int qoff[kGP + 1];
+  const int p0 = blockIdx.x * kGP, np = min(kGP, npairs - p0), nk = K.nk;
+  if (threadIdx.x <= np) {
+    poff[threadIdx.x] = pair_off[p0 + threadIdx.x];
+    qoff[threadIdx.x] = gk_off[p0 + threadIdx.x];
+  }
+  __syncthreads();
+  const int q0 = qoff[0], nq = qoff[np] - q0;  // the host checks nq <= kGK
+  for (int u = threadIdx.x; u < nq * nk; u += kGT) {
+    const int i = u / nk, j = u - i * nk, q = q0 + i;
+    // k.R = 2 pi (kf . n) for R = n1 a1 + n2 a2 + n3 a3 and k in reciprocal-lattice units
+    sincospi(2.0 * (K.kf[j][0] * kn[3 * q] + K.kf[j][1] * kn[3 * q + 1] + K.kf[j][2] * kn[3 * q + 2]), &sn[i][j],
+             &cs[i][j]);
+  }
+  __syncthreads();
+  const long long g0 = poff[0], g1 = poff[np];
+  int pl = 0;  // pair (within the group) of the current element; elements advance monotonically
+  for (long long g = g0 + threadIdx.x; g < g1; g += kGT) {
+    while (g >= poff[pl + 1]) ++pl;
+    const long long e = g - poff[pl];
+    double re[kMaxK], im[kMaxK];
+#pragma unroll
+    for (int j = 0; j < kMaxK; ++j) re[j] = im[j] = 0.0;
+    for (int q = qoff[pl]; q < qoff[pl + 1]; ++q) {
+      const double h = HR[koff[q] + e];
+      const int i = q - q0;
+#pragma unroll
+      for (int j = 0; j < kMaxK; ++j)
+        if (j < nk) {
+          re[j] += cs[i][j] * h;
+          im[j] += sn[i][j] * h;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxK; ++j)
+      if (j < nk) Hk[j * nblock + g] = make_double2(re[j], im[j]);
+  }
+}
+
 }  // namespace
 
 void gint_hr_free(gint_handle *h) {
@@ -219,6 +271,9 @@ int gint_hr_prepare(gint_handle *h) {
     }
   }
   for (int p = 0; p < h->npairs; ++p) gk_off[p + 1] += gk_off[p];
+  h->r_group_ok = true;  // the grouped Bloch kernel holds the phases of every group's keys
+  for (int p0 = 0; p0 < h->npairs; p0 += kGP)
+    if (gk_off[std::min(h->npairs, p0 + kGP)] - gk_off[p0] > kGK) h->r_group_ok = false;
   for (const auto &kv : index) {
     const Key &k = kv.first;
     kT[kv.second] = index.at(Key{k[1], k[0], -k[2], -k[3], -k[4]});
@@ -259,8 +314,13 @@ int gint_hr_bloch(gint_handle *h, const double *HR, int nk, const double *kf, do
     K.nk = std::min(kMaxK, nk - k0);
     for (int j = 0; j < K.nk; ++j)
       for (int c = 0; c < 3; ++c) K.kf[j][c] = kf[3 * (k0 + j) + c];
-    k_bloch<<<(unsigned)h->npairs, 128, 0, st>>>(h->pair_off_dev, h->r_gk_off, h->r_kn, h->r_koff, HR, K, h->nblock,
-                                                 Hk + 2 * (long long)k0 * h->nblock);
+    if (h->r_group_ok)
+      k_bloch_grouped<<<(unsigned)((h->npairs + kGP - 1) / kGP), kGT, 0, st>>>(
+          h->npairs, h->pair_off_dev, h->r_gk_off, h->r_kn, h->r_koff, HR, K, h->nblock,
+          reinterpret_cast<double2 *>(Hk) + (long long)k0 * h->nblock);
+    else
+      k_bloch<<<(unsigned)h->npairs, 128, 0, st>>>(h->pair_off_dev, h->r_gk_off, h->r_kn, h->r_koff, HR, K, h->nblock,
+                                                   Hk + 2 * (long long)k0 * h->nblock);
     if (cudaGetLastError() != cudaSuccess) return GINT_ECUDA;
   }
   return GINT_OK;
