@@ -590,6 +590,20 @@ def main():
             b.record(stream)
             torch.cuda.synchronize()
             lst.append(a.elapsed_time(b))
+    # the local-H pass alone with the strict float64 cross-brick reduction (every tile value added
+    # in float64) instead of the default double-float sums
+    t_h64 = []
+    if tensor:
+        g.set_reduction("fp64")
+        for k in range(3):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.vlocal(V, prec, out=H)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t_h64.append(a.elapsed_time(b))
+        g.set_reduction("double-float")
     ms_per_step = max_over_ranks(sum(t_steps), world, dev) / args.steps
     value = world * 2.0 * W / (ms_per_step * 1e-3) / 1e9
 
@@ -712,6 +726,7 @@ def main():
                    "parallelism": f"replicas{world}"},
         "ms_kernel": tdom, "ms_rho_alone": statistics.mean(t_rho), "ms_vlocal_alone": statistics.mean(t_h),
         "ms_force_alone": statistics.mean(t_f),
+        "ms_vlocal_alone_fp64_reduction": statistics.mean(t_h64) if t_h64 else None,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "fp64_gpu": fp64_gpu,
         "mixed_over_fp64": fp64_gpu["mixed_over_fp64"] if fp64_gpu else None,
         "gpu_launches": launches * args.steps, "serving": serving, "per_R": per_R, "psibeta": psibeta,

@@ -157,6 +157,20 @@ int gint_rho(gint_handle *h, int precision, const double *D_blocks, double *rho,
 /* Local-Hamiltonian pass: H blocks (device, overwritten) from V [n1 n2 n3] (device). */
 int gint_vlocal(gint_handle *h, int precision, const double *V, double *H_blocks, void *stream);
 
+/* Cross-brick reduction of the tensor-core local-H pass (GINT_F16X3 / GINT_F16X1; the FP64 and FP32
+ * paths are unaffected).  The per-brick tiles are float32 (the tensor cores' accumulators); they are
+ * summed over the bricks in a fixed order
+ *   GINT_REDUCE_DOUBLE_FLOAT (default): as double-float pairs (error-free float32 additions into a
+ *     hi + lo pair), the pairs combined in float64: summation error about n^2 2^-48 relative for n
+ *     bricks, far below the float32 rounding of the tiles;
+ *   GINT_REDUCE_FP64: every tile value converted to float64 and added in float64 (the float64 pipe
+ *     of the GB300 makes this the slower reduction).
+ * Both are deterministic.  Applies to later gint_vlocal / gint_vlocal_R / gint_run_batch calls on h
+ * (and to the server's jobs that use h).  GINT_EINVAL for another mode. */
+#define GINT_REDUCE_DOUBLE_FLOAT 0
+#define GINT_REDUCE_FP64 1
+int gint_set_reduction(gint_handle *h, int mode);
+
 /* Local H per lattice vector (paper Sec. 2, H_{mu nu}(R); Sec. 3.3.1, the local-potential matrix
  * element between phi_mu at tau_I and phi_nu at tau_J + R): keys (I, J, R) with
  * R = n1 a1 + n2 a2 + n3 a3, one norb(I) x norb(J) row-major block per key, keys sorted by

@@ -415,6 +415,7 @@ int make_twin(gint_handle *h) {
     gint_destroy(t);
     return GINT_EDEVICE;
   }
+  t->reduce_fp64 = h->reduce_fp64;
   h->twin = t;
   return GINT_OK;
 }
@@ -556,6 +557,13 @@ int gint_vlocal(gint_handle *h, int precision, const double *V, double *H_blocks
     return gint_simt_vlocal(h, precision == GINT_FP64, V, H_blocks, st);
   }
   return gint_tc_vlocal(h, precision, V, H_blocks, st);  // every block element is written
+}
+
+int gint_set_reduction(gint_handle *h, int mode) {
+  if (!h || (mode != GINT_REDUCE_DOUBLE_FLOAT && mode != GINT_REDUCE_FP64)) return GINT_EINVAL;
+  h->reduce_fp64 = mode == GINT_REDUCE_FP64;
+  if (h->twin) h->twin->reduce_fp64 = h->reduce_fp64;
+  return GINT_OK;
 }
 
 int gint_layout_R(gint_handle *h, int *nkeys, long long *nblock_elems, const int **keys, const long long **key_off) {

@@ -96,6 +96,7 @@ struct gint_handle {
   bool r_ready = false;
   int r_status = 0;           // GINT_OK, or why per-R output is unavailable for this geometry
   bool reduce_R = false;      // the next local-H reduction writes H(R) blocks (set around one call)
+  bool reduce_fp64 = false;   // tensor-core local H: cross-brick sums in float64 (gint_set_reduction)
   int r_nkeys = 0, r_nupper = 0;
   long long r_nblock = 0, r_bytes = 0;
   std::vector<int> r_keys_host;         // [nkeys][5]: I, J, n1, n2, n3 (R = n1 a1 + n2 a2 + n3 a3)

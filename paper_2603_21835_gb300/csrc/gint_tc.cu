@@ -1437,6 +1437,7 @@ struct GRedSys {
   const long long *pair_off;
   const int *species;
   double *H;
+  int fp64;  // 1: every tile value added in float64 (gint_set_reduction), 0: double-float pairs
 };
 struct GRed {
   int nsys;
@@ -1460,9 +1461,11 @@ __device__ __forceinline__ void bar_sync(int id, int nthreads) {
 }
 // Upper pair u of system S by NG groups of kRedLanes threads (tid in [0, NG kRedLanes)); part_hi and
 // part_lo hold (NG - 1) kRedE kRedLanes floats each; the groups synchronise on barrier `bar`.
-template <int NG>
-__device__ __forceinline__ void reduce_pair(const GTabs &g, const GRedSys &S, int u, int tid, float *part_hi,
-                                            float *part_lo, int bar) {
+// F64: every tile value converted and added in float64 (a part's float64 sum travels between the
+// groups as the two 32-bit halves of its bits in part_lo / part_hi), the same parts and order.
+template <int NG, bool F64>
+__device__ __forceinline__ void reduce_pair_t(const GTabs &g, const GRedSys &S, int u, int tid, float *part_hi,
+                                              float *part_lo, int bar) {
   const int p = S.hu_pair[u];
   const int I = S.pair_I[p], J = S.pair_J[p];
   const int nI = g.sp[S.species[I]].norb, nJ = g.sp[S.species[J]].norb;
@@ -1477,18 +1480,24 @@ __device__ __forceinline__ void reduce_pair(const GTabs &g, const GRedSys &S, in
     int e[kRedE];
     bool act[kRedE];
     float ah[kRedE], al[kRedE];
+    double ad[kRedE];
 #pragma unroll
     for (int q = 0; q < kRedE; ++q) {
       e[q] = base + q * kRedLanes + ln;
       act[q] = e[q] < ne;
       if (!act[q]) e[q] = 0;  // a valid address; its loads are discarded
       ah[q] = al[q] = 0.f;
+      ad[q] = 0.0;
     }
     auto add = [&](int q, float x) {
-      float sum, err;
-      two_sum(ah[q], x, sum, err);
-      ah[q] = sum;
-      al[q] += err;
+      if (F64) {
+        ad[q] += (double)x;
+      } else {
+        float sum, err;
+        two_sum(ah[q], x, sum, err);
+        ah[q] = sum;
+        al[q] += err;
+      }
     };
     long long k = k0;
     for (; k + kRedB <= k1; k += kRedB) {
@@ -1513,8 +1522,14 @@ __device__ __forceinline__ void reduce_pair(const GTabs &g, const GRedSys &S, in
     if (grp > 0) {
 #pragma unroll
       for (int q = 0; q < kRedE; ++q) {
-        part_hi[((grp - 1) * kRedE + q) * kRedLanes + ln] = ah[q];
-        part_lo[((grp - 1) * kRedE + q) * kRedLanes + ln] = al[q];
+        const int w = ((grp - 1) * kRedE + q) * kRedLanes + ln;
+        if (F64) {
+          part_hi[w] = __int_as_float(__double2hiint(ad[q]));
+          part_lo[w] = __int_as_float(__double2loint(ad[q]));
+        } else {
+          part_hi[w] = ah[q];
+          part_lo[w] = al[q];
+        }
       }
     }
     bar_sync(bar, NG * kRedLanes);
@@ -1522,9 +1537,12 @@ __device__ __forceinline__ void reduce_pair(const GTabs &g, const GRedSys &S, in
 #pragma unroll
       for (int q = 0; q < kRedE; ++q) {
         if (!act[q]) continue;
-        double acc = (double)ah[q] + (double)al[q];
-        for (int g2 = 0; g2 < NG - 1; ++g2)
-          acc += (double)part_hi[(g2 * kRedE + q) * kRedLanes + ln] + (double)part_lo[(g2 * kRedE + q) * kRedLanes + ln];
+        double acc = F64 ? ad[q] : (double)ah[q] + (double)al[q];
+        for (int g2 = 0; g2 < NG - 1; ++g2) {
+          const int w = (g2 * kRedE + q) * kRedLanes + ln;
+          acc += F64 ? __hiloint2double(__float_as_int(part_hi[w]), __float_as_int(part_lo[w]))
+                     : (double)part_hi[w] + (double)part_lo[w];
+        }
         const int j = e[q] / nI, i = e[q] - j * nI;
         S.H[S.pair_off[p] + (long long)i * nJ + j] = acc;
         if (S.pair_T[p] != p) S.H[S.pair_off[S.pair_T[p]] + (long long)j * nI + i] = acc;  // (J, I, -R)
@@ -1532,6 +1550,15 @@ __device__ __forceinline__ void reduce_pair(const GTabs &g, const GRedSys &S, in
     }
     bar_sync(bar, NG * kRedLanes);
   }
+}
+
+template <int NG>
+__device__ __forceinline__ void reduce_pair(const GTabs &g, const GRedSys &S, int u, int tid, float *part_hi,
+                                            float *part_lo, int bar) {
+  if (S.fp64)
+    reduce_pair_t<NG, true>(g, S, u, tid, part_hi, part_lo, bar);
+  else
+    reduce_pair_t<NG, false>(g, S, u, tid, part_hi, part_lo, bar);
 }
 
 __global__ void __launch_bounds__(kRedThreads, 4) k_h_reduce(const __grid_constant__ GTabs g, const __grid_constant__ GRed R) {
@@ -2495,6 +2522,7 @@ static void fill_red_gamma(GRedSys &rs, const gint_task &T) {
   rs.pair_J = h->pair_col_dev;
   rs.pair_T = h->pair_T_dev;
   rs.pair_off = h->pair_off_dev;
+  rs.fp64 = h->reduce_fp64 ? 1 : 0;
 }
 
 static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
@@ -2531,6 +2559,7 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
       rs.hs = h->hs;
       rs.species = h->species_dev;
       rs.H = T.H_blocks;
+      rs.fp64 = h->reduce_fp64 ? 1 : 0;
       if (h->reduce_R) {  // the same tiles keyed by (I, J, R): H(R) blocks
         rs.hu_pair = h->r_hu_key;
         rs.hu_off = h->r_hu_off;

@@ -75,6 +75,7 @@ _lib.gint_grid_dot_noalloc.argtypes = [_vp, _vp, _ll, _d, _vp, _vp]
 _lib.gint_run_batch.argtypes = [ctypes.POINTER(_Task), _i, _i, _vp]
 _lib.gint_run_batch_timed.argtypes = [ctypes.POINTER(_Task), _i, _i, _vp, _vp, _vp]
 _lib.gint_memory.argtypes = [_vp, ctypes.POINTER(_ll)]
+_lib.gint_set_reduction.argtypes = [_vp, _i]
 _lib.gint_layout_R.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_ll), ctypes.POINTER(ctypes.POINTER(_i)),
                                ctypes.POINTER(ctypes.POINTER(_ll))]
 _lib.gint_vlocal_R.argtypes = [_vp, _i, _vp, _vp, _vp]
@@ -102,7 +103,7 @@ _lib.gint_orbitals.argtypes = [_vp, _i, _ll, _vp, _vp, _vp]
 C_ABI_SYMBOLS = ("gint_create", "gint_destroy", "gint_layout", "gint_pairs", "gint_stats", "gint_set_positions",
                  "gint_rho", "gint_vlocal", "gint_force", "gint_grid_dot", "gint_block_dot", "gint_weight",
                  "gint_strerror", "gint_sync", "gint_tc_selftest", "gint_grid_dot_noalloc", "gint_run_batch",
-                 "gint_run_batch_timed", "gint_memory", "gint_layout_R", "gint_vlocal_R", "gint_bloch",
+                 "gint_run_batch_timed", "gint_memory", "gint_set_reduction", "gint_layout_R", "gint_vlocal_R", "gint_bloch",
                  "gint_set_projectors", "gint_psibeta_layout", "gint_psibeta", "gint_cn_create", "gint_cn_destroy",
                  "gint_cn_step", "gint_dm_build", "gint_dm_build_f16x3", "gint_cn_info", "gint_edm",
                  "gint_brick_lists", "gint_orbitals", "gint_server_create", "gint_server_submit", "gint_server_test",
@@ -395,6 +396,12 @@ class Gint:
         _check(_lib.gint_vlocal(self._h, int(precision), _dptr(V, numel=self.ngrid), _dptr(out, numel=self.nblock),
                                 _stream(stream)), "gint_vlocal")
         return out
+
+    def set_reduction(self, mode: str):
+        """Cross-brick sums of the tensor-core local-H pass: "double-float" (default: float32 hi + lo
+        pairs combined in float64) or "fp64" (every tile value added in float64)."""
+        code = {"double-float": 0, "fp64": 1}[mode]
+        _check(_lib.gint_set_reduction(self._h, code), "gint_set_reduction")
 
     def layout_R(self):
         """Keys of the local H per lattice vector (paper Sec. 2, H(R)): (keys [nkeys, 5] int32 rows

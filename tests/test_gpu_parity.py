@@ -190,6 +190,35 @@ def test_si64_sampled_parity(si64, torch_cuda, prec):
         assert np.abs(blk - ref).max() <= TOL[prec] * hmax
 
 
+def test_si64_float64_cross_brick_reduction(si64, torch_cuda):
+    """The strict reduction mode (every float32 tile value added in float64) against the default
+    double-float sums: the same tiles in the same order, so the two agree far below the tiles'
+    own rounding (1e-10 of max|H|; both sums' errors are below 1e-12 here); H(R) as well; and
+    against the oracle at the F16x3 tolerance.  The mode is restored afterwards."""
+    torch = torch_cuda
+    s = si64
+    g, o, w, G = s["g"], s["o"], s["w"], s["G"]
+    Vd = torch.from_numpy(w.V.reshape(-1)).cuda()
+    H_df = g.vlocal(Vd, G.F16X3).cpu().numpy()
+    HR_df = g.vlocal_R(Vd, G.F16X3).cpu().numpy()
+    g.set_reduction("fp64")
+    try:
+        H_64 = g.vlocal(Vd, G.F16X3).cpu().numpy()
+        HR_64 = g.vlocal_R(Vd, G.F16X3).cpu().numpy()
+        g.sync()
+    finally:
+        g.set_reduction("double-float")
+    hmax = np.abs(H_64).max()
+    assert np.abs(H_64 - H_df).max() <= 1e-10 * hmax
+    assert np.abs(HR_64 - HR_df).max() <= 1e-10 * hmax
+    for (I, J) in [(0, 0), (3, 17), (63, 2)]:
+        k = g.block_index(I, J)
+        ref = o.vlocal_block(w.V, I, J)
+        assert np.abs(H_64[g.pair_off[k]:g.pair_off[k + 1]].reshape(ref.shape) - ref).max() <= TOL["f16x3"] * hmax
+    with pytest.raises(G.GintError):
+        G._check(G._lib.gint_set_reduction(g._h, 7), "gint_set_reduction")
+
+
 @pytest.fixture(scope="module")
 def si512(torch_cuda):
     """512-atom Si (4x4x4 supercell, N(0,0.05) displacements), 192^3 grid, D from C 6656x1024 / 32.
