@@ -1867,6 +1867,8 @@ __global__ void __launch_bounds__(kT, 1)
     int pn, pitems;
     unsigned long long bseq;           // the job whose stage bounds follow (claims)
     long long b_i0, b_bb, b_rr, b_ee;  // its first item, first brick, first reduction, end
+    unsigned long long tiles_seq;      // a job whose tile stage this CTA has seen complete (+1)
+    int bad;                           // this item's dependency wait gave up (every thread skips it)
   };
   __shared__ ServeState ss;
   const int t = threadIdx.x, warp = t >> 5;
@@ -1907,6 +1909,7 @@ __global__ void __launch_bounds__(kT, 1)
     ss.pn = ss.pitems = 0;
     ss.pseq = 0;
     ss.bseq = ~0ull;
+    ss.tiles_seq = 0;
     s_plan_next = -1;
   }
   for (;;) {
@@ -2009,12 +2012,28 @@ __global__ void __launch_bounds__(kT, 1)
     } else if (li < r0) {  // a brick
       const long long b = li - b0;
       cx.ok = true;
-      if (t == 0 && ld_acquire_s32(&JS.tiles) < J.n_tile) {
-        flush();
-        wait_count(&JS.tiles, J.n_tile, err);
+      // the job's tiles: awaited once per job and CTA (errors of other CTAs are seen at the next claim)
+      if (t == 0) {
+        ss.bad = 0;
+        if (ss.tiles_seq != seq + 1) {
+          if (ld_acquire_s32(&JS.tiles) < J.n_tile) {
+            flush();
+            if (!wait_count(&JS.tiles, J.n_tile, err)) ss.bad = 1;
+          }
+          if (!ss.bad) ss.tiles_seq = seq + 1;
+        }
+      }
+      // V at the brick's points: loaded now, stored after the unpack (the load overlaps it); the
+      // L1-bypassing load sees V rewritten for a later job.  brick_body reads wv only after its
+      // own barriers.
+      const GSys &S0 = sj.sys;
+      float wvv = 0.f;
+      if (t < 128 && S0.V && (S0.do_h || FORCE)) {
+        int gi, gj, gk;
+        if (brick_point(S0.c, b, t, gi, gj, gk)) wvv = (float)(S0.c.w * __ldcg(S0.V + grid_index(S0.c, gi, gj, gk)));
       }
       __syncthreads();
-      if (!*(volatile unsigned *)err) {  // the same decision in every thread (read after the barrier)
+      if (!ss.bad) {  // the same decision in every thread (read after the barrier)
         const GSys &S = sj.sys;
         if (seq != ss.cur_sys) {  // a new job: points and scales into shared memory
           init_points(S.c, sh);
@@ -2027,10 +2046,6 @@ __global__ void __launch_bounds__(kT, 1)
           }
         }
         const bool do_rho = S.do_rho != 0, do_h = S.do_h != 0;
-        if (t < 128 && S.V && (do_h || FORCE)) {
-          int gi, gj, gk;
-          sh.wv[t] = brick_point(S.c, b, t, gi, gj, gk) ? (float)(S.c.w * __ldcg(S.V + grid_index(S.c, gi, gj, gk))) : 0.f;
-        }
         const long long o0 = S.plan_off[b], o1 = S.plan_off[b + 1];
         const uint32_t bytes = (uint32_t)((o1 - o0) * 16);
         if (S.plan && bytes <= 4u * kPlanWords) {
@@ -2061,6 +2076,7 @@ __global__ void __launch_bounds__(kT, 1)
             }
           }
         }
+        if (t < 128) sh.wv[t] = wvv;  // read by brick_body after its barriers
         brick_body<FORCE>(g, S, b, do_rho, do_h, split3, dsmem, zero, tmem, sh, smem, cx);
         tc_fence_before();
       }
