@@ -1782,8 +1782,9 @@ __global__ void __launch_bounds__(128) k_build_plans(const __grid_constant__ GTa
 // (one task: the density / force and local-H passes of one system) while it runs.  A job's items, in
 // the global item order: kServePrep max-reduction chunks, one scales item, tile items (kServeTilePairs
 // pairs each), one item per brick, reduction items (kServeRedPairs upper pairs each).  A CTA claims
-// items one at a time, in order, by a compare-and-swap on the claim counter that never passes the
-// published count; an item waits (bounded) for the items of its job it depends on (scales after the
+// ranges of a published job's items, in order, by a fetch-and-add on that job's claim counter (a
+// count past the job's end sends the CTA to the next job); an item waits (bounded) for the items of
+// its job it depends on (scales after the
 // chunks, tiles after the scales, bricks after the tiles, reductions after the bricks), which were
 // all claimed earlier, so the wait always ends.  The last item of a job to complete writes the job's
 // completion word into host-mapped memory.  A CTA with nothing to claim for idle_ns (or on the stop
@@ -1806,11 +1807,11 @@ struct GJob {
   long long item0, nitems;          // first item and item count of the job
   unsigned long long seq;
 };
-struct GJobState {  // completed items of the job per kind, and in total (zeroed at publication)
-  int prep, scales, tiles, bricks, red, all, pad[2];
+struct GJobState {  // completed items of the job per kind, in total, and claimed (zeroed at publication)
+  int prep, scales, tiles, bricks, red, all, claim, pad;
 };
 struct GServeCtl {
-  unsigned long long head;       // claimed items
+  unsigned long long head;       // unused (claims count per job)
   unsigned long long tail;       // published items (written by the host)
   unsigned long long first_seq;  // claims never go to jobs before this one (cursor start, host hint)
   int stop;                      // host: leave as soon as idle
@@ -1924,15 +1925,13 @@ __global__ void __launch_bounds__(kT, 1)
         const long long t0 = globaltimer();
         for (;;) {
           if (*(volatile unsigned *)&ctl->err) break;
-          const unsigned long long h = *(volatile unsigned long long *)&ctl->head;
+          // the job at this CTA's cursor, if published (the host writes a job's end before the tail
+          // that covers it); its items are claimed with a fetch-and-add on the job's own counter, so
+          // no claim waits for another and an over-claim is only a count past the job's end
           const unsigned long long tl = ld_acquire_u64(&ctl->tail);
-          if (h < tl) {
-            // the claim's size from the stage of item h (bounds of its job cached): up to kServeRange
-            // bricks or kServeRange / 2 reduction items, clipped to the stage; the short preparation
-            // and tile stages one item at a time so that every CTA helps with them
-            unsigned long long c = ss.cursor;
-            while (ld_acquire_s64(job_end + c) <= (long long)h) ++c;
-            ss.cursor = c;
+          const unsigned long long c = ss.cursor;
+          const long long e = ld_acquire_s64(job_end + c);
+          if (e > 0 && (unsigned long long)e <= tl) {
             if (ss.bseq != c) {
               const GJob *jc = jobs + c % kServeRing;
               ss.b_i0 = __ldcg(&jc->item0);
@@ -1941,35 +1940,33 @@ __global__ void __launch_bounds__(kT, 1)
               ss.b_ee = ss.b_i0 + __ldcg(&jc->nitems);
               ss.bseq = c;
             }
-            const long long hi = (long long)h;
-            const long long lim = hi < ss.b_bb ? 1
-                                  : hi < ss.b_rr ? min((long long)kServeRange, ss.b_rr - hi)
-                                                 : min((long long)kServeRange / 2, ss.b_ee - hi);
-            const unsigned long long r = (unsigned long long)max(
-                1LL, min(lim, (long long)((tl - h) / (4ull * gridDim.x))));
-            unsigned long long got;
-            if (tl - h >= 2ull * gridDim.x * kServeRange) {
-              // plenty published: a plain fetch-and-add cannot pass the tail (at most one claim of
-              // at most kServeRange items per CTA is in progress), so no retry is needed
-              got = atomicAdd(&ctl->head, r);
-            } else {
-              got = atomicCAS(&ctl->head, h, h + r);
-              if (got != h) continue;
+            int *claim = &st[c % kServeRing].claim;
+            const long long n = ss.b_ee - ss.b_i0, cl = *(volatile int *)claim;
+            if (cl < n) {
+              // the claim's size from the stage of the next item: up to kServeRange bricks or
+              // kServeRange / 2 reduction items, fewer as the job's items run low; the short
+              // preparation and tile stages one item at a time so that every CTA helps with them
+              const long long hi = ss.b_i0 + cl;
+              const long long lim = hi < ss.b_bb ? 1
+                                    : hi < ss.b_rr ? min((long long)kServeRange, ss.b_rr - hi)
+                                                   : min((long long)kServeRange / 2, ss.b_ee - hi);
+              const int r = (int)max(1LL, min(lim, (n - cl) / (2LL * gridDim.x)));
+              const long long got = atomicAdd(claim, r);
+              if (got < n) {
+                item = ss.b_i0 + got;
+                ss.range_next = (unsigned long long)(item + 1);
+                ss.range_end = (unsigned long long)(ss.b_i0 + min(got + r, n));
+                break;
+              }
             }
-            item = (long long)got;
-            ss.range_next = got + 1;
-            ss.range_end = got + r;
-            break;
+            ss.cursor = c + 1;  // every item of job c is claimed
+            continue;
           }
           if (*(volatile int *)&ctl->stop || globaltimer() - t0 > idle_ns) break;
           __nanosleep(1000);
         }
       }
-      if (item >= 0) {  // job_end of every published job is written before the tail
-        unsigned long long c = ss.cursor;
-        while (ld_acquire_s64(job_end + c) <= item) ++c;
-        ss.cursor = c;
-      }
+
       s_item = item;
       s_seq = (long long)ss.cursor;
       bulk_wait_read();  // a previous brick item's tiles have left shared memory
@@ -2779,6 +2776,7 @@ extern "C" int gint_server_create(int precision, int forces, double idle_s, gint
   if (cudaHostGetDevicePointer((void **)&v->done_d, v->done_h, 0) != cudaSuccess ||
       cudaMemset(v->ctl, 0, sizeof(GServeCtl)) != cudaSuccess || cudaMemset(v->zero, 0, 512) != cudaSuccess ||
       cudaMemset(v->st, 0, kServeRing * sizeof(GJobState)) != cudaSuccess ||
+      cudaMemset(v->job_end, 0, kServeMaxJobs * sizeof(long long)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&v->kstream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&v->cstream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&v->kdone, cudaEventDisableTiming) != cudaSuccess ||
@@ -2871,7 +2869,7 @@ extern "C" int gint_server_test(gint_server *v, long long ticket, int *done) {
   if (c.err) return (c.err & GINT_ERRBIT_TIMEOUT) ? GINT_ETIMEDOUT : GINT_EDEVICE;
   *done = slot_done(v, (unsigned long long)ticket) ? 1 : 0;
   if (*done) return GINT_OK;
-  return c.head < c.tail ? server_launch(v) : GINT_OK;
+  return server_launch(v);  // its items are not all claimed: the kernel went idle before it was published
 }
 
 extern "C" int gint_server_stats(const gint_server *v, long long *launches, long long *jobs) {
