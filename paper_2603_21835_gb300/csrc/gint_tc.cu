@@ -1677,42 +1677,68 @@ struct GTile {
   GTileSys sys[kMaxBatch];
 };
 
-// Pair p of a system by nt threads (this one t): D block (float64, row-major norb(I) x norb(J)) ->
-// scaled float16 (hi, lo) tile of roundup(norb(I), 8) x porb(J) in core-matrix order
-// [row group][K group][8][8], plus the same tile halved (floating split), or the fixed-point split.
-__device__ __forceinline__ void build_tile(const GTabs &g, const GTileSys &S, int p, bool fixed, int t, int nt) {
+// Pair p of a system: D block (float64, row-major norb(I) x norb(J)) -> scaled float16 (hi, lo)
+// tile of roundup(norb(I), 8) x porb(J) in core-matrix order [row group][K group][8][8], plus the
+// same tile halved (floating split), or the fixed-point split (hi the nearest integer, exact in
+// float16 for |x| < 2048, lo the float16 remainder).
+// One warp builds the tile: a lane takes one row of an 8 x 8 block at a time (8 elements, one
+// 16-byte store per array).  The floating split is formed in float32: the scale is a power of two,
+// so the scaled value is D rounded once to float32 (2^-24 relative, below the split's 2^-22), and
+// hi, x - hi, x / 2 and x / 2 - hi2 are exact in float32.  The fixed-point split (force launches)
+// keeps the remainder x - rint(x) in float64, since it is the lo term of an exact hi * hi sum.
+__device__ __forceinline__ void build_tile_warp(const GTabs &g, const GTileSys &S, int p, bool fixed, int lane) {
   const int I = S.pair_I[p], J = S.pair_J[p];
   const int nI = g.sp[S.species[I]].norb, nJ = g.sp[S.species[J]].norb, pJ = g.sp[S.species[J]].porb;
   const int rI = (nI + 7) & ~7, sJ = pJ >> 3;
-  const double sc = (double)__ldcg(S.scales + 1) * (fixed ? (double)kFxScaleD : 1.0);
+  const float scf = __ldcg(S.scales + 1) * (fixed ? kFxScaleD : 1.f);
   const long long o = S.pair_off[p], to = S.tile_off[p];
-  for (int e = t; e < rI * pJ; e += nt) {
-    const int cm = e >> 6, w = e & 63;
-    const int i = (cm / sJ) * 8 + (w >> 3), j = (cm % sJ) * 8 + (w & 7);
-    const long long q = 2 * to + (long long)cm * 128 + w;  // hi element; lo 64 halves later
-    if (i < nI && j < nJ) {
-      const double x = __ldcg(S.D + o + (long long)i * nJ + j) * sc;
-      if (fixed) {  // hi: the nearest integer (exact in float16: |x| < 2048); the halved tiles are unused
-        const double hx = rint(x);
-        S.Dhl[q] = __float2half_rn((float)hx);
-        S.Dhl[q + 64] = __float2half_rn((float)(x - hx));
-        S.Dhl2[q] = S.Dhl2[q + 64] = __float2half(0.f);
-        continue;
+  const double *__restrict__ Dp = S.D + o;
+  for (int u = lane; u < rI * sJ; u += 32) {  // units: (block, row of the block)
+    const int cm = u >> 3, r8 = u & 7;
+    const int i = (cm / sJ) * 8 + r8, j0 = (cm % sJ) * 8;
+    uint32_t wh[4], wl[4], w2h[4], w2l[4];
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+      float hv[2], lv[2], h2v[2], l2v[2];
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int j = j0 + k + m;
+        const bool in = i < nI && j < nJ;
+        const double d = in ? __ldcg(Dp + (long long)i * nJ + j) : 0.0;
+        if (fixed) {
+          const double x = d * (double)scf, hx = rint(x);
+          hv[m] = (float)hx;
+          lv[m] = (float)(x - hx);
+          h2v[m] = l2v[m] = 0.f;  // the halved tiles are unused in force launches
+        } else {
+          const float x = (float)d * scf;
+          hv[m] = __half2float(__float2half_rn(x));
+          lv[m] = x - hv[m];
+          h2v[m] = __half2float(__float2half_rn(0.5f * x));
+          l2v[m] = 0.5f * x - h2v[m];
+        }
       }
-      const __half h = __float2half_rn((float)x), h2 = __float2half_rn((float)(0.5 * x));
-      S.Dhl[q] = h;
-      S.Dhl[q + 64] = __float2half_rn((float)(x - (double)__half2float(h)));
-      S.Dhl2[q] = h2;
-      S.Dhl2[q + 64] = __float2half_rn((float)(0.5 * x - (double)__half2float(h2)));
-    } else {
-      S.Dhl[q] = S.Dhl[q + 64] = S.Dhl2[q] = S.Dhl2[q + 64] = __float2half(0.f);
+      const __half2 a = __floats2half2_rn(hv[0], hv[1]), b = __floats2half2_rn(lv[0], lv[1]);
+      const __half2 c = __floats2half2_rn(h2v[0], h2v[1]), e = __floats2half2_rn(l2v[0], l2v[1]);
+      wh[k >> 1] = *reinterpret_cast<const uint32_t *>(&a);
+      wl[k >> 1] = *reinterpret_cast<const uint32_t *>(&b);
+      w2h[k >> 1] = *reinterpret_cast<const uint32_t *>(&c);
+      w2l[k >> 1] = *reinterpret_cast<const uint32_t *>(&e);
     }
+    const long long q = 2 * to + (long long)cm * 128 + r8 * 8;  // hi of the row; lo 64 halves later
+    *reinterpret_cast<uint4 *>(S.Dhl + q) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+    *reinterpret_cast<uint4 *>(S.Dhl + q + 64) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+    *reinterpret_cast<uint4 *>(S.Dhl2 + q) = make_uint4(w2h[0], w2h[1], w2h[2], w2h[3]);
+    *reinterpret_cast<uint4 *>(S.Dhl2 + q + 64) = make_uint4(w2l[0], w2l[1], w2l[2], w2l[3]);
   }
 }
 
-// One CTA per pair of any system.
-__global__ void k_build_tiles(const __grid_constant__ GTabs g, const __grid_constant__ GTile TB) {
-  const long long gp = blockIdx.x;
+// One warp per pair of any system, eight pairs per CTA.
+constexpr int kTileWarps = 8;
+__global__ void __launch_bounds__(32 * kTileWarps) k_build_tiles(const __grid_constant__ GTabs g,
+                                                                 const __grid_constant__ GTile TB) {
+  const long long gp = (long long)blockIdx.x * kTileWarps + (threadIdx.x >> 5);
+  if (gp >= TB.start[TB.nsys]) return;
   int lo = 0, hi = TB.nsys - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -1721,7 +1747,7 @@ __global__ void k_build_tiles(const __grid_constant__ GTabs g, const __grid_cons
     else
       hi = mid - 1;
   }
-  build_tile(g, TB.sys[lo], (int)(gp - TB.start[lo]), TB.fixed != 0, threadIdx.x, blockDim.x);
+  build_tile_warp(g, TB.sys[lo], (int)(gp - TB.start[lo]), TB.fixed != 0, threadIdx.x & 31);
 }
 
 // One CTA per brick: the brick's metadata exactly as the brick kernel's slow path builds it,
@@ -2003,8 +2029,8 @@ __global__ void __launch_bounds__(kT, 1)
       __syncthreads();
       if (go && !*(volatile unsigned *)err) {
         const long long p0 = (li - J.n_prep - 1) * kServeTilePairs;
-        for (long long p = p0 + (t >> 7); p < min((long long)J.npairs, p0 + kServeTilePairs); p += kT / 128)
-          build_tile(g, J.tile, (int)p, J.fixed != 0, t & 127, 128);
+        for (long long p = p0 + (t >> 5); p < min((long long)J.npairs, p0 + kServeTilePairs); p += kT / 32)
+          build_tile_warp(g, J.tile, (int)p, J.fixed != 0, t & 31);
       }
     } else if (li < r0) {  // a brick
       const long long b = li - b0;
@@ -2616,7 +2642,7 @@ static int run_group(const gint_task *tk, int n, int split3, cudaStream_t st, cu
   k_prep_scales<<<1, kMaxBatch, 0, st>>>(P);
   TC_CHECK(cudaGetLastError());
   if (pairs > 0) {
-    k_build_tiles<<<(unsigned)pairs, 128, 0, st>>>(tabs, TB);
+    k_build_tiles<<<(unsigned)((pairs + kTileWarps - 1) / kTileWarps), 32 * kTileWarps, 0, st>>>(tabs, TB);
     TC_CHECK(cudaGetLastError());
   }
   if (items > 0) {
