@@ -105,7 +105,8 @@ int gint_create(const gint_desc *desc, gint_handle **out);
 int gint_destroy(gint_handle *h);
 
 /* Sizes of the block layout: total orbitals, number of pairs, float64 elements of a
- * block array.  Any output pointer may be NULL. */
+ * block array (the sparse atom-pair blocks of D and H of paper Sec. 3.3.1, R summed at the Gamma
+ * point).  Any output pointer may be NULL. */
 int gint_layout(const gint_handle *h, int *norb, int *npairs, long long *nblock_elems);
 
 /* Copies the pair list to host arrays: pair_IJ [npairs][2], pair_off [npairs + 1]. */
@@ -147,8 +148,9 @@ int gint_orbitals(gint_handle *h, int precision, long long npts, const double *p
 int gint_memory(const gint_handle *h, long long *device_bytes);
 
 /* Replaces the atom positions from a DEVICE array [natoms][3] and rebuilds the neighbour
- * lists on the device.  The pair set stays fixed: GINT_ESKIN if a pair outside it now
- * overlaps.  Synchronises the stream. */
+ * lists on the device (the BigGrid neighbour relation of paper Sec. 3.3.1 and Fig. 2, renewed as
+ * the ions move in the Ehrenfest dynamics of Sec. 2).  The pair set stays fixed: GINT_ESKIN if a
+ * pair outside it now overlaps.  Synchronises the stream. */
 int gint_set_positions(gint_handle *h, const double *pos_dev, void *stream);
 
 /* Density pass: rho [n1 n2 n3] (device, overwritten) from D blocks (device). */
@@ -290,7 +292,8 @@ typedef struct gint_task {
   double *F;
 } gint_task;
 
-/* Runs the tasks of several systems together (continuous batching of a serving loop).  With the
+/* Runs the tasks of several systems together (the batched dense-tile reformulation of paper
+ * Sec. 3.3.1, here across systems as well as bricks; a serving loop's batches).  With the
  * tensor-core precisions the bricks of all tasks (density / force bricks and local-H bricks) are
  * items of ONE persistent launch, up to 32 tasks per launch (more are split into groups of 32);
  * the per-pair H reduction and the per-call preparation are one launch each for the group.
@@ -340,7 +343,8 @@ int gint_server_stop(gint_server *s);
 int gint_server_destroy(gint_server *s);
 
 /* Float64 reductions on the device, written to out_dev[0] (device):
- *   V != NULL: w * sum_g V_g rho_g  (the energy E);   V == NULL: w * sum_g rho_g (N_e = Tr(DS)). */
+ *   V != NULL: w * sum_g V_g rho_g  (the energy E whose derivative is the local Pulay force of
+ *   paper Sec. 3.3.1);   V == NULL: w * sum_g rho_g (N_e = Tr(DS)). */
 int gint_grid_dot(gint_handle *h, const double *V, const double *rho, double *out_dev, void *stream);
 
 /* Float64 block-array dot product sum_p sum_e A[e] B[e] written to out_dev[0] (e.g. Tr(DH)). */
