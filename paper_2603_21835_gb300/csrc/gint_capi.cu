@@ -216,6 +216,7 @@ int create_impl(const gint_desc *d, bool unfold, gint_handle **out) {
   g.nbj = (d->n2 + GINT_BJ - 1) / GINT_BJ;
   g.nbk = (d->n3 + GINT_BK - 1) / GINT_BK;
   g.nbricks = (long long)g.nbi * g.nbj * g.nbk;
+  if (g.nbricks >= (1LL << 31)) TRY(GINT_ECAPACITY);  // brick indices are 32-bit in the kernels
   g.natoms = d->natoms;
   g.nspecies = d->nspecies;
   // radial tables

@@ -88,10 +88,13 @@ __host__ __device__ __forceinline__ void grid_point(const GCell &g, int i, int j
 }
 
 // Decode a local point index 0..127 of a brick into grid indices; returns false outside the grid.
+// (brick indices fit 32 bits: gint_create refuses grids of 2^31 bricks or more, so the divisions
+// are 32-bit ones, several times cheaper on the GPU than 64-bit ones)
 __host__ __device__ __forceinline__ bool brick_point(const GCell &g, long long b, int p, int &i, int &j, int &k) {
-  int bk = (int)(b % g.nbk);
-  int bj = (int)((b / g.nbk) % g.nbj);
-  int bi = (int)(b / ((long long)g.nbk * g.nbj));
+  const unsigned ub = (unsigned)b, nbk = (unsigned)g.nbk, q = ub / nbk;
+  const int bk = (int)(ub - q * nbk);
+  const int bj = (int)(q % (unsigned)g.nbj);
+  const int bi = (int)(q / (unsigned)g.nbj);
   int pk = p % GINT_BK, pj = (p / GINT_BK) % GINT_BJ, pi = p / (GINT_BK * GINT_BJ);
   i = bi * GINT_BI + pi;
   j = bj * GINT_BJ + pj;
