@@ -1463,7 +1463,7 @@ __device__ __forceinline__ void bar_sync(int id, int nthreads) {
 // part_lo hold (NG - 1) kRedE kRedLanes floats each; the groups synchronise on barrier `bar`.
 // F64: every tile value converted and added in float64 (a part's float64 sum travels between the
 // groups as the two 32-bit halves of its bits in part_lo / part_hi), the same parts and order.
-template <int NG, bool F64>
+template <int NG, bool F64, bool PF>
 __device__ __forceinline__ void reduce_pair_t(const GTabs &g, const GRedSys &S, int u, int tid, float *part_hi,
                                               float *part_lo, int bar) {
   const int p = S.hu_pair[u];
@@ -1500,15 +1500,28 @@ __device__ __forceinline__ void reduce_pair_t(const GTabs &g, const GRedSys &S, 
       }
     };
     long long k = k0;
-    for (; k + kRedB <= k1; k += kRedB) {
-      long long o[kRedB];
+    // PF: the next batch's tile offsets are loaded while the current batch's values are summed, so
+    // the offset and value loads of a batch are not two round trips in a row (the standalone
+    // reduction; the resident kernel keeps the lighter loop, its registers being spoken for)
+    long long o[kRedB];
+    if (PF && k + kRedB <= k1) {
 #pragma unroll
       for (int jj = 0; jj < kRedB; ++jj) o[jj] = __ldg(src + k + jj);
+    }
+    for (; k + kRedB <= k1; k += kRedB) {
+      if (!PF) {
+#pragma unroll
+        for (int jj = 0; jj < kRedB; ++jj) o[jj] = __ldg(src + k + jj);
+      }
       float v[kRedB][kRedE];
 #pragma unroll
       for (int jj = 0; jj < kRedB; ++jj)
 #pragma unroll
         for (int q = 0; q < kRedE; ++q) v[jj][q] = __ldcg(hs + o[jj] + e[q]);  // written by this or another launch
+      if (PF && k + 2 * kRedB <= k1) {
+#pragma unroll
+        for (int jj = 0; jj < kRedB; ++jj) o[jj] = __ldg(src + k + kRedB + jj);
+      }
 #pragma unroll
       for (int jj = 0; jj < kRedB; ++jj)
 #pragma unroll
@@ -1552,13 +1565,13 @@ __device__ __forceinline__ void reduce_pair_t(const GTabs &g, const GRedSys &S, 
   }
 }
 
-template <int NG>
+template <int NG, bool PF = false>
 __device__ __forceinline__ void reduce_pair(const GTabs &g, const GRedSys &S, int u, int tid, float *part_hi,
                                             float *part_lo, int bar) {
   if (S.fp64)
-    reduce_pair_t<NG, true>(g, S, u, tid, part_hi, part_lo, bar);
+    reduce_pair_t<NG, true, PF>(g, S, u, tid, part_hi, part_lo, bar);
   else
-    reduce_pair_t<NG, false>(g, S, u, tid, part_hi, part_lo, bar);
+    reduce_pair_t<NG, false, PF>(g, S, u, tid, part_hi, part_lo, bar);
 }
 
 __global__ void __launch_bounds__(kRedThreads, 4) k_h_reduce(const __grid_constant__ GTabs g, const __grid_constant__ GRed R) {
@@ -1572,7 +1585,7 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_h_reduce(const __grid_consta
     else
       hi = mid - 1;
   }
-  reduce_pair<kRedGroups>(g, R.sys[lo], (int)(gu - R.start[lo]), threadIdx.x, part_hi, part_lo, 0);
+  reduce_pair<kRedGroups, true>(g, R.sys[lo], (int)(gu - R.start[lo]), threadIdx.x, part_hi, part_lo, 0);
 }
 
 // ------------------------------------------------------------------------------ batched preparation
