@@ -945,12 +945,13 @@ case GINT_SHAPE(ns, np_, nd):                                                   
     // ---- phase B: chunks of 16 columns, prefetch warps / MMA thread / epilogue warps
     const uint32_t corr_base = (NP <= 256) ? 256u : 0u;  // separate correction accumulator if it fits
     if (warp == kMmaWarp) {
-      if (lane == 0 && NP <= 256 && split3 && corr_base) {
+      if (NP <= 256 && split3 && corr_base) {
         // common case, straight-line issue (branches and descriptor rebuilds in this loop cost more
-        // issue time than the MMAs take to run): the descriptors' start-address field (bytes / 16)
-        // advances by constants, 256 bytes of P per chunk and 2 bop per stage.  The stage barrier
-        // orders the copies before the MMAs; the epilogue's tensor-memory reads touch finished
-        // columns only, so one tcgen05 fence per item suffices.
+        // issue time than the MMAs take to run): the whole warp runs the loop and one elected lane
+        // issues, the descriptors' start-address field (bytes / 16) advancing by constants, 256
+        // bytes of P per chunk and 2 bop per stage.  The stage barrier orders the copies before the
+        // MMAs; the epilogue's tensor-memory reads touch finished columns only, so one tcgen05
+        // fence per item suffices.
         unsigned *errp = S.err;
         uint32_t s = 0, wrap = 0;
         const uint64_t dah0 = sdesc(smem_u32(Ph), 128, sboP), dal0 = sdesc(smem_u32(Pl), 128, sboP);
@@ -963,11 +964,14 @@ case GINT_SHAPE(ns, np_, nd):                                                   
           const uint32_t id = idesc_f16(128, NP - (int)rowbase), acc = c > 0 ? 1u : 0u;
           const uint64_t dah = dah0 + (uint64_t)(16 * c), dal = dal0 + (uint64_t)(16 * c);
           const uint64_t dbh = dbh0 + (uint64_t)(s * sstep), dbl = dbh + lstep;
-          mma_f16(tmem + rowbase, dah, dbh, id, acc);
-          mma_f16(tmem + 256u + rowbase, dah, dbl, id, acc);
-          mma_f16(tmem + 256u + rowbase, dal, dbh, id, 1u);
-          if (FORCE) mma_f16(tmem + 256u + rowbase, dal, dbl, id, 1u);  // fixed-point split: lo * lo too
-          mma_commit(&sh.done[c]);
+          if (elect_one()) {
+            mma_f16(tmem + rowbase, dah, dbh, id, acc);
+            mma_f16(tmem + 256u + rowbase, dah, dbl, id, acc);
+            mma_f16(tmem + 256u + rowbase, dal, dbh, id, 1u);
+            if (FORCE) mma_f16(tmem + 256u + rowbase, dal, dbl, id, 1u);  // fixed-point split: lo * lo too
+            mma_commit(&sh.done[c]);
+          }
+          __syncwarp();
           if (++s == (uint32_t)nst) {
             s = 0;
             wrap ^= 1u;
@@ -1200,10 +1204,11 @@ case GINT_SHAPE(ns, np_, nd):                                                   
         }
         fence_async_smem();
         __syncthreads();
-        if (t == 0 && NP <= 256 && split3) {
-          // common case, straight-line issue: at most two 128-row tiles of one N <= 256 each; the
-          // descriptors' start-address field advances by 2 sboP / 16 per K step of 16 points, and by
-          // 2048 / 16 from the first to the second tile (orbitals 128-255, rows of A and columns of B)
+        if (warp == 0 && NP <= 256 && split3) {
+          // common case, straight-line issue by an elected lane of warp 0 (which builds no block):
+          // at most two 128-row tiles of one N <= 256 each; the descriptors' start-address field
+          // advances by 2 sboP / 16 per K step of 16 points, and by 2048 / 16 from the first to the
+          // second tile (orbitals 128-255, rows of A and columns of B)
           tc_fence_after();
           const uint64_t wh0 = sdesc(smem_u32(Wh), sboP, 128), wl0 = sdesc(smem_u32(Wl), sboP, 128);
           const uint32_t pofs = (uint32_t)(p0 >> 3) * sboP;
@@ -1212,20 +1217,23 @@ case GINT_SHAPE(ns, np_, nd):                                                   
           const uint32_t id0 = idesc_f16_mn(128, NP), id1 = idesc_f16_mn(128, NP > 128 ? NP - 128 : 16);
           const uint32_t m0 = tmem + (uint32_t)tb[0], m1 = tmem + (uint32_t)tb[1];
           const uint32_t c0 = m0 + corr_base, c1 = m1 + corr_base;
-          for (int ks = 0; ks < hkb / 16; ++ks) {
-            const uint64_t ko = (uint64_t)ks * kstep;
-            const bool first = (j == 0 && ks == 0);
-            const uint32_t am = first ? 0u : 1u, ac = (first && corr_base) ? 0u : 1u;
-            mma_f16(m0, wh0 + ko, ph0 + ko, id0, am);
-            mma_f16(c0, wh0 + ko, pl0 + ko, id0, ac);
-            mma_f16(c0, wl0 + ko, ph0 + ko, id0, 1u);
-            if (NP > 128) {
-              mma_f16(m1, wh0 + ko + 128u, ph0 + ko + 128u, id1, am);
-              mma_f16(c1, wh0 + ko + 128u, pl0 + ko + 128u, id1, ac);
-              mma_f16(c1, wl0 + ko + 128u, ph0 + ko + 128u, id1, 1u);
+          if (elect_one()) {
+            for (int ks = 0; ks < hkb / 16; ++ks) {
+              const uint64_t ko = (uint64_t)ks * kstep;
+              const bool first = (j == 0 && ks == 0);
+              const uint32_t am = first ? 0u : 1u, ac = (first && corr_base) ? 0u : 1u;
+              mma_f16(m0, wh0 + ko, ph0 + ko, id0, am);
+              mma_f16(c0, wh0 + ko, pl0 + ko, id0, ac);
+              mma_f16(c0, wl0 + ko, ph0 + ko, id0, 1u);
+              if (NP > 128) {
+                mma_f16(m1, wh0 + ko + 128u, ph0 + ko + 128u, id1, am);
+                mma_f16(c1, wh0 + ko + 128u, pl0 + ko + 128u, id1, ac);
+                mma_f16(c1, wl0 + ko + 128u, ph0 + ko + 128u, id1, 1u);
+              }
             }
+            mma_commit(&sh.hdone[hh]);
           }
-          mma_commit(&sh.hdone[hh]);
+          __syncwarp();
         } else if (t == 0) {
           tc_fence_after();
           for (int ks = 0; ks < hkb / 16; ++ks) {
