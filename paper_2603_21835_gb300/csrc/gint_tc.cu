@@ -337,6 +337,7 @@ struct BrickSh {
   uint64_t full[kMaxStages];  // density: B stage loaded (bulk-copy transactions)
   uint64_t done[kMaxChunks];  // density: MMAs of chunk c complete (one use per brick)
   uint64_t hdone[2];          // local H: MMAs of a stage complete
+  uint64_t hbuilt[2];         // local H: W P block of a stage written (one arrival per builder warp)
   uint32_t tmem;
   int item, na, np, nent, abort;
   int s_atom[kMAXA], s_no[kMAXA], s_po[kMAXA], s_sp[kMAXA], s_pcol[kMAXA], s_e0[kMAXA + 1];
@@ -1150,7 +1151,10 @@ case GINT_SHAPE(ns, np_, nd):                                                   
       // ================================================================ local H from P
       // H_mu,nu = sum_g (w V_g P_g,mu) P_g,nu: K = grid points in blocks of hkb, both operands
       // MN-major views of [point][orbital] buffers (P itself, and W P built per block in one of
-      // two halves of the stage region, ping-pong with the MMAs of the previous block).
+      // two halves of the stage region, ping-pong with the MMAs of the previous block).  Warps
+      // 1-15 build the blocks and warp 0 issues their MMAs, the two sides paced by mbarriers only
+      // (hbuilt: a half has been written; hdone: its MMAs are complete and it may be rewritten), so
+      // the builders run one block ahead of the MMAs without a CTA-wide barrier per block.
       tc_fence_before();  // the density part's tensor-memory reads are finished
       __syncthreads();
       tc_fence_after();
@@ -1178,13 +1182,14 @@ case GINT_SHAPE(ns, np_, nd):                                                   
       for (int j = 0; j < 128 / hkb; ++j, ++GH) {
         const int hh = GH & 1;
         unsigned char *Wh = B0 + hh * whalf, *Wl = Wh + whalf / 2;
+        const int p0 = j * hkb;
+        if (warp != 0) {
         // the MMAs that last read this half (two blocks ago) are complete
         if (GH >= 2 && !mbar_wait(&sh.hdone[hh], ((GH - 2) >> 1) & 1, S.err)) ok = false;
-        const int p0 = j * hkb;
-        // warps 1-15 build the block while thread 0 may still be issuing the previous block's MMAs.
+        // warps 1-15 build the block while warp 0 may still be issuing the previous block's MMAs.
         // Unit u = (point octet, orbital group, point in octet) with the point fastest: eight
         // consecutive threads touch one 128-byte core-matrix row block (no bank conflicts).
-        for (int u = t - 32; u >= 0 && u < hkb * ng; u += kT - 32) {
+        for (int u = t - 32; u < hkb * ng; u += kT - 32) {
           const int v8 = u >> 3, po8 = v8 / ng, gg = v8 - po8 * ng;
           const int pl = po8 * 8 + (u & 7), pt = p0 + pl;
           const uint32_t so = (pt >> 3) * sboP + gg * 128 + (pt & 7) * 16;
@@ -1202,9 +1207,13 @@ case GINT_SHAPE(ns, np_, nd):                                                   
           *reinterpret_cast<uint4 *>(Wh + dso) = make_uint4(oh[0], oh[1], oh[2], oh[3]);
           *reinterpret_cast<uint4 *>(Wl + dso) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
         }
-        fence_async_smem();
-        __syncthreads();
-        if (warp == 0 && NP <= 256 && split3) {
+        fence_async_smem();  // this thread's writes before the MMAs' (async-proxy) reads
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.hbuilt[hh]);
+        } else {
+        // warp 0: the block's W P is complete (every builder warp has arrived)
+        if (!mbar_wait(&sh.hbuilt[hh], (GH >> 1) & 1, S.err)) ok = false;
+        if (NP <= 256 && split3) {
           // common case, straight-line issue by an elected lane of warp 0 (which builds no block):
           // at most two 128-row tiles of one N <= 256 each; the descriptors' start-address field
           // advances by 2 sboP / 16 per K step of 16 points, and by 2048 / 16 from the first to the
@@ -1234,7 +1243,7 @@ case GINT_SHAPE(ns, np_, nd):                                                   
             mma_commit(&sh.hdone[hh]);
           }
           __syncwarp();
-        } else if (t == 0) {
+        } else if (lane == 0) {
           tc_fence_after();
           for (int ks = 0; ks < hkb / 16; ++ks) {
             const uint32_t kw = (uint32_t)(2 * ks) * sboP, kp = (uint32_t)((p0 >> 3) + 2 * ks) * sboP;
@@ -1260,12 +1269,15 @@ case GINT_SHAPE(ns, np_, nd):                                                   
           }
           mma_commit(&sh.hdone[hh]);
         }
+        __syncwarp();
+        }
       }
       {
         const uint32_t Gp = GH - 1;
         if (!mbar_wait(&sh.hdone[Gp & 1], (Gp >> 1) & 1, S.err)) ok = false;
         tc_fence_after();
       }
+      __syncthreads();  // every block built and its MMAs complete; the column table is visible
     // epilogue: upper slot-pair tiles -> scratch (float32, unscaled), column-major: tile (a, c),
     // a <= c, holds norb(c) columns of norb(a) rows at rowst(a) + norb(a) (cumno(c) - cumno(a));
     // element (i, j) at j norb(a) + i (the row-major norb(c) x norb(a) block (c, a) of the
@@ -1360,6 +1372,8 @@ __global__ void __launch_bounds__(kT, 1)
     for (int c = 0; c < kMaxChunks; ++c) mbar_init(&sh.done[c], 1);
     mbar_init(&sh.hdone[0], 1);
     mbar_init(&sh.hdone[1], 1);
+    mbar_init(&sh.hbuilt[0], kT / 32 - 1);
+    mbar_init(&sh.hbuilt[1], kT / 32 - 1);
     mbar_init(&sh.plan_bar, 1);
     fence_mbar_init();
     sh.abort = 0;
@@ -1925,6 +1939,8 @@ __global__ void __launch_bounds__(kT, 1)
     for (int c = 0; c < kMaxChunks; ++c) mbar_init(&sh.done[c], 1);
     mbar_init(&sh.hdone[0], 1);
     mbar_init(&sh.hdone[1], 1);
+    mbar_init(&sh.hbuilt[0], kT / 32 - 1);
+    mbar_init(&sh.hbuilt[1], kT / 32 - 1);
     mbar_init(&sh.plan_bar, 1);
     fence_mbar_init();
   }
