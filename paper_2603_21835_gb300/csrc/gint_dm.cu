@@ -231,25 +231,28 @@ __global__ void __launch_bounds__(kDmThreads, 1)
   bool ok = true;
 
   if (warp == 0) {
-    // lane 0 issues: chunk c's MMAs (hi hi into ring slot c mod kHH, hi lo + lo hi into the cross
-    // slot), then the refill of chunk c - 1's stage once its MMAs are done; the warp drains chunk
-    // c - 2 (the slot the MMAs of chunk c + 1 will take).
+    // the warp runs the issue loop together (warp-uniform descriptor arithmetic; one elected lane
+    // issues, which keeps the tensor pipe fed better than a loop confined to one lane): chunk c's
+    // MMAs (hi hi into ring slot c mod kHH, hi lo + lo hi into the cross slot), then the refill of
+    // chunk c - 1's stage once its MMAs are done (lane 0 issues the copies); the warp drains chunk
+    // c - 2 (the slot the MMAs of chunk c + 1 will take).  Wait results are lane 0's, broadcast.
     const uint32_t idesc = idesc_f16(kTile, kTile), sbase = smem_u32(smem), dx = tmem + kCrossCol;
     int issued = 0, consumed = 0;
-    if (lane == 0)
-      for (; issued < min(kStages, nq); ++issued) dm_load(sh, smem, PA, PB, I, J, nq, issued);
+    for (; issued < min(kStages, nq); ++issued)
+      if (lane == 0) dm_load(sh, smem, PA, PB, I, J, nq, issued);
     for (int c = 0; c < nq && ok; ++c) {
-      bool lok = true;
-      if (lane == 0) {
-        const int s = c % kStages, a = c % kHH;
-        lok = mbar_wait(&sh.full[s], (uint32_t)(c / kStages) & 1u, status, kErrTimeout, kWaitNs);
-        if (lok) consumed = c + 1;
-        if (lok && c >= kHH)
-          lok = mbar_wait(&sh.hfree[a], (uint32_t)((c / kHH) - 1) & 1u, status, kErrTimeout, kWaitNs);
-        if (lok) {
-          tc_fence_after();
-          const uint32_t sa = sbase + s * kStageBytes, sb = sa + kBlockBytes;
-          const uint32_t dh = tmem + (uint32_t)a * 128u;
+      const int s = c % kStages, a = c % kHH;
+      bool lok = mbar_wait(&sh.full[s], (uint32_t)(c / kStages) & 1u, status, kErrTimeout, kWaitNs);
+      lok = __shfl_sync(0xffffffffu, lok, 0);
+      if (lok) consumed = c + 1;
+      if (lok && c >= kHH)
+        lok = __shfl_sync(0xffffffffu,
+                          mbar_wait(&sh.hfree[a], (uint32_t)((c / kHH) - 1) & 1u, status, kErrTimeout, kWaitNs), 0);
+      if (lok) {
+        tc_fence_after();
+        const uint32_t sa = sbase + s * kStageBytes, sb = sa + kBlockBytes;
+        const uint32_t dh = tmem + (uint32_t)a * 128u;
+        if (elect_one()) {
 #pragma unroll
           for (int ks = 0; ks < kKC / 16; ++ks) {
             const uint32_t o = ks * 256;  // two core matrices along K per step
@@ -261,18 +264,25 @@ __global__ void __launch_bounds__(kDmThreads, 1)
           }
           mma_commit(&sh.empty[s]);
           mma_commit(&sh.hfull[a]);
-          if (c >= 1 && issued < nq) {
-            lok = mbar_wait(&sh.empty[(c - 1) % kStages], (uint32_t)((c - 1) / kStages) & 1u, status, kErrTimeout,
-                            kWaitNs);
-            if (lok) dm_load(sh, smem, PA, PB, I, J, nq, issued++);
+        }
+        __syncwarp();
+        if (c >= 1 && issued < nq) {
+          lok = __shfl_sync(0xffffffffu,
+                            mbar_wait(&sh.empty[(c - 1) % kStages], (uint32_t)((c - 1) / kStages) & 1u, status,
+                                      kErrTimeout, kWaitNs),
+                            0);
+          if (lok) {
+            if (lane == 0) dm_load(sh, smem, PA, PB, I, J, nq, issued);
+            ++issued;
           }
         }
       }
-      ok = __shfl_sync(0xffffffffu, lok, 0);
+      ok = lok;
       if (ok && c >= 2) ok = dm_drain(sh, lane_base, c - 2, sum, cmp, status);
     }
+    if (elect_one()) mma_commit(&sh.done);  // the lane that issued the MMAs
+    __syncwarp();
     if (lane == 0) {
-      mma_commit(&sh.done);
       // no copy may still be landing in shared memory when the CTA exits
       for (int c = consumed; c < issued; ++c)
         mbar_wait(&sh.full[c % kStages], (uint32_t)(c / kStages) & 1u, status, kErrTimeout, kWaitNs);

@@ -1348,10 +1348,10 @@ __global__ void __launch_bounds__(kT, 1)
   const int t = threadIdx.x, warp = t >> 5;
   const int split3 = B.split3;
   const long long total = B.start[B.nsys];
-  // thread 0: fetches the next item and starts the bulk copy of its plan record into planbuf
-  // (the buffer is free: the current item's record was unpacked before the last barrier)
-  auto next_item = [&]() {
-    const long long nx = atomicAdd(work, 1);
+  // thread 0: publishes the next item (nx, claimed from the work counter) and starts the bulk copy
+  // of its plan record into planbuf (the buffer is free: the current item's record was unpacked
+  // before the last barrier)
+  auto next_item = [&](long long nx) {
     sh.item = (int)nx;
     sh.plan_pref = 0;
     if (nx >= total) return;
@@ -1377,7 +1377,7 @@ __global__ void __launch_bounds__(kT, 1)
     mbar_init(&sh.plan_bar, 1);
     fence_mbar_init();
     sh.abort = 0;
-    next_item();
+    next_item(atomicAdd(work, 1));
   }
   if (warp == 0) {
     tmem_alloc(&sh.tmem, 512);
@@ -1401,6 +1401,10 @@ __global__ void __launch_bounds__(kT, 1)
       if (pref) mbar_wait(&sh.plan_bar, pphase & 1u, B.sys[0].err);  // no copy may be in flight at exit
       break;
     }
+    // the next item is claimed now and published after the unpack: the atomic's round trip overlaps
+    // the set-up instead of delaying thread 0's share of the orbital phase
+    long long nclaim = 0;
+    if (t == 0) nclaim = atomicAdd(work, 1);
     const int sidx = batch_sys(B, it);
     const GSys &S = B.sys[sidx];
     const long long b = it - B.start[sidx];
@@ -1435,7 +1439,7 @@ __global__ void __launch_bounds__(kT, 1)
       if (t == 0) bulk_wait_read();
       load_brick(S.c, g, S.nb, S.tile_off, b, sh);  // ends with a barrier
     }
-    if (t == 0) next_item();  // every thread has read sh.item and sh.plan_pref
+    if (t == 0) next_item(nclaim);  // every thread has read sh.item and sh.plan_pref
     ItemCtx cx{fpar, dpar, GH, ok, vpend};
     brick_body<FORCE>(g, S, b, do_rho, do_h, split3, B.dsmem, zero, tmem, sh, smem, cx);
     fpar = cx.fpar;
