@@ -733,7 +733,8 @@ struct ItemCtx {
   uint32_t dpar;  // bit c: phase parity of done[c] (used once per density brick that has a chunk c)
   uint32_t GH;    // local-H stages issued by this CTA
   bool ok;        // no bounded wait has given up
-  bool vpend;     // V of the brick's points is in flight to sh.vd (threads 0-127 each copy one value)
+  bool vpend;     // V of the brick's points is wanted in sh.vd: orbital slice 3 (the last four warps)
+                  // copies one value per thread asynchronously during the orbital phase
 };
 template <bool FORCE>
 __device__ __forceinline__ void brick_body(const GTabs &g, const GSys &S, long long b, bool do_rho, bool do_h,
@@ -758,9 +759,15 @@ __device__ __forceinline__ void brick_body(const GTabs &g, const GSys &S, long l
     const bool valid = brick_point(S.c, b, p, gi, gj, gk);
     const long long gidx = valid ? grid_index(S.c, gi, gj, gk) : 0;
     if (na == 0) {
-      if (cx.vpend && t < 128) cp_async_wait_all();  // no copy into sh.vd outlives the item
+      if (cx.vpend && q == 3) cp_async_wait_all();  // no copy into sh.vd outlives the item
       if (do_rho && q == 0 && valid && S.rho) S.rho[gidx] = 0.0;
       return;
+    }
+    if (cx.vpend && q == 3) {  // V of this thread's point (slice 3 has the fewest atoms)
+      if (valid)
+        cp_async8(&sh.vd[p], S.V + gidx);
+      else
+        sh.vd[p] = 0.0;
     }
     const int nch = NP / kRC;
     const uint32_t sboP = 16u * (uint32_t)NP;  // P row-group stride
@@ -936,9 +943,9 @@ case GINT_SHAPE(ns, np_, nd):                                                   
           *reinterpret_cast<uint4 *>(Pl + off) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
         }
     }
-    if (cx.vpend && t < 128) {  // the copy has had the orbital phase to land
+    if (cx.vpend && q == 3) {  // the copy has had the orbital phase to land
       cp_async_wait_all();
-      sh.wv[t] = (float)(S.c.w * sh.vd[t]);
+      sh.wv[p] = (float)(S.c.w * sh.vd[p]);
     }
     fence_async_smem();
     __syncthreads();
@@ -1348,9 +1355,12 @@ __global__ void __launch_bounds__(kT, 1)
   const int t = threadIdx.x, warp = t >> 5;
   const int split3 = B.split3;
   const long long total = B.start[B.nsys];
-  // thread 0: publishes the next item (nx, claimed from the work counter) and starts the bulk copy
-  // of its plan record into planbuf (the buffer is free: the current item's record was unpacked
-  // before the last barrier)
+  // publishes the next item (nx, claimed from the work counter) and starts the bulk copy of its plan
+  // record into planbuf (the buffer is free: the current item's record was unpacked before the last
+  // barrier).  Inside the item loop lane 0 of the last warp does this (kNextT): its orbital slice
+  // has the fewest atoms whenever the atom count is not a multiple of four, so the claim's round
+  // trip and the plan offsets' loads do not delay the slowest slice (thread 0's)
+  constexpr int kNextT = kT - 32;
   auto next_item = [&](long long nx) {
     sh.item = (int)nx;
     sh.plan_pref = 0;
@@ -1402,9 +1412,9 @@ __global__ void __launch_bounds__(kT, 1)
       break;
     }
     // the next item is claimed now and published after the unpack: the atomic's round trip overlaps
-    // the set-up instead of delaying thread 0's share of the orbital phase
+    // the set-up
     long long nclaim = 0;
-    if (t == 0) nclaim = atomicAdd(work, 1);
+    if (t == kNextT) nclaim = atomicAdd(work, 1);
     const int sidx = batch_sys(B, it);
     const GSys &S = B.sys[sidx];
     const long long b = it - B.start[sidx];
@@ -1418,16 +1428,10 @@ __global__ void __launch_bounds__(kT, 1)
       }
       cur = sidx;
     }
-    // w V at the brick's points: V is copied asynchronously (its DRAM latency would stall the set-up)
-    // and w V formed after the orbitals; the local-H pass and the force epilogue read it later
+    // w V at the brick's points: V is copied asynchronously at the start of the orbital phase by the
+    // last four warps (its DRAM latency would stall the set-up) and w V formed after the orbitals;
+    // the local-H pass and the force epilogue read it later
     const bool vpend = S.V && (do_h || FORCE);
-    if (t < 128 && vpend) {
-      int gi, gj, gk;
-      if (brick_point(S.c, b, t, gi, gj, gk))
-        cp_async8(&sh.vd[t], S.V + grid_index(S.c, gi, gj, gk));
-      else
-        sh.vd[t] = 0.0;
-    }
     // the previous item's local-H tiles have left shared memory (its bulk store has read them)
     // before this item writes any dynamic shared memory: thread 0 waits for that store before the
     // closing barrier of the unpack (the unpack itself writes static shared memory only)
@@ -1439,7 +1443,7 @@ __global__ void __launch_bounds__(kT, 1)
       if (t == 0) bulk_wait_read();
       load_brick(S.c, g, S.nb, S.tile_off, b, sh);  // ends with a barrier
     }
-    if (t == 0) next_item(nclaim);  // every thread has read sh.item and sh.plan_pref
+    if (t == kNextT) next_item(nclaim);  // every thread has read sh.item and sh.plan_pref
     ItemCtx cx{fpar, dpar, GH, ok, vpend};
     brick_body<FORCE>(g, S, b, do_rho, do_h, split3, B.dsmem, zero, tmem, sh, smem, cx);
     fpar = cx.fpar;
