@@ -604,6 +604,26 @@ def main():
             torch.cuda.synchronize()
             t_h64.append(a.elapsed_time(b))
         g.set_reduction("double-float")
+    # new positions (a molecular-dynamics step), on a second handle of the same system with a 0.5 Bohr
+    # pair skin: neighbour lists rebuilt on the device, then the plan records only (moves of 1e-6 Bohr
+    # keep every brick's atoms) or the whole tensor-core layout (moves of N(0, 0.02) Bohr change some
+    # bricks' atom sets); host wall clock around the synchronous call
+    t_pos = {}
+    if not args.no_extras and tensor:
+        gp = G.Gint(w.system, skin=0.5)
+        pos0 = torch.from_numpy(np.ascontiguousarray(w.system.pos)).to(dev)
+        for kind, sig in (("same_bricks", 1e-6), ("new_bricks", 0.02)):
+            ts = []
+            for k in range(3):
+                gen = torch.Generator(device="cpu").manual_seed(100 + k)
+                p2 = pos0 + sig * torch.randn(pos0.shape, generator=gen, dtype=torch.float64).to(dev)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                gp.set_positions(p2)
+                torch.cuda.synchronize()
+                ts.append(1e3 * (time.perf_counter() - t0))
+            t_pos[kind] = statistics.median(ts)
+        gp.close()
     ms_per_step = max_over_ranks(sum(t_steps), world, dev) / args.steps
     value = world * 2.0 * W / (ms_per_step * 1e-3) / 1e9
 
@@ -727,6 +747,7 @@ def main():
         "ms_kernel": tdom, "ms_rho_alone": statistics.mean(t_rho), "ms_vlocal_alone": statistics.mean(t_h),
         "ms_force_alone": statistics.mean(t_f),
         "ms_vlocal_alone_fp64_reduction": statistics.mean(t_h64) if t_h64 else None,
+        "ms_set_positions": t_pos or None,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "fp64_gpu": fp64_gpu,
         "mixed_over_fp64": fp64_gpu["mixed_over_fp64"] if fp64_gpu else None,
         "gpu_launches": launches * args.steps, "serving": serving, "per_R": per_R, "psibeta": psibeta,

@@ -521,7 +521,7 @@ int gint_set_positions(gint_handle *h, const double *pos_dev, void *stream) {
     return GINT_ECUDA;
   int rc = gint_build_neighbours(h, st);
   if (rc) return rc;
-  rc = gint_tc_prepare(h);
+  rc = gint_tc_refresh(h);
   if (rc) return rc;
   gint_hr_free(h);  // H(R) keys follow the new images (rebuilt on first use)
   if (cudaMemcpyAsync(h->pos_host.data(), h->pos_dev, 3 * sizeof(double) * h->geom.natoms, cudaMemcpyDeviceToHost,

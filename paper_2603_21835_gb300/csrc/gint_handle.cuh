@@ -92,6 +92,10 @@ struct gint_handle {
   uint4 *plan = nullptr;                  // per-brick plan records (brick metadata, prefetched by the kernel)
   long long *plan_off_dev = nullptr;      // [nbricks + 1] record offsets, 16-byte units
   long long tc_bytes = 0;                 // device bytes of the tensor-core workspace above
+  // the neighbour structure these layouts were built for (host copies: brick slot offsets, slot atoms,
+  // brick entry offsets); a rebuild for new positions that reproduces it refreshes the plan records only
+  std::vector<long long> tc_at_off, tc_ent_off;
+  std::vector<int> tc_satom;
   // local H per lattice vector (keys (I, J, R); built on first use by gint_hr_prepare)
   bool r_ready = false;
   int r_status = 0;           // GINT_OK, or why per-R output is unavailable for this geometry
@@ -158,6 +162,7 @@ int gint_tc_batch(const gint_task *tasks, int n, int precision, cudaStream_t st,
                   cudaEvent_t ev1);
 int gint_tc_check_capacity(const gint_handle *h);
 int gint_tc_prepare(gint_handle *h);  // layouts and scratch of the tensor-core path (after neighbours)
+int gint_tc_refresh(gint_handle *h);  // after a neighbour rebuild: plan records only, or gint_tc_prepare
 void gint_tc_free(gint_handle *h);
 // gint_hr.cu
 int gint_hr_prepare(gint_handle *h);  // key tables of H(R) (GINT_EUNSUPPORTED if tiles mix R)

@@ -56,48 +56,117 @@ __device__ __noinline__ void image_range(const GGeom &g, const double *pos, int 
   }
 }
 
-// Does the image T of an atom with support radius rc cover any grid point of the brick box?
-__device__ __noinline__ bool image_hits(const GGeom &g, const double T[3], double rc, const int lo[3],
-                                        const int hi[3], const double c[3], double rad) {
-  double D2 = (c[0] - T[0]) * (c[0] - T[0]) + (c[1] - T[1]) * (c[1] - T[1]) + (c[2] - T[2]) * (c[2] - T[2]);
-  if (D2 >= (rc + rad) * (rc + rad)) return false;
-  const double rc2 = rc * rc;
-  for (int ii = lo[0]; ii < hi[0]; ++ii)
-    for (int jj = lo[1]; jj < hi[1]; ++jj)
-      for (int kk = lo[2]; kk < hi[2]; ++kk) {
-        double p[3];
-        grid_point(g, ii, jj, kk, p);
-        double r2 = (p[0] - T[0]) * (p[0] - T[0]) + (p[1] - T[1]) * (p[1] - T[1]) + (p[2] - T[2]) * (p[2] - T[2]);
-        if (r2 < rc2) return true;
-      }
-  return false;
-}
-
-// Enumerates the lattice images of atom I covering brick b, in a fixed order.  For each
-// covering image calls emit(T[3]).  Returns the number of covering images.
-template <typename Emit>
-__device__ int brick_atom_images(const GGeom &g, const double *pos, const int *species, int I, const int lo[3],
-                                 const int hi[3], const double c[3], double rad, Emit emit) {
-  const double rc = g.sp[species[I]].rcut;
-  int nlo[3], nhi[3];
-  image_range(g, pos, I, rc, c, rad, nlo, nhi);
-  int count = 0;
-  for (int n0 = nlo[0]; n0 <= nhi[0]; ++n0)
-    for (int n1 = nlo[1]; n1 <= nhi[1]; ++n1)
-      for (int n2 = nlo[2]; n2 <= nhi[2]; ++n2) {
-        double T[3];
-        for (int d = 0; d < 3; ++d) T[d] = pos[3 * I + d] + n0 * g.cell[d] + n1 * g.cell[3 + d] + n2 * g.cell[6 + d];
-        if (image_hits(g, T, rc, lo, hi, c, rad)) {
-          emit(T);
-          ++count;
-        }
-      }
-  return count;
-}
-
-struct NoEmit {
-  __device__ void operator()(const double *) const {}
+// The brick's grid points relative to the brick-sphere centre c as float32, four per lane (point
+// q = lane + 32 k, k = 0..3, in the order kk fastest, then jj, then ii), for the warp-wide coverage
+// test.  n: the number of points in the box (128 except at the grid's upper faces).
+struct BrickPts {
+  float x[4], y[4], z[4];
+  int n;
 };
+__device__ __forceinline__ void point_of(const int lo[3], const int hi[3], int q, int &ii, int &jj, int &kk) {
+  const int ny = hi[1] - lo[1], nz = hi[2] - lo[2];
+  kk = lo[2] + q % nz;
+  jj = lo[1] + (q / nz) % ny;
+  ii = lo[0] + q / (nz * ny);
+}
+__device__ void brick_points(const GGeom &g, const int lo[3], const int hi[3], const double c[3], int lane,
+                             BrickPts &P) {
+  P.n = (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int q = lane + 32 * k;
+    P.x[k] = P.y[k] = P.z[k] = 0.f;
+    if (q < P.n) {
+      int ii, jj, kk;
+      point_of(lo, hi, q, ii, jj, kk);
+      double p[3];
+      grid_point(g, ii, jj, kk, p);
+      P.x[k] = (float)(p[0] - c[0]);
+      P.y[k] = (float)(p[1] - c[1]);
+      P.z[k] = (float)(p[2] - c[2]);
+    }
+  }
+}
+
+// Does the image T of an atom with support radius rc cover any grid point of the brick box (some
+// point strictly inside the sphere, float64)?  All 32 lanes take part with the same T and rc, each
+// testing its four points.  A float32 squared distance relative to the brick centre decides every
+// point outside a shell |r^2 - rc^2| < m around the sphere; a point inside the shell is decided by
+// the float64 test itself (same expression as a per-point loop), so the answer equals the float64
+// one.  Bound used for m: with |p - c| <= rad and |T - c| < rc + rad (the caller's bounding-sphere
+// test), each float32 difference is off by at most 2^-24 (2 rc + 4 rad) and the float32 r^2 by at
+// most 2 sqrt(3) (rc + 2 rad) 2^-24 (2 rc + 4 rad) + 4 2^-24 r^2, about 1e-7 (2 rc + 4 rad)^2 +
+// 2.4e-7 r^2; m is forty times the first term plus four times the second.  Warp-uniform result.
+__device__ bool warp_image_hits(const GGeom &g, const BrickPts &P, const double T[3], double rc, const int lo[3],
+                                const int hi[3], const double c[3], double rad, int lane) {
+  const float tx = (float)(T[0] - c[0]), ty = (float)(T[1] - c[1]), tz = (float)(T[2] - c[2]);
+  const double rc2 = rc * rc, ext = 2.0 * rc + 4.0 * rad;
+  const double m = 4e-6 * ext * ext + 1e-6 * rc2;
+  const float in2 = (float)(rc2 - m), out2 = (float)(rc2 + m);
+  bool hit = false;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int q = lane + 32 * k;
+    if (q >= P.n) continue;
+    const float dx = P.x[k] - tx, dy = P.y[k] - ty, dz = P.z[k] - tz;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 < in2) {
+      hit = true;
+    } else if (r2 < out2) {
+      int ii, jj, kk;
+      point_of(lo, hi, q, ii, jj, kk);
+      double p[3];
+      grid_point(g, ii, jj, kk, p);
+      const double e2 = (p[0] - T[0]) * (p[0] - T[0]) + (p[1] - T[1]) * (p[1] - T[1]) + (p[2] - T[2]) * (p[2] - T[2]);
+      if (e2 < rc2) hit = true;
+    }
+  }
+  return __any_sync(0xffffffffu, hit);
+}
+
+// The lattice images of the warp's atoms (lane l: atom a0 + l) near brick b, one candidate at a
+// time: every image in the atom's image range whose bounding-sphere test passes (centre distance
+// below rc + rad) is tested against the brick's points by the whole warp, in lane order and, within
+// a lane, in the order n0, n1, n2 ascending.  visit(src, T, hit) runs in every lane with the same
+// arguments (src: the lane whose atom the image belongs to).
+template <typename Visit>
+__device__ void warp_atom_images(const GGeom &g, const double *pos, const int *species, int a0, int lane,
+                                 const int lo[3], const int hi[3], const double c[3], double rad, const BrickPts &P,
+                                 Visit visit) {
+  const int I = a0 + lane;
+  const bool va = I < g.natoms;
+  const double rc = va ? g.sp[species[I]].rcut : 0.0;
+  int nlo[3] = {0, 0, 0}, nhi[3] = {-1, -1, -1};
+  if (va) image_range(g, pos, I, rc, c, rad, nlo, nhi);
+  const int s1 = max(0, nhi[1] - nlo[1] + 1), s2 = max(0, nhi[2] - nlo[2] + 1);
+  const int nimg = max(0, nhi[0] - nlo[0] + 1) * s1 * s2;
+  const double lim2 = (rc + rad) * (rc + rad);
+  int k = 0;
+  double T[3] = {0.0, 0.0, 0.0};
+  auto next = [&]() -> bool {
+    while (k < nimg) {
+      const int i0 = k / (s1 * s2), r = k - i0 * s1 * s2, i1 = r / s2, i2 = r - i1 * s2;
+      ++k;
+      const int n0 = nlo[0] + i0, n1 = nlo[1] + i1, n2 = nlo[2] + i2;
+      for (int d = 0; d < 3; ++d) T[d] = pos[3 * I + d] + n0 * g.cell[d] + n1 * g.cell[3 + d] + n2 * g.cell[6 + d];
+      const double D2 = (c[0] - T[0]) * (c[0] - T[0]) + (c[1] - T[1]) * (c[1] - T[1]) + (c[2] - T[2]) * (c[2] - T[2]);
+      if (!(D2 >= lim2)) return true;
+    }
+    return false;
+  };
+  bool cand = next();
+  for (;;) {
+    const unsigned m = __ballot_sync(0xffffffffu, cand);
+    if (!m) break;
+    const int src = __ffs(m) - 1;
+    double Ts[3];
+    for (int d = 0; d < 3; ++d) Ts[d] = __shfl_sync(0xffffffffu, T[d], src);
+    const double rcs = __shfl_sync(0xffffffffu, rc, src);
+    const bool hit = warp_image_hits(g, P, Ts, rcs, lo, hi, c, rad, lane);
+    visit(src, Ts, hit);
+    if (lane == src) cand = next();
+  }
+}
 
 __device__ __forceinline__ int warp_excl_scan(int v, int lane) {
   int x = v;
@@ -123,11 +192,15 @@ __global__ void k_brick_count(GGeom g, const double *pos, const int *species, in
   brick_box(g, b, lo, hi);
   double c[3], rad;
   brick_sphere(g, lo, hi, c, rad);
+  BrickPts P;
+  brick_points(g, lo, hi, c, lane, P);
   int at = 0, ent = 0, orb = 0;
   for (int a0 = 0; a0 < g.natoms; a0 += 32) {
-    int I = a0 + lane;
+    const int I = a0 + lane;
     int cnt = 0;
-    if (I < g.natoms) cnt = brick_atom_images(g, pos, species, I, lo, hi, c, rad, NoEmit());
+    warp_atom_images(g, pos, species, a0, lane, lo, hi, c, rad, P, [&](int src, const double *, bool hit) {
+      if (hit && lane == src) ++cnt;
+    });
     const int slots = unfold ? cnt : (cnt > 0);
     at += (int)warp_sum_ll(slots);
     ent += (int)warp_sum_ll(cnt);
@@ -188,7 +261,9 @@ __global__ void k_brick_scan(long long nb, const int *n_at, const int *n_ent, co
   }
 }
 
-// One warp per brick: writes slots (atom, column, first entry) and entries (image shifts).
+// One warp per brick: writes slots (atom, column, first entry) and entries (image shifts): the
+// images are visited twice in the same order, to count them (offsets of each atom's slots and
+// entries) and to write them.
 __global__ void k_brick_fill(GGeom g, const double *pos, const int *species, int unfold, const long long *at_off,
                              const long long *ent_off, int *s_atom, int *s_col, long long *s_ent, double *e_shift,
                              unsigned *err) {
@@ -199,37 +274,44 @@ __global__ void k_brick_fill(GGeom g, const double *pos, const int *species, int
   brick_box(g, b, lo, hi);
   double c[3], rad;
   brick_sphere(g, lo, hi, c, rad);
+  BrickPts P;
+  brick_points(g, lo, hi, c, lane, P);
   long long slot = at_off[b], ent = ent_off[b];
   const long long slot_end = at_off[b + 1], ent_end = ent_off[b + 1];
   int col = 0;
   for (int a0 = 0; a0 < g.natoms; a0 += 32) {
-    int I = a0 + lane;
+    const int I = a0 + lane;
     int cnt = 0;
-    if (I < g.natoms) cnt = brick_atom_images(g, pos, species, I, lo, hi, c, rad, NoEmit());
+    warp_atom_images(g, pos, species, a0, lane, lo, hi, c, rad, P, [&](int src, const double *, bool hit) {
+      if (hit && lane == src) ++cnt;
+    });
     const int nsl = unfold ? cnt : (cnt > 0);  // slots of this atom
-    int my_slot = warp_excl_scan(nsl, lane);
-    int my_ent = warp_excl_scan(cnt, lane);
-    int no = (cnt > 0) ? g.sp[species[I]].norb : 0;
-    int my_col = warp_excl_scan(nsl * no, lane);
+    const int my_slot = warp_excl_scan(nsl, lane);
+    const int my_ent = warp_excl_scan(cnt, lane);
+    const int no = (cnt > 0) ? g.sp[species[I]].norb : 0;
+    const int my_col = warp_excl_scan(nsl * no, lane);
     if (cnt > 0) {
-      long long k = slot + my_slot;
-      long long e0 = ent + my_ent;
+      const long long k = slot + my_slot;
+      const long long e0 = ent + my_ent;
       for (int j = 0; j < nsl; ++j)
         if (k + j < slot_end) {
           s_atom[k + j] = I;
           s_col[k + j] = col + my_col + j * no;
           s_ent[k + j] = e0 + j;
         }
-      long long e = e0;
-      brick_atom_images(g, pos, species, I, lo, hi, c, rad, [&](const double *T) {
-        if (e < ent_end) {
-          e_shift[3 * e + 0] = T[0];
-          e_shift[3 * e + 1] = T[1];
-          e_shift[3 * e + 2] = T[2];
-        }
-        ++e;
-      });
     }
+    long long e = ent + my_ent;
+    if (__any_sync(0xffffffffu, cnt > 0))
+      warp_atom_images(g, pos, species, a0, lane, lo, hi, c, rad, P, [&](int src, const double *T, bool hit) {
+        if (hit && lane == src) {
+          if (e < ent_end) {
+            e_shift[3 * e + 0] = T[0];
+            e_shift[3 * e + 1] = T[1];
+            e_shift[3 * e + 2] = T[2];
+          }
+          ++e;
+        }
+      });
     slot += warp_sum_ll(nsl);
     ent += warp_sum_ll(cnt);
     col += (int)warp_sum_ll(nsl * no);

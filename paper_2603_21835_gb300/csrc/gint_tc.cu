@@ -2379,6 +2379,9 @@ void gint_tc_free(gint_handle *h) {
 // brick order so that the float64 reduction order is deterministic).
 int gint_tc_prepare(gint_handle *h) {
   gint_tc_free(h);
+  h->tc_at_off.clear();  // set again once every layout below is built
+  h->tc_ent_off.clear();
+  h->tc_satom.clear();
   const GGeom &g = h->geom;
   const int na_tot = g.natoms;
   // D tiles: roundup(norb(I), 8) x porb(J) per pair
@@ -2516,6 +2519,39 @@ int gint_tc_prepare(gint_handle *h) {
   h->tc_bytes += (nb + 1) * (long long)sizeof(long long) + std::max<long long>(plan_off[nb], 1) * 16;
   TC_CHECK(cudaMemcpy(h->plan_off_dev, plan_off.data(), (nb + 1) * sizeof(long long), cudaMemcpyHostToDevice));
   // (bricks beyond the kernels' capacity get no records: compute calls report GINT_ECAPACITY)
+  if (nb > 0 && h->max_brick_atoms <= kMAXA && h->max_brick_ent <= kMAXE && h->max_brick_porb <= kNPMAX) {
+    TC_CHECK(cudaMemset(h->err_word, 0, sizeof(unsigned)));
+    k_build_plans<<<(unsigned)nb, 128>>>(h->geom, static_cast<const GCell &>(h->geom), h->nbr(), h->tile_off_dev,
+                                         h->plan_off_dev, reinterpret_cast<uint32_t *>(h->plan), h->err_word);
+    TC_CHECK(cudaGetLastError());
+    TC_CHECK(cudaDeviceSynchronize());
+    unsigned err = 0;
+    TC_CHECK(cudaMemcpy(&err, h->err_word, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (err) return GINT_EDEVICE;
+  }
+  satom.resize(h->nslots);
+  h->tc_at_off.swap(at_off);
+  h->tc_ent_off.swap(ent_off);
+  h->tc_satom.swap(satom);
+  return GINT_OK;
+}
+
+// New positions, neighbour lists rebuilt: when every brick keeps its slots (the same atoms in the
+// same order) and its entry count, the D tile layout, the scratch ranges and the per-pair
+// contribution lists stay valid and only the plan records (entry positions relative to the brick)
+// change, so only k_build_plans runs again; otherwise the layouts are rebuilt (gint_tc_prepare).
+int gint_tc_refresh(gint_handle *h) {
+  const long long nb = h->geom.nbricks;
+  if (!h->Dt_hl || !h->plan || (long long)h->tc_at_off.size() != nb + 1 ||
+      (long long)h->tc_ent_off.size() != nb + 1 || (long long)h->tc_satom.size() != h->nslots)
+    return gint_tc_prepare(h);
+  std::vector<long long> at_off(nb + 1), ent_off(nb + 1);
+  std::vector<int> satom(std::max<long long>(h->nslots, 1));
+  TC_CHECK(cudaMemcpy(at_off.data(), h->b_at_off, (nb + 1) * sizeof(long long), cudaMemcpyDeviceToHost));
+  TC_CHECK(cudaMemcpy(ent_off.data(), h->b_ent_off, (nb + 1) * sizeof(long long), cudaMemcpyDeviceToHost));
+  if (h->nslots) TC_CHECK(cudaMemcpy(satom.data(), h->s_atom, h->nslots * sizeof(int), cudaMemcpyDeviceToHost));
+  satom.resize(h->nslots);
+  if (at_off != h->tc_at_off || ent_off != h->tc_ent_off || satom != h->tc_satom) return gint_tc_prepare(h);
   if (nb > 0 && h->max_brick_atoms <= kMAXA && h->max_brick_ent <= kMAXE && h->max_brick_porb <= kNPMAX) {
     TC_CHECK(cudaMemset(h->err_word, 0, sizeof(unsigned)));
     k_build_plans<<<(unsigned)nb, 128>>>(h->geom, static_cast<const GCell &>(h->geom), h->nbr(), h->tile_off_dev,

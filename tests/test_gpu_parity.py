@@ -295,3 +295,38 @@ def test_water_cluster_with_eight_column_atoms(torch_cuda):
         ftol = FTOL_ABS[prec] if FTOL_ABS[prec] is not None else 1e-11 * np.abs(ref_F).max()
         assert np.abs(F - ref_F).max() <= ftol, prec
     g.close()
+
+
+@pytest.mark.parametrize("sigma", [1e-6, 0.08])
+def test_moved_positions_match_a_fresh_handle(torch_cuda, sigma):
+    """gint_set_positions within the skin: a move so small that every brick keeps its atoms (only the
+    plan records are rebuilt; a stale record would be off by about the move, 1e-6, against 1e-13
+    allowed) and one that changes bricks' atom sets (layouts rebuilt; the pair set kept from
+    creation can hold more blocks than a fresh handle's, which can change max|D| and so the float16
+    scales: compared at the mixed-precision tolerance).  Either way rho, H and the forces also match
+    the oracle at the new positions."""
+    import dataclasses
+
+    import torch
+
+    from paper_2603_21835_gb300 import gint as G
+
+    w = inputs.config_workload("si8_g48")
+    pos = w.system.pos + np.random.default_rng(11).normal(0.0, sigma, w.system.pos.shape)
+    moved = dataclasses.replace(w.system, pos=pos)
+    g = G.Gint(w.system, skin=0.5)
+    g.set_positions(torch.from_numpy(np.ascontiguousarray(pos)).cuda())
+    f = G.Gint(moved, skin=0.5)
+    out = []
+    for h in (g, f):
+        rho, H, F, _ = _run(G, h, h.dense_to_blocks(w.D), w.V, G.F16X3, torch)
+        h.sync()
+        out.append((rho, h.blocks_to_dense(H), F))
+        h.close()
+    (rg, Hg, Fg), (rf, Hf, Ff) = out
+    same, fsame = (1e-13, 1e-12) if sigma < 1e-3 else (TOL["f16x3"], FTOL_ABS["f16x3"])
+    assert _rel(rg, rf) <= same and _rel(Hg, Hf) <= same and np.abs(Fg - Ff).max() <= fsame
+    o = Oracle(moved)
+    assert _rel(rg, o.rho(w.D).reshape(rg.shape)) <= TOL["f16x3"]
+    assert _rel(Hg, o.vlocal(w.V)) <= TOL["f16x3"]
+    assert np.abs(Fg - o.force(w.D, w.V)).max() <= FTOL_ABS["f16x3"]
