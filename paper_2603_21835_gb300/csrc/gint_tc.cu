@@ -2431,6 +2431,11 @@ int gint_tc_prepare(gint_handle *h) {
   std::vector<long long> ent_off(nb + 1);
   TC_CHECK(cudaMemcpy(ent_off.data(), h->b_ent_off, (nb + 1) * sizeof(long long), cudaMemcpyDeviceToHost));
   std::vector<long long> plan_off(nb + 1, 0);  // plan records, 16-byte units
+  // the bricks' slot-pair tables (global pair index or -1, row slot major), from the neighbour build
+  std::vector<long long> bp_off(nb + 1);
+  std::vector<int> bpair(std::max<long long>(h->npairtab, 1));
+  TC_CHECK(cudaMemcpy(bp_off.data(), h->b_pair_off, (nb + 1) * sizeof(long long), cudaMemcpyDeviceToHost));
+  if (h->npairtab) TC_CHECK(cudaMemcpy(bpair.data(), h->b_pair, h->npairtab * sizeof(int), cudaMemcpyDeviceToHost));
   // pass 1: sizes and counts
   for (long long b = 0; b < nb; ++b) {
     const long long s0 = at_off[b], s1 = at_off[b + 1];
@@ -2451,9 +2456,11 @@ int gint_tc_prepare(gint_handle *h) {
       rest -= no[a];
     }
     hs_off[b + 1] = hs_off[b] + ((tot + 3) & ~3LL);  // 16-byte aligned ranges (one bulk copy each)
-    for (long long a = s0; a < s1; ++a)
-      for (long long c = a; c < s1; ++c) {
-        const int p = find_pair(satom[a], satom[c]);
+    const long long nab = s1 - s0;
+    const int *bpb = bpair.data() + bp_off[b];
+    for (long long a = 0; a < nab; ++a)
+      for (long long c = a; c < nab; ++c) {
+        const int p = bpb[a * nab + c];
         if (p >= 0) cnt[p + 1]++;
       }
   }
@@ -2481,10 +2488,12 @@ int gint_tc_prepare(gint_handle *h) {
       cum += no[s - s0];
     }
     long long rowst = 0, cumno_a = 0;
-    for (long long a = 0; a < s1 - s0; ++a) {
+    const long long nab = s1 - s0;
+    const int *bpb = bpair.data() + bp_off[b];
+    for (long long a = 0; a < nab; ++a) {
       long long cumno_c = cumno_a;
-      for (long long c = a; c < s1 - s0; ++c) {
-        const int p = find_pair(satom[s0 + a], satom[s0 + c]);
+      for (long long c = a; c < nab; ++c) {
+        const int p = bpb[a * nab + c];
         if (p >= 0) src[pstart[p] + fill[p]++] = hs_off[b] + rowst + (long long)no[a] * (cumno_c - cumno_a);
         cumno_c += no[c];
       }
