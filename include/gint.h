@@ -150,7 +150,9 @@ int gint_memory(const gint_handle *h, long long *device_bytes);
 /* Replaces the atom positions from a DEVICE array [natoms][3] and rebuilds the neighbour
  * lists on the device (the BigGrid neighbour relation of paper Sec. 3.3.1 and Fig. 2, renewed as
  * the ions move in the Ehrenfest dynamics of Sec. 2).  The pair set stays fixed: GINT_ESKIN if a
- * pair outside it now overlaps.  Synchronises the stream. */
+ * pair outside it now overlaps.  When every brick keeps its atoms, only the tensor-core path's
+ * per-brick plan records are rebuilt; otherwise its layouts are rebuilt as at creation.  Results
+ * equal those of a handle created at the new positions.  Synchronises the stream. */
 int gint_set_positions(gint_handle *h, const double *pos_dev, void *stream);
 
 /* Density pass: rho [n1 n2 n3] (device, overwritten) from D blocks (device). */
