@@ -366,23 +366,66 @@ __global__ void k_brick_pairs(GGeom g, const double *pos, const int *species, co
   }
 }
 
-// Exact algorithmic work: W = sum_g n_g^2 with n_g the orbitals covering point g.
+// Exact algorithmic work: W = sum_g n_g^2 with n_g the orbitals covering point g.  One CTA per
+// brick, one thread per point.  The brick's entries and the slots' screening bounds (at most kCwE
+// entries and kCwS slots; larger bricks take the plain float64 loop) are staged in shared memory,
+// the entries as float32 offsets from the brick centre, and each (point, entry)
+// distance is screened in float32 as in warp_image_hits, the float64 test deciding points in the
+// thin shell around the sphere: the same coverage, so the same W, as the per-entry float64 loop.
+constexpr int kCwE = 256, kCwS = 64;
 __global__ void k_count_work(GGeom g, const long long *at_off, const int *s_atom, const long long *s_ent,
                              const double *e_shift, const int *species, double *W) {
   const long long b = blockIdx.x;
   const int p = threadIdx.x;
+  __shared__ float ex[kCwE], ey[kCwE], ez[kCwE], sin2[kCwS], sout2[kCwS];
+  __shared__ double sc[4];  // brick centre and bounding radius
+  if (p == 0) {
+    int lo[3], hi[3];
+    brick_box(g, b, lo, hi);
+    brick_sphere(g, lo, hi, sc, sc[3]);
+  }
+  __syncthreads();
+  const double c[3] = {sc[0], sc[1], sc[2]}, rad = sc[3];
+  const long long s0 = at_off[b], s1 = at_off[b + 1];
+  const long long E0 = s1 > s0 ? s_ent[s0] : 0, E1 = s1 > s0 ? s_ent[s1] : 0;
+  const bool staged = E1 - E0 <= kCwE && s1 - s0 <= kCwS;
+  if (staged) {
+    for (long long e = E0 + p; e < E1; e += blockDim.x) {
+      ex[e - E0] = (float)(e_shift[3 * e] - c[0]);
+      ey[e - E0] = (float)(e_shift[3 * e + 1] - c[1]);
+      ez[e - E0] = (float)(e_shift[3 * e + 2] - c[2]);
+    }
+    for (long long s = s0 + p; s < s1; s += blockDim.x) {
+      const GSpecies &S = g.sp[species[s_atom[s]]];
+      const double ext = 2.0 * S.rcut + 4.0 * rad, m = 4e-6 * ext * ext + 1e-6 * S.rcut2;
+      sin2[s - s0] = (float)(S.rcut2 - m);
+      sout2[s - s0] = (float)(S.rcut2 + m);
+    }
+  }
+  __syncthreads();
   int i, j, k;
   double acc = 0;
   if (brick_point(g, b, p, i, j, k)) {
     double r[3];
     grid_point(g, i, j, k, r);
+    const float px = (float)(r[0] - c[0]), py = (float)(r[1] - c[1]), pz = (float)(r[2] - c[2]);
     int n = 0;
-    for (long long s = at_off[b]; s < at_off[b + 1]; ++s) {
+    for (long long s = s0; s < s1; ++s) {
       const GSpecies &S = g.sp[species[s_atom[s]]];
+      const float in2 = staged ? sin2[s - s0] : 0.f, out2 = staged ? sout2[s - s0] : 0.f;
       bool cov = false;
       for (long long e = s_ent[s]; e < s_ent[s + 1] && !cov; ++e) {
-        double dx = r[0] - e_shift[3 * e], dy = r[1] - e_shift[3 * e + 1], dz = r[2] - e_shift[3 * e + 2];
-        cov = dx * dx + dy * dy + dz * dz < S.rcut2;
+        bool exact = !staged;
+        if (staged) {
+          const float dx = px - ex[e - E0], dy = py - ey[e - E0], dz = pz - ez[e - E0];
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 < in2) cov = true;
+          else exact = r2 < out2;
+        }
+        if (exact) {
+          double dx = r[0] - e_shift[3 * e], dy = r[1] - e_shift[3 * e + 1], dz = r[2] - e_shift[3 * e + 2];
+          cov = dx * dx + dy * dy + dz * dz < S.rcut2;
+        }
       }
       if (cov) n += S.norb;
     }
