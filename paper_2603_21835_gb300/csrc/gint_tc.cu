@@ -36,6 +36,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "gint_handle.cuh"
@@ -2427,7 +2428,6 @@ int gint_tc_prepare(gint_handle *h) {
   std::vector<long long> hs_off(nb + 1, 0);
   std::vector<long long> cnt(h->npairs + 1, 0);
   int npmax = 0;
-  std::vector<int> no;  // orbital counts (norb) of the brick's slots (local-H scratch tiles hold no padding)
   std::vector<long long> ent_off(nb + 1);
   TC_CHECK(cudaMemcpy(ent_off.data(), h->b_ent_off, (nb + 1) * sizeof(long long), cudaMemcpyDeviceToHost));
   std::vector<long long> plan_off(nb + 1, 0);  // plan records, 16-byte units
@@ -2436,33 +2436,66 @@ int gint_tc_prepare(gint_handle *h) {
   std::vector<int> bpair(std::max<long long>(h->npairtab, 1));
   TC_CHECK(cudaMemcpy(bp_off.data(), h->b_pair_off, (nb + 1) * sizeof(long long), cudaMemcpyDeviceToHost));
   if (h->npairtab) TC_CHECK(cudaMemcpy(bpair.data(), h->b_pair, h->npairtab * sizeof(int), cudaMemcpyDeviceToHost));
-  // pass 1: sizes and counts
-  for (long long b = 0; b < nb; ++b) {
-    const long long s0 = at_off[b], s1 = at_off[b + 1];
-    int cur = 0;
-    long long cum = 0;
-    no.assign(s1 - s0, 0);
-    for (long long s = s0; s < s1; ++s) {
-      const GSpecies &S = g.sp[h->species_host[satom[s]]];
-      cur = place_slot(cur, S.porb) + S.porb;
-      no[s - s0] = S.norb;
-      cum += S.norb;
-    }
-    npmax = std::max(npmax, (cur + 15) & ~15);
-    plan_off[b + 1] = plan_off[b] + plan_words((int)(s1 - s0), (int)(ent_off[b + 1] - ent_off[b]), (cur + 15) & ~15) / 4;
-    long long tot = 0, rest = cum;
-    for (long long a = 0; a < s1 - s0; ++a) {
-      tot += (long long)no[a] * rest;
-      rest -= no[a];
-    }
-    hs_off[b + 1] = hs_off[b] + ((tot + 3) & ~3LL);  // 16-byte aligned ranges (one bulk copy each)
-    const long long nab = s1 - s0;
-    const int *bpb = bpair.data() + bp_off[b];
-    for (long long a = 0; a < nab; ++a)
-      for (long long c = a; c < nab; ++c) {
-        const int p = bpb[a * nab + c];
-        if (p >= 0) cnt[p + 1]++;
+  // pass 1: sizes and counts, the bricks split into nthr contiguous ranges on host threads; each
+  // range counts its own contributions per pair (tcnt), so that pass 2 can place them in brick
+  // order without a shared cursor
+  const int nthr = (int)std::max<long long>(1, std::min<long long>({16, (long long)std::thread::hardware_concurrency(),
+                                                                      (nb + 1023) / 1024}));
+  std::vector<long long> bstart(nthr + 1);
+  for (int k = 0; k <= nthr; ++k) bstart[k] = nb * k / nthr;
+  std::vector<std::vector<long long>> tcnt(nthr, std::vector<long long>(h->npairs, 0));
+  std::vector<long long> hs_sz(nb), plan_sz(nb);
+  std::vector<int> np_thr(nthr, 0);
+  auto pass1 = [&](int k) {
+    std::vector<int> nol;
+    long long *tc = tcnt[k].data();
+    for (long long b = bstart[k]; b < bstart[k + 1]; ++b) {
+      const long long s0 = at_off[b], s1 = at_off[b + 1];
+      int cur = 0;
+      long long cum = 0;
+      nol.assign(s1 - s0, 0);
+      for (long long s = s0; s < s1; ++s) {
+        const GSpecies &S = g.sp[h->species_host[satom[s]]];
+        cur = place_slot(cur, S.porb) + S.porb;
+        nol[s - s0] = S.norb;
+        cum += S.norb;
       }
+      np_thr[k] = std::max(np_thr[k], (cur + 15) & ~15);
+      plan_sz[b] = plan_words((int)(s1 - s0), (int)(ent_off[b + 1] - ent_off[b]), (cur + 15) & ~15) / 4;
+      long long tot = 0, rest = cum;
+      for (long long a = 0; a < s1 - s0; ++a) {
+        tot += (long long)nol[a] * rest;
+        rest -= nol[a];
+      }
+      hs_sz[b] = (tot + 3) & ~3LL;  // 16-byte aligned ranges (one bulk copy each)
+      const long long nab = s1 - s0;
+      const int *bpb = bpair.data() + bp_off[b];
+      for (long long a = 0; a < nab; ++a)
+        for (long long c = a; c < nab; ++c) {
+          const int p = bpb[a * nab + c];
+          if (p >= 0) tc[p]++;
+        }
+    }
+  };
+  auto run_threads = [&](auto &&fn) {  // ranges 1.. on new threads (serially if none can start), 0 here
+    std::vector<std::thread> th;
+    int k = 1;
+    try {
+      for (; k < nthr; ++k) th.emplace_back(fn, k);
+    } catch (...) {
+    }
+    for (int r = k; r < nthr; ++r) fn(r);
+    fn(0);
+    for (auto &t : th) t.join();
+  };
+  run_threads(pass1);
+  for (long long b = 0; b < nb; ++b) {
+    plan_off[b + 1] = plan_off[b] + plan_sz[b];
+    hs_off[b + 1] = hs_off[b] + hs_sz[b];
+  }
+  for (int k = 0; k < nthr; ++k) {
+    npmax = std::max(npmax, np_thr[k]);
+    for (long long p = 0; p < h->npairs; ++p) cnt[p + 1] += tcnt[k][p];
   }
   h->max_brick_porb = npmax;
   h->hs_elems = hs_off[nb];
@@ -2478,29 +2511,42 @@ int gint_tc_prepare(gint_handle *h) {
         uoff.push_back(uoff.back() + cnt[p + 1]);
       }
   std::vector<long long> src(std::max<long long>(uoff.back(), 1));
-  std::vector<long long> fill(h->npairs, 0);
-  for (long long b = 0; b < nb; ++b) {
-    const long long s0 = at_off[b], s1 = at_off[b + 1];
-    no.assign(s1 - s0, 0);
-    long long cum = 0;
-    for (long long s = s0; s < s1; ++s) {
-      no[s - s0] = g.sp[h->species_host[satom[s]]].norb;
-      cum += no[s - s0];
-    }
-    long long rowst = 0, cumno_a = 0;
-    const long long nab = s1 - s0;
-    const int *bpb = bpair.data() + bp_off[b];
-    for (long long a = 0; a < nab; ++a) {
-      long long cumno_c = cumno_a;
-      for (long long c = a; c < nab; ++c) {
-        const int p = bpb[a * nab + c];
-        if (p >= 0) src[pstart[p] + fill[p]++] = hs_off[b] + rowst + (long long)no[a] * (cumno_c - cumno_a);
-        cumno_c += no[c];
-      }
-      rowst += (long long)no[a] * (cum - cumno_a);
-      cumno_a += no[a];
+  // each range's first place in every pair's list: the pair's start plus the earlier ranges' counts
+  for (long long p = 0; p < h->npairs; ++p) {
+    long long at = pstart[p];
+    for (int k = 0; k < nthr; ++k) {
+      const long long n = tcnt[k][p];
+      tcnt[k][p] = at;
+      at += n;
     }
   }
+  auto pass2 = [&](int k) {
+    std::vector<int> nol;
+    long long *cur = tcnt[k].data();
+    for (long long b = bstart[k]; b < bstart[k + 1]; ++b) {
+      const long long s0 = at_off[b], s1 = at_off[b + 1];
+      nol.assign(s1 - s0, 0);
+      long long cum = 0;
+      for (long long s = s0; s < s1; ++s) {
+        nol[s - s0] = g.sp[h->species_host[satom[s]]].norb;
+        cum += nol[s - s0];
+      }
+      long long rowst = 0, cumno_a = 0;
+      const long long nab = s1 - s0;
+      const int *bpb = bpair.data() + bp_off[b];
+      for (long long a = 0; a < nab; ++a) {
+        long long cumno_c = cumno_a;
+        for (long long c = a; c < nab; ++c) {
+          const int p = bpb[a * nab + c];
+          if (p >= 0) src[cur[p]++] = hs_off[b] + rowst + (long long)nol[a] * (cumno_c - cumno_a);
+          cumno_c += nol[c];
+        }
+        rowst += (long long)nol[a] * (cum - cumno_a);
+        cumno_a += nol[a];
+      }
+    }
+  };
+  run_threads(pass2);
   h->nupper = (int)upair.size();
   if (cudaMalloc(&h->hs_brick_off, (nb + 1) * sizeof(long long)) != cudaSuccess ||
       cudaMalloc(&h->hs, std::max<long long>(h->hs_elems, 1) * sizeof(float)) != cudaSuccess ||
