@@ -53,7 +53,7 @@ constexpr int kMAXE = 160;       // (atom, image) entries of a brick
 constexpr int kRC = 16;          // density chunk width (one f16 K step)
 constexpr long long kWaitNs = 2000000000LL;  // bounded mbarrier waits: 2 s
 constexpr unsigned char kNoSlot = 255;
-constexpr int kMmaWarp = 5;  // lane 0 issues the density MMAs
+constexpr int kMmaWarp = 5;  // the warp that runs the density MMA loop (one elected lane issues)
 constexpr float kFxScaleD = 1.f / 16.f;  // fixed-point D scale relative to the floating split's
 constexpr uint32_t kHTail = 2048;  // >= 15 core matrices of 128 bytes read above the last local-H operand rows
 // density phase B roles: epilogue groups of four warps (warps 0-3, 6-9), the MMA warp (5), and the
